@@ -1,0 +1,164 @@
+"""Pins of the oracle's charges, forces and integrators: finite differences,
+conservation laws, textbook integrator behaviour and the O(dt^2) agreement
+with Born-Oppenheimer MD (Sec. IV)."""
+
+import dataclasses
+
+import numpy as np
+import pytest
+
+from workloads import (ModelParams, XLParams, TYPE_O, TYPE_H, config1_system,
+                       molecular_water, thermal_velocities)
+from oracle import tb, density, observables, md
+
+P = ModelParams()
+# kappa rescaling for the molecular pin systems: their charge response has
+# largest eigenvalue ~4.3, and the K = 5 recursion is stable for
+# kappa (1 + lambda) below ~3.6, so kappa0 = 1.82 is rescaled by 0.15.
+XL_PIN = dataclasses.replace(XLParams(), kappa_scale=0.15)
+
+
+def _water_molecule(box=30.0, r=0.96):
+    th = np.deg2rad(104.5)
+    O = np.array([10.0, 10.0, 10.0])
+    R = np.array([O, O + r * np.array([np.sin(th / 2), np.cos(th / 2), 0]),
+                  O + r * np.array([-np.sin(th / 2), np.cos(th / 2), 0])])
+    return R, np.array([TYPE_O, TYPE_H, TYPE_H], dtype=np.int32), box
+
+
+def test_mulliken_neutrality():
+    """Sum_i q_i = 2 Tr D - N_e = 0 when Tr D = N_occ."""
+    s = config1_system()
+    h = tb.build_h(s.R, s.types, s.box, P)
+    G = tb.build_gamma(s.R, s.box, P)
+    H = tb.build_H(h, G, s.types, np.zeros(s.natoms))
+    D = density.density_T0(H, int(s.n_occ(P))).D
+    q = observables.mulliken(D, s.types, P)
+    assert abs(q.sum()) < 1e-10
+    # a hand count for one O and one H
+    offs = tb.orbital_offsets(s.types)
+    assert q[0] == pytest.approx(2 * np.trace(D[offs[0]:offs[1], offs[0]:offs[1]]) - 6.0)
+    j = s.natoms - 1
+    assert q[j] == pytest.approx(2 * D[offs[j], offs[j]] - 1.0)
+
+
+@pytest.mark.parametrize("which", ["molecule", "random24"])
+def test_forces_are_minus_energy_gradient_at_fixed_n(which):
+    """F = -dE/dR at fixed n with D = theta(mu0 - H[n]) recomputed at every
+    displaced geometry: central differences of the potential energy."""
+    if which == "molecule":
+        R, types, box = _water_molecule()
+        n_aux = np.array([1.2, -0.5, -0.7])
+        nocc = 4
+    else:
+        s = config1_system()
+        R, types, box = s.R, s.types, s.box
+        n_aux = 0.3 * np.sin(np.arange(s.natoms))
+        n_aux -= n_aux.mean()
+        nocc = int(s.n_occ(P))
+
+    def energy(Rx):
+        H, G, res, q, pairs = md.electronic_state(Rx, types, box, P, n_aux, nocc)
+        return observables.potential_energy(Rx, types, box, P, res.D, q, n_aux, pairs)
+
+    H, G, res, q, pairs = md.electronic_state(R, types, box, P, n_aux, nocc)
+    F = observables.forces(R, types, box, P, res.D, q, n_aux, pairs)
+    h = 1e-5
+    atoms = range(len(types)) if which == "molecule" else [0, 5, 9, 17]
+    for a in atoms:
+        for k in range(3):
+            Rp, Rm = R.copy(), R.copy()
+            Rp[a, k] += h
+            Rm[a, k] -= h
+            fd = -(energy(Rp) - energy(Rm)) / (2 * h)
+            assert F[a, k] == pytest.approx(fd, rel=2e-6, abs=2e-6)
+    # no net force (translation invariance)
+    assert np.allclose(F.sum(axis=0), 0.0, atol=1e-9)
+
+
+def test_energy_at_scf_is_the_scc_tb_energy():
+    """At n = q: E = 2 Tr[hD] + 1/2 q^T gamma q (+ E_pair)."""
+    R, types, box = _water_molecule()
+    q, fr, it = md.scf(R, types, box, P, 4)
+    assert it > 0
+    h = tb.build_h(R, types, box, P)
+    G = tb.build_gamma(R, box, P)
+    E = observables.potential_energy(R, types, box, P, fr.D, q, q)
+    assert E == pytest.approx(2 * np.sum(h * fr.D) + 0.5 * q @ G @ q + tb.pair_energy(R, box, P))
+
+
+def test_velocity_verlet_harmonic_energy_error_is_second_order():
+    """Velocity Verlet on a harmonic oscillator: the energy error is O(dt^2)."""
+    k, m = 3.0, 2.0
+    conv = 9.648533e-3
+
+    def run(dt, T=40.0):
+        x, v = np.array([[1.0, 0, 0]]), np.zeros((1, 3))
+        F = -k * x
+        E0 = 0.5 * k * 1.0
+        err = 0.0
+        for _ in range(int(round(T / dt))):
+            v = md.velocity_verlet_kick(v, F, np.array([m]), dt)
+            x = x + dt * v
+            F = -k * x
+            v = md.velocity_verlet_kick(v, F, np.array([m]), dt)
+            E = 0.5 * k * float(np.sum(x * x)) + 0.5 * m * float(np.sum(v * v)) / conv
+            err = max(err, abs(E - E0))
+        return err
+
+    e1, e2 = run(0.4), run(0.2)
+    assert e1 / e2 == pytest.approx(4.0, rel=0.1)
+
+
+def test_modified_verlet_fixed_point_and_decay():
+    """sum c_k = 0, so a constant history n = q is a fixed point of Eq. Verl_n;
+    a perturbation decays for kappa_eff below the K = 5 stability limit."""
+    xl = XLParams()
+    assert sum(xl.c) == 0.0
+    q = np.array([0.3, -0.1, -0.2])
+    hist = [q.copy() for _ in range(xl.K + 1)]
+    assert np.allclose(md.modified_verlet_n(hist, q, xl), q, atol=1e-15)
+    for kappa_eff in (0.5, 1.82, 3.0):
+        x = dataclasses.replace(xl, kappa_scale=kappa_eff / xl.kappa0)
+        hist = [np.array([1.0])] + [np.zeros(1) for _ in range(xl.K)]
+        for _ in range(4000):
+            hist = [md.modified_verlet_n(hist, np.zeros(1), x)] + hist[:-1]
+        assert abs(hist[0][0]) < 1e-3
+    x = dataclasses.replace(xl, kappa_scale=4.2 / xl.kappa0)
+    hist = [np.array([1.0])] + [np.zeros(1) for _ in range(xl.K)]
+    for _ in range(200):
+        hist = [md.modified_verlet_n(hist, np.zeros(1), x)] + hist[:-1]
+    assert abs(hist[0][0]) > 1e3
+
+
+def test_xlbomd_conserves_energy_and_tracks_charges():
+    """Fast-QMMD on a molecular pin system: E_tot fluctuates at the meV level
+    without drift and n follows q (Fig. 2 idea)."""
+    s = molecular_water(1, 12.0, seed=0)
+    M = s.masses(P)
+    v0 = thermal_velocities(M, 300.0, seed=100)
+    tr = md.xlbomd(s.R, s.types, s.box, P, XL_PIN, v0, M, s.n_occ(P), 120)
+    E = np.array(tr.E_tot)
+    sigma, drift = md.energy_drift(E, XL_PIN.dt, s.natoms)
+    assert np.max(np.abs(E - E[0])) < 5e-3
+    assert abs(drift) < 0.05
+    assert max(np.max(np.abs(a - b)) for a, b in zip(tr.n, tr.q)) < 0.05
+    # the kinetic energy really changes (the molecule vibrates)
+    assert np.ptp(tr.KE) > 10 * np.max(np.abs(E - E[0]))
+
+
+def test_xlbomd_deviation_from_bomd_is_second_order_in_dt():
+    """Sec. IV: charges and forces of Fast-QMMD deviate from BOMD as O(dt^2)."""
+    s = molecular_water(1, 12.0, seed=0)
+    M = s.masses(P)
+    v0 = thermal_velocities(M, 300.0, seed=100)
+    T = 8.0
+    dev = []
+    for dt in (0.2, 0.1):
+        xl = dataclasses.replace(XL_PIN, dt=dt)
+        nst = int(round(T / dt))
+        a = md.xlbomd(s.R, s.types, s.box, P, xl, v0, M, s.n_occ(P), nst)
+        b = md.bomd(s.R, s.types, s.box, P, dt, v0, M, s.n_occ(P), nst)
+        dq = np.sqrt(np.mean([np.mean((x - y) ** 2) for x, y in zip(a.q, b.q)]))
+        dev.append(dq)
+    assert dev[0] / dev[1] == pytest.approx(4.0, rel=0.3)

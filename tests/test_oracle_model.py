@@ -1,0 +1,152 @@
+"""Pins of the oracle's tight-binding model (App. D) against closed forms,
+finite differences and invariants that do not reuse the oracle's formulas."""
+
+import numpy as np
+import pytest
+
+from workloads import ModelParams, TYPE_O, TYPE_H, config1_system
+from oracle import tb
+
+P = ModelParams()
+
+
+def _fd(fun, x, h=1e-6):
+    return (fun(x + h) - fun(x - h)) / (2 * h)
+
+
+@pytest.mark.parametrize("radial", [tb.hopping_radial, tb.pair_radial])
+def test_tail_matches_C2_at_r1_and_vanishes_at_rcut(radial):
+    """App. D: t(R) matches value, first and second derivative of zeta at R1 and
+    sets all three to zero at R_cut."""
+    r = radial(P)
+    val = lambda x: r(x)[0]
+    r1, rc = P.r1, P.rcut
+    e = 1e-7
+    # value and slope are continuous at r1
+    assert val(r1 - e) == pytest.approx(val(r1 + e), rel=1e-6)
+    assert r(r1 - e)[1] == pytest.approx(r(r1 + e)[1], rel=1e-5)
+    # second derivative continuous at r1 (one-sided central differences)
+    h = 1e-4
+    d2_left = (val(r1 - 2 * h) - 2 * val(r1 - h) + val(r1)) / h**2
+    d2_right = (val(r1) - 2 * val(r1 + h) + val(r1 + 2 * h)) / h**2
+    assert d2_left == pytest.approx(d2_right, rel=2e-3)
+    # value, slope and curvature vanish at rc
+    assert abs(val(rc - 1e-9)) < 1e-12 * max(1.0, abs(val(r1)))
+    assert abs(r(rc - 1e-9)[1]) < 1e-9
+    h = 1e-3
+    d2_end = (val(rc - 2 * h) - 2 * val(rc - h) + val(rc)) / h**2
+    assert abs(d2_end) < 2e-2 * abs(d2_left)
+    assert r(rc + 0.1) == (0.0, 0.0)
+
+
+@pytest.mark.parametrize("radial", [tb.hopping_radial, tb.pair_radial, tb.gamma_radial])
+def test_radial_derivatives_match_finite_differences(radial):
+    r = radial(P)
+    for x in [0.3, 0.9, 1.7, 3.0, 4.99, 5.01, 5.5, 5.95]:
+        assert r(x)[1] == pytest.approx(_fd(lambda y: r(y)[0], x), rel=1e-6, abs=1e-10)
+
+
+def test_gamma_onsite_is_hubbard_u_and_decays_like_coulomb():
+    g = tb.gamma_radial(P)
+    assert g(0.0)[0] == pytest.approx(P.hubbard_u, rel=1e-15)
+    # at r >> k/U (and well inside the window) g -> k/r times the window
+    r = 0.6
+    x = r / P.gamma_cut
+    w = (1 - x) ** 4 * (1 + 4 * x)
+    a = P.coulomb_k / P.hubbard_u
+    assert g(r)[0] == pytest.approx(P.coulomb_k / np.hypot(r, a) * w)
+    assert g(P.gamma_cut)[0] == 0.0
+
+
+def test_gamma_matrix_positive_definite():
+    """gamma is a product of positive-definite radial kernels, so the periodic
+    gamma matrix is positive definite (the SCC functional is convex)."""
+    s = config1_system()
+    G = tb.build_gamma(s.R, s.box, P)
+    assert np.allclose(G, G.T)
+    assert np.linalg.eigvalsh(G).min() > 0.5
+
+
+def test_slater_koster_diatomic_along_z():
+    """Closed-form two-centre blocks for a bond along +z (l = (0, 0, 1))."""
+    r = 1.3
+    V = P.t_hop * np.exp(-r / P.r_decay)
+    Vr = tb.hopping_radial(P)
+    blk, _ = tb.sk_block(TYPE_O, TYPE_O, np.array([0.0, 0.0, r]), Vr)
+    expect = np.zeros((4, 4))
+    expect[0, 0] = -V             # ss-sigma
+    expect[0, 3] = V              # s -> pz: +l_z Vsp
+    expect[3, 0] = -V             # pz -> s: -l_z Vsp
+    expect[3, 3] = V              # pz pz: pp-sigma
+    expect[1, 1] = expect[2, 2] = -V   # px px, py py: pp-pi
+    assert np.allclose(blk, expect, atol=1e-15)
+    blk, _ = tb.sk_block(TYPE_H, TYPE_O, np.array([0.0, 0.0, r]), Vr)
+    assert np.allclose(blk, [[-V, 0, 0, V]])
+    blk, _ = tb.sk_block(TYPE_O, TYPE_H, np.array([0.0, 0.0, r]), Vr)
+    assert np.allclose(blk, [[-V], [0], [0], [-V]])
+
+
+def test_slater_koster_reciprocity_and_derivative():
+    """h_{a,b}(d) = h_{b,a}(-d)^T, and d(block)/dd matches finite differences."""
+    Vr = tb.hopping_radial(P)
+    rng = np.random.default_rng(3)
+    for ta, tb_ in [(TYPE_O, TYPE_O), (TYPE_O, TYPE_H), (TYPE_H, TYPE_O), (TYPE_H, TYPE_H)]:
+        d = rng.normal(size=3)
+        d *= 1.4 / np.linalg.norm(d)
+        b1, db = tb.sk_block(ta, tb_, d, Vr)
+        b2, _ = tb.sk_block(tb_, ta, -d, Vr)
+        assert np.allclose(b1, b2.T, atol=1e-15)
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = 1e-6
+            fd = (tb.sk_block(ta, tb_, d + e, Vr)[0] - tb.sk_block(ta, tb_, d - e, Vr)[0]) / 2e-6
+            assert np.allclose(db[:, :, k], fd, rtol=1e-6, atol=1e-10)
+
+
+def test_h_spectrum_invariant_under_rigid_rotation():
+    """A wrong angular factor in the Slater-Koster table breaks rotational
+    invariance of the spectrum of an isolated cluster."""
+    rng = np.random.default_rng(1)
+    R = rng.uniform(0, 3.0, size=(5, 3)) + 20.0
+    types = np.array([TYPE_O, TYPE_O, TYPE_H, TYPE_H, TYPE_O], dtype=np.int32)
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    R2 = (R - 21.5) @ Q.T + 21.5
+    e1 = np.linalg.eigvalsh(tb.build_h(R, types, 100.0, P))
+    e2 = np.linalg.eigvalsh(tb.build_h(R2, types, 100.0, P))
+    assert np.allclose(e1, e2, atol=1e-12)
+
+
+def test_H_is_h_plus_charge_shift_on_every_orbital_of_the_atom():
+    s = config1_system()
+    h = tb.build_h(s.R, s.types, s.box, P)
+    G = tb.build_gamma(s.R, s.box, P)
+    assert np.allclose(h, h.T)
+    n = np.linspace(-0.5, 0.5, s.natoms)
+    H = tb.build_H(h, G, s.types, n)
+    offs = tb.orbital_offsets(s.types)
+    d = np.diag(H - h)
+    for i in range(s.natoms):
+        assert np.allclose(d[offs[i]:offs[i + 1]], sum(G[i, j] * n[j] for j in range(s.natoms)))
+    assert np.allclose(H - np.diag(np.diag(H)), h - np.diag(np.diag(h)))
+
+
+def test_periodic_images_small_box():
+    """Two atoms in a box smaller than the cut-off see several images; the
+    hopping matches an explicit sum over lattice translations."""
+    box = 4.0
+    R = np.array([[0.2, 0.3, 0.1], [1.1, 0.4, 0.3]])
+    types = np.array([TYPE_H, TYPE_H], dtype=np.int32)
+    h = tb.build_h(R, types, box, P)
+    Vr = tb.hopping_radial(P)
+    ref01 = 0.0
+    ref00 = 0.0
+    for a in range(-3, 4):
+        for b in range(-3, 4):
+            for c in range(-3, 4):
+                T = box * np.array([a, b, c])
+                r01 = np.linalg.norm(R[1] - R[0] + T)
+                ref01 += -Vr(r01)[0]
+                if (a, b, c) != (0, 0, 0):
+                    ref00 += -Vr(np.linalg.norm(T))[0]
+    assert h[0, 1] == pytest.approx(ref01, rel=1e-12)
+    assert h[0, 0] == pytest.approx(P.eps_s_H + ref00, rel=1e-12)
