@@ -1,0 +1,225 @@
+/*
+ * tbmd.h -- C ABI of the GB300 (sm_103a) Fast-QMMD / SP2 density-matrix library.
+ *
+ * Implements the per-step hot path of optimization-free extended-Lagrangian
+ * Born-Oppenheimer MD for orthogonal self-consistent-charge tight binding
+ * (Niklasson & Cawkwell, "Fast method for quantum mechanical molecular
+ * dynamics"): the Hamiltonian H[n] (App. D, Eq. DFTB_2 with S = I,
+ * Eq. EL_Orth_c), the density matrix D = theta(mu0 I - H[n]) by SP2
+ * purification (Sec. III.B, App. D.2) or the Fermi operator at T_e > 0
+ * (Eq. EL_4c, Eq. DM_perp), Mulliken charges (App. D), forces and energy
+ * (Eq. EL_Orth_a, Eq. Etot_Orth) and the XL-BOMD integration of R and of the
+ * auxiliary charges n (velocity Verlet; Eq. Verl_n).
+ *
+ * Conventions
+ *   - Plain C, every function returns int: TB_OK (0) or a negative TB_ERR_*.
+ *     No C++ exception crosses the ABI.
+ *   - Units: eV, Angstrom, amu, fs.  Velocities in A/fs.
+ *   - Every array pointer is a DEVICE pointer owned by the caller unless a
+ *     comment says otherwise.  Matrices are dense, row-major, symmetric,
+ *     leading dimension = n, orbitals grouped by atom (O-like: s, px, py, pz;
+ *     H-like: s).
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t passed as
+ *     void*; NULL = legacy default stream).  A call returns after enqueueing:
+ *     the return value reports argument and launch errors only.  Convergence
+ *     and numerical status are written to the device-side report structs,
+ *     valid after the stream has been synchronised.
+ *   - Entry points that need scratch memory take a caller-allocated device
+ *     workspace and its size; the matching *_workspace_size query gives the
+ *     minimum.  The library itself calls no cudaMalloc.
+ *   - A context is bound to the device current when it was created; calls
+ *     must be made with that device current.
+ */
+#ifndef TBMD_H
+#define TBMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TB_OK                  0
+#define TB_ERR_ARG            -1  /* invalid argument (null pointer, bad size, workspace too small) */
+#define TB_ERR_NOT_CONVERGED  -2  /* iteration cap reached (report status only) */
+#define TB_ERR_GAP            -3  /* no gap at N_occ: trace cannot reach N_occ (report status only) */
+#define TB_ERR_OOM            -4  /* capacity or admission budget exceeded */
+#define TB_ERR_TIMEOUT        -5  /* a device-side wait gave up after its time limit */
+#define TB_ERR_CUDA           -6  /* a CUDA runtime call or launch failed */
+#define TB_ERR_UNSUPPORTED    -7  /* option not supported on this device/build */
+
+/* atom types */
+#define TB_TYPE_O 0  /* s, px, py, pz */
+#define TB_TYPE_H 1  /* s */
+
+/* arithmetic of the purification GEMMs */
+#define TB_PREC_FP64    0  /* FP64 FMA (the plain FP64 path) */
+#define TB_PREC_TF32    1  /* tcgen05 kind::tf32, FP32 accumulate */
+#define TB_PREC_TF32X3  2  /* tcgen05 kind::tf32 on hi/lo splits: hi*hi + hi*lo + lo*hi */
+#define TB_PREC_BF16    3  /* tcgen05 kind::f16 (bf16), FP32 accumulate */
+#define TB_PREC_BF16X3  4  /* tcgen05 kind::f16 (bf16) on hi/lo splits */
+
+typedef struct tb_ctx tb_ctx;
+
+/* Model constants of the orthogonal SCC-TB recipe (App. D).  Hopping
+ * V(r) = t_hop exp(-r/r_decay), Slater-Koster two-centre table with
+ * ss-sigma = -V, sp-sigma = +V, pp-sigma = +V, pp-pi = -V; V and the pair
+ * potential phi(r) = pair_a exp(-r/pair_rho) are replaced on [r1, rcut) by
+ * the quintic tail of App. D.  gamma(r) = coulomb_k / sqrt(r^2 + (coulomb_k/
+ * hubbard_u)^2) * w(r/gamma_cut), w(x) = (1-x)^4 (1+4x), summed over periodic
+ * images. */
+typedef struct {
+  double eps_s_O, eps_p_O, eps_s_H;   /* onsite energies */
+  double t_hop, r_decay;              /* hopping magnitude and decay length */
+  double hubbard_u, coulomb_k, gamma_cut;
+  double r1, rcut;                    /* tail start, cut-off of h and phi */
+  double n0_O, n0_H;                  /* valence electrons of the neutral atoms */
+  double pair_a, pair_rho;            /* E_pair (pair_a = 0: off) */
+} tb_params;
+
+/* A periodic system.  types and orb_off are device arrays. */
+typedef struct {
+  int natoms;                 /* N >= 1 */
+  int norb;                   /* n = orb_off[N] */
+  const int32_t* types;       /* [N] TB_TYPE_O / TB_TYPE_H */
+  const int32_t* orb_off;     /* [N+1] first orbital of atom i; orb_off[N] = n */
+  double box;                 /* cubic box side (A) > 0 */
+} tb_system;
+
+/* Options of dm_sp2. */
+typedef struct {
+  int precision;        /* TB_PREC_* of the purification GEMMs */
+  int max_iter;         /* cap on projections of the main phase, 1..120 */
+  double tol;           /* stop when Tr X - Tr X^2 <= tol (FP64 path) */
+  int refine_iters;     /* FP64 projections after a tensor-core phase, 0..4 */
+  int rule;             /* 0: X^2 when |Tr X^2 - N| <= |2Tr X - Tr X^2 - N| (look-ahead), 1: X^2 when Tr X > N */
+} tb_sp2_opts;
+
+/* Written on the device by dm_sp2 (caller-owned device memory). */
+typedef struct {
+  int status;           /* TB_OK, TB_ERR_NOT_CONVERGED, TB_ERR_GAP, TB_ERR_TIMEOUT */
+  int iters;            /* projections of the main phase */
+  int refine_iters;     /* FP64 refinement projections applied */
+  int n;                /* matrix size */
+  double eps_min, eps_max;  /* Gershgorin bounds of H */
+  double trace;         /* Tr D */
+  double idem_trace;    /* Tr D - Tr D^2 of the returned D */
+  double idem_fro;      /* ||X^2 - X||_F of the input of the last FP64 projection, -1 if none */
+  uint64_t branch_bits[2];  /* bit k: branch of main-phase projection k (1 = 2X - X^2) */
+  uint64_t refine_bits;     /* bit k: branch of refinement projection k */
+} tb_sp2_report;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on the current device.  *ctx is owned by the caller and
+ * released with tb_ctx_destroy.  Fails with TB_ERR_UNSUPPORTED when the
+ * device is not sm_103 (this build contains sm_103a code only). */
+int tb_ctx_create(tb_ctx** ctx);
+int tb_ctx_destroy(tb_ctx* ctx);
+/* Static description of a status code. */
+const char* tb_status_string(int status);
+/* Last error message recorded by the context (valid until the next call). */
+const char* tb_ctx_last_error(const tb_ctx* ctx);
+
+/* ----------------------------------------------------------- a1: H[n] build */
+
+/* H[n] = h(R) + diag(sum_l gamma_il n_l) over every orbital of atom i
+ * (App. D, Eq. DFTB_2 with S = I; Eq. EL_Orth_c).
+ *   R      [N*3] positions (any image; minimum-image convention applied)
+ *   n_aux  [N] auxiliary charges n (NULL: all zero)
+ *   H      [n*n] output, fully overwritten
+ *   gamma  [N*N] output: gamma_ij summed over periodic images, gamma_ii
+ *          includes U and the self-image terms. */
+int tb_build_H(tb_ctx* ctx, const tb_params* p, const tb_system* sys,
+               const double* R, const double* n_aux, double* H, double* gamma,
+               void* stream);
+
+/* ------------------------------------------------- a2..a6: SP2 purification */
+
+/* Minimum workspace bytes of dm_sp2 for an n x n matrix. */
+int dm_sp2_workspace_size(int n, const tb_sp2_opts* opts, size_t* bytes);
+
+/* D = theta(mu0 I - H) with Tr D = n_occ by the SP2 recursion (Sec. III.B):
+ * X0 = (eps_max I - H)/(eps_max - eps_min) from Gershgorin bounds; repeat
+ * X <- X^2 or 2X - X^2 (branch chosen by trace, opts->rule) until
+ * Tr X - Tr X^2 <= tol, then opts->refine_iters FP64 projections when the main
+ * phase ran on the tensor cores.  Traces are accumulated in FP64.
+ *   H [n*n] input (FP64), D [n*n] output (FP64), report: device, may be NULL.
+ * Branch and stop decisions are taken on the device: no host synchronisation
+ * inside.  The workspace must not be shared by concurrent calls. */
+int dm_sp2(tb_ctx* ctx, const double* H, int n, double n_occ, const tb_sp2_opts* opts,
+           double* D, void* workspace, size_t workspace_bytes, tb_sp2_report* report,
+           void* stream);
+
+/* ------------------------------------------------------------- a7: charges */
+
+/* Mulliken net charges q_i = 2 sum_{a in i} D_aa - N0_i (App. D).
+ *   D [n*n], q [N] output. */
+int mulliken(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const double* D,
+             double* q, void* stream);
+
+/* ------------------------------------------------------ a8: forces, energy */
+
+/* F = -dE/dR at fixed n and E = 2 Tr[hD] + 1/2 (2q - n)^T gamma n + E_pair
+ * (Eq. EL_Orth_a, Eq. Etot_Orth with the reading documented in the design doc).
+ *   R [N*3], D [n*n], q [N], n_aux [N], gamma [N*N] (from tb_build_H)
+ *   F [N*3] output (eV/A); energy [4] output: E_pot, 2Tr[hD], E_scc, E_pair. */
+int tb_forces(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const double* R,
+              const double* D, const double* q, const double* n_aux, const double* gamma,
+              double* F, double* energy, void* stream);
+
+/* -------------------------------------------------------- a9: XL-BOMD step */
+
+#define TB_XL_KMAX 8
+
+/* Modified Verlet with dissipation for n (Eq. Verl_n):
+ * n_{t+dt} = 2n_t - n_{t-dt} + kappa (q_t - n_t) + alpha sum_{k=0}^{K} c_k n_{t-k dt}. */
+typedef struct {
+  double dt;                 /* fs */
+  double kappa;              /* dt^2 w^2 after the rescaling factor */
+  double alpha;
+  int K;                     /* 1..TB_XL_KMAX */
+  double c[TB_XL_KMAX + 1];
+} tb_xl_params;
+
+/* Device-resident MD state.  All arrays are device memory owned by the caller. */
+typedef struct {
+  tb_system sys;
+  double n_occ;
+  double* R;            /* [N*3] */
+  double* v;            /* [N*3] A/fs */
+  double* F;            /* [N*3] force at R (valid after xlbomd_init) */
+  const double* mass;   /* [N] amu */
+  double* n_hist;       /* [(K+1)*N] ring buffer; n_t in slot (step mod (K+1)) */
+  double* q;            /* [N] Mulliken charges of the last D */
+  double* H;            /* [n*n] */
+  double* D;            /* [n*n] */
+  double* gamma;        /* [N*N] */
+  double* energies;     /* [8]: E_tot, E_pot, 2Tr[hD], E_scc, E_pair, KE, max|n-q|, step */
+  tb_sp2_report* sp2_report;  /* may be NULL */
+  void* workspace;      /* dm_sp2 workspace (dm_sp2_workspace_size(norb)) */
+  size_t workspace_bytes;
+  int64_t step;         /* steps taken; advanced by xlbomd_step */
+} tb_md_state;
+
+/* Initial state (App. D.3): SCF-converge the charges with Anderson mixing
+ * (max|q - n| <= scf_tol or scf_max_iter iterations; host-side mixing of
+ * N-vectors, synchronises the stream), set the whole n history to q and
+ * compute F and the energies.  *scf_iters_out (host) gets the iteration
+ * count or -1 when the cap was reached (the state is still usable). */
+int xlbomd_init(tb_ctx* ctx, const tb_params* p, tb_md_state* st, const tb_xl_params* xp,
+                const tb_sp2_opts* so, double scf_tol, int scf_max_iter, int* scf_iters_out,
+                void* stream);
+
+/* One Fast-QMMD step (Eqs. EL_3ax, EL_3bx; App. D.3): half kick, drift,
+ * n update (Eq. Verl_n), H[n] (tb_build_H), D (dm_sp2), q (mulliken),
+ * F and E (tb_forces), half kick, kinetic energy.  Fully asynchronous. */
+int xlbomd_step(tb_ctx* ctx, const tb_params* p, tb_md_state* st, const tb_xl_params* xp,
+                const tb_sp2_opts* so, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TBMD_H */

@@ -1,0 +1,165 @@
+// Internal declarations shared by the CUDA translation units of libtbmd.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/tbmd.h"
+
+struct tb_ctx {
+  int device;
+  int sm_count;
+  int cc_major, cc_minor;
+  PFN_cuTensorMapEncodeTiled_v12000 encode_tiled;
+  char last_error[512];
+};
+
+// Record a formatted message in the context and return `code`.
+int tb_fail(tb_ctx* ctx, int code, const char* fmt, ...);
+
+#define TB_CUDA_TRY(ctx, expr)                                                     \
+  do {                                                                             \
+    cudaError_t e_ = (expr);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return tb_fail((ctx), TB_ERR_CUDA, "%s failed: %s (%s:%d)", #expr,           \
+                     cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+  } while (0)
+
+#define TB_LAUNCH_CHECK(ctx)                                                       \
+  do {                                                                             \
+    cudaError_t e_ = cudaGetLastError();                                           \
+    if (e_ != cudaSuccess)                                                         \
+      return tb_fail((ctx), TB_ERR_CUDA, "kernel launch failed: %s (%s:%d)",       \
+                     cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+  } while (0)
+
+static inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ----------------------------------------------------------------- model
+
+// Device copy of the model constants with the App. D tail coefficients
+// precomputed on the host (closed form, see model.cu).
+struct ModelDev {
+  double eps_s_O, eps_p_O, eps_s_H;
+  double t_hop, inv_decay;
+  double U, kc, a2, gcut;
+  double r1, rcut;
+  double n0_O, n0_H;
+  double pair_a, inv_prho;
+  double Bhop[6], Bpair[6];
+  double range;  // max(rcut, gcut)
+  double box;
+};
+
+int tb_model_from_params(tb_ctx* ctx, const tb_params* p, double box, ModelDev* m);
+
+// ------------------------------------------------------------------- SP2
+
+// Device-side state of one dm_sp2 call (lives in the workspace).
+#define SP2_MAX_ITER 120
+#define SP2_MAX_REFINE 4
+struct SP2State {
+  int done;          // main phase finished (converged or capped)
+  int iters;         // projections applied in the main phase
+  int status;        // TB_OK / TB_ERR_*
+  int rdone;         // refinement finished
+  int riters;        // refinement projections applied
+  int err;           // device-side error code (timeouts)
+  int pad0, pad1;
+  double emin, emax;
+  double t1[SP2_MAX_ITER + 2];   // Tr X_k
+  double t2[SP2_MAX_ITER + 2];   // ||X_k||_F^2
+  double rt1[SP2_MAX_REFINE + 2], rt2[SP2_MAX_REFINE + 2];
+  double idem_fro;               // ||X^2 - X||_F of the last FP64 projection input
+  unsigned long long branch[2];
+  unsigned long long rbranch;
+};
+
+// Parameters of a purification step shared by the FP64 and tensor-core kernels.
+struct SP2StepArgs {
+  int n;          // true size
+  int ld;         // padded leading dimension (multiple of the tile)
+  double nocc;
+  double tol;
+  int rule;
+  int k;          // projection index within its phase
+  int max_iter;   // phase cap
+  int phase;      // 0 = main, 1 = FP64 refinement
+  int nparts_in;  // number of trace partials written by the previous kernel
+  SP2State* st;
+  const double* parts_in;   // [nparts_in * 2]
+  double* parts_out;        // [ntiles * 2]
+};
+
+// Tensor-core purification step (gemm_tc.cu).  X_in / X_out are FP32 masters
+// (ld x ld); hi/lo operand arrays of the input are read through the tensor
+// maps; the epilogue writes the FP32 master and the hi/lo operands of the
+// output.
+int sp2_tc_step(tb_ctx* ctx, int precision, const SP2StepArgs& a,
+                const CUtensorMap* map_hi, const CUtensorMap* map_lo,
+                const float* X_in, float* X_out, void* out_hi, void* out_lo,
+                cudaStream_t stream);
+int sp2_tc_num_tiles(int ld);
+int sp2_tc_tile();
+size_t sp2_tc_operand_bytes(int precision);  // bytes per element of one operand array
+
+// Encode a 2D row-major tensor map over an ld x ld operand array for the
+// tensor-core kernel (gemm_tc.cu).
+int sp2_tc_make_map(tb_ctx* ctx, int precision, const void* base, int ld, CUtensorMap* map);
+
+// ------------------------------------------------------------ utilities
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Deterministic sum of `np` partial pairs by one warp (fixed order): lane l
+// adds partials l, l+32, ..., then a fixed butterfly.  Same result in every CTA.
+__device__ __forceinline__ void warp_reduce_partials(const double* parts, int np, double* s0,
+                                                     double* s1) {
+  const int lane = threadIdx.x & 31;
+  double a = 0.0, b = 0.0;
+  for (int i = lane; i < np; i += 32) {
+    a += parts[2 * i];
+    b += parts[2 * i + 1];
+  }
+  *s0 = warp_sum(a);
+  *s1 = warp_sum(b);
+}
+
+// Decision of SP2 projection k from the traces of X_k (t1 = Tr X, t2 = Tr X^2).
+// Returns 1 when the phase stops before projection k, else 0 and sets *branch.
+// Main phase on the tensor cores also stops when the idempotency error no
+// longer falls (its floor is set by the FP32 storage of X).
+__device__ __forceinline__ int sp2_decide(const SP2StepArgs& a, double t1, double t2,
+                                          const double* hist_t1, const double* hist_t2,
+                                          bool stagnation_stop, int* branch) {
+  const double e = t1 - t2;
+  if (e <= a.tol) return 1;
+  if (a.k >= a.max_iter) return 1;
+  if (stagnation_stop && a.k >= 2) {
+    const double e2 = hist_t1[a.k - 2] - hist_t2[a.k - 2];
+    if (e < 1.0 && e > 0.5 * e2) return 1;
+  }
+  if (a.rule == 0)
+    *branch = (fabs(t2 - a.nocc) <= fabs(2.0 * t1 - t2 - a.nocc)) ? 0 : 1;
+  else
+    *branch = (t1 > a.nocc) ? 0 : 1;
+  return 0;
+}

@@ -1,0 +1,71 @@
+// Context, status strings and error recording of the C ABI.
+
+#include "common.cuh"
+
+#include <new>
+#include <string.h>
+
+int tb_fail(tb_ctx* ctx, int code, const char* fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->last_error, sizeof(ctx->last_error), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+extern "C" const char* tb_status_string(int status) {
+  switch (status) {
+    case TB_OK: return "ok";
+    case TB_ERR_ARG: return "invalid argument";
+    case TB_ERR_NOT_CONVERGED: return "not converged";
+    case TB_ERR_GAP: return "no gap at the occupation";
+    case TB_ERR_OOM: return "capacity exceeded";
+    case TB_ERR_TIMEOUT: return "device wait timed out";
+    case TB_ERR_CUDA: return "CUDA error";
+    case TB_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+extern "C" const char* tb_ctx_last_error(const tb_ctx* ctx) { return ctx ? ctx->last_error : "null context"; }
+
+extern "C" int tb_ctx_create(tb_ctx** out) {
+  if (!out) return TB_ERR_ARG;
+  *out = nullptr;
+  tb_ctx* ctx = new (std::nothrow) tb_ctx();
+  if (!ctx) return TB_ERR_OOM;
+  ctx->last_error[0] = 0;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return TB_ERR_CUDA;
+  }
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, ctx->device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return TB_ERR_CUDA;
+  }
+  ctx->sm_count = prop.multiProcessorCount;
+  ctx->cc_major = prop.major;
+  ctx->cc_minor = prop.minor;
+  if (!(prop.major == 10 && prop.minor == 3)) {
+    delete ctx;
+    return TB_ERR_UNSUPPORTED;
+  }
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  ctx->encode_tiled = (e == cudaSuccess && q == cudaDriverEntryPointSuccess)
+                          ? reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn)
+                          : nullptr;
+  *out = ctx;
+  return TB_OK;
+}
+
+extern "C" int tb_ctx_destroy(tb_ctx* ctx) {
+  delete ctx;
+  return TB_OK;
+}

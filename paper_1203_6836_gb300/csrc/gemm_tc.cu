@@ -1,0 +1,493 @@
+// Tensor-core SP2 projection (row a4): X_{k+1} = X_k^2 or 2 X_k - X_k^2
+// (Sec. III.B) as a tcgen05 GEMM on sm_103a.
+//
+// One CTA computes one 128 x 128 tile of X_k X_k (X symmetric, so both
+// operands are row blocks of X read K-major).  Warp roles (192 threads):
+//   warp 0   one thread issues TMA tile loads (128B swizzle) into a ring of
+//            shared-memory stages, completion tracked by mbarriers;
+//   warp 1   allocates the TMEM accumulator (128 lanes x 128 FP32 columns)
+//            and one thread issues tcgen05.mma (kind::f16 with bf16 or
+//            kind::tf32), committing each stage back to the producer;
+//   warps 2-5 epilogue: tcgen05.ld the accumulator, apply the SP2 branch
+//            using the FP32 master of X_k, write the FP32 master and the
+//            bf16/tf32 operand splits of X_{k+1}, and accumulate the FP64
+//            trace partials (Tr X, ||X||_F^2, ||X^2 - X||_F^2) of the tile.
+// Split precisions (x3) keep X ~ hi + lo in two operand arrays and
+// accumulate hi*hi + hi*lo + lo*hi in the same FP32 accumulator.
+//
+// Every mbarrier wait gives up after 2 s of %globaltimer time, records
+// TB_ERR_TIMEOUT in the SP2 state and unwinds (freeing TMEM) instead of
+// hanging.
+
+#include "common.cuh"
+
+#include <cuda_bf16.h>
+
+namespace {
+
+constexpr int BM = 128, BN = 128;
+constexpr int TILE_BYTES = 128 * 128;  // 128 rows x 128 bytes
+constexpr int kThreads = 192;
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+template <int P>
+struct Prec {
+  static constexpr bool tf32 = (P == TB_PREC_TF32 || P == TB_PREC_TF32X3);
+  static constexpr bool split = (P == TB_PREC_TF32X3 || P == TB_PREC_BF16X3);
+  static constexpr int eb = tf32 ? 4 : 2;          // operand bytes
+  static constexpr int bk = 128 / eb;              // elements per 128-byte row
+  static constexpr int uk = 32 / eb;               // K of one MMA instruction
+  static constexpr int nop = split ? 2 : 1;        // operand arrays
+  static constexpr int stage_bytes = 2 * nop * TILE_BYTES;
+  static constexpr int stages = split ? 3 : 6;
+  static constexpr int smem_bytes = stages * stage_bytes + 1024;
+};
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: true when the phase completed, false on abort/timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtime();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtime() - t0 > kWaitNs) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+      "[%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(2) << 61;
+  return d;
+}
+// Instruction descriptor: D = F32, A/B format `fmt` (bf16 = 1, tf32 = 2),
+// both K-major, N = 128, M = 128.
+__host__ __device__ constexpr uint32_t idesc(uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+template <bool TF32>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  if constexpr (TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(id), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(id), "r"(acc)
+        : "memory");
+  }
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+      "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+      "[%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+        "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+        "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+        "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Operand split of a row segment of 32 FP32 values into hi (and lo).
+template <int P>
+__device__ __forceinline__ void store_operands(const float (&y)[32], void* hi_row, void* lo_row) {
+  if constexpr (Prec<P>::tf32) {
+    uint4* h = reinterpret_cast<uint4*>(hi_row);
+    uint4* l = reinterpret_cast<uint4*>(lo_row);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      float hv[4], lv[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        hv[t] = to_tf32(y[4 * j + t]);
+        lv[t] = to_tf32(y[4 * j + t] - hv[t]);
+      }
+      h[j] = make_uint4(__float_as_uint(hv[0]), __float_as_uint(hv[1]), __float_as_uint(hv[2]),
+                        __float_as_uint(hv[3]));
+      if constexpr (Prec<P>::split)
+        l[j] = make_uint4(__float_as_uint(lv[0]), __float_as_uint(lv[1]), __float_as_uint(lv[2]),
+                          __float_as_uint(lv[3]));
+    }
+  } else {
+    uint4* h = reinterpret_cast<uint4*>(hi_row);
+    uint4* l = reinterpret_cast<uint4*>(lo_row);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const float a0 = y[8 * j + 2 * t], a1 = y[8 * j + 2 * t + 1];
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(a0), h1 = __float2bfloat16_rn(a1);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(a0 - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(a1 - __bfloat162float(h1));
+        hw[t] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        lw[t] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+      }
+      h[j] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      if constexpr (Prec<P>::split) l[j] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+  }
+}
+
+// X0 (FP32 master) -> operand arrays, elementwise.
+template <int P>
+__global__ void __launch_bounds__(256) k_split(const float* __restrict__ X, int ld, void* hi, void* lo) {
+  const size_t segs = (size_t)ld * ld / 32;
+  for (size_t sidx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; sidx < segs;
+       sidx += (size_t)gridDim.x * blockDim.x) {
+    float y[32];
+    const float4* src = reinterpret_cast<const float4*>(X + sidx * 32);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float4 v = src[j];
+      y[4 * j] = v.x;
+      y[4 * j + 1] = v.y;
+      y[4 * j + 2] = v.z;
+      y[4 * j + 3] = v.w;
+    }
+    char* h = static_cast<char*>(hi) + sidx * 32 * Prec<P>::eb;
+    char* l = lo ? static_cast<char*>(lo) + sidx * 32 * Prec<P>::eb : h;
+    store_operands<P>(y, h, l);
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_sp2_step_tc(SP2StepArgs a, const __grid_constant__ CUtensorMap mh,
+                  const __grid_constant__ CUtensorMap ml, const float* __restrict__ Xin,
+                  float* __restrict__ Xout, void* __restrict__ ohi, void* __restrict__ olo) {
+  using C = Prec<P>;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[C::stages], empty[C::stages], tfull;
+  __shared__ uint32_t tmem_base;
+  __shared__ double s_t[3];
+  __shared__ int s_dec[2];
+  __shared__ volatile int s_abort;
+  __shared__ double s_red[4][3];
+
+  SP2State* st = a.st;
+  if (st->done || st->err) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // ---- decision for projection k from the partials of X_k (same in every CTA)
+  if (warp == 0) {
+    double x = 0, y = 0, z = 0;
+    for (int i = lane; i < a.nparts_in; i += 32) {
+      x += a.parts_in[3 * i];
+      y += a.parts_in[3 * i + 1];
+      z += a.parts_in[3 * i + 2];
+    }
+    x = warp_sum(x);
+    y = warp_sum(y);
+    z = warp_sum(z);
+    if (lane == 0) {
+      int br = 0;
+      const int stop = sp2_decide(a, x, y, st->t1, st->t2, true, &br);
+      s_t[0] = x;
+      s_t[1] = y;
+      s_t[2] = z;
+      s_dec[0] = stop;
+      s_dec[1] = br;
+    }
+  }
+  __syncthreads();
+  const int stop = s_dec[0], br = s_dec[1];
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    st->t1[a.k] = s_t[0];
+    st->t2[a.k] = s_t[1];
+    if (stop) {
+      st->iters = a.k;
+      st->done = 1;
+    } else if (br) {
+      st->branch[a.k >> 6] |= 1ull << (a.k & 63);
+    }
+  }
+  if (stop) return;
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int nk = a.ld / C::bk;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&tfull, 1);
+    s_abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_base, BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ producer
+    prefetch_map(&mh);
+    if (C::split) prefetch_map(&ml);
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % C::stages;
+      if (kb >= C::stages && !mbar_wait(&empty[s], ((kb / C::stages) - 1) & 1, &s_abort)) break;
+      uint8_t* base = smem + s * C::stage_bytes;
+      mbar_expect_tx(&full[s], C::stage_bytes);
+      tma_load_2d(base, &mh, &full[s], kb * C::bk, m0);
+      tma_load_2d(base + TILE_BYTES, &mh, &full[s], kb * C::bk, n0);
+      if constexpr (C::split) {
+        tma_load_2d(base + 2 * TILE_BYTES, &ml, &full[s], kb * C::bk, m0);
+        tma_load_2d(base + 3 * TILE_BYTES, &ml, &full[s], kb * C::bk, n0);
+      }
+      issued = kb + 1;
+    }
+    if (s_abort) {
+      // let every issued copy land before the CTA can exit
+      for (int kb = (issued > C::stages ? issued - C::stages : 0); kb < issued; ++kb) {
+        const int s = kb % C::stages;
+        const unsigned long long t0 = gtime();
+        while (!mbar_try(&full[s], (kb / C::stages) & 1) && gtime() - t0 < kWaitNs) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    constexpr uint32_t id = idesc(C::tf32 ? 2u : 1u);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % C::stages;
+      if (!mbar_wait(&full[s], (kb / C::stages) & 1, &s_abort)) break;
+      tc_fence_after();
+      const uint32_t base = smem_u32(smem + s * C::stage_bytes);
+#pragma unroll
+      for (int ks = 0; ks < C::bk / C::uk; ++ks) {
+        const uint32_t koff = ks * 32;
+        const uint64_t ah = sdesc(base + koff);
+        const uint64_t bh = sdesc(base + TILE_BYTES + koff);
+        umma<C::tf32>(tmem, ah, bh, id, (kb | ks) != 0);
+        if constexpr (C::split) {
+          const uint64_t al = sdesc(base + 2 * TILE_BYTES + koff);
+          const uint64_t bl = sdesc(base + 3 * TILE_BYTES + koff);
+          umma<C::tf32>(tmem, ah, bl, id, 1u);
+          umma<C::tf32>(tmem, al, bh, id, 1u);
+        }
+      }
+      umma_commit(&empty[s]);
+    }
+    umma_commit(&tfull);
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ epilogue
+    double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    const int q = warp & 3;
+    const int row = 32 * q + lane;
+    if (mbar_wait(&tfull, 0, &s_abort)) {
+      tc_fence_after();
+      const size_t gr = (size_t)(m0 + row);
+      const float* xin = Xin + gr * a.ld + n0;
+      float* xout = Xout + gr * a.ld + n0;
+      char* hrow = static_cast<char*>(ohi) + (gr * a.ld + n0) * C::eb;
+      char* lrow = olo ? static_cast<char*>(olo) + (gr * a.ld + n0) * C::eb : hrow;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t v[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + 32 * c, v);
+        float y[32];
+        const float4* xi = reinterpret_cast<const float4*>(xin + 32 * c);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float4 x4 = xi[j];
+          const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const float cxx = __uint_as_float(v[4 * j + t]);
+            const float x = xs[t];
+            const float yy = br ? fmaf(2.0f, x, -cxx) : cxx;
+            y[4 * j + t] = yy;
+            t2 += (double)yy * (double)yy;
+            const double dd = (double)cxx - (double)x;
+            t3 += dd * dd;
+          }
+        }
+        if (m0 == n0) {
+          const int dc = row - 32 * c;
+          if (dc >= 0 && dc < 32) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j == dc) t1 += (double)y[j];
+          }
+        }
+        float4* xo = reinterpret_cast<float4*>(xout + 32 * c);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) xo[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
+        store_operands<P>(y, hrow + 32 * c * C::eb, lrow + 32 * c * C::eb);
+      }
+    }
+    t1 = warp_sum(t1);
+    t2 = warp_sum(t2);
+    t3 = warp_sum(t3);
+    if (lane == 0) {
+      s_red[q][0] = t1;
+      s_red[q][1] = t2;
+      s_red[q][2] = t3;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 64) {
+    const int cta = blockIdx.y * gridDim.x + blockIdx.x;
+    a.parts_out[3 * cta] = s_red[0][0] + s_red[1][0] + s_red[2][0] + s_red[3][0];
+    a.parts_out[3 * cta + 1] = s_red[0][1] + s_red[1][1] + s_red[2][1] + s_red[3][1];
+    a.parts_out[3 * cta + 2] = s_red[0][2] + s_red[1][2] + s_red[2][2] + s_red[3][2];
+    if (s_abort) atomicExch(&st->err, TB_ERR_TIMEOUT);
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    if (s_abort && lane == 0) {
+      // the issuer always commits tfull after its loop: wait (bounded) until
+      // every issued MMA has retired before the accumulator is freed
+      const unsigned long long t0 = gtime();
+      while (!mbar_try(&tfull, 0) && gtime() - t0 < kWaitNs) {
+      }
+    }
+    __syncwarp();
+    tmem_dealloc(tmem, BN);
+  }
+}
+
+template <int P>
+int launch_step(tb_ctx* ctx, const SP2StepArgs& a, const CUtensorMap* mh, const CUtensorMap* ml,
+                const float* Xin, float* Xout, void* ohi, void* olo, cudaStream_t s) {
+  using C = Prec<P>;
+  if (a.k < 0) {
+    // split X0 into operand arrays
+    k_split<P><<<1184, 256, 0, s>>>(Xin, a.ld, ohi, olo);
+    TB_LAUNCH_CHECK(ctx);
+    return TB_OK;
+  }
+  static bool attr_set = false;
+  if (!attr_set) {
+    TB_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sp2_step_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          C::smem_bytes));
+    attr_set = true;
+  }
+  const dim3 grid(a.ld / BN, a.ld / BM);
+  k_sp2_step_tc<P><<<grid, kThreads, C::smem_bytes, s>>>(a, *mh, *ml, Xin, Xout, ohi, olo);
+  TB_LAUNCH_CHECK(ctx);
+  return TB_OK;
+}
+
+}  // namespace
+
+int sp2_tc_tile() { return BM; }
+int sp2_tc_num_tiles(int ld) { return (ld / BM) * (ld / BN); }
+size_t sp2_tc_operand_bytes(int precision) {
+  return (precision == TB_PREC_TF32 || precision == TB_PREC_TF32X3) ? 4 : 2;
+}
+
+int sp2_tc_make_map(tb_ctx* ctx, int precision, const void* base, int ld, CUtensorMap* map) {
+  if (!ctx->encode_tiled) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
+  const bool tf = precision == TB_PREC_TF32 || precision == TB_PREC_TF32X3;
+  const size_t eb = tf ? 4 : 2;
+  const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)ld};
+  const cuuint64_t strides[1] = {(cuuint64_t)(ld * eb)};
+  const cuuint32_t box[2] = {(cuuint32_t)(128 / eb), 128};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = ctx->encode_tiled(map, tf ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                                 2, const_cast<void*>(base), dims, strides, box, estr,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return tb_fail(ctx, TB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return TB_OK;
+}
+
+int sp2_tc_step(tb_ctx* ctx, int precision, const SP2StepArgs& a, const CUtensorMap* mh,
+                const CUtensorMap* ml, const float* Xin, float* Xout, void* ohi, void* olo,
+                cudaStream_t s) {
+  switch (precision) {
+    case TB_PREC_TF32: return launch_step<TB_PREC_TF32>(ctx, a, mh, ml, Xin, Xout, ohi, olo, s);
+    case TB_PREC_TF32X3: return launch_step<TB_PREC_TF32X3>(ctx, a, mh, ml, Xin, Xout, ohi, olo, s);
+    case TB_PREC_BF16: return launch_step<TB_PREC_BF16>(ctx, a, mh, ml, Xin, Xout, ohi, olo, s);
+    case TB_PREC_BF16X3: return launch_step<TB_PREC_BF16X3>(ctx, a, mh, ml, Xin, Xout, ohi, olo, s);
+    default: return tb_fail(ctx, TB_ERR_ARG, "precision %d has no tensor-core path", precision);
+  }
+}

@@ -1,0 +1,293 @@
+// XL-BOMD (Fast-QMMD) integration on device-resident state (row a9).
+//
+// Nuclei: velocity Verlet with F = -dE/dR at fixed n (App. D.3).
+// Auxiliary charges: modified Verlet with dissipation, Eq. Verl_n,
+//   n_{t+dt} = 2 n_t - n_{t-dt} + kappa (q_t - n_t) + alpha sum_{k=0}^{K} c_k n_{t-k dt},
+// with the Mulliken charges q_t of D[n_t] in place of sigma_t (Eq. EL_Orth_b).
+// The n history lives in a (K+1)-slot ring buffer; n_t sits in slot
+// (step mod (K+1)).  A step enqueues: half kick + drift, n update, H[n]
+// build, SP2, Mulliken, forces/energy, half kick + kinetic energy; nothing
+// synchronises the host.
+//
+// Initialisation (App. D.3): SCF-converged charges to a high degree, then
+// the whole history set to q.  The SCF loop runs the same device kernels
+// and mixes the N-vector of charges on the host with Anderson/Pulay mixing.
+
+#include "common.cuh"
+
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+namespace {
+
+constexpr double kEvAmuToAFs2 = 9.648533e-3;  // 1 eV/(A amu) in A/fs^2
+
+__global__ void k_kick_drift(int N, double* __restrict__ v, const double* __restrict__ F,
+                             const double* __restrict__ mass, double dt, double* __restrict__ R) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double s = 0.5 * dt * kEvAmuToAFs2 / mass[i];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double vv = v[3 * i + c] + s * F[3 * i + c];
+    v[3 * i + c] = vv;
+    R[3 * i + c] += dt * vv;
+  }
+}
+
+// Eq. Verl_n.  slot(j) = (t - j) mod (K+1) holds n_{t-j}; the result goes to
+// slot (t+1) mod (K+1) = slot(K), read before it is overwritten.
+__global__ void k_n_update(int N, double* __restrict__ hist, int64_t t, int K, const double* __restrict__ q,
+                           double kappa, double alpha, tb_xl_params xp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int S = K + 1;
+  double nv[TB_XL_KMAX + 1];
+  for (int j = 0; j <= K; ++j) {
+    const int slot = (int)(((t - j) % S + S) % S);
+    nv[j] = hist[(size_t)slot * N + i];
+  }
+  double diss = 0.0;
+  for (int j = 0; j <= K; ++j) diss += xp.c[j] * nv[j];
+  const double n_new = 2.0 * nv[0] - nv[1] + kappa * (q[i] - nv[0]) + alpha * diss;
+  const int out = (int)(((t + 1) % S + S) % S);
+  hist[(size_t)out * N + i] = n_new;
+}
+
+// Second half kick, kinetic energy, E_tot and max|n - q| in one block.
+__global__ void __launch_bounds__(256) k_kick_energy(int N, double* __restrict__ v, const double* __restrict__ F,
+                                                     const double* __restrict__ mass, double dt, int kick,
+                                                     const double* __restrict__ n_cur,
+                                                     const double* __restrict__ q, double* __restrict__ E,
+                                                     int64_t step) {
+  __shared__ double s_ke[8], s_dq[8];
+  double ke = 0.0, dq = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const double s = 0.5 * dt * kEvAmuToAFs2 / mass[i];
+    double v2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double vv = v[3 * i + c];
+      if (kick) {
+        vv += s * F[3 * i + c];
+        v[3 * i + c] = vv;
+      }
+      v2 += vv * vv;
+    }
+    ke += 0.5 * mass[i] * v2 / kEvAmuToAFs2;
+    dq = fmax(dq, fabs(n_cur[i] - q[i]));
+  }
+  ke = warp_sum(ke);
+  dq = warp_max(dq);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s_ke[w] = ke;
+    s_dq[w] = dq;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += s_ke[k];
+      b = fmax(b, s_dq[k]);
+    }
+    E[5] = a;
+    E[0] = a + E[1];
+    E[6] = b;
+    E[7] = (double)step;
+  }
+}
+
+__global__ void k_fill_hist(int N, int S, const double* __restrict__ q, double* __restrict__ hist) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  for (int s = 0; s < S; ++s) hist[(size_t)s * N + i] = q[i];
+}
+
+int check_state(tb_ctx* ctx, const tb_md_state* st, const tb_xl_params* xp, const tb_sp2_opts* so) {
+  if (!st || !xp || !so) return tb_fail(ctx, TB_ERR_ARG, "null state/params/options");
+  if (xp->K < 1 || xp->K > TB_XL_KMAX) return tb_fail(ctx, TB_ERR_ARG, "K = %d outside 1..%d", xp->K, TB_XL_KMAX);
+  if (!st->R || !st->v || !st->F || !st->mass || !st->n_hist || !st->q || !st->H || !st->D || !st->gamma ||
+      !st->energies || !st->workspace)
+    return tb_fail(ctx, TB_ERR_ARG, "null array in tb_md_state");
+  if (!(xp->dt > 0)) return tb_fail(ctx, TB_ERR_ARG, "dt must be > 0");
+  return TB_OK;
+}
+
+inline const double* slot_ptr(const tb_md_state* st, int K, int64_t t) {
+  const int S = K + 1;
+  const int slot = (int)(((t % S) + S) % S);
+  return st->n_hist + (size_t)slot * st->sys.natoms;
+}
+
+// H[n] -> D -> q -> F, E for the current positions and the given n.
+int electronic_step(tb_ctx* ctx, const tb_params* p, tb_md_state* st, const tb_sp2_opts* so,
+                    const double* n_aux, cudaStream_t s) {
+  int rc = tb_build_H(ctx, p, &st->sys, st->R, n_aux, st->H, st->gamma, s);
+  if (rc) return rc;
+  rc = dm_sp2(ctx, st->H, st->sys.norb, st->n_occ, so, st->D, st->workspace, st->workspace_bytes,
+              st->sp2_report, s);
+  if (rc) return rc;
+  rc = mulliken(ctx, p, &st->sys, st->D, st->q, s);
+  if (rc) return rc;
+  return tb_forces(ctx, p, &st->sys, st->R, st->D, st->q, n_aux, st->gamma, st->F, st->energies + 1, s);
+}
+
+// Anderson / Pulay mixing of x (the charges n) with residual f = q - n:
+// minimise ||f_k - dF g|| over g (normal equations, Gaussian elimination with
+// partial pivoting and a small ridge), then x_new = x_k - dX g + beta (f_k - dF g).
+void anderson(const std::vector<std::vector<double>>& xs, const std::vector<std::vector<double>>& fs,
+              double beta, std::vector<double>& out) {
+  const size_t N = xs.back().size();
+  const int m = (int)xs.size() - 1;
+  const std::vector<double>& xk = xs.back();
+  const std::vector<double>& fk = fs.back();
+  out.assign(N, 0.0);
+  if (m <= 0) {
+    for (size_t i = 0; i < N; ++i) out[i] = xk[i] + beta * fk[i];
+    return;
+  }
+  std::vector<std::vector<double>> dF(m, std::vector<double>(N)), dX(m, std::vector<double>(N));
+  for (int j = 0; j < m; ++j)
+    for (size_t i = 0; i < N; ++i) {
+      dF[j][i] = fs[j + 1][i] - fs[j][i];
+      dX[j][i] = xs[j + 1][i] - xs[j][i];
+    }
+  std::vector<double> A(m * m), b(m), g(m);
+  double diag_max = 0.0;
+  for (int r = 0; r < m; ++r) {
+    for (int c = 0; c < m; ++c) {
+      double s = 0.0;
+      for (size_t i = 0; i < N; ++i) s += dF[r][i] * dF[c][i];
+      A[r * m + c] = s;
+    }
+    double s = 0.0;
+    for (size_t i = 0; i < N; ++i) s += dF[r][i] * fk[i];
+    b[r] = s;
+    diag_max = fmax(diag_max, A[r * m + r]);
+  }
+  for (int r = 0; r < m; ++r) A[r * m + r] += 1e-12 * diag_max + 1e-300;
+  // Gaussian elimination with partial pivoting
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < m; ++r)
+      if (fabs(A[r * m + c]) > fabs(A[piv * m + c])) piv = r;
+    if (piv != c) {
+      for (int k = 0; k < m; ++k) {
+        double t = A[c * m + k];
+        A[c * m + k] = A[piv * m + k];
+        A[piv * m + k] = t;
+      }
+      double t = b[c];
+      b[c] = b[piv];
+      b[piv] = t;
+    }
+    const double d = A[c * m + c];
+    if (d == 0.0) continue;
+    for (int r = c + 1; r < m; ++r) {
+      const double f = A[r * m + c] / d;
+      for (int k = c; k < m; ++k) A[r * m + k] -= f * A[c * m + k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = m - 1; r >= 0; --r) {
+    double s = b[r];
+    for (int k = r + 1; k < m; ++k) s -= A[r * m + k] * g[k];
+    g[r] = A[r * m + r] != 0.0 ? s / A[r * m + r] : 0.0;
+  }
+  for (size_t i = 0; i < N; ++i) {
+    double xb = xk[i], fb = fk[i];
+    for (int j = 0; j < m; ++j) {
+      xb -= dX[j][i] * g[j];
+      fb -= dF[j][i] * g[j];
+    }
+    out[i] = xb + beta * fb;
+  }
+}
+
+}  // namespace
+
+extern "C" int xlbomd_init(tb_ctx* ctx, const tb_params* p, tb_md_state* st, const tb_xl_params* xp,
+                           const tb_sp2_opts* so, double scf_tol, int scf_max_iter, int* scf_iters_out,
+                           void* stream) {
+  if (!ctx) return TB_ERR_ARG;
+  int rc = check_state(ctx, st, xp, so);
+  if (rc) return rc;
+  cudaStream_t s = as_stream(stream);
+  const int N = st->sys.natoms;
+  const int S = xp->K + 1;
+  // slot 0 is the working n during the SCF; the history is filled afterwards
+  double* n_dev = st->n_hist;
+  std::vector<double> n(N, 0.0), q(N), f(N), nn;
+  std::vector<std::vector<double>> xs, fs;
+  const int hist = 8;
+  const double beta = 0.2;
+  int iters = -1;
+  for (int it = 0; it < scf_max_iter; ++it) {
+    TB_CUDA_TRY(ctx, cudaMemcpyAsync(n_dev, n.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+    rc = tb_build_H(ctx, p, &st->sys, st->R, n_dev, st->H, st->gamma, s);
+    if (rc) return rc;
+    rc = dm_sp2(ctx, st->H, st->sys.norb, st->n_occ, so, st->D, st->workspace, st->workspace_bytes,
+                st->sp2_report, s);
+    if (rc) return rc;
+    rc = mulliken(ctx, p, &st->sys, st->D, st->q, s);
+    if (rc) return rc;
+    TB_CUDA_TRY(ctx, cudaMemcpyAsync(q.data(), st->q, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+    TB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    double res = 0.0;
+    for (int i = 0; i < N; ++i) {
+      f[i] = q[i] - n[i];
+      res = fmax(res, fabs(f[i]));
+    }
+    if (res <= scf_tol) {
+      iters = it;
+      break;
+    }
+    xs.push_back(n);
+    fs.push_back(f);
+    if ((int)xs.size() > hist) {
+      xs.erase(xs.begin());
+      fs.erase(fs.begin());
+    }
+    anderson(xs, fs, beta, nn);
+    n = nn;
+  }
+  if (scf_iters_out) *scf_iters_out = iters;
+  // the whole history is set to the last Mulliken charges (n = q)
+  TB_CUDA_TRY(ctx, cudaMemcpyAsync(n_dev, q.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  k_fill_hist<<<(N + 127) / 128, 128, 0, s>>>(N, S, n_dev, st->n_hist);
+  TB_LAUNCH_CHECK(ctx);
+  st->step = 0;
+  rc = electronic_step(ctx, p, st, so, slot_ptr(st, xp->K, 0), s);
+  if (rc) return rc;
+  k_kick_energy<<<1, 256, 0, s>>>(N, st->v, st->F, st->mass, xp->dt, 0, slot_ptr(st, xp->K, 0), st->q,
+                                  st->energies, 0);
+  TB_LAUNCH_CHECK(ctx);
+  // the host vectors must outlive the async copies above
+  TB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  return TB_OK;
+}
+
+extern "C" int xlbomd_step(tb_ctx* ctx, const tb_params* p, tb_md_state* st, const tb_xl_params* xp,
+                           const tb_sp2_opts* so, void* stream) {
+  if (!ctx) return TB_ERR_ARG;
+  int rc = check_state(ctx, st, xp, so);
+  if (rc) return rc;
+  cudaStream_t s = as_stream(stream);
+  const int N = st->sys.natoms;
+  const int nb = (N + 127) / 128;
+  k_kick_drift<<<nb, 128, 0, s>>>(N, st->v, st->F, st->mass, xp->dt, st->R);
+  TB_LAUNCH_CHECK(ctx);
+  k_n_update<<<nb, 128, 0, s>>>(N, st->n_hist, st->step, xp->K, st->q, xp->kappa, xp->alpha, *xp);
+  TB_LAUNCH_CHECK(ctx);
+  const int64_t t1 = st->step + 1;
+  const double* n_new = slot_ptr(st, xp->K, t1);
+  rc = electronic_step(ctx, p, st, so, n_new, s);
+  if (rc) return rc;
+  k_kick_energy<<<1, 256, 0, s>>>(N, st->v, st->F, st->mass, xp->dt, 1, n_new, st->q, st->energies, t1);
+  TB_LAUNCH_CHECK(ctx);
+  st->step = t1;
+  return TB_OK;
+}

@@ -1,0 +1,517 @@
+// SP2 purification (rows a2, a3, a4 FP64 path, a6): D = theta(mu0 I - H).
+//
+// Sec. III.B ("recursive second order spectral projection"), with the
+// reading: X0 = (eps_max I - H)/(eps_max - eps_min) from Gershgorin bounds;
+// each projection replaces X by X^2 or by 2X - X^2, the branch chosen from
+// Tr X and Tr X^2 = ||X||_F^2 (look-ahead rule: the projection whose trace
+// lands closer to N_occ); stop when Tr X - Tr X^2 <= tol.
+//
+// Device-side control: the host enqueues max_iter + 1 step kernels; kernel k
+// first reduces, in a fixed order, the trace partials written by the
+// epilogue of kernel k-1, takes the stop/branch decision (identical in every
+// CTA) and either returns at once or computes X_{k+1}.  No host
+// synchronisation happens inside dm_sp2.
+//
+// Precision paths: TB_PREC_FP64 runs every projection as an FP64 GEMM; the
+// tensor-core paths (gemm_tc.cu) keep X as an FP32 master plus bf16/tf32
+// operand splits and hand the final iterate to `refine_iters` FP64
+// projections.  Traces and their reductions are FP64 throughout.
+
+#include "common.cuh"
+
+#include <algorithm>
+
+namespace {
+
+constexpr int kF64Tile = 64;     // FP64 GEMM output tile
+constexpr int kF64K = 16;        // FP64 GEMM k-step
+constexpr int kInitTile = 64;    // X0 / conversion tile
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+struct Layout {
+  int n, ld, prec;
+  size_t off_state, off_bparts, off_parts, off_f0, off_f1, off_m0, off_m1, off_h0, off_l0, off_h1,
+      off_l1, total;
+  int max_parts;
+};
+
+Layout make_layout(int n, int prec, int refine) {
+  Layout L{};
+  L.n = n;
+  L.prec = prec;
+  const bool tc = prec != TB_PREC_FP64;
+  L.ld = round_up(std::max(n, 1), tc ? sp2_tc_tile() : kF64Tile);
+  const int t_f64 = (L.ld / kF64Tile) * (L.ld / kF64Tile);
+  const int t_init = (L.ld / kInitTile) * (L.ld / kInitTile);
+  const int t_tc = tc ? sp2_tc_num_tiles(L.ld) : 0;
+  L.max_parts = std::max(std::max(t_f64, t_init), t_tc);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o += (bytes + 1023) / 1024 * 1024;
+    return r;
+  };
+  L.off_state = take(sizeof(SP2State));
+  L.off_bparts = take(sizeof(double) * 2 * ((L.ld + 7) / 8));
+  L.off_parts = take(sizeof(double) * 3 * 2 * (size_t)L.max_parts);
+  const size_t nn = (size_t)L.ld * L.ld;
+  const bool need_f64 = !tc || refine > 0;
+  L.off_f0 = need_f64 ? take(sizeof(double) * nn) : 0;
+  L.off_f1 = need_f64 ? take(sizeof(double) * nn) : 0;
+  if (tc) {
+    const size_t ob = sp2_tc_operand_bytes(prec);
+    const bool split = prec == TB_PREC_TF32X3 || prec == TB_PREC_BF16X3;
+    L.off_m0 = take(sizeof(float) * nn);
+    L.off_m1 = take(sizeof(float) * nn);
+    L.off_h0 = take(ob * nn);
+    L.off_h1 = take(ob * nn);
+    L.off_l0 = split ? take(ob * nn) : 0;
+    L.off_l1 = split ? take(ob * nn) : 0;
+  }
+  L.total = o;
+  return L;
+}
+
+// ----------------------------------------------------------- Gershgorin bounds
+
+// Warp per row: c_i = H_ii, r_i = sum_{j != i} |H_ij|; per-block min(c - r),
+// max(c + r) into bparts.
+__global__ void __launch_bounds__(256) k_bounds(const double* __restrict__ H, int n,
+                                                double* __restrict__ bparts) {
+  __shared__ double smin[8], smax[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + warp;
+  double lo = INFINITY, hi = -INFINITY;
+  if (row < n) {
+    const double* Hr = H + (size_t)row * n;
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s += (j == row) ? 0.0 : fabs(Hr[j]);
+    s = warp_sum(s);
+    const double c = Hr[row];
+    lo = c - s;
+    hi = c + s;
+  }
+  if (lane == 0) {
+    smin[warp] = lo;
+    smax[warp] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = smin[0], b = smax[0];
+    for (int w = 1; w < 8; ++w) {
+      a = fmin(a, smin[w]);
+      b = fmax(b, smax[w]);
+    }
+    bparts[2 * blockIdx.x] = a;
+    bparts[2 * blockIdx.x + 1] = b;
+  }
+}
+
+// Every block reduces the bound partials (fixed order) and writes its tile
+// of X0 = (emax I - H)/(emax - emin), zero outside n x n, plus the tile's
+// trace partials (Tr X0, ||X0||_F^2).  Output: FP64 X (X64 != nullptr) or the
+// FP32 master of the tensor-core path (its operand split follows in gemm_tc.cu).
+__device__ __forceinline__ void block_sum3(double a, double b, double c, double* out) {
+  __shared__ double sh[3][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  if (lane == 0) {
+    sh[0][warp] = a;
+    sh[1][warp] = b;
+    sh[2][warp] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0, y = 0, z = 0;
+    for (int w = 0; w < nw; ++w) {
+      x += sh[0][w];
+      y += sh[1][w];
+      z += sh[2][w];
+    }
+    out[0] = x;
+    out[1] = y;
+    out[2] = z;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_init_x(const double* __restrict__ H, int n, int ld,
+                                                const double* __restrict__ bparts, int nbparts,
+                                                SP2State* st, double* __restrict__ X64,
+                                                float* __restrict__ X32, double* __restrict__ parts) {
+  __shared__ double s_lo, s_hi;
+  if (threadIdx.x < 32) {
+    double a = INFINITY, b = -INFINITY;
+    for (int i = threadIdx.x; i < nbparts; i += 32) {
+      a = fmin(a, bparts[2 * i]);
+      b = fmax(b, bparts[2 * i + 1]);
+    }
+    a = warp_min(a);
+    b = warp_max(b);
+    if (threadIdx.x == 0) {
+      s_lo = a;
+      s_hi = b;
+    }
+  }
+  __syncthreads();
+  const double emin = s_lo, emax = s_hi;
+  double w = emax - emin;
+  if (!(w > 0.0)) w = 1.0;  // H = c I: X0 = 0 (no gap; reported through the trace)
+  const double inv = 1.0 / w;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    st->emin = emin;
+    st->emax = emax;
+  }
+  const int r0 = blockIdx.y * kInitTile, c0 = blockIdx.x * kInitTile;
+  double t1 = 0.0, t2 = 0.0;
+  for (int e = threadIdx.x; e < kInitTile * kInitTile; e += blockDim.x) {
+    const int r = r0 + e / kInitTile, c = c0 + e % kInitTile;
+    double x = 0.0;
+    if (r < n && c < n) x = ((r == c ? emax : 0.0) - H[(size_t)r * n + c]) * inv;
+    if (X64) {
+      X64[(size_t)r * ld + c] = x;
+    } else {
+      const float xf = (float)x;
+      X32[(size_t)r * ld + c] = xf;
+      x = (double)xf;
+    }
+    if (r == c) t1 += x;
+    t2 += x * x;
+  }
+  block_sum3(t1, t2, 0.0, parts + 3 * (blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+// ------------------------------------------------------------ FP64 GEMM step
+
+// X_out = X_in^2 or 2 X_in - X_in^2 for one 64x64 output tile; 256 threads,
+// each 4x4 outputs at rows ty + 16i, cols tx + 16j; k-step 16 through shared
+// memory.  X is symmetric, so B = X is read row-major like A.
+__global__ void __launch_bounds__(256) k_sp2_step_f64(SP2StepArgs a, const double* __restrict__ X,
+                                                      double* __restrict__ Y) {
+  __shared__ double As[kF64K][kF64Tile + 1];
+  __shared__ double Bs[kF64K][kF64Tile + 1];
+  __shared__ double s_t[3];
+  __shared__ int s_dec[2];
+  SP2State* st = a.st;
+  const int done = a.phase == 0 ? st->done : st->rdone;
+  if (done || st->err) return;
+  if (threadIdx.x < 32) {
+    double t1, t2;
+    {
+      const int lane = threadIdx.x;
+      double x = 0, y = 0, z = 0;
+      for (int i = lane; i < a.nparts_in; i += 32) {
+        x += a.parts_in[3 * i];
+        y += a.parts_in[3 * i + 1];
+        z += a.parts_in[3 * i + 2];
+      }
+      t1 = warp_sum(x);
+      t2 = warp_sum(y);
+      z = warp_sum(z);
+      if (lane == 0) {
+        s_t[0] = t1;
+        s_t[1] = t2;
+        s_t[2] = z;
+        int br = 0;
+        const double* h1 = a.phase == 0 ? st->t1 : st->rt1;
+        const double* h2 = a.phase == 0 ? st->t2 : st->rt2;
+        const int stop = sp2_decide(a, t1, t2, h1, h2, false, &br);
+        s_dec[0] = stop;
+        s_dec[1] = br;
+      }
+    }
+  }
+  __syncthreads();
+  const int stop = s_dec[0], br = s_dec[1];
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    if (a.phase == 0) {
+      st->t1[a.k] = s_t[0];
+      st->t2[a.k] = s_t[1];
+      if (stop) {
+        st->iters = a.k;
+        st->done = 1;
+      } else if (br) {
+        st->branch[a.k >> 6] |= 1ull << (a.k & 63);
+      }
+    } else {
+      st->rt1[a.k] = s_t[0];
+      st->rt2[a.k] = s_t[1];
+      if (a.k > 0) st->idem_fro = sqrt(s_t[2]);
+      if (stop) {
+        st->riters = a.k;
+        st->rdone = 1;
+      } else if (br) {
+        st->rbranch |= 1ull << a.k;
+      }
+    }
+  }
+  if (stop) return;
+
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int row0 = blockIdx.y * kF64Tile, col0 = blockIdx.x * kF64Tile;
+  const int ld = a.ld;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int k0 = 0; k0 < ld; k0 += kF64K) {
+    // 64 rows x 16 k of A (rows of X) and 16 k x 64 cols of B (rows of X)
+    for (int e = threadIdx.x; e < kF64Tile * kF64K; e += 256) {
+      const int r = e / kF64K, kk = e % kF64K;
+      As[kk][r] = X[(size_t)(row0 + r) * ld + k0 + kk];
+      const int kb = e / kF64Tile, c = e % kF64Tile;
+      Bs[kb][c] = X[(size_t)(k0 + kb) * ld + col0 + c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kF64K; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
+      const double x = X[(size_t)r * ld + c];
+      const double cxx = acc[i][j];
+      const double y = br ? 2.0 * x - cxx : cxx;
+      Y[(size_t)r * ld + c] = y;
+      if (r == c) t1 += y;
+      t2 += y * y;
+      t3 += (cxx - x) * (cxx - x);
+    }
+  block_sum3(t1, t2, t3, a.parts_out + 3 * (blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+// FP32 master (buffer chosen by the main phase's iteration count) -> FP64,
+// with trace partials: the start of the FP64 refinement.
+__global__ void __launch_bounds__(256) k_to_f64(const SP2State* st, const float* __restrict__ M0,
+                                                const float* __restrict__ M1, int ld,
+                                                double* __restrict__ F, double* __restrict__ parts) {
+  const float* M = (st->iters & 1) ? M1 : M0;
+  const int r0 = blockIdx.y * kInitTile, c0 = blockIdx.x * kInitTile;
+  double t1 = 0.0, t2 = 0.0;
+  for (int e = threadIdx.x; e < kInitTile * kInitTile; e += blockDim.x) {
+    const int r = r0 + e / kInitTile, c = c0 + e % kInitTile;
+    const double x = (double)M[(size_t)r * ld + c];
+    F[(size_t)r * ld + c] = x;
+    if (r == c) t1 += x;
+    t2 += x * x;
+  }
+  block_sum3(t1, t2, 0.0, parts + 3 * (blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+// Copy the final iterate into D (n x n) and fill the report.
+__global__ void __launch_bounds__(256) k_finalize(SP2State* st, int n, int ld, int mode,
+                                                  const double* __restrict__ F0,
+                                                  const double* __restrict__ F1,
+                                                  const float* __restrict__ M0,
+                                                  const float* __restrict__ M1,
+                                                  double* __restrict__ D, double nocc,
+                                                  tb_sp2_report* rep) {
+  // mode 0: FP64 main phase; 1: FP64 refinement; 2: FP32 master, no refinement
+  const size_t total = (size_t)n * n;
+  const int sel = mode == 1 ? (st->riters & 1) : (st->iters & 1);
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / n), c = (int)(e % n);
+    double x;
+    if (mode == 2)
+      x = (double)(sel ? M1 : M0)[(size_t)r * ld + c];
+    else
+      x = (sel ? F1 : F0)[(size_t)r * ld + c];
+    D[e] = x;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && rep) {
+    double t1, t2;
+    if (mode == 1) {
+      t1 = st->rt1[st->riters];
+      t2 = st->rt2[st->riters];
+    } else {
+      t1 = st->t1[st->iters];
+      t2 = st->t2[st->iters];
+    }
+    int status = TB_OK;
+    const double e = t1 - t2;
+    if (st->err) status = st->err;
+    else if (fabs(t1 - nocc) > 0.25) status = TB_ERR_GAP;
+    else if (mode != 2 && e > 1e-6 * fmax(1.0, nocc)) status = TB_ERR_NOT_CONVERGED;
+    rep->status = status;
+    rep->iters = st->iters;
+    rep->refine_iters = mode == 1 ? st->riters : 0;
+    rep->n = n;
+    rep->eps_min = st->emin;
+    rep->eps_max = st->emax;
+    rep->trace = t1;
+    rep->idem_trace = e;
+    rep->idem_fro = mode == 1 && st->riters > 0 ? st->idem_fro : -1.0;
+    rep->branch_bits[0] = st->branch[0];
+    rep->branch_bits[1] = st->branch[1];
+    rep->refine_bits = st->rbranch;
+  }
+}
+
+}  // namespace
+
+extern "C" int dm_sp2_workspace_size(int n, const tb_sp2_opts* o, size_t* bytes) {
+  if (!o || !bytes || n < 1) return TB_ERR_ARG;
+  if (o->precision < TB_PREC_FP64 || o->precision > TB_PREC_BF16X3) return TB_ERR_ARG;
+  *bytes = make_layout(n, o->precision, o->refine_iters).total;
+  return TB_OK;
+}
+
+extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb_sp2_opts* o,
+                      double* D, void* ws, size_t ws_bytes, tb_sp2_report* rep, void* stream) {
+  if (!ctx) return TB_ERR_ARG;
+  if (!H || !D || !o || !ws) return tb_fail(ctx, TB_ERR_ARG, "null argument to dm_sp2");
+  if (n < 1) return tb_fail(ctx, TB_ERR_ARG, "n = %d", n);
+  if (o->precision < TB_PREC_FP64 || o->precision > TB_PREC_BF16X3)
+    return tb_fail(ctx, TB_ERR_ARG, "unknown precision %d", o->precision);
+  if (o->max_iter < 1 || o->max_iter > SP2_MAX_ITER)
+    return tb_fail(ctx, TB_ERR_ARG, "max_iter %d outside 1..%d", o->max_iter, SP2_MAX_ITER);
+  if (o->refine_iters < 0 || o->refine_iters > SP2_MAX_REFINE)
+    return tb_fail(ctx, TB_ERR_ARG, "refine_iters %d outside 0..%d", o->refine_iters, SP2_MAX_REFINE);
+  if (!(nocc >= 0.0) || nocc > n) return tb_fail(ctx, TB_ERR_ARG, "n_occ %g outside [0, n]", nocc);
+  const bool tc = o->precision != TB_PREC_FP64;
+  const int refine = tc ? o->refine_iters : 0;
+  const Layout L = make_layout(n, o->precision, refine);
+  if (ws_bytes < L.total)
+    return tb_fail(ctx, TB_ERR_ARG, "workspace %zu bytes < required %zu", ws_bytes, L.total);
+  if ((reinterpret_cast<uintptr_t>(ws) & 1023) != 0)
+    return tb_fail(ctx, TB_ERR_ARG, "workspace must be 1024-byte aligned");
+  cudaStream_t s = as_stream(stream);
+  char* base = static_cast<char*>(ws);
+  SP2State* st = reinterpret_cast<SP2State*>(base + L.off_state);
+  double* bparts = reinterpret_cast<double*>(base + L.off_bparts);
+  double* parts = reinterpret_cast<double*>(base + L.off_parts);
+  double* slot[2] = {parts, parts + 3 * (size_t)L.max_parts};
+  double* F0 = L.off_f0 ? reinterpret_cast<double*>(base + L.off_f0) : nullptr;
+  double* F1 = L.off_f1 ? reinterpret_cast<double*>(base + L.off_f1) : nullptr;
+  if (!tc) {
+    F0 = reinterpret_cast<double*>(base + L.off_f0);
+    F1 = reinterpret_cast<double*>(base + L.off_f1);
+  }
+  float* M[2] = {nullptr, nullptr};
+  void* Hi[2] = {nullptr, nullptr};
+  void* Lo[2] = {nullptr, nullptr};
+  if (tc) {
+    M[0] = reinterpret_cast<float*>(base + L.off_m0);
+    M[1] = reinterpret_cast<float*>(base + L.off_m1);
+    Hi[0] = base + L.off_h0;
+    Hi[1] = base + L.off_h1;
+    if (L.off_l0) {
+      Lo[0] = base + L.off_l0;
+      Lo[1] = base + L.off_l1;
+    }
+  }
+  const int ld = L.ld;
+
+  TB_CUDA_TRY(ctx, cudaMemsetAsync(st, 0, sizeof(SP2State), s));
+  const int nb = (n + 7) / 8;
+  k_bounds<<<nb, 256, 0, s>>>(H, n, bparts);
+  TB_LAUNCH_CHECK(ctx);
+  const dim3 g_init(ld / kInitTile, ld / kInitTile);
+  const int np_init = g_init.x * g_init.y;
+  k_init_x<<<g_init, 256, 0, s>>>(H, n, ld, bparts, nb, st, tc ? nullptr : F0, tc ? M[0] : nullptr,
+                                  slot[0]);
+  TB_LAUNCH_CHECK(ctx);
+
+  SP2StepArgs a{};
+  a.n = n;
+  a.ld = ld;
+  a.nocc = nocc;
+  a.rule = o->rule;
+  a.st = st;
+  if (!tc) {
+    a.tol = o->tol;
+    a.max_iter = o->max_iter;
+    a.phase = 0;
+    const dim3 g(ld / kF64Tile, ld / kF64Tile);
+    for (int k = 0; k <= o->max_iter; ++k) {
+      a.k = k;
+      a.nparts_in = k == 0 ? np_init : (int)(g.x * g.y);
+      a.parts_in = slot[k & 1];
+      a.parts_out = slot[(k + 1) & 1];
+      k_sp2_step_f64<<<g, 256, 0, s>>>(a, (k & 1) ? F1 : F0, (k & 1) ? F0 : F1);
+      TB_LAUNCH_CHECK(ctx);
+    }
+    const int fb = std::min(1184, (int)(((size_t)n * n + 255) / 256));
+    k_finalize<<<fb, 256, 0, s>>>(st, n, ld, 0, F0, F1, nullptr, nullptr, D, nocc, rep);
+    TB_LAUNCH_CHECK(ctx);
+    return TB_OK;
+  }
+
+  // tensor-core main phase: split X0 into operands, then projections
+  CUtensorMap mh[2], ml[2];
+  for (int b = 0; b < 2; ++b) {
+    int rc = sp2_tc_make_map(ctx, o->precision, Hi[b], ld, &mh[b]);
+    if (rc) return rc;
+    if (Lo[b]) {
+      rc = sp2_tc_make_map(ctx, o->precision, Lo[b], ld, &ml[b]);
+      if (rc) return rc;
+    } else {
+      ml[b] = mh[b];
+    }
+  }
+  a.tol = o->tol;
+  a.max_iter = o->max_iter;
+  a.phase = 0;
+  // k = -1 converts X0 to operands (the kernel's split-only mode)
+  {
+    SP2StepArgs c = a;
+    c.k = -1;
+    c.nparts_in = 0;
+    int rc = sp2_tc_step(ctx, o->precision, c, nullptr, nullptr, M[0], M[0], Hi[0], Lo[0], s);
+    if (rc) return rc;
+  }
+  const int ntc = sp2_tc_num_tiles(ld);
+  for (int k = 0; k <= o->max_iter; ++k) {
+    a.k = k;
+    a.nparts_in = k == 0 ? np_init : ntc;
+    a.parts_in = slot[k & 1];
+    a.parts_out = slot[(k + 1) & 1];
+    const int i = k & 1, j = (k + 1) & 1;
+    int rc = sp2_tc_step(ctx, o->precision, a, &mh[i], &ml[i], M[i], M[j], Hi[j], Lo[j], s);
+    if (rc) return rc;
+  }
+  const int fb = std::min(1184, (int)(((size_t)n * n + 255) / 256));
+  if (refine == 0) {
+    k_finalize<<<fb, 256, 0, s>>>(st, n, ld, 2, nullptr, nullptr, M[0], M[1], D, nocc, rep);
+    TB_LAUNCH_CHECK(ctx);
+    return TB_OK;
+  }
+  // FP64 refinement
+  const dim3 gc(ld / kInitTile, ld / kInitTile);
+  k_to_f64<<<gc, 256, 0, s>>>(st, M[0], M[1], ld, F0, slot[0]);
+  TB_LAUNCH_CHECK(ctx);
+  SP2StepArgs r = a;
+  r.phase = 1;
+  r.max_iter = refine;
+  r.tol = o->tol;
+  const dim3 g(ld / kF64Tile, ld / kF64Tile);
+  for (int k = 0; k <= refine; ++k) {
+    r.k = k;
+    r.nparts_in = k == 0 ? (int)(gc.x * gc.y) : (int)(g.x * g.y);
+    r.parts_in = slot[k & 1];
+    r.parts_out = slot[(k + 1) & 1];
+    k_sp2_step_f64<<<g, 256, 0, s>>>(r, (k & 1) ? F1 : F0, (k & 1) ? F0 : F1);
+    TB_LAUNCH_CHECK(ctx);
+  }
+  k_finalize<<<fb, 256, 0, s>>>(st, n, ld, 1, F0, F1, nullptr, nullptr, D, nocc, rep);
+  TB_LAUNCH_CHECK(ctx);
+  return TB_OK;
+}

@@ -1,0 +1,119 @@
+"""Device-side containers for calling libtbmd from PyTorch: torch owns the
+memory, these helpers only lay out arrays and fill the C structs."""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import tbmd
+
+NORB = {tbmd.TB_TYPE_O: 4, tbmd.TB_TYPE_H: 1}
+
+
+def orbital_offsets(types: np.ndarray) -> np.ndarray:
+    """First orbital of each atom (orbitals grouped by atom), length N + 1."""
+    counts = np.where(np.asarray(types) == tbmd.TB_TYPE_O, 4, 1)
+    return np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+
+
+class DeviceSystem:
+    """Atom types, orbital offsets and positions of one periodic system on a device."""
+
+    def __init__(self, R: np.ndarray, types: np.ndarray, box: float, device="cuda"):
+        self.device = torch.device(device)
+        self.types = torch.as_tensor(np.asarray(types, dtype=np.int32), device=self.device)
+        offs = orbital_offsets(types)
+        self.orb_off = torch.as_tensor(offs, device=self.device)
+        self.R = torch.as_tensor(np.asarray(R, dtype=np.float64), device=self.device).contiguous()
+        self.natoms = int(len(types))
+        self.norb = int(offs[-1])
+        self.box = float(box)
+        self.sys = tbmd.tb_system(natoms=self.natoms, norb=self.norb, types=self.types.data_ptr(),
+                                  orb_off=self.orb_off.data_ptr(), box=self.box)
+
+
+class Workspace:
+    """A 1024-byte aligned device buffer carved out of a torch uint8 tensor."""
+
+    def __init__(self, nbytes: int, device="cuda"):
+        self.buf = torch.empty(int(nbytes) + 1024, dtype=torch.uint8, device=device)
+        base = self.buf.data_ptr()
+        self.ptr = (base + 1023) // 1024 * 1024
+        self.nbytes = int(nbytes)
+
+
+def sp2_opts(precision: str = "fp64", max_iter: int = 100, tol: float = 1e-10, refine: int = 2,
+             rule: int = 0) -> tbmd.tb_sp2_opts:
+    return tbmd.tb_sp2_opts(precision=tbmd.PREC[precision], max_iter=max_iter, tol=tol,
+                            refine_iters=refine, rule=rule)
+
+
+def xl_params(dt: float, kappa: float, alpha: float, c) -> tbmd.tb_xl_params:
+    x = tbmd.tb_xl_params(dt=dt, kappa=kappa, alpha=alpha, K=len(c) - 1)
+    for k, ck in enumerate(c):
+        x.c[k] = float(ck)
+    return x
+
+
+def report_to_dict(buf: torch.Tensor) -> dict:
+    """Decode a tb_sp2_report held in a device uint8 tensor."""
+    raw = buf.detach().cpu().numpy().tobytes()
+    r = tbmd.tb_sp2_report.from_buffer_copy(raw[:ctypes.sizeof(tbmd.tb_sp2_report)])
+    return {"status": r.status, "iters": r.iters, "refine_iters": r.refine_iters, "n": r.n,
+            "eps_min": r.eps_min, "eps_max": r.eps_max, "trace": r.trace, "idem_trace": r.idem_trace,
+            "idem_fro": r.idem_fro,
+            "branches": [(int(r.branch_bits[k >> 6]) >> (k & 63)) & 1 for k in range(r.iters)],
+            "refine_branches": [(int(r.refine_bits) >> k) & 1 for k in range(r.refine_iters)]}
+
+
+def new_report(device="cuda") -> torch.Tensor:
+    return torch.zeros(ctypes.sizeof(tbmd.tb_sp2_report), dtype=torch.uint8, device=device)
+
+
+class DensitySolver:
+    """dm_sp2 with its workspace sized for n (reused across calls on one stream)."""
+
+    def __init__(self, ctx: tbmd.Context, n: int, opts: tbmd.tb_sp2_opts, device="cuda"):
+        self.ctx, self.n, self.opts = ctx, int(n), opts
+        self.ws = Workspace(tbmd.dm_sp2_workspace_size(n, opts), device)
+        self.report = new_report(device)
+
+    def __call__(self, H: torch.Tensor, n_occ: float, D: torch.Tensor, stream=None):
+        tbmd.dm_sp2(self.ctx, H, self.n, n_occ, self.opts, D, self.ws.ptr, self.ws.nbytes, self.report, stream)
+        return D
+
+
+class MDState:
+    """Device arrays of one XL-BOMD trajectory and its tb_md_state."""
+
+    def __init__(self, ds: DeviceSystem, v0: np.ndarray, masses: np.ndarray, n_occ: float, K: int,
+                 opts: tbmd.tb_sp2_opts):
+        dev = ds.device
+        N, n = ds.natoms, ds.norb
+        f64 = dict(dtype=torch.float64, device=dev)
+        self.ds = ds
+        self.R = ds.R
+        self.v = torch.as_tensor(np.asarray(v0, dtype=np.float64), device=dev).contiguous()
+        self.F = torch.zeros(N, 3, **f64)
+        self.mass = torch.as_tensor(np.asarray(masses, dtype=np.float64), device=dev)
+        self.n_hist = torch.zeros(K + 1, N, **f64)
+        self.q = torch.zeros(N, **f64)
+        self.H = torch.zeros(n, n, **f64)
+        self.D = torch.zeros(n, n, **f64)
+        self.gamma = torch.zeros(N, N, **f64)
+        self.energies = torch.zeros(8, **f64)
+        self.report = new_report(dev)
+        self.ws = Workspace(tbmd.dm_sp2_workspace_size(n, opts), dev)
+        self.K = K
+        self.st = tbmd.tb_md_state(
+            sys=ds.sys, n_occ=float(n_occ), R=self.R.data_ptr(), v=self.v.data_ptr(), F=self.F.data_ptr(),
+            mass=self.mass.data_ptr(), n_hist=self.n_hist.data_ptr(), q=self.q.data_ptr(),
+            H=self.H.data_ptr(), D=self.D.data_ptr(), gamma=self.gamma.data_ptr(),
+            energies=self.energies.data_ptr(), sp2_report=self.report.data_ptr(),
+            workspace=self.ws.ptr, workspace_bytes=self.ws.nbytes, step=0)
+
+    def n_current(self) -> torch.Tensor:
+        return self.n_hist[int(self.st.step) % (self.K + 1)]

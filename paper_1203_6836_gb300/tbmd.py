@@ -1,0 +1,221 @@
+"""ctypes binding of libtbmd (include/tbmd.h): the same names, argument
+marshalling only.  Every computation runs in the CUDA library; when the
+library is missing the calls raise instead of falling back to anything.
+
+Array arguments accept raw device addresses (int) or objects with a
+`data_ptr()` method (torch CUDA tensors); `stream` accepts a cudaStream_t
+address, a torch stream, or None for the current torch stream.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtbmd.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "tbmd.h")
+
+TB_OK = 0
+TB_ERR_ARG = -1
+TB_ERR_NOT_CONVERGED = -2
+TB_ERR_GAP = -3
+TB_ERR_OOM = -4
+TB_ERR_TIMEOUT = -5
+TB_ERR_CUDA = -6
+TB_ERR_UNSUPPORTED = -7
+
+TB_TYPE_O = 0
+TB_TYPE_H = 1
+
+PREC = {"fp64": 0, "tf32": 1, "tf32x3": 2, "bf16": 3, "bf16x3": 4}
+XL_KMAX = 8
+
+
+class TBError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+class tb_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "eps_s_O", "eps_p_O", "eps_s_H", "t_hop", "r_decay", "hubbard_u", "coulomb_k",
+        "gamma_cut", "r1", "rcut", "n0_O", "n0_H", "pair_a", "pair_rho")]
+
+    @classmethod
+    def from_model(cls, m) -> "tb_params":
+        """Copy the attributes of the same names from a model-constants object."""
+        return cls(**{n: float(getattr(m, n)) for n, _ in cls._fields_})
+
+
+class tb_system(ctypes.Structure):
+    _fields_ = [("natoms", ctypes.c_int), ("norb", ctypes.c_int),
+                ("types", ctypes.c_void_p), ("orb_off", ctypes.c_void_p), ("box", ctypes.c_double)]
+
+
+class tb_sp2_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
+                ("refine_iters", ctypes.c_int), ("rule", ctypes.c_int)]
+
+
+class tb_sp2_report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("refine_iters", ctypes.c_int),
+                ("n", ctypes.c_int), ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double),
+                ("trace", ctypes.c_double), ("idem_trace", ctypes.c_double),
+                ("idem_fro", ctypes.c_double), ("branch_bits", ctypes.c_uint64 * 2),
+                ("refine_bits", ctypes.c_uint64)]
+
+
+class tb_xl_params(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("kappa", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("K", ctypes.c_int), ("c", ctypes.c_double * (XL_KMAX + 1))]
+
+
+class tb_md_state(ctypes.Structure):
+    _fields_ = [("sys", tb_system), ("n_occ", ctypes.c_double),
+                ("R", ctypes.c_void_p), ("v", ctypes.c_void_p), ("F", ctypes.c_void_p),
+                ("mass", ctypes.c_void_p), ("n_hist", ctypes.c_void_p), ("q", ctypes.c_void_p),
+                ("H", ctypes.c_void_p), ("D", ctypes.c_void_p), ("gamma", ctypes.c_void_p),
+                ("energies", ctypes.c_void_p), ("sp2_report", ctypes.c_void_p),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
+                ("step", ctypes.c_int64)]
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "tb_ctx_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
+    "tb_ctx_destroy": (ctypes.c_int, [_P]),
+    "tb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "tb_ctx_last_error": (ctypes.c_char_p, [_P]),
+    "tb_build_H": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P, _P, _P, _P]),
+    "dm_sp2_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(tb_sp2_opts),
+                                             ctypes.POINTER(ctypes.c_size_t)]),
+    "dm_sp2": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(tb_sp2_opts), _P, _P,
+                              ctypes.c_size_t, _P, _P]),
+    "mulliken": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P, _P]),
+    "tb_forces": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P, _P, _P, _P,
+                                 _P, _P, _P]),
+    "xlbomd_init": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_md_state),
+                                   ctypes.POINTER(tb_xl_params), ctypes.POINTER(tb_sp2_opts), ctypes.c_double,
+                                   ctypes.c_int, ctypes.POINTER(ctypes.c_int), _P]),
+    "xlbomd_step": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_md_state),
+                                   ctypes.POINTER(tb_xl_params), ctypes.POINTER(tb_sp2_opts), _P]),
+}
+
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/tbmd.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?(?:int|char\s*\*|const char\s*\*|size_t)\s*\**\s*"
+                                 r"([A-Za-z_]\w*)\s*\(", txt, flags=re.M)))
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libtbmd.so (raises when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1203_6836_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+class Context:
+    """tb_ctx bound to the current CUDA device."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        rc = lib().tb_ctx_create(ctypes.byref(h))
+        if rc != TB_OK:
+            raise TBError(rc, "tb_ctx_create: " + lib().tb_status_string(rc).decode())
+        self.handle = h
+
+    def check(self, rc: int, what: str) -> int:
+        if rc != TB_OK:
+            msg = lib().tb_ctx_last_error(self.handle).decode()
+            raise TBError(rc, f"{what}: {msg or lib().tb_status_string(rc).decode()}")
+        return rc
+
+    def close(self):
+        if self.handle:
+            lib().tb_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tb_build_H(ctx: Context, p: tb_params, sys: tb_system, R, n_aux, H, gamma, stream=None) -> int:
+    return ctx.check(lib().tb_build_H(ctx.handle, ctypes.byref(p), ctypes.byref(sys), _ptr(R), _ptr(n_aux),
+                                      _ptr(H), _ptr(gamma), _stream(stream)), "tb_build_H")
+
+
+def dm_sp2_workspace_size(n: int, opts: tb_sp2_opts) -> int:
+    b = ctypes.c_size_t()
+    rc = lib().dm_sp2_workspace_size(int(n), ctypes.byref(opts), ctypes.byref(b))
+    if rc != TB_OK:
+        raise TBError(rc, "dm_sp2_workspace_size")
+    return int(b.value)
+
+
+def dm_sp2(ctx: Context, H, n: int, n_occ: float, opts: tb_sp2_opts, D, workspace, workspace_bytes: int,
+           report=None, stream=None) -> int:
+    return ctx.check(lib().dm_sp2(ctx.handle, _ptr(H), int(n), float(n_occ), ctypes.byref(opts), _ptr(D),
+                                  _ptr(workspace), int(workspace_bytes), _ptr(report), _stream(stream)),
+                     "dm_sp2")
+
+
+def mulliken(ctx: Context, p: tb_params, sys: tb_system, D, q, stream=None) -> int:
+    return ctx.check(lib().mulliken(ctx.handle, ctypes.byref(p), ctypes.byref(sys), _ptr(D), _ptr(q),
+                                    _stream(stream)), "mulliken")
+
+
+def tb_forces(ctx: Context, p: tb_params, sys: tb_system, R, D, q, n_aux, gamma, F, energy, stream=None) -> int:
+    return ctx.check(lib().tb_forces(ctx.handle, ctypes.byref(p), ctypes.byref(sys), _ptr(R), _ptr(D), _ptr(q),
+                                     _ptr(n_aux), _ptr(gamma), _ptr(F), _ptr(energy), _stream(stream)),
+                     "tb_forces")
+
+
+def xlbomd_init(ctx: Context, p: tb_params, st: tb_md_state, xp: tb_xl_params, so: tb_sp2_opts,
+                scf_tol: float, scf_max_iter: int, stream=None) -> int:
+    it = ctypes.c_int()
+    ctx.check(lib().xlbomd_init(ctx.handle, ctypes.byref(p), ctypes.byref(st), ctypes.byref(xp),
+                                ctypes.byref(so), float(scf_tol), int(scf_max_iter), ctypes.byref(it),
+                                _stream(stream)), "xlbomd_init")
+    return int(it.value)
+
+
+def xlbomd_step(ctx: Context, p: tb_params, st: tb_md_state, xp: tb_xl_params, so: tb_sp2_opts,
+                stream=None) -> int:
+    return ctx.check(lib().xlbomd_step(ctx.handle, ctypes.byref(p), ctypes.byref(st), ctypes.byref(xp),
+                                       ctypes.byref(so), _stream(stream)), "xlbomd_step")

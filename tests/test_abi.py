@@ -1,0 +1,33 @@
+"""The C ABI library builds for sm_103a and exports every function that
+include/tbmd.h declares (no GPU needed: nothing is called)."""
+
+import ctypes
+import os
+
+from paper_1203_6836_gb300 import build, tbmd
+
+
+def test_library_builds_and_exports_header_symbols():
+    path = build.build()
+    assert os.path.exists(path)
+    lib = ctypes.CDLL(path)
+    names = tbmd.header_functions()
+    assert {"tb_ctx_create", "tb_build_H", "dm_sp2", "mulliken", "tb_forces", "xlbomd_step"} <= set(names)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, f"declared in tbmd.h but not exported: {missing}"
+
+
+def test_binding_covers_every_header_function():
+    assert set(tbmd.header_functions()) <= set(tbmd._SIGS), set(tbmd.header_functions()) - set(tbmd._SIGS)
+
+
+def test_status_strings_and_argument_errors_without_gpu():
+    lib = tbmd.lib()
+    assert lib.tb_status_string(tbmd.TB_ERR_ARG) == b"invalid argument"
+    opts = tbmd.tb_sp2_opts(precision=0, max_iter=100, tol=1e-10, refine_iters=0, rule=0)
+    assert lib.dm_sp2_workspace_size(0, ctypes.byref(opts), ctypes.byref(ctypes.c_size_t())) == tbmd.TB_ERR_ARG
+    size = ctypes.c_size_t()
+    assert lib.dm_sp2_workspace_size(4094, ctypes.byref(opts), ctypes.byref(size)) == tbmd.TB_OK
+    assert size.value >= 2 * 8 * 4096 * 4096
+    # a null context is rejected before anything touches the device
+    assert lib.dm_sp2(None, None, 10, 5.0, ctypes.byref(opts), None, None, 0, None, None) == tbmd.TB_ERR_ARG

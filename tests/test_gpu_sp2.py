@@ -1,0 +1,147 @@
+"""dm_sp2 on the GPU against the oracle's density matrices (eigh of the same
+H, plain definition D = theta(mu0 I - H)) and its SP2 recursion.
+
+Tolerances: the FP64 path stops at Tr X - Tr X^2 <= 1e-11, which bounds the
+distance to the projector by ~1e-11 per eigenvalue, so ||dD||_F/sqrt(n)
+<= 1e-9 leaves room for rounding.  The tensor-core paths are held to the
+target ||dD||_F/sqrt(n) <= 1e-6 when their products carry ~FP32 accuracy
+(x3 splits) followed by two FP64 projections, on spectra whose relative gap
+gap/(eps_max - eps_min) is >= 0.05; single-pass tf32/bf16 products carry
+~1e-3 relative error and are only held to 1e-2.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from workloads import random_gapped_matrix, water_system, ModelParams, config1_system
+from oracle import density, tb
+from paper_1203_6836_gb300 import tbmd
+from paper_1203_6836_gb300.device import DensitySolver, sp2_opts, report_to_dict
+
+pytestmark = pytest.mark.gpu
+P = ModelParams()
+
+
+def _run(ctx, H: np.ndarray, nocc: float, prec="fp64", refine=2, tol=1e-11, max_iter=100, rule=0):
+    n = H.shape[0]
+    Ht = torch.as_tensor(H, device="cuda")
+    D = torch.empty_like(Ht)
+    solver = DensitySolver(ctx, n, sp2_opts(prec, max_iter=max_iter, tol=tol, refine=refine, rule=rule))
+    solver(Ht, nocc, D)
+    torch.cuda.synchronize()
+    return D.cpu().numpy(), report_to_dict(solver.report)
+
+
+def _err(D, Dref):
+    return np.linalg.norm(D - Dref) / np.sqrt(D.shape[0])
+
+
+def test_two_level_and_ring_closed_forms(ctx):
+    a, ap, b = -1.3, 0.7, 0.45
+    H = np.array([[a, b], [b, ap]])
+    rad = np.sqrt(((a - ap) / 2) ** 2 + b * b)
+    D_ref = 0.5 * (np.eye(2) - (H - 0.5 * (a + ap) * np.eye(2)) / rad)
+    D, rep = _run(ctx, H, 1.0, tol=1e-14)
+    assert rep["status"] == tbmd.TB_OK
+    assert np.abs(D - D_ref).max() < 1e-12
+    t = 1.7
+    H = np.zeros((6, 6))
+    for i in range(6):
+        H[i, (i + 1) % 6] = H[(i + 1) % 6, i] = -t
+    idx = np.arange(6)
+    diff = idx[:, None] - idx[None, :]
+    D_ref = sum(np.cos(2 * np.pi * k * diff / 6) for k in (0, 1, -1)) / 6
+    D, rep = _run(ctx, H, 3.0, tol=1e-14)
+    assert np.abs(D - D_ref).max() < 1e-11
+
+
+def test_diagonal_and_edge_occupations(ctx):
+    e = np.array([3.0, -1.0, 0.5, -2.0, 7.0, 0.1])
+    D, rep = _run(ctx, np.diag(e), 3.0)
+    assert np.abs(D - np.diag([0, 1, 0, 1, 0, 1.0])).max() < 1e-9
+    H, _ = random_gapped_matrix(50, 20, seed=3)
+    D, rep = _run(ctx, H, 0.0)
+    assert np.abs(D).max() < 1e-9
+    D, rep = _run(ctx, H, 50.0)
+    assert np.abs(D - np.eye(50)).max() < 1e-9
+
+
+@pytest.mark.parametrize("n,nocc,seed", [(37, 11, 0), (64, 40, 1), (130, 51, 2), (300, 120, 3), (513, 200, 4)])
+def test_fp64_matches_eigh_and_oracle_recursion(ctx, n, nocc, seed):
+    H, _ = random_gapped_matrix(n, nocc, gap=0.5, width=30.0, seed=seed)
+    ref = density.density_T0(H, nocc)
+    D, rep = _run(ctx, H, nocc, tol=1e-11)
+    assert rep["status"] == tbmd.TB_OK
+    assert _err(D, ref.D) < 1e-9
+    assert abs(rep["trace"] - nocc) < 1e-9
+    lo, hi = density.gershgorin(H)
+    assert rep["eps_min"] == pytest.approx(lo, rel=1e-12)
+    assert rep["eps_max"] == pytest.approx(hi, rel=1e-12)
+    # same projections as the oracle's SP2 recursion
+    o = density.sp2(H, nocc, tol=1e-11)
+    assert rep["iters"] == o.iters
+    assert rep["branches"] == o.branches
+
+
+def test_fp64_simple_rule_and_not_converged_status(ctx):
+    H, _ = random_gapped_matrix(90, 33, gap=0.3, width=20.0, seed=7)
+    ref = density.density_T0(H, 33)
+    D, rep = _run(ctx, H, 33, rule=1)
+    assert _err(D, ref.D) < 1e-9
+    o = density.sp2(H, 33, tol=1e-11, rule="simple")
+    assert rep["branches"] == o.branches
+    D, rep = _run(ctx, H, 33, max_iter=3)
+    assert rep["status"] == tbmd.TB_ERR_NOT_CONVERGED
+    assert rep["iters"] == 3
+
+
+def test_fp64_water_hamiltonian(ctx):
+    s = config1_system()
+    h = tb.build_h(s.R, s.types, s.box, P)
+    G = tb.build_gamma(s.R, s.box, P)
+    rng = np.random.default_rng(11)
+    n_aux = rng.normal(0, 0.3, s.natoms)
+    n_aux -= n_aux.mean()
+    H = tb.build_H(h, G, s.types, n_aux)
+    nocc = s.n_occ(P)
+    ref = density.density_T0(H, int(nocc))
+    D, rep = _run(ctx, H, nocc, tol=1e-12, max_iter=120)
+    assert ref.gap > 1e-3
+    assert rep["status"] == tbmd.TB_OK
+    assert _err(D, ref.D) < 1e-8
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("n,nocc,seed", [(200, 70, 0), (600, 260, 1), (1000, 333, 2)])
+def test_tensor_core_split_paths_meet_target(ctx, prec, n, nocc, seed):
+    H, eps = random_gapped_matrix(n, nocc, gap=2.0, width=30.0, seed=seed)
+    ref = density.density_T0(H, nocc)
+    D, rep = _run(ctx, H, nocc, prec=prec, refine=2)
+    assert rep["status"] == tbmd.TB_OK, rep
+    assert rep["refine_iters"] == 2
+    assert _err(D, ref.D) < 1e-6, (_err(D, ref.D), rep)
+    assert abs(rep["trace"] - nocc) < 1e-5
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_tensor_core_single_pass_paths(ctx, prec):
+    H, eps = random_gapped_matrix(384, 150, gap=2.0, width=30.0, seed=5)
+    ref = density.density_T0(H, 150)
+    D, rep = _run(ctx, H, 150, prec=prec, refine=2)
+    assert _err(D, ref.D) < 1e-2
+    assert abs(rep["trace"] - 150) < 1e-2
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_tensor_core_water_system(ctx, prec):
+    """300-atom water-like system with neutral charges (n = 600, several
+    128-tiles and a ragged tail)."""
+    s = water_system(300, density=1.0, seed=0)
+    H = tb.build_H(tb.build_h(s.R, s.types, s.box, P), tb.build_gamma(s.R, s.box, P), s.types,
+                   np.zeros(s.natoms))
+    nocc = s.n_occ(P)
+    ref = density.density_T0(H, int(nocc))
+    D, rep = _run(ctx, H, nocc, prec=prec, refine=2)
+    assert rep["status"] == tbmd.TB_OK
+    assert _err(D, ref.D) < 1e-6
