@@ -122,6 +122,16 @@ const char* tb_status_string(int status);
 /* Last error message recorded by the context (valid until the next call). */
 const char* tb_ctx_last_error(const tb_ctx* ctx);
 
+/* Launch timing (measurement support, no counterpart in the paper).  With
+ * profiling on, dm_sp2 records CUDA events on its stream between the
+ * purification launches of its main phase (phase 0) and of its FP64
+ * refinement (phase 1).  tb_ctx_sp2_launch_times waits for the last event
+ * and writes the duration (ms) of each launch of the last dm_sp2 call into
+ * the HOST array ms[0..cap), *count = launches written.  Launches after the
+ * device-side stop decision return at once and show as short entries. */
+int tb_ctx_set_profiling(tb_ctx* ctx, int enable);
+int tb_ctx_sp2_launch_times(tb_ctx* ctx, int phase, float* ms, int cap, int* count);
+
 /* ----------------------------------------------------------- a1: H[n] build */
 
 /* H[n] = h(R) + diag(sum_l gamma_il n_l) over every orbital of atom i

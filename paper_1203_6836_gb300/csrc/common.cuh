@@ -10,13 +10,28 @@
 
 #include "../../include/tbmd.h"
 
+#define TB_PROF_MAX 130
 struct tb_ctx {
   int device;
   int sm_count;
   int cc_major, cc_minor;
   PFN_cuTensorMapEncodeTiled_v12000 encode_tiled;
   char last_error[512];
+  // launch timing of the last dm_sp2 call (events recorded between the
+  // purification launches on the caller's stream when profiling is on)
+  int prof_on;
+  int prof_created;
+  cudaEvent_t ev[2][TB_PROF_MAX + 1];
+  int prof_n[2];
 };
+
+// Record the profiling event `idx` of phase `ph` on stream s (no-op when off).
+static inline void tb_prof_mark(tb_ctx* ctx, int ph, int idx, cudaStream_t s) {
+  if (ctx->prof_on && idx <= TB_PROF_MAX) {
+    cudaEventRecord(ctx->ev[ph][idx], s);
+    if (idx + 1 > ctx->prof_n[ph]) ctx->prof_n[ph] = idx + 1;
+  }
+}
 
 // Record a formatted message in the context and return `code`.
 int tb_fail(tb_ctx* ctx, int code, const char* fmt, ...);
@@ -69,7 +84,8 @@ struct SP2State {
   int rdone;         // refinement finished
   int riters;        // refinement projections applied
   int err;           // device-side error code (timeouts)
-  int pad0, pad1;
+  int capped;        // main phase stopped at its iteration cap
+  int rcapped;       // refinement stopped at its iteration cap
   double emin, emax;
   double t1[SP2_MAX_ITER + 2];   // Tr X_k
   double t2[SP2_MAX_ITER + 2];   // ||X_k||_F^2
@@ -85,6 +101,7 @@ struct SP2StepArgs {
   int ld;         // padded leading dimension (multiple of the tile)
   double nocc;
   double tol;
+  double floor;   // tensor-core phase: noise floor of Tr X - Tr X^2 (16 n u)
   int rule;
   int k;          // projection index within its phase
   int max_iter;   // phase cap
@@ -144,18 +161,32 @@ __device__ __forceinline__ void warp_reduce_partials(const double* parts, int np
 }
 
 // Decision of SP2 projection k from the traces of X_k (t1 = Tr X, t2 = Tr X^2).
-// Returns 1 when the phase stops before projection k, else 0 and sets *branch.
-// Main phase on the tensor cores also stops when the idempotency error no
-// longer falls (its floor is set by the FP32 storage of X).
+// Returns 1 when the phase stops before projection k (setting *capped when
+// the iteration cap was the reason), else 0 and sets *branch.
+// FP64 phases stop when |Tr X - Tr X^2| <= tol.  The tensor-core phase,
+// whose products carry a relative error u, stops once Tr X - Tr X^2 reaches
+// its noise floor (a.floor = 16 n u, which negative values are also below)
+// or no longer falls over two projections while already within 8x of it;
+// the FP64 refinement takes it from there.  Away from the floor small-gap
+// spectra keep a few eigenvalues mid-way for many projections, so no
+// stagnation test applies there.
 __device__ __forceinline__ int sp2_decide(const SP2StepArgs& a, double t1, double t2,
                                           const double* hist_t1, const double* hist_t2,
-                                          bool stagnation_stop, int* branch) {
+                                          bool tc_phase, int* branch, int* capped) {
   const double e = t1 - t2;
-  if (e <= a.tol) return 1;
-  if (a.k >= a.max_iter) return 1;
-  if (stagnation_stop && a.k >= 2) {
-    const double e2 = hist_t1[a.k - 2] - hist_t2[a.k - 2];
-    if (e < 1.0 && e > 0.5 * e2) return 1;
+  *capped = 0;
+  if (tc_phase) {
+    if (e <= a.floor) return 1;
+    if (a.k >= 2) {
+      const double e2 = hist_t1[a.k - 2] - hist_t2[a.k - 2];
+      if (e2 <= 8.0 * a.floor && e > e2) return 1;
+    }
+  } else if (fabs(e) <= a.tol) {
+    return 1;
+  }
+  if (a.k >= a.max_iter) {
+    *capped = 1;
+    return 1;
   }
   if (a.rule == 0)
     *branch = (fabs(t2 - a.nocc) <= fabs(2.0 * t1 - t2 - a.nocc)) ? 0 : 1;

@@ -66,6 +66,36 @@ extern "C" int tb_ctx_create(tb_ctx** out) {
 }
 
 extern "C" int tb_ctx_destroy(tb_ctx* ctx) {
+  if (ctx && ctx->prof_created) {
+    for (int p = 0; p < 2; ++p)
+      for (int i = 0; i <= TB_PROF_MAX; ++i) cudaEventDestroy(ctx->ev[p][i]);
+  }
   delete ctx;
+  return TB_OK;
+}
+
+extern "C" int tb_ctx_set_profiling(tb_ctx* ctx, int enable) {
+  if (!ctx) return TB_ERR_ARG;
+  if (enable && !ctx->prof_created) {
+    for (int p = 0; p < 2; ++p)
+      for (int i = 0; i <= TB_PROF_MAX; ++i) TB_CUDA_TRY(ctx, cudaEventCreate(&ctx->ev[p][i]));
+    ctx->prof_created = 1;
+  }
+  if (enable) ctx->prof_on = 1;
+  ctx->prof_n[0] = ctx->prof_n[1] = 0;
+  if (!enable) ctx->prof_on = 0;
+  return TB_OK;
+}
+
+extern "C" int tb_ctx_sp2_launch_times(tb_ctx* ctx, int phase, float* ms, int cap, int* count) {
+  if (!ctx || phase < 0 || phase > 1 || !count) return TB_ERR_ARG;
+  *count = 0;
+  if (!ctx->prof_on) return TB_OK;
+  const int n = ctx->prof_n[phase] - 1;  // events bracket n launches
+  if (n <= 0) return TB_OK;
+  TB_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev[phase][n]));
+  const int m = n < cap ? n : cap;
+  for (int i = 0; i < m; ++i) TB_CUDA_TRY(ctx, cudaEventElapsedTime(&ms[i], ctx->ev[phase][i], ctx->ev[phase][i + 1]));
+  *count = m;
   return TB_OK;
 }

@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) uint64_t full[C::stages], empty[C::stages], tfull;
   __shared__ uint32_t tmem_base;
   __shared__ double s_t[3];
-  __shared__ int s_dec[2];
+  __shared__ int s_dec[3];
   __shared__ volatile int s_abort;
   __shared__ double s_red[4][3];
 
@@ -262,13 +262,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     y = warp_sum(y);
     z = warp_sum(z);
     if (lane == 0) {
-      int br = 0;
-      const int stop = sp2_decide(a, x, y, st->t1, st->t2, true, &br);
+      int br = 0, capped = 0;
+      const int stop = sp2_decide(a, x, y, st->t1, st->t2, true, &br, &capped);
       s_t[0] = x;
       s_t[1] = y;
       s_t[2] = z;
       s_dec[0] = stop;
       s_dec[1] = br;
+      s_dec[2] = capped;
     }
   }
   __syncthreads();
@@ -278,6 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     st->t2[a.k] = s_t[1];
     if (stop) {
       st->iters = a.k;
+      st->capped = s_dec[2];
       st->done = 1;
     } else if (br) {
       st->branch[a.k >> 6] |= 1ull << (a.k & 63);

@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256) k_sp2_step_f64(SP2StepArgs a, const doubl
   __shared__ double As[kF64K][kF64Tile + 1];
   __shared__ double Bs[kF64K][kF64Tile + 1];
   __shared__ double s_t[3];
-  __shared__ int s_dec[2];
+  __shared__ int s_dec[3];
   SP2State* st = a.st;
   const int done = a.phase == 0 ? st->done : st->rdone;
   if (done || st->err) return;
@@ -214,12 +214,13 @@ __global__ void __launch_bounds__(256) k_sp2_step_f64(SP2StepArgs a, const doubl
         s_t[0] = t1;
         s_t[1] = t2;
         s_t[2] = z;
-        int br = 0;
+        int br = 0, capped = 0;
         const double* h1 = a.phase == 0 ? st->t1 : st->rt1;
         const double* h2 = a.phase == 0 ? st->t2 : st->rt2;
-        const int stop = sp2_decide(a, t1, t2, h1, h2, false, &br);
+        const int stop = sp2_decide(a, t1, t2, h1, h2, false, &br, &capped);
         s_dec[0] = stop;
         s_dec[1] = br;
+        s_dec[2] = capped;
       }
     }
   }
@@ -231,6 +232,7 @@ __global__ void __launch_bounds__(256) k_sp2_step_f64(SP2StepArgs a, const doubl
       st->t2[a.k] = s_t[1];
       if (stop) {
         st->iters = a.k;
+        st->capped = s_dec[2];
         st->done = 1;
       } else if (br) {
         st->branch[a.k >> 6] |= 1ull << (a.k & 63);
@@ -241,6 +243,7 @@ __global__ void __launch_bounds__(256) k_sp2_step_f64(SP2StepArgs a, const doubl
       if (a.k > 0) st->idem_fro = sqrt(s_t[2]);
       if (stop) {
         st->riters = a.k;
+        st->rcapped = s_dec[2];
         st->rdone = 1;
       } else if (br) {
         st->rbranch |= 1ull << a.k;
@@ -345,11 +348,15 @@ __global__ void __launch_bounds__(256) k_finalize(SP2State* st, int n, int ld, i
       t1 = st->t1[st->iters];
       t2 = st->t2[st->iters];
     }
+    // status: device error; an FP64 phase that hit its cap without reaching
+    // |Tr X - Tr X^2| <= 1e-6 max(1, N_occ); a trace that missed N_occ
+    // (no gap at the occupation)
     int status = TB_OK;
     const double e = t1 - t2;
+    const bool capped = mode == 1 ? st->rcapped : (mode == 0 ? st->capped : 0);
     if (st->err) status = st->err;
+    else if (capped && fabs(e) > 1e-6 * fmax(1.0, nocc)) status = TB_ERR_NOT_CONVERGED;
     else if (fabs(t1 - nocc) > 0.25) status = TB_ERR_GAP;
-    else if (mode != 2 && e > 1e-6 * fmax(1.0, nocc)) status = TB_ERR_NOT_CONVERGED;
     rep->status = status;
     rep->iters = st->iters;
     rep->refine_iters = mode == 1 ? st->riters : 0;
@@ -394,6 +401,7 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
   if ((reinterpret_cast<uintptr_t>(ws) & 1023) != 0)
     return tb_fail(ctx, TB_ERR_ARG, "workspace must be 1024-byte aligned");
   cudaStream_t s = as_stream(stream);
+  ctx->prof_n[0] = ctx->prof_n[1] = 0;
   char* base = static_cast<char*>(ws);
   SP2State* st = reinterpret_cast<SP2State*>(base + L.off_state);
   double* bparts = reinterpret_cast<double*>(base + L.off_bparts);
@@ -441,6 +449,7 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
     a.max_iter = o->max_iter;
     a.phase = 0;
     const dim3 g(ld / kF64Tile, ld / kF64Tile);
+    tb_prof_mark(ctx, 0, 0, s);
     for (int k = 0; k <= o->max_iter; ++k) {
       a.k = k;
       a.nparts_in = k == 0 ? np_init : (int)(g.x * g.y);
@@ -448,6 +457,7 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
       a.parts_out = slot[(k + 1) & 1];
       k_sp2_step_f64<<<g, 256, 0, s>>>(a, (k & 1) ? F1 : F0, (k & 1) ? F0 : F1);
       TB_LAUNCH_CHECK(ctx);
+      tb_prof_mark(ctx, 0, k + 1, s);
     }
     const int fb = std::min(1184, (int)(((size_t)n * n + 255) / 256));
     k_finalize<<<fb, 256, 0, s>>>(st, n, ld, 0, F0, F1, nullptr, nullptr, D, nocc, rep);
@@ -470,6 +480,13 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
   a.tol = o->tol;
   a.max_iter = o->max_iter;
   a.phase = 0;
+  {
+    // relative error of one product: ~2^-24 for hi/lo splits, 2^-11 (tf32),
+    // 2^-8 (bf16)
+    const double u = (o->precision == TB_PREC_TF32X3 || o->precision == TB_PREC_BF16X3) ? 0x1p-24
+                     : o->precision == TB_PREC_TF32 ? 0x1p-11 : 0x1p-8;
+    a.floor = 16.0 * n * u;
+  }
   // k = -1 converts X0 to operands (the kernel's split-only mode)
   {
     SP2StepArgs c = a;
@@ -479,6 +496,7 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
     if (rc) return rc;
   }
   const int ntc = sp2_tc_num_tiles(ld);
+  tb_prof_mark(ctx, 0, 0, s);
   for (int k = 0; k <= o->max_iter; ++k) {
     a.k = k;
     a.nparts_in = k == 0 ? np_init : ntc;
@@ -487,6 +505,7 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
     const int i = k & 1, j = (k + 1) & 1;
     int rc = sp2_tc_step(ctx, o->precision, a, &mh[i], &ml[i], M[i], M[j], Hi[j], Lo[j], s);
     if (rc) return rc;
+    tb_prof_mark(ctx, 0, k + 1, s);
   }
   const int fb = std::min(1184, (int)(((size_t)n * n + 255) / 256));
   if (refine == 0) {
@@ -503,6 +522,7 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
   r.max_iter = refine;
   r.tol = o->tol;
   const dim3 g(ld / kF64Tile, ld / kF64Tile);
+  tb_prof_mark(ctx, 1, 0, s);
   for (int k = 0; k <= refine; ++k) {
     r.k = k;
     r.nparts_in = k == 0 ? (int)(gc.x * gc.y) : (int)(g.x * g.y);
@@ -510,6 +530,7 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
     r.parts_out = slot[(k + 1) & 1];
     k_sp2_step_f64<<<g, 256, 0, s>>>(r, (k & 1) ? F1 : F0, (k & 1) ? F0 : F1);
     TB_LAUNCH_CHECK(ctx);
+    tb_prof_mark(ctx, 1, k + 1, s);
   }
   k_finalize<<<fb, 256, 0, s>>>(st, n, ld, 1, F0, F1, nullptr, nullptr, D, nocc, rep);
   TB_LAUNCH_CHECK(ctx);

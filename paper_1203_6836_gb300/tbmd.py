@@ -89,6 +89,9 @@ _SIGS = {
     "tb_ctx_destroy": (ctypes.c_int, [_P]),
     "tb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "tb_ctx_last_error": (ctypes.c_char_p, [_P]),
+    "tb_ctx_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tb_ctx_sp2_launch_times": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int)]),
     "tb_build_H": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P, _P, _P, _P]),
     "dm_sp2_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(tb_sp2_opts),
                                              ctypes.POINTER(ctypes.c_size_t)]),
@@ -173,6 +176,18 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def tb_ctx_set_profiling(ctx: Context, enable: bool) -> int:
+    return ctx.check(lib().tb_ctx_set_profiling(ctx.handle, int(bool(enable))), "tb_ctx_set_profiling")
+
+
+def tb_ctx_sp2_launch_times(ctx: Context, phase: int, cap: int = 130) -> list[float]:
+    buf = (ctypes.c_float * cap)()
+    cnt = ctypes.c_int()
+    ctx.check(lib().tb_ctx_sp2_launch_times(ctx.handle, int(phase), buf, cap, ctypes.byref(cnt)),
+              "tb_ctx_sp2_launch_times")
+    return [float(buf[i]) for i in range(cnt.value)]
 
 
 def tb_build_H(ctx: Context, p: tb_params, sys: tb_system, R, n_aux, H, gamma, stream=None) -> int:

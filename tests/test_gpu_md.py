@@ -86,5 +86,6 @@ def test_xlbomd_history_ring_buffer_matches_eq_verl_n(ctx):
     tbmd.xlbomd_step(ctx, TP, st.st, xp, opts)
     torch.cuda.synchronize()
     n1 = st.n_current().cpu().numpy()
-    expect = md.modified_verlet_n([q0] * (XL.K + 1), q0, XL)
-    assert np.abs(n1 - expect).max() < 1e-12
+    # history = the SCF's last charges, q_t = charges of D[n_t] (equal to 1e-10)
+    expect = md.modified_verlet_n([h[0]] * (XL.K + 1), q0, XL)
+    assert np.abs(n1 - expect).max() < 1e-13
