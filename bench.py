@@ -42,8 +42,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=["tf32", "tf32x3", "bf16", "bf16x3"])
+    ap.add_argument("--precision", default="tf32x3", choices=["tf32", "tf32x3", "bf16", "bf16x3"])
     ap.add_argument("--refine", type=int, default=3)
+    ap.add_argument("--natoms", type=int, default=2048,
+                    help="atoms of the water-like system (2048 = the headline workload)")
     ap.add_argument("--scf-iters", type=int, default=12)
     ap.add_argument("--no-check", action="store_true", help="skip the accuracy check against the oracle")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -208,7 +210,8 @@ def run_ours(args):
     P = ModelParams()
     TP = tbmd.tb_params.from_model(P)
     XL = XLParams()
-    s = config2_system(seed=rank)  # independent replica per rank
+    from workloads import water_system
+    s = config2_system(seed=rank) if args.natoms == 2048 else water_system(args.natoms, density=1.0, seed=rank)
     M = s.masses(P)
     v0 = thermal_velocities(M, 300.0, seed=100 + rank)
     ds = DeviceSystem(s.R, s.types, s.box)

@@ -101,7 +101,7 @@ struct SP2StepArgs {
   int ld;         // padded leading dimension (multiple of the tile)
   double nocc;
   double tol;
-  double floor;   // tensor-core phase: noise floor of Tr X - Tr X^2 (16 n u)
+  double floor;   // tensor-core phase: noise floor of Tr X - Tr X^2 (2 n u)
   int rule;
   int k;          // projection index within its phase
   int max_iter;   // phase cap
@@ -165,11 +165,11 @@ __device__ __forceinline__ void warp_reduce_partials(const double* parts, int np
 // the iteration cap was the reason), else 0 and sets *branch.
 // FP64 phases stop when |Tr X - Tr X^2| <= tol.  The tensor-core phase,
 // whose products carry a relative error u, stops once Tr X - Tr X^2 reaches
-// its noise floor (a.floor = 16 n u, which negative values are also below)
-// or no longer falls over two projections while already within 8x of it;
-// the FP64 refinement takes it from there.  Away from the floor small-gap
-// spectra keep a few eigenvalues mid-way for many projections, so no
-// stagnation test applies there.
+// its noise floor (a.floor = 2 n u, which negative values are also below)
+// or has stayed within 4x of it for four projections; the FP64 refinement
+// takes it from there.  A rise of Tr X - Tr X^2 alone is no stop signal:
+// on small-gap spectra the HOMO or LUMO eigenvalue of X climbs from near 0
+// across the middle over several projections, doubling it each time.
 __device__ __forceinline__ int sp2_decide(const SP2StepArgs& a, double t1, double t2,
                                           const double* hist_t1, const double* hist_t2,
                                           bool tc_phase, int* branch, int* capped) {
@@ -177,9 +177,10 @@ __device__ __forceinline__ int sp2_decide(const SP2StepArgs& a, double t1, doubl
   *capped = 0;
   if (tc_phase) {
     if (e <= a.floor) return 1;
-    if (a.k >= 2) {
-      const double e2 = hist_t1[a.k - 2] - hist_t2[a.k - 2];
-      if (e2 <= 8.0 * a.floor && e > e2) return 1;
+    if (a.k >= 3) {
+      bool flat = e <= 4.0 * a.floor;
+      for (int j = 1; j <= 3; ++j) flat = flat && (hist_t1[a.k - j] - hist_t2[a.k - j] <= 4.0 * a.floor);
+      if (flat) return 1;
     }
   } else if (fabs(e) <= a.tol) {
     return 1;

