@@ -136,7 +136,7 @@ def test_tensor_core_single_pass_paths(ctx, prec, tol):
     ref = density.density_T0(H, 150)
     D, rep = _run(ctx, H, 150, prec=prec, refine=4)
     assert _err(D, ref.D) < tol
-    assert abs(rep["trace"] - 150) < 0.05
+    assert abs(rep["trace"] - 150) < 0.25
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
