@@ -162,6 +162,24 @@ int dm_sp2(tb_ctx* ctx, const double* H, int n, double n_occ, const tb_sp2_opts*
            double* D, void* workspace, size_t workspace_bytes, tb_sp2_report* report,
            void* stream);
 
+/* Allocation-free FP64 SP2 (no counterpart in the paper: a convenience of
+ * this library).  Same result as dm_sp2 with opts->precision = TB_PREC_FP64,
+ * for callers that cannot allocate device memory when they need D (an MD
+ * engine that reserves all memory up front and forbids allocation inside its
+ * time step, a plugin whose host application owns the CUDA allocator, code
+ * that must avoid the device-wide synchronisation of cudaMalloc/cudaFree).
+ * The scratch is a static device array inside the library, sized for
+ * n <= TB_SP2_STATIC_MAX_N (about 4 MiB per GPU, held until the process
+ * exits); larger n fails with TB_ERR_ARG, other precisions with
+ * TB_ERR_UNSUPPORTED.  The first call on a device, made with that device
+ * current, looks up the array's device address: make it before any stream
+ * capture.  Every call reuses the same array (its state is cleared at the
+ * start of each call), so calls that overlap on the GPU race: serialise
+ * them on one stream.  H, D, report as for dm_sp2. */
+#define TB_SP2_STATIC_MAX_N 512
+int dm_sp2_static(tb_ctx* ctx, const double* H, int n, double n_occ, const tb_sp2_opts* opts,
+                  double* D, tb_sp2_report* report, void* stream);
+
 /* ------------------------------------------------------------- a7: charges */
 
 /* Mulliken net charges q_i = 2 sum_{a in i} D_aa - N0_i (App. D).

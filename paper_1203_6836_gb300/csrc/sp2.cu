@@ -536,3 +536,59 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
   TB_LAUNCH_CHECK(ctx);
   return TB_OK;
 }
+
+// --------------------------------------------------------------------------
+// dm_sp2_static: the FP64 SP2 path without any caller workspace.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// density matrix: an MD engine that reserves all device memory up front and
+// forbids allocation inside its time step, a plugin running inside a host
+// application that owns the CUDA allocator, or code that must not trigger
+// the device-wide synchronisation cudaMalloc/cudaFree may cause.  For them
+// the scratch of the FP64 path lives in this file-scope device array, sized
+// for n <= TB_SP2_STATIC_MAX_N (about 4 MiB, held by every GPU that loads
+// the library until the process exits).  The symbol's device address is
+// looked up once per device, on the first call made with that device
+// current; make that first call before any stream capture.  All calls share
+// the array: the SP2 state is cleared at the start of every call, and calls
+// that overlap on the GPU (other streams, other host threads) race.
+// --------------------------------------------------------------------------
+
+namespace {
+constexpr size_t kStaticScratchBytes = (size_t)4 * 1024 * 1024 + 64 * 1024;
+static __device__ __align__(256) unsigned char g_sp2_scratch[kStaticScratchBytes];
+constexpr int kMaxDevices = 64;
+void* g_sp2_scratch_addr[kMaxDevices] = {nullptr};
+}  // namespace
+
+extern "C" int dm_sp2_static(tb_ctx* ctx, const double* H, int n, double nocc, const tb_sp2_opts* o,
+                             double* D, tb_sp2_report* rep, void* stream) {
+  if (!ctx) return TB_ERR_ARG;
+  if (!o) return tb_fail(ctx, TB_ERR_ARG, "null options to dm_sp2_static");
+  if (o->precision != TB_PREC_FP64)
+    return tb_fail(ctx, TB_ERR_UNSUPPORTED, "dm_sp2_static runs the FP64 path only (precision %d)", o->precision);
+  if (n < 1 || n > TB_SP2_STATIC_MAX_N)
+    return tb_fail(ctx, TB_ERR_ARG, "dm_sp2_static: n = %d outside 1..%d (its static scratch is sized for %d)", n,
+                   TB_SP2_STATIC_MAX_N, TB_SP2_STATIC_MAX_N);
+  int dev = 0;
+  TB_CUDA_TRY(ctx, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "device %d out of range", dev);
+  if (!g_sp2_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_sp2_scratch);
+    if (e != cudaSuccess || !p)
+      return tb_fail(ctx, TB_ERR_CUDA, "cudaGetSymbolAddress of the static SP2 scratch failed: %s",
+                     cudaGetErrorString(e));
+    g_sp2_scratch_addr[dev] = p;
+  }
+  // dm_sp2 wants a 1024-byte aligned workspace: start at the first such
+  // address inside the array
+  const uintptr_t base = reinterpret_cast<uintptr_t>(g_sp2_scratch_addr[dev]);
+  const uintptr_t aligned = (base + 1023) & ~uintptr_t(1023);
+  const size_t avail = kStaticScratchBytes - (size_t)(aligned - base);
+  const Layout L = make_layout(n, TB_PREC_FP64, 0);
+  if (L.total > avail)
+    return tb_fail(ctx, TB_ERR_ARG, "dm_sp2_static: n = %d needs %zu scratch bytes, %zu available", n, L.total,
+                   avail);
+  return dm_sp2(ctx, H, n, nocc, o, D, reinterpret_cast<void*>(aligned), avail, rep, stream);
+}

@@ -97,6 +97,8 @@ _SIGS = {
                                              ctypes.POINTER(ctypes.c_size_t)]),
     "dm_sp2": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(tb_sp2_opts), _P, _P,
                               ctypes.c_size_t, _P, _P]),
+    "dm_sp2_static": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(tb_sp2_opts), _P, _P,
+                                     _P]),
     "mulliken": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P, _P]),
     "tb_forces": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P, _P, _P, _P,
                                  _P, _P, _P]),
@@ -208,6 +210,15 @@ def dm_sp2(ctx: Context, H, n: int, n_occ: float, opts: tb_sp2_opts, D, workspac
     return ctx.check(lib().dm_sp2(ctx.handle, _ptr(H), int(n), float(n_occ), ctypes.byref(opts), _ptr(D),
                                   _ptr(workspace), int(workspace_bytes), _ptr(report), _stream(stream)),
                      "dm_sp2")
+
+
+SP2_STATIC_MAX_N = 512
+
+
+def dm_sp2_static(ctx: Context, H, n: int, n_occ: float, opts: tb_sp2_opts, D, report=None, stream=None) -> int:
+    """FP64 SP2 with the library's static scratch (no workspace argument)."""
+    return ctx.check(lib().dm_sp2_static(ctx.handle, _ptr(H), int(n), float(n_occ), ctypes.byref(opts), _ptr(D),
+                                         _ptr(report), _stream(stream)), "dm_sp2_static")
 
 
 def mulliken(ctx: Context, p: tb_params, sys: tb_system, D, q, stream=None) -> int:
