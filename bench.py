@@ -374,8 +374,10 @@ def run_ours(args):
                          "peak_source": f"{peaks['source']} bf16_tflops_sustained x {ratio} ({'tf32' if tf else 'bf16'})",
                          "mma_per_product": mmas, "mma_frac": achieved * mmas / peak,
                          "avg_launch_ms": avg_ms},
-            "fp64_refine_kernel": {"avg_launch_ms": ref_avg,
-                                   "tflops": 2.0 * float(n) ** 3 / (ref_avg * 1e-3) / 1e12 if ref_work else None},
+            "refine_kernel": {"kind": "emulated FP64 (21 exact bf16 slice products)" if opts.refine_mode == 0
+                              else "FP64 FMA",
+                              "avg_launch_ms": ref_avg,
+                              "tflops": 2.0 * float(n) ** 3 / (ref_avg * 1e-3) / 1e12 if ref_work else None},
             "fp64_path": fp64,
             "accuracy_vs_oracle": check,
             "cpu_baseline": cpu,
@@ -386,7 +388,7 @@ def run_ours(args):
         }
         # kernel launches per step: main phase (max_iter + 1 + split) + FP64 refinement
         # (refine + 2) + bounds/init/finalize + H build (2) + Mulliken + forces + MD (3)
-        per_step = (100 + 2) + (args.refine + 2) + 3 + 2 + 1 + 1 + 3
+        per_step = (100 + 2) + (2 * args.refine + 2) + 3 + 2 + 1 + 1 + 3
         result["gpu_launches"] = per_step * args.steps
         print(json.dumps(result), flush=True)
     if world > 1:

@@ -94,6 +94,9 @@ typedef struct {
   double tol;           /* stop when Tr X - Tr X^2 <= tol (FP64 path) */
   int refine_iters;     /* FP64 projections after a tensor-core phase, 0..4 */
   int rule;             /* 0: X^2 when |Tr X^2 - N| <= |2Tr X - Tr X^2 - N| (look-ahead), 1: X^2 when Tr X > N */
+  int refine_mode;      /* 0: refinement products emulate FP64 exactly on the bf16 tensor cores
+                           (integer slices, FP64 result; needs n <= 4096, else FP64 FMA is used);
+                           1: FP64 FMA */
 } tb_sp2_opts;
 
 /* Written on the device by dm_sp2 (caller-owned device memory). */

@@ -124,6 +124,13 @@ int sp2_tc_num_tiles(int ld);
 int sp2_tc_tile();
 size_t sp2_tc_operand_bytes(int precision);  // bytes per element of one operand array
 
+// Emulated-FP64 projection on the tensor cores (gemm_oz.cu): splits X_in
+// (FP64, ld x ld) into bf16 slices, then X_out = X_in^2 or 2 X_in - X_in^2.
+int sp2_oz_step(tb_ctx* ctx, const SP2StepArgs& a, const double* Xin, double* Xout, void* slices, int* exps,
+                cudaStream_t s);
+int sp2_oz_max_ld();
+size_t sp2_oz_slice_bytes(int ld);
+
 // Encode a 2D row-major tensor map over an ld x ld operand array for the
 // tensor-core kernel (gemm_tc.cu).
 int sp2_tc_make_map(tb_ctx* ctx, int precision, const void* base, int ld, CUtensorMap* map);

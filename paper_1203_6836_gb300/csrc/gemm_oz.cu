@@ -1,0 +1,330 @@
+// Emulated-FP64 SP2 projection on the tensor cores (row a6, refinement).
+//
+// The FP64 refinement projections X <- X^2 or 2X - X^2 (Sec. III.B, App. D.2)
+// would run on GB300's FP64 units at ~1.2 TFLOP/s.  Instead the product is
+// formed exactly from integer slices on the bf16 tensor cores, following the
+// error-free splitting of Ozaki, Ogita, Oishi and Rump (Numer. Algorithms
+// 2012) in the tensor-core form of Mukunoki et al. (ISC 2020):
+//
+//   row scaling  x_ij = 2^{e_i} r_ij, |r_ij| <= 1 (e_i from the row maximum)
+//   slicing      r = sum_{s=1..S} d_s 2^{-6s}, d_s integers (|d_1| <= 64,
+//                |d_s| <= 32 for s >= 2), each exact in bf16
+//   products     P_st = sum_k d_s(i,k) d_t(j,k): integers with |P| <= K 2^12,
+//                exact in the FP32 accumulator for K <= 4096
+//   sum          (X X)_ij = 2^{e_i + e_j} sum_{s+t <= S+1} 2^{-6(s+t)} P_st,
+//                recombined exactly in int64 fixed point, then rounded once
+//                to FP64.
+// With S = 6 the slices carry 36 bits of each row-scaled entry and the pairs
+// dropped (s + t > 7) contribute below ~2^-32 of |x_i| |x_j|: FP64-grade for
+// the refinement, for 21 bf16 products instead of one FP64 GEMM.
+//
+// Kernel layout: one CTA per 128 x 128 output tile; warp 0 issues TMA loads
+// of (slice s, row block m) and (slice t, row block n) tiles, warp 1 issues
+// tcgen05.mma into a ring of four TMEM accumulators (512 columns), warps
+// 2-9 drain each pair's accumulator into int64 registers (64 columns per
+// thread) and finally apply the SP2 branch in FP64 with the trace partials.
+
+#include "common.cuh"
+#include "tc_ptx.cuh"
+
+#include <cuda_bf16.h>
+
+namespace {
+
+using namespace tcx;
+
+constexpr int kS = 6;          // slices
+constexpr int kBeta = 6;       // bits per slice
+constexpr int kPairs = 21;     // (s, t) with s + t <= kS + 1
+constexpr int kTile = 128;
+constexpr int kBK = 64;        // bf16 per 128-byte row
+constexpr int kTileBytes = kTile * 128;
+constexpr int kStages = 6;
+constexpr int kStageBytes = 2 * kTileBytes;
+constexpr int kSmem = kStages * kStageBytes + 1024;
+constexpr int kThreads = 320;
+constexpr int kNacc = 4;       // TMEM accumulators of 128 columns
+
+struct SliceMaps {
+  CUtensorMap m[kS];
+};
+
+__device__ __forceinline__ void pair_of(int p, int* s, int* t) {
+  // (1,1..6), (2,1..5), ..., (6,1)
+  int ss = 1, rem = p;
+  while (rem >= kS + 1 - ss) {
+    rem -= kS + 1 - ss;
+    ++ss;
+  }
+  *s = ss;
+  *t = rem + 1;
+}
+
+// One warp per row: e_i from the row maximum, then the six signed 6-bit
+// digits of every entry of the row (exact arithmetic on powers of two).
+__global__ void __launch_bounds__(256) k_oz_split(const SP2State* st, const double* __restrict__ X, int ld,
+                                                  __nv_bfloat16* __restrict__ slices, int* __restrict__ exps) {
+  if (st->rdone || st->err) return;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= ld) return;
+  const double* xr = X + (size_t)row * ld;
+  double mx = 0.0;
+  for (int j = lane; j < ld; j += 32) mx = fmax(mx, fabs(xr[j]));
+  mx = warp_max(mx);
+  int e = 0;
+  if (mx > 0.0) {
+    frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): |x| / 2^e <= 1
+  }
+  if (lane == 0) exps[row] = e;
+  const size_t plane = (size_t)ld * ld;
+  for (int j = lane; j < ld; j += 32) {
+    double r = ldexp(xr[j], -e);
+#pragma unroll
+    for (int s = 1; s <= kS; ++s) {
+      const double d = rint(ldexp(r, kBeta * s));
+      r -= ldexp(d, -kBeta * s);
+      slices[(s - 1) * plane + (size_t)row * ld + j] = __double2bfloat16(d);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_sp2_step_oz(SP2StepArgs a, const __grid_constant__ SliceMaps maps, const int* __restrict__ exps,
+                  const double* __restrict__ Xin, double* __restrict__ Xout) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull[kNacc], tempty[kNacc];
+  __shared__ uint32_t tmem_base;
+  __shared__ double s_t[3];
+  __shared__ int s_dec[3];
+  __shared__ volatile int s_abort;
+  __shared__ double s_red[8][3];
+
+  SP2State* st = a.st;
+  if (st->rdone || st->err) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (warp == 0) {
+    double x = 0, y = 0, z = 0;
+    for (int i = lane; i < a.nparts_in; i += 32) {
+      x += a.parts_in[3 * i];
+      y += a.parts_in[3 * i + 1];
+      z += a.parts_in[3 * i + 2];
+    }
+    x = warp_sum(x);
+    y = warp_sum(y);
+    z = warp_sum(z);
+    if (lane == 0) {
+      int br = 0, capped = 0;
+      const int stop = sp2_decide(a, x, y, st->rt1, st->rt2, false, &br, &capped);
+      s_t[0] = x;
+      s_t[1] = y;
+      s_t[2] = z;
+      s_dec[0] = stop;
+      s_dec[1] = br;
+      s_dec[2] = capped;
+    }
+  }
+  __syncthreads();
+  const int stop = s_dec[0], br = s_dec[1];
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    st->rt1[a.k] = s_t[0];
+    st->rt2[a.k] = s_t[1];
+    if (a.k > 0) st->idem_fro = sqrt(s_t[2]);
+    if (stop) {
+      st->riters = a.k;
+      st->rcapped = s_dec[2];
+      st->rdone = 1;
+    } else if (br) {
+      st->rbranch |= 1ull << a.k;
+    }
+  }
+  if (stop) return;
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int m0 = blockIdx.y * kTile, n0 = blockIdx.x * kTile;
+  const int nk = a.ld / kBK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < kNacc; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 8);
+    }
+    s_abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_base, kNacc * kTile);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------------- producer
+    for (int i = 0; i < kS; ++i) prefetch_map(&maps.m[i]);
+    int g = 0, issued = 0;
+    for (int p = 0; p < kPairs && !s_abort; ++p) {
+      int s, t;
+      pair_of(p, &s, &t);
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int stg = g % kStages;
+        if (g >= kStages && !mbar_wait(&empty[stg], ((g / kStages) - 1) & 1, &s_abort)) break;
+        uint8_t* base = smem + stg * kStageBytes;
+        mbar_expect_tx(&full[stg], kStageBytes);
+        tma_load_2d(base, &maps.m[s - 1], &full[stg], kb * kBK, m0);
+        tma_load_2d(base + kTileBytes, &maps.m[t - 1], &full[stg], kb * kBK, n0);
+        issued = g + 1;
+      }
+    }
+    if (s_abort) {
+      for (int q = (issued > kStages ? issued - kStages : 0); q < issued; ++q) {
+        const unsigned long long t0 = gtime();
+        while (!mbar_try(&full[q % kStages], (q / kStages) & 1) && gtime() - t0 < kWaitNs) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------------------------------------------------- MMA issuer
+    constexpr uint32_t id = idesc(1u);
+    int g = 0;
+    for (int p = 0; p < kPairs && !s_abort; ++p) {
+      const int acc = p % kNacc;
+      if (p >= kNacc && !mbar_wait(&tempty[acc], ((p / kNacc) - 1) & 1, &s_abort)) break;
+      tc_fence_after();
+      const uint32_t d = tmem + acc * kTile;
+      bool ok = true;
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int stg = g % kStages;
+        if (!mbar_wait(&full[stg], (g / kStages) & 1, &s_abort)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t base = smem_u32(smem + stg * kStageBytes);
+#pragma unroll
+        for (int ks = 0; ks < kBK / 16; ++ks) {
+          umma<false>(d, sdesc(base + ks * 32), sdesc(base + kTileBytes + ks * 32), id, (kb | ks) != 0);
+        }
+        umma_commit(&empty[stg]);
+      }
+      umma_commit(&tfull[acc]);
+      if (!ok) break;
+    }
+  } else if (warp >= 2) {
+    // ---------------------------------------------------------- epilogue
+    const int q = warp & 3;          // TMEM lane quarter
+    const int h = (warp - 2) >> 2;   // column half
+    const int row = 32 * q + lane;
+    long long acc64[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) acc64[j] = 0;
+    bool ok = true;
+    for (int p = 0; p < kPairs && ok; ++p) {
+      int s, t;
+      pair_of(p, &s, &t);
+      const int acc = p % kNacc;
+      if (!mbar_wait(&tfull[acc], (p / kNacc) & 1, &s_abort)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const int shift = kBeta * (kS + 1 - s - t);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        uint32_t v[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + acc * kTile + 64 * h + 32 * c, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc64[32 * c + j] += __float2ll_rz(__uint_as_float(v[j])) << shift;
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[acc])) : "memory");
+    }
+    double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    if (ok) {
+      const int gr = m0 + row;
+      const int er = exps[gr];
+      const double* xin = Xin + (size_t)gr * a.ld + n0 + 64 * h;
+      double* xout = Xout + (size_t)gr * a.ld + n0 + 64 * h;
+      const int* ec = exps + n0 + 64 * h;
+#pragma unroll
+      for (int j = 0; j < 64; ++j) {
+        const double cxx = ldexp((double)acc64[j], er + ec[j] - kBeta * (kS + 1));
+        const double x = xin[j];
+        const double y = br ? 2.0 * x - cxx : cxx;
+        xout[j] = y;
+        if (gr == n0 + 64 * h + j) t1 += y;
+        t2 += y * y;
+        t3 += (cxx - x) * (cxx - x);
+      }
+    }
+    t1 = warp_sum(t1);
+    t2 = warp_sum(t2);
+    t3 = warp_sum(t3);
+    if (lane == 0) {
+      s_red[warp - 2][0] = t1;
+      s_red[warp - 2][1] = t2;
+      s_red[warp - 2][2] = t3;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 64) {
+    double x = 0, y = 0, z = 0;
+    for (int w = 0; w < 8; ++w) {
+      x += s_red[w][0];
+      y += s_red[w][1];
+      z += s_red[w][2];
+    }
+    const int cta = blockIdx.y * gridDim.x + blockIdx.x;
+    a.parts_out[3 * cta] = x;
+    a.parts_out[3 * cta + 1] = y;
+    a.parts_out[3 * cta + 2] = z;
+    if (s_abort) atomicExch(&st->err, TB_ERR_TIMEOUT);
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    if (s_abort && lane == 0) {
+      // every accumulator ring slot got a final commit from the issuer or is
+      // idle: wait (bounded) for the last one before freeing TMEM
+      for (int b = 0; b < kNacc; ++b) {
+        const unsigned long long t0 = gtime();
+        while (!mbar_try(&tfull[b], 0) && gtime() - t0 < kWaitNs) {
+        }
+      }
+    }
+    __syncwarp();
+    tmem_dealloc(tmem, kNacc * kTile);
+  }
+}
+
+}  // namespace
+
+int sp2_oz_max_ld() { return 4096; }
+size_t sp2_oz_slice_bytes(int ld) { return (size_t)kS * ld * ld * sizeof(__nv_bfloat16); }
+
+int sp2_oz_step(tb_ctx* ctx, const SP2StepArgs& a, const double* Xin, double* Xout, void* slices, int* exps,
+                cudaStream_t s) {
+  if (a.ld > 4096 || a.ld % kTile) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "emulated FP64 needs ld <= 4096");
+  static bool attr_set = false;
+  if (!attr_set) {
+    TB_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sp2_step_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+    attr_set = true;
+  }
+  k_oz_split<<<(a.ld * 32 + 255) / 256, 256, 0, s>>>(a.st, Xin, a.ld, static_cast<__nv_bfloat16*>(slices), exps);
+  TB_LAUNCH_CHECK(ctx);
+  SliceMaps maps;
+  const size_t plane = (size_t)a.ld * a.ld * sizeof(__nv_bfloat16);
+  for (int i = 0; i < kS; ++i) {
+    int rc = sp2_tc_make_map(ctx, TB_PREC_BF16, static_cast<char*>(slices) + i * plane, a.ld, &maps.m[i]);
+    if (rc) return rc;
+  }
+  const dim3 grid(a.ld / kTile, a.ld / kTile);
+  k_sp2_step_oz<<<grid, kThreads, kSmem, s>>>(a, maps, exps, Xin, Xout);
+  TB_LAUNCH_CHECK(ctx);
+  return TB_OK;
+}

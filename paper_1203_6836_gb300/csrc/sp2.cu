@@ -32,11 +32,12 @@ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 struct Layout {
   int n, ld, prec;
   size_t off_state, off_bparts, off_parts, off_f0, off_f1, off_m0, off_m1, off_h0, off_l0, off_h1,
-      off_l1, total;
+      off_l1, off_slices, off_exps, total;
   int max_parts;
+  bool oz;  // refinement by the emulated-FP64 tensor-core kernel
 };
 
-Layout make_layout(int n, int prec, int refine) {
+Layout make_layout(int n, int prec, int refine, int refine_mode = 1) {
   Layout L{};
   L.n = n;
   L.prec = prec;
@@ -68,6 +69,11 @@ Layout make_layout(int n, int prec, int refine) {
     L.off_h1 = take(ob * nn);
     L.off_l0 = split ? take(ob * nn) : 0;
     L.off_l1 = split ? take(ob * nn) : 0;
+    L.oz = refine > 0 && refine_mode == 0 && L.ld <= sp2_oz_max_ld();
+    if (L.oz) {
+      L.off_slices = take(sp2_oz_slice_bytes(L.ld));
+      L.off_exps = take(sizeof(int) * (size_t)L.ld);
+    }
   }
   L.total = o;
   return L;
@@ -377,7 +383,7 @@ __global__ void __launch_bounds__(256) k_finalize(SP2State* st, int n, int ld, i
 extern "C" int dm_sp2_workspace_size(int n, const tb_sp2_opts* o, size_t* bytes) {
   if (!o || !bytes || n < 1) return TB_ERR_ARG;
   if (o->precision < TB_PREC_FP64 || o->precision > TB_PREC_BF16X3) return TB_ERR_ARG;
-  *bytes = make_layout(n, o->precision, o->refine_iters).total;
+  *bytes = make_layout(n, o->precision, o->refine_iters, o->refine_mode).total;
   return TB_OK;
 }
 
@@ -395,7 +401,9 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
   if (!(nocc >= 0.0) || nocc > n) return tb_fail(ctx, TB_ERR_ARG, "n_occ %g outside [0, n]", nocc);
   const bool tc = o->precision != TB_PREC_FP64;
   const int refine = tc ? o->refine_iters : 0;
-  const Layout L = make_layout(n, o->precision, refine);
+  if (o->refine_mode < 0 || o->refine_mode > 1)
+    return tb_fail(ctx, TB_ERR_ARG, "refine_mode %d outside 0..1", o->refine_mode);
+  const Layout L = make_layout(n, o->precision, refine, o->refine_mode);
   if (ws_bytes < L.total)
     return tb_fail(ctx, TB_ERR_ARG, "workspace %zu bytes < required %zu", ws_bytes, L.total);
   if ((reinterpret_cast<uintptr_t>(ws) & 1023) != 0)
@@ -522,14 +530,23 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
   r.max_iter = refine;
   r.tol = o->tol;
   const dim3 g(ld / kF64Tile, ld / kF64Tile);
+  const int np_ref = L.oz ? sp2_tc_num_tiles(ld) : (int)(g.x * g.y);
   tb_prof_mark(ctx, 1, 0, s);
   for (int k = 0; k <= refine; ++k) {
     r.k = k;
-    r.nparts_in = k == 0 ? (int)(gc.x * gc.y) : (int)(g.x * g.y);
+    r.nparts_in = k == 0 ? (int)(gc.x * gc.y) : np_ref;
     r.parts_in = slot[k & 1];
     r.parts_out = slot[(k + 1) & 1];
-    k_sp2_step_f64<<<g, 256, 0, s>>>(r, (k & 1) ? F1 : F0, (k & 1) ? F0 : F1);
-    TB_LAUNCH_CHECK(ctx);
+    double* Fin = (k & 1) ? F1 : F0;
+    double* Fout = (k & 1) ? F0 : F1;
+    if (L.oz && k < refine) {
+      int rc = sp2_oz_step(ctx, r, Fin, Fout, base + L.off_slices, reinterpret_cast<int*>(base + L.off_exps), s);
+      if (rc) return rc;
+    } else {
+      // FP64 FMA projection (or, at k = refine, only the final decision)
+      k_sp2_step_f64<<<g, 256, 0, s>>>(r, Fin, Fout);
+      TB_LAUNCH_CHECK(ctx);
+    }
     tb_prof_mark(ctx, 1, k + 1, s);
   }
   k_finalize<<<fb, 256, 0, s>>>(st, n, ld, 1, F0, F1, nullptr, nullptr, D, nocc, rep);

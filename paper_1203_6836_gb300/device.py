@@ -45,10 +45,14 @@ class Workspace:
         self.nbytes = int(nbytes)
 
 
+REFINE = {"emulated": 0, "fp64": 1}
+
+
 def sp2_opts(precision: str = "fp64", max_iter: int = 100, tol: float = 1e-10, refine: int = 2,
-             rule: int = 0) -> tbmd.tb_sp2_opts:
+             rule: int = 0, refine_mode: str = "emulated") -> tbmd.tb_sp2_opts:
+    """refine_mode: "emulated" (exact-slice FP64 emulation on the tensor cores) or "fp64" (FMA)."""
     return tbmd.tb_sp2_opts(precision=tbmd.PREC[precision], max_iter=max_iter, tol=tol,
-                            refine_iters=refine, rule=rule)
+                            refine_iters=refine, rule=rule, refine_mode=REFINE[refine_mode])
 
 
 def xl_params(dt: float, kappa: float, alpha: float, c) -> tbmd.tb_xl_params:

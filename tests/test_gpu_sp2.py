@@ -153,3 +153,31 @@ def test_tensor_core_water_system_meets_target(ctx, prec, natoms):
     assert rep["status"] == tbmd.TB_OK
     assert _err(D, ref.D) < 1e-6
     assert abs(rep["trace"] - nocc) < 1e-6
+
+
+@pytest.mark.parametrize("natoms", [300, 600])
+def test_emulated_fp64_refinement_matches_fma_refinement(ctx, natoms):
+    """The refinement projections on the tensor cores (exact integer slices,
+    FP64 result) agree with FP64 FMA projections to far below the target:
+    both start from the same tensor-core iterate and apply the same branches."""
+    P_ = ModelParams()
+    s = water_system(natoms, density=1.0, seed=1)
+    H = tb.build_H(tb.build_h(s.R, s.types, s.box, P_), tb.build_gamma(s.R, s.box, P_), s.types,
+                   np.zeros(s.natoms))
+    nocc = s.n_occ(P_)
+    ref = density.density_T0(H, int(nocc))
+    out = {}
+    for mode in ("emulated", "fp64"):
+        n = H.shape[0]
+        Ht = torch.as_tensor(H, device="cuda")
+        D = torch.empty_like(Ht)
+        solver = DensitySolver(ctx, n, sp2_opts("tf32x3", refine=3, refine_mode=mode))
+        solver(Ht, nocc, D)
+        torch.cuda.synchronize()
+        out[mode] = (D.cpu().numpy(), report_to_dict(solver.report))
+    (De, re_), (Df, rf) = out["emulated"], out["fp64"]
+    assert re_["status"] == rf["status"] == tbmd.TB_OK
+    assert re_["refine_branches"] == rf["refine_branches"]
+    assert np.abs(De - Df).max() < 1e-9
+    assert abs(re_["idem_trace"]) < 1e-8
+    assert _err(De, ref.D) < 1e-6
