@@ -374,7 +374,7 @@ def run_ours(args):
                          "peak_source": f"{peaks['source']} bf16_tflops_sustained x {ratio} ({'tf32' if tf else 'bf16'})",
                          "mma_per_product": mmas, "mma_frac": achieved * mmas / peak,
                          "avg_launch_ms": avg_ms},
-            "refine_kernel": {"kind": "emulated FP64 (21 exact bf16 slice products)" if opts.refine_mode == 0
+            "refine_kernel": {"kind": "emulated FP64 (28 exact bf16 slice products)" if opts.refine_mode == 0
                               else "FP64 FMA",
                               "avg_launch_ms": ref_avg,
                               "tflops": 2.0 * float(n) ** 3 / (ref_avg * 1e-3) / 1e12 if ref_work else None},

