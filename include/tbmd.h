@@ -97,6 +97,11 @@ typedef struct {
   int refine_mode;      /* 0: refinement products emulate FP64 exactly on the bf16 tensor cores
                            (integer slices, FP64 result; needs n <= 4096, else FP64 FMA is used);
                            1: FP64 FMA */
+  double tau;           /* > 0: thresholded block-sparse SP2 (Sec. III.B): after X0 and after every
+                           projection, 32 x 32 blocks with Frobenius norm < tau are set to zero;
+                           tensor-core precisions only, n <= 32768, no refinement */
+  int bsr_blocks_per_row; /* capacity of the block-sparse pattern in 128 x 128 blocks per block
+                             row (0: all, never overflows); exceeding it reports TB_ERR_OOM */
 } tb_sp2_opts;
 
 /* Written on the device by dm_sp2 (caller-owned device memory). */

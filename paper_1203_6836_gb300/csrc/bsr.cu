@@ -1,0 +1,816 @@
+// Thresholded block-sparse SP2 (row a5): the linear-scaling form of the
+// purification (Sec. III.B, Table I tau > 0 rows).
+//
+// Reading: after X0 and after every projection, every 32 x 32 block of X whose
+// Frobenius norm is below tau is set to zero (the paper drops elements below
+// tau; the 32 x 32 block rule is the block-sparse reading).
+//
+// GB300 layout: X is stored as 128 x 128 super-blocks (one tcgen05 tile) in a
+// block-sparse-row structure, ping-ponged between two buffers.  A super-block
+// is stored when at least one of its sixteen 32 x 32 sub-blocks survives the
+// drop rule; dropped sub-blocks inside a stored super-block hold zeros, so the
+// arithmetic is the same as dropping 32 x 32 blocks.  For n <= 32768 there are
+// at most 256 super-rows and each row's pattern is a 256-bit bitmap.
+//
+// Per projection (all on the device, no host synchronisation):
+//   decide  reduce the trace partials of X_k, take the stop/branch decision
+//           (every CTA the same), build each row's bitmaps of stored and live
+//           (not all-zero) super-blocks;
+//   symbolic  candidates of row I = OR of the live bitmaps of its live
+//           columns; scans give the output slots; each output block (I,J)
+//           gets the list of common K (live in both rows I and J, X symmetric)
+//           as pairs of source slots;
+//   numeric  a persistent tcgen05 kernel walks the output blocks: TMA loads
+//           the (I,K) and (J,K) tiles of every pair into shared memory, the
+//           MMA accumulates in TMEM (double-buffered between blocks), the
+//           epilogue applies the branch (X^2 or 2X - X^2), zeroes every 32 x 32
+//           sub-block with ||.||_F < tau (one warp owns a 32-row band, so a
+//           sub-block norm is a warp reduction), writes the FP32 master and
+//           operand splits, and accumulates FP64 trace partials.
+// The final iterate is scattered into the dense FP64 D.
+
+#include "common.cuh"
+#include "tc_ptx.cuh"
+
+#include <algorithm>
+
+namespace {
+
+using namespace tcx;
+
+constexpr int SB = 128;            // super-block side (tcgen05 tile)
+constexpr int MW = 8;              // bitmap words per row (256 super-rows)
+constexpr int kMaxNsb = MW * 32;
+constexpr int kThreads = 192;      // numeric kernel: TMA, MMA, 4 epilogue warps
+constexpr int kTiles = SB * SB;    // elements per super-block
+constexpr int kMaxGrid = 256;      // persistent numeric grid (<= SMs)
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+struct Buf {
+  int* row_ptr;      // [nsb + 1]
+  int* col;          // [cap]
+  int* nz;           // [cap] live flag (some sub-block kept)
+  uint32_t* stored;  // [nsb * MW]
+  uint32_t* live;    // [nsb * MW]
+  float* val;        // [cap * kTiles] FP32 master
+  void* hi;          // [cap * kTiles] operands
+  void* lo;
+};
+
+struct Sym {
+  uint32_t* cand;    // [nsb * MW]
+  int* cnt;          // [nsb]
+  int* out_row;      // [cap]
+  int* old_idx;      // [cap]
+  int* pcnt;         // [cap]
+  int* pair_ptr;     // [cap + 1]
+  int2* pairs;       // [pcap]
+  int* scal;         // [4]: blocks of the new pattern, pairs
+  uint16_t* flags;   // [nsb * nsb] X0 sub-block keep masks
+};
+
+struct Args {
+  int n, ld, nsb, cap, pcap;
+  double nocc, tau2, floor, tol;
+  int rule, k, max_iter;
+  SP2State* st;
+  const double* parts_in;
+  int nparts_in;
+  double* parts_out;
+};
+
+__device__ __forceinline__ int popc_below(const uint32_t* m, int bit) {
+  int r = 0;
+  for (int w = 0; w < (bit >> 5); ++w) r += __popc(m[w]);
+  const uint32_t part = m[bit >> 5] & ((1u << (bit & 31)) - 1u);
+  return r + __popc(part);
+}
+
+// ------------------------------------------------------------------ init
+
+// emin/emax from the Gershgorin partials (one block).
+__global__ void k_bsr_bounds(const double* bparts, int nb, SP2State* st) {
+  double a = INFINITY, b = -INFINITY;
+  for (int i = threadIdx.x; i < nb; i += 32) {
+    a = fmin(a, bparts[2 * i]);
+    b = fmax(b, bparts[2 * i + 1]);
+  }
+  a = warp_min(a);
+  b = warp_max(b);
+  if (threadIdx.x == 0) {
+    st->emin = a;
+    st->emax = b;
+  }
+}
+
+__device__ __forceinline__ double x0_val(const double* H, int n, int r, int c, double emax, double inv) {
+  if (r >= n || c >= n) return 0.0;
+  return ((r == c ? emax : 0.0) - H[(size_t)r * n + c]) * inv;
+}
+
+// One block per super-block (I, J) of X0: the 16 sub-block norms of
+// X0 = (emax I - H)/(emax - emin), kept where ||.||_F >= tau.
+__global__ void __launch_bounds__(256) k_bsr_init_flags(const double* __restrict__ H, Args a, Sym sy) {
+  __shared__ double sq[16];
+  if (threadIdx.x < 16) sq[threadIdx.x] = 0.0;
+  __syncthreads();
+  const int I = blockIdx.y, J = blockIdx.x;
+  const double emin = a.st->emin, emax = a.st->emax;
+  double w = emax - emin;
+  if (!(w > 0.0)) w = 1.0;
+  const double inv = 1.0 / w;
+  const int r = threadIdx.x >> 1, h = threadIdx.x & 1;
+  double part[2] = {0.0, 0.0};
+  for (int c = 0; c < 64; ++c) {
+    const double x = x0_val(H, a.n, I * SB + r, J * SB + 64 * h + c, emax, inv);
+    part[c >> 5] += x * x;
+  }
+  atomicAdd(&sq[(r >> 5) * 4 + 2 * h], part[0]);
+  atomicAdd(&sq[(r >> 5) * 4 + 2 * h + 1], part[1]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint16_t f = 0;
+    for (int s = 0; s < 16; ++s)
+      if (sq[s] >= a.tau2 && sq[s] > 0.0) f |= (uint16_t)(1u << s);
+    sy.flags[(size_t)I * a.nsb + J] = f;
+  }
+}
+
+// Row I of X0: stored = live bitmap of its kept super-blocks, count.
+__global__ void k_bsr_init_rows(Args a, Sym sy, Buf b) {
+  const int I = blockIdx.x;
+  __shared__ uint32_t m[MW];
+  if (threadIdx.x < MW) m[threadIdx.x] = 0u;
+  __syncthreads();
+  for (int J = threadIdx.x; J < a.nsb; J += blockDim.x)
+    if (sy.flags[(size_t)I * a.nsb + J]) atomicOr(&m[J >> 5], 1u << (J & 31));
+  __syncthreads();
+  if (threadIdx.x < MW) {
+    b.stored[I * MW + threadIdx.x] = m[threadIdx.x];
+    b.live[I * MW + threadIdx.x] = m[threadIdx.x];
+  }
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int w = 0; w < MW; ++w) c += __popc(m[w]);
+    sy.cnt[I] = c;
+  }
+}
+
+// Exclusive scan of cnt[0..nsb) into row_ptr (one block); total into scal[0].
+__global__ void k_bsr_scan_rows(Args a, Sym sy, int* row_ptr) {
+  if (a.st->done || a.st->err) return;
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int i = 0; i < a.nsb; ++i) {
+      row_ptr[i] = s;
+      s += sy.cnt[i];
+    }
+    row_ptr[a.nsb] = s;
+    sy.scal[0] = s;
+    if (s > a.cap) atomicExch(&a.st->err, TB_ERR_OOM);
+  }
+}
+
+// Fill the X0 blocks of row I (one block per row): values with dropped
+// sub-blocks zeroed, operand splits, trace partials of the row.
+template <int P>
+__global__ void __launch_bounds__(256) k_bsr_init_fill(const double* __restrict__ H, Args a, Sym sy, Buf b) {
+  if (a.st->err) return;
+  const int I = blockIdx.x;
+  const double emin = a.st->emin, emax = a.st->emax;
+  double w = emax - emin;
+  if (!(w > 0.0)) w = 1.0;
+  const double inv = 1.0 / w;
+  double t1 = 0.0, t2 = 0.0;
+  int o = b.row_ptr[I];
+  for (int J = 0; J < a.nsb; ++J) {
+    const uint16_t f = sy.flags[(size_t)I * a.nsb + J];
+    if (!f) continue;
+    if (threadIdx.x == 0) {
+      b.col[o] = J;
+      b.nz[o] = 1;
+    }
+    // 128 rows x 4 segments of 32: 512 segments over 256 threads
+    for (int seg = threadIdx.x; seg < SB * 4; seg += blockDim.x) {
+      const int r = seg >> 2, cs = seg & 3;
+      const bool keep = (f >> ((r >> 5) * 4 + cs)) & 1;
+      float y[32];
+      for (int j = 0; j < 32; ++j) {
+        const double x = keep ? x0_val(H, a.n, I * SB + r, J * SB + 32 * cs + j, emax, inv) : 0.0;
+        y[j] = (float)x;
+        const double xf = (double)y[j];
+        t2 += xf * xf;
+        if (I == J && r == 32 * cs + j) t1 += xf;
+      }
+      const size_t e0 = (size_t)o * kTiles + (size_t)r * SB + 32 * cs;
+      float* dst = b.val + e0;
+      for (int j = 0; j < 32; ++j) dst[j] = y[j];
+      char* h = static_cast<char*>(b.hi) + e0 * Prec<P>::eb;
+      char* l = b.lo ? static_cast<char*>(b.lo) + e0 * Prec<P>::eb : h;
+      store_operands<P>(y, h, l);
+    }
+    ++o;
+  }
+  __shared__ double s1[8], s2[8];
+  t1 = warp_sum(t1);
+  t2 = warp_sum(t2);
+  if ((threadIdx.x & 31) == 0) {
+    s1[threadIdx.x >> 5] = t1;
+    s2[threadIdx.x >> 5] = t2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0, y = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      x += s1[q];
+      y += s2[q];
+    }
+    a.parts_out[3 * I] = x;
+    a.parts_out[3 * I + 1] = y;
+    a.parts_out[3 * I + 2] = 0.0;
+  }
+}
+
+// ------------------------------------------------------- per projection
+
+// Decision for projection k (every block the same) and the bitmaps of row I
+// of X_k: stored blocks and live (not all-zero) blocks.
+__global__ void k_bsr_decide(Args a, Buf b) {
+  __shared__ int s_stop;
+  __shared__ uint32_t ms[MW], ml[MW];
+  SP2State* st = a.st;
+  if (st->done || st->err) return;
+  if (threadIdx.x < 32) {
+    double x = 0, y = 0;
+    for (int i = threadIdx.x; i < a.nparts_in; i += 32) {
+      x += a.parts_in[3 * i];
+      y += a.parts_in[3 * i + 1];
+    }
+    x = warp_sum(x);
+    y = warp_sum(y);
+    if (threadIdx.x == 0) {
+      SP2StepArgs d{};
+      d.nocc = a.nocc;
+      d.tol = a.tol;
+      d.floor = a.floor;
+      d.rule = a.rule;
+      d.k = a.k;
+      d.max_iter = a.max_iter;
+      int br = 0, capped = 0;
+      const int stop = sp2_decide(d, x, y, st->t1, st->t2, true, &br, &capped);
+      s_stop = stop;
+      if (blockIdx.x == 0) {
+        st->t1[a.k] = x;
+        st->t2[a.k] = y;
+        if (stop) {
+          st->iters = a.k;
+          st->capped = capped;
+          st->done = 1;
+        } else if (br) {
+          st->branch[a.k >> 6] |= 1ull << (a.k & 63);
+        }
+      }
+    }
+  }
+  if (threadIdx.x < MW) {
+    ms[threadIdx.x] = 0u;
+    ml[threadIdx.x] = 0u;
+  }
+  __syncthreads();
+  if (s_stop) return;
+  const int I = blockIdx.x;
+  for (int o = b.row_ptr[I] + threadIdx.x; o < b.row_ptr[I + 1]; o += blockDim.x) {
+    const int J = b.col[o];
+    atomicOr(&ms[J >> 5], 1u << (J & 31));
+    if (b.nz[o]) atomicOr(&ml[J >> 5], 1u << (J & 31));
+  }
+  __syncthreads();
+  if (threadIdx.x < MW) {
+    b.stored[I * MW + threadIdx.x] = ms[threadIdx.x];
+    b.live[I * MW + threadIdx.x] = ml[threadIdx.x];
+  }
+}
+
+// Candidate columns of row I: OR of the live bitmaps of its live columns.
+__global__ void k_bsr_cand(Args a, Buf b, Sym sy) {
+  __shared__ uint32_t c[MW];
+  if (a.st->done || a.st->err) return;
+  const int I = blockIdx.x;
+  if (threadIdx.x < MW) c[threadIdx.x] = 0u;
+  __syncthreads();
+  const uint32_t* li = b.live + I * MW;
+  for (int K = threadIdx.x; K < a.nsb; K += blockDim.x)
+    if ((li[K >> 5] >> (K & 31)) & 1u)
+      for (int w = 0; w < MW; ++w) atomicOr(&c[w], b.live[K * MW + w]);
+  __syncthreads();
+  if (threadIdx.x < MW) sy.cand[I * MW + threadIdx.x] = c[threadIdx.x];
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < MW; ++w) s += __popc(c[w]);
+    sy.cnt[I] = s;
+  }
+}
+
+// Output blocks of row I: column, source slot of X_IJ (or -1), pair count.
+__global__ void k_bsr_fill_out(Args a, Buf bo, Buf bn, Sym sy) {
+  if (a.st->done || a.st->err) return;
+  const int I = blockIdx.x;
+  const uint32_t* ci = sy.cand + I * MW;
+  const uint32_t* si = bo.stored + I * MW;
+  const uint32_t* li = bo.live + I * MW;
+  for (int J = threadIdx.x; J < a.nsb; J += blockDim.x) {
+    if (!((ci[J >> 5] >> (J & 31)) & 1u)) continue;
+    const int o = bn.row_ptr[I] + popc_below(ci, J);
+    bn.col[o] = J;
+    bn.nz[o] = 0;
+    sy.out_row[o] = I;
+    sy.old_idx[o] = ((si[J >> 5] >> (J & 31)) & 1u) ? bo.row_ptr[I] + popc_below(si, J) : -1;
+    int pc = 0;
+    const uint32_t* lj = bo.live + J * MW;
+    for (int w = 0; w < MW; ++w) pc += __popc(li[w] & lj[w]);
+    sy.pcnt[o] = pc;
+  }
+}
+
+// Exclusive scan of the pair counts of all output blocks (one block).
+__global__ void __launch_bounds__(1024) k_bsr_scan_pairs(Args a, Sym sy) {
+  __shared__ int part[1024];
+  if (a.st->done || a.st->err) return;
+  const int nb = sy.scal[0];
+  const int per = (nb + blockDim.x - 1) / blockDim.x;
+  const int lo = threadIdx.x * per, hi = min(nb, lo + per);
+  int s = 0;
+  for (int i = lo; i < hi; ++i) s += sy.pcnt[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      const int v = part[t];
+      part[t] = acc;
+      acc += v;
+    }
+    sy.scal[1] = acc;
+    sy.pair_ptr[nb] = acc;
+    if (acc > a.pcap) atomicExch(&a.st->err, TB_ERR_OOM);
+  }
+  __syncthreads();
+  int run = part[threadIdx.x];
+  for (int i = lo; i < hi; ++i) {
+    sy.pair_ptr[i] = run;
+    run += sy.pcnt[i];
+  }
+}
+
+// Pairs (slot of X_IK, slot of X_JK) of every output block (I, J).
+__global__ void k_bsr_pairs(Args a, Buf bo, Buf bn, Sym sy) {
+  if (a.st->done || a.st->err) return;
+  const int nb = sy.scal[0];
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < nb; o += gridDim.x * blockDim.x) {
+    const int I = sy.out_row[o], J = bn.col[o];
+    const uint32_t* li = bo.live + I * MW;
+    const uint32_t* lj = bo.live + J * MW;
+    const uint32_t* si = bo.stored + I * MW;
+    const uint32_t* sj = bo.stored + J * MW;
+    int p = sy.pair_ptr[o];
+    for (int w = 0; w < MW; ++w) {
+      uint32_t m = li[w] & lj[w];
+      while (m) {
+        const int K = 32 * w + __ffs(m) - 1;
+        m &= m - 1u;
+        sy.pairs[p++] = make_int2(bo.row_ptr[I] + popc_below(si, K), bo.row_ptr[J] + popc_below(sj, K));
+      }
+    }
+  }
+}
+
+// Persistent numeric projection.
+template <int P>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_bsr_step_tc(Args a, const __grid_constant__ CUtensorMap mh, const __grid_constant__ CUtensorMap ml,
+                  Buf bo, Buf bn, Sym sy) {
+  using C = Prec<P>;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[C::stages], empty[C::stages], tfull[2], tempty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int s_abort;
+  __shared__ double s_red[4][3];
+  SP2State* st = a.st;
+  if (st->done || st->err) return;
+  const int br = (int)((st->branch[a.k >> 6] >> (a.k & 63)) & 1ull);
+  const int nb = sy.scal[0];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    s_abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_base, 2 * SB);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  constexpr int chunks = SB / C::bk;  // k-steps of one super-block
+
+  if (warp == 0 && lane == 0) {
+    prefetch_map(&mh);
+    if (C::split) prefetch_map(&ml);
+    int g = 0, issued = 0;
+    for (int o = blockIdx.x; o < nb && !s_abort; o += gridDim.x) {
+      const int p0 = sy.pair_ptr[o], p1 = sy.pair_ptr[o + 1];
+      for (int p = p0; p < p1 && !s_abort; ++p) {
+        const int2 pr = sy.pairs[p];
+        for (int c = 0; c < chunks; ++c, ++g) {
+          const int s = g % C::stages;
+          if (g >= C::stages && !mbar_wait(&empty[s], ((g / C::stages) - 1) & 1, &s_abort)) break;
+          uint8_t* base = smem + s * C::stage_bytes;
+          mbar_expect_tx(&full[s], C::stage_bytes);
+          tma_load_2d(base, &mh, &full[s], c * C::bk, pr.x * SB);
+          tma_load_2d(base + 128 * 128, &mh, &full[s], c * C::bk, pr.y * SB);
+          if constexpr (C::split) {
+            tma_load_2d(base + 2 * 128 * 128, &ml, &full[s], c * C::bk, pr.x * SB);
+            tma_load_2d(base + 3 * 128 * 128, &ml, &full[s], c * C::bk, pr.y * SB);
+          }
+          issued = g + 1;
+        }
+      }
+    }
+    if (s_abort) {
+      for (int q = (issued > C::stages ? issued - C::stages : 0); q < issued; ++q) {
+        const unsigned long long t0 = gtime();
+        while (!mbar_try(&full[q % C::stages], (q / C::stages) & 1) && gtime() - t0 < kWaitNs) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t id = idesc(C::tf32 ? 2u : 1u);
+    int g = 0, it = 0;
+    for (int o = blockIdx.x; o < nb && !s_abort; o += gridDim.x, ++it) {
+      const int buf = it & 1;
+      if (it >= 2 && !mbar_wait(&tempty[buf], ((it >> 1) - 1) & 1, &s_abort)) break;
+      tc_fence_after();
+      const uint32_t d = tmem + buf * SB;
+      const int p0 = sy.pair_ptr[o], p1 = sy.pair_ptr[o + 1];
+      bool first = true;
+      for (int p = p0; p < p1 && !s_abort; ++p) {
+        for (int c = 0; c < chunks; ++c, ++g) {
+          const int s = g % C::stages;
+          if (!mbar_wait(&full[s], (g / C::stages) & 1, &s_abort)) break;
+          tc_fence_after();
+          const uint32_t base = smem_u32(smem + s * C::stage_bytes);
+#pragma unroll
+          for (int ks = 0; ks < C::bk / C::uk; ++ks) {
+            const uint32_t koff = ks * 32;
+            const uint64_t ah = sdesc(base + koff), bh = sdesc(base + 128 * 128 + koff);
+            umma<C::tf32>(d, ah, bh, id, first ? 0u : 1u);
+            first = false;
+            if constexpr (C::split) {
+              umma<C::tf32>(d, ah, sdesc(base + 3 * 128 * 128 + koff), id, 1u);
+              umma<C::tf32>(d, sdesc(base + 2 * 128 * 128 + koff), bh, id, 1u);
+            }
+          }
+          umma_commit(&empty[s]);
+        }
+      }
+      umma_commit(&tfull[buf]);
+    }
+  } else if (warp >= 2) {
+    const int q = warp & 3;
+    const int row = 32 * q + lane;
+    double t1 = 0.0, t2 = 0.0;
+    int it = 0;
+    for (int o = blockIdx.x; o < nb; o += gridDim.x, ++it) {
+      const int buf = it & 1;
+      if (!mbar_wait(&tfull[buf], (it >> 1) & 1, &s_abort)) break;
+      tc_fence_after();
+      const bool has = sy.pair_ptr[o + 1] > sy.pair_ptr[o];
+      const int I = sy.out_row[o], J = bn.col[o];
+      const int oi = sy.old_idx[o];
+      const float* xold = oi >= 0 ? bo.val + (size_t)oi * kTiles + (size_t)row * SB : nullptr;
+      float* xnew = bn.val + (size_t)o * kTiles + (size_t)row * SB;
+      char* hrow = static_cast<char*>(bn.hi) + ((size_t)o * kTiles + (size_t)row * SB) * C::eb;
+      char* lrow = bn.lo ? static_cast<char*>(bn.lo) + ((size_t)o * kTiles + (size_t)row * SB) * C::eb : hrow;
+      int kept = 0;
+#pragma unroll 1
+      for (int c = 0; c < 4; ++c) {
+        uint32_t v[32];
+        if (has) {
+          tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + buf * SB + 32 * c, v);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = 0u;
+        }
+        float y[32];
+        double ss = 0.0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float cxx = __uint_as_float(v[j]);
+          const float x = xold ? xold[32 * c + j] : 0.0f;
+          y[j] = br ? fmaf(2.0f, x, -cxx) : cxx;
+          ss += (double)y[j] * (double)y[j];
+        }
+        ss = warp_sum(ss);  // squared Frobenius norm of sub-block (q, c)
+        const bool keep = ss >= a.tau2 && ss > 0.0;
+        if (!keep) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) y[j] = 0.0f;
+        } else {
+          kept = 1;
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          t2 += (double)y[j] * (double)y[j];
+          if (I == J && row == 32 * c + j) t1 += (double)y[j];
+        }
+        float4* xo = reinterpret_cast<float4*>(xnew + 32 * c);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) xo[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
+        store_operands<P>(y, hrow + 32 * c * C::eb, lrow + 32 * c * C::eb);
+      }
+      tc_fence_before();
+      if (lane == 0) {
+        // the block is live when any of its 32-row bands kept a sub-block
+        // (nz[o] was zeroed when the output pattern was built)
+        if (kept) atomicOr(&bn.nz[o], 1);
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[buf])) : "memory");
+      }
+    }
+    t1 = warp_sum(t1);
+    t2 = warp_sum(t2);
+    if (lane == 0) {
+      s_red[q][0] = t1;
+      s_red[q][1] = t2;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 64) {
+    a.parts_out[3 * blockIdx.x] = s_red[0][0] + s_red[1][0] + s_red[2][0] + s_red[3][0];
+    a.parts_out[3 * blockIdx.x + 1] = s_red[0][1] + s_red[1][1] + s_red[2][1] + s_red[3][1];
+    a.parts_out[3 * blockIdx.x + 2] = 0.0;
+    if (s_abort) atomicExch(&st->err, TB_ERR_TIMEOUT);
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    if (s_abort && lane == 0) {
+      for (int b = 0; b < 2; ++b) {
+        const unsigned long long t0 = gtime();
+        while (!mbar_try(&tfull[b], 0) && gtime() - t0 < kWaitNs) {
+        }
+      }
+    }
+    __syncwarp();
+    tmem_dealloc(tmem, 2 * SB);
+  }
+}
+
+// Final iterate (buffer chosen by the iteration count) -> dense FP64 D.
+__global__ void k_bsr_to_dense(const SP2State* st, Args a, Buf b0, Buf b1, Sym sy0, Sym sy1, double* D) {
+  if (st->err) return;  // D stays zero; the report carries the error
+  const Buf& b = (st->iters & 1) ? b1 : b0;
+  const int nblk = min(b.row_ptr[a.nsb], a.cap);
+  for (int o = blockIdx.x; o < nblk; o += gridDim.x) {
+    // the row of slot o: last row whose start is <= o
+    int lo = 0, hi = a.nsb;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (b.row_ptr[mid] <= o) lo = mid;
+      else hi = mid;
+    }
+    const int I = lo, J = b.col[o];
+    for (int e = threadIdx.x; e < kTiles; e += blockDim.x) {
+      const int r = I * SB + e / SB, c = J * SB + e % SB;
+      if (r < a.n && c < a.n) D[(size_t)r * a.n + c] = (double)b.val[(size_t)o * kTiles + e];
+    }
+  }
+}
+
+__global__ void k_bsr_report(SP2State* st, Args a, Buf b0, Buf b1, tb_sp2_report* rep, int* nblk_out) {
+  const Buf& b = (st->iters & 1) ? b1 : b0;
+  if (nblk_out) *nblk_out = min(b.row_ptr[a.nsb], a.cap);
+  if (!rep) return;
+  const double t1 = st->t1[st->iters], t2 = st->t2[st->iters];
+  int status = TB_OK;
+  if (st->err) status = st->err;
+  else if (fabs(t1 - a.nocc) > 0.25) status = TB_ERR_GAP;
+  rep->status = status;
+  rep->iters = st->iters;
+  rep->refine_iters = 0;
+  rep->n = a.n;
+  rep->eps_min = st->emin;
+  rep->eps_max = st->emax;
+  rep->trace = t1;
+  rep->idem_trace = t1 - t2;
+  rep->idem_fro = -1.0;
+  rep->branch_bits[0] = st->branch[0];
+  rep->branch_bits[1] = st->branch[1];
+  rep->refine_bits = 0;
+}
+
+struct BsrLayout {
+  int n, ld, nsb, cap, pcap;
+  size_t off_state, off_bparts, off_parts, off_scal, off_flags, off_cand, off_cnt, off_outrow, off_oldidx,
+      off_pcnt, off_pptr, off_pairs;
+  size_t off_rp[2], off_col[2], off_nz[2], off_st[2], off_lv[2], off_val[2], off_hi[2], off_lo[2];
+  size_t total;
+  int nparts;
+};
+
+BsrLayout bsr_layout(int n, int prec, int bpr, int nsm) {
+  BsrLayout L{};
+  L.n = n;
+  L.ld = round_up(std::max(n, 1), SB);
+  L.nsb = L.ld / SB;
+  const int per_row = (bpr <= 0 || bpr > L.nsb) ? L.nsb : bpr;
+  L.cap = L.nsb * per_row;
+  L.pcap = L.cap * per_row;
+  L.nparts = std::max(L.nsb, kMaxGrid);
+  (void)nsm;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o += (bytes + 1023) / 1024 * 1024;
+    return r;
+  };
+  const size_t eb = (prec == TB_PREC_TF32 || prec == TB_PREC_TF32X3) ? 4 : 2;
+  const bool split = prec == TB_PREC_TF32X3 || prec == TB_PREC_BF16X3;
+  L.off_state = take(sizeof(SP2State));
+  L.off_bparts = take(sizeof(double) * 2 * ((n + 7) / 8));
+  L.off_parts = take(sizeof(double) * 3 * 2 * L.nparts);
+  L.off_scal = take(sizeof(int) * 4);
+  L.off_flags = take(sizeof(uint16_t) * (size_t)L.nsb * L.nsb);
+  L.off_cand = take(sizeof(uint32_t) * MW * L.nsb);
+  L.off_cnt = take(sizeof(int) * L.nsb);
+  L.off_outrow = take(sizeof(int) * L.cap);
+  L.off_oldidx = take(sizeof(int) * L.cap);
+  L.off_pcnt = take(sizeof(int) * L.cap);
+  L.off_pptr = take(sizeof(int) * (L.cap + 1));
+  L.off_pairs = take(sizeof(int2) * (size_t)L.pcap);
+  for (int b = 0; b < 2; ++b) {
+    L.off_rp[b] = take(sizeof(int) * (L.nsb + 1));
+    L.off_col[b] = take(sizeof(int) * L.cap);
+    L.off_nz[b] = take(sizeof(int) * L.cap);
+    L.off_st[b] = take(sizeof(uint32_t) * MW * L.nsb);
+    L.off_lv[b] = take(sizeof(uint32_t) * MW * L.nsb);
+    L.off_val[b] = take(sizeof(float) * (size_t)L.cap * kTiles);
+    L.off_hi[b] = take(eb * (size_t)L.cap * kTiles);
+    L.off_lo[b] = split ? take(eb * (size_t)L.cap * kTiles) : 0;
+  }
+  L.total = o;
+  return L;
+}
+
+int make_block_map(tb_ctx* ctx, int prec, const void* base, int rows, CUtensorMap* map) {
+  const bool tf = prec == TB_PREC_TF32 || prec == TB_PREC_TF32X3;
+  const size_t eb = tf ? 4 : 2;
+  const cuuint64_t dims[2] = {(cuuint64_t)SB, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(SB * eb)};
+  const cuuint32_t box[2] = {(cuuint32_t)(128 / eb), 128};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = ctx->encode_tiled(map, tf ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                                 const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return tb_fail(ctx, TB_ERR_CUDA, "cuTensorMapEncodeTiled (blocks) failed (%d)", (int)r);
+  return TB_OK;
+}
+
+template <int P>
+int run_bsr(tb_ctx* ctx, const double* H, int n, double nocc, const tb_sp2_opts* o, double* D, void* ws,
+            size_t ws_bytes, tb_sp2_report* rep, cudaStream_t s) {
+  const BsrLayout L = bsr_layout(n, o->precision, o->bsr_blocks_per_row, ctx->sm_count);
+  if (ws_bytes < L.total)
+    return tb_fail(ctx, TB_ERR_ARG, "workspace %zu bytes < required %zu (block-sparse)", ws_bytes, L.total);
+  char* base = static_cast<char*>(ws);
+  SP2State* st = reinterpret_cast<SP2State*>(base + L.off_state);
+  double* bparts = reinterpret_cast<double*>(base + L.off_bparts);
+  double* parts = reinterpret_cast<double*>(base + L.off_parts);
+  double* slot[2] = {parts, parts + 3 * (size_t)L.nparts};
+  Sym sy{};
+  sy.cand = reinterpret_cast<uint32_t*>(base + L.off_cand);
+  sy.cnt = reinterpret_cast<int*>(base + L.off_cnt);
+  sy.out_row = reinterpret_cast<int*>(base + L.off_outrow);
+  sy.old_idx = reinterpret_cast<int*>(base + L.off_oldidx);
+  sy.pcnt = reinterpret_cast<int*>(base + L.off_pcnt);
+  sy.pair_ptr = reinterpret_cast<int*>(base + L.off_pptr);
+  sy.pairs = reinterpret_cast<int2*>(base + L.off_pairs);
+  sy.scal = reinterpret_cast<int*>(base + L.off_scal);
+  sy.flags = reinterpret_cast<uint16_t*>(base + L.off_flags);
+  Buf b[2];
+  for (int i = 0; i < 2; ++i) {
+    b[i].row_ptr = reinterpret_cast<int*>(base + L.off_rp[i]);
+    b[i].col = reinterpret_cast<int*>(base + L.off_col[i]);
+    b[i].nz = reinterpret_cast<int*>(base + L.off_nz[i]);
+    b[i].stored = reinterpret_cast<uint32_t*>(base + L.off_st[i]);
+    b[i].live = reinterpret_cast<uint32_t*>(base + L.off_lv[i]);
+    b[i].val = reinterpret_cast<float*>(base + L.off_val[i]);
+    b[i].hi = base + L.off_hi[i];
+    b[i].lo = L.off_lo[i] ? base + L.off_lo[i] : nullptr;
+  }
+  CUtensorMap mh[2], ml[2];
+  for (int i = 0; i < 2; ++i) {
+    int rc = make_block_map(ctx, o->precision, b[i].hi, L.cap * SB, &mh[i]);
+    if (rc) return rc;
+    if (b[i].lo) {
+      rc = make_block_map(ctx, o->precision, b[i].lo, L.cap * SB, &ml[i]);
+      if (rc) return rc;
+    } else {
+      ml[i] = mh[i];
+    }
+  }
+  Args a{};
+  a.n = n;
+  a.ld = L.ld;
+  a.nsb = L.nsb;
+  a.cap = L.cap;
+  a.pcap = L.pcap;
+  a.nocc = nocc;
+  a.tau2 = o->tau * o->tau;
+  a.tol = o->tol;
+  a.rule = o->rule;
+  a.max_iter = o->max_iter;
+  a.st = st;
+  {
+    const double u = (o->precision == TB_PREC_TF32X3 || o->precision == TB_PREC_BF16X3) ? 0x1p-24
+                     : o->precision == TB_PREC_TF32 ? 0x1p-11 : 0x1p-8;
+    a.floor = 2.0 * n * u;
+  }
+  ctx->prof_n[0] = ctx->prof_n[1] = 0;
+  TB_CUDA_TRY(ctx, cudaMemsetAsync(st, 0, sizeof(SP2State), s));
+  const int nb = (n + 7) / 8;
+  int rc = sp2_launch_bounds(ctx, H, n, bparts, s);
+  if (rc) return rc;
+  k_bsr_bounds<<<1, 32, 0, s>>>(bparts, nb, st);
+  TB_LAUNCH_CHECK(ctx);
+  k_bsr_init_flags<<<dim3(L.nsb, L.nsb), 256, 0, s>>>(H, a, sy);
+  TB_LAUNCH_CHECK(ctx);
+  k_bsr_init_rows<<<L.nsb, 256, 0, s>>>(a, sy, b[0]);
+  TB_LAUNCH_CHECK(ctx);
+  k_bsr_scan_rows<<<1, 32, 0, s>>>(a, sy, b[0].row_ptr);
+  TB_LAUNCH_CHECK(ctx);
+  a.parts_out = slot[0];
+  k_bsr_init_fill<P><<<L.nsb, 256, 0, s>>>(H, a, sy, b[0]);
+  TB_LAUNCH_CHECK(ctx);
+
+  using Cf = Prec<P>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    TB_CUDA_TRY(ctx, cudaFuncSetAttribute(k_bsr_step_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          Cf::smem_bytes));
+    attr_set = true;
+  }
+  const int grid = std::max(1, std::min(ctx->sm_count, kMaxGrid));
+  tb_prof_mark(ctx, 0, 0, s);
+  for (int k = 0; k <= o->max_iter; ++k) {
+    a.k = k;
+    a.parts_in = slot[k & 1];
+    a.nparts_in = k == 0 ? L.nsb : grid;
+    a.parts_out = slot[(k + 1) & 1];
+    Buf& bo = b[k & 1];
+    Buf& bn = b[(k + 1) & 1];
+    k_bsr_decide<<<L.nsb, 128, 0, s>>>(a, bo);
+    k_bsr_cand<<<L.nsb, 256, 0, s>>>(a, bo, sy);
+    k_bsr_scan_rows<<<1, 32, 0, s>>>(a, sy, bn.row_ptr);
+    k_bsr_fill_out<<<L.nsb, 256, 0, s>>>(a, bo, bn, sy);
+    k_bsr_scan_pairs<<<1, 1024, 0, s>>>(a, sy);
+    k_bsr_pairs<<<std::max(1, std::min(L.cap, 4096) / 128 + 1), 128, 0, s>>>(a, bo, bn, sy);
+    k_bsr_step_tc<P><<<grid, kThreads, Cf::smem_bytes, s>>>(a, mh[k & 1], ml[k & 1], bo, bn, sy);
+    TB_LAUNCH_CHECK(ctx);
+    tb_prof_mark(ctx, 0, k + 1, s);
+  }
+  TB_CUDA_TRY(ctx, cudaMemsetAsync(D, 0, sizeof(double) * (size_t)n * n, s));
+  k_bsr_to_dense<<<std::min(4096, std::max(1, L.cap)), 256, 0, s>>>(st, a, b[0], b[1], sy, sy, D);
+  TB_LAUNCH_CHECK(ctx);
+  k_bsr_report<<<1, 1, 0, s>>>(st, a, b[0], b[1], rep, nullptr);
+  TB_LAUNCH_CHECK(ctx);
+  return TB_OK;
+}
+
+}  // namespace
+
+int dm_sp2_bsr_workspace(int n, const tb_sp2_opts* o, int nsm, size_t* bytes) {
+  if (n > kMaxNsb * SB) return TB_ERR_UNSUPPORTED;
+  *bytes = bsr_layout(n, o->precision, o->bsr_blocks_per_row, nsm).total;
+  return TB_OK;
+}
+
+int dm_sp2_bsr(tb_ctx* ctx, const double* H, int n, double nocc, const tb_sp2_opts* o, double* D, void* ws,
+               size_t ws_bytes, tb_sp2_report* rep, cudaStream_t s) {
+  if (n > kMaxNsb * SB) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "block-sparse SP2 supports n <= %d", kMaxNsb * SB);
+  switch (o->precision) {
+    case TB_PREC_TF32: return run_bsr<TB_PREC_TF32>(ctx, H, n, nocc, o, D, ws, ws_bytes, rep, s);
+    case TB_PREC_TF32X3: return run_bsr<TB_PREC_TF32X3>(ctx, H, n, nocc, o, D, ws, ws_bytes, rep, s);
+    case TB_PREC_BF16: return run_bsr<TB_PREC_BF16>(ctx, H, n, nocc, o, D, ws, ws_bytes, rep, s);
+    case TB_PREC_BF16X3: return run_bsr<TB_PREC_BF16X3>(ctx, H, n, nocc, o, D, ws, ws_bytes, rep, s);
+    default: return tb_fail(ctx, TB_ERR_UNSUPPORTED, "block-sparse SP2 needs a tensor-core precision");
+  }
+}

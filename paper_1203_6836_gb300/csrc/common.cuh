@@ -131,6 +131,14 @@ int sp2_oz_step(tb_ctx* ctx, const SP2StepArgs& a, const double* Xin, double* Xo
 int sp2_oz_max_ld();
 size_t sp2_oz_slice_bytes(int ld);
 
+// Gershgorin partial bounds of the rows of H (sp2.cu).
+int sp2_launch_bounds(tb_ctx* ctx, const double* H, int n, double* bparts, cudaStream_t s);
+
+// Thresholded block-sparse SP2 (bsr.cu).
+int dm_sp2_bsr_workspace(int n, const tb_sp2_opts* o, int nsm, size_t* bytes);
+int dm_sp2_bsr(tb_ctx* ctx, const double* H, int n, double nocc, const tb_sp2_opts* o, double* D, void* ws,
+               size_t ws_bytes, tb_sp2_report* rep, cudaStream_t s);
+
 // Encode a 2D row-major tensor map over an ld x ld operand array for the
 // tensor-core kernel (gemm_tc.cu).
 int sp2_tc_make_map(tb_ctx* ctx, int precision, const void* base, int ld, CUtensorMap* map);

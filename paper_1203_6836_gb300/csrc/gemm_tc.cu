@@ -31,60 +31,8 @@ using namespace tcx;
 constexpr int BM = 128, BN = 128;
 constexpr int TILE_BYTES = 128 * 128;  // 128 rows x 128 bytes
 constexpr int kThreads = 192;
+constexpr int kGroup = 8;  // tile-rows swept together (L2 locality)
 
-template <int P>
-struct Prec {
-  static constexpr bool tf32 = (P == TB_PREC_TF32 || P == TB_PREC_TF32X3);
-  static constexpr bool split = (P == TB_PREC_TF32X3 || P == TB_PREC_BF16X3);
-  static constexpr int eb = tf32 ? 4 : 2;          // operand bytes
-  static constexpr int bk = 128 / eb;              // elements per 128-byte row
-  static constexpr int uk = 32 / eb;               // K of one MMA instruction
-  static constexpr int nop = split ? 2 : 1;        // operand arrays
-  static constexpr int stage_bytes = 2 * nop * TILE_BYTES;
-  static constexpr int stages = split ? 3 : 6;
-  static constexpr int smem_bytes = stages * stage_bytes + 1024;
-};
-
-// Operand split of a row segment of 32 FP32 values into hi (and lo).
-template <int P>
-__device__ __forceinline__ void store_operands(const float (&y)[32], void* hi_row, void* lo_row) {
-  if constexpr (Prec<P>::tf32) {
-    uint4* h = reinterpret_cast<uint4*>(hi_row);
-    uint4* l = reinterpret_cast<uint4*>(lo_row);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      float hv[4], lv[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        hv[t] = to_tf32(y[4 * j + t]);
-        lv[t] = to_tf32(y[4 * j + t] - hv[t]);
-      }
-      h[j] = make_uint4(__float_as_uint(hv[0]), __float_as_uint(hv[1]), __float_as_uint(hv[2]),
-                        __float_as_uint(hv[3]));
-      if constexpr (Prec<P>::split)
-        l[j] = make_uint4(__float_as_uint(lv[0]), __float_as_uint(lv[1]), __float_as_uint(lv[2]),
-                          __float_as_uint(lv[3]));
-    }
-  } else {
-    uint4* h = reinterpret_cast<uint4*>(hi_row);
-    uint4* l = reinterpret_cast<uint4*>(lo_row);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      uint32_t hw[4], lw[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const float a0 = y[8 * j + 2 * t], a1 = y[8 * j + 2 * t + 1];
-        const __nv_bfloat16 h0 = __float2bfloat16_rn(a0), h1 = __float2bfloat16_rn(a1);
-        const __nv_bfloat16 l0 = __float2bfloat16_rn(a0 - __bfloat162float(h0));
-        const __nv_bfloat16 l1 = __float2bfloat16_rn(a1 - __bfloat162float(h1));
-        hw[t] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-        lw[t] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-      }
-      h[j] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-      if constexpr (Prec<P>::split) l[j] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-    }
-  }
-}
 
 // X0 (FP32 master) -> operand arrays, elementwise.
 template <int P>
@@ -164,7 +112,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (stop) return;
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  // L2-aware raster: consecutive CTAs sweep a group of kGroup tile-rows
+  // column by column, so a wave of CTAs reads a compact set of row blocks of X
+  int tm, tn;
+  {
+    const int nt = gridDim.x;  // tiles per dimension (square grid)
+    const int pid = blockIdx.y * nt + blockIdx.x;
+    const int per_group = kGroup * nt;
+    const int g = pid / per_group;
+    const int first = g * kGroup;
+    const int gsize = min(kGroup, nt - first);
+    const int r = pid % per_group;
+    tm = first + r % gsize;
+    tn = r / gsize;
+  }
+  const int m0 = tm * BM, n0 = tn * BN;
   const int nk = a.ld / C::bk;
 
   if (threadIdx.x == 0) {

@@ -380,9 +380,16 @@ __global__ void __launch_bounds__(256) k_finalize(SP2State* st, int n, int ld, i
 
 }  // namespace
 
+int sp2_launch_bounds(tb_ctx* ctx, const double* H, int n, double* bparts, cudaStream_t s) {
+  k_bounds<<<(n + 7) / 8, 256, 0, s>>>(H, n, bparts);
+  TB_LAUNCH_CHECK(ctx);
+  return TB_OK;
+}
+
 extern "C" int dm_sp2_workspace_size(int n, const tb_sp2_opts* o, size_t* bytes) {
   if (!o || !bytes || n < 1) return TB_ERR_ARG;
   if (o->precision < TB_PREC_FP64 || o->precision > TB_PREC_BF16X3) return TB_ERR_ARG;
+  if (o->tau > 0.0) return dm_sp2_bsr_workspace(n, o, 0, bytes);
   *bytes = make_layout(n, o->precision, o->refine_iters, o->refine_mode).total;
   return TB_OK;
 }
@@ -401,6 +408,13 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
   if (!(nocc >= 0.0) || nocc > n) return tb_fail(ctx, TB_ERR_ARG, "n_occ %g outside [0, n]", nocc);
   const bool tc = o->precision != TB_PREC_FP64;
   const int refine = tc ? o->refine_iters : 0;
+  if (o->tau < 0.0) return tb_fail(ctx, TB_ERR_ARG, "tau %g < 0", o->tau);
+  if (o->tau > 0.0) {
+    if (!tc) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "block-sparse SP2 (tau > 0) needs a tensor-core precision");
+    if ((reinterpret_cast<uintptr_t>(ws) & 1023) != 0)
+      return tb_fail(ctx, TB_ERR_ARG, "workspace must be 1024-byte aligned");
+    return dm_sp2_bsr(ctx, H, n, nocc, o, D, ws, ws_bytes, rep, as_stream(stream));
+  }
   if (o->refine_mode < 0 || o->refine_mode > 1)
     return tb_fail(ctx, TB_ERR_ARG, "refine_mode %d outside 0..1", o->refine_mode);
   const Layout L = make_layout(n, o->precision, refine, o->refine_mode);

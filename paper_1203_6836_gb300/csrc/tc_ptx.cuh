@@ -3,6 +3,8 @@
 
 #include "common.cuh"
 
+#include <cuda_bf16.h>
+
 namespace tcx {
 
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits give up after 2 s
@@ -131,5 +133,62 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
+
+
+// Traits of the tensor-core precisions: operand bytes, elements per 128-byte
+// row (one 128B-swizzle atom), K of one MMA instruction, hi/lo split.
+template <int P>
+struct Prec {
+  static constexpr bool tf32 = (P == TB_PREC_TF32 || P == TB_PREC_TF32X3);
+  static constexpr bool split = (P == TB_PREC_TF32X3 || P == TB_PREC_BF16X3);
+  static constexpr int eb = tf32 ? 4 : 2;          // operand bytes
+  static constexpr int bk = 128 / eb;              // elements per 128-byte row
+  static constexpr int uk = 32 / eb;               // K of one MMA instruction
+  static constexpr int nop = split ? 2 : 1;        // operand arrays
+  static constexpr int stage_bytes = 2 * nop * 128 * 128;
+  static constexpr int stages = split ? 3 : 6;
+  static constexpr int smem_bytes = stages * stage_bytes + 1024;
+};
+
+// Operand split of a row segment of 32 FP32 values into hi (and lo).
+template <int P>
+__device__ __forceinline__ void store_operands(const float (&y)[32], void* hi_row, void* lo_row) {
+  if constexpr (Prec<P>::tf32) {
+    uint4* h = reinterpret_cast<uint4*>(hi_row);
+    uint4* l = reinterpret_cast<uint4*>(lo_row);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      float hv[4], lv[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        hv[t] = to_tf32(y[4 * j + t]);
+        lv[t] = to_tf32(y[4 * j + t] - hv[t]);
+      }
+      h[j] = make_uint4(__float_as_uint(hv[0]), __float_as_uint(hv[1]), __float_as_uint(hv[2]),
+                        __float_as_uint(hv[3]));
+      if constexpr (Prec<P>::split)
+        l[j] = make_uint4(__float_as_uint(lv[0]), __float_as_uint(lv[1]), __float_as_uint(lv[2]),
+                          __float_as_uint(lv[3]));
+    }
+  } else {
+    uint4* h = reinterpret_cast<uint4*>(hi_row);
+    uint4* l = reinterpret_cast<uint4*>(lo_row);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const float a0 = y[8 * j + 2 * t], a1 = y[8 * j + 2 * t + 1];
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(a0), h1 = __float2bfloat16_rn(a1);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(a0 - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(a1 - __bfloat162float(h1));
+        hw[t] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        lw[t] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+      }
+      h[j] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      if constexpr (Prec<P>::split) l[j] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+  }
+}
 
 }  // namespace tcx

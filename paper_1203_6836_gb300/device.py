@@ -49,10 +49,13 @@ REFINE = {"emulated": 0, "fp64": 1}
 
 
 def sp2_opts(precision: str = "fp64", max_iter: int = 100, tol: float = 1e-10, refine: int = 2,
-             rule: int = 0, refine_mode: str = "emulated") -> tbmd.tb_sp2_opts:
-    """refine_mode: "emulated" (exact-slice FP64 emulation on the tensor cores) or "fp64" (FMA)."""
+             rule: int = 0, refine_mode: str = "emulated", tau: float = 0.0,
+             blocks_per_row: int = 0) -> tbmd.tb_sp2_opts:
+    """refine_mode: "emulated" (exact-slice FP64 emulation on the tensor cores) or "fp64" (FMA);
+    tau > 0 selects the thresholded block-sparse path."""
     return tbmd.tb_sp2_opts(precision=tbmd.PREC[precision], max_iter=max_iter, tol=tol,
-                            refine_iters=refine, rule=rule, refine_mode=REFINE[refine_mode])
+                            refine_iters=refine, rule=rule, refine_mode=REFINE[refine_mode], tau=tau,
+                            bsr_blocks_per_row=blocks_per_row)
 
 
 def xl_params(dt: float, kappa: float, alpha: float, c) -> tbmd.tb_xl_params:

@@ -57,7 +57,8 @@ class tb_system(ctypes.Structure):
 
 class tb_sp2_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
-                ("refine_iters", ctypes.c_int), ("rule", ctypes.c_int), ("refine_mode", ctypes.c_int)]
+                ("refine_iters", ctypes.c_int), ("rule", ctypes.c_int), ("refine_mode", ctypes.c_int),
+                ("tau", ctypes.c_double), ("bsr_blocks_per_row", ctypes.c_int)]
 
 
 class tb_sp2_report(ctypes.Structure):

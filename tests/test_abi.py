@@ -24,7 +24,8 @@ def test_binding_covers_every_header_function():
 def test_status_strings_and_argument_errors_without_gpu():
     lib = tbmd.lib()
     assert lib.tb_status_string(tbmd.TB_ERR_ARG) == b"invalid argument"
-    opts = tbmd.tb_sp2_opts(precision=0, max_iter=100, tol=1e-10, refine_iters=0, rule=0, refine_mode=1)
+    opts = tbmd.tb_sp2_opts(precision=0, max_iter=100, tol=1e-10, refine_iters=0, rule=0, refine_mode=1, tau=0.0,
+                            bsr_blocks_per_row=0)
     assert lib.dm_sp2_workspace_size(0, ctypes.byref(opts), ctypes.byref(ctypes.c_size_t())) == tbmd.TB_ERR_ARG
     size = ctypes.c_size_t()
     assert lib.dm_sp2_workspace_size(4094, ctypes.byref(opts), ctypes.byref(size)) == tbmd.TB_OK
