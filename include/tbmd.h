@@ -188,6 +188,43 @@ int dm_sp2(tb_ctx* ctx, const double* H, int n, double n_occ, const tb_sp2_opts*
 int dm_sp2_static(tb_ctx* ctx, const double* H, int n, double n_occ, const tb_sp2_opts* opts,
                   double* D, tb_sp2_report* report, void* stream);
 
+/* ------------------------------------------------- a10: finite temperature */
+
+/* Options of dm_fermi. */
+typedef struct {
+  int precision;      /* tensor-core precision of the products: TB_PREC_TF32 .. TB_PREC_BF16X3 */
+  int m;              /* doubling steps (0: 16); needs beta max|eps - mu| <= 2^(m+1) */
+  int ns_iters;       /* Newton-Schulz steps per inverse, counting the first (0: 4) */
+  int mu_iters;       /* cap on chemical-potential updates (one expansion each), 1..40 */
+  double trace_tol;   /* stop when |Tr D - N_occ| <= trace_tol (0: 1e-7 max(1, N_occ)) */
+} tb_fermi_opts;
+
+/* Written on the device by dm_fermi. */
+typedef struct {
+  int status;         /* TB_OK, TB_ERR_NOT_CONVERGED (trace not reached), TB_ERR_TIMEOUT */
+  int mu_iters;       /* expansions performed */
+  int m;              /* doubling steps per expansion */
+  int n;
+  double mu;          /* chemical potential of the returned D */
+  double trace;       /* Tr D */
+  double trace_dd;    /* Tr D(I - D) (= dTr D/dmu / beta) */
+  double eps_min, eps_max;
+} tb_fermi_report;
+
+int dm_fermi_workspace_size(int n, const tb_fermi_opts* opts, size_t* bytes);
+
+/* D = (exp(beta (H - mu I)) + 1)^-1, beta = 1/kT, with mu such that
+ * Tr D = n_occ (Eq. EL_4c, Eq. DM_perp; canonical), by the GEMM-only
+ * recursive Fermi-operator expansion: from X0 = I/2 - beta/2^(m+2) (H - mu I),
+ * m steps X <- X^2 [X^2 + (I - X)^2]^-1, each doubling beta, carried out on
+ * E = X - I/2 as E <- 2E (I + 4E^2)^-1 (inverse by Newton-Schulz).  mu: safeguarded Newton steps with dTr D/dmu =
+ * beta Tr[D(I - D)] inside a bisection bracket, all on the device.
+ *   H [n*n], D [n*n] (FP64); mu: device double, in = initial guess (NaN: the
+ *   spectral midpoint), out = chemical potential of D; report: device or NULL. */
+int dm_fermi(tb_ctx* ctx, const double* H, int n, double n_occ, double kT, const tb_fermi_opts* opts,
+             double* D, double* mu, void* workspace, size_t workspace_bytes, tb_fermi_report* report,
+             void* stream);
+
 /* ------------------------------------------------------------- a7: charges */
 
 /* Mulliken net charges q_i = 2 sum_{a in i} D_aa - N0_i (App. D).

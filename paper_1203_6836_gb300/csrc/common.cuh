@@ -131,6 +131,25 @@ int sp2_oz_step(tb_ctx* ctx, const SP2StepArgs& a, const double* Xin, double* Xo
 int sp2_oz_max_ld();
 size_t sp2_oz_slice_bytes(int ld);
 
+// Generic tensor-core product out = alpha A B + beta E + gamma I of symmetric,
+// commuting matrices (gemm_tc.cu); all matrices ld x ld, FP32 masters with
+// operand splits; parts (2 doubles per CTA: Tr out, ||out||^2) optional.
+struct GemmArgs {
+  int n, ld;
+  float alpha, beta, gamma;
+  const float* E;
+  float* out;
+  void* ohi;
+  void* olo;
+  double* parts;
+  const int* skip;
+  int* err;
+};
+int tc_gemm(tb_ctx* ctx, int precision, const GemmArgs& g, const CUtensorMap* ah, const CUtensorMap* al,
+            const CUtensorMap* bh, const CUtensorMap* bl, cudaStream_t s);
+int tc_split(tb_ctx* ctx, int precision, const float* X, size_t count, void* hi, void* lo, const int* skip,
+             cudaStream_t s);
+
 // Gershgorin partial bounds of the rows of H (sp2.cu).
 int sp2_launch_bounds(tb_ctx* ctx, const double* H, int n, double* bparts, cudaStream_t s);
 

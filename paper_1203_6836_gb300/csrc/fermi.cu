@@ -1,0 +1,351 @@
+// Finite-temperature density matrix (row a10): the Fermi operator
+// D = (exp(beta (H - mu I)) + 1)^-1 with Tr D = N_occ (Eq. EL_4c,
+// Eq. DM_perp; canonical reading), by a GEMM-only recursive expansion.
+//
+// With y = 1/(1 + e^t), y^2 / (y^2 + (1 - y)^2) = 1/(1 + e^{2t}): one step of
+// X <- X^2 [X^2 + (I - X)^2]^-1 doubles the inverse temperature.  Starting
+// from the linearised X0 = I/2 - beta/2^{m+2} (H - mu I) (f at beta/2^m), m
+// steps give f at beta.  The steps are carried out on the deviation
+// E = X - I/2, for which the same map reads
+//   E <- 2 E (I + 4 E^2)^-1                        (tanh double-angle form)
+// E is small while the early steps double it, so FP32-level products keep a
+// relative accuracy there (errors add up over the m steps instead of being
+// doubled m times as absolute errors of X would be).  Per step:
+//   A = I + 4 E E                                  (one product, affine epilogue;
+//                                                   spectrum in [1, 2])
+//   Z = A^-1: Z1 = 4/3 I - 4/9 A, then Newton-Schulz Z <- Z (2I - A Z)
+//   E <- 2 E Z                                     (one product)
+//   E <- (E + E^T)/2                               (rounding breaks the exact
+//                                                   commutation of the factors)
+// All factors are functions of H, hence symmetric and commuting, so every
+// product is a tensor-core GEMM with the second operand read by rows.
+// D = I/2 + E on the n x n block.
+// The chemical potential: safeguarded Newton steps on Tr D(mu) = N_occ with
+// dTr D/dmu = beta Tr[D(I - D)] inside a bisection bracket, one full
+// expansion per step; every decision is taken on the device.
+
+#include "common.cuh"
+
+#include <algorithm>
+#include <math.h>
+
+namespace {
+
+constexpr int kTile = 128;
+constexpr int kMaxMu = 40;
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+struct FoeState {
+  double mu, lo, hi;
+  double emin, emax;
+  int done, iters, capped, err;
+  double tr[kMaxMu + 1], trdd[kMaxMu + 1], mus[kMaxMu + 1];
+};
+
+struct Mat {
+  float* m;
+  void* hi;
+  void* lo;
+  CUtensorMap mh, ml;
+};
+
+__global__ void k_foe_bounds(const double* bparts, int nb, FoeState* st, const double* mu_in, double kT) {
+  double a = INFINITY, b = -INFINITY;
+  for (int i = threadIdx.x; i < nb; i += 32) {
+    a = fmin(a, bparts[2 * i]);
+    b = fmax(b, bparts[2 * i + 1]);
+  }
+  a = warp_min(a);
+  b = warp_max(b);
+  if (threadIdx.x == 0) {
+    st->emin = a;
+    st->emax = b;
+    st->lo = a - 40.0 * kT - 1.0;
+    st->hi = b + 40.0 * kT + 1.0;
+    const double g = mu_in ? *mu_in : NAN;
+    st->mu = (isfinite(g) && g > st->lo && g < st->hi) ? g : 0.5 * (a + b);
+  }
+}
+
+// E0 = -c (H - mu I) on the n x n block (X0 = I/2 + E0), zero in the padding.
+__global__ void __launch_bounds__(256) k_foe_x0(const double* __restrict__ H, int n, int ld, const FoeState* st,
+                                                double c, float* __restrict__ X) {
+  if (st->done || st->err) return;
+  const double mu = st->mu;
+  const size_t total = (size_t)ld * ld;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ld), col = (int)(e % ld);
+    double x = 0.0;
+    if (r < n && col < n) x = (r == col ? c * mu : 0.0) - c * H[(size_t)r * n + col];
+    X[e] = (float)x;
+  }
+}
+
+// Z1 = 4/3 I - 4/9 A on the n x n block (padding stays zero): one
+// Newton-Schulz step from Z0 = 2/3 I, leaving ||I - A Z1|| <= 1/9.
+__global__ void __launch_bounds__(256) k_foe_z1(const FoeState* st, int n, int ld, const float* __restrict__ A,
+                                                float* __restrict__ Z) {
+  if (st->done || st->err) return;
+  const size_t total = (size_t)ld * ld;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ld), col = (int)(e % ld);
+    Z[e] = (r == col && r < n ? (4.0f / 3.0f) : 0.0f) - (4.0f / 9.0f) * A[e];
+  }
+}
+
+// X <- (X + X^T)/2 in place, 32 x 32 tile pairs through shared memory.  The
+// factors commute only up to rounding, so every product P Q^T of the
+// tensor-core kernel leaves an antisymmetric error that the doubling steps
+// would amplify; the symmetric part is the exact-arithmetic value.  Also
+// refreshes the trace partials (Tr X, ||X||_F^2) when parts != nullptr.
+__global__ void __launch_bounds__(256) k_foe_sym(const FoeState* st, int ld, float* __restrict__ X,
+                                                 double* __restrict__ parts) {
+  __shared__ float a[32][33], b[32][33];
+  if (st->done || st->err) return;
+  const int nt = ld / 32;
+  // blockIdx.x enumerates tile pairs (I <= J) row by row
+  int p = blockIdx.x, I = 0;
+  while (p >= nt - I) {
+    p -= nt - I;
+    ++I;
+  }
+  const int J = I + p;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int r = ty; r < 32; r += 8) {
+    a[r][tx] = X[(size_t)(32 * I + r) * ld + 32 * J + tx];
+    b[r][tx] = X[(size_t)(32 * J + r) * ld + 32 * I + tx];
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const float v = 0.5f * (a[r][tx] + b[tx][r]);
+    X[(size_t)(32 * I + r) * ld + 32 * J + tx] = v;
+    X[(size_t)(32 * J + tx) * ld + 32 * I + r] = v;
+  }
+}
+
+// After an expansion: Tr E and ||E||_F^2 from the last product's partials
+// give Tr D = n/2 + Tr E and Tr D(I - D) = n/4 - ||E||_F^2; then the stop
+// test and the next mu (one block, every quantity FP64).
+__global__ void k_foe_mu(FoeState* st, const double* parts, int np, int n, double nocc, double beta, double tol,
+                         int it, int max_it) {
+  if (st->done || st->err) return;
+  double x = 0.0, y = 0.0;
+  for (int i = threadIdx.x; i < np; i += 32) {
+    x += parts[2 * i];
+    y += parts[2 * i + 1];
+  }
+  x = warp_sum(x);
+  y = warp_sum(y);
+  if (threadIdx.x != 0) return;
+  const double mu = st->mu;
+  const double trd = 0.5 * n + x;
+  const double trdd = 0.25 * n - y;  // Tr D(I - D)
+  x = trd;
+  y = trd - trdd;  // ||D||_F^2
+  st->tr[it] = x;
+  st->trdd[it] = x - y;
+  st->mus[it] = mu;
+  st->iters = it + 1;
+  const double dev = x - nocc;
+  if (fabs(dev) <= tol) {
+    st->done = 1;
+    return;
+  }
+  if (it + 1 >= max_it) {
+    st->done = 1;
+    st->capped = 1;
+    return;
+  }
+  if (dev < 0.0) st->lo = mu;
+  else st->hi = mu;
+  const double slope = beta * (x - y);
+  double next = slope > 1e-12 ? mu - dev / slope : NAN;
+  if (!(next > st->lo && next < st->hi)) next = 0.5 * (st->lo + st->hi);
+  st->mu = next;
+}
+
+// Copy the last X of expansion `it` into the result buffer, only when that
+// expansion ran (a converged outer loop skips the later ones).
+__global__ void __launch_bounds__(256) k_foe_keep(const FoeState* st, int it, size_t count,
+                                                  const float* __restrict__ src, float* __restrict__ dst) {
+  if (st->iters != it + 1 || src == dst) return;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = src[e];
+}
+
+__global__ void __launch_bounds__(256) k_foe_finalize(const FoeState* st, int n, int ld, const float* __restrict__ X,
+                                                      double* __restrict__ D, double nocc, double tol, int m,
+                                                      double* mu_out, tb_fermi_report* rep) {
+  const size_t total = (size_t)n * n;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / n), c = (int)(e % n);
+    D[e] = (double)X[(size_t)r * ld + c] + (r == c ? 0.5 : 0.0);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int it = st->iters > 0 ? st->iters - 1 : 0;
+    const double mu = st->mus[it];
+    if (mu_out) *mu_out = mu;
+    if (rep) {
+      rep->status = st->err ? st->err : (fabs(st->tr[it] - nocc) <= tol ? TB_OK : TB_ERR_NOT_CONVERGED);
+      rep->mu_iters = st->iters;
+      rep->m = m;
+      rep->n = n;
+      rep->mu = mu;
+      rep->trace = st->tr[it];
+      rep->trace_dd = st->trdd[it];
+      rep->eps_min = st->emin;
+      rep->eps_max = st->emax;
+    }
+  }
+}
+
+struct FoeLayout {
+  int ld;
+  size_t off_state, off_bparts, off_parts, off_mat[5][3], off_res, total;
+  int nparts;
+};
+
+FoeLayout foe_layout(int n, int prec) {
+  FoeLayout L{};
+  L.ld = round_up(std::max(n, 1), kTile);
+  L.nparts = (L.ld / kTile) * (L.ld / kTile);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o += (bytes + 1023) / 1024 * 1024;
+    return r;
+  };
+  const size_t nn = (size_t)L.ld * L.ld;
+  const size_t eb = (prec == TB_PREC_TF32 || prec == TB_PREC_TF32X3) ? 4 : 2;
+  const bool split = prec == TB_PREC_TF32X3 || prec == TB_PREC_BF16X3;
+  L.off_state = take(sizeof(FoeState));
+  L.off_bparts = take(sizeof(double) * 2 * ((n + 7) / 8));
+  L.off_parts = take(sizeof(double) * 2 * (size_t)L.nparts);
+  for (int i = 0; i < 5; ++i) {
+    L.off_mat[i][0] = take(sizeof(float) * nn);
+    L.off_mat[i][1] = take(eb * nn);
+    L.off_mat[i][2] = split ? take(eb * nn) : 0;
+  }
+  L.off_res = take(sizeof(float) * nn);
+  L.total = o;
+  return L;
+}
+
+int valid_opts(const tb_fermi_opts* o) {
+  return o && o->precision >= TB_PREC_TF32 && o->precision <= TB_PREC_BF16X3 && o->m >= 0 && o->m <= 40 &&
+         o->ns_iters >= 0 && o->ns_iters <= 12 && o->mu_iters >= 1 && o->mu_iters <= kMaxMu;
+}
+
+}  // namespace
+
+extern "C" int dm_fermi_workspace_size(int n, const tb_fermi_opts* o, size_t* bytes) {
+  if (!bytes || n < 1 || !valid_opts(o)) return TB_ERR_ARG;
+  *bytes = foe_layout(n, o->precision).total;
+  return TB_OK;
+}
+
+extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double kT, const tb_fermi_opts* o,
+                        double* D, double* mu, void* ws, size_t ws_bytes, tb_fermi_report* rep, void* stream) {
+  if (!ctx) return TB_ERR_ARG;
+  if (!H || !D || !ws) return tb_fail(ctx, TB_ERR_ARG, "null argument to dm_fermi");
+  if (n < 1 || !(kT > 0.0) || !(nocc >= 0.0) || nocc > n) return tb_fail(ctx, TB_ERR_ARG, "bad n, kT or n_occ");
+  if (!valid_opts(o)) return tb_fail(ctx, TB_ERR_ARG, "invalid tb_fermi_opts");
+  const FoeLayout L = foe_layout(n, o->precision);
+  if (ws_bytes < L.total) return tb_fail(ctx, TB_ERR_ARG, "workspace %zu bytes < required %zu", ws_bytes, L.total);
+  if ((reinterpret_cast<uintptr_t>(ws) & 1023) != 0) return tb_fail(ctx, TB_ERR_ARG, "workspace must be 1024-byte aligned");
+  cudaStream_t s = as_stream(stream);
+  char* base = static_cast<char*>(ws);
+  FoeState* st = reinterpret_cast<FoeState*>(base + L.off_state);
+  double* bparts = reinterpret_cast<double*>(base + L.off_bparts);
+  double* parts = reinterpret_cast<double*>(base + L.off_parts);
+  Mat M[5];  // X, A, Z, T, Y (next X)
+  for (int i = 0; i < 5; ++i) {
+    M[i].m = reinterpret_cast<float*>(base + L.off_mat[i][0]);
+    M[i].hi = base + L.off_mat[i][1];
+    M[i].lo = L.off_mat[i][2] ? base + L.off_mat[i][2] : nullptr;
+    int rc = sp2_tc_make_map(ctx, o->precision, M[i].hi, L.ld, &M[i].mh);
+    if (rc) return rc;
+    if (M[i].lo) {
+      rc = sp2_tc_make_map(ctx, o->precision, M[i].lo, L.ld, &M[i].ml);
+      if (rc) return rc;
+    } else {
+      M[i].ml = M[i].mh;
+    }
+  }
+  const double beta = 1.0 / kT;
+  const int m = o->m > 0 ? o->m : 16;
+  const int ns = o->ns_iters > 0 ? o->ns_iters : 4;
+  const double tol = o->trace_tol > 0.0 ? o->trace_tol : 1e-7 * std::max(1.0, nocc);
+  const double c = beta / std::ldexp(1.0, m + 2);
+  const size_t nn = (size_t)L.ld * L.ld;
+  int* skip = &st->done;
+  int* errp = &st->err;
+  float* res = reinterpret_cast<float*>(base + L.off_res);
+
+  TB_CUDA_TRY(ctx, cudaMemsetAsync(st, 0, sizeof(FoeState), s));
+  int rc = sp2_launch_bounds(ctx, H, n, bparts, s);
+  if (rc) return rc;
+  k_foe_bounds<<<1, 32, 0, s>>>(bparts, (n + 7) / 8, st, mu, kT);
+  TB_LAUNCH_CHECK(ctx);
+
+  auto gemm = [&](Mat& A, Mat& B, Mat& out, float alpha, float betac, const float* E, float gamma,
+                  double* prt) -> int {
+    GemmArgs g{};
+    g.n = n;
+    g.ld = L.ld;
+    g.alpha = alpha;
+    g.beta = betac;
+    g.gamma = gamma;
+    g.E = E;
+    g.out = out.m;
+    g.ohi = out.hi;
+    g.olo = out.lo;
+    g.parts = prt;
+    g.skip = skip;
+    g.err = errp;
+    return tc_gemm(ctx, o->precision, g, &A.mh, &A.ml, &B.mh, &B.ml, s);
+  };
+  const int ntile = L.ld / 32;
+  const int ntp = ntile * (ntile + 1) / 2;
+  for (int it = 0; it < o->mu_iters; ++it) {
+    Mat* X = &M[0];
+    Mat* A = &M[1];
+    Mat* Z = &M[2];
+    Mat* T = &M[3];
+    Mat* Y = &M[4];
+    k_foe_x0<<<1184, 256, 0, s>>>(H, n, L.ld, st, c, X->m);
+    TB_LAUNCH_CHECK(ctx);
+    rc = tc_split(ctx, o->precision, X->m, nn, X->hi, X->lo, skip, s);
+    if (rc) return rc;
+    for (int step = 0; step < m; ++step) {
+      // A = I + 4 E E
+      if ((rc = gemm(*X, *X, *A, 4.0f, 0.0f, nullptr, 1.0f, nullptr))) return rc;
+      // Z1 = 4/3 I - 4/9 A, then Newton-Schulz
+      k_foe_z1<<<1184, 256, 0, s>>>(st, n, L.ld, A->m, Z->m);
+      TB_LAUNCH_CHECK(ctx);
+      if ((rc = tc_split(ctx, o->precision, Z->m, nn, Z->hi, Z->lo, skip, s))) return rc;
+      for (int k = 1; k < ns; ++k) {
+        if ((rc = gemm(*A, *Z, *T, -1.0f, 0.0f, nullptr, 2.0f, nullptr))) return rc;  // T = 2I - A Z
+        if ((rc = gemm(*Z, *T, *Y, 1.0f, 0.0f, nullptr, 0.0f, nullptr))) return rc;   // Z <- Z T
+        std::swap(Z, Y);
+      }
+      // E <- 2 E Z (trace partials of the last step), then its symmetric
+      // part and fresh operand splits
+      const bool last = step == m - 1;
+      if ((rc = gemm(*X, *Z, *Y, 2.0f, 0.0f, nullptr, 0.0f, last ? parts : nullptr))) return rc;
+      std::swap(X, Y);
+      k_foe_sym<<<ntp, 256, 0, s>>>(st, L.ld, X->m, nullptr);
+      TB_LAUNCH_CHECK(ctx);
+      if (!last && (rc = tc_split(ctx, o->precision, X->m, nn, X->hi, X->lo, skip, s))) return rc;
+    }
+    k_foe_mu<<<1, 32, 0, s>>>(st, parts, L.nparts, n, nocc, beta, tol, it, o->mu_iters);
+    TB_LAUNCH_CHECK(ctx);
+    k_foe_keep<<<1184, 256, 0, s>>>(st, it, nn, X->m, res);
+    TB_LAUNCH_CHECK(ctx);
+  }
+  const int fb = std::min(1184, (int)(((size_t)n * n + 255) / 256));
+  k_foe_finalize<<<fb, 256, 0, s>>>(st, n, L.ld, res, D, nocc, tol, m, mu, rep);
+  TB_LAUNCH_CHECK(ctx);
+  return TB_OK;
+}

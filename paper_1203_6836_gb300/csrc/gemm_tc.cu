@@ -331,3 +331,226 @@ int sp2_tc_step(tb_ctx* ctx, int precision, const SP2StepArgs& a, const CUtensor
     default: return tb_fail(ctx, TB_ERR_ARG, "precision %d has no tensor-core path", precision);
   }
 }
+
+// --------------------------------------------------------------------------
+// Generic product of two symmetric, mutually commuting matrices (functions of
+// the same H) for the Fermi-operator expansion:
+//   out = alpha * (A B) + beta * E + gamma * I
+// with A, B given as tensor-core operand splits (B symmetric, so its rows are
+// read K-major), E an optional FP32 matrix.  Writes the FP32 master and the
+// operand splits of `out` and FP64 partials (Tr out, ||out||_F^2).  Returns
+// at once when *skip is non-zero (device-side early exit of a converged
+// outer iteration).
+// --------------------------------------------------------------------------
+
+namespace {
+
+template <int P>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_tc(GemmArgs g, const __grid_constant__ CUtensorMap ah, const __grid_constant__ CUtensorMap al,
+              const __grid_constant__ CUtensorMap bh, const __grid_constant__ CUtensorMap bl) {
+  using C = Prec<P>;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[C::stages], empty[C::stages], tfull;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int s_abort;
+  __shared__ double s_red[4][2];
+  if (g.skip && *g.skip) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  int tm, tn;
+  {
+    const int nt = gridDim.x;
+    const int pid = blockIdx.y * nt + blockIdx.x;
+    const int per_group = kGroup * nt;
+    const int gi = pid / per_group;
+    const int first = gi * kGroup;
+    const int gsize = min(kGroup, nt - first);
+    const int r = pid % per_group;
+    tm = first + r % gsize;
+    tn = r / gsize;
+  }
+  const int m0 = tm * BM, n0 = tn * BN;
+  const int nk = g.ld / C::bk;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&tfull, 1);
+    s_abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_base, BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  if (warp == 0 && lane == 0) {
+    prefetch_map(&ah);
+    prefetch_map(&bh);
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % C::stages;
+      if (kb >= C::stages && !mbar_wait(&empty[s], ((kb / C::stages) - 1) & 1, &s_abort)) break;
+      uint8_t* base = smem + s * C::stage_bytes;
+      mbar_expect_tx(&full[s], C::stage_bytes);
+      tma_load_2d(base, &ah, &full[s], kb * C::bk, m0);
+      tma_load_2d(base + TILE_BYTES, &bh, &full[s], kb * C::bk, n0);
+      if constexpr (C::split) {
+        tma_load_2d(base + 2 * TILE_BYTES, &al, &full[s], kb * C::bk, m0);
+        tma_load_2d(base + 3 * TILE_BYTES, &bl, &full[s], kb * C::bk, n0);
+      }
+      issued = kb + 1;
+    }
+    if (s_abort) {
+      for (int kb = (issued > C::stages ? issued - C::stages : 0); kb < issued; ++kb) {
+        const unsigned long long t0 = gtime();
+        while (!mbar_try(&full[kb % C::stages], (kb / C::stages) & 1) && gtime() - t0 < kWaitNs) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t id = idesc(C::tf32 ? 2u : 1u);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % C::stages;
+      if (!mbar_wait(&full[s], (kb / C::stages) & 1, &s_abort)) break;
+      tc_fence_after();
+      const uint32_t base = smem_u32(smem + s * C::stage_bytes);
+#pragma unroll
+      for (int ks = 0; ks < C::bk / C::uk; ++ks) {
+        const uint32_t koff = ks * 32;
+        const uint64_t a0 = sdesc(base + koff), b0 = sdesc(base + TILE_BYTES + koff);
+        umma<C::tf32>(tmem, a0, b0, id, (kb | ks) != 0);
+        if constexpr (C::split) {
+          umma<C::tf32>(tmem, a0, sdesc(base + 3 * TILE_BYTES + koff), id, 1u);
+          umma<C::tf32>(tmem, sdesc(base + 2 * TILE_BYTES + koff), b0, id, 1u);
+        }
+      }
+      umma_commit(&empty[s]);
+    }
+    umma_commit(&tfull);
+  } else if (warp >= 2) {
+    double t1 = 0.0, t2 = 0.0;
+    const int q = warp & 3;
+    const int row = 32 * q + lane;
+    if (mbar_wait(&tfull, 0, &s_abort)) {
+      tc_fence_after();
+      const size_t gr = (size_t)(m0 + row);
+      const float* erow = g.E ? g.E + gr * g.ld + n0 : nullptr;
+      float* orow = g.out + gr * g.ld + n0;
+      char* hrow = static_cast<char*>(g.ohi) + (gr * g.ld + n0) * C::eb;
+      char* lrow = g.olo ? static_cast<char*>(g.olo) + (gr * g.ld + n0) * C::eb : hrow;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t v[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + 32 * c, v);
+        float y[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = n0 + 32 * c + j;
+          float val = g.alpha * __uint_as_float(v[j]);
+          if (erow) val = fmaf(g.beta, erow[32 * c + j], val);
+          if (col == (int)gr && (int)gr < g.n) val += g.gamma;
+          y[j] = val;
+          t2 += (double)val * (double)val;
+          if (col == (int)gr) t1 += (double)val;
+        }
+        float4* xo = reinterpret_cast<float4*>(orow + 32 * c);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) xo[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
+        store_operands<P>(y, hrow + 32 * c * C::eb, lrow + 32 * c * C::eb);
+      }
+    }
+    t1 = warp_sum(t1);
+    t2 = warp_sum(t2);
+    if (lane == 0) {
+      s_red[q][0] = t1;
+      s_red[q][1] = t2;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 64) {
+    if (g.parts) {
+      const int cta = blockIdx.y * gridDim.x + blockIdx.x;
+      g.parts[2 * cta] = s_red[0][0] + s_red[1][0] + s_red[2][0] + s_red[3][0];
+      g.parts[2 * cta + 1] = s_red[0][1] + s_red[1][1] + s_red[2][1] + s_red[3][1];
+    }
+    if (s_abort && g.err) atomicExch(g.err, TB_ERR_TIMEOUT);
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    if (s_abort && lane == 0) {
+      const unsigned long long t0 = gtime();
+      while (!mbar_try(&tfull, 0) && gtime() - t0 < kWaitNs) {
+      }
+    }
+    __syncwarp();
+    tmem_dealloc(tmem, BN);
+  }
+}
+
+template <int P>
+int launch_gemm(tb_ctx* ctx, const GemmArgs& g, const CUtensorMap* ah, const CUtensorMap* al,
+                const CUtensorMap* bh, const CUtensorMap* bl, cudaStream_t s) {
+  using C = Prec<P>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    TB_CUDA_TRY(ctx, cudaFuncSetAttribute(k_gemm_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes));
+    attr_set = true;
+  }
+  const dim3 grid(g.ld / BN, g.ld / BM);
+  k_gemm_tc<P><<<grid, kThreads, C::smem_bytes, s>>>(g, *ah, *al, *bh, *bl);
+  TB_LAUNCH_CHECK(ctx);
+  return TB_OK;
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_split_only(const float* __restrict__ X, size_t count, void* hi, void* lo,
+                                                    const int* skip) {
+  if (skip && *skip) return;
+  const size_t segs = count / 32;
+  for (size_t sidx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; sidx < segs;
+       sidx += (size_t)gridDim.x * blockDim.x) {
+    float y[32];
+    const float4* src = reinterpret_cast<const float4*>(X + sidx * 32);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float4 v = src[j];
+      y[4 * j] = v.x;
+      y[4 * j + 1] = v.y;
+      y[4 * j + 2] = v.z;
+      y[4 * j + 3] = v.w;
+    }
+    char* h = static_cast<char*>(hi) + sidx * 32 * Prec<P>::eb;
+    char* l = lo ? static_cast<char*>(lo) + sidx * 32 * Prec<P>::eb : h;
+    store_operands<P>(y, h, l);
+  }
+}
+
+}  // namespace
+
+int tc_gemm(tb_ctx* ctx, int precision, const GemmArgs& g, const CUtensorMap* ah, const CUtensorMap* al,
+            const CUtensorMap* bh, const CUtensorMap* bl, cudaStream_t s) {
+  switch (precision) {
+    case TB_PREC_TF32: return launch_gemm<TB_PREC_TF32>(ctx, g, ah, al, bh, bl, s);
+    case TB_PREC_TF32X3: return launch_gemm<TB_PREC_TF32X3>(ctx, g, ah, al, bh, bl, s);
+    case TB_PREC_BF16: return launch_gemm<TB_PREC_BF16>(ctx, g, ah, al, bh, bl, s);
+    case TB_PREC_BF16X3: return launch_gemm<TB_PREC_BF16X3>(ctx, g, ah, al, bh, bl, s);
+    default: return tb_fail(ctx, TB_ERR_ARG, "precision %d has no tensor-core path", precision);
+  }
+}
+
+int tc_split(tb_ctx* ctx, int precision, const float* X, size_t count, void* hi, void* lo, const int* skip,
+             cudaStream_t s) {
+  switch (precision) {
+    case TB_PREC_TF32: k_split_only<TB_PREC_TF32><<<1184, 256, 0, s>>>(X, count, hi, lo, skip); break;
+    case TB_PREC_TF32X3: k_split_only<TB_PREC_TF32X3><<<1184, 256, 0, s>>>(X, count, hi, lo, skip); break;
+    case TB_PREC_BF16: k_split_only<TB_PREC_BF16><<<1184, 256, 0, s>>>(X, count, hi, lo, skip); break;
+    case TB_PREC_BF16X3: k_split_only<TB_PREC_BF16X3><<<1184, 256, 0, s>>>(X, count, hi, lo, skip); break;
+    default: return tb_fail(ctx, TB_ERR_ARG, "precision %d has no tensor-core path", precision);
+  }
+  TB_LAUNCH_CHECK(ctx);
+  return TB_OK;
+}

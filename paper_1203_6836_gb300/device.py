@@ -124,3 +124,31 @@ class MDState:
 
     def n_current(self) -> torch.Tensor:
         return self.n_hist[int(self.st.step) % (self.K + 1)]
+
+
+def fermi_opts(precision: str = "tf32x3", m: int = 16, ns_iters: int = 4, mu_iters: int = 30,
+               trace_tol: float = 0.0) -> tbmd.tb_fermi_opts:
+    return tbmd.tb_fermi_opts(precision=tbmd.PREC[precision], m=m, ns_iters=ns_iters, mu_iters=mu_iters,
+                              trace_tol=trace_tol)
+
+
+def fermi_report_to_dict(buf: torch.Tensor) -> dict:
+    raw = buf.detach().cpu().numpy().tobytes()
+    r = tbmd.tb_fermi_report.from_buffer_copy(raw[:ctypes.sizeof(tbmd.tb_fermi_report)])
+    return {k: getattr(r, k) for k, _ in tbmd.tb_fermi_report._fields_}
+
+
+class FermiSolver:
+    """dm_fermi with its workspace sized for n; mu is kept on the device and
+    warm-starts the next call."""
+
+    def __init__(self, ctx: tbmd.Context, n: int, opts: tbmd.tb_fermi_opts, device="cuda"):
+        self.ctx, self.n, self.opts = ctx, int(n), opts
+        self.ws = Workspace(tbmd.dm_fermi_workspace_size(n, opts), device)
+        self.report = torch.zeros(ctypes.sizeof(tbmd.tb_fermi_report), dtype=torch.uint8, device=device)
+        self.mu = torch.full((1,), float("nan"), dtype=torch.float64, device=device)
+
+    def __call__(self, H: torch.Tensor, n_occ: float, kT: float, D: torch.Tensor, stream=None):
+        tbmd.dm_fermi(self.ctx, H, self.n, n_occ, kT, self.opts, D, self.mu, self.ws.ptr, self.ws.nbytes,
+                      self.report, stream)
+        return D

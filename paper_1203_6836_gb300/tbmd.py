@@ -69,6 +69,17 @@ class tb_sp2_report(ctypes.Structure):
                 ("refine_bits", ctypes.c_uint64)]
 
 
+class tb_fermi_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("m", ctypes.c_int), ("ns_iters", ctypes.c_int),
+                ("mu_iters", ctypes.c_int), ("trace_tol", ctypes.c_double)]
+
+
+class tb_fermi_report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("mu_iters", ctypes.c_int), ("m", ctypes.c_int), ("n", ctypes.c_int),
+                ("mu", ctypes.c_double), ("trace", ctypes.c_double), ("trace_dd", ctypes.c_double),
+                ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double)]
+
+
 class tb_xl_params(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("kappa", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("K", ctypes.c_int), ("c", ctypes.c_double * (XL_KMAX + 1))]
@@ -100,6 +111,10 @@ _SIGS = {
                               ctypes.c_size_t, _P, _P]),
     "dm_sp2_static": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(tb_sp2_opts), _P, _P,
                                      _P]),
+    "dm_fermi_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(tb_fermi_opts),
+                                               ctypes.POINTER(ctypes.c_size_t)]),
+    "dm_fermi": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                ctypes.POINTER(tb_fermi_opts), _P, _P, _P, ctypes.c_size_t, _P, _P]),
     "mulliken": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P, _P]),
     "tb_forces": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P, _P, _P, _P,
                                  _P, _P, _P]),
@@ -211,6 +226,21 @@ def dm_sp2(ctx: Context, H, n: int, n_occ: float, opts: tb_sp2_opts, D, workspac
     return ctx.check(lib().dm_sp2(ctx.handle, _ptr(H), int(n), float(n_occ), ctypes.byref(opts), _ptr(D),
                                   _ptr(workspace), int(workspace_bytes), _ptr(report), _stream(stream)),
                      "dm_sp2")
+
+
+def dm_fermi_workspace_size(n: int, opts: tb_fermi_opts) -> int:
+    b = ctypes.c_size_t()
+    rc = lib().dm_fermi_workspace_size(int(n), ctypes.byref(opts), ctypes.byref(b))
+    if rc != TB_OK:
+        raise TBError(rc, "dm_fermi_workspace_size")
+    return int(b.value)
+
+
+def dm_fermi(ctx: Context, H, n: int, n_occ: float, kT: float, opts: tb_fermi_opts, D, mu, workspace,
+             workspace_bytes: int, report=None, stream=None) -> int:
+    return ctx.check(lib().dm_fermi(ctx.handle, _ptr(H), int(n), float(n_occ), float(kT), ctypes.byref(opts),
+                                    _ptr(D), _ptr(mu), _ptr(workspace), int(workspace_bytes), _ptr(report),
+                                    _stream(stream)), "dm_fermi")
 
 
 SP2_STATIC_MAX_N = 512
