@@ -188,6 +188,32 @@ int dm_sp2(tb_ctx* ctx, const double* H, int n, double n_occ, const tb_sp2_opts*
 int dm_sp2_static(tb_ctx* ctx, const double* H, int n, double n_occ, const tb_sp2_opts* opts,
                   double* D, tb_sp2_report* report, void* stream);
 
+/* ----------------------------------------- grouped SP2 (many small systems) */
+
+/* Workspace for a batch of `count` systems of sizes n[i] (host array,
+ * 1 <= n[i] <= 512). */
+int dm_sp2_grouped_workspace_size(int count, const int* n, const tb_sp2_opts* opts, size_t* bytes);
+
+/* Plan a batch: SP2 (Sec. III.B, as dm_sp2's tensor-core main phase, no
+ * refinement) of `count` independent systems in one persistent launch.
+ *   n, n_occ   host arrays [count]
+ *   H, D       host arrays [count] of device pointers to n[i] x n[i] FP64 matrices
+ *   reports    device array [count] of tb_sp2_report, or NULL
+ * Copies the per-system descriptors into the workspace; with autotune != 0 it
+ * also times each launch configuration (tile width 64 or 128, persistent grid
+ * of all or half the SMs) on the batch itself and keeps the fastest (the
+ * batch is solved several times).  Synchronises `stream`.  One plan per
+ * context at a time: a new plan replaces the previous one. */
+int dm_sp2_grouped_plan(tb_ctx* ctx, int count, const int* n, const double* n_occ, const double* const* H,
+                        double* const* D, tb_sp2_report* reports, const tb_sp2_opts* opts, int autotune,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
+/* Run the planned batch: one memset and one kernel launch on `stream`, no
+ * host synchronisation, so it can be captured in a CUDA graph.  The H
+ * matrices may change between runs (the pointers may not).
+ * *config_out (host, may be NULL) = tile width * 10000 + grid size. */
+int dm_sp2_grouped_run(tb_ctx* ctx, void* workspace, int* config_out, void* stream);
+
 /* ------------------------------------------------- a10: finite temperature */
 
 /* Options of dm_fermi. */

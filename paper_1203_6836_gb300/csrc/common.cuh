@@ -23,6 +23,9 @@ struct tb_ctx {
   int prof_created;
   cudaEvent_t ev[2][TB_PROF_MAX + 1];
   int prof_n[2];
+  // host copy of the last grouped-SP2 plan and the workspace it lives in
+  alignas(64) char plan_cache[4096];
+  void* plan_ws;
 };
 
 // Record the profiling event `idx` of phase `ph` on stream s (no-op when off).

@@ -1,0 +1,578 @@
+// Many independent SP2 problems in one persistent launch (SP2 of Sec. III.B
+// applied to a batch of systems of uneven size).
+//
+// Each CTA takes whole systems from a device queue (largest first) and runs
+// every step of the SP2 recursion for its system without leaving the kernel:
+// Gershgorin bounds, X0, then the projections X <- X^2 or 2X - X^2 as tcgen05
+// tiles (TMA -> shared memory -> TMEM, warp-specialised as in the dense
+// kernel), the FP64 trace reductions and the stop/branch decisions (all in
+// the CTA), and finally D.  Between two projections the CTA synchronises and
+// fences its global writes for the async proxy, so the next projection's TMA
+// loads see them.  All systems' X live in one stacked array (system s owns
+// rows [row_off_s, row_off_s + ld_s) and columns [0, ld_s)), so four tensor
+// maps per ping-pong buffer cover the batch.
+//
+// The plan call copies the per-system descriptors to the device once and
+// autotunes the launch (tile width BN in {64, 128} and the persistent grid)
+// by timing each candidate on the batch itself; the run call is a memset of
+// the queue counter and one kernel launch, so it can be captured into a CUDA
+// graph.
+
+#include "common.cuh"
+#include "tc_ptx.cuh"
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+namespace {
+
+using namespace tcx;
+
+constexpr int BM = 128;
+constexpr int kThreads = 192;
+constexpr int kMaxLd = 512;
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+struct GDesc {
+  const double* H;
+  double* D;
+  tb_sp2_report* rep;
+  int n, ld, row_off, pad;
+  double nocc;
+};
+
+struct GArgs {
+  int count, max_iter, rule, cols;  // cols: stacked width
+  double tol_floor_u;               // relative product error u (floor = 2 n u)
+  const GDesc* desc;
+  int* queue;
+  float* M[2];
+  void* Hi[2];
+  void* Lo[2];
+  int* err;
+};
+
+template <int P, int BN>
+struct GCfg {
+  using C = Prec<P>;
+  static constexpr int a_bytes = BM * 128;
+  static constexpr int b_bytes = BN * 128;
+  static constexpr int stage_bytes = (a_bytes + b_bytes) * C::nop;
+  static constexpr int stages = (200 * 1024) / stage_bytes;
+  static constexpr int smem = stages * stage_bytes + 1024;
+};
+
+__device__ __forceinline__ void fence_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+template <int P, int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_sp2_grouped(GArgs ga, const __grid_constant__ CUtensorMap ah0, const __grid_constant__ CUtensorMap al0,
+                  const __grid_constant__ CUtensorMap bh0, const __grid_constant__ CUtensorMap bl0,
+                  const __grid_constant__ CUtensorMap ah1, const __grid_constant__ CUtensorMap al1,
+                  const __grid_constant__ CUtensorMap bh1, const __grid_constant__ CUtensorMap bl1) {
+  using C = Prec<P>;
+  using G = GCfg<P, BN>;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[G::stages], empty[G::stages], tfull[2], tempty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int s_abort;
+  __shared__ int s_sys, s_stop, s_br;
+  __shared__ double s_red[8][3];
+  __shared__ double s_t1, s_t2, s_lo, s_hi;
+  __shared__ double s_hist[2][SP2_MAX_ITER + 2];
+  __shared__ unsigned long long s_branch[2];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < G::stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    s_abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_base, 2 * BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  // pipeline counters persist across tiles, projections and systems
+  int g_prod = 0, g_mma = 0, t_mma = 0, t_epi = 0;
+
+  while (true) {
+    if (threadIdx.x == 0) s_sys = atomicAdd(ga.queue, 1);
+    __syncthreads();
+    const int sys = s_sys;
+    if (sys >= ga.count || s_abort) break;
+    const GDesc d = ga.desc[sys];
+    const int n = d.n, ld = d.ld, ro = d.row_off;
+    const int nt_m = ld / BM, nt_n = ld / BN, ntiles = nt_m * nt_n;
+    const int nk = ld / C::bk;
+
+    // ---- Gershgorin bounds (warp per row)
+    double lo = INFINITY, hi = -INFINITY;
+    for (int r = warp; r < n; r += kThreads / 32) {
+      double sabs = 0.0;
+      for (int c = lane; c < n; c += 32) sabs += (c == r) ? 0.0 : fabs(d.H[(size_t)r * n + c]);
+      sabs = warp_sum(sabs);
+      const double hd = d.H[(size_t)r * n + r];
+      lo = fmin(lo, hd - sabs);
+      hi = fmax(hi, hd + sabs);
+    }
+    if (lane == 0) {
+      s_red[warp][0] = lo;
+      s_red[warp][1] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = s_red[0][0], b = s_red[0][1];
+      for (int w = 1; w < kThreads / 32; ++w) {
+        a = fmin(a, s_red[w][0]);
+        b = fmax(b, s_red[w][1]);
+      }
+      s_lo = a;
+      s_hi = b;
+      s_branch[0] = s_branch[1] = 0ull;
+    }
+    __syncthreads();
+    // ---- X0 into buffer 0, trace partials
+    {
+      const double emin = s_lo, emax = s_hi;
+      double w = emax - emin;
+      if (!(w > 0.0)) w = 1.0;
+      const double inv = 1.0 / w;
+      double t1 = 0.0, t2 = 0.0;
+      for (int seg = threadIdx.x; seg < ld * (ld / 32); seg += kThreads) {
+        const int r = seg / (ld / 32), c0 = 32 * (seg % (ld / 32));
+        float y[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int c = c0 + j;
+          double x = 0.0;
+          if (r < n && c < n) x = ((r == c ? emax : 0.0) - d.H[(size_t)r * n + c]) * inv;
+          y[j] = (float)x;
+          const double xf = y[j];
+          t2 += xf * xf;
+          if (r == c) t1 += xf;
+        }
+        const size_t e0 = (size_t)(ro + r) * ga.cols + c0;
+        float* dst = ga.M[0] + e0;
+        for (int j = 0; j < 32; ++j) dst[j] = y[j];
+        char* h = static_cast<char*>(ga.Hi[0]) + e0 * C::eb;
+        char* l = ga.Lo[0] ? static_cast<char*>(ga.Lo[0]) + e0 * C::eb : h;
+        store_operands<P>(y, h, l);
+      }
+      t1 = warp_sum(t1);
+      t2 = warp_sum(t2);
+      if (lane == 0) {
+        s_red[warp][0] = t1;
+        s_red[warp][1] = t2;
+      }
+      fence_async_global();
+      __syncthreads();
+    }
+    const double floor_e = 2.0 * n * ga.tol_floor_u;
+    int k = 0;
+    for (;; ++k) {
+      // ---- decision for projection k (every thread the same)
+      if (threadIdx.x == 0) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+          t1 += s_red[w][0];
+          t2 += s_red[w][1];
+        }
+        s_hist[0][k] = t1;
+        s_hist[1][k] = t2;
+        s_t1 = t1;
+        s_t2 = t2;
+        const double e = t1 - t2;
+        int stop = 0;
+        if (e <= floor_e) stop = 1;
+        if (!stop && k >= 3) {
+          bool flat = e <= 4.0 * floor_e;
+          for (int j = 1; j <= 3; ++j) flat = flat && (s_hist[0][k - j] - s_hist[1][k - j] <= 4.0 * floor_e);
+          if (flat) stop = 1;
+        }
+        if (k >= ga.max_iter) stop = 2;
+        int br = 0;
+        if (!stop) {
+          br = ga.rule == 0 ? (fabs(t2 - d.nocc) <= fabs(2.0 * t1 - t2 - d.nocc) ? 0 : 1) : (t1 > d.nocc ? 0 : 1);
+          if (br) s_branch[k >> 6] |= 1ull << (k & 63);
+        }
+        s_stop = stop;
+        s_br = br;
+      }
+      __syncthreads();
+      if (s_stop || s_abort) break;
+      for (int w = threadIdx.x; w < 8; w += kThreads) s_red[w][0] = s_red[w][1] = 0.0;
+      const int br = s_br;
+      const int ib = k & 1, ob = (k + 1) & 1;
+      __syncthreads();
+      if (warp == 0 && lane == 0) {
+        const CUtensorMap* mah = ib ? &ah1 : &ah0;
+        const CUtensorMap* mal = ib ? &al1 : &al0;
+        const CUtensorMap* mbh = ib ? &bh1 : &bh0;
+        const CUtensorMap* mbl = ib ? &bl1 : &bl0;
+        for (int t = 0; t < ntiles && !s_abort; ++t) {
+          const int m0 = (t / nt_n) * BM, n0 = (t % nt_n) * BN;
+          for (int kb = 0; kb < nk; ++kb, ++g_prod) {
+            const int s = g_prod % G::stages;
+            if (g_prod >= G::stages && !mbar_wait(&empty[s], ((g_prod / G::stages) - 1) & 1, &s_abort)) break;
+            uint8_t* base = smem + s * G::stage_bytes;
+            mbar_expect_tx(&full[s], G::stage_bytes);
+            tma_load_2d(base, mah, &full[s], kb * C::bk, ro + m0);
+            tma_load_2d(base + G::a_bytes, mbh, &full[s], kb * C::bk, ro + n0);
+            if constexpr (C::split) {
+              tma_load_2d(base + G::a_bytes + G::b_bytes, mal, &full[s], kb * C::bk, ro + m0);
+              tma_load_2d(base + 2 * G::a_bytes + G::b_bytes, mbl, &full[s], kb * C::bk, ro + n0);
+            }
+          }
+        }
+      } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t id = idesc(C::tf32 ? 2u : 1u, BM, BN);
+        for (int t = 0; t < ntiles && !s_abort; ++t, ++t_mma) {
+          const int acc = t_mma & 1;
+          if (t_mma >= 2 && !mbar_wait(&tempty[acc], ((t_mma >> 1) - 1) & 1, &s_abort)) break;
+          tc_fence_after();
+          const uint32_t dt = tmem + acc * BN;
+          for (int kb = 0; kb < nk; ++kb, ++g_mma) {
+            const int s = g_mma % G::stages;
+            if (!mbar_wait(&full[s], (g_mma / G::stages) & 1, &s_abort)) break;
+            tc_fence_after();
+            const uint32_t base = smem_u32(smem + s * G::stage_bytes);
+#pragma unroll
+            for (int ks = 0; ks < C::bk / C::uk; ++ks) {
+              const uint32_t koff = ks * 32;
+              const uint64_t a0 = sdesc(base + koff), b0 = sdesc(base + G::a_bytes + koff);
+              umma<C::tf32>(dt, a0, b0, id, (kb | ks) != 0);
+              if constexpr (C::split) {
+                umma<C::tf32>(dt, a0, sdesc(base + 2 * G::a_bytes + G::b_bytes + koff), id, 1u);
+                umma<C::tf32>(dt, sdesc(base + G::a_bytes + G::b_bytes + koff), b0, id, 1u);
+              }
+            }
+            umma_commit(&empty[s]);
+          }
+          umma_commit(&tfull[acc]);
+        }
+      } else if (warp >= 2) {
+        const int q = warp & 3;
+        const int row = 32 * q + lane;
+        double t1 = 0.0, t2 = 0.0;
+        for (int t = 0; t < ntiles; ++t, ++t_epi) {
+          const int acc = t_epi & 1;
+          if (!mbar_wait(&tfull[acc], (t_epi >> 1) & 1, &s_abort)) break;
+          tc_fence_after();
+          const int m0 = (t / nt_n) * BM, n0 = (t % nt_n) * BN;
+          const size_t grow = (size_t)(ro + m0 + row);
+          const float* xin = ga.M[ib] + grow * ga.cols + n0;
+          float* xout = ga.M[ob] + grow * ga.cols + n0;
+          char* hrow = static_cast<char*>(ga.Hi[ob]) + (grow * ga.cols + n0) * C::eb;
+          char* lrow = ga.Lo[ob] ? static_cast<char*>(ga.Lo[ob]) + (grow * ga.cols + n0) * C::eb : hrow;
+#pragma unroll 1
+          for (int c = 0; c < BN / 32; ++c) {
+            uint32_t v[32];
+            tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + acc * BN + 32 * c, v);
+            float y[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float cxx = __uint_as_float(v[j]);
+              const float x = xin[32 * c + j];
+              y[j] = br ? fmaf(2.0f, x, -cxx) : cxx;
+              t2 += (double)y[j] * (double)y[j];
+              if (m0 + row == n0 + 32 * c + j) t1 += (double)y[j];
+            }
+            float4* xo = reinterpret_cast<float4*>(xout + 32 * c);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) xo[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
+            store_operands<P>(y, hrow + 32 * c * C::eb, lrow + 32 * c * C::eb);
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[acc])) : "memory");
+        }
+        t1 = warp_sum(t1);
+        t2 = warp_sum(t2);
+        if (lane == 0) {
+          s_red[warp][0] = t1;
+          s_red[warp][1] = t2;
+        }
+        fence_async_global();
+      }
+      __syncthreads();
+    }
+    // ---- D from the final iterate (buffer k % 2), report
+    {
+      const float* X = ga.M[k & 1];
+      for (size_t e = threadIdx.x; e < (size_t)n * n; e += kThreads) {
+        const int r = (int)(e / n), c = (int)(e % n);
+        d.D[e] = (double)X[(size_t)(ro + r) * ga.cols + c];
+      }
+      if (threadIdx.x == 0 && d.rep) {
+        tb_sp2_report* rp = d.rep;
+        const double e = s_t1 - s_t2;
+        rp->status = s_abort ? TB_ERR_TIMEOUT : (fabs(s_t1 - d.nocc) > 0.25 ? TB_ERR_GAP : TB_OK);
+        rp->iters = k;
+        rp->refine_iters = 0;
+        rp->n = n;
+        rp->eps_min = s_lo;
+        rp->eps_max = s_hi;
+        rp->trace = s_t1;
+        rp->idem_trace = e;
+        rp->idem_fro = -1.0;
+        rp->branch_bits[0] = s_branch[0];
+        rp->branch_bits[1] = s_branch[1];
+        rp->refine_bits = 0;
+      }
+      __syncthreads();
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && s_abort && ga.err) atomicExch(ga.err, TB_ERR_TIMEOUT);
+  if (warp == 1) {
+    tc_fence_after();
+    if (s_abort && lane == 0) {
+      for (int b = 0; b < 2; ++b) {
+        const unsigned long long t0 = gtime();
+        while (!mbar_try(&tfull[b], 0) && gtime() - t0 < kWaitNs) {
+        }
+      }
+    }
+    __syncwarp();
+    tmem_dealloc(tmem, 2 * BN);
+  }
+}
+
+// Plan header kept at the start of the workspace.
+struct Plan {
+  int count, precision, rule, max_iter;
+  int rows, cols;
+  int bn, grid;
+  double u;
+  size_t off_desc, off_queue, off_err, off_m[2], off_hi[2], off_lo[2], total;
+  CUtensorMap ah[2], al[2], bh[2], bl[2];  // bh/bl for the chosen bn
+  CUtensorMap bh64[2], bl64[2], bh128[2], bl128[2];
+};
+
+static_assert(sizeof(Plan) <= sizeof(((tb_ctx*)nullptr)->plan_cache), "plan cache too small");
+
+size_t layout(int count, const int* n, int prec, Plan* p) {
+  int rows = 0, cols = 0;
+  for (int i = 0; i < count; ++i) {
+    const int ld = round_up(std::max(n[i], 1), BM);
+    rows += ld;
+    cols = std::max(cols, ld);
+  }
+  p->rows = rows;
+  p->cols = cols;
+  size_t o = (sizeof(Plan) + 1023) / 1024 * 1024;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o += (bytes + 1023) / 1024 * 1024;
+    return r;
+  };
+  const size_t eb = (prec == TB_PREC_TF32 || prec == TB_PREC_TF32X3) ? 4 : 2;
+  const bool split = prec == TB_PREC_TF32X3 || prec == TB_PREC_BF16X3;
+  const size_t cells = (size_t)rows * cols;
+  p->off_desc = take(sizeof(GDesc) * (size_t)count);
+  p->off_queue = take(sizeof(int) * 4);
+  p->off_err = take(sizeof(int) * 4);
+  for (int b = 0; b < 2; ++b) {
+    p->off_m[b] = take(sizeof(float) * cells);
+    p->off_hi[b] = take(eb * cells);
+    p->off_lo[b] = split ? take(eb * cells) : 0;
+  }
+  p->total = o;
+  return o;
+}
+
+int make_map(tb_ctx* ctx, int prec, const void* base, int rows, int cols, int box_rows, CUtensorMap* map) {
+  const bool tf = prec == TB_PREC_TF32 || prec == TB_PREC_TF32X3;
+  const size_t eb = tf ? 4 : 2;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(cols * eb)};
+  const cuuint32_t box[2] = {(cuuint32_t)(128 / eb), (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = ctx->encode_tiled(map, tf ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                                 const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return tb_fail(ctx, TB_ERR_CUDA, "cuTensorMapEncodeTiled (grouped) failed (%d)", (int)r);
+  return TB_OK;
+}
+
+template <int P, int BN>
+int launch(tb_ctx* ctx, const Plan& p, char* base, int grid, cudaStream_t s) {
+  using G = GCfg<P, BN>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    TB_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sp2_grouped<P, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::smem));
+    attr_set = true;
+  }
+  GArgs ga{};
+  ga.count = p.count;
+  ga.max_iter = p.max_iter;
+  ga.rule = p.rule;
+  ga.cols = p.cols;
+  ga.tol_floor_u = p.u;
+  ga.desc = reinterpret_cast<const GDesc*>(base + p.off_desc);
+  ga.queue = reinterpret_cast<int*>(base + p.off_queue);
+  ga.err = reinterpret_cast<int*>(base + p.off_err);
+  for (int b = 0; b < 2; ++b) {
+    ga.M[b] = reinterpret_cast<float*>(base + p.off_m[b]);
+    ga.Hi[b] = base + p.off_hi[b];
+    ga.Lo[b] = p.off_lo[b] ? base + p.off_lo[b] : nullptr;
+  }
+  const CUtensorMap* bh = BN == 64 ? p.bh64 : p.bh128;
+  const CUtensorMap* bl = BN == 64 ? p.bl64 : p.bl128;
+  TB_CUDA_TRY(ctx, cudaMemsetAsync(ga.queue, 0, sizeof(int), s));
+  k_sp2_grouped<P, BN><<<grid, kThreads, G::smem, s>>>(ga, p.ah[0], p.al[0], bh[0], bl[0], p.ah[1], p.al[1],
+                                                       bh[1], bl[1]);
+  TB_LAUNCH_CHECK(ctx);
+  return TB_OK;
+}
+
+int launch_any(tb_ctx* ctx, const Plan& p, char* base, int bn, int grid, cudaStream_t s) {
+  const bool b64 = bn == 64;
+  switch (p.precision) {
+    case TB_PREC_TF32: return b64 ? launch<TB_PREC_TF32, 64>(ctx, p, base, grid, s) : launch<TB_PREC_TF32, 128>(ctx, p, base, grid, s);
+    case TB_PREC_TF32X3: return b64 ? launch<TB_PREC_TF32X3, 64>(ctx, p, base, grid, s) : launch<TB_PREC_TF32X3, 128>(ctx, p, base, grid, s);
+    case TB_PREC_BF16: return b64 ? launch<TB_PREC_BF16, 64>(ctx, p, base, grid, s) : launch<TB_PREC_BF16, 128>(ctx, p, base, grid, s);
+    case TB_PREC_BF16X3: return b64 ? launch<TB_PREC_BF16X3, 64>(ctx, p, base, grid, s) : launch<TB_PREC_BF16X3, 128>(ctx, p, base, grid, s);
+    default: return tb_fail(ctx, TB_ERR_UNSUPPORTED, "grouped SP2 needs a tensor-core precision");
+  }
+}
+
+}  // namespace
+
+extern "C" int dm_sp2_grouped_workspace_size(int count, const int* n, const tb_sp2_opts* o, size_t* bytes) {
+  if (count < 1 || !n || !o || !bytes) return TB_ERR_ARG;
+  for (int i = 0; i < count; ++i)
+    if (n[i] < 1 || n[i] > kMaxLd) return TB_ERR_ARG;
+  Plan p{};
+  *bytes = layout(count, n, o->precision, &p);
+  return TB_OK;
+}
+
+extern "C" int dm_sp2_grouped_plan(tb_ctx* ctx, int count, const int* n, const double* nocc,
+                                   const double* const* H, double* const* D, tb_sp2_report* reports,
+                                   const tb_sp2_opts* o, int autotune, void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx) return TB_ERR_ARG;
+  if (count < 1 || !n || !nocc || !H || !D || !o || !ws)
+    return tb_fail(ctx, TB_ERR_ARG, "null argument to dm_sp2_grouped_plan");
+  if (o->precision == TB_PREC_FP64 || o->precision > TB_PREC_BF16X3)
+    return tb_fail(ctx, TB_ERR_UNSUPPORTED, "grouped SP2 needs a tensor-core precision");
+  if (o->max_iter < 1 || o->max_iter > SP2_MAX_ITER) return tb_fail(ctx, TB_ERR_ARG, "max_iter outside 1..%d", SP2_MAX_ITER);
+  for (int i = 0; i < count; ++i)
+    if (n[i] < 1 || n[i] > kMaxLd || !H[i] || !D[i] || !(nocc[i] >= 0.0) || nocc[i] > n[i])
+      return tb_fail(ctx, TB_ERR_ARG, "system %d: n = %d (1..%d), n_occ = %g", i, n[i], kMaxLd, nocc[i]);
+  if ((reinterpret_cast<uintptr_t>(ws) & 1023) != 0) return tb_fail(ctx, TB_ERR_ARG, "workspace must be 1024-byte aligned");
+  Plan p{};
+  const size_t need = layout(count, n, o->precision, &p);
+  if (ws_bytes < need) return tb_fail(ctx, TB_ERR_ARG, "workspace %zu bytes < required %zu", ws_bytes, need);
+  cudaStream_t s = as_stream(stream);
+  char* base = static_cast<char*>(ws);
+  p.count = count;
+  p.precision = o->precision;
+  p.rule = o->rule;
+  p.max_iter = o->max_iter;
+  p.u = (o->precision == TB_PREC_TF32X3 || o->precision == TB_PREC_BF16X3) ? 0x1p-24
+        : o->precision == TB_PREC_TF32 ? 0x1p-11 : 0x1p-8;
+  // descriptors, largest system first (longest-processing-time order)
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+  std::vector<GDesc> desc(count);
+  int row = 0;
+  for (int j = 0; j < count; ++j) {
+    const int i = order[j];
+    GDesc d{};
+    d.H = H[i];
+    d.D = D[i];
+    d.rep = reports ? reports + i : nullptr;
+    d.n = n[i];
+    d.ld = round_up(n[i], BM);
+    d.row_off = row;
+    d.nocc = nocc[i];
+    row += d.ld;
+    desc[j] = d;
+  }
+  TB_CUDA_TRY(ctx, cudaMemcpyAsync(base + p.off_desc, desc.data(), sizeof(GDesc) * count, cudaMemcpyHostToDevice, s));
+  TB_CUDA_TRY(ctx, cudaMemsetAsync(base + p.off_err, 0, sizeof(int) * 4, s));
+  // the stacked operand arrays start zeroed: padding columns beyond a
+  // system's ld are never read, and its padding inside ld is written by X0
+  for (int b = 0; b < 2; ++b) {
+    int rc = make_map(ctx, p.precision, base + p.off_hi[b], p.rows, p.cols, BM, &p.ah[b]);
+    if (rc) return rc;
+    rc = make_map(ctx, p.precision, base + p.off_hi[b], p.rows, p.cols, 64, &p.bh64[b]);
+    if (rc) return rc;
+    rc = make_map(ctx, p.precision, base + p.off_hi[b], p.rows, p.cols, 128, &p.bh128[b]);
+    if (rc) return rc;
+    if (p.off_lo[b]) {
+      rc = make_map(ctx, p.precision, base + p.off_lo[b], p.rows, p.cols, BM, &p.al[b]);
+      if (rc) return rc;
+      rc = make_map(ctx, p.precision, base + p.off_lo[b], p.rows, p.cols, 64, &p.bl64[b]);
+      if (rc) return rc;
+      rc = make_map(ctx, p.precision, base + p.off_lo[b], p.rows, p.cols, 128, &p.bl128[b]);
+      if (rc) return rc;
+    } else {
+      p.al[b] = p.ah[b];
+      p.bl64[b] = p.bh64[b];
+      p.bl128[b] = p.bh128[b];
+    }
+  }
+  p.bn = 128;
+  p.grid = std::max(1, ctx->sm_count);
+  if (autotune) {
+    // time every candidate on the batch itself and keep the fastest
+    const int bns[2] = {128, 64};
+    const int grids[2] = {ctx->sm_count, std::max(1, ctx->sm_count / 2)};
+    cudaEvent_t e0, e1;
+    TB_CUDA_TRY(ctx, cudaEventCreate(&e0));
+    TB_CUDA_TRY(ctx, cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int bi = 0; bi < 2; ++bi)
+      for (int gi = 0; gi < 2; ++gi) {
+        int rc = launch_any(ctx, p, base, bns[bi], grids[gi], s);  // warm-up
+        if (rc) return rc;
+        TB_CUDA_TRY(ctx, cudaEventRecord(e0, s));
+        rc = launch_any(ctx, p, base, bns[bi], grids[gi], s);
+        if (rc) return rc;
+        TB_CUDA_TRY(ctx, cudaEventRecord(e1, s));
+        TB_CUDA_TRY(ctx, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        TB_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          p.bn = bns[bi];
+          p.grid = grids[gi];
+        }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  TB_CUDA_TRY(ctx, cudaMemcpyAsync(base, &p, sizeof(Plan), cudaMemcpyHostToDevice, s));
+  TB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  // a host copy of the plan lives in the context for the run call
+  std::copy(reinterpret_cast<const char*>(&p), reinterpret_cast<const char*>(&p) + sizeof(Plan), ctx->plan_cache);
+  ctx->plan_ws = ws;
+  return TB_OK;
+}
+
+extern "C" int dm_sp2_grouped_run(tb_ctx* ctx, void* ws, int* bn_out, void* stream) {
+  if (!ctx || !ws) return TB_ERR_ARG;
+  if (ctx->plan_ws != ws) return tb_fail(ctx, TB_ERR_ARG, "workspace has no plan in this context");
+  Plan p;
+  std::copy(ctx->plan_cache, ctx->plan_cache + sizeof(Plan), reinterpret_cast<char*>(&p));
+  if (bn_out) *bn_out = p.bn * 10000 + p.grid;
+  return launch_any(ctx, p, static_cast<char*>(ws), p.bn, p.grid, as_stream(stream));
+}

@@ -115,6 +115,13 @@ _SIGS = {
                                                ctypes.POINTER(ctypes.c_size_t)]),
     "dm_fermi": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                 ctypes.POINTER(tb_fermi_opts), _P, _P, _P, ctypes.c_size_t, _P, _P]),
+    "dm_sp2_grouped_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                     ctypes.POINTER(tb_sp2_opts), ctypes.POINTER(ctypes.c_size_t)]),
+    "dm_sp2_grouped_plan": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.POINTER(ctypes.c_void_p), _P, ctypes.POINTER(tb_sp2_opts),
+                                           ctypes.c_int, _P, ctypes.c_size_t, _P]),
+    "dm_sp2_grouped_run": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int), _P]),
     "mulliken": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P, _P]),
     "tb_forces": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P, _P, _P, _P,
                                  _P, _P, _P]),
@@ -241,6 +248,36 @@ def dm_fermi(ctx: Context, H, n: int, n_occ: float, kT: float, opts: tb_fermi_op
     return ctx.check(lib().dm_fermi(ctx.handle, _ptr(H), int(n), float(n_occ), float(kT), ctypes.byref(opts),
                                     _ptr(D), _ptr(mu), _ptr(workspace), int(workspace_bytes), _ptr(report),
                                     _stream(stream)), "dm_fermi")
+
+
+def _ints(v):
+    return (ctypes.c_int * len(v))(*[int(x) for x in v])
+
+
+def dm_sp2_grouped_workspace_size(n_list, opts: tb_sp2_opts) -> int:
+    b = ctypes.c_size_t()
+    rc = lib().dm_sp2_grouped_workspace_size(len(n_list), _ints(n_list), ctypes.byref(opts), ctypes.byref(b))
+    if rc != TB_OK:
+        raise TBError(rc, "dm_sp2_grouped_workspace_size")
+    return int(b.value)
+
+
+def dm_sp2_grouped_plan(ctx: Context, n_list, nocc_list, H_list, D_list, reports, opts: tb_sp2_opts,
+                        autotune: bool, workspace, workspace_bytes: int, stream=None) -> int:
+    cnt = len(n_list)
+    nocc = (ctypes.c_double * cnt)(*[float(x) for x in nocc_list])
+    hp = (ctypes.c_void_p * cnt)(*[_ptr(h) for h in H_list])
+    dp = (ctypes.c_void_p * cnt)(*[_ptr(d) for d in D_list])
+    return ctx.check(lib().dm_sp2_grouped_plan(ctx.handle, cnt, _ints(n_list), nocc, hp, dp, _ptr(reports),
+                                               ctypes.byref(opts), int(bool(autotune)), _ptr(workspace),
+                                               int(workspace_bytes), _stream(stream)), "dm_sp2_grouped_plan")
+
+
+def dm_sp2_grouped_run(ctx: Context, workspace, stream=None) -> int:
+    cfg = ctypes.c_int()
+    ctx.check(lib().dm_sp2_grouped_run(ctx.handle, _ptr(workspace), ctypes.byref(cfg), _stream(stream)),
+              "dm_sp2_grouped_run")
+    return int(cfg.value)
 
 
 SP2_STATIC_MAX_N = 512
