@@ -11,6 +11,9 @@ and the whole n history is set to q.  Reading: Anderson (Pulay) mixing to
 max |q - n| <= 1e-10.
 BOMD reference: every step is SCF-converged (n = q), starting from the
 previous step's charges.
+At T_e > 0 the constant of motion is E_tot = KE + U - T_e S (Eq. Etot), with
+S the entropy of Eq. Entropy evaluated on the occupation numbers, i.e. the
+eigenvalues of D (the approximation of Eq. Ent_Approx at n != rho).
 """
 
 from __future__ import annotations
@@ -114,13 +117,21 @@ class Trajectory:
     F: list
     R: list
     gap: list
+    TS: list = dataclasses.field(default_factory=list)
+
+
+def _TS(D: np.ndarray, kT: float) -> float:
+    """T_e S (eV) from the eigenvalues of D (Eqs. Entropy, Ent_Approx); 0 at T_e = 0."""
+    if kT <= 0.0:
+        return 0.0
+    return kT * density.entropy_kB(np.linalg.eigvalsh(D))
 
 
 def xlbomd(R0, types, box, p: ModelParams, xl: XLParams, v0, masses, n_occ, nsteps: int,
            scf_tol: float = 1e-10, kT: float = 0.0, record_R: bool = False) -> Trajectory:
     """Fast-QMMD trajectory (module docstring).  Step order: half kick, drift,
     n update from (n history, q_t), H[n_{t+1}] -> D -> q_{t+1}, force, half kick."""
-    q0, fr, _ = scf(R0, types, box, p, n_occ, tol=scf_tol)
+    q0, fr, _ = scf(R0, types, box, p, n_occ, tol=scf_tol, kT=kT)
     R, v = R0.copy(), v0.copy()
     n_hist = [q0.copy() for _ in range(xl.K + 1)]
     q_t = q0
@@ -131,7 +142,9 @@ def xlbomd(R0, types, box, p: ModelParams, xl: XLParams, v0, masses, n_occ, nste
     def record(R, v, D, q, n_aux, F, gap):
         Ep = observables.potential_energy(R, types, box, p, D, q, n_aux)
         KE = observables.kinetic_energy(v, masses)
-        traj.E_tot.append(KE + Ep)
+        TS = _TS(D, kT)
+        traj.E_tot.append(KE + Ep - TS)
+        traj.TS.append(TS)
         traj.E_pot.append(Ep)
         traj.KE.append(KE)
         traj.q.append(q.copy())

@@ -162,3 +162,21 @@ def test_xlbomd_deviation_from_bomd_is_second_order_in_dt():
         dq = np.sqrt(np.mean([np.mean((x - y) ** 2) for x, y in zip(a.q, b.q)]))
         dev.append(dq)
     assert dev[0] / dev[1] == pytest.approx(4.0, rel=0.3)
+
+
+def test_xlbomd_finite_temperature_entropy_term_restores_conservation():
+    """Eqs. Etot, Entropy: at T_e > 0, KE + U alone is not conserved, while
+    KE + U - T_e S (S from the occupation numbers, the eigenvalues of D) is.
+    kT = 1.5 eV puts fractional occupations across the 1.75 eV gap of the
+    molecule, so the entropy term is large and changes along the path."""
+    s = molecular_water(1, 12.0, seed=0)
+    M = s.masses(P)
+    v0 = thermal_velocities(M, 600.0, seed=101)
+    tr = md.xlbomd(s.R, s.types, s.box, P, XL_PIN, v0, M, s.n_occ(P), 80, kT=1.5)
+    E = np.array(tr.E_tot)
+    TS = np.array(tr.TS)
+    E_no_S = E + TS
+    assert np.min(TS) > 0.01
+    assert np.max(np.abs(E - E[0])) < 0.05 * np.max(np.abs(E_no_S - E_no_S[0]))
+    # the charges still follow q at T_e > 0
+    assert max(np.max(np.abs(a - b)) for a, b in zip(tr.n, tr.q)) < 0.05
