@@ -214,7 +214,7 @@ int dm_sp2_grouped_plan(tb_ctx* ctx, int count, const int* n, const double* n_oc
  * *config_out (host, may be NULL) = tile width * 10000 + grid size. */
 int dm_sp2_grouped_run(tb_ctx* ctx, void* workspace, int* config_out, void* stream);
 
-/* ------------------------------------------------- a10: finite temperature */
+/* ------------------------------------------- a10: finite temperature solve */
 
 /* Options of dm_fermi. */
 typedef struct {
@@ -236,6 +236,7 @@ typedef struct {
   double trace_dd;    /* Tr D(I - D) (= dTr D/dmu / beta) */
   double eps_min, eps_max;
 } tb_fermi_report;
+
 
 int dm_fermi_workspace_size(int n, const tb_fermi_opts* opts, size_t* bytes);
 
@@ -290,16 +291,23 @@ typedef struct {
   double* v;            /* [N*3] A/fs */
   double* F;            /* [N*3] force at R (valid after xlbomd_init) */
   const double* mass;   /* [N] amu */
-  double* n_hist;       /* [(K+1)*N] ring buffer; n_t in slot (step mod (K+1)) */
+  double* n_hist;       /* [(K+1)*N] shift register: slot j (N doubles) holds n_{t-j} */
   double* q;            /* [N] Mulliken charges of the last D */
   double* H;            /* [n*n] */
   double* D;            /* [n*n] */
   double* gamma;        /* [N*N] */
-  double* energies;     /* [8]: E_tot, E_pot, 2Tr[hD], E_scc, E_pair, KE, max|n-q|, step */
+  double* energies;     /* [8]: E_tot, E_pot, 2Tr[hD], E_scc, E_pair, KE, max|n-q|, steps
+                           (E_pot, E_tot without the entropy term -T_e S at kT > 0) */
   tb_sp2_report* sp2_report;  /* may be NULL */
-  void* workspace;      /* dm_sp2 workspace (dm_sp2_workspace_size(norb)) */
+  void* workspace;      /* dm_sp2 workspace (dm_sp2_workspace_size(norb)), or the dm_fermi
+                           workspace when kT > 0 */
   size_t workspace_bytes;
-  int64_t step;         /* steps taken; advanced by xlbomd_step */
+  int64_t step;         /* host count of steps enqueued by xlbomd_step (energies[7] is the
+                           device count, which also advances in graph replays) */
+  double kT;            /* electronic temperature (eV); > 0: D by dm_fermi (Eq. EL_4c), else SP2 */
+  tb_fermi_opts fermi;  /* options of dm_fermi when kT > 0 */
+  double* mu;           /* device double: chemical potential, carried between steps (kT > 0) */
+  tb_fermi_report* fermi_report;  /* device, may be NULL */
 } tb_md_state;
 
 /* Initial state (App. D.3): SCF-converge the charges with Anderson mixing
@@ -312,10 +320,109 @@ int xlbomd_init(tb_ctx* ctx, const tb_params* p, tb_md_state* st, const tb_xl_pa
                 void* stream);
 
 /* One Fast-QMMD step (Eqs. EL_3ax, EL_3bx; App. D.3): half kick, drift,
- * n update (Eq. Verl_n), H[n] (tb_build_H), D (dm_sp2), q (mulliken),
- * F and E (tb_forces), half kick, kinetic energy.  Fully asynchronous. */
+ * n update (Eq. Verl_n), H[n] (tb_build_H), D (dm_sp2, or dm_fermi when
+ * st->kT > 0), q (mulliken), F and E (tb_forces), half kick, kinetic energy.
+ * Fully asynchronous, and every launch has the same arguments from step to
+ * step: a step captured into a CUDA graph (stream capture) replays as the
+ * next step each time the graph is launched.  Under capture, dm_fermi's
+ * chemical-potential loop becomes a conditional (while) graph node. */
 int xlbomd_step(tb_ctx* ctx, const tb_params* p, tb_md_state* st, const tb_xl_params* xp,
                 const tb_sp2_opts* so, void* stream);
+
+/* ---------------------------------------------- serving: continuous batching */
+
+/* A request loop over many XL-BOMD trajectories of uneven size on one GPU.
+ * The paper has no serving counterpart; each step it runs is xlbomd_step.
+ *
+ * Each admitted trajectory keeps its whole state resident in one device
+ * allocation: R, v, F, the n history, q, H, D, gamma, mu and the workspace
+ * of its density solve.  Trajectories are admitted in the order they were
+ * added, while the sum of the admitted footprints (tb_server_footprint)
+ * stays within hbm_budget.  The others wait, and are admitted when a retired
+ * trajectory frees its memory.  Admission runs the initial SCF (xlbomd_init,
+ * synchronous) and captures one step into a CUDA graph.
+ *
+ * Step requests are served in submission order with at most one step in
+ * flight per trajectory, on up to max_slots CUDA streams.  A request is
+ * launched (one graph launch) as soon as its trajectory is idle and a slot
+ * is free, while other steps are still running, so steps of different
+ * trajectories overlap on the device.  The runtime is single-threaded: call
+ * it from one host thread.  Host times are seconds since tb_server_create,
+ * from a steady clock. */
+#define TB_SERVER_MAX_SLOTS 64
+
+typedef struct tb_server tb_server;
+
+typedef struct {
+  int max_slots;        /* steps in flight at once, one stream each: 1..TB_SERVER_MAX_SLOTS */
+  size_t hbm_budget;    /* device bytes the admitted trajectories may hold together
+                           (0: 90% of the free memory at create) */
+  double kT;            /* electronic temperature (eV): > 0 D by dm_fermi, 0 by dm_sp2 */
+  tb_xl_params xl;      /* integration parameters of every trajectory */
+  tb_sp2_opts sp2;      /* density options at kT = 0 */
+  tb_fermi_opts fermi;  /* density options at kT > 0 */
+  double scf_tol;       /* initial SCF: max|q - n| */
+  int scf_max_iter;     /* initial SCF cap (>= 1) */
+} tb_server_opts;
+
+/* One finished step request. */
+typedef struct {
+  int64_t request;      /* id returned by tb_server_submit (or the replay index order) */
+  int traj;             /* trajectory id */
+  int status;           /* status of the step's density solve (TB_OK, TB_ERR_NOT_CONVERGED, ...) */
+  int64_t step;         /* the trajectory's step count after this step */
+  double t_submit;      /* host time of the request (replay: its scheduled arrival) */
+  double t_launch;      /* host time of the graph launch */
+  double t_done;        /* host time at which the completion was observed */
+  double gpu_ms;        /* device time between the step's start and end events on its stream */
+  double energies[8];   /* tb_md_state energies after the step */
+} tb_completion;
+
+typedef struct {
+  int trajectories, admitted, waiting, running, queued;
+  size_t bytes_in_use, budget;
+  int64_t submitted, completed;
+} tb_server_counts;
+
+int tb_server_create(tb_ctx* ctx, const tb_params* p, const tb_server_opts* opts, tb_server** out);
+/* Waits for the steps in flight, then frees every resource of the server. */
+int tb_server_destroy(tb_server* server);
+
+/* Device bytes a trajectory of natoms atoms (host types[natoms]) holds. */
+int tb_server_footprint(const tb_server* server, int natoms, const int32_t* types, size_t* bytes);
+
+/* Register a trajectory (host arrays, copied: types[N], R0[N*3] A, v0[N*3]
+ * A/fs, mass[N] amu, cubic box side, n_occ = N_e/2) and admit it at once if
+ * its footprint fits.  *traj_out = its id.  TB_ERR_OOM when the footprint
+ * alone exceeds the budget. */
+int tb_server_add(tb_server* server, int natoms, const int32_t* types, double box, const double* R0,
+                  const double* v0, const double* mass, double n_occ, int* traj_out);
+
+/* Queue one step of trajectory traj; *request_out (may be NULL) = its id. */
+int tb_server_submit(tb_server* server, int traj, int64_t* request_out);
+
+/* One scheduling pass: collect finished steps into out[0..max_out), free
+ * retired trajectories, admit waiting ones, launch queued requests.  wait != 0:
+ * repeat until at least one completion or nothing is in flight. */
+int tb_server_poll(tb_server* server, int wait, tb_completion* out, int max_out, int* n_out);
+
+/* Retire a trajectory: its queued steps still run; then its memory is freed
+ * and waiting trajectories are admitted.  No new requests are accepted. */
+int tb_server_retire(tb_server* server, int traj);
+
+/* Copy a trajectory's state to host memory (any pointer may be NULL):
+ * R[N*3], v[N*3], q[N], n_t[N], energies[8].  The trajectory must be
+ * admitted and idle. */
+int tb_server_read(tb_server* server, int traj, double* R, double* v, double* q, double* n_t, double* energies);
+
+int tb_server_stats(const tb_server* server, tb_server_counts* out);
+
+/* Replay an arrival trace in real time: request i (trajectory traj[i]) is
+ * submitted when arrival_s[i] seconds (non-decreasing) have passed since the
+ * call; polls until all have finished and writes out[i] for request i, with
+ * t_submit = the scheduled arrival.  Needs a server with nothing in flight. */
+int tb_server_replay(tb_server* server, int count, const double* arrival_s, const int* traj,
+                     tb_completion* out);
 
 #ifdef __cplusplus
 }

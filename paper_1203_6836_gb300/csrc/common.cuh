@@ -26,6 +26,9 @@ struct tb_ctx {
   // host copy of the last grouped-SP2 plan and the workspace it lives in
   alignas(64) char plan_cache[4096];
   void* plan_ws;
+  // side stream on which the body of a conditional (while) graph node is
+  // captured (created on first use)
+  cudaStream_t loop_stream;
 };
 
 // Record the profiling event `idx` of phase `ph` on stream s (no-op when off).
@@ -35,6 +38,26 @@ static inline void tb_prof_mark(tb_ctx* ctx, int ph, int idx, cudaStream_t s) {
     if (idx + 1 > ctx->prof_n[ph]) ctx->prof_n[ph] = idx + 1;
   }
 }
+
+// A loop whose trip count the device decides.  When the caller's stream is
+// being captured into a CUDA graph, tb_loop_begin adds a conditional (while)
+// node at the capture point and captures the body, launched once on
+// `body_stream`, into it; the body's last kernel clears the condition with
+// cudaGraphSetConditional(handle, 0).  Otherwise the host unrolls the body up
+// to its cap on the caller's stream and the kernels of the rounds after the
+// device's stop decision return at once.  The kernels and their order are the
+// same in both forms.
+struct DevLoop {
+  int graph;                          // 1: body captured into a while node
+  cudaStream_t outer;                 // the caller's stream
+  cudaStream_t body_stream;           // where the body is launched
+  cudaGraphConditionalHandle handle;  // valid when graph == 1
+  cudaGraphNode_t node;
+};
+int tb_loop_begin(tb_ctx* ctx, cudaStream_t s, DevLoop* L);
+// Close the body capture (also on an error path: pass the error code, which
+// is returned unchanged).
+int tb_loop_end(tb_ctx* ctx, DevLoop* L, int rc);
 
 // Record a formatted message in the context and return `code`.
 int tb_fail(tb_ctx* ctx, int code, const char* fmt, ...);

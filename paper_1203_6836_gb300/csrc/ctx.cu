@@ -65,7 +65,44 @@ extern "C" int tb_ctx_create(tb_ctx** out) {
   return TB_OK;
 }
 
+int tb_loop_begin(tb_ctx* ctx, cudaStream_t s, DevLoop* L) {
+  *L = DevLoop{};
+  L->outer = s;
+  L->body_stream = s;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  TB_CUDA_TRY(ctx, cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return TB_OK;
+  if (!ctx->loop_stream) TB_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->loop_stream, cudaStreamNonBlocking));
+  TB_CUDA_TRY(ctx, cudaGraphConditionalHandleCreate(&L->handle, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = L->handle;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  TB_CUDA_TRY(ctx, cudaGraphAddNode(&L->node, g, deps, nullptr, nd, &np));
+  TB_CUDA_TRY(ctx, cudaStreamUpdateCaptureDependencies(s, &L->node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  TB_CUDA_TRY(ctx, cudaStreamBeginCaptureToGraph(ctx->loop_stream, np.conditional.phGraph_out[0], nullptr, nullptr,
+                                                 0, cudaStreamCaptureModeRelaxed));
+  L->graph = 1;
+  L->body_stream = ctx->loop_stream;
+  return TB_OK;
+}
+
+int tb_loop_end(tb_ctx* ctx, DevLoop* L, int rc) {
+  if (!L->graph) return rc;
+  L->graph = 0;
+  cudaGraph_t body = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(L->body_stream, &body);
+  if (rc) return rc;
+  if (e != cudaSuccess) return tb_fail(ctx, TB_ERR_CUDA, "loop body capture: %s", cudaGetErrorString(e));
+  return TB_OK;
+}
+
 extern "C" int tb_ctx_destroy(tb_ctx* ctx) {
+  if (ctx && ctx->loop_stream) cudaStreamDestroy(ctx->loop_stream);
   if (ctx && ctx->prof_created) {
     for (int p = 0; p < 2; ++p)
       for (int i = 0; i <= TB_PROF_MAX; ++i) cudaEventDestroy(ctx->ev[p][i]);

@@ -40,6 +40,7 @@ struct FoeState {
   double mu, lo, hi;
   double emin, emax;
   int done, iters, capped, err;
+  int ran;  // 1: the last k_foe_mu evaluated an expansion (it was not skipped)
   double tr[kMaxMu + 1], trdd[kMaxMu + 1], mus[kMaxMu + 1];
 };
 
@@ -126,10 +127,19 @@ __global__ void __launch_bounds__(256) k_foe_sym(const FoeState* st, int ld, flo
 
 // After an expansion: Tr E and ||E||_F^2 from the last product's partials
 // give Tr D = n/2 + Tr E and Tr D(I - D) = n/4 - ||E||_F^2; then the stop
-// test and the next mu (one block, every quantity FP64).
+// test and the next mu (one block, every quantity FP64).  The expansion index
+// is the device count st->iters.  Inside a while graph node (cond != 0) the
+// condition is cleared on every stop: converged, capped, or an error flag
+// raised by a product of this expansion.
 __global__ void k_foe_mu(FoeState* st, const double* parts, int np, int n, double nocc, double beta, double tol,
-                         int it, int max_it) {
-  if (st->done || st->err) return;
+                         int max_it, cudaGraphConditionalHandle handle, int cond) {
+  if (st->done || st->err || st->iters >= max_it) {
+    if (threadIdx.x == 0) {
+      st->ran = 0;
+      if (cond) cudaGraphSetConditional(handle, 0);
+    }
+    return;
+  }
   double x = 0.0, y = 0.0;
   for (int i = threadIdx.x; i < np; i += 32) {
     x += parts[2 * i];
@@ -138,6 +148,7 @@ __global__ void k_foe_mu(FoeState* st, const double* parts, int np, int n, doubl
   x = warp_sum(x);
   y = warp_sum(y);
   if (threadIdx.x != 0) return;
+  const int it = st->iters;
   const double mu = st->mu;
   const double trd = 0.5 * n + x;
   const double trdd = 0.25 * n - y;  // Tr D(I - D)
@@ -147,29 +158,29 @@ __global__ void k_foe_mu(FoeState* st, const double* parts, int np, int n, doubl
   st->trdd[it] = x - y;
   st->mus[it] = mu;
   st->iters = it + 1;
+  st->ran = 1;
   const double dev = x - nocc;
   if (fabs(dev) <= tol) {
     st->done = 1;
-    return;
-  }
-  if (it + 1 >= max_it) {
+  } else if (it + 1 >= max_it) {
     st->done = 1;
     st->capped = 1;
-    return;
+  } else {
+    if (dev < 0.0) st->lo = mu;
+    else st->hi = mu;
+    const double slope = beta * (x - y);
+    double next = slope > 1e-12 ? mu - dev / slope : NAN;
+    if (!(next > st->lo && next < st->hi)) next = 0.5 * (st->lo + st->hi);
+    st->mu = next;
   }
-  if (dev < 0.0) st->lo = mu;
-  else st->hi = mu;
-  const double slope = beta * (x - y);
-  double next = slope > 1e-12 ? mu - dev / slope : NAN;
-  if (!(next > st->lo && next < st->hi)) next = 0.5 * (st->lo + st->hi);
-  st->mu = next;
+  if (cond && st->done) cudaGraphSetConditional(handle, 0);
 }
 
-// Copy the last X of expansion `it` into the result buffer, only when that
+// Copy the last X of an expansion into the result buffer, only when that
 // expansion ran (a converged outer loop skips the later ones).
-__global__ void __launch_bounds__(256) k_foe_keep(const FoeState* st, int it, size_t count,
-                                                  const float* __restrict__ src, float* __restrict__ dst) {
-  if (st->iters != it + 1 || src == dst) return;
+__global__ void __launch_bounds__(256) k_foe_keep(const FoeState* st, size_t count, const float* __restrict__ src,
+                                                  float* __restrict__ dst) {
+  if (!st->ran || src == dst) return;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
     dst[e] = src[e];
 }
@@ -289,6 +300,12 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
   k_foe_bounds<<<1, 32, 0, s>>>(bparts, (n + 7) / 8, st, mu, kT);
   TB_LAUNCH_CHECK(ctx);
 
+  // the chemical-potential loop: a while graph node under capture, else
+  // mu_iters unrolled rounds that return at once after the stop decision
+  DevLoop loop;
+  if ((rc = tb_loop_begin(ctx, s, &loop))) return rc;
+  cudaStream_t ls = loop.body_stream;
+  const int rounds = loop.graph ? 1 : o->mu_iters;
   auto gemm = [&](Mat& A, Mat& B, Mat& out, float alpha, float betac, const float* E, float gamma,
                   double* prt) -> int {
     GemmArgs g{};
@@ -304,46 +321,49 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
     g.parts = prt;
     g.skip = skip;
     g.err = errp;
-    return tc_gemm(ctx, o->precision, g, &A.mh, &A.ml, &B.mh, &B.ml, s);
+    return tc_gemm(ctx, o->precision, g, &A.mh, &A.ml, &B.mh, &B.ml, ls);
   };
   const int ntile = L.ld / 32;
   const int ntp = ntile * (ntile + 1) / 2;
-  for (int it = 0; it < o->mu_iters; ++it) {
+  auto expansion = [&]() -> int {
+    int r;
     Mat* X = &M[0];
     Mat* A = &M[1];
     Mat* Z = &M[2];
     Mat* T = &M[3];
     Mat* Y = &M[4];
-    k_foe_x0<<<1184, 256, 0, s>>>(H, n, L.ld, st, c, X->m);
+    k_foe_x0<<<1184, 256, 0, ls>>>(H, n, L.ld, st, c, X->m);
     TB_LAUNCH_CHECK(ctx);
-    rc = tc_split(ctx, o->precision, X->m, nn, X->hi, X->lo, skip, s);
-    if (rc) return rc;
+    if ((r = tc_split(ctx, o->precision, X->m, nn, X->hi, X->lo, skip, ls))) return r;
     for (int step = 0; step < m; ++step) {
       // A = I + 4 E E
-      if ((rc = gemm(*X, *X, *A, 4.0f, 0.0f, nullptr, 1.0f, nullptr))) return rc;
+      if ((r = gemm(*X, *X, *A, 4.0f, 0.0f, nullptr, 1.0f, nullptr))) return r;
       // Z1 = 4/3 I - 4/9 A, then Newton-Schulz
-      k_foe_z1<<<1184, 256, 0, s>>>(st, n, L.ld, A->m, Z->m);
+      k_foe_z1<<<1184, 256, 0, ls>>>(st, n, L.ld, A->m, Z->m);
       TB_LAUNCH_CHECK(ctx);
-      if ((rc = tc_split(ctx, o->precision, Z->m, nn, Z->hi, Z->lo, skip, s))) return rc;
+      if ((r = tc_split(ctx, o->precision, Z->m, nn, Z->hi, Z->lo, skip, ls))) return r;
       for (int k = 1; k < ns; ++k) {
-        if ((rc = gemm(*A, *Z, *T, -1.0f, 0.0f, nullptr, 2.0f, nullptr))) return rc;  // T = 2I - A Z
-        if ((rc = gemm(*Z, *T, *Y, 1.0f, 0.0f, nullptr, 0.0f, nullptr))) return rc;   // Z <- Z T
+        if ((r = gemm(*A, *Z, *T, -1.0f, 0.0f, nullptr, 2.0f, nullptr))) return r;  // T = 2I - A Z
+        if ((r = gemm(*Z, *T, *Y, 1.0f, 0.0f, nullptr, 0.0f, nullptr))) return r;   // Z <- Z T
         std::swap(Z, Y);
       }
       // E <- 2 E Z (trace partials of the last step), then its symmetric
       // part and fresh operand splits
       const bool last = step == m - 1;
-      if ((rc = gemm(*X, *Z, *Y, 2.0f, 0.0f, nullptr, 0.0f, last ? parts : nullptr))) return rc;
+      if ((r = gemm(*X, *Z, *Y, 2.0f, 0.0f, nullptr, 0.0f, last ? parts : nullptr))) return r;
       std::swap(X, Y);
-      k_foe_sym<<<ntp, 256, 0, s>>>(st, L.ld, X->m, nullptr);
+      k_foe_sym<<<ntp, 256, 0, ls>>>(st, L.ld, X->m, nullptr);
       TB_LAUNCH_CHECK(ctx);
-      if (!last && (rc = tc_split(ctx, o->precision, X->m, nn, X->hi, X->lo, skip, s))) return rc;
+      if (!last && (r = tc_split(ctx, o->precision, X->m, nn, X->hi, X->lo, skip, ls))) return r;
     }
-    k_foe_mu<<<1, 32, 0, s>>>(st, parts, L.nparts, n, nocc, beta, tol, it, o->mu_iters);
+    k_foe_mu<<<1, 32, 0, ls>>>(st, parts, L.nparts, n, nocc, beta, tol, o->mu_iters, loop.handle, loop.graph);
     TB_LAUNCH_CHECK(ctx);
-    k_foe_keep<<<1184, 256, 0, s>>>(st, it, nn, X->m, res);
+    k_foe_keep<<<1184, 256, 0, ls>>>(st, nn, X->m, res);
     TB_LAUNCH_CHECK(ctx);
-  }
+    return TB_OK;
+  };
+  for (int it = 0; it < rounds && rc == TB_OK; ++it) rc = expansion();
+  if ((rc = tb_loop_end(ctx, &loop, rc))) return rc;
   const int fb = std::min(1184, (int)(((size_t)n * n + 255) / 256));
   k_foe_finalize<<<fb, 256, 0, s>>>(st, n, L.ld, res, D, nocc, tol, m, mu, rep);
   TB_LAUNCH_CHECK(ctx);

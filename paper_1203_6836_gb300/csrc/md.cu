@@ -4,10 +4,12 @@
 // Auxiliary charges: modified Verlet with dissipation, Eq. Verl_n,
 //   n_{t+dt} = 2 n_t - n_{t-dt} + kappa (q_t - n_t) + alpha sum_{k=0}^{K} c_k n_{t-k dt},
 // with the Mulliken charges q_t of D[n_t] in place of sigma_t (Eq. EL_Orth_b).
-// The n history lives in a (K+1)-slot ring buffer; n_t sits in slot
-// (step mod (K+1)).  A step enqueues: half kick + drift, n update, H[n]
-// build, SP2, Mulliken, forces/energy, half kick + kinetic energy; nothing
-// synchronises the host.
+// The n history is a (K+1)-slot shift register, slot j = n_{t-j}: each step
+// moves it down one slot on the device, so every launch of a step has the
+// same arguments and a step can be captured once into a CUDA graph and
+// replayed.  A step enqueues: half kick + drift, n update, H[n] build, D
+// (SP2, or the Fermi operator at kT > 0), Mulliken, forces/energy, half kick
+// + kinetic energy; nothing synchronises the host.
 //
 // Initialisation (App. D.3): SCF-converged charges to a high degree, then
 // the whole history set to q.  The SCF loop runs the same device kernels
@@ -37,31 +39,27 @@ __global__ void k_kick_drift(int N, double* __restrict__ v, const double* __rest
   }
 }
 
-// Eq. Verl_n.  slot(j) = (t - j) mod (K+1) holds n_{t-j}; the result goes to
-// slot (t+1) mod (K+1) = slot(K), read before it is overwritten.
-__global__ void k_n_update(int N, double* __restrict__ hist, int64_t t, int K, const double* __restrict__ q,
-                           double kappa, double alpha, tb_xl_params xp) {
+// Eq. Verl_n on the shift register: thread i reads n_{t-j} (slot j) of its
+// atom, shifts them down one slot and puts n_{t+dt} in slot 0.
+__global__ void k_n_update(int N, double* __restrict__ hist, int K, const double* __restrict__ q, double kappa,
+                           double alpha, tb_xl_params xp) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const int S = K + 1;
   double nv[TB_XL_KMAX + 1];
-  for (int j = 0; j <= K; ++j) {
-    const int slot = (int)(((t - j) % S + S) % S);
-    nv[j] = hist[(size_t)slot * N + i];
-  }
+  for (int j = 0; j <= K; ++j) nv[j] = hist[(size_t)j * N + i];
   double diss = 0.0;
   for (int j = 0; j <= K; ++j) diss += xp.c[j] * nv[j];
   const double n_new = 2.0 * nv[0] - nv[1] + kappa * (q[i] - nv[0]) + alpha * diss;
-  const int out = (int)(((t + 1) % S + S) % S);
-  hist[(size_t)out * N + i] = n_new;
+  for (int j = K; j >= 1; --j) hist[(size_t)j * N + i] = nv[j - 1];
+  hist[i] = n_new;
 }
 
-// Second half kick, kinetic energy, E_tot and max|n - q| in one block.
+// Second half kick, kinetic energy, E_tot and max|n - q| in one block; the
+// step counter E[7] is 0 after the initial state (kick = 0), +1 per step.
 __global__ void __launch_bounds__(256) k_kick_energy(int N, double* __restrict__ v, const double* __restrict__ F,
                                                      const double* __restrict__ mass, double dt, int kick,
                                                      const double* __restrict__ n_cur,
-                                                     const double* __restrict__ q, double* __restrict__ E,
-                                                     int64_t step) {
+                                                     const double* __restrict__ q, double* __restrict__ E) {
   __shared__ double s_ke[8], s_dq[8];
   double ke = 0.0, dq = 0.0;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -96,7 +94,7 @@ __global__ void __launch_bounds__(256) k_kick_energy(int N, double* __restrict__
     E[5] = a;
     E[0] = a + E[1];
     E[6] = b;
-    E[7] = (double)step;
+    E[7] = kick ? E[7] + 1.0 : 0.0;
   }
 }
 
@@ -113,13 +111,18 @@ int check_state(tb_ctx* ctx, const tb_md_state* st, const tb_xl_params* xp, cons
       !st->energies || !st->workspace)
     return tb_fail(ctx, TB_ERR_ARG, "null array in tb_md_state");
   if (!(xp->dt > 0)) return tb_fail(ctx, TB_ERR_ARG, "dt must be > 0");
+  if (st->kT > 0.0 && !st->mu) return tb_fail(ctx, TB_ERR_ARG, "kT > 0 needs the device mu");
   return TB_OK;
 }
 
-inline const double* slot_ptr(const tb_md_state* st, int K, int64_t t) {
-  const int S = K + 1;
-  const int slot = (int)(((t % S) + S) % S);
-  return st->n_hist + (size_t)slot * st->sys.natoms;
+// D from H: Fermi operator (dm_fermi, mu carried in st->mu) when kT > 0, else
+// the T_e = 0 projector by SP2.
+int density(tb_ctx* ctx, tb_md_state* st, const tb_sp2_opts* so, cudaStream_t s) {
+  if (st->kT > 0.0)
+    return dm_fermi(ctx, st->H, st->sys.norb, st->n_occ, st->kT, &st->fermi, st->D, st->mu, st->workspace,
+                    st->workspace_bytes, st->fermi_report, s);
+  return dm_sp2(ctx, st->H, st->sys.norb, st->n_occ, so, st->D, st->workspace, st->workspace_bytes,
+                st->sp2_report, s);
 }
 
 // H[n] -> D -> q -> F, E for the current positions and the given n.
@@ -127,8 +130,7 @@ int electronic_step(tb_ctx* ctx, const tb_params* p, tb_md_state* st, const tb_s
                     const double* n_aux, cudaStream_t s) {
   int rc = tb_build_H(ctx, p, &st->sys, st->R, n_aux, st->H, st->gamma, s);
   if (rc) return rc;
-  rc = dm_sp2(ctx, st->H, st->sys.norb, st->n_occ, so, st->D, st->workspace, st->workspace_bytes,
-              st->sp2_report, s);
+  rc = density(ctx, st, so, s);
   if (rc) return rc;
   rc = mulliken(ctx, p, &st->sys, st->D, st->q, s);
   if (rc) return rc;
@@ -229,8 +231,7 @@ extern "C" int xlbomd_init(tb_ctx* ctx, const tb_params* p, tb_md_state* st, con
     TB_CUDA_TRY(ctx, cudaMemcpyAsync(n_dev, n.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
     rc = tb_build_H(ctx, p, &st->sys, st->R, n_dev, st->H, st->gamma, s);
     if (rc) return rc;
-    rc = dm_sp2(ctx, st->H, st->sys.norb, st->n_occ, so, st->D, st->workspace, st->workspace_bytes,
-                st->sp2_report, s);
+    rc = density(ctx, st, so, s);
     if (rc) return rc;
     rc = mulliken(ctx, p, &st->sys, st->D, st->q, s);
     if (rc) return rc;
@@ -260,10 +261,9 @@ extern "C" int xlbomd_init(tb_ctx* ctx, const tb_params* p, tb_md_state* st, con
   k_fill_hist<<<(N + 127) / 128, 128, 0, s>>>(N, S, n_dev, st->n_hist);
   TB_LAUNCH_CHECK(ctx);
   st->step = 0;
-  rc = electronic_step(ctx, p, st, so, slot_ptr(st, xp->K, 0), s);
+  rc = electronic_step(ctx, p, st, so, st->n_hist, s);
   if (rc) return rc;
-  k_kick_energy<<<1, 256, 0, s>>>(N, st->v, st->F, st->mass, xp->dt, 0, slot_ptr(st, xp->K, 0), st->q,
-                                  st->energies, 0);
+  k_kick_energy<<<1, 256, 0, s>>>(N, st->v, st->F, st->mass, xp->dt, 0, st->n_hist, st->q, st->energies);
   TB_LAUNCH_CHECK(ctx);
   // the host vectors must outlive the async copies above
   TB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
@@ -280,14 +280,12 @@ extern "C" int xlbomd_step(tb_ctx* ctx, const tb_params* p, tb_md_state* st, con
   const int nb = (N + 127) / 128;
   k_kick_drift<<<nb, 128, 0, s>>>(N, st->v, st->F, st->mass, xp->dt, st->R);
   TB_LAUNCH_CHECK(ctx);
-  k_n_update<<<nb, 128, 0, s>>>(N, st->n_hist, st->step, xp->K, st->q, xp->kappa, xp->alpha, *xp);
+  k_n_update<<<nb, 128, 0, s>>>(N, st->n_hist, xp->K, st->q, xp->kappa, xp->alpha, *xp);
   TB_LAUNCH_CHECK(ctx);
-  const int64_t t1 = st->step + 1;
-  const double* n_new = slot_ptr(st, xp->K, t1);
-  rc = electronic_step(ctx, p, st, so, n_new, s);
+  rc = electronic_step(ctx, p, st, so, st->n_hist, s);
   if (rc) return rc;
-  k_kick_energy<<<1, 256, 0, s>>>(N, st->v, st->F, st->mass, xp->dt, 1, n_new, st->q, st->energies, t1);
+  k_kick_energy<<<1, 256, 0, s>>>(N, st->v, st->F, st->mass, xp->dt, 1, st->n_hist, st->q, st->energies);
   TB_LAUNCH_CHECK(ctx);
-  st->step = t1;
+  st->step += 1;
   return TB_OK;
 }

@@ -94,10 +94,11 @@ class DensitySolver:
 
 
 class MDState:
-    """Device arrays of one XL-BOMD trajectory and its tb_md_state."""
+    """Device arrays of one XL-BOMD trajectory and its tb_md_state (T_e = 0 with
+    SP2 options, or kT > 0 with Fermi-operator options)."""
 
     def __init__(self, ds: DeviceSystem, v0: np.ndarray, masses: np.ndarray, n_occ: float, K: int,
-                 opts: tbmd.tb_sp2_opts):
+                 opts: tbmd.tb_sp2_opts, kT: float = 0.0, fermi: "tbmd.tb_fermi_opts" = None):
         dev = ds.device
         N, n = ds.natoms, ds.norb
         f64 = dict(dtype=torch.float64, device=dev)
@@ -113,17 +114,25 @@ class MDState:
         self.gamma = torch.zeros(N, N, **f64)
         self.energies = torch.zeros(8, **f64)
         self.report = new_report(dev)
-        self.ws = Workspace(tbmd.dm_sp2_workspace_size(n, opts), dev)
+        self.fermi_report = torch.zeros(ctypes.sizeof(tbmd.tb_fermi_report), dtype=torch.uint8, device=dev)
+        self.mu = torch.full((1,), float("nan"), dtype=torch.float64, device=dev)
+        if kT > 0.0:
+            fermi = fermi or fermi_opts()
+            self.ws = Workspace(tbmd.dm_fermi_workspace_size(n, fermi), dev)
+        else:
+            fermi = tbmd.tb_fermi_opts()
+            self.ws = Workspace(tbmd.dm_sp2_workspace_size(n, opts), dev)
         self.K = K
         self.st = tbmd.tb_md_state(
             sys=ds.sys, n_occ=float(n_occ), R=self.R.data_ptr(), v=self.v.data_ptr(), F=self.F.data_ptr(),
             mass=self.mass.data_ptr(), n_hist=self.n_hist.data_ptr(), q=self.q.data_ptr(),
             H=self.H.data_ptr(), D=self.D.data_ptr(), gamma=self.gamma.data_ptr(),
             energies=self.energies.data_ptr(), sp2_report=self.report.data_ptr(),
-            workspace=self.ws.ptr, workspace_bytes=self.ws.nbytes, step=0)
+            workspace=self.ws.ptr, workspace_bytes=self.ws.nbytes, step=0, kT=float(kT), fermi=fermi,
+            mu=self.mu.data_ptr(), fermi_report=self.fermi_report.data_ptr())
 
     def n_current(self) -> torch.Tensor:
-        return self.n_hist[int(self.st.step) % (self.K + 1)]
+        return self.n_hist[0]
 
 
 def fermi_opts(precision: str = "tf32x3", m: int = 16, ns_iters: int = 4, mu_iters: int = 30,
@@ -152,3 +161,64 @@ class FermiSolver:
         tbmd.dm_fermi(self.ctx, H, self.n, n_occ, kT, self.opts, D, self.mu, self.ws.ptr, self.ws.nbytes,
                       self.report, stream)
         return D
+
+
+class Server:
+    """tb_server: continuous batching of XL-BOMD step requests (C++ runtime)."""
+
+    def __init__(self, ctx: tbmd.Context, p: tbmd.tb_params, xl: tbmd.tb_xl_params, kT: float = 0.1,
+                 max_slots: int = 16, hbm_budget: int = 0, sp2: "tbmd.tb_sp2_opts" = None,
+                 fermi: "tbmd.tb_fermi_opts" = None, scf_tol: float = 1e-8, scf_max_iter: int = 200):
+        self.ctx = ctx
+        o = tbmd.tb_server_opts(max_slots=int(max_slots), hbm_budget=int(hbm_budget), kT=float(kT), xl=xl,
+                                sp2=sp2 or sp2_opts("tf32x3", refine=3), fermi=fermi or fermi_opts(),
+                                scf_tol=float(scf_tol), scf_max_iter=int(scf_max_iter))
+        self.opts = o
+        self.handle = tbmd.tb_server_create(ctx, p, o)
+        self.natoms = []
+
+    def footprint(self, types) -> int:
+        return tbmd.tb_server_footprint(self.ctx, self.handle, types)
+
+    def add(self, types, box, R0, v0, mass, n_occ) -> int:
+        t = tbmd.tb_server_add(self.ctx, self.handle, types, box, R0, v0, mass, n_occ)
+        self.natoms.append(len(types))
+        return t
+
+    def submit(self, traj: int) -> int:
+        return tbmd.tb_server_submit(self.ctx, self.handle, traj)
+
+    def poll(self, wait: bool = False, max_out: int = 64) -> list:
+        return tbmd.tb_server_poll(self.ctx, self.handle, wait, max_out)
+
+    def drain(self) -> list:
+        """Poll until nothing is queued or in flight; all completions."""
+        out = []
+        while True:
+            out += self.poll(wait=True)
+            st = self.stats()
+            if st["running"] == 0 and st["queued"] == 0:
+                return out
+
+    def retire(self, traj: int):
+        tbmd.tb_server_retire(self.ctx, self.handle, traj)
+
+    def read(self, traj: int) -> dict:
+        return tbmd.tb_server_read(self.ctx, self.handle, traj, self.natoms[traj])
+
+    def stats(self) -> dict:
+        return tbmd.tb_server_stats(self.ctx, self.handle)
+
+    def replay(self, arrival_s, traj) -> list:
+        return tbmd.tb_server_replay(self.ctx, self.handle, arrival_s, traj)
+
+    def close(self):
+        if self.handle:
+            tbmd.tb_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

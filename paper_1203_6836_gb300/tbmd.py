@@ -69,6 +69,11 @@ class tb_sp2_report(ctypes.Structure):
                 ("refine_bits", ctypes.c_uint64)]
 
 
+class tb_xl_params(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("kappa", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("K", ctypes.c_int), ("c", ctypes.c_double * (XL_KMAX + 1))]
+
+
 class tb_fermi_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("m", ctypes.c_int), ("ns_iters", ctypes.c_int),
                 ("mu_iters", ctypes.c_int), ("trace_tol", ctypes.c_double)]
@@ -80,11 +85,6 @@ class tb_fermi_report(ctypes.Structure):
                 ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double)]
 
 
-class tb_xl_params(ctypes.Structure):
-    _fields_ = [("dt", ctypes.c_double), ("kappa", ctypes.c_double), ("alpha", ctypes.c_double),
-                ("K", ctypes.c_int), ("c", ctypes.c_double * (XL_KMAX + 1))]
-
-
 class tb_md_state(ctypes.Structure):
     _fields_ = [("sys", tb_system), ("n_occ", ctypes.c_double),
                 ("R", ctypes.c_void_p), ("v", ctypes.c_void_p), ("F", ctypes.c_void_p),
@@ -92,10 +92,30 @@ class tb_md_state(ctypes.Structure):
                 ("H", ctypes.c_void_p), ("D", ctypes.c_void_p), ("gamma", ctypes.c_void_p),
                 ("energies", ctypes.c_void_p), ("sp2_report", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
-                ("step", ctypes.c_int64)]
+                ("step", ctypes.c_int64), ("kT", ctypes.c_double), ("fermi", tb_fermi_opts),
+                ("mu", ctypes.c_void_p), ("fermi_report", ctypes.c_void_p)]
+
+
+class tb_server_opts(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("kT", ctypes.c_double),
+                ("xl", tb_xl_params), ("sp2", tb_sp2_opts), ("fermi", tb_fermi_opts),
+                ("scf_tol", ctypes.c_double), ("scf_max_iter", ctypes.c_int)]
+
+
+class tb_completion(ctypes.Structure):
+    _fields_ = [("request", ctypes.c_int64), ("traj", ctypes.c_int), ("status", ctypes.c_int),
+                ("step", ctypes.c_int64), ("t_submit", ctypes.c_double), ("t_launch", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("gpu_ms", ctypes.c_double), ("energies", ctypes.c_double * 8)]
+
+
+class tb_server_counts(ctypes.Structure):
+    _fields_ = [("trajectories", ctypes.c_int), ("admitted", ctypes.c_int), ("waiting", ctypes.c_int),
+                ("running", ctypes.c_int), ("queued", ctypes.c_int), ("bytes_in_use", ctypes.c_size_t),
+                ("budget", ctypes.c_size_t), ("submitted", ctypes.c_int64), ("completed", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
 _SIGS = {
     "tb_ctx_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
     "tb_ctx_destroy": (ctypes.c_int, [_P]),
@@ -130,6 +150,21 @@ _SIGS = {
                                    ctypes.c_int, ctypes.POINTER(ctypes.c_int), _P]),
     "xlbomd_step": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_md_state),
                                    ctypes.POINTER(tb_xl_params), ctypes.POINTER(tb_sp2_opts), _P]),
+    "tb_server_create": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_server_opts),
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "tb_server_destroy": (ctypes.c_int, [_P]),
+    "tb_server_footprint": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_size_t)]),
+    "tb_server_add": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_double, _D, _D,
+                                     _D, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
+    "tb_server_submit": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
+    "tb_server_poll": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(tb_completion), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "tb_server_retire": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tb_server_read": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D, _D, _D]),
+    "tb_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(tb_server_counts)]),
+    "tb_server_replay": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(tb_completion)]),
 }
 
 _lib = None
@@ -313,3 +348,87 @@ def xlbomd_step(ctx: Context, p: tb_params, st: tb_md_state, xp: tb_xl_params, s
                 stream=None) -> int:
     return ctx.check(lib().xlbomd_step(ctx.handle, ctypes.byref(p), ctypes.byref(st), ctypes.byref(xp),
                                        ctypes.byref(so), _stream(stream)), "xlbomd_step")
+
+
+# ------------------------------------------------------------------ serving
+
+def _dptr(a):
+    """Pointer to a C-contiguous float64 NumPy array (or None)."""
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def tb_server_create(ctx: Context, p: tb_params, opts: tb_server_opts) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    ctx.check(lib().tb_server_create(ctx.handle, ctypes.byref(p), ctypes.byref(opts), ctypes.byref(h)),
+              "tb_server_create")
+    return h
+
+
+def tb_server_destroy(server) -> int:
+    return lib().tb_server_destroy(server)
+
+
+def tb_server_footprint(ctx: Context, server, types) -> int:
+    import numpy as np
+    t = np.ascontiguousarray(types, dtype=np.int32)
+    b = ctypes.c_size_t()
+    ctx.check(lib().tb_server_footprint(server, len(t), t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                        ctypes.byref(b)), "tb_server_footprint")
+    return int(b.value)
+
+
+def tb_server_add(ctx: Context, server, types, box: float, R0, v0, mass, n_occ: float) -> int:
+    import numpy as np
+    t = np.ascontiguousarray(types, dtype=np.int32)
+    R = np.ascontiguousarray(R0, dtype=np.float64)
+    v = np.ascontiguousarray(v0, dtype=np.float64)
+    m = np.ascontiguousarray(mass, dtype=np.float64)
+    out = ctypes.c_int()
+    ctx.check(lib().tb_server_add(server, len(t), t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), float(box),
+                                  _dptr(R), _dptr(v), _dptr(m), float(n_occ), ctypes.byref(out)), "tb_server_add")
+    return int(out.value)
+
+
+def tb_server_submit(ctx: Context, server, traj: int) -> int:
+    rid = ctypes.c_int64()
+    ctx.check(lib().tb_server_submit(server, int(traj), ctypes.byref(rid)), "tb_server_submit")
+    return int(rid.value)
+
+
+def tb_server_poll(ctx: Context, server, wait: bool = False, max_out: int = 64) -> list:
+    buf = (tb_completion * max_out)()
+    n = ctypes.c_int()
+    ctx.check(lib().tb_server_poll(server, int(bool(wait)), buf, max_out, ctypes.byref(n)), "tb_server_poll")
+    return [buf[i] for i in range(n.value)]
+
+
+def tb_server_retire(ctx: Context, server, traj: int) -> int:
+    return ctx.check(lib().tb_server_retire(server, int(traj)), "tb_server_retire")
+
+
+def tb_server_read(ctx: Context, server, traj: int, natoms: int) -> dict:
+    import numpy as np
+    R = np.zeros((natoms, 3))
+    v = np.zeros((natoms, 3))
+    q = np.zeros(natoms)
+    n = np.zeros(natoms)
+    E = np.zeros(8)
+    ctx.check(lib().tb_server_read(server, int(traj), _dptr(R), _dptr(v), _dptr(q), _dptr(n), _dptr(E)),
+              "tb_server_read")
+    return {"R": R, "v": v, "q": q, "n": n, "E": E}
+
+
+def tb_server_stats(ctx: Context, server) -> dict:
+    c = tb_server_counts()
+    ctx.check(lib().tb_server_stats(server, ctypes.byref(c)), "tb_server_stats")
+    return {k: getattr(c, k) for k, _ in tb_server_counts._fields_}
+
+
+def tb_server_replay(ctx: Context, server, arrival_s, traj) -> list:
+    import numpy as np
+    a = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    t = np.ascontiguousarray(traj, dtype=np.int32)
+    out = (tb_completion * len(a))()
+    ctx.check(lib().tb_server_replay(server, len(a), _dptr(a), t.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                     out), "tb_server_replay")
+    return list(out)

@@ -32,3 +32,12 @@ def test_status_strings_and_argument_errors_without_gpu():
     assert size.value >= 2 * 8 * 4096 * 4096
     # a null context is rejected before anything touches the device
     assert lib.dm_sp2(None, None, 10, 5.0, ctypes.byref(opts), None, None, 0, None, None) == tbmd.TB_ERR_ARG
+    # serving entry points reject a null server or context without touching the device
+    so = tbmd.tb_server_opts(max_slots=4)
+    out = ctypes.c_void_p()
+    assert lib.tb_server_create(None, None, ctypes.byref(so), ctypes.byref(out)) == tbmd.TB_ERR_ARG
+    n = ctypes.c_int()
+    assert lib.tb_server_poll(None, 0, None, 0, ctypes.byref(n)) == tbmd.TB_ERR_ARG
+    assert lib.tb_server_submit(None, 0, None) == tbmd.TB_ERR_ARG
+    assert lib.tb_server_destroy(None) == tbmd.TB_OK
+    assert ctypes.sizeof(tbmd.tb_completion) == 8 + 4 + 4 + 8 + 4 * 8 + 8 * 8

@@ -69,8 +69,9 @@ def test_xlbomd_trajectory_matches_oracle(ctx, m, box):
     assert g["report"]["status"] == tbmd.TB_OK
 
 
-def test_xlbomd_history_ring_buffer_matches_eq_verl_n(ctx):
-    """After init the whole history equals q; one step applies Eq. Verl_n."""
+def test_xlbomd_history_shift_register_matches_eq_verl_n(ctx):
+    """After init the whole history equals q; one step applies Eq. Verl_n and
+    moves the history down one slot."""
     s = molecular_water(1, 12.0, seed=1)
     M = s.masses(P)
     v0 = thermal_velocities(M, 300.0, seed=7)
@@ -89,3 +90,6 @@ def test_xlbomd_history_ring_buffer_matches_eq_verl_n(ctx):
     # history = the SCF's last charges, q_t = charges of D[n_t] (equal to 1e-10)
     expect = md.modified_verlet_n([h[0]] * (XL.K + 1), q0, XL)
     assert np.abs(n1 - expect).max() < 1e-13
+    h1 = st.n_hist.cpu().numpy()
+    assert np.array_equal(h1[1:], h[:-1])
+    assert st.energies[7].item() == 1.0
