@@ -128,10 +128,12 @@ def _TS(D: np.ndarray, kT: float) -> float:
 
 
 def xlbomd(R0, types, box, p: ModelParams, xl: XLParams, v0, masses, n_occ, nsteps: int,
-           scf_tol: float = 1e-10, kT: float = 0.0, record_R: bool = False) -> Trajectory:
+           scf_tol: float = 1e-10, kT: float = 0.0, record_R: bool = False, scf_max_iter: int = 300,
+           scf_strict: bool = True) -> Trajectory:
     """Fast-QMMD trajectory (module docstring).  Step order: half kick, drift,
-    n update from (n history, q_t), H[n_{t+1}] -> D -> q_{t+1}, force, half kick."""
-    q0, fr, _ = scf(R0, types, box, p, n_occ, tol=scf_tol, kT=kT)
+    n update from (n history, q_t), H[n_{t+1}] -> D -> q_{t+1}, force, half kick.
+    scf_strict=False starts from the last SCF iterate when the cap is reached."""
+    q0, fr, _ = scf(R0, types, box, p, n_occ, tol=scf_tol, kT=kT, max_iter=scf_max_iter, strict=scf_strict)
     R, v = R0.copy(), v0.copy()
     n_hist = [q0.copy() for _ in range(xl.K + 1)]
     q_t = q0
