@@ -116,6 +116,9 @@ typedef struct {
   double idem_fro;      /* ||X^2 - X||_F of the input of the last FP64 projection, -1 if none */
   uint64_t branch_bits[2];  /* bit k: branch of main-phase projection k (1 = 2X - X^2) */
   uint64_t refine_bits;     /* bit k: branch of refinement projection k */
+  int64_t block_products;   /* block-sparse path: 128 x 128 block products executed over all
+                               projections (2 * 128^3 flops each); 0 on the dense paths */
+  int64_t blocks;           /* block-sparse path: stored 128 x 128 blocks of the returned D; else 0 */
 } tb_sp2_report;
 
 /* ---------------------------------------------------------------- context */
@@ -136,7 +139,11 @@ const char* tb_ctx_last_error(const tb_ctx* ctx);
  * refinement (phase 1).  tb_ctx_sp2_launch_times waits for the last event
  * and writes the duration (ms) of each launch of the last dm_sp2 call into
  * the HOST array ms[0..cap), *count = launches written.  Launches after the
- * device-side stop decision return at once and show as short entries. */
+ * device-side stop decision return at once and show as short entries.
+ * Block-sparse path (tau > 0): phase 0 entry k is the whole projection k
+ * (symbolic and numeric kernels); phase 1 holds events around the numeric
+ * kernels, so its entry 2k is numeric kernel k and entry 2k+1 the symbolic
+ * kernels of projection k+1.  At most 130 entries per phase are kept. */
 int tb_ctx_set_profiling(tb_ctx* ctx, int enable);
 int tb_ctx_sp2_launch_times(tb_ctx* ctx, int phase, float* ms, int cap, int* count);
 
@@ -370,6 +377,7 @@ typedef struct {
   int64_t request;      /* id returned by tb_server_submit (or the replay index order) */
   int traj;             /* trajectory id */
   int status;           /* status of the step's density solve (TB_OK, TB_ERR_NOT_CONVERGED, ...) */
+  int solver_iters;     /* SP2 projections (kT = 0) or Fermi-operator expansions (kT > 0) */
   int64_t step;         /* the trajectory's step count after this step */
   double t_submit;      /* host time of the request (replay: its scheduled arrival) */
   double t_launch;      /* host time of the graph launch */

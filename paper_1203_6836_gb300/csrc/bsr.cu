@@ -353,6 +353,7 @@ __global__ void __launch_bounds__(1024) k_bsr_scan_pairs(Args a, Sym sy) {
     }
     sy.scal[1] = acc;
     sy.pair_ptr[nb] = acc;
+    a.st->block_products += (unsigned long long)acc;
     if (acc > a.pcap) atomicExch(&a.st->err, TB_ERR_OOM);
   }
   __syncthreads();
@@ -614,6 +615,8 @@ __global__ void k_bsr_report(SP2State* st, Args a, Buf b0, Buf b1, tb_sp2_report
   rep->branch_bits[0] = st->branch[0];
   rep->branch_bits[1] = st->branch[1];
   rep->refine_bits = 0;
+  rep->block_products = (long long)st->block_products;
+  rep->blocks = min(b.row_ptr[a.nsb], a.cap);
 }
 
 struct BsrLayout {
@@ -783,8 +786,10 @@ int run_bsr(tb_ctx* ctx, const double* H, int n, double nocc, const tb_sp2_opts*
     k_bsr_fill_out<<<L.nsb, 256, 0, s>>>(a, bo, bn, sy);
     k_bsr_scan_pairs<<<1, 1024, 0, s>>>(a, sy);
     k_bsr_pairs<<<std::max(1, std::min(L.cap, 4096) / 128 + 1), 128, 0, s>>>(a, bo, bn, sy);
+    tb_prof_mark(ctx, 1, 2 * k, s);
     k_bsr_step_tc<P><<<grid, kThreads, Cf::smem_bytes, s>>>(a, mh[k & 1], ml[k & 1], bo, bn, sy);
     TB_LAUNCH_CHECK(ctx);
+    tb_prof_mark(ctx, 1, 2 * k + 1, s);
     tb_prof_mark(ctx, 0, k + 1, s);
   }
   TB_CUDA_TRY(ctx, cudaMemsetAsync(D, 0, sizeof(double) * (size_t)n * n, s));

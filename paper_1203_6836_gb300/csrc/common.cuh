@@ -119,6 +119,7 @@ struct SP2State {
   double idem_fro;               // ||X^2 - X||_F of the last FP64 projection input
   unsigned long long branch[2];
   unsigned long long rbranch;
+  unsigned long long block_products;  // block-sparse path: executed 128^3 block products
 };
 
 // Parameters of a purification step shared by the FP64 and tensor-core kernels.

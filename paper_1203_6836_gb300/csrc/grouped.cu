@@ -331,6 +331,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         rp->branch_bits[0] = s_branch[0];
         rp->branch_bits[1] = s_branch[1];
         rp->refine_bits = 0;
+        rp->block_products = 0;
+        rp->blocks = 0;
       }
       __syncthreads();
     }

@@ -65,6 +65,8 @@ struct Slot {
 
 constexpr size_t kAlign = 1024;
 constexpr size_t kHostDoubles = 8 + 16;  // energies + a report (<= 128 bytes)
+static_assert(sizeof(tb_sp2_report) <= 16 * sizeof(double) && sizeof(tb_fermi_report) <= 16 * sizeof(double),
+              "solver report does not fit the pinned completion buffer");
 
 inline size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -292,7 +294,8 @@ int collect(tb_server* sv, tb_completion* out, int max_out, int* n_out) {
     c = tb_completion{};
     c.request = sl.req.id;
     c.traj = sl.req.traj;
-    c.status = *reinterpret_cast<const int*>(T.host + 8);
+    c.status = reinterpret_cast<const int*>(T.host + 8)[0];
+    c.solver_iters = reinterpret_cast<const int*>(T.host + 8)[1];  // iters / mu_iters
     c.step = (int64_t)T.host[7];
     c.t_submit = sl.req.t_submit;
     c.t_launch = sl.t_launch;

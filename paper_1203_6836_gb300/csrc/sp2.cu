@@ -375,6 +375,8 @@ __global__ void __launch_bounds__(256) k_finalize(SP2State* st, int n, int ld, i
     rep->branch_bits[0] = st->branch[0];
     rep->branch_bits[1] = st->branch[1];
     rep->refine_bits = st->rbranch;
+    rep->block_products = 0;
+    rep->blocks = 0;
   }
 }
 

@@ -71,7 +71,7 @@ def report_to_dict(buf: torch.Tensor) -> dict:
     r = tbmd.tb_sp2_report.from_buffer_copy(raw[:ctypes.sizeof(tbmd.tb_sp2_report)])
     return {"status": r.status, "iters": r.iters, "refine_iters": r.refine_iters, "n": r.n,
             "eps_min": r.eps_min, "eps_max": r.eps_max, "trace": r.trace, "idem_trace": r.idem_trace,
-            "idem_fro": r.idem_fro,
+            "idem_fro": r.idem_fro, "block_products": r.block_products, "blocks": r.blocks,
             "branches": [(int(r.branch_bits[k >> 6]) >> (k & 63)) & 1 for k in range(r.iters)],
             "refine_branches": [(int(r.refine_bits) >> k) & 1 for k in range(r.refine_iters)]}
 

@@ -66,7 +66,7 @@ class tb_sp2_report(ctypes.Structure):
                 ("n", ctypes.c_int), ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double),
                 ("trace", ctypes.c_double), ("idem_trace", ctypes.c_double),
                 ("idem_fro", ctypes.c_double), ("branch_bits", ctypes.c_uint64 * 2),
-                ("refine_bits", ctypes.c_uint64)]
+                ("refine_bits", ctypes.c_uint64), ("block_products", ctypes.c_int64), ("blocks", ctypes.c_int64)]
 
 
 class tb_xl_params(ctypes.Structure):
@@ -104,7 +104,7 @@ class tb_server_opts(ctypes.Structure):
 
 class tb_completion(ctypes.Structure):
     _fields_ = [("request", ctypes.c_int64), ("traj", ctypes.c_int), ("status", ctypes.c_int),
-                ("step", ctypes.c_int64), ("t_submit", ctypes.c_double), ("t_launch", ctypes.c_double),
+                ("solver_iters", ctypes.c_int), ("step", ctypes.c_int64), ("t_submit", ctypes.c_double), ("t_launch", ctypes.c_double),
                 ("t_done", ctypes.c_double), ("gpu_ms", ctypes.c_double), ("energies", ctypes.c_double * 8)]
 
 

@@ -40,4 +40,4 @@ def test_status_strings_and_argument_errors_without_gpu():
     assert lib.tb_server_poll(None, 0, None, 0, ctypes.byref(n)) == tbmd.TB_ERR_ARG
     assert lib.tb_server_submit(None, 0, None) == tbmd.TB_ERR_ARG
     assert lib.tb_server_destroy(None) == tbmd.TB_OK
-    assert ctypes.sizeof(tbmd.tb_completion) == 8 + 4 + 4 + 8 + 4 * 8 + 8 * 8
+    assert ctypes.sizeof(tbmd.tb_completion) == 8 + 4 + 4 + 4 + 4 + 8 + 4 * 8 + 8 * 8
