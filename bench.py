@@ -731,30 +731,36 @@ def run_batched(args):
 
 def run_serving(args):
     """64 finite-temperature XL-BOMD trajectories, atom counts log-uniform in
-    [32, 2048], Poisson step requests at 2000/s through tb_server."""
+    [32, 2048], Poisson step requests at 2000/s through tb_server.  Each
+    trajectory is water-like vapour (H2O-like molecules at 0.1 g/cc) with the
+    kappa scaled to 0.06 kappa0: at 1.0 g/cc this SCC-TB recipe is near-metallic
+    and the plain modified-Verlet charge dynamics diverges (largest eigenvalue
+    of I - dq/dn ~ 24); the vapour's is ~9.3 and kappa * 9.3 ~ 1 is stable."""
+    import dataclasses
     import numpy as np
     import torch
     from paper_1203_6836_gb300 import tbmd
     from paper_1203_6836_gb300.device import Server, fermi_opts, sp2_opts, xl_params
-    from workloads import ModelParams, XLParams, water_system, serving_trajectories, thermal_velocities
+    from workloads import ModelParams, XLParams, molecular_liquid, serving_trajectories, thermal_velocities
     ctx = _setup_gpu()
     P = ModelParams()
     TP = tbmd.tb_params.from_model(P)
-    XL = XLParams()
+    XL = dataclasses.replace(XLParams(), kappa_scale=0.06)
     xp = xl_params(XL.dt, XL.kappa, XL.alpha, XL.c)
     sizes, arrivals, which = serving_trajectories(n_requests=args.requests)
     fo = fermi_opts(args.precision)
-    sv = Server(ctx, TP, xp, kT=0.1, max_slots=32, fermi=fo, scf_tol=1e-5, scf_max_iter=8)
+    sv = Server(ctx, TP, xp, kT=0.1, max_slots=32, fermi=fo, scf_tol=1e-5, scf_max_iter=20)
     systems = []
     t0 = time.perf_counter()
     for i, N in enumerate(sizes):
-        w = water_system(int(N), density=1.0, seed=2000 + i)
+        w = molecular_liquid(max(1, int(round(N / 3))), 0.1, seed=2000 + i)
         M = w.masses(P)
         v0 = thermal_velocities(M, 300.0, seed=3000 + i)
         sv.add(w.types, w.box, w.R, v0, M, w.n_occ(P))
         systems.append(w)
     admit_s = time.perf_counter() - t0
     norb = [int(np.sum(np.where(w.types == 0, 4, 1))) for w in systems]
+    natoms = [w.natoms for w in systems]
     # warm-up: one step of every trajectory
     for t in range(len(sizes)):
         sv.submit(t)
@@ -785,19 +791,22 @@ def run_serving(args):
         w = systems[i]
         M = w.masses(P)
         md.xlbomd(w.R, w.types, w.box, P, XL, thermal_velocities(M, 300.0, seed=3000 + int(i)), M, w.n_occ(P), 3,
-                  scf_tol=1e-5, kT=0.1, scf_max_iter=8, scf_strict=False)
+                  scf_tol=1e-5, kT=0.1, scf_max_iter=40, scf_strict=False)
         done += 3
     cpu_rate = done / (time.perf_counter() - t0)
     line = _common(args, "served finite-T XL-BOMD steps/s; p50/p99 step latency", value, "steps/s",
                    1e3 / value, f"{args.precision}+f64",
-                   f"64 trajectories, atom counts log-uniform in [32,2048] (seed 5), kT=0.1 eV (GEMM-only FOE), "
-                   f"{len(out)} Poisson step requests at 2000/s (seed 6), one step in flight per trajectory",
+                   f"64 trajectories of water-like vapour (H2O-like molecules, 0.1 g/cc), atom counts log-uniform "
+                   f"in [32,2048] (seed 5), kT=0.1 eV (GEMM-only FOE), kappa 0.06 kappa0, {len(out)} Poisson step "
+                   f"requests at 2000/s (seed 6), one step in flight per trajectory",
                    latency_ms={"p50": _pct(lat, 0.5), "p99": _pct(lat, 0.99), "max": max(lat)},
                    service_ms={"p50": _pct(svc, 0.5), "p99": _pct(svc, 0.99)},
                    requests_ok=ok, wall_s=wall, admission_s=admit_s,
                    server={"slots": 32, "bytes_in_use": st["bytes_in_use"], "budget": st["budget"],
                            "admitted": st["admitted"]},
                    foe={"m": fo.m, "ns_iters": ns, "mean_expansions_per_step": sum(c.solver_iters for c in out) / len(out)},
+                   stability={"max_abs_n_minus_q": max(c.energies[6] for c in out),
+                              "atoms": [min(natoms), max(natoms)]},
                    roofline={"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": achieved / peak, "traffic": None,
                              "kernel": "k_gemm_tc (FOE products of all trajectories, aggregate over the run)",

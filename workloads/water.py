@@ -289,6 +289,34 @@ def config3_system(seed: int = 0) -> WaterSystem:
     return water_system(16384, density=1.0, seed=seed, morton=True)
 
 
+def molecular_liquid(n_mol: int, density: float = 1.0, seed: int = 0, bond: float = 0.96,
+                     angle_deg: float = 104.5, jitter: float = 0.1,
+                     p: ModelParams = ModelParams()) -> WaterSystem:
+    """n_mol H2O-like molecules at `density` g/cc: O atoms on the first n_mol
+    sites (row order) of the smallest cubic grid that holds them, Gaussian
+    jitter, random orientations (O-H `bond` A, H-O-H `angle_deg`).  Atom
+    order: all O, then the H pairs in molecule order."""
+    rng = np.random.default_rng(seed)
+    box = box_from_density(n_mol, 2 * n_mol, density, p)
+    m = 1
+    while m ** 3 < n_mol:
+        m += 1
+    grid = (np.arange(m) + 0.5) / m * box
+    th = math.radians(angle_deg)
+    u1 = np.array([math.sin(th / 2), math.cos(th / 2), 0.0]) * bond
+    u2 = np.array([-math.sin(th / 2), math.cos(th / 2), 0.0]) * bond
+    Os, Hs = [], []
+    for k in range(n_mol):
+        x, y, z = grid[k // (m * m)], grid[(k // m) % m], grid[k % m]
+        O = np.array([x, y, z]) + rng.normal(0.0, jitter, 3)
+        Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+        Os.append(O)
+        Hs += [O + Q @ u1, O + Q @ u2]
+    R = np.mod(np.array(Os + Hs), box)
+    types = np.array([TYPE_O] * len(Os) + [TYPE_H] * len(Hs), dtype=np.int32)
+    return WaterSystem(R=R, types=types, box=float(box), seed=seed)
+
+
 def molecular_water(m: int, box: float, seed: int = 0, bond: float = 0.96,
                     angle_deg: float = 104.5, jitter: float = 0.1) -> WaterSystem:
     """m^3 H2O-like molecules (O-H `bond` A, H-O-H `angle_deg`) with random
