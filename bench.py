@@ -276,6 +276,11 @@ def run_ours(args):
     avg_ms = sum(work) / len(work) if work else float("nan")
     achieved = 2.0 * float(n) ** 3 / (avg_ms * 1e-3) / 1e12
     mmas = 3 if args.precision.endswith("x3") else 1
+    # the kernel computes the nt(nt+1)/2 upper-triangle 128 x 128 tiles of the
+    # padded ld x ld product and mirrors them
+    ld = (n + 127) // 128 * 128
+    nt = ld // 128
+    tri_frac = (nt + 1) / (2 * nt)
     ref_work = ref_ms[:last["refine_iters"]]
     ref_avg = sum(ref_work) / len(ref_work) if ref_work else float("nan")
 
@@ -380,7 +385,8 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": None,
                          "kernel": f"k_sp2_step_tc<{args.precision}>",
                          "peak_source": f"{peaks['source']} bf16_tflops_sustained x {ratio} ({'tf32' if tf else 'bf16'})",
-                         "mma_per_product": mmas, "mma_frac": achieved * mmas / peak,
+                         "mma_per_product": mmas, "upper_triangle_tiles": tri_frac,
+                         "mma_frac": achieved * mmas * tri_frac * (ld / n) ** 3 / peak,
                          "avg_launch_ms": avg_ms},
             "refine_kernel": {"kind": "emulated FP64 (28 exact bf16 slice products)" if opts.refine_mode == 0
                               else "FP64 FMA",

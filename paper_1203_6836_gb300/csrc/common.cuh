@@ -148,6 +148,8 @@ int sp2_tc_step(tb_ctx* ctx, int precision, const SP2StepArgs& a,
                 const float* X_in, float* X_out, void* out_hi, void* out_lo,
                 cudaStream_t stream);
 int sp2_tc_num_tiles(int ld);
+// Partials (CTAs) of one persistent tensor-core projection (<= sp2_tc_num_tiles).
+int sp2_tc_num_parts(const tb_ctx* ctx, int ld);
 int sp2_tc_tile();
 size_t sp2_tc_operand_bytes(int precision);  // bytes per element of one operand array
 
@@ -156,6 +158,8 @@ size_t sp2_tc_operand_bytes(int precision);  // bytes per element of one operand
 int sp2_oz_step(tb_ctx* ctx, const SP2StepArgs& a, const double* Xin, double* Xout, void* slices, int* exps,
                 cudaStream_t s);
 int sp2_oz_max_ld();
+// Partials (CTAs, one per upper-triangle tile) of one emulated-FP64 projection.
+int sp2_oz_num_parts(int ld);
 size_t sp2_oz_slice_bytes(int ld);
 
 // Generic tensor-core product out = alpha A B + beta E + gamma I of symmetric,

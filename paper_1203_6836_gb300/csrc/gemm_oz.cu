@@ -19,7 +19,9 @@
 // and the always-positive diagonal pairs (s, s), s >= 5, bias a diagonal
 // entry by ~K 2^-60.  28 bf16 products replace one FP64 GEMM.
 //
-// Kernel layout: one CTA per 128 x 128 output tile; warp 0 issues TMA loads
+// Kernel layout: one CTA per 128 x 128 tile of the upper triangle (X^2 is
+// symmetric; the epilogue also writes each off-diagonal tile transposed,
+// one coalesced 32-lane store per column); warp 0 issues TMA loads
 // of (slice s, row block m) and (slice t, row block n) tiles, warp 1 issues
 // tcgen05.mma into a ring of four TMEM accumulators (512 columns), warps
 // 2-9 drain each pair's accumulator into int64 registers (64 columns per
@@ -62,7 +64,11 @@ __device__ __forceinline__ void pair_of(int p, int* s, int* t) {
 }
 
 // One warp per row: e_i from the row maximum, then the kS signed 6-bit
-// digits of every entry of the row (exact arithmetic on powers of two).
+// digits of every entry of the row.  r = x 2^{-e} is scaled exactly and
+// rounded once to the integer R = rint(r 2^{6 kS}) (|R| <= 2^42); the digits
+// are R's balanced base-64 digits, peeled off from the least significant
+// end in int64 arithmetic: d in [-32, 31] for s >= 2 and |d_1| <= 64, all
+// exact in bf16.  Four consecutive entries per lane per pass.
 __global__ void __launch_bounds__(256) k_oz_split(const SP2State* st, const double* __restrict__ X, int ld,
                                                   __nv_bfloat16* __restrict__ slices, int* __restrict__ exps) {
   if (st->rdone || st->err) return;
@@ -71,23 +77,56 @@ __global__ void __launch_bounds__(256) k_oz_split(const SP2State* st, const doub
   if (row >= ld) return;
   const double* xr = X + (size_t)row * ld;
   double mx = 0.0;
-  for (int j = lane; j < ld; j += 32) mx = fmax(mx, fabs(xr[j]));
+  for (int j = 4 * lane; j < ld; j += 128) {
+    const double2 u = *reinterpret_cast<const double2*>(xr + j);
+    const double2 w = *reinterpret_cast<const double2*>(xr + j + 2);
+    mx = fmax(mx, fmax(fmax(fabs(u.x), fabs(u.y)), fmax(fabs(w.x), fabs(w.y))));
+  }
   mx = warp_max(mx);
   int e = 0;
   if (mx > 0.0) {
     frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): |x| / 2^e <= 1
+    e = max(e, -960);  // keeps 2^{42 - e} finite; such rows are below every digit
   }
   if (lane == 0) exps[row] = e;
   const size_t plane = (size_t)ld * ld;
-  for (int j = lane; j < ld; j += 32) {
-    double r = ldexp(xr[j], -e);
+  const double scale = ldexp(1.0, kBeta * kS - e);  // exact power of two
+  for (int j = 4 * lane; j < ld; j += 128) {
+    const double2 u = *reinterpret_cast<const double2*>(xr + j);
+    const double2 w = *reinterpret_cast<const double2*>(xr + j + 2);
+    long long R[4] = {__double2ll_rn(u.x * scale), __double2ll_rn(u.y * scale), __double2ll_rn(w.x * scale),
+                      __double2ll_rn(w.y * scale)};
+    unsigned short dg[kS][4];
 #pragma unroll
-    for (int s = 1; s <= kS; ++s) {
-      const double d = rint(ldexp(r, kBeta * s));
-      r -= ldexp(d, -kBeta * s);
-      slices[(s - 1) * plane + (size_t)row * ld + j] = __double2bfloat16(d);
+    for (int s = kS - 1; s >= 1; --s) {
+#pragma unroll
+      for (int e4 = 0; e4 < 4; ++e4) {
+        const long long d = ((R[e4] + 32) & 63) - 32;  // balanced remainder in [-32, 31]
+        R[e4] = (R[e4] - d) >> kBeta;                  // exact division by 64
+        dg[s][e4] = __bfloat16_as_ushort(__float2bfloat16_rn((float)d));
+      }
+    }
+#pragma unroll
+    for (int e4 = 0; e4 < 4; ++e4) dg[0][e4] = __bfloat16_as_ushort(__float2bfloat16_rn((float)R[e4]));
+#pragma unroll
+    for (int s = 0; s < kS; ++s) {
+      uint2 pk;
+      pk.x = (uint32_t)dg[s][0] | ((uint32_t)dg[s][1] << 16);
+      pk.y = (uint32_t)dg[s][2] | ((uint32_t)dg[s][3] << 16);
+      *reinterpret_cast<uint2*>(slices + s * plane + (size_t)row * ld + j) = pk;
     }
   }
+}
+
+// Row-major upper-triangle tile t -> (I, J), I <= J, of an nt x nt tiling.
+__device__ __forceinline__ void tri_tile(int t, int nt, int* I, int* J) {
+  int i = 0;
+  while (t >= nt - i) {
+    t -= nt - i;
+    ++i;
+  }
+  *I = i;
+  *J = i + t;
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -128,7 +167,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   __syncthreads();
   const int stop = s_dec[0], br = s_dec[1];
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->rt1[a.k] = s_t[0];
     st->rt2[a.k] = s_t[1];
     if (a.k > 0) st->idem_fro = sqrt(s_t[2]);
@@ -143,7 +182,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (stop) return;
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int m0 = blockIdx.y * kTile, n0 = blockIdx.x * kTile;
+  // X X is symmetric: CTA b computes upper-triangle tile b and also writes it
+  // transposed
+  int tI, tJ;
+  tri_tile(blockIdx.x, a.ld / kTile, &tI, &tJ);
+  const int m0 = tI * kTile, n0 = tJ * kTile;
+  const bool mirror = tI != tJ;
   const int nk = a.ld / kBK;
 
   if (threadIdx.x == 0) {
@@ -252,16 +296,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       const double* xin = Xin + (size_t)gr * a.ld + n0 + 64 * h;
       double* xout = Xout + (size_t)gr * a.ld + n0 + 64 * h;
       const int* ec = exps + n0 + 64 * h;
+      const double w = mirror ? 2.0 : 1.0;  // the transposed copy counts too
+      double u2 = 0.0, u3 = 0.0;
 #pragma unroll
       for (int j = 0; j < 64; ++j) {
         const double cxx = ldexp((double)acc64[j], er + ec[j] - kBeta * (kS + 1));
         const double x = xin[j];
         const double y = br ? 2.0 * x - cxx : cxx;
         xout[j] = y;
+        // element (gr, n0 + 64h + j) is also element (n0 + 64h + j, gr): for
+        // each j the 32 lanes write 32 consecutive values
+        if (mirror) Xout[(size_t)(n0 + 64 * h + j) * a.ld + gr] = y;
         if (gr == n0 + 64 * h + j) t1 += y;
-        t2 += y * y;
-        t3 += (cxx - x) * (cxx - x);
+        u2 += y * y;
+        u3 += (cxx - x) * (cxx - x);
       }
+      t2 = w * u2;
+      t3 = w * u3;
     }
     t1 = warp_sum(t1);
     t2 = warp_sum(t2);
@@ -281,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       y += s_red[w][1];
       z += s_red[w][2];
     }
-    const int cta = blockIdx.y * gridDim.x + blockIdx.x;
+    const int cta = blockIdx.x;
     a.parts_out[3 * cta] = x;
     a.parts_out[3 * cta + 1] = y;
     a.parts_out[3 * cta + 2] = z;
@@ -306,6 +357,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 }  // namespace
 
 int sp2_oz_max_ld() { return 4096; }
+int sp2_oz_num_parts(int ld) {
+  const int nt = ld / kTile;
+  return nt * (nt + 1) / 2;
+}
 size_t sp2_oz_slice_bytes(int ld) { return (size_t)kS * ld * ld * sizeof(__nv_bfloat16); }
 
 int sp2_oz_step(tb_ctx* ctx, const SP2StepArgs& a, const double* Xin, double* Xout, void* slices, int* exps,
@@ -324,8 +379,8 @@ int sp2_oz_step(tb_ctx* ctx, const SP2StepArgs& a, const double* Xin, double* Xo
     int rc = sp2_tc_make_map(ctx, TB_PREC_BF16, static_cast<char*>(slices) + i * plane, a.ld, &maps.m[i]);
     if (rc) return rc;
   }
-  const dim3 grid(a.ld / kTile, a.ld / kTile);
-  k_sp2_step_oz<<<grid, kThreads, kSmem, s>>>(a, maps, exps, Xin, Xout);
+  const int nt = a.ld / kTile;
+  k_sp2_step_oz<<<nt * (nt + 1) / 2, kThreads, kSmem, s>>>(a, maps, exps, Xin, Xout);
   TB_LAUNCH_CHECK(ctx);
   return TB_OK;
 }

@@ -1,23 +1,30 @@
 // Tensor-core SP2 projection (row a4): X_{k+1} = X_k^2 or 2 X_k - X_k^2
 // (Sec. III.B) as a tcgen05 GEMM on sm_103a.
 //
-// One CTA computes one 128 x 128 tile of X_k X_k (X symmetric, so both
-// operands are row blocks of X read K-major).  Warp roles (192 threads):
+// X_k is symmetric and so is X_k^2: only the nt(nt+1)/2 tiles (I <= J) of
+// the upper triangle are computed, and the epilogue writes every
+// off-diagonal tile twice, as (I, J) and transposed as (J, I).  Both
+// operands are row blocks of X read K-major.  The grid is persistent (at
+// most one CTA per SM); CTA b takes tiles b, b + G, b + 2G, ... of the
+// row-major upper triangle.  Warp roles (192 threads):
 //   warp 0   one thread issues TMA tile loads (128B swizzle) into a ring of
-//            shared-memory stages, completion tracked by mbarriers;
-//   warp 1   allocates the TMEM accumulator (128 lanes x 128 FP32 columns)
-//            and one thread issues tcgen05.mma (kind::f16 with bf16 or
-//            kind::tf32), committing each stage back to the producer;
+//            shared-memory stages that runs on across tiles, completion
+//            tracked by mbarriers;
+//   warp 1   allocates two TMEM accumulators (2 x 128 FP32 columns) and one
+//            thread issues tcgen05.mma (kind::f16 with bf16 or kind::tf32)
+//            into them alternately, so the next tile's MMAs overlap the
+//            epilogue of the previous one;
 //   warps 2-5 epilogue: tcgen05.ld the accumulator, apply the SP2 branch
 //            using the FP32 master of X_k, write the FP32 master and the
-//            bf16/tf32 operand splits of X_{k+1}, and accumulate the FP64
-//            trace partials (Tr X, ||X||_F^2, ||X^2 - X||_F^2) of the tile.
+//            operand splits of X_{k+1} (the transposed copy with one
+//            coalesced 32-lane store per column), and accumulate the FP64
+//            trace partials (Tr X, ||X||_F^2, ||X^2 - X||_F^2) per CTA.
 // Split precisions (x3) keep X ~ hi + lo in two operand arrays and
 // accumulate hi*hi + hi*lo + lo*hi in the same FP32 accumulator.
 //
 // Every mbarrier wait gives up after 2 s of %globaltimer time, records
-// TB_ERR_TIMEOUT in the SP2 state and unwinds (freeing TMEM) instead of
-// hanging.
+// TB_ERR_TIMEOUT in the SP2 state and unwinds (waiting, bounded, for its own
+// copies and MMAs, then freeing TMEM) instead of hanging.
 
 #include "common.cuh"
 #include "tc_ptx.cuh"
@@ -56,6 +63,17 @@ __global__ void __launch_bounds__(256) k_split(const float* __restrict__ X, int 
   }
 }
 
+// Row-major upper-triangle tile t -> (I, J), I <= J, of an nt x nt tiling.
+__device__ __forceinline__ void tri_tile(int t, int nt, int* I, int* J) {
+  int i = 0;
+  while (t >= nt - i) {
+    t -= nt - i;
+    ++i;
+  }
+  *I = i;
+  *J = i + t;
+}
+
 template <int P>
 __global__ void __launch_bounds__(kThreads, 1)
     k_sp2_step_tc(SP2StepArgs a, const __grid_constant__ CUtensorMap mh,
@@ -63,7 +81,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                   float* __restrict__ Xout, void* __restrict__ ohi, void* __restrict__ olo) {
   using C = Prec<P>;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[C::stages], empty[C::stages], tfull;
+  __shared__ __align__(8) uint64_t full[C::stages], empty[C::stages], tfull[2], tempty[2], mdone;
   __shared__ uint32_t tmem_base;
   __shared__ double s_t[3];
   __shared__ int s_dec[3];
@@ -98,7 +116,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   __syncthreads();
   const int stop = s_dec[0], br = s_dec[1];
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->t1[a.k] = s_t[0];
     st->t2[a.k] = s_t[1];
     if (stop) {
@@ -112,21 +130,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (stop) return;
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  // L2-aware raster: consecutive CTAs sweep a group of kGroup tile-rows
-  // column by column, so a wave of CTAs reads a compact set of row blocks of X
-  int tm, tn;
-  {
-    const int nt = gridDim.x;  // tiles per dimension (square grid)
-    const int pid = blockIdx.y * nt + blockIdx.x;
-    const int per_group = kGroup * nt;
-    const int g = pid / per_group;
-    const int first = g * kGroup;
-    const int gsize = min(kGroup, nt - first);
-    const int r = pid % per_group;
-    tm = first + r % gsize;
-    tn = r / gsize;
-  }
-  const int m0 = tm * BM, n0 = tn * BN;
+  const int nt = a.ld / BM;
+  const int ntiles = nt * (nt + 1) / 2;
   const int nk = a.ld / C::bk;
 
   if (threadIdx.x == 0) {
@@ -134,11 +139,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&tfull, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    mbar_init(&mdone, 1);
     s_abort = 0;
     fence_barrier_init();
   }
-  if (warp == 1) tmem_alloc(&tmem_base, BN);
+  if (warp == 1) tmem_alloc(&tmem_base, 2 * BN);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -148,69 +157,88 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ producer
     prefetch_map(&mh);
     if (C::split) prefetch_map(&ml);
-    int issued = 0;
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % C::stages;
-      if (kb >= C::stages && !mbar_wait(&empty[s], ((kb / C::stages) - 1) & 1, &s_abort)) break;
-      uint8_t* base = smem + s * C::stage_bytes;
-      mbar_expect_tx(&full[s], C::stage_bytes);
-      tma_load_2d(base, &mh, &full[s], kb * C::bk, m0);
-      tma_load_2d(base + TILE_BYTES, &mh, &full[s], kb * C::bk, n0);
-      if constexpr (C::split) {
-        tma_load_2d(base + 2 * TILE_BYTES, &ml, &full[s], kb * C::bk, m0);
-        tma_load_2d(base + 3 * TILE_BYTES, &ml, &full[s], kb * C::bk, n0);
+    int g = 0, issued = 0;
+    for (int t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x) {
+      int I, J;
+      tri_tile(t, nt, &I, &J);
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = g % C::stages;
+        if (g >= C::stages && !mbar_wait(&empty[s], ((g / C::stages) - 1) & 1, &s_abort)) break;
+        uint8_t* base = smem + s * C::stage_bytes;
+        mbar_expect_tx(&full[s], C::stage_bytes);
+        tma_load_2d(base, &mh, &full[s], kb * C::bk, I * BM);
+        tma_load_2d(base + TILE_BYTES, &mh, &full[s], kb * C::bk, J * BN);
+        if constexpr (C::split) {
+          tma_load_2d(base + 2 * TILE_BYTES, &ml, &full[s], kb * C::bk, I * BM);
+          tma_load_2d(base + 3 * TILE_BYTES, &ml, &full[s], kb * C::bk, J * BN);
+        }
+        issued = g + 1;
       }
-      issued = kb + 1;
     }
     if (s_abort) {
       // let every issued copy land before the CTA can exit
-      for (int kb = (issued > C::stages ? issued - C::stages : 0); kb < issued; ++kb) {
-        const int s = kb % C::stages;
+      for (int q = (issued > C::stages ? issued - C::stages : 0); q < issued; ++q) {
         const unsigned long long t0 = gtime();
-        while (!mbar_try(&full[s], (kb / C::stages) & 1) && gtime() - t0 < kWaitNs) {
+        while (!mbar_try(&full[q % C::stages], (q / C::stages) & 1) && gtime() - t0 < kWaitNs) {
         }
       }
     }
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
     constexpr uint32_t id = idesc(C::tf32 ? 2u : 1u);
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % C::stages;
-      if (!mbar_wait(&full[s], (kb / C::stages) & 1, &s_abort)) break;
+    int g = 0, it = 0;
+    for (int t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x, ++it) {
+      const int buf = it & 1;
+      if (it >= 2 && !mbar_wait(&tempty[buf], ((it >> 1) - 1) & 1, &s_abort)) break;
       tc_fence_after();
-      const uint32_t base = smem_u32(smem + s * C::stage_bytes);
+      const uint32_t d = tmem + buf * BN;
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = g % C::stages;
+        if (!mbar_wait(&full[s], (g / C::stages) & 1, &s_abort)) break;
+        tc_fence_after();
+        const uint32_t base = smem_u32(smem + s * C::stage_bytes);
 #pragma unroll
-      for (int ks = 0; ks < C::bk / C::uk; ++ks) {
-        const uint32_t koff = ks * 32;
-        const uint64_t ah = sdesc(base + koff);
-        const uint64_t bh = sdesc(base + TILE_BYTES + koff);
-        umma<C::tf32>(tmem, ah, bh, id, (kb | ks) != 0);
-        if constexpr (C::split) {
-          const uint64_t al = sdesc(base + 2 * TILE_BYTES + koff);
-          const uint64_t bl = sdesc(base + 3 * TILE_BYTES + koff);
-          umma<C::tf32>(tmem, ah, bl, id, 1u);
-          umma<C::tf32>(tmem, al, bh, id, 1u);
+        for (int ks = 0; ks < C::bk / C::uk; ++ks) {
+          const uint32_t koff = ks * 32;
+          const uint64_t ah = sdesc(base + koff);
+          const uint64_t bh = sdesc(base + TILE_BYTES + koff);
+          umma<C::tf32>(d, ah, bh, id, (kb | ks) != 0);
+          if constexpr (C::split) {
+            umma<C::tf32>(d, ah, sdesc(base + 3 * TILE_BYTES + koff), id, 1u);
+            umma<C::tf32>(d, sdesc(base + 2 * TILE_BYTES + koff), bh, id, 1u);
+          }
         }
+        umma_commit(&empty[s]);
       }
-      umma_commit(&empty[s]);
+      umma_commit(&tfull[buf]);
     }
-    umma_commit(&tfull);
+    // arrives once every MMA this thread issued has completed
+    umma_commit(&mdone);
   } else if (warp >= 2) {
     // ------------------------------------------------------------ epilogue
     double t1 = 0.0, t2 = 0.0, t3 = 0.0;
     const int q = warp & 3;
     const int row = 32 * q + lane;
-    if (mbar_wait(&tfull, 0, &s_abort)) {
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int buf = it & 1;
+      if (!mbar_wait(&tfull[buf], (it >> 1) & 1, &s_abort)) break;
       tc_fence_after();
+      int I, J;
+      tri_tile(t, nt, &I, &J);
+      const int m0 = I * BM, n0 = J * BN;
+      const bool mirror = I != J;
+      const double w = mirror ? 2.0 : 1.0;  // the transposed copy counts too
       const size_t gr = (size_t)(m0 + row);
       const float* xin = Xin + gr * a.ld + n0;
       float* xout = Xout + gr * a.ld + n0;
       char* hrow = static_cast<char*>(ohi) + (gr * a.ld + n0) * C::eb;
       char* lrow = olo ? static_cast<char*>(olo) + (gr * a.ld + n0) * C::eb : hrow;
+      double u2 = 0.0, u3 = 0.0;
 #pragma unroll 1
       for (int c = 0; c < BN / 32; ++c) {
         uint32_t v[32];
-        tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + 32 * c, v);
+        tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + buf * BN + 32 * c, v);
         float y[32];
         const float4* xi = reinterpret_cast<const float4*>(xin + 32 * c);
 #pragma unroll
@@ -218,17 +246,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           const float4 x4 = xi[j];
           const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            const float cxx = __uint_as_float(v[4 * j + t]);
-            const float x = xs[t];
+          for (int e = 0; e < 4; ++e) {
+            const float cxx = __uint_as_float(v[4 * j + e]);
+            const float x = xs[e];
             const float yy = br ? fmaf(2.0f, x, -cxx) : cxx;
-            y[4 * j + t] = yy;
-            t2 += (double)yy * (double)yy;
+            y[4 * j + e] = yy;
+            u2 += (double)yy * (double)yy;
             const double dd = (double)cxx - (double)x;
-            t3 += dd * dd;
+            u3 += dd * dd;
           }
         }
-        if (m0 == n0) {
+        if (!mirror) {
           const int dc = row - 32 * c;
           if (dc >= 0 && dc < 32) {
 #pragma unroll
@@ -240,7 +268,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int j = 0; j < 8; ++j) xo[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
         store_operands<P>(y, hrow + 32 * c * C::eb, lrow + 32 * c * C::eb);
+        if (mirror) {
+          // element (row, 32c + j) of tile (I, J) is element (32c + j, row) of
+          // tile (J, I): for each j the 32 lanes write 32 consecutive values
+          const size_t col0 = (size_t)n0 + 32 * c;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const size_t idx = (col0 + j) * a.ld + m0 + row;
+            Xout[idx] = y[j];
+            store_operand1<P>(y[j], ohi, olo ? olo : ohi, idx);
+          }
+        }
       }
+      t2 += w * u2;
+      t3 += w * u3;
+      tc_fence_before();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[buf])) : "memory");
     }
     t1 = warp_sum(t1);
     t2 = warp_sum(t2);
@@ -254,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x == 64) {
-    const int cta = blockIdx.y * gridDim.x + blockIdx.x;
+    const int cta = blockIdx.x;
     a.parts_out[3 * cta] = s_red[0][0] + s_red[1][0] + s_red[2][0] + s_red[3][0];
     a.parts_out[3 * cta + 1] = s_red[0][1] + s_red[1][1] + s_red[2][1] + s_red[3][1];
     a.parts_out[3 * cta + 2] = s_red[0][2] + s_red[1][2] + s_red[2][2] + s_red[3][2];
@@ -262,15 +305,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (warp == 1) {
     tc_fence_after();
-    if (s_abort && lane == 0) {
-      // the issuer always commits tfull after its loop: wait (bounded) until
-      // every issued MMA has retired before the accumulator is freed
+    if (lane == 0) {
+      // wait (bounded) until every issued MMA has retired before TMEM is freed
       const unsigned long long t0 = gtime();
-      while (!mbar_try(&tfull, 0) && gtime() - t0 < kWaitNs) {
+      while (!mbar_try(&mdone, 0) && gtime() - t0 < kWaitNs) {
       }
     }
     __syncwarp();
-    tmem_dealloc(tmem, BN);
+    tmem_dealloc(tmem, 2 * BN);
   }
 }
 
@@ -290,7 +332,7 @@ int launch_step(tb_ctx* ctx, const SP2StepArgs& a, const CUtensorMap* mh, const 
                                           C::smem_bytes));
     attr_set = true;
   }
-  const dim3 grid(a.ld / BN, a.ld / BM);
+  const int grid = sp2_tc_num_parts(ctx, a.ld);
   k_sp2_step_tc<P><<<grid, kThreads, C::smem_bytes, s>>>(a, *mh, *ml, Xin, Xout, ohi, olo);
   TB_LAUNCH_CHECK(ctx);
   return TB_OK;
@@ -300,6 +342,10 @@ int launch_step(tb_ctx* ctx, const SP2StepArgs& a, const CUtensorMap* mh, const 
 
 int sp2_tc_tile() { return BM; }
 int sp2_tc_num_tiles(int ld) { return (ld / BM) * (ld / BN); }
+int sp2_tc_num_parts(const tb_ctx* ctx, int ld) {
+  const int nt = ld / BM;
+  return std::max(1, std::min(nt * (nt + 1) / 2, ctx->sm_count));
+}
 size_t sp2_tc_operand_bytes(int precision) {
   return (precision == TB_PREC_TF32 || precision == TB_PREC_TF32X3) ? 4 : 2;
 }

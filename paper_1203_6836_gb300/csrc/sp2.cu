@@ -519,7 +519,7 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
     int rc = sp2_tc_step(ctx, o->precision, c, nullptr, nullptr, M[0], M[0], Hi[0], Lo[0], s);
     if (rc) return rc;
   }
-  const int ntc = sp2_tc_num_tiles(ld);
+  const int ntc = sp2_tc_num_parts(ctx, ld);
   tb_prof_mark(ctx, 0, 0, s);
   for (int k = 0; k <= o->max_iter; ++k) {
     a.k = k;
@@ -546,7 +546,7 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
   r.max_iter = refine;
   r.tol = o->tol;
   const dim3 g(ld / kF64Tile, ld / kF64Tile);
-  const int np_ref = L.oz ? sp2_tc_num_tiles(ld) : (int)(g.x * g.y);
+  const int np_ref = L.oz ? sp2_oz_num_parts(ld) : (int)(g.x * g.y);
   tb_prof_mark(ctx, 1, 0, s);
   for (int k = 0; k <= refine; ++k) {
     r.k = k;

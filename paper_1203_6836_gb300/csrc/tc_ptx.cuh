@@ -191,4 +191,19 @@ __device__ __forceinline__ void store_operands(const float (&y)[32], void* hi_ro
   }
 }
 
+// Operand split of one FP32 value into hi (and lo) at element index idx.
+template <int P>
+__device__ __forceinline__ void store_operand1(float y, void* hi, void* lo, size_t idx) {
+  if constexpr (Prec<P>::tf32) {
+    const float hv = to_tf32(y);
+    reinterpret_cast<uint32_t*>(hi)[idx] = __float_as_uint(hv);
+    if constexpr (Prec<P>::split) reinterpret_cast<uint32_t*>(lo)[idx] = __float_as_uint(to_tf32(y - hv));
+  } else {
+    const __nv_bfloat16 h = __float2bfloat16_rn(y);
+    reinterpret_cast<unsigned short*>(hi)[idx] = __bfloat16_as_ushort(h);
+    if constexpr (Prec<P>::split)
+      reinterpret_cast<unsigned short*>(lo)[idx] = __bfloat16_as_ushort(__float2bfloat16_rn(y - __bfloat162float(h)));
+  }
+}
+
 }  // namespace tcx
