@@ -755,7 +755,7 @@ def run_serving(args):
     xp = xl_params(XL.dt, XL.kappa, XL.alpha, XL.c)
     sizes, arrivals, which = serving_trajectories(n_requests=args.requests)
     fo = fermi_opts(args.precision)
-    sv = Server(ctx, TP, xp, kT=0.1, max_slots=32, fermi=fo, scf_tol=1e-5, scf_max_iter=20)
+    sv = Server(ctx, TP, xp, kT=0.1, max_slots=32, fermi=fo, scf_tol=1e-6, scf_max_iter=100)
     systems = []
     t0 = time.perf_counter()
     for i, N in enumerate(sizes):

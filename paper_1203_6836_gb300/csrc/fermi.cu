@@ -15,10 +15,12 @@
 //                                                   spectrum in [1, 2])
 //   Z = A^-1: Z1 = 4/3 I - 4/9 A, then Newton-Schulz Z <- Z (2I - A Z)
 //   E <- 2 E Z                                     (one product)
-//   E <- (E + E^T)/2                               (rounding breaks the exact
-//                                                   commutation of the factors)
 // All factors are functions of H, hence symmetric and commuting, so every
-// product is a tensor-core GEMM with the second operand read by rows.
+// product is a tensor-core GEMM with the second operand read by rows, and
+// its result is symmetric: the product kernel computes the upper-triangle
+// tiles and mirrors them, so every iterate is exactly symmetric (rounding
+// errors would otherwise leave an antisymmetric part that the doubling
+// steps amplify).
 // D = I/2 + E on the n x n block.
 // The chemical potential: safeguarded Newton steps on Tr D(mu) = N_occ with
 // dTr D/dmu = beta Tr[D(I - D)] inside a bisection bracket, one full
@@ -92,36 +94,6 @@ __global__ void __launch_bounds__(256) k_foe_z1(const FoeState* st, int n, int l
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / ld), col = (int)(e % ld);
     Z[e] = (r == col && r < n ? (4.0f / 3.0f) : 0.0f) - (4.0f / 9.0f) * A[e];
-  }
-}
-
-// X <- (X + X^T)/2 in place, 32 x 32 tile pairs through shared memory.  The
-// factors commute only up to rounding, so every product P Q^T of the
-// tensor-core kernel leaves an antisymmetric error that the doubling steps
-// would amplify; the symmetric part is the exact-arithmetic value.  Also
-// refreshes the trace partials (Tr X, ||X||_F^2) when parts != nullptr.
-__global__ void __launch_bounds__(256) k_foe_sym(const FoeState* st, int ld, float* __restrict__ X,
-                                                 double* __restrict__ parts) {
-  __shared__ float a[32][33], b[32][33];
-  if (st->done || st->err) return;
-  const int nt = ld / 32;
-  // blockIdx.x enumerates tile pairs (I <= J) row by row
-  int p = blockIdx.x, I = 0;
-  while (p >= nt - I) {
-    p -= nt - I;
-    ++I;
-  }
-  const int J = I + p;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-  for (int r = ty; r < 32; r += 8) {
-    a[r][tx] = X[(size_t)(32 * I + r) * ld + 32 * J + tx];
-    b[r][tx] = X[(size_t)(32 * J + r) * ld + 32 * I + tx];
-  }
-  __syncthreads();
-  for (int r = ty; r < 32; r += 8) {
-    const float v = 0.5f * (a[r][tx] + b[tx][r]);
-    X[(size_t)(32 * I + r) * ld + 32 * J + tx] = v;
-    X[(size_t)(32 * J + tx) * ld + 32 * I + r] = v;
   }
 }
 
@@ -323,8 +295,6 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
     g.err = errp;
     return tc_gemm(ctx, o->precision, g, &A.mh, &A.ml, &B.mh, &B.ml, ls);
   };
-  const int ntile = L.ld / 32;
-  const int ntp = ntile * (ntile + 1) / 2;
   auto expansion = [&]() -> int {
     int r;
     Mat* X = &M[0];
@@ -347,16 +317,14 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
         if ((r = gemm(*Z, *T, *Y, 1.0f, 0.0f, nullptr, 0.0f, nullptr))) return r;   // Z <- Z T
         std::swap(Z, Y);
       }
-      // E <- 2 E Z (trace partials of the last step), then its symmetric
-      // part and fresh operand splits
+      // E <- 2 E Z (trace partials of the last step); the product kernel
+      // writes exactly symmetric results with their operand splits
       const bool last = step == m - 1;
       if ((r = gemm(*X, *Z, *Y, 2.0f, 0.0f, nullptr, 0.0f, last ? parts : nullptr))) return r;
       std::swap(X, Y);
-      k_foe_sym<<<ntp, 256, 0, ls>>>(st, L.ld, X->m, nullptr);
-      TB_LAUNCH_CHECK(ctx);
-      if (!last && (r = tc_split(ctx, o->precision, X->m, nn, X->hi, X->lo, skip, ls))) return r;
     }
-    k_foe_mu<<<1, 32, 0, ls>>>(st, parts, L.nparts, n, nocc, beta, tol, o->mu_iters, loop.handle, loop.graph);
+    k_foe_mu<<<1, 32, 0, ls>>>(st, parts, sp2_tc_num_parts(ctx, L.ld), n, nocc, beta, tol, o->mu_iters,
+                               loop.handle, loop.graph);
     TB_LAUNCH_CHECK(ctx);
     k_foe_keep<<<1184, 256, 0, ls>>>(st, nn, X->m, res);
     TB_LAUNCH_CHECK(ctx);

@@ -38,7 +38,6 @@ using namespace tcx;
 constexpr int BM = 128, BN = 128;
 constexpr int TILE_BYTES = 128 * 128;  // 128 rows x 128 bytes
 constexpr int kThreads = 192;
-constexpr int kGroup = 8;  // tile-rows swept together (L2 locality)
 
 
 // X0 (FP32 master) -> operand arrays, elementwise.
@@ -383,10 +382,13 @@ int sp2_tc_step(tb_ctx* ctx, int precision, const SP2StepArgs& a, const CUtensor
 // the same H) for the Fermi-operator expansion:
 //   out = alpha * (A B) + beta * E + gamma * I
 // with A, B given as tensor-core operand splits (B symmetric, so its rows are
-// read K-major), E an optional FP32 matrix.  Writes the FP32 master and the
-// operand splits of `out` and FP64 partials (Tr out, ||out||_F^2).  Returns
-// at once when *skip is non-zero (device-side early exit of a converged
-// outer iteration).
+// read K-major), E an optional symmetric FP32 matrix.  A B is then symmetric:
+// like the SP2 projection, a persistent grid computes the upper-triangle
+// tiles into two alternating TMEM accumulators and writes each off-diagonal
+// tile also transposed, so `out` is exactly symmetric.  Writes the FP32
+// master and the operand splits of `out` and per-CTA FP64 partials
+// (Tr out, ||out||_F^2).  Returns at once when *skip is non-zero
+// (device-side early exit of a converged outer iteration).
 // --------------------------------------------------------------------------
 
 namespace {
@@ -397,37 +399,30 @@ __global__ void __launch_bounds__(kThreads, 1)
               const __grid_constant__ CUtensorMap bh, const __grid_constant__ CUtensorMap bl) {
   using C = Prec<P>;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[C::stages], empty[C::stages], tfull;
+  __shared__ __align__(8) uint64_t full[C::stages], empty[C::stages], tfull[2], tempty[2], mdone;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_abort;
   __shared__ double s_red[4][2];
   if (g.skip && *g.skip) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  int tm, tn;
-  {
-    const int nt = gridDim.x;
-    const int pid = blockIdx.y * nt + blockIdx.x;
-    const int per_group = kGroup * nt;
-    const int gi = pid / per_group;
-    const int first = gi * kGroup;
-    const int gsize = min(kGroup, nt - first);
-    const int r = pid % per_group;
-    tm = first + r % gsize;
-    tn = r / gsize;
-  }
-  const int m0 = tm * BM, n0 = tn * BN;
+  const int nt = g.ld / BM;
+  const int ntiles = nt * (nt + 1) / 2;
   const int nk = g.ld / C::bk;
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&tfull, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    mbar_init(&mdone, 1);
     s_abort = 0;
     fence_barrier_init();
   }
-  if (warp == 1) tmem_alloc(&tmem_base, BN);
+  if (warp == 1) tmem_alloc(&tmem_base, 2 * BN);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -435,62 +430,83 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0 && lane == 0) {
     prefetch_map(&ah);
     prefetch_map(&bh);
-    int issued = 0;
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % C::stages;
-      if (kb >= C::stages && !mbar_wait(&empty[s], ((kb / C::stages) - 1) & 1, &s_abort)) break;
-      uint8_t* base = smem + s * C::stage_bytes;
-      mbar_expect_tx(&full[s], C::stage_bytes);
-      tma_load_2d(base, &ah, &full[s], kb * C::bk, m0);
-      tma_load_2d(base + TILE_BYTES, &bh, &full[s], kb * C::bk, n0);
-      if constexpr (C::split) {
-        tma_load_2d(base + 2 * TILE_BYTES, &al, &full[s], kb * C::bk, m0);
-        tma_load_2d(base + 3 * TILE_BYTES, &bl, &full[s], kb * C::bk, n0);
+    int gk = 0, issued = 0;
+    for (int t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x) {
+      int I, J;
+      tri_tile(t, nt, &I, &J);
+      for (int kb = 0; kb < nk; ++kb, ++gk) {
+        const int s = gk % C::stages;
+        if (gk >= C::stages && !mbar_wait(&empty[s], ((gk / C::stages) - 1) & 1, &s_abort)) break;
+        uint8_t* base = smem + s * C::stage_bytes;
+        mbar_expect_tx(&full[s], C::stage_bytes);
+        tma_load_2d(base, &ah, &full[s], kb * C::bk, I * BM);
+        tma_load_2d(base + TILE_BYTES, &bh, &full[s], kb * C::bk, J * BN);
+        if constexpr (C::split) {
+          tma_load_2d(base + 2 * TILE_BYTES, &al, &full[s], kb * C::bk, I * BM);
+          tma_load_2d(base + 3 * TILE_BYTES, &bl, &full[s], kb * C::bk, J * BN);
+        }
+        issued = gk + 1;
       }
-      issued = kb + 1;
     }
     if (s_abort) {
-      for (int kb = (issued > C::stages ? issued - C::stages : 0); kb < issued; ++kb) {
+      for (int q = (issued > C::stages ? issued - C::stages : 0); q < issued; ++q) {
         const unsigned long long t0 = gtime();
-        while (!mbar_try(&full[kb % C::stages], (kb / C::stages) & 1) && gtime() - t0 < kWaitNs) {
+        while (!mbar_try(&full[q % C::stages], (q / C::stages) & 1) && gtime() - t0 < kWaitNs) {
         }
       }
     }
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t id = idesc(C::tf32 ? 2u : 1u);
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % C::stages;
-      if (!mbar_wait(&full[s], (kb / C::stages) & 1, &s_abort)) break;
+    int gk = 0, it = 0;
+    for (int t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x, ++it) {
+      const int buf = it & 1;
+      if (it >= 2 && !mbar_wait(&tempty[buf], ((it >> 1) - 1) & 1, &s_abort)) break;
       tc_fence_after();
-      const uint32_t base = smem_u32(smem + s * C::stage_bytes);
+      const uint32_t d = tmem + buf * BN;
+      for (int kb = 0; kb < nk; ++kb, ++gk) {
+        const int s = gk % C::stages;
+        if (!mbar_wait(&full[s], (gk / C::stages) & 1, &s_abort)) break;
+        tc_fence_after();
+        const uint32_t base = smem_u32(smem + s * C::stage_bytes);
 #pragma unroll
-      for (int ks = 0; ks < C::bk / C::uk; ++ks) {
-        const uint32_t koff = ks * 32;
-        const uint64_t a0 = sdesc(base + koff), b0 = sdesc(base + TILE_BYTES + koff);
-        umma<C::tf32>(tmem, a0, b0, id, (kb | ks) != 0);
-        if constexpr (C::split) {
-          umma<C::tf32>(tmem, a0, sdesc(base + 3 * TILE_BYTES + koff), id, 1u);
-          umma<C::tf32>(tmem, sdesc(base + 2 * TILE_BYTES + koff), b0, id, 1u);
+        for (int ks = 0; ks < C::bk / C::uk; ++ks) {
+          const uint32_t koff = ks * 32;
+          const uint64_t a0 = sdesc(base + koff), b0 = sdesc(base + TILE_BYTES + koff);
+          umma<C::tf32>(d, a0, b0, id, (kb | ks) != 0);
+          if constexpr (C::split) {
+            umma<C::tf32>(d, a0, sdesc(base + 3 * TILE_BYTES + koff), id, 1u);
+            umma<C::tf32>(d, sdesc(base + 2 * TILE_BYTES + koff), b0, id, 1u);
+          }
         }
+        umma_commit(&empty[s]);
       }
-      umma_commit(&empty[s]);
+      umma_commit(&tfull[buf]);
     }
-    umma_commit(&tfull);
+    // arrives once every MMA this thread issued has completed
+    umma_commit(&mdone);
   } else if (warp >= 2) {
     double t1 = 0.0, t2 = 0.0;
     const int q = warp & 3;
     const int row = 32 * q + lane;
-    if (mbar_wait(&tfull, 0, &s_abort)) {
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int buf = it & 1;
+      if (!mbar_wait(&tfull[buf], (it >> 1) & 1, &s_abort)) break;
       tc_fence_after();
+      int I, J;
+      tri_tile(t, nt, &I, &J);
+      const int m0 = I * BM, n0 = J * BN;
+      const bool mirror = I != J;
       const size_t gr = (size_t)(m0 + row);
       const float* erow = g.E ? g.E + gr * g.ld + n0 : nullptr;
       float* orow = g.out + gr * g.ld + n0;
       char* hrow = static_cast<char*>(g.ohi) + (gr * g.ld + n0) * C::eb;
       char* lrow = g.olo ? static_cast<char*>(g.olo) + (gr * g.ld + n0) * C::eb : hrow;
+      double u2 = 0.0, u3 = 0.0, lower = 0.0;
 #pragma unroll 1
       for (int c = 0; c < BN / 32; ++c) {
         uint32_t v[32];
-        tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + 32 * c, v);
+        tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + buf * BN + 32 * c, v);
         float y[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
@@ -499,14 +515,45 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (erow) val = fmaf(g.beta, erow[32 * c + j], val);
           if (col == (int)gr && (int)gr < g.n) val += g.gamma;
           y[j] = val;
-          t2 += (double)val * (double)val;
+          u2 += (double)val * (double)val;
+          if (col < (int)gr) lower += (double)val * (double)val;
           if (col == (int)gr) t1 += (double)val;
         }
-        float4* xo = reinterpret_cast<float4*>(orow + 32 * c);
+        const size_t col0 = (size_t)n0 + 32 * c;
+        if (mirror) {
+          float4* xo = reinterpret_cast<float4*>(orow + 32 * c);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) xo[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
-        store_operands<P>(y, hrow + 32 * c * C::eb, lrow + 32 * c * C::eb);
+          for (int j = 0; j < 8; ++j) xo[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
+          store_operands<P>(y, hrow + 32 * c * C::eb, lrow + 32 * c * C::eb);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const size_t idx = (col0 + j) * g.ld + gr;
+            g.out[idx] = y[j];
+            store_operand1<P>(y[j], g.ohi, g.olo ? g.olo : g.ohi, idx);
+          }
+        } else {
+          // diagonal tile: its upper triangle (col >= row) is kept and
+          // mirrored, so the tile is exactly symmetric too
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const size_t col = col0 + j;
+            if (col < gr) continue;
+            const size_t idx = gr * g.ld + col, tdx = col * g.ld + gr;
+            g.out[idx] = y[j];
+            store_operand1<P>(y[j], g.ohi, g.olo ? g.olo : g.ohi, idx);
+            if (col > gr) {
+              g.out[tdx] = y[j];
+              store_operand1<P>(y[j], g.ohi, g.olo ? g.olo : g.ohi, tdx);
+              u3 += (double)y[j] * (double)y[j];
+            }
+          }
+        }
       }
+      // off-diagonal tiles count twice; in a diagonal tile the kept upper
+      // triangle counts twice off the diagonal (u3) and the lower one not at all
+      t2 += mirror ? 2.0 * u2 : u2 + u3 - lower;
+      tc_fence_before();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[buf])) : "memory");
     }
     t1 = warp_sum(t1);
     t2 = warp_sum(t2);
@@ -519,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (threadIdx.x == 64) {
     if (g.parts) {
-      const int cta = blockIdx.y * gridDim.x + blockIdx.x;
+      const int cta = blockIdx.x;
       g.parts[2 * cta] = s_red[0][0] + s_red[1][0] + s_red[2][0] + s_red[3][0];
       g.parts[2 * cta + 1] = s_red[0][1] + s_red[1][1] + s_red[2][1] + s_red[3][1];
     }
@@ -527,13 +574,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (warp == 1) {
     tc_fence_after();
-    if (s_abort && lane == 0) {
+    if (lane == 0) {
+      // wait (bounded) until every issued MMA has retired before TMEM is freed
       const unsigned long long t0 = gtime();
-      while (!mbar_try(&tfull, 0) && gtime() - t0 < kWaitNs) {
+      while (!mbar_try(&mdone, 0) && gtime() - t0 < kWaitNs) {
       }
     }
     __syncwarp();
-    tmem_dealloc(tmem, BN);
+    tmem_dealloc(tmem, 2 * BN);
   }
 }
 
@@ -546,8 +594,7 @@ int launch_gemm(tb_ctx* ctx, const GemmArgs& g, const CUtensorMap* ah, const CUt
     TB_CUDA_TRY(ctx, cudaFuncSetAttribute(k_gemm_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes));
     attr_set = true;
   }
-  const dim3 grid(g.ld / BN, g.ld / BM);
-  k_gemm_tc<P><<<grid, kThreads, C::smem_bytes, s>>>(g, *ah, *al, *bh, *bl);
+  k_gemm_tc<P><<<sp2_tc_num_parts(ctx, g.ld), kThreads, C::smem_bytes, s>>>(g, *ah, *al, *bh, *bl);
   TB_LAUNCH_CHECK(ctx);
   return TB_OK;
 }
