@@ -493,7 +493,9 @@ extern "C" int tb_forces(tb_ctx* ctx, const tb_params* p, const tb_system* sys, 
   cudaStream_t s = as_stream(stream);
   TB_CUDA_TRY(ctx, cudaMemsetAsync(energy, 0, 4 * sizeof(double), s));
   const int N = sys->natoms;
-  k_forces<<<(N * 32 + 255) / 256, 256, 0, s>>>(m, N, sys->types, sys->orb_off, R, D, sys->norb, q,
+  // one warp per atom, one warp per block: FP64 runs at ~8 GFLOP/s per SM on
+  // GB300, so small systems spread their atoms over as many SMs as possible
+  k_forces<<<N, 32, 0, s>>>(m, N, sys->types, sys->orb_off, R, D, sys->norb, q,
                                                   n_aux, gamma, F, energy);
   TB_LAUNCH_CHECK(ctx);
   return TB_OK;

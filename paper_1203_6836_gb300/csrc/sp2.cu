@@ -23,11 +23,16 @@
 
 namespace {
 
-constexpr int kF64Tile = 64;     // FP64 GEMM output tile
+constexpr int kF64Tile = 64;     // FP64 GEMM output tile (padding unit of the FP64 path)
 constexpr int kF64K = 16;        // FP64 GEMM k-step
 constexpr int kInitTile = 64;    // X0 / conversion tile
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Output tile of the FP64 projection: GB300 runs FP64 at ~8 GFLOP/s per SM,
+// so small matrices are cut into 16 x 16 tiles to spread one product over
+// many SMs; from ld = 576 on, 64 x 64 tiles give enough CTAs.
+inline int f64_tile(int ld) { return ld <= 512 ? 16 : kF64Tile; }
 
 struct Layout {
   int n, ld, prec;
@@ -43,7 +48,7 @@ Layout make_layout(int n, int prec, int refine, int refine_mode = 1) {
   L.prec = prec;
   const bool tc = prec != TB_PREC_FP64;
   L.ld = round_up(std::max(n, 1), tc ? sp2_tc_tile() : kF64Tile);
-  const int t_f64 = (L.ld / kF64Tile) * (L.ld / kF64Tile);
+  const int t_f64 = (L.ld / f64_tile(L.ld)) * (L.ld / f64_tile(L.ld));
   const int t_init = (L.ld / kInitTile) * (L.ld / kInitTile);
   const int t_tc = tc ? sp2_tc_num_tiles(L.ld) : 0;
   L.max_parts = std::max(std::max(t_f64, t_init), t_tc);
@@ -194,10 +199,13 @@ __global__ void __launch_bounds__(256) k_init_x(const double* __restrict__ H, in
 // X_out = X_in^2 or 2 X_in - X_in^2 for one 64x64 output tile; 256 threads,
 // each 4x4 outputs at rows ty + 16i, cols tx + 16j; k-step 16 through shared
 // memory.  X is symmetric, so B = X is read row-major like A.
+// T x T output tile per CTA, 16 x 16 threads, (T/16)^2 outputs per thread.
+template <int T>
 __global__ void __launch_bounds__(256) k_sp2_step_f64(SP2StepArgs a, const double* __restrict__ X,
                                                       double* __restrict__ Y) {
-  __shared__ double As[kF64K][kF64Tile + 1];
-  __shared__ double Bs[kF64K][kF64Tile + 1];
+  constexpr int R = T / 16;
+  __shared__ double As[kF64K][T + 1];
+  __shared__ double Bs[kF64K][T + 1];
   __shared__ double s_t[3];
   __shared__ int s_dec[3];
   SP2State* st = a.st;
@@ -259,41 +267,41 @@ __global__ void __launch_bounds__(256) k_sp2_step_f64(SP2StepArgs a, const doubl
   if (stop) return;
 
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int row0 = blockIdx.y * kF64Tile, col0 = blockIdx.x * kF64Tile;
+  const int row0 = blockIdx.y * T, col0 = blockIdx.x * T;
   const int ld = a.ld;
-  double acc[4][4];
+  double acc[R][R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < R; ++j) acc[i][j] = 0.0;
   for (int k0 = 0; k0 < ld; k0 += kF64K) {
-    // 64 rows x 16 k of A (rows of X) and 16 k x 64 cols of B (rows of X)
-    for (int e = threadIdx.x; e < kF64Tile * kF64K; e += 256) {
+    // T rows x 16 k of A (rows of X) and 16 k x T cols of B (rows of X)
+    for (int e = threadIdx.x; e < T * kF64K; e += 256) {
       const int r = e / kF64K, kk = e % kF64K;
       As[kk][r] = X[(size_t)(row0 + r) * ld + k0 + kk];
-      const int kb = e / kF64Tile, c = e % kF64Tile;
+      const int kb = e / T, c = e % T;
       Bs[kb][c] = X[(size_t)(k0 + kb) * ld + col0 + c];
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kF64K; ++kk) {
-      double av[4], bv[4];
+      double av[R], bv[R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < R; ++i) av[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < R; ++j) bv[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        for (int j = 0; j < R; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
     }
     __syncthreads();
   }
   double t1 = 0.0, t2 = 0.0, t3 = 0.0;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < R; ++j) {
       const int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
       const double x = X[(size_t)r * ld + c];
       const double cxx = acc[i][j];
@@ -304,6 +312,11 @@ __global__ void __launch_bounds__(256) k_sp2_step_f64(SP2StepArgs a, const doubl
       t3 += (cxx - x) * (cxx - x);
     }
   block_sum3(t1, t2, t3, a.parts_out + 3 * (blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+void launch_f64(dim3 g, const SP2StepArgs& a, const double* X, double* Y, cudaStream_t s) {
+  if (f64_tile(a.ld) == 16) k_sp2_step_f64<16><<<g, 256, 0, s>>>(a, X, Y);
+  else k_sp2_step_f64<kF64Tile><<<g, 256, 0, s>>>(a, X, Y);
 }
 
 // FP32 master (buffer chosen by the main phase's iteration count) -> FP64,
@@ -472,14 +485,14 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
     a.tol = o->tol;
     a.max_iter = o->max_iter;
     a.phase = 0;
-    const dim3 g(ld / kF64Tile, ld / kF64Tile);
+    const dim3 g(ld / f64_tile(ld), ld / f64_tile(ld));
     tb_prof_mark(ctx, 0, 0, s);
     for (int k = 0; k <= o->max_iter; ++k) {
       a.k = k;
       a.nparts_in = k == 0 ? np_init : (int)(g.x * g.y);
       a.parts_in = slot[k & 1];
       a.parts_out = slot[(k + 1) & 1];
-      k_sp2_step_f64<<<g, 256, 0, s>>>(a, (k & 1) ? F1 : F0, (k & 1) ? F0 : F1);
+      launch_f64(g, a, (k & 1) ? F1 : F0, (k & 1) ? F0 : F1, s);
       TB_LAUNCH_CHECK(ctx);
       tb_prof_mark(ctx, 0, k + 1, s);
     }
@@ -545,7 +558,7 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
   r.phase = 1;
   r.max_iter = refine;
   r.tol = o->tol;
-  const dim3 g(ld / kF64Tile, ld / kF64Tile);
+  const dim3 g(ld / f64_tile(ld), ld / f64_tile(ld));
   const int np_ref = L.oz ? sp2_oz_num_parts(ld) : (int)(g.x * g.y);
   tb_prof_mark(ctx, 1, 0, s);
   for (int k = 0; k <= refine; ++k) {
@@ -560,7 +573,7 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
       if (rc) return rc;
     } else {
       // FP64 FMA projection (or, at k = refine, only the final decision)
-      k_sp2_step_f64<<<g, 256, 0, s>>>(r, Fin, Fout);
+      launch_f64(g, r, Fin, Fout, s);
       TB_LAUNCH_CHECK(ctx);
     }
     tb_prof_mark(ctx, 1, k + 1, s);
