@@ -116,8 +116,10 @@ typedef struct {
   double idem_fro;      /* ||X^2 - X||_F of the input of the last FP64 projection, -1 if none */
   uint64_t branch_bits[2];  /* bit k: branch of main-phase projection k (1 = 2X - X^2) */
   uint64_t refine_bits;     /* bit k: branch of refinement projection k */
-  int64_t block_products;   /* block-sparse path: 128 x 128 block products executed over all
-                               projections (2 * 128^3 flops each); 0 on the dense paths */
+  int64_t block_products;   /* block-sparse path: 128 x 128 block products of the full products
+                               X X over all projections (2 * 128^3 flops each; the kernel
+                               computes the upper-triangle blocks, about half, and mirrors
+                               them); 0 on the dense paths */
   int64_t blocks;           /* block-sparse path: stored 128 x 128 blocks of the returned D; else 0 */
 } tb_sp2_report;
 

@@ -328,7 +328,8 @@ __global__ void k_bsr_fill_out(Args a, Buf bo, Buf bn, Sym sy) {
     sy.old_idx[o] = ((si[J >> 5] >> (J & 31)) & 1u) ? bo.row_ptr[I] + popc_below(si, J) : -1;
     int pc = 0;
     const uint32_t* lj = bo.live + J * MW;
-    for (int w = 0; w < MW; ++w) pc += __popc(li[w] & lj[w]);
+    if (J >= I)  // X^2 is symmetric: blocks below the diagonal are written as mirrors
+      for (int w = 0; w < MW; ++w) pc += __popc(li[w] & lj[w]);
     sy.pcnt[o] = pc;
   }
 }
@@ -370,11 +371,14 @@ __global__ void k_bsr_pairs(Args a, Buf bo, Buf bn, Sym sy) {
   const int nb = sy.scal[0];
   for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < nb; o += gridDim.x * blockDim.x) {
     const int I = sy.out_row[o], J = bn.col[o];
+    if (J < I) continue;
     const uint32_t* li = bo.live + I * MW;
     const uint32_t* lj = bo.live + J * MW;
     const uint32_t* si = bo.stored + I * MW;
     const uint32_t* sj = bo.stored + J * MW;
     int p = sy.pair_ptr[o];
+    // the mirrored block (J, I) of the full product has as many block products
+    if (J > I) atomicAdd(&a.st->block_products, (unsigned long long)sy.pcnt[o]);
     for (int w = 0; w < MW; ++w) {
       uint32_t m = li[w] & lj[w];
       while (m) {
@@ -393,7 +397,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                   Buf bo, Buf bn, Sym sy) {
   using C = Prec<P>;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[C::stages], empty[C::stages], tfull[2], tempty[2];
+  __shared__ __align__(8) uint64_t full[C::stages], empty[C::stages], tfull[2], tempty[2], mdone;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_abort;
   __shared__ double s_red[4][3];
@@ -412,6 +416,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], 4);
     }
+    mbar_init(&mdone, 1);
     s_abort = 0;
     fence_barrier_init();
   }
@@ -427,6 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (C::split) prefetch_map(&ml);
     int g = 0, issued = 0;
     for (int o = blockIdx.x; o < nb && !s_abort; o += gridDim.x) {
+      if (bn.col[o] < sy.out_row[o]) continue;  // mirror of an upper block
       const int p0 = sy.pair_ptr[o], p1 = sy.pair_ptr[o + 1];
       for (int p = p0; p < p1 && !s_abort; ++p) {
         const int2 pr = sy.pairs[p];
@@ -455,7 +461,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t id = idesc(C::tf32 ? 2u : 1u);
     int g = 0, it = 0;
-    for (int o = blockIdx.x; o < nb && !s_abort; o += gridDim.x, ++it) {
+    for (int o = blockIdx.x; o < nb && !s_abort; o += gridDim.x) {
+      if (bn.col[o] < sy.out_row[o]) continue;
       const int buf = it & 1;
       if (it >= 2 && !mbar_wait(&tempty[buf], ((it >> 1) - 1) & 1, &s_abort)) break;
       tc_fence_after();
@@ -483,18 +490,27 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       umma_commit(&tfull[buf]);
+      ++it;
     }
+    // arrives once every MMA this thread issued has completed
+    umma_commit(&mdone);
   } else if (warp >= 2) {
     const int q = warp & 3;
     const int row = 32 * q + lane;
     double t1 = 0.0, t2 = 0.0;
     int it = 0;
-    for (int o = blockIdx.x; o < nb; o += gridDim.x, ++it) {
+    for (int o = blockIdx.x; o < nb; o += gridDim.x) {
+      if (bn.col[o] < sy.out_row[o]) continue;
       const int buf = it & 1;
-      if (!mbar_wait(&tfull[buf], (it >> 1) & 1, &s_abort)) break;
+      ++it;
+      if (!mbar_wait(&tfull[buf], ((it - 1) >> 1) & 1, &s_abort)) break;
       tc_fence_after();
       const bool has = sy.pair_ptr[o + 1] > sy.pair_ptr[o];
       const int I = sy.out_row[o], J = bn.col[o];
+      const bool mirror = J > I;
+      // slot of the transposed block (J, I) in the new pattern
+      const int om = mirror ? bn.row_ptr[J] + popc_below(sy.cand + J * MW, I) : o;
+      float* xmir = bn.val + (size_t)om * kTiles;
       const int oi = sy.old_idx[o];
       const float* xold = oi >= 0 ? bo.val + (size_t)oi * kTiles + (size_t)row * SB : nullptr;
       float* xnew = bn.val + (size_t)o * kTiles + (size_t)row * SB;
@@ -527,21 +543,36 @@ __global__ void __launch_bounds__(kThreads, 1)
         } else {
           kept = 1;
         }
+        double u2 = 0.0;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          t2 += (double)y[j] * (double)y[j];
+          u2 += (double)y[j] * (double)y[j];
           if (I == J && row == 32 * c + j) t1 += (double)y[j];
         }
+        t2 += mirror ? 2.0 * u2 : u2;
         float4* xo = reinterpret_cast<float4*>(xnew + 32 * c);
 #pragma unroll
         for (int j = 0; j < 8; ++j) xo[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
         store_operands<P>(y, hrow + 32 * c * C::eb, lrow + 32 * c * C::eb);
+        if (mirror) {
+          // element (row, 32c + j) of block (I, J) is element (32c + j, row) of
+          // block (J, I): for each j the 32 lanes write 32 consecutive values
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const size_t e = (size_t)(32 * c + j) * SB + row;
+            xmir[e] = y[j];
+            store_operand1<P>(y[j], bn.hi, bn.lo ? bn.lo : bn.hi, (size_t)om * kTiles + e);
+          }
+        }
       }
       tc_fence_before();
       if (lane == 0) {
         // the block is live when any of its 32-row bands kept a sub-block
         // (nz[o] was zeroed when the output pattern was built)
-        if (kept) atomicOr(&bn.nz[o], 1);
+        if (kept) {
+          atomicOr(&bn.nz[o], 1);
+          if (mirror) atomicOr(&bn.nz[om], 1);
+        }
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[buf])) : "memory");
       }
     }
@@ -562,11 +593,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (warp == 1) {
     tc_fence_after();
-    if (s_abort && lane == 0) {
-      for (int b = 0; b < 2; ++b) {
-        const unsigned long long t0 = gtime();
-        while (!mbar_try(&tfull[b], 0) && gtime() - t0 < kWaitNs) {
-        }
+    if (lane == 0) {
+      // wait (bounded) until every issued MMA has retired before TMEM is freed
+      const unsigned long long t0 = gtime();
+      while (!mbar_try(&mdone, 0) && gtime() - t0 < kWaitNs) {
       }
     }
     __syncwarp();

@@ -6,7 +6,9 @@
 // Gershgorin bounds, X0, then the projections X <- X^2 or 2X - X^2 as tcgen05
 // tiles (TMA -> shared memory -> TMEM, warp-specialised as in the dense
 // kernel), the FP64 trace reductions and the stop/branch decisions (all in
-// the CTA), and finally D.  Between two projections the CTA synchronises and
+// the CTA), and finally D.  With square tiles (BN = 128) only the upper
+// triangle of the symmetric X^2 is computed and each off-diagonal tile is
+// also written transposed.  Between two projections the CTA synchronises and
 // fences its global writes for the async proxy, so the next projection's TMA
 // loads see them.  All systems' X live in one stacked array (system s owns
 // rows [row_off_s, row_off_s + ld_s) and columns [0, ld_s)), so four tensor
@@ -68,6 +70,17 @@ __device__ __forceinline__ void fence_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// Row-major upper-triangle tile t -> (I, J), I <= J, of an nt x nt tiling.
+__device__ __forceinline__ void tri_tile(int t, int nt, int* I, int* J) {
+  int i = 0;
+  while (t >= nt - i) {
+    t -= nt - i;
+    ++i;
+  }
+  *I = i;
+  *J = i + t;
+}
+
 template <int P, int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     k_sp2_grouped(GArgs ga, const __grid_constant__ CUtensorMap ah0, const __grid_constant__ CUtensorMap al0,
@@ -76,6 +89,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                   const __grid_constant__ CUtensorMap bh1, const __grid_constant__ CUtensorMap bl1) {
   using C = Prec<P>;
   using G = GCfg<P, BN>;
+  constexpr bool kSym = BN == BM;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[G::stages], empty[G::stages], tfull[2], tempty[2];
   __shared__ uint32_t tmem_base;
@@ -115,7 +129,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (sys >= ga.count || s_abort) break;
     const GDesc d = ga.desc[sys];
     const int n = d.n, ld = d.ld, ro = d.row_off;
-    const int nt_m = ld / BM, nt_n = ld / BN, ntiles = nt_m * nt_n;
+    // square tiles (BN = BM): only the upper triangle of the symmetric X^2 is
+    // computed and mirrored; otherwise every tile
+    const int nt_m = ld / BM, nt_n = ld / BN;
+    const int ntiles = kSym ? nt_m * (nt_m + 1) / 2 : nt_m * nt_n;
     const int nk = ld / C::bk;
 
     // ---- Gershgorin bounds (warp per row)
@@ -223,7 +240,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         const CUtensorMap* mbh = ib ? &bh1 : &bh0;
         const CUtensorMap* mbl = ib ? &bl1 : &bl0;
         for (int t = 0; t < ntiles && !s_abort; ++t) {
-          const int m0 = (t / nt_n) * BM, n0 = (t % nt_n) * BN;
+          int m0 = (t / nt_n) * BM, n0 = (t % nt_n) * BN;
+          if constexpr (kSym) {
+            int I, J;
+            tri_tile(t, nt_m, &I, &J);
+            m0 = I * BM;
+            n0 = J * BN;
+          }
           for (int kb = 0; kb < nk; ++kb, ++g_prod) {
             const int s = g_prod % G::stages;
             if (g_prod >= G::stages && !mbar_wait(&empty[s], ((g_prod / G::stages) - 1) & 1, &s_abort)) break;
@@ -271,8 +294,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int acc = t_epi & 1;
           if (!mbar_wait(&tfull[acc], (t_epi >> 1) & 1, &s_abort)) break;
           tc_fence_after();
-          const int m0 = (t / nt_n) * BM, n0 = (t % nt_n) * BN;
+          int m0 = (t / nt_n) * BM, n0 = (t % nt_n) * BN;
+          if constexpr (kSym) {
+            int I, J;
+            tri_tile(t, nt_m, &I, &J);
+            m0 = I * BM;
+            n0 = J * BN;
+          }
+          const bool mirror = kSym && m0 != n0;
           const size_t grow = (size_t)(ro + m0 + row);
+          double u2 = 0.0;
           const float* xin = ga.M[ib] + grow * ga.cols + n0;
           float* xout = ga.M[ob] + grow * ga.cols + n0;
           char* hrow = static_cast<char*>(ga.Hi[ob]) + (grow * ga.cols + n0) * C::eb;
@@ -287,14 +318,25 @@ __global__ void __launch_bounds__(kThreads, 1)
               const float cxx = __uint_as_float(v[j]);
               const float x = xin[32 * c + j];
               y[j] = br ? fmaf(2.0f, x, -cxx) : cxx;
-              t2 += (double)y[j] * (double)y[j];
+              u2 += (double)y[j] * (double)y[j];
               if (m0 + row == n0 + 32 * c + j) t1 += (double)y[j];
             }
             float4* xo = reinterpret_cast<float4*>(xout + 32 * c);
 #pragma unroll
             for (int j = 0; j < 8; ++j) xo[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
             store_operands<P>(y, hrow + 32 * c * C::eb, lrow + 32 * c * C::eb);
+            if (mirror) {
+              // element (m0 + row, n0 + 32c + j) is also (n0 + 32c + j, m0 + row):
+              // for each j the 32 lanes write 32 consecutive values
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const size_t idx = (size_t)(ro + n0 + 32 * c + j) * ga.cols + m0 + row;
+                ga.M[ob][idx] = y[j];
+                store_operand1<P>(y[j], ga.Hi[ob], ga.Lo[ob] ? ga.Lo[ob] : ga.Hi[ob], idx);
+              }
+            }
           }
+          t2 += mirror ? 2.0 * u2 : u2;
           tc_fence_before();
           __syncwarp();
           if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[acc])) : "memory");
