@@ -35,6 +35,11 @@ namespace {
 
 constexpr int kTile = 128;
 constexpr int kMaxMu = 40;
+// First-order canonical correction: when the Newton step after an expansion
+// satisfies |beta dmu| <= kCorr, D(mu + dmu) = D + beta dmu D(I - D) + O(dmu^2)
+// replaces another expansion; the neglected term is at most
+// (beta dmu)^2 / 2 * max f(1-f)(1-2f) < 1e-7.
+constexpr double kCorr = 1e-3;
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
@@ -42,7 +47,9 @@ struct FoeState {
   double mu, lo, hi;
   double emin, emax;
   int done, iters, capped, err;
-  int ran;  // 1: the last k_foe_mu evaluated an expansion (it was not skipped)
+  int ran;     // 1: the last k_foe_mu evaluated an expansion (it was not skipped)
+  int nocorr;  // 0: apply the first-order correction by dmu to the last expansion
+  double dmu;
   double tr[kMaxMu + 1], trdd[kMaxMu + 1], mus[kMaxMu + 1];
 };
 
@@ -68,6 +75,7 @@ __global__ void k_foe_bounds(const double* bparts, int nb, FoeState* st, const d
     st->hi = b + 40.0 * kT + 1.0;
     const double g = mu_in ? *mu_in : NAN;
     st->mu = (isfinite(g) && g > st->lo && g < st->hi) ? g : 0.5 * (a + b);
+    st->nocorr = 1;
   }
 }
 
@@ -141,9 +149,19 @@ __global__ void k_foe_mu(FoeState* st, const double* parts, int np, int n, doubl
     if (dev < 0.0) st->lo = mu;
     else st->hi = mu;
     const double slope = beta * (x - y);
-    double next = slope > 1e-12 ? mu - dev / slope : NAN;
-    if (!(next > st->lo && next < st->hi)) next = 0.5 * (st->lo + st->hi);
-    st->mu = next;
+    const double step = slope > 1e-12 ? -dev / slope : NAN;
+    if (fabs(beta * step) <= kCorr) {
+      // accept this expansion with the first-order shift to mu + step
+      st->done = 1;
+      st->nocorr = 0;
+      st->dmu = step;
+      st->tr[it] = x + slope * step;
+      st->mus[it] = mu + step;
+    } else {
+      double next = mu + step;
+      if (!(next > st->lo && next < st->hi)) next = 0.5 * (st->lo + st->hi);
+      st->mu = next;
+    }
   }
   if (cond && st->done) cudaGraphSetConditional(handle, 0);
 }
@@ -155,6 +173,20 @@ __global__ void __launch_bounds__(256) k_foe_keep(const FoeState* st, size_t cou
   if (!st->ran || src == dst) return;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
     dst[e] = src[e];
+}
+
+// E <- E + beta dmu (I/4 - E^2) on the n x n block (D(I - D) = I/4 - E^2),
+// with T = E^2 from the product kernel; skipped unless the correction applies.
+__global__ void __launch_bounds__(256) k_foe_correct(const FoeState* st, int n, int ld, double beta,
+                                                     const float* __restrict__ T, float* __restrict__ E) {
+  if (st->nocorr) return;
+  const float c = (float)(beta * st->dmu);
+  const size_t total = (size_t)n * n;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / n), col = (int)(e % n);
+    const size_t i = (size_t)r * ld + col;
+    E[i] = fmaf(c, (r == col ? 0.25f : 0.0f) - T[i], E[i]);
+  }
 }
 
 __global__ void __launch_bounds__(256) k_foe_finalize(const FoeState* st, int n, int ld, const float* __restrict__ X,
@@ -278,6 +310,7 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
   if ((rc = tb_loop_begin(ctx, s, &loop))) return rc;
   cudaStream_t ls = loop.body_stream;
   const int rounds = loop.graph ? 1 : o->mu_iters;
+  int* gskip = skip;
   auto gemm = [&](Mat& A, Mat& B, Mat& out, float alpha, float betac, const float* E, float gamma,
                   double* prt) -> int {
     GemmArgs g{};
@@ -291,10 +324,12 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
     g.ohi = out.hi;
     g.olo = out.lo;
     g.parts = prt;
-    g.skip = skip;
+    g.skip = gskip;
     g.err = errp;
     return tc_gemm(ctx, o->precision, g, &A.mh, &A.ml, &B.mh, &B.ml, ls);
   };
+  Mat* xf = &M[0];  // final iterate and a free matrix after an expansion
+  Mat* af = &M[1];
   auto expansion = [&]() -> int {
     int r;
     Mat* X = &M[0];
@@ -328,10 +363,22 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
     TB_LAUNCH_CHECK(ctx);
     k_foe_keep<<<1184, 256, 0, ls>>>(st, nn, X->m, res);
     TB_LAUNCH_CHECK(ctx);
+    xf = X;
+    af = A;
     return TB_OK;
   };
   for (int it = 0; it < rounds && rc == TB_OK; ++it) rc = expansion();
   if ((rc = tb_loop_end(ctx, &loop, rc))) return rc;
+  // first-order canonical correction of the accepted expansion (its E and
+  // operand splits are still in *xf): T = E^2, then E += beta dmu (I/4 - T)
+  ls = s;
+  gskip = &st->nocorr;
+  if ((rc = gemm(*xf, *xf, *af, 1.0f, 0.0f, nullptr, 0.0f, nullptr))) return rc;
+  {
+    const int fb = std::min(1184, (int)(((size_t)n * n + 255) / 256));
+    k_foe_correct<<<fb, 256, 0, s>>>(st, n, L.ld, beta, af->m, res);
+    TB_LAUNCH_CHECK(ctx);
+  }
   const int fb = std::min(1184, (int)(((size_t)n * n + 255) / 256));
   k_foe_finalize<<<fb, 256, 0, s>>>(st, n, L.ld, res, D, nocc, tol, m, mu, rep);
   TB_LAUNCH_CHECK(ctx);
