@@ -254,7 +254,9 @@ int dm_fermi_workspace_size(int n, const tb_fermi_opts* opts, size_t* bytes);
  * recursive Fermi-operator expansion: from X0 = I/2 - beta/2^(m+2) (H - mu I),
  * m steps X <- X^2 [X^2 + (I - X)^2]^-1, each doubling beta, carried out on
  * E = X - I/2 as E <- 2E (I + 4E^2)^-1 (inverse by Newton-Schulz).  mu: safeguarded Newton steps with dTr D/dmu =
- * beta Tr[D(I - D)] inside a bisection bracket, all on the device.
+ * beta Tr[D(I - D)] inside a bisection bracket, all on the device; when a Newton step dmu is small
+ * (|beta dmu| <= 1e-3) the last expansion is shifted to mu + dmu to first order, D + beta dmu D(I - D),
+ * instead of being repeated (error below 1e-7).
  *   H [n*n], D [n*n] (FP64); mu: device double, in = initial guess (NaN: the
  *   spectral midpoint), out = chemical potential of D; report: device or NULL. */
 int dm_fermi(tb_ctx* ctx, const double* H, int n, double n_occ, double kT, const tb_fermi_opts* opts,
