@@ -657,7 +657,7 @@ def run_batched(args):
     ws = Workspace(tbmd.dm_sp2_grouped_workspace_size(ns, opts))
     stream = torch.cuda.current_stream()
     results = {}
-    for label, auto in (("fixed", False), ("autotuned", True)):
+    for label, auto in (("fixed", 0), ("autotuned", 1)):
         tbmd.dm_sp2_grouped_plan(ctx, ns, nocc, Ht, Dt, rep, opts, auto, ws.ptr, ws.nbytes)
         cfg = tbmd.dm_sp2_grouped_run(ctx, ws.ptr)
         side = torch.cuda.Stream()
@@ -719,10 +719,11 @@ def run_batched(args):
                    "512 water-like systems, atom counts uniform in [16,256] (seed 4), n=32..512, SP2 to 1e-8 "
                    "in one persistent grouped launch (CUDA graph replay)",
                    batch_per_s=1e3 / a["ms"], systems_ok=st_ok,
-                   autotune={"chosen": {"tile_n": a["config"] // 10000, "grid": a["config"] % 10000},
+                   autotune={"chosen": {"cluster": a["config"] // 10 ** 7, "tile_n": (a["config"] // 10 ** 4) % 1000,
+                                        "grid": a["config"] % 10 ** 4},
                              "autotuned_ms": a["ms"], "fixed_ms": results["fixed"]["ms"],
-                             "fixed": {"tile_n": results["fixed"]["config"] // 10000,
-                                       "grid": results["fixed"]["config"] % 10000}},
+                             "fixed": {"cluster": 1, "tile_n": (results["fixed"]["config"] // 10 ** 4) % 1000,
+                                       "grid": results["fixed"]["config"] % 10 ** 4}},
                    latency_ms={"p50": a["ms"], "p99": _pct(a["ms_all"], 0.99)},
                    roofline={"bound": "tensor", "achieved": value, "peak": peak, "unit": "TFLOP/s",
                              "frac": value / peak, "traffic": None,

@@ -208,11 +208,14 @@ int dm_sp2_grouped_workspace_size(int count, const int* n, const tb_sp2_opts* op
  *   n, n_occ   host arrays [count]
  *   H, D       host arrays [count] of device pointers to n[i] x n[i] FP64 matrices
  *   reports    device array [count] of tb_sp2_report, or NULL
- * Copies the per-system descriptors into the workspace; with autotune != 0 it
- * also times each launch configuration (tile width 64 or 128, persistent grid
- * of all or half the SMs) on the batch itself and keeps the fastest (the
- * batch is solved several times).  Synchronises `stream`.  One plan per
- * context at a time: a new plan replaces the previous one. */
+ * Copies the per-system descriptors into the workspace.  autotune selects the
+ * launch form: 0 = one CTA per system, 128-wide tiles, one CTA per SM;
+ * 4 or 8 = thread-block clusters of that many CTAs per system (the CTAs split
+ * each projection's tiles; as many clusters as fit at once); 1 = time every
+ * form (tile width 64 or 128 with all or half the SMs, clusters of 4 or 8) on
+ * the batch itself and keep the fastest (the batch is solved several times).
+ * Synchronises `stream`.  One plan per context at a time: a new plan replaces
+ * the previous one. */
 int dm_sp2_grouped_plan(tb_ctx* ctx, int count, const int* n, const double* n_occ, const double* const* H,
                         double* const* D, tb_sp2_report* reports, const tb_sp2_opts* opts, int autotune,
                         void* workspace, size_t workspace_bytes, void* stream);
@@ -220,7 +223,8 @@ int dm_sp2_grouped_plan(tb_ctx* ctx, int count, const int* n, const double* n_oc
 /* Run the planned batch: one memset and one kernel launch on `stream`, no
  * host synchronisation, so it can be captured in a CUDA graph.  The H
  * matrices may change between runs (the pointers may not).
- * *config_out (host, may be NULL) = tile width * 10000 + grid size. */
+ * *config_out (host, may be NULL) = cluster size * 10^7 + tile width * 10^4 +
+ * grid size (cluster size 1: one CTA per system). */
 int dm_sp2_grouped_run(tb_ctx* ctx, void* workspace, int* config_out, void* stream);
 
 /* ------------------------------------------- a10: finite temperature solve */

@@ -396,11 +396,387 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Cluster form: a thread-block cluster of CS CTAs (one per SM) runs one system
+// at a time.  The CTAs split the rows of the Gershgorin bounds, of X0 and of
+// D, and the upper-triangle 128 x 128 tiles of every projection (tile t goes
+// to CTA t mod CS); their FP64 partials meet in CTA 0's shared memory
+// (distributed shared memory), and a cluster barrier (release/acquire)
+// separates the projections, after which every CTA takes the same decision
+// from the same partials in the same order.  Fewer systems are in flight at
+// once than with one CTA per system, so their working sets stay in L2.
+// Every CTA of a cluster passes the same sequence of cluster barriers: the
+// decisions are cluster-uniform, and a bounded wait that gives up marks the
+// CTA's partials, which stops all of them together.
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// Generic pointer to the same shared variable in CTA `rank` of the cluster.
+template <typename T>
+__device__ __forceinline__ T* cluster_map(T* p, uint32_t rank) {
+  uint64_t in = reinterpret_cast<uint64_t>(p), out;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(in), "r"(rank));
+  return reinterpret_cast<T*>(out);
+}
+
+template <int P, int CS>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_sp2_grouped_cl(GArgs ga, const __grid_constant__ CUtensorMap ah0, const __grid_constant__ CUtensorMap al0,
+                     const __grid_constant__ CUtensorMap ah1, const __grid_constant__ CUtensorMap al1) {
+  using C = Prec<P>;
+  using G = GCfg<P, BM>;
+  constexpr int BN = BM;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[G::stages], empty[G::stages], tfull[2], tempty[2], mdone;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int s_abort;
+  __shared__ int s_sys;
+  __shared__ double s_red[8][3];
+  // partials of every CTA, valid in CTA 0: [parity][rank] = (t1, t2, abort)
+  __shared__ double s_part[2][CS][3];
+  __shared__ double s_bnd[CS][2];
+  __shared__ double s_hist[2][SP2_MAX_ITER + 2];
+  __shared__ unsigned long long s_branch[2];
+  __shared__ double s_t1, s_t2, s_lo, s_hi;
+  __shared__ int s_stop, s_br;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < G::stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    mbar_init(&mdone, 1);
+    s_abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_base, 2 * BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  int g_prod = 0, g_mma = 0, t_mma = 0, t_epi = 0;
+  double* part0 = cluster_map(&s_part[0][0][0], 0);  // CTA 0's partials
+  double* bnd0 = cluster_map(&s_bnd[0][0], 0);
+  cluster_sync();  // every CTA of the cluster is running
+
+  bool quit = false;
+  while (!quit) {
+    if (rank == 0 && threadIdx.x == 0) {
+      const int sys = atomicAdd(ga.queue, 1);
+      for (int r = 0; r < CS; ++r) *cluster_map(&s_sys, (uint32_t)r) = sys;
+    }
+    cluster_sync();
+    const int sys = s_sys;
+    if (sys >= ga.count) break;
+    const GDesc d = ga.desc[sys];
+    const int n = d.n, ld = d.ld, ro = d.row_off;
+    const int nt = ld / BM;
+    const int ntiles = nt * (nt + 1) / 2;
+    const int nk = ld / C::bk;
+
+    // ---- Gershgorin bounds: rows rank, rank + CS, ... (warp per row)
+    {
+      double lo = INFINITY, hi = -INFINITY;
+      for (int r = (int)rank + CS * warp; r < n; r += CS * (kThreads / 32)) {
+        double sabs = 0.0;
+        for (int c = lane; c < n; c += 32) sabs += (c == r) ? 0.0 : fabs(d.H[(size_t)r * n + c]);
+        sabs = warp_sum(sabs);
+        const double hd = d.H[(size_t)r * n + r];
+        lo = fmin(lo, hd - sabs);
+        hi = fmax(hi, hd + sabs);
+      }
+      if (lane == 0) {
+        s_red[warp][0] = lo;
+        s_red[warp][1] = hi;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double a = s_red[0][0], b = s_red[0][1];
+        for (int w = 1; w < kThreads / 32; ++w) {
+          a = fmin(a, s_red[w][0]);
+          b = fmax(b, s_red[w][1]);
+        }
+        bnd0[2 * rank] = a;
+        bnd0[2 * rank + 1] = b;
+      }
+      cluster_sync();
+      if (threadIdx.x == 0) {
+        double a = bnd0[0], b = bnd0[1];
+        for (int r = 1; r < CS; ++r) {
+          a = fmin(a, bnd0[2 * r]);
+          b = fmax(b, bnd0[2 * r + 1]);
+        }
+        s_lo = a;
+        s_hi = b;
+        s_branch[0] = s_branch[1] = 0ull;
+      }
+      __syncthreads();
+    }
+    // ---- X0 into buffer 0: row segments of 32 split over the cluster
+    {
+      const double emin = s_lo, emax = s_hi;
+      double w = emax - emin;
+      if (!(w > 0.0)) w = 1.0;
+      const double inv = 1.0 / w;
+      double t1 = 0.0, t2 = 0.0;
+      const int segs = ld * (ld / 32);
+      for (int seg = (int)rank * kThreads + threadIdx.x; seg < segs; seg += CS * kThreads) {
+        const int r = seg / (ld / 32), c0 = 32 * (seg % (ld / 32));
+        float y[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int c = c0 + j;
+          double x = 0.0;
+          if (r < n && c < n) x = ((r == c ? emax : 0.0) - d.H[(size_t)r * n + c]) * inv;
+          y[j] = (float)x;
+          const double xf = y[j];
+          t2 += xf * xf;
+          if (r == c) t1 += xf;
+        }
+        const size_t e0 = (size_t)(ro + r) * ga.cols + c0;
+        float4* dst = reinterpret_cast<float4*>(ga.M[0] + e0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) dst[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
+        char* h = static_cast<char*>(ga.Hi[0]) + e0 * C::eb;
+        char* l = ga.Lo[0] ? static_cast<char*>(ga.Lo[0]) + e0 * C::eb : h;
+        store_operands<P>(y, h, l);
+      }
+      t1 = warp_sum(t1);
+      t2 = warp_sum(t2);
+      if (lane == 0) {
+        s_red[warp][0] = t1;
+        s_red[warp][1] = t2;
+      }
+      fence_async_global();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w2 = 0; w2 < kThreads / 32; ++w2) {
+          a += s_red[w2][0];
+          b += s_red[w2][1];
+        }
+        part0[3 * rank] = a;
+        part0[3 * rank + 1] = b;
+        part0[3 * rank + 2] = 0.0;
+      }
+      cluster_sync();
+      fence_async_global();
+    }
+    const double floor_e = 2.0 * n * ga.tol_floor_u;
+    int k = 0;
+    for (;; ++k) {
+      // ---- decision for projection k from the cluster's partials (parity k)
+      if (threadIdx.x == 0) {
+        const double* pk = part0 + (k & 1) * CS * 3;
+        double t1 = 0.0, t2 = 0.0, ab = 0.0;
+        for (int r = 0; r < CS; ++r) {
+          t1 += pk[3 * r];
+          t2 += pk[3 * r + 1];
+          ab += pk[3 * r + 2];
+        }
+        s_hist[0][k] = t1;
+        s_hist[1][k] = t2;
+        s_t1 = t1;
+        s_t2 = t2;
+        const double e = t1 - t2;
+        int stop = 0;
+        if (e <= floor_e) stop = 1;
+        if (!stop && k >= 3) {
+          bool flat = e <= 4.0 * floor_e;
+          for (int j = 1; j <= 3; ++j) flat = flat && (s_hist[0][k - j] - s_hist[1][k - j] <= 4.0 * floor_e);
+          if (flat) stop = 1;
+        }
+        if (k >= ga.max_iter) stop = 2;
+        if (ab != 0.0) stop = 3;
+        int br = 0;
+        if (!stop) {
+          br = ga.rule == 0 ? (fabs(t2 - d.nocc) <= fabs(2.0 * t1 - t2 - d.nocc) ? 0 : 1) : (t1 > d.nocc ? 0 : 1);
+          if (br) s_branch[k >> 6] |= 1ull << (k & 63);
+        }
+        s_stop = stop;
+        s_br = br;
+      }
+      __syncthreads();
+      if (s_stop) break;
+      const int br = s_br;
+      const int ib = k & 1, ob = (k + 1) & 1;
+      if (warp == 0 && lane == 0) {
+        const CUtensorMap* mah = ib ? &ah1 : &ah0;
+        const CUtensorMap* mal = ib ? &al1 : &al0;
+        for (int t = (int)rank; t < ntiles && !s_abort; t += CS) {
+          int I, J;
+          tri_tile(t, nt, &I, &J);
+          for (int kb = 0; kb < nk; ++kb, ++g_prod) {
+            const int s = g_prod % G::stages;
+            if (g_prod >= G::stages && !mbar_wait(&empty[s], ((g_prod / G::stages) - 1) & 1, &s_abort)) break;
+            uint8_t* base = smem + s * G::stage_bytes;
+            mbar_expect_tx(&full[s], G::stage_bytes);
+            tma_load_2d(base, mah, &full[s], kb * C::bk, ro + I * BM);
+            tma_load_2d(base + G::a_bytes, mah, &full[s], kb * C::bk, ro + J * BN);
+            if constexpr (C::split) {
+              tma_load_2d(base + G::a_bytes + G::b_bytes, mal, &full[s], kb * C::bk, ro + I * BM);
+              tma_load_2d(base + 2 * G::a_bytes + G::b_bytes, mal, &full[s], kb * C::bk, ro + J * BN);
+            }
+          }
+        }
+      } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t id = idesc(C::tf32 ? 2u : 1u, BM, BN);
+        for (int t = (int)rank; t < ntiles && !s_abort; t += CS, ++t_mma) {
+          const int acc = t_mma & 1;
+          if (t_mma >= 2 && !mbar_wait(&tempty[acc], ((t_mma >> 1) - 1) & 1, &s_abort)) break;
+          tc_fence_after();
+          const uint32_t dt = tmem + acc * BN;
+          for (int kb = 0; kb < nk; ++kb, ++g_mma) {
+            const int s = g_mma % G::stages;
+            if (!mbar_wait(&full[s], (g_mma / G::stages) & 1, &s_abort)) break;
+            tc_fence_after();
+            const uint32_t base = smem_u32(smem + s * G::stage_bytes);
+#pragma unroll
+            for (int ks = 0; ks < C::bk / C::uk; ++ks) {
+              const uint32_t koff = ks * 32;
+              const uint64_t a0 = sdesc(base + koff), b0 = sdesc(base + G::a_bytes + koff);
+              umma<C::tf32>(dt, a0, b0, id, (kb | ks) != 0);
+              if constexpr (C::split) {
+                umma<C::tf32>(dt, a0, sdesc(base + 2 * G::a_bytes + G::b_bytes + koff), id, 1u);
+                umma<C::tf32>(dt, sdesc(base + G::a_bytes + G::b_bytes + koff), b0, id, 1u);
+              }
+            }
+            umma_commit(&empty[s]);
+          }
+          umma_commit(&tfull[acc]);
+        }
+      } else if (warp >= 2) {
+        const int q = warp & 3;
+        const int row = 32 * q + lane;
+        double t1 = 0.0, t2 = 0.0;
+        for (int t = (int)rank; t < ntiles; t += CS, ++t_epi) {
+          const int acc = t_epi & 1;
+          if (!mbar_wait(&tfull[acc], (t_epi >> 1) & 1, &s_abort)) break;
+          tc_fence_after();
+          int I, J;
+          tri_tile(t, nt, &I, &J);
+          const int m0 = I * BM, n0 = J * BN;
+          const bool mirror = m0 != n0;
+          const size_t grow = (size_t)(ro + m0 + row);
+          const float* xin = ga.M[ib] + grow * ga.cols + n0;
+          float* xout = ga.M[ob] + grow * ga.cols + n0;
+          char* hrow = static_cast<char*>(ga.Hi[ob]) + (grow * ga.cols + n0) * C::eb;
+          char* lrow = ga.Lo[ob] ? static_cast<char*>(ga.Lo[ob]) + (grow * ga.cols + n0) * C::eb : hrow;
+          double u2 = 0.0;
+#pragma unroll 1
+          for (int c = 0; c < BN / 32; ++c) {
+            uint32_t v[32];
+            tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + acc * BN + 32 * c, v);
+            float y[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float cxx = __uint_as_float(v[j]);
+              const float x = xin[32 * c + j];
+              y[j] = br ? fmaf(2.0f, x, -cxx) : cxx;
+              u2 += (double)y[j] * (double)y[j];
+              if (m0 + row == n0 + 32 * c + j) t1 += (double)y[j];
+            }
+            float4* xo = reinterpret_cast<float4*>(xout + 32 * c);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) xo[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
+            store_operands<P>(y, hrow + 32 * c * C::eb, lrow + 32 * c * C::eb);
+            if (mirror) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const size_t idx = (size_t)(ro + n0 + 32 * c + j) * ga.cols + m0 + row;
+                ga.M[ob][idx] = y[j];
+                store_operand1<P>(y[j], ga.Hi[ob], ga.Lo[ob] ? ga.Lo[ob] : ga.Hi[ob], idx);
+              }
+            }
+          }
+          t2 += mirror ? 2.0 * u2 : u2;
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[acc])) : "memory");
+        }
+        t1 = warp_sum(t1);
+        t2 = warp_sum(t2);
+        if (lane == 0) {
+          s_red[warp][0] = t1;
+          s_red[warp][1] = t2;
+        }
+        fence_async_global();
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w2 = 2; w2 < kThreads / 32; ++w2) {
+          a += s_red[w2][0];
+          b += s_red[w2][1];
+        }
+        double* pn = part0 + ob * CS * 3;
+        pn[3 * rank] = a;
+        pn[3 * rank + 1] = b;
+        pn[3 * rank + 2] = s_abort ? 1.0 : 0.0;
+      }
+      cluster_sync();
+      fence_async_global();
+    }
+    // ---- D from the final iterate (buffer k % 2): rows split over the cluster
+    {
+      const float* X = ga.M[k & 1];
+      for (int r = (int)rank + CS * warp; r < n; r += CS * (kThreads / 32))
+        for (int c = lane; c < n; c += 32) d.D[(size_t)r * n + c] = (double)X[(size_t)(ro + r) * ga.cols + c];
+      if (rank == 0 && threadIdx.x == 0 && d.rep) {
+        tb_sp2_report* rp = d.rep;
+        rp->status = s_stop == 3 ? TB_ERR_TIMEOUT : (fabs(s_t1 - d.nocc) > 0.25 ? TB_ERR_GAP : TB_OK);
+        rp->iters = k;
+        rp->refine_iters = 0;
+        rp->n = n;
+        rp->eps_min = s_lo;
+        rp->eps_max = s_hi;
+        rp->trace = s_t1;
+        rp->idem_trace = s_t1 - s_t2;
+        rp->idem_fro = -1.0;
+        rp->branch_bits[0] = s_branch[0];
+        rp->branch_bits[1] = s_branch[1];
+        rp->refine_bits = 0;
+        rp->block_products = 0;
+        rp->blocks = 0;
+      }
+      if (s_stop == 3) quit = true;  // cluster-uniform: every CTA saw the same partials
+    }
+    __syncthreads();
+  }
+  cluster_sync();  // no CTA leaves while another may still address its shared memory
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && s_abort && ga.err) atomicExch(ga.err, TB_ERR_TIMEOUT);
+  if (warp == 1) {
+    tc_fence_after();
+    if (lane == 0) {
+      umma_commit(&mdone);
+      const unsigned long long t0 = gtime();
+      while (!mbar_try(&mdone, 0) && gtime() - t0 < kWaitNs) {
+      }
+    }
+    __syncwarp();
+    tmem_dealloc(tmem, 2 * BN);
+  }
+}
+
 // Plan header kept at the start of the workspace.
 struct Plan {
   int count, precision, rule, max_iter;
   int rows, cols;
-  int bn, grid;
+  int bn, grid, cs;  // cs > 1: cluster form with cs CTAs per system
   double u;
   size_t off_desc, off_queue, off_err, off_m[2], off_hi[2], off_lo[2], total;
   CUtensorMap ah[2], al[2], bh[2], bl[2];  // bh/bl for the chosen bn
@@ -454,14 +830,7 @@ int make_map(tb_ctx* ctx, int prec, const void* base, int rows, int cols, int bo
   return TB_OK;
 }
 
-template <int P, int BN>
-int launch(tb_ctx* ctx, const Plan& p, char* base, int grid, cudaStream_t s) {
-  using G = GCfg<P, BN>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    TB_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sp2_grouped<P, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::smem));
-    attr_set = true;
-  }
+GArgs make_args(const Plan& p, char* base) {
   GArgs ga{};
   ga.count = p.count;
   ga.max_iter = p.max_iter;
@@ -476,6 +845,18 @@ int launch(tb_ctx* ctx, const Plan& p, char* base, int grid, cudaStream_t s) {
     ga.Hi[b] = base + p.off_hi[b];
     ga.Lo[b] = p.off_lo[b] ? base + p.off_lo[b] : nullptr;
   }
+  return ga;
+}
+
+template <int P, int BN>
+int launch(tb_ctx* ctx, const Plan& p, char* base, int grid, cudaStream_t s) {
+  using G = GCfg<P, BN>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    TB_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sp2_grouped<P, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::smem));
+    attr_set = true;
+  }
+  const GArgs ga = make_args(p, base);
   const CUtensorMap* bh = BN == 64 ? p.bh64 : p.bh128;
   const CUtensorMap* bl = BN == 64 ? p.bl64 : p.bl128;
   TB_CUDA_TRY(ctx, cudaMemsetAsync(ga.queue, 0, sizeof(int), s));
@@ -483,6 +864,57 @@ int launch(tb_ctx* ctx, const Plan& p, char* base, int grid, cudaStream_t s) {
                                                        bh[1], bl[1]);
   TB_LAUNCH_CHECK(ctx);
   return TB_OK;
+}
+
+// Cluster form: as many clusters of CS CTAs as can be resident at once.
+template <int P, int CS>
+int launch_cl(tb_ctx* ctx, const Plan& p, char* base, cudaStream_t s, int* grid_out) {
+  using G = GCfg<P, BM>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    TB_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sp2_grouped_cl<P, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          G::smem));
+    attr_set = true;
+  }
+  const GArgs ga = make_args(p, base);
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = G::smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(std::max(CS, ctx->sm_count / CS * CS));
+  int nclusters = 0;
+  TB_CUDA_TRY(ctx, cudaOccupancyMaxActiveClusters(&nclusters, k_sp2_grouped_cl<P, CS>, &cfg));
+  if (nclusters < 1) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "no cluster of %d CTAs fits", CS);
+  cfg.gridDim = dim3(nclusters * CS);
+  if (grid_out) *grid_out = nclusters * CS;
+  TB_CUDA_TRY(ctx, cudaMemsetAsync(ga.queue, 0, sizeof(int), s));
+  TB_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, k_sp2_grouped_cl<P, CS>, ga, p.ah[0], p.al[0], p.ah[1], p.al[1]));
+  return TB_OK;
+}
+
+int launch_cl_any(tb_ctx* ctx, const Plan& p, char* base, int cs, cudaStream_t s, int* grid_out) {
+  switch (p.precision) {
+    case TB_PREC_TF32:
+      return cs == 8 ? launch_cl<TB_PREC_TF32, 8>(ctx, p, base, s, grid_out)
+                     : launch_cl<TB_PREC_TF32, 4>(ctx, p, base, s, grid_out);
+    case TB_PREC_TF32X3:
+      return cs == 8 ? launch_cl<TB_PREC_TF32X3, 8>(ctx, p, base, s, grid_out)
+                     : launch_cl<TB_PREC_TF32X3, 4>(ctx, p, base, s, grid_out);
+    case TB_PREC_BF16:
+      return cs == 8 ? launch_cl<TB_PREC_BF16, 8>(ctx, p, base, s, grid_out)
+                     : launch_cl<TB_PREC_BF16, 4>(ctx, p, base, s, grid_out);
+    case TB_PREC_BF16X3:
+      return cs == 8 ? launch_cl<TB_PREC_BF16X3, 8>(ctx, p, base, s, grid_out)
+                     : launch_cl<TB_PREC_BF16X3, 4>(ctx, p, base, s, grid_out);
+    default: return tb_fail(ctx, TB_ERR_UNSUPPORTED, "grouped SP2 needs a tensor-core precision");
+  }
 }
 
 int launch_any(tb_ctx* ctx, const Plan& p, char* base, int bn, int grid, cudaStream_t s) {
@@ -576,31 +1008,47 @@ extern "C" int dm_sp2_grouped_plan(tb_ctx* ctx, int count, const int* n, const d
   }
   p.bn = 128;
   p.grid = std::max(1, ctx->sm_count);
-  if (autotune) {
-    // time every candidate on the batch itself and keep the fastest
-    const int bns[2] = {128, 64};
-    const int grids[2] = {ctx->sm_count, std::max(1, ctx->sm_count / 2)};
+  p.cs = 1;
+  if (autotune == 4 || autotune == 8) {
+    p.cs = autotune;
+    int rc = launch_cl_any(ctx, p, base, p.cs, s, &p.grid);  // sizes the grid (and warms up)
+    if (rc) return rc;
+  } else if (autotune) {
+    // time every candidate on the batch itself and keep the fastest: one CTA
+    // per system with 128- or 64-wide tiles and a full or half grid, or
+    // clusters of 4 or 8 CTAs per system
+    struct Cand {
+      int bn, grid, cs;
+    };
+    const Cand cands[6] = {{128, ctx->sm_count, 1}, {128, std::max(1, ctx->sm_count / 2), 1},
+                           {64, ctx->sm_count, 1},  {64, std::max(1, ctx->sm_count / 2), 1},
+                           {128, 0, 4},             {128, 0, 8}};
     cudaEvent_t e0, e1;
     TB_CUDA_TRY(ctx, cudaEventCreate(&e0));
     TB_CUDA_TRY(ctx, cudaEventCreate(&e1));
     float best = 1e30f;
-    for (int bi = 0; bi < 2; ++bi)
-      for (int gi = 0; gi < 2; ++gi) {
-        int rc = launch_any(ctx, p, base, bns[bi], grids[gi], s);  // warm-up
-        if (rc) return rc;
-        TB_CUDA_TRY(ctx, cudaEventRecord(e0, s));
-        rc = launch_any(ctx, p, base, bns[bi], grids[gi], s);
-        if (rc) return rc;
-        TB_CUDA_TRY(ctx, cudaEventRecord(e1, s));
-        TB_CUDA_TRY(ctx, cudaEventSynchronize(e1));
-        float ms = 0.f;
-        TB_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-          best = ms;
-          p.bn = bns[bi];
-          p.grid = grids[gi];
-        }
+    for (const Cand& c : cands) {
+      int grid = c.grid;
+      auto run = [&]() {
+        return c.cs > 1 ? launch_cl_any(ctx, p, base, c.cs, s, &grid) : launch_any(ctx, p, base, c.bn, c.grid, s);
+      };
+      int rc = run();  // warm-up
+      if (rc == TB_ERR_UNSUPPORTED) continue;  // no cluster of that size fits
+      if (rc) return rc;
+      TB_CUDA_TRY(ctx, cudaEventRecord(e0, s));
+      rc = run();
+      if (rc) return rc;
+      TB_CUDA_TRY(ctx, cudaEventRecord(e1, s));
+      TB_CUDA_TRY(ctx, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      TB_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        p.bn = c.bn;
+        p.grid = grid;
+        p.cs = c.cs;
       }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
@@ -617,6 +1065,7 @@ extern "C" int dm_sp2_grouped_run(tb_ctx* ctx, void* ws, int* bn_out, void* stre
   if (ctx->plan_ws != ws) return tb_fail(ctx, TB_ERR_ARG, "workspace has no plan in this context");
   Plan p;
   std::copy(ctx->plan_cache, ctx->plan_cache + sizeof(Plan), reinterpret_cast<char*>(&p));
-  if (bn_out) *bn_out = p.bn * 10000 + p.grid;
+  if (bn_out) *bn_out = p.cs * 10000000 + p.bn * 10000 + p.grid;
+  if (p.cs > 1) return launch_cl_any(ctx, p, static_cast<char*>(ws), p.cs, as_stream(stream), nullptr);
   return launch_any(ctx, p, static_cast<char*>(ws), p.bn, p.grid, as_stream(stream));
 }

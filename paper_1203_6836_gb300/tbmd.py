@@ -298,13 +298,14 @@ def dm_sp2_grouped_workspace_size(n_list, opts: tb_sp2_opts) -> int:
 
 
 def dm_sp2_grouped_plan(ctx: Context, n_list, nocc_list, H_list, D_list, reports, opts: tb_sp2_opts,
-                        autotune: bool, workspace, workspace_bytes: int, stream=None) -> int:
+                        autotune: int, workspace, workspace_bytes: int, stream=None) -> int:
+    """autotune: 0 one CTA per system, 1 time every launch form, 4 / 8 clusters of that size."""
     cnt = len(n_list)
     nocc = (ctypes.c_double * cnt)(*[float(x) for x in nocc_list])
     hp = (ctypes.c_void_p * cnt)(*[_ptr(h) for h in H_list])
     dp = (ctypes.c_void_p * cnt)(*[_ptr(d) for d in D_list])
     return ctx.check(lib().dm_sp2_grouped_plan(ctx.handle, cnt, _ints(n_list), nocc, hp, dp, _ptr(reports),
-                                               ctypes.byref(opts), int(bool(autotune)), _ptr(workspace),
+                                               ctypes.byref(opts), int(autotune), _ptr(workspace),
                                                int(workspace_bytes), _stream(stream)), "dm_sp2_grouped_plan")
 
 

@@ -50,10 +50,15 @@ def ctypes_size():
     return ctypes.sizeof(tbmd.tb_sp2_report)
 
 
-def test_grouped_batch_matches_eigh(ctx):
+@pytest.mark.parametrize("mode", [1, 4, 8])
+def test_grouped_batch_matches_eigh(ctx, mode):
+    """mode 1: autotuned launch form; 4 / 8: clusters of that many CTAs per system."""
     Hs, nocc = _batch(40)
-    Ht, Dt, rep, ws, cfg = _solve(ctx, Hs, nocc, autotune=True)
-    assert cfg // 10000 in (64, 128)
+    Ht, Dt, rep, ws, cfg = _solve(ctx, Hs, nocc, autotune=mode)
+    cs, bn = cfg // 10 ** 7, (cfg // 10 ** 4) % 1000
+    assert bn in (64, 128) and cs in (1, 4, 8)
+    if mode > 1:
+        assert cs == mode
     errs = []
     for i, H in enumerate(Hs):
         r = report_to_dict(rep[i])
@@ -66,17 +71,19 @@ def test_grouped_batch_matches_eigh(ctx):
     assert np.median(errs) < 3e-6
 
 
-def test_grouped_same_alone_and_in_the_mix(ctx):
+@pytest.mark.parametrize("mode", [0, 4])
+def test_grouped_same_alone_and_in_the_mix(ctx, mode):
     Hs, nocc = _batch(24, seed=9)
-    _, Dall, _, _, _ = _solve(ctx, Hs, nocc, autotune=False)
+    _, Dall, _, _, _ = _solve(ctx, Hs, nocc, autotune=mode)
     for j in (0, 7, 23):
-        _, Done, _, _, _ = _solve(ctx, [Hs[j]], [nocc[j]], autotune=False)
+        _, Done, _, _, _ = _solve(ctx, [Hs[j]], [nocc[j]], autotune=mode)
         assert torch.equal(Done[0], Dall[j])
 
 
-def test_grouped_run_replays_in_a_cuda_graph(ctx):
+@pytest.mark.parametrize("mode", [0, 8])
+def test_grouped_run_replays_in_a_cuda_graph(ctx, mode):
     Hs, nocc = _batch(16, seed=11)
-    Ht, Dt, rep, ws, cfg = _solve(ctx, Hs, nocc, autotune=False)
+    Ht, Dt, rep, ws, cfg = _solve(ctx, Hs, nocc, autotune=mode)
     first = [d.clone() for d in Dt]
     for d in Dt:
         d.zero_()
