@@ -35,11 +35,16 @@ namespace {
 
 constexpr int kTile = 128;
 constexpr int kMaxMu = 40;
-// First-order canonical correction: when the Newton step after an expansion
-// satisfies |beta dmu| <= kCorr, D(mu + dmu) = D + beta dmu D(I - D) + O(dmu^2)
-// replaces another expansion; the neglected term is at most
-// (beta dmu)^2 / 2 * max f(1-f)(1-2f) < 1e-7.
-constexpr double kCorr = 1e-3;
+// First-order canonical correction: the last expansion is accepted and shifted
+// by the Newton step dmu = -(Tr D - N) / (beta Tr[D(I - D)]) as
+// D(mu + dmu) = D + beta dmu D(I - D) + R, which makes the trace exact to
+// first order.  D(I - D) is positive semi-definite with eigenvalues <= 1/4, so
+// ||R||_F <= (beta dmu)^2 / 2 * Tr[D(I - D)] = |beta dmu| |Tr D - N| / 2; the
+// shift replaces another expansion when that bound is below kCorrFro sqrt(n)
+// and |beta dmu| <= kCorrMax (first-order regime).  Gapped systems (small
+// Tr[D(I - D)]) accept large shifts inside the gap, metallic ones small ones.
+constexpr double kCorrFro = 1e-7;
+constexpr double kCorrMax = 0.1;
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
@@ -140,7 +145,18 @@ __global__ void k_foe_mu(FoeState* st, const double* parts, int np, int n, doubl
   st->iters = it + 1;
   st->ran = 1;
   const double dev = x - nocc;
-  if (fabs(dev) <= tol) {
+  const double slope = beta * (x - y);
+  const double step = slope > 1e-12 ? -dev / slope : NAN;
+  const bool shift = fabs(beta * step) <= kCorrMax &&
+                     0.5 * fabs(beta * step) * fabs(dev) <= kCorrFro * sqrt((double)max(n, 1));
+  if (shift) {
+    // accept this expansion with the first-order shift to mu + step
+    st->done = 1;
+    st->nocorr = 0;
+    st->dmu = step;
+    st->tr[it] = x + slope * step;
+    st->mus[it] = mu + step;
+  } else if (fabs(dev) <= tol) {
     st->done = 1;
   } else if (it + 1 >= max_it) {
     st->done = 1;
@@ -148,20 +164,9 @@ __global__ void k_foe_mu(FoeState* st, const double* parts, int np, int n, doubl
   } else {
     if (dev < 0.0) st->lo = mu;
     else st->hi = mu;
-    const double slope = beta * (x - y);
-    const double step = slope > 1e-12 ? -dev / slope : NAN;
-    if (fabs(beta * step) <= kCorr) {
-      // accept this expansion with the first-order shift to mu + step
-      st->done = 1;
-      st->nocorr = 0;
-      st->dmu = step;
-      st->tr[it] = x + slope * step;
-      st->mus[it] = mu + step;
-    } else {
-      double next = mu + step;
-      if (!(next > st->lo && next < st->hi)) next = 0.5 * (st->lo + st->hi);
-      st->mu = next;
-    }
+    double next = mu + step;
+    if (!(next > st->lo && next < st->hi)) next = 0.5 * (st->lo + st->hi);
+    st->mu = next;
   }
   if (cond && st->done) cudaGraphSetConditional(handle, 0);
 }

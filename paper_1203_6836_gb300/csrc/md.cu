@@ -98,6 +98,18 @@ __global__ void __launch_bounds__(256) k_kick_energy(int N, double* __restrict__
   }
 }
 
+// mu[0] <- 2 mu[1] - mu[2] (the start of this step's dm_fermi), or mu[1]
+// when only one previous value is known.
+__global__ void k_mu_predict(double* mu) {
+  const double a = mu[1], b = mu[2];
+  if (isfinite(a)) mu[0] = isfinite(b) ? 2.0 * a - b : a;
+}
+// mu[2] <- mu[1], mu[1] <- mu[0] after a step's dm_fermi.
+__global__ void k_mu_shift(double* mu) {
+  mu[2] = mu[1];
+  mu[1] = mu[0];
+}
+
 __global__ void k_fill_hist(int N, int S, const double* __restrict__ q, double* __restrict__ hist) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -265,6 +277,12 @@ extern "C" int xlbomd_init(tb_ctx* ctx, const tb_params* p, tb_md_state* st, con
   if (rc) return rc;
   k_kick_energy<<<1, 256, 0, s>>>(N, st->v, st->F, st->mass, xp->dt, 0, st->n_hist, st->q, st->energies);
   TB_LAUNCH_CHECK(ctx);
+  if (st->kT > 0.0) {
+    const double nan2[2] = {NAN, NAN};
+    TB_CUDA_TRY(ctx, cudaMemcpyAsync(st->mu + 1, nan2, sizeof(nan2), cudaMemcpyHostToDevice, s));
+    k_mu_shift<<<1, 1, 0, s>>>(st->mu);  // mu[1] = the initial state's mu
+    TB_LAUNCH_CHECK(ctx);
+  }
   // the host vectors must outlive the async copies above
   TB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
   return TB_OK;
@@ -282,8 +300,16 @@ extern "C" int xlbomd_step(tb_ctx* ctx, const tb_params* p, tb_md_state* st, con
   TB_LAUNCH_CHECK(ctx);
   k_n_update<<<nb, 128, 0, s>>>(N, st->n_hist, xp->K, st->q, xp->kappa, xp->alpha, *xp);
   TB_LAUNCH_CHECK(ctx);
+  if (st->kT > 0.0) {
+    k_mu_predict<<<1, 1, 0, s>>>(st->mu);
+    TB_LAUNCH_CHECK(ctx);
+  }
   rc = electronic_step(ctx, p, st, so, st->n_hist, s);
   if (rc) return rc;
+  if (st->kT > 0.0) {
+    k_mu_shift<<<1, 1, 0, s>>>(st->mu);
+    TB_LAUNCH_CHECK(ctx);
+  }
   k_kick_energy<<<1, 256, 0, s>>>(N, st->v, st->F, st->mass, xp->dt, 1, st->n_hist, st->q, st->energies);
   TB_LAUNCH_CHECK(ctx);
   st->step += 1;
