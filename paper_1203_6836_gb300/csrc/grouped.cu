@@ -167,23 +167,28 @@ __global__ void __launch_bounds__(kThreads, 1)
       double w = emax - emin;
       if (!(w > 0.0)) w = 1.0;
       const double inv = 1.0 / w;
+      const float invf = (float)inv, emaxf = (float)emax;
       double t1 = 0.0, t2 = 0.0;
       for (int seg = threadIdx.x; seg < ld * (ld / 32); seg += kThreads) {
         const int r = seg / (ld / 32), c0 = 32 * (seg % (ld / 32));
         float y[32];
+        float s2 = 0.0f;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int c = c0 + j;
-          double x = 0.0;
-          if (r < n && c < n) x = ((r == c ? emax : 0.0) - d.H[(size_t)r * n + c]) * inv;
-          y[j] = (float)x;
-          const double xf = y[j];
-          t2 += xf * xf;
-          if (r == c) t1 += xf;
+          float x = 0.0f;
+          // FP32 arithmetic (one rounding of H): |error| ~ 1e-7 |H| / w, the size
+          // of the FP32 rounding of X0 itself
+          if (r < n && c < n) x = ((r == c ? emaxf : 0.0f) - (float)d.H[(size_t)r * n + c]) * invf;
+          y[j] = x;
+          s2 = fmaf(x, x, s2);
+          if (r == c) t1 += (double)x;
         }
+        t2 += (double)s2;
         const size_t e0 = (size_t)(ro + r) * ga.cols + c0;
-        float* dst = ga.M[0] + e0;
-        for (int j = 0; j < 32; ++j) dst[j] = y[j];
+        float4* dst = reinterpret_cast<float4*>(ga.M[0] + e0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) dst[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
         char* h = static_cast<char*>(ga.Hi[0]) + e0 * C::eb;
         char* l = ga.Lo[0] ? static_cast<char*>(ga.Lo[0]) + e0 * C::eb : h;
         store_operands<P>(y, h, l);
@@ -313,14 +318,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t v[32];
             tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + acc * BN + 32 * c, v);
             float y[32];
+            float c2 = 0.0f;  // chunk sum in FP32, accumulated in FP64 (GB300 FP64 is slow)
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const float cxx = __uint_as_float(v[j]);
               const float x = xin[32 * c + j];
               y[j] = br ? fmaf(2.0f, x, -cxx) : cxx;
-              u2 += (double)y[j] * (double)y[j];
+              c2 = fmaf(y[j], y[j], c2);
               if (m0 + row == n0 + 32 * c + j) t1 += (double)y[j];
             }
+            u2 += (double)c2;
             float4* xo = reinterpret_cast<float4*>(xout + 32 * c);
 #pragma unroll
             for (int j = 0; j < 8; ++j) xo[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
@@ -354,10 +361,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---- D from the final iterate (buffer k % 2), report
     {
       const float* X = ga.M[k & 1];
-      for (size_t e = threadIdx.x; e < (size_t)n * n; e += kThreads) {
-        const int r = (int)(e / n), c = (int)(e % n);
-        d.D[e] = (double)X[(size_t)(ro + r) * ga.cols + c];
-      }
+      for (int r = warp; r < n; r += kThreads / 32)
+        for (int c = lane; c < n; c += 32) d.D[(size_t)r * n + c] = (double)X[(size_t)(ro + r) * ga.cols + c];
       if (threadIdx.x == 0 && d.rep) {
         tb_sp2_report* rp = d.rep;
         const double e = s_t1 - s_t2;
@@ -530,21 +535,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       double w = emax - emin;
       if (!(w > 0.0)) w = 1.0;
       const double inv = 1.0 / w;
+      const float invf = (float)inv, emaxf = (float)emax;
       double t1 = 0.0, t2 = 0.0;
       const int segs = ld * (ld / 32);
       for (int seg = (int)rank * kThreads + threadIdx.x; seg < segs; seg += CS * kThreads) {
         const int r = seg / (ld / 32), c0 = 32 * (seg % (ld / 32));
         float y[32];
+        float s2 = 0.0f;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int c = c0 + j;
-          double x = 0.0;
-          if (r < n && c < n) x = ((r == c ? emax : 0.0) - d.H[(size_t)r * n + c]) * inv;
-          y[j] = (float)x;
-          const double xf = y[j];
-          t2 += xf * xf;
-          if (r == c) t1 += xf;
+          float x = 0.0f;
+          // FP32 arithmetic (one rounding of H): |error| ~ 1e-7 |H| / w, the size
+          // of the FP32 rounding of X0 itself
+          if (r < n && c < n) x = ((r == c ? emaxf : 0.0f) - (float)d.H[(size_t)r * n + c]) * invf;
+          y[j] = x;
+          s2 = fmaf(x, x, s2);
+          if (r == c) t1 += (double)x;
         }
+        t2 += (double)s2;
         const size_t e0 = (size_t)(ro + r) * ga.cols + c0;
         float4* dst = reinterpret_cast<float4*>(ga.M[0] + e0);
 #pragma unroll
@@ -680,14 +689,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t v[32];
             tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + acc * BN + 32 * c, v);
             float y[32];
+            float c2 = 0.0f;  // chunk sum in FP32, accumulated in FP64 (GB300 FP64 is slow)
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const float cxx = __uint_as_float(v[j]);
               const float x = xin[32 * c + j];
               y[j] = br ? fmaf(2.0f, x, -cxx) : cxx;
-              u2 += (double)y[j] * (double)y[j];
+              c2 = fmaf(y[j], y[j], c2);
               if (m0 + row == n0 + 32 * c + j) t1 += (double)y[j];
             }
+            u2 += (double)c2;
             float4* xo = reinterpret_cast<float4*>(xout + 32 * c);
 #pragma unroll
             for (int j = 0; j < 8; ++j) xo[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
