@@ -130,6 +130,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def aggregate_replicas(elapsed_ms: float, work: float, device: str) -> tuple[float, float]:
+    """Whole-job figures of independent replicas (one per rank, no collective in
+    the data path): the slowest rank's time and the sum of all ranks' work.
+    Identity without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(elapsed_ms), float(work)
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    w = torch.tensor([work], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
 # ---------------------------------------------------------------- CPU oracle
 
 def cpu_oracle_sample(max_seconds: float = 20.0) -> dict:
@@ -260,12 +275,7 @@ def run_ours(args):
     reps = [report_to_dict(reports[k]) for k in range(args.steps)]
     proj = sum(r["iters"] + r["refine_iters"] for r in reps)
     flops = 2.0 * float(n) ** 3 * proj
-    if world > 1:
-        t = torch.tensor([total_ms, flops], dtype=torch.float64, device="cuda")
-        tmax = t[0:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        total_ms, flops = float(tmax.item()), float(t[1].item())
+    total_ms, flops = aggregate_replicas(total_ms, flops, "cuda")
     value = flops / (total_ms * 1e-3) / 1e12
     last = reps[-1]
 
