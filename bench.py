@@ -3,8 +3,9 @@
 
 One step = one XL-BOMD (Fast-QMMD) step of the 2048-atom water-like system
 (682 O + 1366 H, n = 4094 orbitals, 1.0 g/cc, seed 0): half kick + drift,
-the n update of Eq. Verl_n, H[n], D by SP2 (tensor-core projections + FP64
-refinement), Mulliken charges, forces and energy, half kick.  Every stage
+the n update of Eq. Verl_n, H[n], D by SP2 (tf32x3 tensor-core projections,
+then two FP64-exact refinement projections), Mulliken charges, forces and
+energy, half kick.  Every stage
 runs in libtbmd's CUDA kernels; state stays on the device.
 
 value = SP2 D-matrix throughput: algorithmic flops of the purification
@@ -49,7 +50,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="tf32x3", choices=["tf32", "tf32x3", "bf16", "bf16x3"])
-    ap.add_argument("--refine", type=int, default=3)
+    ap.add_argument("--refine", type=int, default=2, help="FP64 (emulated) refinement projections")
     ap.add_argument("--natoms", type=int, default=2048,
                     help="atoms of the water-like system (2048 = the headline workload)")
     ap.add_argument("--scf-iters", type=int, default=12)
