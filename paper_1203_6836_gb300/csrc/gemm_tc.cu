@@ -73,6 +73,29 @@ __device__ __forceinline__ void tri_tile(int t, int nt, int* I, int* J) {
   *J = i + t;
 }
 
+// Work units of a persistent grid of G CTAs over T tiles: the tiles that
+// would leave the last round less than half full are split into two
+// 64-column halves, so that round is nearly full (T = 528 on 152 CTAs: three
+// rounds of tiles, then 144 halves instead of 72 tiles).
+struct Units {
+  int T, full, U;  // tiles, units before the halves, all units
+};
+__device__ __forceinline__ Units make_units(int T, int G) {
+  const int F = T / G, rem = T - F * G;
+  const bool split = rem > 0 && 2 * rem <= G;
+  return Units{T, split ? F * G : T, split ? F * G + 2 * rem : T};
+}
+// Unit u -> tile t and half (-1: the whole 128-column tile).
+__device__ __forceinline__ void unit_tile(const Units& w, int u, int* t, int* half) {
+  if (u < w.full) {
+    *t = u;
+    *half = -1;
+  } else {
+    *t = w.full + ((u - w.full) >> 1);
+    *half = (u - w.full) & 1;
+  }
+}
+
 template <int P>
 __global__ void __launch_bounds__(kThreads, 1)
     k_sp2_step_tc(SP2StepArgs a, const __grid_constant__ CUtensorMap mh,
@@ -130,7 +153,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int nt = a.ld / BM;
-  const int ntiles = nt * (nt + 1) / 2;
+  const Units wu = make_units(nt * (nt + 1) / 2, gridDim.x);
   const int nk = a.ld / C::bk;
 
   if (threadIdx.x == 0) {
@@ -157,8 +180,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     prefetch_map(&mh);
     if (C::split) prefetch_map(&ml);
     int g = 0, issued = 0;
-    for (int t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x) {
-      int I, J;
+    for (int u = blockIdx.x; u < wu.U && !s_abort; u += gridDim.x) {
+      int t, half, I, J;
+      unit_tile(wu, u, &t, &half);
       tri_tile(t, nt, &I, &J);
       for (int kb = 0; kb < nk; ++kb, ++g) {
         const int s = g % C::stages;
@@ -184,9 +208,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
-    constexpr uint32_t id = idesc(C::tf32 ? 2u : 1u);
+    constexpr uint32_t id128 = idesc(C::tf32 ? 2u : 1u);
+    constexpr uint32_t id64 = idesc(C::tf32 ? 2u : 1u, 128, 64);
     int g = 0, it = 0;
-    for (int t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x, ++it) {
+    for (int u = blockIdx.x; u < wu.U && !s_abort; u += gridDim.x, ++it) {
+      int t, half;
+      unit_tile(wu, u, &t, &half);
+      const uint32_t id = half < 0 ? id128 : id64;
+      // a half unit multiplies by rows [64 half, 64 half + 64) of the B tile:
+      // 8 KB into it, a whole number of 1 KB swizzle atoms
+      const uint32_t boff = half > 0 ? 64 * 128 : 0;
       const int buf = it & 1;
       if (it >= 2 && !mbar_wait(&tempty[buf], ((it >> 1) - 1) & 1, &s_abort)) break;
       tc_fence_after();
@@ -200,10 +231,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int ks = 0; ks < C::bk / C::uk; ++ks) {
           const uint32_t koff = ks * 32;
           const uint64_t ah = sdesc(base + koff);
-          const uint64_t bh = sdesc(base + TILE_BYTES + koff);
+          const uint64_t bh = sdesc(base + TILE_BYTES + boff + koff);
           umma<C::tf32>(d, ah, bh, id, (kb | ks) != 0);
           if constexpr (C::split) {
-            umma<C::tf32>(d, ah, sdesc(base + 3 * TILE_BYTES + koff), id, 1u);
+            umma<C::tf32>(d, ah, sdesc(base + 3 * TILE_BYTES + boff + koff), id, 1u);
             umma<C::tf32>(d, sdesc(base + 2 * TILE_BYTES + koff), bh, id, 1u);
           }
         }
@@ -219,13 +250,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;
     const int row = 32 * q + lane;
     int it = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    for (int u = blockIdx.x; u < wu.U; u += gridDim.x, ++it) {
       const int buf = it & 1;
       if (!mbar_wait(&tfull[buf], (it >> 1) & 1, &s_abort)) break;
       tc_fence_after();
-      int I, J;
+      int t, half, I, J;
+      unit_tile(wu, u, &t, &half);
       tri_tile(t, nt, &I, &J);
-      const int m0 = I * BM, n0 = J * BN;
+      const int m0 = I * BM, n0 = J * BN + (half > 0 ? 64 : 0);
+      const int nchunk = half < 0 ? BN / 32 : 2;
       const bool mirror = I != J;
       const double w = mirror ? 2.0 : 1.0;  // the transposed copy counts too
       const size_t gr = (size_t)(m0 + row);
@@ -235,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       char* lrow = olo ? static_cast<char*>(olo) + (gr * a.ld + n0) * C::eb : hrow;
       double u2 = 0.0, u3 = 0.0;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = 0; c < nchunk; ++c) {
         uint32_t v[32];
         tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + buf * BN + 32 * c, v);
         float y[32];
@@ -256,7 +289,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         if (!mirror) {
-          const int dc = row - 32 * c;
+          // diagonal tile (or one of its halves): element j is on the diagonal
+          // when m0 + row == n0 + 32c + j
+          const int dc = m0 + row - n0 - 32 * c;
           if (dc >= 0 && dc < 32) {
 #pragma unroll
             for (int j = 0; j < 32; ++j)
