@@ -395,7 +395,10 @@ def run_ours(args):
             "sp2": {"projections_per_step": proj / args.steps, "last_step": {k: last[k] for k in (
                 "status", "iters", "refine_iters", "trace", "idem_trace")}},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         # DRAM bytes per launch (read + write) of the current kernel, from the
+                         # ncu capture in profiles/k_sp2_step_tc_tf32x3_n4094.md (tf32x3, n = 4094)
+                         "traffic": 573.75e6 if (args.precision == "tf32x3" and n == 4094) else None,
                          "kernel": f"k_sp2_step_tc<{args.precision}>",
                          "peak_source": f"{peaks['source']} bf16_tflops_sustained x {ratio} ({'tf32' if tf else 'bf16'})",
                          "mma_per_product": mmas, "upper_triangle_tiles": tri_frac,
