@@ -795,12 +795,8 @@ int run_bsr(tb_ctx* ctx, const double* H, int n, double nocc, const tb_sp2_opts*
   TB_LAUNCH_CHECK(ctx);
 
   using Cf = Prec<P>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    TB_CUDA_TRY(ctx, cudaFuncSetAttribute(k_bsr_step_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          Cf::smem_bytes));
-    attr_set = true;
-  }
+  static unsigned long long attr_done = 0;
+  if (int rc_attr = tb_smem_attr(ctx, k_bsr_step_tc<P>, Cf::smem_bytes, &attr_done)) return rc_attr;
   const int grid = std::max(1, std::min(ctx->sm_count, kMaxGrid));
   tb_prof_mark(ctx, 0, 0, s);
   for (int k = 0; k <= o->max_iter; ++k) {

@@ -80,6 +80,18 @@ int tb_fail(tb_ctx* ctx, int code, const char* fmt, ...);
 
 static inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Raise a kernel's dynamic shared-memory limit once per device (function
+// attributes belong to the device's context); *done is the caller's static
+// bit mask of devices already set.
+template <typename K>
+int tb_smem_attr(tb_ctx* ctx, K kernel, int bytes, unsigned long long* done) {
+  const unsigned long long bit = 1ull << (ctx->device & 63);
+  if (*done & bit) return TB_OK;
+  TB_CUDA_TRY(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  *done |= bit;
+  return TB_OK;
+}
+
 // ----------------------------------------------------------------- model
 
 // Device copy of the model constants with the App. D tail coefficients

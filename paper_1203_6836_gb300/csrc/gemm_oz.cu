@@ -366,11 +366,8 @@ size_t sp2_oz_slice_bytes(int ld) { return (size_t)kS * ld * ld * sizeof(__nv_bf
 int sp2_oz_step(tb_ctx* ctx, const SP2StepArgs& a, const double* Xin, double* Xout, void* slices, int* exps,
                 cudaStream_t s) {
   if (a.ld > 4096 || a.ld % kTile) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "emulated FP64 needs ld <= 4096");
-  static bool attr_set = false;
-  if (!attr_set) {
-    TB_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sp2_step_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
-    attr_set = true;
-  }
+  static unsigned long long attr_done = 0;
+  if (int rc_attr = tb_smem_attr(ctx, k_sp2_step_oz, kSmem, &attr_done)) return rc_attr;
   k_oz_split<<<(a.ld * 32 + 255) / 256, 256, 0, s>>>(a.st, Xin, a.ld, static_cast<__nv_bfloat16*>(slices), exps);
   TB_LAUNCH_CHECK(ctx);
   SliceMaps maps;

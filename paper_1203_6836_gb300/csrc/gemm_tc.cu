@@ -360,12 +360,8 @@ int launch_step(tb_ctx* ctx, const SP2StepArgs& a, const CUtensorMap* mh, const 
     TB_LAUNCH_CHECK(ctx);
     return TB_OK;
   }
-  static bool attr_set = false;
-  if (!attr_set) {
-    TB_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sp2_step_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          C::smem_bytes));
-    attr_set = true;
-  }
+  static unsigned long long attr_done = 0;
+  if (int rc_attr = tb_smem_attr(ctx, k_sp2_step_tc<P>, C::smem_bytes, &attr_done)) return rc_attr;
   const int grid = sp2_tc_num_parts(ctx, a.ld);
   k_sp2_step_tc<P><<<grid, kThreads, C::smem_bytes, s>>>(a, *mh, *ml, Xin, Xout, ohi, olo);
   TB_LAUNCH_CHECK(ctx);
@@ -624,11 +620,8 @@ template <int P>
 int launch_gemm(tb_ctx* ctx, const GemmArgs& g, const CUtensorMap* ah, const CUtensorMap* al,
                 const CUtensorMap* bh, const CUtensorMap* bl, cudaStream_t s) {
   using C = Prec<P>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    TB_CUDA_TRY(ctx, cudaFuncSetAttribute(k_gemm_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem_bytes));
-    attr_set = true;
-  }
+  static unsigned long long attr_done = 0;
+  if (int rc_attr = tb_smem_attr(ctx, k_gemm_tc<P>, C::smem_bytes, &attr_done)) return rc_attr;
   k_gemm_tc<P><<<sp2_tc_num_parts(ctx, g.ld), kThreads, C::smem_bytes, s>>>(g, *ah, *al, *bh, *bl);
   TB_LAUNCH_CHECK(ctx);
   return TB_OK;

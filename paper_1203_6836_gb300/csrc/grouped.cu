@@ -862,11 +862,8 @@ GArgs make_args(const Plan& p, char* base) {
 template <int P, int BN>
 int launch(tb_ctx* ctx, const Plan& p, char* base, int grid, cudaStream_t s) {
   using G = GCfg<P, BN>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    TB_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sp2_grouped<P, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::smem));
-    attr_set = true;
-  }
+  static unsigned long long attr_done = 0;
+  if (int rc_attr = tb_smem_attr(ctx, k_sp2_grouped<P, BN>, G::smem, &attr_done)) return rc_attr;
   const GArgs ga = make_args(p, base);
   const CUtensorMap* bh = BN == 64 ? p.bh64 : p.bh128;
   const CUtensorMap* bl = BN == 64 ? p.bl64 : p.bl128;
@@ -881,12 +878,8 @@ int launch(tb_ctx* ctx, const Plan& p, char* base, int grid, cudaStream_t s) {
 template <int P, int CS>
 int launch_cl(tb_ctx* ctx, const Plan& p, char* base, cudaStream_t s, int* grid_out) {
   using G = GCfg<P, BM>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    TB_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sp2_grouped_cl<P, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          G::smem));
-    attr_set = true;
-  }
+  static unsigned long long attr_done = 0;
+  if (int rc_attr = tb_smem_attr(ctx, k_sp2_grouped_cl<P, CS>, G::smem, &attr_done)) return rc_attr;
   const GArgs ga = make_args(p, base);
   cudaLaunchConfig_t cfg{};
   cudaLaunchAttribute attr[1];
