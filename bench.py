@@ -595,6 +595,7 @@ def run_sparse(args):
     peaks = measured_peaks()
     peak = peaks["bf16_tflops_sustained"] * 0.5
     nsb = (n + 127) // 128
+    Prec_eb = 4 if args.precision.startswith("tf32") else 2
     # dense FP64 path on the 1/8-size subsystem (2048 atoms) for context
     # end to end: H from pinned host memory, D back
     hH = torch.empty(H.shape, dtype=torch.float64, pin_memory=True).copy_(H)
@@ -616,6 +617,61 @@ def run_sparse(args):
     density.sp2(Ho, w.n_occ(P), max_iter=2, tol=0.0, tau=1e-5)
     dt = time.perf_counter() - t0
     no = Ho.shape[0]
+    # XL-BOMD with the block-sparse D: steps/s of the same system, then the
+    # energy drift of 50 steps on the 1/8-size Morton subsystem against the dense
+    # path (tf32x3 products + two FP64-exact refinements)
+    from paper_1203_6836_gb300.device import MDState, xl_params
+    from workloads import XLParams, thermal_velocities
+    from oracle import md as omd
+    XL = XLParams()
+    xp = xl_params(XL.dt, XL.kappa, XL.alpha, XL.c)
+    del sol, D, H, G, hH, hD
+    torch.cuda.empty_cache()
+    M = s.masses(P)
+    st = MDState(ds, thermal_velocities(M, 300.0, seed=100), M, s.n_occ(P), XL.K, opts)
+    tbmd.xlbomd_init(ctx, TP, st.st, xp, opts, 1e-6, 2)
+    tbmd.xlbomd_step(ctx, TP, st.st, xp, opts)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    md_steps = 3
+    e0.record(stream)
+    for _ in range(md_steps):
+        tbmd.xlbomd_step(ctx, TP, st.st, xp, opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    md_ms = e0.elapsed_time(e1) / md_steps
+    del st
+    torch.cuda.empty_cache()
+    # the drift study runs on water-like vapour (125 H2O-like molecules, 0.1 g/cc,
+    # Morton order): the 1.0 g/cc random recipe has no T_e = 0 SCF fixed point
+    # and its XL-BOMD diverges on every path; the vapour keeps a gap (0.1-0.7 eV)
+    # at this size with kappa = 0.06 kappa0, while at 683 molecules the T_e = 0
+    # gap closes and both paths diverge
+    import dataclasses
+    from workloads import molecular_liquid
+    XLv = dataclasses.replace(XL, kappa_scale=0.06)
+    xp = xl_params(XLv.dt, XLv.kappa, XLv.alpha, XLv.c)
+    sub = molecular_liquid(125, 0.1, seed=0, morton=True)
+    Ms = sub.masses(P)
+    v0 = thermal_velocities(Ms, 300.0, seed=100)
+    drift = {}
+    for label, o in (("block_sparse_tau1e-5", sp2_opts(args.precision, max_iter=60, tau=1e-5)),
+                     ("dense_refined", sp2_opts(args.precision, max_iter=100, tol=1e-10, refine=2))):
+        dsub = DeviceSystem(sub.R, sub.types, sub.box)
+        st = MDState(dsub, v0, Ms, sub.n_occ(P), XLv.K, o)
+        tbmd.xlbomd_init(ctx, TP, st.st, xp, o, 1e-8, 200)
+        E = []
+        for k in range(51):
+            if k:
+                tbmd.xlbomd_step(ctx, TP, st.st, xp, o)
+            E.append(st.energies[0].item())
+        sig, slope = omd.energy_drift(E, XLv.dt, sub.natoms)
+        drift[label] = {"sigma_eV": sig, "drift_eV_per_atom_ps": slope, "E_tot": E}
+        del st
+    dE = float(np.max(np.abs(np.array(drift["block_sparse_tau1e-5"]["E_tot"]) -
+                             np.array(drift["dense_refined"]["E_tot"]))))
+    for v in drift.values():
+        del v["E_tot"]
     line = _common(args, "thresholded block-sparse SP2: block-product TFLOP/s", value, "TFLOP/s",
                    total / args.steps, f"{args.precision}+f64",
                    f"{s.natoms} atoms, n={n}, 1.0 g/cc, Morton order, seed 0; SP2 with "
@@ -625,6 +681,9 @@ def run_sparse(args):
                         "stored_blocks_of_D": last["blocks"], "block_fill": last["blocks"] / nsb ** 2,
                         "block_products_per_D": last["block_products"],
                         "dense_equivalent_tflops": 2.0 * n ** 3 * last["iters"] / (total / args.steps * 1e-3) / 1e12},
+                   operand_stream={"GB_per_s": 4 * 128 * 128 * Prec_eb * (last["block_products"] / 2) / max(1, last["iters"])
+                                   / (avg_num * 1e-3) / 1e9, "hbm_peak_GB_per_s": peaks["hbm_gbs"],
+                                   "note": "operand tiles streamed by the numeric kernel (upper blocks) per launch time"},
                    roofline={"bound": "tensor", "achieved": per_launch / (avg_num * 1e-3) / 1e12, "peak": peak,
                              "unit": "TFLOP/s", "frac": per_launch / (avg_num * 1e-3) / 1e12 / peak,
                              "traffic": None, "kernel": f"k_bsr_step_tc<{args.precision}>",
@@ -634,6 +693,10 @@ def run_sparse(args):
                                  "kind": "oracle",
                                  "sample": f"2 thresholded FP64 projections (NumPy, dense storage) of the "
                                            f"n={no} 1/8-size Morton system, {dt:.1f} s"},
+                   xlbomd={"steps_per_s": 1e3 / md_ms, "ms_per_step": md_ms, "system": f"{s.natoms} atoms, tau=1e-5"},
+                   drift_50_steps={"system": f"water-like vapour, {sub.natoms} atoms (125 H2O-like molecules), "
+                                             "0.1 g/cc, Morton order, T_e = 0, kappa 0.06 kappa0", **drift,
+                                   "max_abs_dE_tot_eV": dE},
                    e2e={"value": 2.0 * 128 ** 3 * r_e2e["block_products"] / e2e_s / 1e12, "unit": "TFLOP/s",
                         "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8},
                    gpu_launches=args.steps * (8 * 61 + 8), clocks=clocks)

@@ -290,12 +290,13 @@ def config3_system(seed: int = 0) -> WaterSystem:
 
 
 def molecular_liquid(n_mol: int, density: float = 1.0, seed: int = 0, bond: float = 0.96,
-                     angle_deg: float = 104.5, jitter: float = 0.1,
+                     angle_deg: float = 104.5, jitter: float = 0.1, morton: bool = False,
                      p: ModelParams = ModelParams()) -> WaterSystem:
     """n_mol H2O-like molecules at `density` g/cc: O atoms on the first n_mol
     sites (row order) of the smallest cubic grid that holds them, Gaussian
     jitter, random orientations (O-H `bond` A, H-O-H `angle_deg`).  Atom
-    order: all O, then the H pairs in molecule order."""
+    order: all O, then the H pairs in molecule order, or Morton order of the
+    positions with `morton`."""
     rng = np.random.default_rng(seed)
     box = box_from_density(n_mol, 2 * n_mol, density, p)
     m = 1
@@ -314,6 +315,10 @@ def molecular_liquid(n_mol: int, density: float = 1.0, seed: int = 0, bond: floa
         Hs += [O + Q @ u1, O + Q @ u2]
     R = np.mod(np.array(Os + Hs), box)
     types = np.array([TYPE_O] * len(Os) + [TYPE_H] * len(Hs), dtype=np.int32)
+    if morton:
+        perm = _morton_order(R, float(box))
+        R = R[perm].copy()
+        types = types[perm].copy()
     return WaterSystem(R=R, types=types, box=float(box), seed=seed)
 
 
