@@ -44,6 +44,7 @@ constexpr int kMaxNsb = MW * 32;
 constexpr int kThreads = 192;      // numeric kernel: TMA, MMA, 4 epilogue warps
 constexpr int kTiles = SB * SB;    // elements per super-block
 constexpr int kMaxGrid = 256;      // persistent numeric grid (<= SMs)
+constexpr int kBand = 8;           // block rows whose outputs the numeric kernel walks together
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
@@ -66,7 +67,8 @@ struct Sym {
   int* pcnt;         // [cap]
   int* pair_ptr;     // [cap + 1]
   int2* pairs;       // [pcap]
-  int* scal;         // [4]: blocks of the new pattern, pairs
+  int* scal;         // [4]: blocks of the new pattern, pairs, upper blocks
+  int* order;        // [cap] upper output blocks in the numeric kernel's order
   uint16_t* flags;   // [nsb * nsb] X0 sub-block keep masks
 };
 
@@ -390,6 +392,54 @@ __global__ void k_bsr_pairs(Args a, Buf bo, Buf bn, Sym sy) {
   }
 }
 
+// Upper output blocks (I <= J) in (band of kBand block rows, column J, row I)
+// order.  The persistent numeric kernel takes them in this order, so the CTAs
+// working at the same time cover a few columns of one band: they share the
+// (I, K) tiles of the band's rows and the (J, K) tiles of those columns in L2
+// instead of each streaming its own.  One block; one warp per band.
+__global__ void __launch_bounds__(1024) k_bsr_order(Args a, Buf bn, Sym sy) {
+  __shared__ int s_off[kMaxNsb / kBand + 1];
+  if (a.st->done || a.st->err) return;
+  const int nbands = (a.nsb + kBand - 1) / kBand;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int b = warp; b < nbands; b += nw) {
+    int c = 0;
+    for (int I = b * kBand; I < min(a.nsb, (b + 1) * kBand); ++I) {
+      if (lane < MW) {
+        uint32_t m = sy.cand[I * MW + lane];
+        const int lo = I - 32 * lane;  // keep bits J >= I
+        if (lo >= 32) m = 0u;
+        else if (lo > 0) m &= ~((1u << lo) - 1u);
+        c += __popc(m);
+      }
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) s_off[b] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int b = 0; b < nbands; ++b) {
+      const int v = s_off[b];
+      s_off[b] = acc;
+      acc += v;
+    }
+    sy.scal[2] = acc;
+  }
+  __syncthreads();
+  for (int b = warp; b < nbands; b += nw) {
+    int pos = s_off[b];
+    const int I0 = b * kBand;
+    const int I = I0 + lane;
+    for (int J = I0; J < a.nsb; ++J) {
+      const bool has = lane < kBand && I < a.nsb && I <= J && ((sy.cand[I * MW + (J >> 5)] >> (J & 31)) & 1u);
+      const unsigned m = __ballot_sync(0xffffffffu, has);
+      if (has) sy.order[pos + __popc(m & ((1u << lane) - 1u))] = bn.row_ptr[I] + popc_below(sy.cand + I * MW, J);
+      pos += __popc(m);
+    }
+  }
+}
+
 // Persistent numeric projection.
 template <int P>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -404,7 +454,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   SP2State* st = a.st;
   if (st->done || st->err) return;
   const int br = (int)((st->branch[a.k >> 6] >> (a.k & 63)) & 1ull);
-  const int nb = sy.scal[0];
+  const int nu = sy.scal[2];  // upper output blocks, walked in sy.order
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   if (threadIdx.x == 0) {
@@ -431,8 +481,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     prefetch_map(&mh);
     if (C::split) prefetch_map(&ml);
     int g = 0, issued = 0;
-    for (int o = blockIdx.x; o < nb && !s_abort; o += gridDim.x) {
-      if (bn.col[o] < sy.out_row[o]) continue;  // mirror of an upper block
+    for (int u = blockIdx.x; u < nu && !s_abort; u += gridDim.x) {
+      const int o = sy.order[u];
       const int p0 = sy.pair_ptr[o], p1 = sy.pair_ptr[o + 1];
       for (int p = p0; p < p1 && !s_abort; ++p) {
         const int2 pr = sy.pairs[p];
@@ -461,8 +511,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t id = idesc(C::tf32 ? 2u : 1u);
     int g = 0, it = 0;
-    for (int o = blockIdx.x; o < nb && !s_abort; o += gridDim.x) {
-      if (bn.col[o] < sy.out_row[o]) continue;
+    for (int u = blockIdx.x; u < nu && !s_abort; u += gridDim.x) {
+      const int o = sy.order[u];
       const int buf = it & 1;
       if (it >= 2 && !mbar_wait(&tempty[buf], ((it >> 1) - 1) & 1, &s_abort)) break;
       tc_fence_after();
@@ -499,8 +549,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row = 32 * q + lane;
     double t1 = 0.0, t2 = 0.0;
     int it = 0;
-    for (int o = blockIdx.x; o < nb; o += gridDim.x) {
-      if (bn.col[o] < sy.out_row[o]) continue;
+    for (int u = blockIdx.x; u < nu; u += gridDim.x) {
+      const int o = sy.order[u];
       const int buf = it & 1;
       ++it;
       if (!mbar_wait(&tfull[buf], ((it - 1) >> 1) & 1, &s_abort)) break;
@@ -652,7 +702,7 @@ __global__ void k_bsr_report(SP2State* st, Args a, Buf b0, Buf b1, tb_sp2_report
 struct BsrLayout {
   int n, ld, nsb, cap, pcap;
   size_t off_state, off_bparts, off_parts, off_scal, off_flags, off_cand, off_cnt, off_outrow, off_oldidx,
-      off_pcnt, off_pptr, off_pairs;
+      off_pcnt, off_pptr, off_pairs, off_order;
   size_t off_rp[2], off_col[2], off_nz[2], off_st[2], off_lv[2], off_val[2], off_hi[2], off_lo[2];
   size_t total;
   int nparts;
@@ -688,6 +738,7 @@ BsrLayout bsr_layout(int n, int prec, int bpr, int nsm) {
   L.off_pcnt = take(sizeof(int) * L.cap);
   L.off_pptr = take(sizeof(int) * (L.cap + 1));
   L.off_pairs = take(sizeof(int2) * (size_t)L.pcap);
+  L.off_order = take(sizeof(int) * L.cap);
   for (int b = 0; b < 2; ++b) {
     L.off_rp[b] = take(sizeof(int) * (L.nsb + 1));
     L.off_col[b] = take(sizeof(int) * L.cap);
@@ -737,6 +788,7 @@ int run_bsr(tb_ctx* ctx, const double* H, int n, double nocc, const tb_sp2_opts*
   sy.pair_ptr = reinterpret_cast<int*>(base + L.off_pptr);
   sy.pairs = reinterpret_cast<int2*>(base + L.off_pairs);
   sy.scal = reinterpret_cast<int*>(base + L.off_scal);
+  sy.order = reinterpret_cast<int*>(base + L.off_order);
   sy.flags = reinterpret_cast<uint16_t*>(base + L.off_flags);
   Buf b[2];
   for (int i = 0; i < 2; ++i) {
@@ -812,6 +864,7 @@ int run_bsr(tb_ctx* ctx, const double* H, int n, double nocc, const tb_sp2_opts*
     k_bsr_fill_out<<<L.nsb, 256, 0, s>>>(a, bo, bn, sy);
     k_bsr_scan_pairs<<<1, 1024, 0, s>>>(a, sy);
     k_bsr_pairs<<<std::max(1, std::min(L.cap, 4096) / 128 + 1), 128, 0, s>>>(a, bo, bn, sy);
+    k_bsr_order<<<1, 1024, 0, s>>>(a, bn, sy);
     tb_prof_mark(ctx, 1, 2 * k, s);
     k_bsr_step_tc<P><<<grid, kThreads, Cf::smem_bytes, s>>>(a, mh[k & 1], ml[k & 1], bo, bn, sy);
     TB_LAUNCH_CHECK(ctx);
