@@ -405,10 +405,15 @@ __global__ void __launch_bounds__(256) k_forces(ModelDev m, int N, const int32_t
   const double na = n_aux[a];
   double f[3] = {0.0, 0.0, 0.0};
   double e_band = 0.0, e_pair = 0.0, e_scc = 0.0;
-  for (int b = lane; b < N; b += 32) {
-    e_scc += G[(size_t)a * N + b] * n_aux[b];
+  // Pass 1 (lanes over all b): the gamma-n sum and an FP32 screen; the atoms b
+  // with an image in range are compacted into a shared-memory list.  Pass 2:
+  // all 32 lanes work through the list (about 3 of every 32 atoms are in range
+  // at 1 g/cc), each lane summing its entries in list order.
+  constexpr int kNb = 512;
+  __shared__ int s_nb_all[8][kNb];  // one list per warp (up to 256 threads)
+  int* s_nb = s_nb_all[threadIdx.x >> 5];
+  auto pair_terms = [&](int b) {
     const double* Rb = R + 3 * b;
-    if (b != a && !screen_f32(Ra, Rb, (float)m.box, (float)m.range)) continue;
     const int tb = types[b], ob = offs[b];
     const double wb = 2.0 * q[b] - n_aux[b];
     const double nb = n_aux[b];
@@ -453,6 +458,24 @@ __global__ void __launch_bounds__(256) k_forces(ModelDev m, int N, const int32_t
             for (int k = 0; k < 3; ++k) f[k] += c * l[k];
           }
         }
+    };
+  int cnt = 0;
+  for (int b0 = 0; b0 < N; b0 += 32) {
+    const int b = b0 + lane;
+    bool hit = false;
+    if (b < N) {
+      e_scc += G[(size_t)a * N + b] * n_aux[b];
+      hit = b == a || screen_f32(Ra, R + 3 * b, (float)m.box, (float)m.range);
+    }
+    const unsigned mk = __ballot_sync(0xffffffffu, hit);
+    if (hit) s_nb[cnt + __popc(mk & ((1u << lane) - 1u))] = b;
+    cnt += __popc(mk);
+    if (cnt > kNb - 32 || b0 + 32 >= N) {
+      __syncwarp();
+      for (int e = lane; e < cnt; e += 32) pair_terms(s_nb[e]);
+      __syncwarp();
+      cnt = 0;
+    }
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) f[k] = warp_sum(f[k]);
