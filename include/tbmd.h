@@ -258,10 +258,11 @@ int dm_fermi_workspace_size(int n, const tb_fermi_opts* opts, size_t* bytes);
  * recursive Fermi-operator expansion: from X0 = I/2 - beta/2^(m+2) (H - mu I),
  * m steps X <- X^2 [X^2 + (I - X)^2]^-1, each doubling beta, carried out on
  * E = X - I/2 as E <- 2E (I + 4E^2)^-1 (inverse by Newton-Schulz).  mu: safeguarded Newton steps with dTr D/dmu =
- * beta Tr[D(I - D)] inside a bisection bracket, all on the device.  The accepted expansion is
- * shifted by its Newton step dmu to first order, D + beta dmu D(I - D) (exact trace), whenever
- * the neglected term, bounded by |beta dmu| |Tr D - N| / 2 in Frobenius norm, is below
- * 1e-7 sqrt(n); a larger step runs another expansion.
+ * beta Tr[D(I - D)] inside a bisection bracket, all on the device.  After each expansion the
+ * products E^2 and E^3 give D(I - D) and D(I - D)(I - 2D); the expansion is accepted and shifted
+ * by u = beta dmu to second order, D + u D(I - D) + u^2/2 D(I - D)(I - 2D), with u from the trace
+ * condition, whenever the remainder bound |u|^3/6 Tr[D(I - D)] (Frobenius) is below 1e-7 sqrt(n);
+ * otherwise the Newton step starts another expansion.
  *   H [n*n], D [n*n] (FP64); mu: device double, in = initial guess (NaN: the
  *   spectral midpoint), out = chemical potential of D; report: device or NULL. */
 int dm_fermi(tb_ctx* ctx, const double* H, int n, double n_occ, double kT, const tb_fermi_opts* opts,
@@ -322,10 +323,11 @@ typedef struct {
                            device count, which also advances in graph replays) */
   double kT;            /* electronic temperature (eV); > 0: D by dm_fermi (Eq. EL_4c), else SP2 */
   tb_fermi_opts fermi;  /* options of dm_fermi when kT > 0 */
-  double* mu;           /* device double[3] (kT > 0): [0] the chemical potential passed to and
-                           returned by dm_fermi, [1], [2] the values of the last two steps
-                           (NaN until known); each step starts dm_fermi from the linear
-                           extrapolation 2 mu[1] - mu[2] */
+  double* mu;           /* device double[4] (kT > 0): [0] the chemical potential passed to and
+                           returned by dm_fermi, [1..3] the values of the last three steps
+                           (NaN until known); each step starts dm_fermi from the quadratic
+                           extrapolation 3 mu[1] - 3 mu[2] + mu[3] (linear or constant while
+                           fewer are known) */
   tb_fermi_report* fermi_report;  /* device, may be NULL */
 } tb_md_state;
 

@@ -35,14 +35,17 @@ namespace {
 
 constexpr int kTile = 128;
 constexpr int kMaxMu = 40;
-// First-order canonical correction: the last expansion is accepted and shifted
-// by the Newton step dmu = -(Tr D - N) / (beta Tr[D(I - D)]) as
-// D(mu + dmu) = D + beta dmu D(I - D) + R, which makes the trace exact to
-// first order.  D(I - D) is positive semi-definite with eigenvalues <= 1/4, so
-// ||R||_F <= (beta dmu)^2 / 2 * Tr[D(I - D)] = |beta dmu| |Tr D - N| / 2; the
-// shift replaces another expansion when that bound is below kCorrFro sqrt(n)
-// and |beta dmu| <= kCorrMax (first-order regime).  Gapped systems (small
-// Tr[D(I - D)]) accept large shifts inside the gap, metallic ones small ones.
+// Canonical shift: the last expansion is accepted and shifted by u = beta dmu
+// to second order,
+//   D(mu + dmu) = D + u D(I - D) + u^2/2 D(I - D)(I - 2D) + R,
+// with D(I - D) = I/4 - E^2 and D(I - D)(I - 2D) = 2E^3 - E/2 (two products,
+// E^2 and E^3, after every expansion), u the root of the trace condition
+// Tr D + u Tr[D(I-D)] + u^2/2 Tr[D(I-D)(I-2D)] = N_occ near -(Tr D - N)/Tr[D(I-D)].
+// The remainder involves the third derivative beta^3 f(1-f)(1-6f+6f^2), whose
+// last factor is at most 1 in magnitude, so ||R||_F <= |u|^3/6 Tr[D(I - D)]
+// (D(I - D) is positive semi-definite with eigenvalues <= 1/4).  The shift
+// replaces another expansion when that bound is below kCorrFro sqrt(n) and
+// |u| <= kCorrMax.
 constexpr double kCorrFro = 1e-7;
 constexpr double kCorrMax = 0.1;
 
@@ -53,8 +56,9 @@ struct FoeState {
   double emin, emax;
   int done, iters, capped, err;
   int ran;     // 1: the last k_foe_mu evaluated an expansion (it was not skipped)
-  int nocorr;  // 0: apply the first-order correction by dmu to the last expansion
-  double dmu;
+  int nocorr;  // 0: apply the canonical shift u to the last expansion
+  double dmu;  // u / beta
+  double u;
   double tr[kMaxMu + 1], trdd[kMaxMu + 1], mus[kMaxMu + 1];
 };
 
@@ -116,8 +120,8 @@ __global__ void __launch_bounds__(256) k_foe_z1(const FoeState* st, int n, int l
 // is the device count st->iters.  Inside a while graph node (cond != 0) the
 // condition is cleared on every stop: converged, capped, or an error flag
 // raised by a product of this expansion.
-__global__ void k_foe_mu(FoeState* st, const double* parts, int np, int n, double nocc, double beta, double tol,
-                         int max_it, cudaGraphConditionalHandle handle, int cond) {
+__global__ void k_foe_mu(FoeState* st, const double* parts, const double* parts3, int np, int n, double nocc,
+                         double beta, double tol, int max_it, cudaGraphConditionalHandle handle, int cond) {
   if (st->done || st->err || st->iters >= max_it) {
     if (threadIdx.x == 0) {
       st->ran = 0;
@@ -125,37 +129,44 @@ __global__ void k_foe_mu(FoeState* st, const double* parts, int np, int n, doubl
     }
     return;
   }
-  double x = 0.0, y = 0.0;
+  double x = 0.0, y = 0.0, z = 0.0;
   for (int i = threadIdx.x; i < np; i += 32) {
     x += parts[2 * i];
     y += parts[2 * i + 1];
+    z += parts3[2 * i];
   }
-  x = warp_sum(x);
-  y = warp_sum(y);
+  x = warp_sum(x);  // Tr E
+  y = warp_sum(y);  // ||E||_F^2
+  z = warp_sum(z);  // Tr E^3
   if (threadIdx.x != 0) return;
   const int it = st->iters;
   const double mu = st->mu;
   const double trd = 0.5 * n + x;
-  const double trdd = 0.25 * n - y;  // Tr D(I - D)
-  x = trd;
-  y = trd - trdd;  // ||D||_F^2
-  st->tr[it] = x;
-  st->trdd[it] = x - y;
+  const double t1 = 0.25 * n - y;        // Tr D(I - D)
+  const double t2 = 2.0 * z - 0.5 * x;   // Tr D(I - D)(I - 2D)
+  st->tr[it] = trd;
+  st->trdd[it] = t1;
   st->mus[it] = mu;
   st->iters = it + 1;
   st->ran = 1;
-  const double dev = x - nocc;
-  const double slope = beta * (x - y);
-  const double step = slope > 1e-12 ? -dev / slope : NAN;
-  const bool shift = fabs(beta * step) <= kCorrMax &&
-                     0.5 * fabs(beta * step) * fabs(dev) <= kCorrFro * sqrt((double)max(n, 1));
+  const double dev = trd - nocc;
+  const double step = t1 > 1e-12 ? -dev / (beta * t1) : NAN;  // Newton step on mu
+  double u = beta * step;
+  for (int k = 0; k < 3 && isfinite(u); ++k) {  // root of dev + t1 u + t2 u^2/2 near the Newton step
+    const double g = dev + u * (t1 + 0.5 * t2 * u), gp = t1 + t2 * u;
+    if (!(gp > 0.0)) break;
+    u -= g / gp;
+  }
+  const bool shift = isfinite(u) && fabs(u) <= kCorrMax &&
+                     fabs(u) * u * u / 6.0 * t1 <= kCorrFro * sqrt((double)max(n, 1));
   if (shift) {
-    // accept this expansion with the first-order shift to mu + step
+    // accept this expansion with the second-order shift to mu + u / beta
     st->done = 1;
     st->nocorr = 0;
-    st->dmu = step;
-    st->tr[it] = x + slope * step;
-    st->mus[it] = mu + step;
+    st->u = u;
+    st->dmu = u / beta;
+    st->tr[it] = trd + u * (t1 + 0.5 * t2 * u);
+    st->mus[it] = mu + u / beta;
   } else if (fabs(dev) <= tol) {
     st->done = 1;
   } else if (it + 1 >= max_it) {
@@ -180,17 +191,20 @@ __global__ void __launch_bounds__(256) k_foe_keep(const FoeState* st, size_t cou
     dst[e] = src[e];
 }
 
-// E <- E + beta dmu (I/4 - E^2) on the n x n block (D(I - D) = I/4 - E^2),
-// with T = E^2 from the product kernel; skipped unless the correction applies.
-__global__ void __launch_bounds__(256) k_foe_correct(const FoeState* st, int n, int ld, double beta,
-                                                     const float* __restrict__ T, float* __restrict__ E) {
+// E <- E + u (I/4 - E^2) + u^2/2 (2 E^3 - E/2) on the n x n block, with
+// T = E^2 and U = E^3 from the product kernel; skipped unless the shift applies.
+__global__ void __launch_bounds__(256) k_foe_correct(const FoeState* st, int n, int ld, const float* __restrict__ T,
+                                                     const float* __restrict__ U, float* __restrict__ E) {
   if (st->nocorr) return;
-  const float c = (float)(beta * st->dmu);
+  const float u = (float)st->u, h = 0.5f * u * u;
   const size_t total = (size_t)n * n;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / n), col = (int)(e % n);
     const size_t i = (size_t)r * ld + col;
-    E[i] = fmaf(c, (r == col ? 0.25f : 0.0f) - T[i], E[i]);
+    const float x = E[i];
+    const float first = (r == col ? 0.25f : 0.0f) - T[i];
+    const float second = 2.0f * U[i] - 0.5f * x;
+    E[i] = fmaf(h, second, fmaf(u, first, x));
   }
 }
 
@@ -222,7 +236,7 @@ __global__ void __launch_bounds__(256) k_foe_finalize(const FoeState* st, int n,
 
 struct FoeLayout {
   int ld;
-  size_t off_state, off_bparts, off_parts, off_mat[5][3], off_res, total;
+  size_t off_state, off_bparts, off_parts, off_parts3, off_mat[5][3], off_res, total;
   int nparts;
 };
 
@@ -242,6 +256,7 @@ FoeLayout foe_layout(int n, int prec) {
   L.off_state = take(sizeof(FoeState));
   L.off_bparts = take(sizeof(double) * 2 * ((n + 7) / 8));
   L.off_parts = take(sizeof(double) * 2 * (size_t)L.nparts);
+  L.off_parts3 = take(sizeof(double) * 2 * (size_t)L.nparts);
   for (int i = 0; i < 5; ++i) {
     L.off_mat[i][0] = take(sizeof(float) * nn);
     L.off_mat[i][1] = take(eb * nn);
@@ -279,6 +294,7 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
   FoeState* st = reinterpret_cast<FoeState*>(base + L.off_state);
   double* bparts = reinterpret_cast<double*>(base + L.off_bparts);
   double* parts = reinterpret_cast<double*>(base + L.off_parts);
+  double* parts3 = reinterpret_cast<double*>(base + L.off_parts3);
   Mat M[5];  // X, A, Z, T, Y (next X)
   for (int i = 0; i < 5; ++i) {
     M[i].m = reinterpret_cast<float*>(base + L.off_mat[i][0]);
@@ -315,7 +331,6 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
   if ((rc = tb_loop_begin(ctx, s, &loop))) return rc;
   cudaStream_t ls = loop.body_stream;
   const int rounds = loop.graph ? 1 : o->mu_iters;
-  int* gskip = skip;
   auto gemm = [&](Mat& A, Mat& B, Mat& out, float alpha, float betac, const float* E, float gamma,
                   double* prt) -> int {
     GemmArgs g{};
@@ -329,12 +344,13 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
     g.ohi = out.hi;
     g.olo = out.lo;
     g.parts = prt;
-    g.skip = gskip;
+    g.skip = skip;
     g.err = errp;
     return tc_gemm(ctx, o->precision, g, &A.mh, &A.ml, &B.mh, &B.ml, ls);
   };
-  Mat* xf = &M[0];  // final iterate and a free matrix after an expansion
+  Mat* xf = &M[0];  // final iterate, E^2 and E^3 after an expansion
   Mat* af = &M[1];
+  Mat* zf = &M[2];
   auto expansion = [&]() -> int {
     int r;
     Mat* X = &M[0];
@@ -363,25 +379,26 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
       if ((r = gemm(*X, *Z, *Y, 2.0f, 0.0f, nullptr, 0.0f, last ? parts : nullptr))) return r;
       std::swap(X, Y);
     }
-    k_foe_mu<<<1, 32, 0, ls>>>(st, parts, sp2_tc_num_parts(ctx, L.ld), n, nocc, beta, tol, o->mu_iters,
+    // E^2 and E^3 (with Tr E^3) for the canonical shift
+    if ((r = gemm(*X, *X, *A, 1.0f, 0.0f, nullptr, 0.0f, nullptr))) return r;
+    if ((r = gemm(*X, *A, *Z, 1.0f, 0.0f, nullptr, 0.0f, parts3))) return r;
+    k_foe_mu<<<1, 32, 0, ls>>>(st, parts, parts3, sp2_tc_num_parts(ctx, L.ld), n, nocc, beta, tol, o->mu_iters,
                                loop.handle, loop.graph);
     TB_LAUNCH_CHECK(ctx);
     k_foe_keep<<<1184, 256, 0, ls>>>(st, nn, X->m, res);
     TB_LAUNCH_CHECK(ctx);
     xf = X;
     af = A;
+    zf = Z;
     return TB_OK;
   };
   for (int it = 0; it < rounds && rc == TB_OK; ++it) rc = expansion();
   if ((rc = tb_loop_end(ctx, &loop, rc))) return rc;
-  // first-order canonical correction of the accepted expansion (its E and
-  // operand splits are still in *xf): T = E^2, then E += beta dmu (I/4 - T)
-  ls = s;
-  gskip = &st->nocorr;
-  if ((rc = gemm(*xf, *xf, *af, 1.0f, 0.0f, nullptr, 0.0f, nullptr))) return rc;
+  // canonical shift of the accepted expansion (its E, E^2, E^3 are still in
+  // *xf, *af, *zf)
   {
     const int fb = std::min(1184, (int)(((size_t)n * n + 255) / 256));
-    k_foe_correct<<<fb, 256, 0, s>>>(st, n, L.ld, beta, af->m, res);
+    k_foe_correct<<<fb, 256, 0, s>>>(st, n, L.ld, af->m, zf->m, res);
     TB_LAUNCH_CHECK(ctx);
   }
   const int fb = std::min(1184, (int)(((size_t)n * n + 255) / 256));

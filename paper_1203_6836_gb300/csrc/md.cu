@@ -98,14 +98,17 @@ __global__ void __launch_bounds__(256) k_kick_energy(int N, double* __restrict__
   }
 }
 
-// mu[0] <- 2 mu[1] - mu[2] (the start of this step's dm_fermi), or mu[1]
-// when only one previous value is known.
+// mu[0] <- the start of this step's dm_fermi, extrapolated from the last
+// steps' values mu[1..3] (quadratic 3 mu1 - 3 mu2 + mu3, linear 2 mu1 - mu2,
+// or mu1, as far as they are known).
 __global__ void k_mu_predict(double* mu) {
-  const double a = mu[1], b = mu[2];
-  if (isfinite(a)) mu[0] = isfinite(b) ? 2.0 * a - b : a;
+  const double a = mu[1], b = mu[2], c = mu[3];
+  if (!isfinite(a)) return;
+  mu[0] = !isfinite(b) ? a : !isfinite(c) ? 2.0 * a - b : 3.0 * a - 3.0 * b + c;
 }
-// mu[2] <- mu[1], mu[1] <- mu[0] after a step's dm_fermi.
+// mu[3] <- mu[2] <- mu[1] <- mu[0] after a step's dm_fermi.
 __global__ void k_mu_shift(double* mu) {
+  mu[3] = mu[2];
   mu[2] = mu[1];
   mu[1] = mu[0];
 }
@@ -278,8 +281,8 @@ extern "C" int xlbomd_init(tb_ctx* ctx, const tb_params* p, tb_md_state* st, con
   k_kick_energy<<<1, 256, 0, s>>>(N, st->v, st->F, st->mass, xp->dt, 0, st->n_hist, st->q, st->energies);
   TB_LAUNCH_CHECK(ctx);
   if (st->kT > 0.0) {
-    const double nan2[2] = {NAN, NAN};
-    TB_CUDA_TRY(ctx, cudaMemcpyAsync(st->mu + 1, nan2, sizeof(nan2), cudaMemcpyHostToDevice, s));
+    const double nan3[3] = {NAN, NAN, NAN};
+    TB_CUDA_TRY(ctx, cudaMemcpyAsync(st->mu + 1, nan3, sizeof(nan3), cudaMemcpyHostToDevice, s));
     k_mu_shift<<<1, 1, 0, s>>>(st->mu);  // mu[1] = the initial state's mu
     TB_LAUNCH_CHECK(ctx);
   }

@@ -119,7 +119,7 @@ int layout_for(tb_server* sv, int N, int n, Layout* L) {
   L->energies = take(sizeof(double) * 8);
   L->sp2rep = take(sizeof(tb_sp2_report));
   L->fermirep = take(sizeof(tb_fermi_report));
-  L->mu = take(3 * sizeof(double));
+  L->mu = take(4 * sizeof(double));
   L->types = take(sizeof(int32_t) * N);
   L->orb = take(sizeof(int32_t) * (N + 1));
   L->ws = take(ws);
@@ -148,8 +148,8 @@ int admit(tb_server* sv, int t) {
   TB_CUDA_TRY(ctx, cudaMemcpyAsync(b + L.types, T.types.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, s));
   TB_CUDA_TRY(ctx,
               cudaMemcpyAsync(b + L.orb, T.orb_off.data(), sizeof(int32_t) * (N + 1), cudaMemcpyHostToDevice, s));
-  const double nan3[3] = {NAN, NAN, NAN};
-  TB_CUDA_TRY(ctx, cudaMemcpyAsync(b + L.mu, nan3, sizeof(nan3), cudaMemcpyHostToDevice, s));
+  const double nan4[4] = {NAN, NAN, NAN, NAN};
+  TB_CUDA_TRY(ctx, cudaMemcpyAsync(b + L.mu, nan4, sizeof(nan4), cudaMemcpyHostToDevice, s));
   tb_md_state& st = T.st;
   st = tb_md_state{};
   st.sys.natoms = N;

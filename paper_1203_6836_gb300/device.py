@@ -115,7 +115,7 @@ class MDState:
         self.energies = torch.zeros(8, **f64)
         self.report = new_report(dev)
         self.fermi_report = torch.zeros(ctypes.sizeof(tbmd.tb_fermi_report), dtype=torch.uint8, device=dev)
-        self.mu = torch.full((3,), float("nan"), dtype=torch.float64, device=dev)
+        self.mu = torch.full((4,), float("nan"), dtype=torch.float64, device=dev)
         if kT > 0.0:
             fermi = fermi or fermi_opts()
             self.ws = Workspace(tbmd.dm_fermi_workspace_size(n, fermi), dev)
