@@ -310,7 +310,10 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
     }
   }
   const double beta = 1.0 / kT;
-  const int m = o->m > 0 ? o->m : 16;
+  // m = 14: X0 is the linearised Fermi function at beta / 2^m, which shifts the
+  // effective beta of a state at beta |eps - mu| = 5 by (5 / 2^m)^2 / 12 < 1e-8
+  // relative, and keeps X0 in [0, 1] for |eps - mu| <= 2^(m+1) / beta
+  const int m = o->m > 0 ? o->m : 14;
   const int ns = o->ns_iters > 0 ? o->ns_iters : 4;
   const double tol = o->trace_tol > 0.0 ? o->trace_tol : 1e-7 * std::max(1.0, nocc);
   const double c = beta / std::ldexp(1.0, m + 2);
