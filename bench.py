@@ -152,10 +152,10 @@ def cpu_oracle_sample(max_seconds: float = 20.0) -> dict:
     """The oracle's FP64 SP2 (NumPy/BLAS) on the same 4094-orbital H, timed on
     the host cores for a bounded number of projections."""
     import numpy as np
-    from workloads import ModelParams, config2_system
+    from workloads import ModelParams, water_2048_atoms
     from oracle import tb, density
     P = ModelParams()
-    s = config2_system()
+    s = water_2048_atoms()
     H = tb.build_H(tb.build_h(s.R, s.types, s.box, P), tb.build_gamma(s.R, s.box, P), s.types,
                    np.zeros(s.natoms))
     n = H.shape[0]
@@ -179,10 +179,10 @@ def run_reference(args):
     if rank != 0:
         return
     import numpy as np
-    from workloads import ModelParams, config2_system
+    from workloads import ModelParams, water_2048_atoms
     from oracle import tb, density
     P = ModelParams()
-    s = config2_system()
+    s = water_2048_atoms()
     H = tb.build_H(tb.build_h(s.R, s.types, s.box, P), tb.build_gamma(s.R, s.box, P), s.types,
                    np.zeros(s.natoms))
     n = H.shape[0]
@@ -226,7 +226,7 @@ def run_ours(args):
 
     from paper_1203_6836_gb300 import build, tbmd
     from paper_1203_6836_gb300.device import DeviceSystem, MDState, sp2_opts, xl_params, report_to_dict
-    from workloads import ModelParams, XLParams, config2_system, thermal_velocities
+    from workloads import ModelParams, XLParams, water_2048_atoms, thermal_velocities
 
     if rank == 0:
         build.build()
@@ -237,7 +237,7 @@ def run_ours(args):
     TP = tbmd.tb_params.from_model(P)
     XL = XLParams()
     from workloads import water_system
-    s = config2_system(seed=rank) if args.natoms == 2048 else water_system(args.natoms, density=1.0, seed=rank)
+    s = water_2048_atoms(seed=rank) if args.natoms == 2048 else water_system(args.natoms, density=1.0, seed=rank)
     M = s.masses(P)
     v0 = thermal_velocities(M, 300.0, seed=100 + rank)
     ds = DeviceSystem(s.R, s.types, s.box)
@@ -375,7 +375,7 @@ def run_ours(args):
             check = {"D_fro_per_sqrt_n": float(np.linalg.norm(Dg - ref.D) / np.sqrt(n)),
                      "q_max_abs": float(np.abs(q.cpu().numpy() - qo).max()),
                      "band_energy_abs_eV": float(abs(2 * np.sum(h0 * Dg) - 2 * np.sum(h0 * ref.D))),
-                     "gap_eV": float(ref.gap), "inputs": "R of config 2, n = 0"}
+                     "gap_eV": float(ref.gap), "inputs": "R of the 2048-atom system, n = 0"}
 
         cpu = None
         if not args.no_cpu and world == 1:
@@ -455,12 +455,12 @@ def run_small(args):
     import torch
     from paper_1203_6836_gb300 import tbmd
     from paper_1203_6836_gb300.device import DeviceSystem, MDState, sp2_opts, xl_params
-    from workloads import ModelParams, XLParams, config1_system, thermal_velocities
+    from workloads import ModelParams, XLParams, water_24_atoms, thermal_velocities
     ctx = _setup_gpu()
     P = ModelParams()
     TP = tbmd.tb_params.from_model(P)
     XL = XLParams()
-    s = config1_system()
+    s = water_24_atoms()
     M = s.masses(P)
     v0 = thermal_velocities(M, 300.0, seed=100)
     ds = DeviceSystem(s.R, s.types, s.box)
@@ -548,11 +548,11 @@ def run_sparse(args):
     import torch
     from paper_1203_6836_gb300 import tbmd
     from paper_1203_6836_gb300.device import DeviceSystem, DensitySolver, sp2_opts, report_to_dict
-    from workloads import ModelParams, config3_system, water_system
+    from workloads import ModelParams, water_16384_atoms_morton, water_system
     ctx = _setup_gpu()
     P = ModelParams()
     TP = tbmd.tb_params.from_model(P)
-    s = config3_system() if args.sparse_natoms == 16384 else water_system(args.sparse_natoms, density=1.0, seed=0,
+    s = water_16384_atoms_morton() if args.sparse_natoms == 16384 else water_system(args.sparse_natoms, density=1.0, seed=0,
                                                                             morton=True)
     ds = DeviceSystem(s.R, s.types, s.box)
     n = ds.norb

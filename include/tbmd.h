@@ -127,7 +127,7 @@ typedef struct {
 
 /* Create a context on the current device.  *ctx is owned by the caller and
  * released with tb_ctx_destroy.  Fails with TB_ERR_UNSUPPORTED when the
- * device is not sm_103 (this build contains sm_103a code only). */
+ * device is not sm_103 (the library contains sm_103a code only). */
 int tb_ctx_create(tb_ctx** ctx);
 int tb_ctx_destroy(tb_ctx* ctx);
 /* Static description of a status code. */
@@ -280,7 +280,9 @@ int mulliken(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const double
 /* ------------------------------------------------------ a8: forces, energy */
 
 /* F = -dE/dR at fixed n and E = 2 Tr[hD] + 1/2 (2q - n)^T gamma n + E_pair
- * (Eq. EL_Orth_a, Eq. Etot_Orth with the reading documented in the design doc).
+ * (Eq. EL_Orth_a, Eq. Etot_Orth; the population multiplying d gamma / dR is taken net of
+ * the neutral-atom reference, which makes the energy and force of Eq. EL_Orth_a
+ * consistent; at n = q E is the SCC-TB energy 2 Tr[hD] + 1/2 q^T gamma q + E_pair).
  *   R [N*3], D [n*n], q [N], n_aux [N], gamma [N*N] (from tb_build_H)
  *   F [N*3] output (eV/A); energy [4] output: E_pot, 2Tr[hD], E_scc, E_pair. */
 int tb_forces(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const double* R,

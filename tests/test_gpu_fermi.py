@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 import torch
 
-from workloads import random_gapped_matrix, water_system, ModelParams, config1_system
+from workloads import random_gapped_matrix, water_system, ModelParams, water_24_atoms
 from oracle import density, tb
 from paper_1203_6836_gb300 import tbmd
 from paper_1203_6836_gb300.device import FermiSolver, fermi_opts, fermi_report_to_dict
@@ -39,7 +39,7 @@ def _err(A, B):
 
 
 def _c1_H(seed=0):
-    s = config1_system()
+    s = water_24_atoms()
     rng = np.random.default_rng(seed)
     na = rng.normal(0, 0.3, s.natoms)
     na -= na.mean()

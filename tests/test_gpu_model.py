@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 import torch
 
-from workloads import ModelParams, config1_system, molecular_water, water_system
+from workloads import ModelParams, water_24_atoms, molecular_water, water_system
 from oracle import tb, observables
 from paper_1203_6836_gb300 import tbmd
 from paper_1203_6836_gb300.device import DeviceSystem
@@ -18,7 +18,7 @@ TP = tbmd.tb_params.from_model(P)
 
 def _system(which):
     if which == "c1":
-        return config1_system()
+        return water_24_atoms()
     if which == "mol":
         return molecular_water(2, 7.0, seed=3)
     if which == "small_box":

@@ -20,7 +20,7 @@ import numpy as np
 import pytest
 import torch
 
-from workloads import random_gapped_matrix, water_system, ModelParams, config1_system
+from workloads import random_gapped_matrix, water_system, ModelParams, water_24_atoms
 from oracle import density, tb
 from paper_1203_6836_gb300 import tbmd
 from paper_1203_6836_gb300.device import DensitySolver, sp2_opts, report_to_dict
@@ -103,7 +103,7 @@ def test_fp64_simple_rule_and_not_converged_status(ctx):
 
 
 def test_fp64_water_hamiltonian(ctx):
-    s = config1_system()
+    s = water_24_atoms()
     h = tb.build_h(s.R, s.types, s.box, P)
     G = tb.build_gamma(s.R, s.box, P)
     rng = np.random.default_rng(11)

@@ -7,7 +7,7 @@ import dataclasses
 import numpy as np
 import pytest
 
-from workloads import (ModelParams, XLParams, TYPE_O, TYPE_H, config1_system,
+from workloads import (ModelParams, XLParams, TYPE_O, TYPE_H, water_24_atoms,
                        molecular_water, thermal_velocities)
 from oracle import tb, density, observables, md
 
@@ -28,7 +28,7 @@ def _water_molecule(box=30.0, r=0.96):
 
 def test_mulliken_neutrality():
     """Sum_i q_i = 2 Tr D - N_e = 0 when Tr D = N_occ."""
-    s = config1_system()
+    s = water_24_atoms()
     h = tb.build_h(s.R, s.types, s.box, P)
     G = tb.build_gamma(s.R, s.box, P)
     H = tb.build_H(h, G, s.types, np.zeros(s.natoms))
@@ -51,7 +51,7 @@ def test_forces_are_minus_energy_gradient_at_fixed_n(which):
         n_aux = np.array([1.2, -0.5, -0.7])
         nocc = 4
     else:
-        s = config1_system()
+        s = water_24_atoms()
         R, types, box = s.R, s.types, s.box
         n_aux = 0.3 * np.sin(np.arange(s.natoms))
         n_aux -= n_aux.mean()

@@ -4,7 +4,7 @@ finite differences and invariants that do not reuse the oracle's formulas."""
 import numpy as np
 import pytest
 
-from workloads import ModelParams, TYPE_O, TYPE_H, config1_system
+from workloads import ModelParams, TYPE_O, TYPE_H, water_24_atoms
 from oracle import tb
 
 P = ModelParams()
@@ -61,7 +61,7 @@ def test_gamma_onsite_is_hubbard_u_and_decays_like_coulomb():
 def test_gamma_matrix_positive_definite():
     """gamma is a product of positive-definite radial kernels, so the periodic
     gamma matrix is positive definite (the SCC functional is convex)."""
-    s = config1_system()
+    s = water_24_atoms()
     G = tb.build_gamma(s.R, s.box, P)
     assert np.allclose(G, G.T)
     assert np.linalg.eigvalsh(G).min() > 0.5
@@ -117,7 +117,7 @@ def test_h_spectrum_invariant_under_rigid_rotation():
 
 
 def test_H_is_h_plus_charge_shift_on_every_orbital_of_the_atom():
-    s = config1_system()
+    s = water_24_atoms()
     h = tb.build_h(s.R, s.types, s.box, P)
     G = tb.build_gamma(s.R, s.box, P)
     assert np.allclose(h, h.T)

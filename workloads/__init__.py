@@ -12,5 +12,5 @@ from .water import (  # noqa: F401
     TYPE_O, TYPE_H, ModelParams, XLParams, WaterSystem,
     atom_counts, box_from_density, water_system, thermal_velocities,
     random_gapped_matrix, batch_sizes, serving_trajectories,
-    config1_system, config2_system, config3_system, molecular_water, molecular_liquid,
+    water_24_atoms, water_2048_atoms, water_16384_atoms_morton, molecular_water, molecular_liquid,
 )

@@ -273,17 +273,17 @@ def serving_trajectories(count: int = 64, lo: int = 32, hi: int = 2048, rate: fl
     return sizes, arrivals, which
 
 
-def config1_system() -> WaterSystem:
+def water_24_atoms() -> WaterSystem:
     """8 O + 16 H in a 6.5 A periodic cube, seed 0 (n = 48 orbitals)."""
     return water_system(n_O=8, n_H=16, box=6.5, seed=0)
 
 
-def config2_system(seed: int = 0) -> WaterSystem:
+def water_2048_atoms(seed: int = 0) -> WaterSystem:
     """2048 atoms (682 O + 1366 H, n = 4094 orbitals) at 1.0 g/cc."""
     return water_system(2048, density=1.0, seed=seed)
 
 
-def config3_system(seed: int = 0) -> WaterSystem:
+def water_16384_atoms_morton(seed: int = 0) -> WaterSystem:
     """16384 atoms (5460 O + 10924 H, n = 32764 orbitals) at 1.0 g/cc,
     Morton-ordered so that the density matrix is block sparse."""
     return water_system(16384, density=1.0, seed=seed, morton=True)
