@@ -17,16 +17,18 @@
 //           (every CTA the same), build each row's bitmaps of stored and live
 //           (not all-zero) super-blocks;
 //   symbolic  candidates of row I = OR of the live bitmaps of its live
-//           columns; scans give the output slots; each output block (I,J)
-//           gets the list of common K (live in both rows I and J, X symmetric)
-//           as pairs of source slots;
-//   numeric  a persistent tcgen05 kernel walks the output blocks: TMA loads
-//           the (I,K) and (J,K) tiles of every pair into shared memory, the
-//           MMA accumulates in TMEM (double-buffered between blocks), the
-//           epilogue applies the branch (X^2 or 2X - X^2), zeroes every 32 x 32
+//           columns; scans give the output slots; each upper output block
+//           (I <= J; X^2 and its pattern are symmetric) gets the list of common
+//           K (live in both rows I and J) as pairs of source slots; the upper
+//           blocks are listed in (band of 8 block rows, column, row) order;
+//   numeric  a persistent tcgen05 kernel walks that list: TMA loads the (I,K)
+//           and (J,K) tiles of every pair into shared memory, the MMA
+//           accumulates in TMEM (double-buffered between blocks), the epilogue
+//           applies the branch (X^2 or 2X - X^2), zeroes every 32 x 32
 //           sub-block with ||.||_F < tau (one warp owns a 32-row band, so a
 //           sub-block norm is a warp reduction), writes the FP32 master and
-//           operand splits, and accumulates FP64 trace partials.
+//           operand splits of block (I,J) and, transposed, of its mirror (J,I),
+//           and accumulates FP64 trace partials.
 // The final iterate is scattered into the dense FP64 D.
 
 #include "common.cuh"

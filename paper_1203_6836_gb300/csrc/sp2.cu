@@ -12,10 +12,12 @@
 // CTA) and either returns at once or computes X_{k+1}.  No host
 // synchronisation happens inside dm_sp2.
 //
-// Precision paths: TB_PREC_FP64 runs every projection as an FP64 GEMM; the
-// tensor-core paths (gemm_tc.cu) keep X as an FP32 master plus bf16/tf32
-// operand splits and hand the final iterate to `refine_iters` FP64
-// projections.  Traces and their reductions are FP64 throughout.
+// Precision paths: TB_PREC_FP64 runs every projection as an FP64 GEMM (16 x 16
+// output tiles for ld <= 512, 64 x 64 above); the tensor-core paths
+// (gemm_tc.cu) keep X as an FP32 master plus bf16/tf32 operand splits and
+// hand the final iterate to `refine_iters` FP64 projections, computed exactly
+// from integer slices on the bf16 tensor cores (gemm_oz.cu, ld <= 4096) or
+// with FP64 FMAs.  Traces and their reductions are FP64 throughout.
 
 #include "common.cuh"
 
