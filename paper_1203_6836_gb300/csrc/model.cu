@@ -216,7 +216,10 @@ __global__ void __launch_bounds__(256) k_build_pairs(ModelDev m, int N, const in
 #pragma unroll
     for (int b = 0; b < 4; ++b) B[a][b] = 0.0;
   double gsum = (i == j) ? m.U : 0.0;
-  if (screen_f32(Ri, Rj, (float)m.box, (float)m.range) || i == j) {
+  // H and gamma were zeroed: pairs with no image in range write nothing
+  // (gamma's window and h's tail both end at the cut-off)
+  if (!(screen_f32(Ri, Rj, (float)m.box, (float)m.range) || i == j)) return;
+  {
     double d0[3];
     min_image(Ri, Rj, m.box, d0);
     int lo[3], hi[3];
@@ -303,6 +306,7 @@ extern "C" int tb_build_H(tb_ctx* ctx, const tb_params* p, const tb_system* sys,
   cudaStream_t s = as_stream(stream);
   const int N = sys->natoms, n = sys->norb;
   TB_CUDA_TRY(ctx, cudaMemsetAsync(H, 0, sizeof(double) * (size_t)n * n, s));
+  TB_CUDA_TRY(ctx, cudaMemsetAsync(gamma, 0, sizeof(double) * (size_t)N * N, s));
   dim3 grid((N + 255) / 256, N);
   k_build_pairs<<<grid, 256, 0, s>>>(m, N, sys->types, sys->orb_off, R, H, n, gamma);
   TB_LAUNCH_CHECK(ctx);
