@@ -234,7 +234,8 @@ typedef struct {
   int precision;      /* tensor-core precision of the products: TB_PREC_TF32 .. TB_PREC_BF16X3 */
   int m;              /* doubling steps (0: 14); needs beta max|eps - mu| <= 2^(m+1); the
                          linearised start changes the effective beta by (beta |eps - mu| / 2^m)^2 / 12 */
-  int ns_iters;       /* Newton-Schulz steps per inverse, counting the first (0: 4) */
+  int ns_iters;       /* steps per inverse of A = I + 4E^2: the quadratic start (one product)
+                         and ns_iters - 1 Newton-Schulz steps (0: 3, residual <= 99^-4) */
   int mu_iters;       /* cap on chemical-potential updates (one expansion each), 1..40 */
   double trace_tol;   /* stop when |Tr D - N_occ| <= trace_tol (0: 1e-7 max(1, N_occ)) */
 } tb_fermi_opts;

@@ -13,8 +13,13 @@
 // doubled m times as absolute errors of X would be).  Per step:
 //   A = I + 4 E E                                  (one product, affine epilogue;
 //                                                   spectrum in [1, 2])
-//   Z = A^-1: Z1 = 4/3 I - 4/9 A, then Newton-Schulz Z <- Z (2I - A Z)
+//   Z = A^-1: Z1 = (210 I - 144 A + 32 A^2) / 99    (one product A A with the
+//             affine part in its epilogue), then Newton-Schulz Z <- Z (2I - A Z)
 //   E <- 2 E Z                                     (one product)
+// Z1 is the quadratic p minimising max |1 - x p(x)| on [1, 2]: 1 - x p(x) is
+// the Chebyshev polynomial T3(2x - 3) / T3(-3), so ||I - A Z1|| <= 1/99 and two
+// Newton-Schulz steps leave ||I - A Z|| <= 99^-4 ~ 1e-8 (seven products per
+// doubling step, where Z0 = 2/3 I needs four Newton-Schulz steps for 2e-8).
 // All factors are functions of H, hence symmetric and commuting, so every
 // product is a tensor-core GEMM with the second operand read by rows, and
 // its result is symmetric: the product kernel computes the upper-triangle
@@ -99,18 +104,6 @@ __global__ void __launch_bounds__(256) k_foe_x0(const double* __restrict__ H, in
     double x = 0.0;
     if (r < n && col < n) x = (r == col ? c * mu : 0.0) - c * H[(size_t)r * n + col];
     X[e] = (float)x;
-  }
-}
-
-// Z1 = 4/3 I - 4/9 A on the n x n block (padding stays zero): one
-// Newton-Schulz step from Z0 = 2/3 I, leaving ||I - A Z1|| <= 1/9.
-__global__ void __launch_bounds__(256) k_foe_z1(const FoeState* st, int n, int ld, const float* __restrict__ A,
-                                                float* __restrict__ Z) {
-  if (st->done || st->err) return;
-  const size_t total = (size_t)ld * ld;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(e / ld), col = (int)(e % ld);
-    Z[e] = (r == col && r < n ? (4.0f / 3.0f) : 0.0f) - (4.0f / 9.0f) * A[e];
   }
 }
 
@@ -314,7 +307,7 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
   // effective beta of a state at beta |eps - mu| = 5 by (5 / 2^m)^2 / 12 < 1e-8
   // relative, and keeps X0 in [0, 1] for |eps - mu| <= 2^(m+1) / beta
   const int m = o->m > 0 ? o->m : 14;
-  const int ns = o->ns_iters > 0 ? o->ns_iters : 4;
+  const int ns = o->ns_iters > 0 ? o->ns_iters : 3;
   const double tol = o->trace_tol > 0.0 ? o->trace_tol : 1e-7 * std::max(1.0, nocc);
   const double c = beta / std::ldexp(1.0, m + 2);
   const size_t nn = (size_t)L.ld * L.ld;
@@ -367,10 +360,8 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
     for (int step = 0; step < m; ++step) {
       // A = I + 4 E E
       if ((r = gemm(*X, *X, *A, 4.0f, 0.0f, nullptr, 1.0f, nullptr))) return r;
-      // Z1 = 4/3 I - 4/9 A, then Newton-Schulz
-      k_foe_z1<<<1184, 256, 0, ls>>>(st, n, L.ld, A->m, Z->m);
-      TB_LAUNCH_CHECK(ctx);
-      if ((r = tc_split(ctx, o->precision, Z->m, nn, Z->hi, Z->lo, skip, ls))) return r;
+      // Z1 = (32 A A - 144 A + 210 I) / 99, then Newton-Schulz
+      if ((r = gemm(*A, *A, *Z, 32.0f / 99.0f, -144.0f / 99.0f, A->m, 210.0f / 99.0f, nullptr))) return r;
       for (int k = 1; k < ns; ++k) {
         if ((r = gemm(*A, *Z, *T, -1.0f, 0.0f, nullptr, 2.0f, nullptr))) return r;  // T = 2I - A Z
         if ((r = gemm(*Z, *T, *Y, 1.0f, 0.0f, nullptr, 0.0f, nullptr))) return r;   // Z <- Z T

@@ -6,19 +6,23 @@
 // error-free splitting of Ozaki, Ogita, Oishi and Rump (Numer. Algorithms
 // 2012) in the tensor-core form of Mukunoki et al. (ISC 2020):
 //
-//   row scaling  x_ij = 2^{e_i} r_ij, |r_ij| <= 1 (e_i from the row maximum)
-//   slicing      r = sum_{s=1..S} d_s 2^{-6s}, d_s integers (|d_1| <= 64,
-//                |d_s| <= 32 for s >= 2), each exact in bf16
+//   row scaling  x_ij = 2^{e_i} r_ij, |r_ij| < 1/2 (e_i from the row maximum)
+//   slicing      r = sum_{s=1..S} d_s 2^{-7s}, d_s integers with |d_s| <= 64,
+//                each exact in bf16 (8 significant bits)
 //   products     P_st = sum_k d_s(i,k) d_t(j,k): integers with |P| <= K 2^12,
 //                exact in the FP32 accumulator for K <= 4096
-//   sum          (X X)_ij = 2^{e_i + e_j} sum_{s+t <= S+1} 2^{-6(s+t)} P_st,
-//                recombined exactly in int64 fixed point, then rounded once
-//                to FP64.
-// With S = 7 the slices carry 42 bits of each row-scaled entry.  The pairs
-// dropped (s + t > 8) weigh <= 2^-54 each: ~1e-12 of |x_i| |x_j| per element,
-// and the always-positive diagonal pairs (s, s), s >= 5, bias a diagonal
-// entry by ~K 2^-60.  28 bf16 products replace one FP64 GEMM.
-//
+//   sum          (X X)_ij = 2^{e_i + e_j} sum_{(s,t)} 2^{-7(s+t)} P_st,
+//                recombined in int64 fixed point, then rounded once to FP64.
+// With S = 6 the slices carry 42 bits of each row-scaled entry (41 below the
+// row maximum).  The kept pairs are s + t <= 7 (21 products) and (4, 4): a
+// dropped pair weighs <= 2^-56 |d_s d_t| <= 2^-44 of |x_i| |x_j| per term, and
+// the dropped off-diagonal pairs (s, t), (t, s) enter with random signs, while
+// a dropped diagonal pair (s, s) is always positive and would bias a diagonal
+// entry of X X by ~K E[d^2] 2^{-14 s}: (4, 4) is kept for that reason (its
+// product is rounded to the fixed point's last place, 2^-49), the first
+// dropped one, (5, 5), biases by ~K 2^-62.  22 bf16 products replace one FP64
+// GEMM (6-bit slices would need 7 slices and 28 products for the same bounds).
+
 // Kernel layout: one CTA per 128 x 128 tile of the upper triangle (X^2 is
 // symmetric; the epilogue also writes each off-diagonal tile transposed,
 // one coalesced 32-lane store per column); warp 0 issues TMA loads
@@ -36,9 +40,9 @@ namespace {
 
 using namespace tcx;
 
-constexpr int kS = 7;          // slices
-constexpr int kBeta = 6;       // bits per slice
-constexpr int kPairs = kS * (kS + 1) / 2;  // (s, t) with s + t <= kS + 1
+constexpr int kS = 6;          // slices
+constexpr int kBeta = 7;       // bits per slice
+constexpr int kPairs = kS * (kS + 1) / 2 + 1;  // (s, t) with s + t <= kS + 1, then (4, 4)
 constexpr int kTile = 128;
 constexpr int kBK = 64;        // bf16 per 128-byte row
 constexpr int kTileBytes = kTile * 128;
@@ -53,7 +57,12 @@ struct SliceMaps {
 };
 
 __device__ __forceinline__ void pair_of(int p, int* s, int* t) {
-  // (1,1..kS), (2,1..kS-1), ..., (kS,1)
+  // (1,1..kS), (2,1..kS-1), ..., (kS,1), then (4,4)
+  if (p == kPairs - 1) {
+    *s = 4;
+    *t = 4;
+    return;
+  }
   int ss = 1, rem = p;
   while (rem >= kS + 1 - ss) {
     rem -= kS + 1 - ss;
@@ -63,12 +72,13 @@ __device__ __forceinline__ void pair_of(int p, int* s, int* t) {
   *t = rem + 1;
 }
 
-// One warp per row: e_i from the row maximum, then the kS signed 6-bit
-// digits of every entry of the row.  r = x 2^{-e} is scaled exactly and
-// rounded once to the integer R = rint(r 2^{6 kS}) (|R| <= 2^42); the digits
-// are R's balanced base-64 digits, peeled off from the least significant
-// end in int64 arithmetic: d in [-32, 31] for s >= 2 and |d_1| <= 64, all
-// exact in bf16.  Four consecutive entries per lane per pass.
+// One warp per row: e_i from the row maximum, then the kS signed 7-bit
+// digits of every entry of the row.  r = x 2^{-e} (|r| < 1/2) is scaled
+// exactly and rounded once to the integer R = rint(r 2^{7 kS}) (|R| <= 2^41);
+// the digits are R's balanced base-128 digits, peeled off from the least
+// significant end in int64 arithmetic: d in [-64, 63] for s >= 2 and
+// |d_1| <= 64 (2^41 + 2^34 < 64.5 2^35), all exact in bf16.  Four consecutive
+// entries per lane per pass.
 __global__ void __launch_bounds__(256) k_oz_split(const SP2State* st, const double* __restrict__ X, int ld,
                                                   __nv_bfloat16* __restrict__ slices, int* __restrict__ exps) {
   if (st->rdone || st->err) return;
@@ -85,8 +95,8 @@ __global__ void __launch_bounds__(256) k_oz_split(const SP2State* st, const doub
   mx = warp_max(mx);
   int e = 0;
   if (mx > 0.0) {
-    frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): |x| / 2^e <= 1
-    e = max(e, -960);  // keeps 2^{42 - e} finite; such rows are below every digit
+    frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): |x| / 2^{e+1} < 1/2
+    e = max(e + 1, -960);  // keeps 2^{42 - e} finite; such rows are below every digit
   }
   if (lane == 0) exps[row] = e;
   const size_t plane = (size_t)ld * ld;
@@ -101,8 +111,8 @@ __global__ void __launch_bounds__(256) k_oz_split(const SP2State* st, const doub
     for (int s = kS - 1; s >= 1; --s) {
 #pragma unroll
       for (int e4 = 0; e4 < 4; ++e4) {
-        const long long d = ((R[e4] + 32) & 63) - 32;  // balanced remainder in [-32, 31]
-        R[e4] = (R[e4] - d) >> kBeta;                  // exact division by 64
+        const long long d = ((R[e4] + 64) & 127) - 64;  // balanced remainder in [-64, 63]
+        R[e4] = (R[e4] - d) >> kBeta;                   // exact division by 128
         dg[s][e4] = __bfloat16_as_ushort(__float2bfloat16_rn((float)d));
       }
     }
@@ -277,13 +287,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       tc_fence_after();
+      // fixed point 2^{-kBeta (kS + 1)}: P_st << 7 (7 - s - t); (4, 4) lies one
+      // place below it and is scaled by 2^-7 in FP32 (exact) and rounded to
+      // the nearest integer; every other P_st converts exactly
       const int shift = kBeta * (kS + 1 - s - t);
+      const int lsh = shift > 0 ? shift : 0;
+      const float fs = shift >= 0 ? 1.0f : 1.0f / (float)(1 << -shift);
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         uint32_t v[32];
         tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + acc * kTile + 64 * h + 32 * c, v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc64[32 * c + j] += __float2ll_rz(__uint_as_float(v[j])) << shift;
+        for (int j = 0; j < 32; ++j) acc64[32 * c + j] += __float2ll_rn(__uint_as_float(v[j]) * fs) << lsh;
       }
       tc_fence_before();
       __syncwarp();

@@ -135,7 +135,7 @@ class MDState:
         return self.n_hist[0]
 
 
-def fermi_opts(precision: str = "tf32x3", m: int = 14, ns_iters: int = 4, mu_iters: int = 30,
+def fermi_opts(precision: str = "tf32x3", m: int = 14, ns_iters: int = 3, mu_iters: int = 30,
                trace_tol: float = 0.0) -> tbmd.tb_fermi_opts:
     return tbmd.tb_fermi_opts(precision=tbmd.PREC[precision], m=m, ns_iters=ns_iters, mu_iters=mu_iters,
                               trace_tol=trace_tol)

@@ -84,8 +84,12 @@ def test_finite_temperature_trajectory_matches_oracle(ctx):
         if k:
             tbmd.xlbomd_step(ctx, TP, st.st, xp, opts)
         torch.cuda.synchronize()
+        # the expansion's tf32x3 products leave q ~1e-7 from the oracle's
+        # Fermi-Dirac charges (bounded here by 1e-5); the force difference that
+        # causes (~ dq x 4 eV/A per e) moves an H atom by dF t^2 / 2M after 20
+        # steps of 0.25 fs: 5e-7 A for dq = 1e-6
         assert np.abs(st.q.cpu().numpy() - o.q[k]).max() < 1e-5, k
-        assert np.abs(st.R.cpu().numpy() - o.R[k]).max() < 1e-7, k
+        assert np.abs(st.R.cpu().numpy() - o.R[k]).max() < 5e-7, k
         assert st.energies[1].item() == pytest.approx(o.E_pot[k], abs=2e-6 * s.natoms)
     rep = tbmd.tb_fermi_report.from_buffer_copy(st.fermi_report.cpu().numpy().tobytes())
     assert rep.status == tbmd.TB_OK and rep.mu_iters >= 1
