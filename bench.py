@@ -171,7 +171,7 @@ def cpu_oracle_sample(max_seconds: float = 20.0) -> dict:
         k *= 2
     flops = 2.0 * n ** 3 * r.iters
     return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{r.iters} FP64 SP2 projections (NumPy matmul) of the n={n} config-2 H, {dt:.1f} s"}
+            "sample": f"{r.iters} FP64 SP2 projections (NumPy matmul) of the n={n} water-like H, {dt:.1f} s"}
 
 
 def run_reference(args):
