@@ -863,8 +863,9 @@ def run_serving(args):
     svc = [c.gpu_ms for c in out]
     ok = sum(c.status == tbmd.TB_OK for c in out)
     ns = fo.ns_iters
-    # products per expansion: m doubling steps of 2 ns + 1 products, then E^2 and E^3
-    foe_flops = sum(c.solver_iters * (fo.m * (2 * ns + 1) + 2) * 2.0 * norb[c.traj] ** 3 for c in out)
+    # products per expansion: the start (2), m doubling steps of 2 ns + 1 (m as
+    # the device chose it for that step), then E^2 and E^3
+    foe_flops = sum(c.solver_iters * (c.solver_m * (2 * ns + 1) + 4) * 2.0 * norb[c.traj] ** 3 for c in out)
     span = max(c.t_done for c in out) - min(c.t_submit for c in out)
     value = len(out) / span
     peaks = measured_peaks()
@@ -892,7 +893,8 @@ def run_serving(args):
                    requests_ok=ok, wall_s=wall, admission_s=admit_s,
                    server={"slots": 32, "bytes_in_use": st["bytes_in_use"], "budget": st["budget"],
                            "admitted": st["admitted"]},
-                   foe={"m": fo.m, "ns_iters": ns, "mean_expansions_per_step": sum(c.solver_iters for c in out) / len(out)},
+                   foe={"m_max": fo.m, "m_used": sorted({c.solver_m for c in out}), "ns_iters": ns,
+                        "mean_expansions_per_step": sum(c.solver_iters for c in out) / len(out)},
                    stability={"max_abs_n_minus_q": max(c.energies[6] for c in out),
                               "atoms": [min(natoms), max(natoms)]},
                    roofline={"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

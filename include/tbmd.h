@@ -232,8 +232,12 @@ int dm_sp2_grouped_run(tb_ctx* ctx, void* workspace, int* config_out, void* stre
 /* Options of dm_fermi. */
 typedef struct {
   int precision;      /* tensor-core precision of the products: TB_PREC_TF32 .. TB_PREC_BF16X3 */
-  int m;              /* doubling steps (0: 14); needs beta max|eps - mu| <= 2^(m+1); the
-                         linearised start changes the effective beta by (beta |eps - mu| / 2^m)^2 / 12 */
+  int m;              /* most doubling steps (0: 14) after the third-order start E0 = L - 4/3 L^3,
+                         L = -beta/2^(m+2) (H - mu I) (relative error 2 z^4/15, z = beta |eps - mu| /
+                         2^(m+1)); the device uses the fewest m >= 8 (or this m if smaller) with
+                         beta (eps_max - eps_min + 80 kT + 2 eV) <= 2^(m+1) (Gershgorin bounds; the
+                         start is defined for |z| <= 1) and reports it; if even this m is too small
+                         the report's status is TB_ERR_ARG and D holds no result */
   int ns_iters;       /* steps per inverse of A = I + 4E^2: the quadratic start (one product)
                          and ns_iters - 1 Newton-Schulz steps (0: 3, residual <= 99^-4) */
   int mu_iters;       /* cap on chemical-potential updates (one expansion each), 1..40 */
@@ -244,7 +248,7 @@ typedef struct {
 typedef struct {
   int status;         /* TB_OK, TB_ERR_NOT_CONVERGED (trace not reached), TB_ERR_TIMEOUT */
   int mu_iters;       /* expansions performed */
-  int m;              /* doubling steps per expansion */
+  int m;              /* doubling steps per expansion used on the device */
   int n;
   double mu;          /* chemical potential of the returned D */
   double trace;       /* Tr D */
@@ -257,8 +261,9 @@ int dm_fermi_workspace_size(int n, const tb_fermi_opts* opts, size_t* bytes);
 
 /* D = (exp(beta (H - mu I)) + 1)^-1, beta = 1/kT, with mu such that
  * Tr D = n_occ (Eq. EL_4c, Eq. DM_perp; canonical), by the GEMM-only
- * recursive Fermi-operator expansion: from X0 = I/2 - beta/2^(m+2) (H - mu I),
- * m steps X <- X^2 [X^2 + (I - X)^2]^-1, each doubling beta, carried out on
+ * recursive Fermi-operator expansion: from X0 = f at beta/2^m (E0 = X0 - I/2 =
+ * -tanh(beta (H - mu I)/2^(m+1))/2 to third order), m steps
+ * X <- X^2 [X^2 + (I - X)^2]^-1, each doubling beta, carried out on
  * E = X - I/2 as E <- 2E (I + 4E^2)^-1 (inverse by Newton-Schulz).  mu: safeguarded Newton steps with dTr D/dmu =
  * beta Tr[D(I - D)] inside a bisection bracket, all on the device.  After each expansion the
  * products E^2 and E^3 give D(I - D) and D(I - D)(I - 2D); the expansion is accepted and shifted
@@ -396,6 +401,7 @@ typedef struct {
   int traj;             /* trajectory id */
   int status;           /* status of the step's density solve (TB_OK, TB_ERR_NOT_CONVERGED, ...) */
   int solver_iters;     /* SP2 projections (kT = 0) or Fermi-operator expansions (kT > 0) */
+  int solver_m;         /* kT > 0: doubling steps per expansion (tb_fermi_report.m); else 0 */
   int64_t step;         /* the trajectory's step count after this step */
   double t_submit;      /* host time of the request (replay: its scheduled arrival) */
   double t_launch;      /* host time of the graph launch */

@@ -4,10 +4,23 @@
 //
 // With y = 1/(1 + e^t), y^2 / (y^2 + (1 - y)^2) = 1/(1 + e^{2t}): one step of
 // X <- X^2 [X^2 + (I - X)^2]^-1 doubles the inverse temperature.  Starting
-// from the linearised X0 = I/2 - beta/2^{m+2} (H - mu I) (f at beta/2^m), m
-// steps give f at beta.  The steps are carried out on the deviation
-// E = X - I/2, for which the same map reads
+// from X0 = f at beta/2^m, m steps give f at beta.  The steps are carried out
+// on the deviation E = X - I/2, for which the same map reads
 //   E <- 2 E (I + 4 E^2)^-1                        (tanh double-angle form)
+// and f at beta/2^m is E0 = -tanh(Z)/2, Z = beta (H - mu I) / 2^{m+1}.  The
+// start takes tanh to third order: with L = -Z/2,
+//   E0 = L - 4/3 L^3                               (two products, L^2 and L L^2)
+// whose relative error 2 z^4/15 the doubling steps do not amplify (tanh(2y)
+// has a relative sensitivity (1 - t^2)/(1 + t^2) <= 1 to tanh(y) = t).  In
+// FP64 on a 20 eV wide spectrum at kT = 0.1 eV it reaches the Fermi function
+// to 2e-14 with m = 10 and 4e-12 with m = 8 (the linearised start E0 = L:
+// 1e-8 and 2e-7), far below the products' FP32-level error, so m is set by
+// the range of the start: both forms need |z| <= 1 (z - z^3/3 is monotone
+// there), beta max|eps - mu| <= 2^{m+1}.  The bounds kernel takes, for the
+// whole chemical-potential bracket [lo, hi], the smallest m >= kMinM with
+// beta (hi - lo) <= 2^{m+1}; the host issues m_max doubling steps and the
+// first m_max - m return at once (device flags), so one captured graph serves
+// every spectrum width up to beta (hi - lo) = 2^{m_max + 1}.
 // E is small while the early steps double it, so FP32-level products keep a
 // relative accuracy there (errors add up over the m steps instead of being
 // doubled m times as absolute errors of X would be).  Per step:
@@ -40,6 +53,9 @@ namespace {
 
 constexpr int kTile = 128;
 constexpr int kMaxMu = 40;
+constexpr int kMaxM = 40;   // doubling steps issued at most
+constexpr int kMinM = 8;    // doubling steps used at least
+constexpr int kMats = 6;    // E0/E1 (the iterate, alternating), A, Z, T, Y
 // Canonical shift: the last expansion is accepted and shifted by u = beta dmu
 // to second order,
 //   D(mu + dmu) = D + u D(I - D) + u^2/2 D(I - D)(I - 2D) + R,
@@ -64,6 +80,9 @@ struct FoeState {
   int nocorr;  // 0: apply the canonical shift u to the last expansion
   double dmu;  // u / beta
   double u;
+  double c;    // start scale beta / 2^{meff+2}
+  int meff;    // doubling steps used
+  int skipd[kMaxM];  // 1: doubling step k returns at once (k < m_max - meff, or done)
   double tr[kMaxMu + 1], trdd[kMaxMu + 1], mus[kMaxMu + 1];
 };
 
@@ -74,7 +93,13 @@ struct Mat {
   CUtensorMap mh, ml;
 };
 
-__global__ void k_foe_bounds(const double* bparts, int nb, FoeState* st, const double* mu_in, double kT) {
+// Gershgorin bounds, the bisection bracket, the first mu and the number of
+// doubling steps: the start needs beta |eps - mu| <= 2^{m+1} for every
+// eigenvalue and every mu of the bracket, so m is the smallest value >= kMinM
+// with beta (hi - lo) <= 2^{m+1}; when even m_max does not reach, the expansion
+// is not defined: TB_ERR_ARG, nothing runs.
+__global__ void k_foe_bounds(const double* bparts, int nb, FoeState* st, const double* mu_in, double kT,
+                             int m_max) {
   double a = INFINITY, b = -INFINITY;
   for (int i = threadIdx.x; i < nb; i += 32) {
     a = fmin(a, bparts[2 * i]);
@@ -90,14 +115,26 @@ __global__ void k_foe_bounds(const double* bparts, int nb, FoeState* st, const d
     const double g = mu_in ? *mu_in : NAN;
     st->mu = (isfinite(g) && g > st->lo && g < st->hi) ? g : 0.5 * (a + b);
     st->nocorr = 1;
+    const double z = (st->hi - st->lo) / kT;
+    int m = kMinM < m_max ? kMinM : m_max;
+    while (m < m_max && !(z <= ldexp(1.0, m + 1))) ++m;
+    st->meff = m;
+    st->c = 1.0 / (kT * ldexp(1.0, m + 2));
+    const bool bad = !(z <= ldexp(1.0, m + 1));
+    if (bad) {
+      st->err = TB_ERR_ARG;
+      st->done = 1;
+    }
+    for (int k = 0; k < kMaxM; ++k) st->skipd[k] = bad || k < m_max - m;
   }
 }
 
-// E0 = -c (H - mu I) on the n x n block (X0 = I/2 + E0), zero in the padding.
+// L = -c (H - mu I), c = beta / 2^{m+2} (m: the doubling steps used), on the
+// n x n block, zero in the padding.
 __global__ void __launch_bounds__(256) k_foe_x0(const double* __restrict__ H, int n, int ld, const FoeState* st,
-                                                double c, float* __restrict__ X) {
+                                                float* __restrict__ X) {
   if (st->done || st->err) return;
-  const double mu = st->mu;
+  const double mu = st->mu, c = st->c;
   const size_t total = (size_t)ld * ld;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / ld), col = (int)(e % ld);
@@ -172,7 +209,18 @@ __global__ void k_foe_mu(FoeState* st, const double* parts, const double* parts3
     if (!(next > st->lo && next < st->hi)) next = 0.5 * (st->lo + st->hi);
     st->mu = next;
   }
+  if (st->done)
+    for (int k = 0; k < kMaxM; ++k) st->skipd[k] = 1;
   if (cond && st->done) cudaGraphSetConditional(handle, 0);
+}
+
+// Word copy of one iterate array into the other iterate buffer (skipped once
+// the expansion loop is done).
+__global__ void __launch_bounds__(256) k_foe_copy(const FoeState* st, const uint32_t* __restrict__ src,
+                                                  uint32_t* __restrict__ dst, size_t words) {
+  if (st->done || st->err) return;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < words; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = src[e];
 }
 
 // Copy the last X of an expansion into the result buffer, only when that
@@ -202,7 +250,7 @@ __global__ void __launch_bounds__(256) k_foe_correct(const FoeState* st, int n, 
 }
 
 __global__ void __launch_bounds__(256) k_foe_finalize(const FoeState* st, int n, int ld, const float* __restrict__ X,
-                                                      double* __restrict__ D, double nocc, double tol, int m,
+                                                      double* __restrict__ D, double nocc, double tol,
                                                       double* mu_out, tb_fermi_report* rep) {
   const size_t total = (size_t)n * n;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
@@ -216,7 +264,7 @@ __global__ void __launch_bounds__(256) k_foe_finalize(const FoeState* st, int n,
     if (rep) {
       rep->status = st->err ? st->err : (fabs(st->tr[it] - nocc) <= tol ? TB_OK : TB_ERR_NOT_CONVERGED);
       rep->mu_iters = st->iters;
-      rep->m = m;
+      rep->m = st->meff;
       rep->n = n;
       rep->mu = mu;
       rep->trace = st->tr[it];
@@ -229,7 +277,7 @@ __global__ void __launch_bounds__(256) k_foe_finalize(const FoeState* st, int n,
 
 struct FoeLayout {
   int ld;
-  size_t off_state, off_bparts, off_parts, off_parts3, off_mat[5][3], off_res, total;
+  size_t off_state, off_bparts, off_parts, off_parts3, off_mat[kMats][3], off_res, total;
   int nparts;
 };
 
@@ -250,7 +298,7 @@ FoeLayout foe_layout(int n, int prec) {
   L.off_bparts = take(sizeof(double) * 2 * ((n + 7) / 8));
   L.off_parts = take(sizeof(double) * 2 * (size_t)L.nparts);
   L.off_parts3 = take(sizeof(double) * 2 * (size_t)L.nparts);
-  for (int i = 0; i < 5; ++i) {
+  for (int i = 0; i < kMats; ++i) {
     L.off_mat[i][0] = take(sizeof(float) * nn);
     L.off_mat[i][1] = take(eb * nn);
     L.off_mat[i][2] = split ? take(eb * nn) : 0;
@@ -288,8 +336,8 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
   double* bparts = reinterpret_cast<double*>(base + L.off_bparts);
   double* parts = reinterpret_cast<double*>(base + L.off_parts);
   double* parts3 = reinterpret_cast<double*>(base + L.off_parts3);
-  Mat M[5];  // X, A, Z, T, Y (next X)
-  for (int i = 0; i < 5; ++i) {
+  Mat M[kMats];  // E (two, alternating), A, Z, T, Y
+  for (int i = 0; i < kMats; ++i) {
     M[i].m = reinterpret_cast<float*>(base + L.off_mat[i][0]);
     M[i].hi = base + L.off_mat[i][1];
     M[i].lo = L.off_mat[i][2] ? base + L.off_mat[i][2] : nullptr;
@@ -303,14 +351,13 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
     }
   }
   const double beta = 1.0 / kT;
-  // m = 14: X0 is the linearised Fermi function at beta / 2^m, which shifts the
-  // effective beta of a state at beta |eps - mu| = 5 by (5 / 2^m)^2 / 12 < 1e-8
-  // relative, and keeps X0 in [0, 1] for |eps - mu| <= 2^(m+1) / beta
+  // at most m doubling steps (m = 14: beta (hi - lo) <= 32768); the device uses
+  // the fewest that the bracket allows, at least kMinM
   const int m = o->m > 0 ? o->m : 14;
   const int ns = o->ns_iters > 0 ? o->ns_iters : 3;
   const double tol = o->trace_tol > 0.0 ? o->trace_tol : 1e-7 * std::max(1.0, nocc);
-  const double c = beta / std::ldexp(1.0, m + 2);
   const size_t nn = (size_t)L.ld * L.ld;
+  const size_t eb = (o->precision == TB_PREC_TF32 || o->precision == TB_PREC_TF32X3) ? 4 : 2;
   int* skip = &st->done;
   int* errp = &st->err;
   float* res = reinterpret_cast<float*>(base + L.off_res);
@@ -318,7 +365,7 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
   TB_CUDA_TRY(ctx, cudaMemsetAsync(st, 0, sizeof(FoeState), s));
   int rc = sp2_launch_bounds(ctx, H, n, bparts, s);
   if (rc) return rc;
-  k_foe_bounds<<<1, 32, 0, s>>>(bparts, (n + 7) / 8, st, mu, kT);
+  k_foe_bounds<<<1, 32, 0, s>>>(bparts, (n + 7) / 8, st, mu, kT, m);
   TB_LAUNCH_CHECK(ctx);
 
   // the chemical-potential loop: a while graph node under capture, else
@@ -328,7 +375,7 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
   cudaStream_t ls = loop.body_stream;
   const int rounds = loop.graph ? 1 : o->mu_iters;
   auto gemm = [&](Mat& A, Mat& B, Mat& out, float alpha, float betac, const float* E, float gamma,
-                  double* prt) -> int {
+                  double* prt, int* skp = nullptr) -> int {
     GemmArgs g{};
     g.n = n;
     g.ld = L.ld;
@@ -340,7 +387,7 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
     g.ohi = out.hi;
     g.olo = out.lo;
     g.parts = prt;
-    g.skip = skip;
+    g.skip = skp ? skp : skip;
     g.err = errp;
     return tc_gemm(ctx, o->precision, g, &A.mh, &A.ml, &B.mh, &B.ml, ls);
   };
@@ -349,30 +396,48 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
   Mat* zf = &M[2];
   auto expansion = [&]() -> int {
     int r;
-    Mat* X = &M[0];
+    Mat* E[2] = {&M[0], &M[5]};
     Mat* A = &M[1];
     Mat* Z = &M[2];
     Mat* T = &M[3];
     Mat* Y = &M[4];
-    k_foe_x0<<<1184, 256, 0, ls>>>(H, n, L.ld, st, c, X->m);
+    k_foe_x0<<<1184, 256, 0, ls>>>(H, n, L.ld, st, Y->m);
     TB_LAUNCH_CHECK(ctx);
-    if ((r = tc_split(ctx, o->precision, X->m, nn, X->hi, X->lo, skip, ls))) return r;
+    if ((r = tc_split(ctx, o->precision, Y->m, nn, Y->hi, Y->lo, skip, ls))) return r;
+    // E0 = L - 4/3 L L^2 in both iterate buffers: the first doubling step the
+    // device runs may be any of the m issued ones
+    if ((r = gemm(*Y, *Y, *A, 1.0f, 0.0f, nullptr, 0.0f, nullptr))) return r;
+    if ((r = gemm(*Y, *A, *E[0], -4.0f / 3.0f, 1.0f, Y->m, 0.0f, nullptr))) return r;
+    {
+      const void* src[3] = {E[0]->m, E[0]->hi, E[0]->lo};
+      void* dst[3] = {E[1]->m, E[1]->hi, E[1]->lo};
+      const size_t words[3] = {nn, eb * nn / 4, eb * nn / 4};
+      for (int i = 0; i < 3; ++i) {
+        if (!src[i]) continue;
+        k_foe_copy<<<1184, 256, 0, ls>>>(st, static_cast<const uint32_t*>(src[i]), static_cast<uint32_t*>(dst[i]),
+                                         words[i]);
+        TB_LAUNCH_CHECK(ctx);
+      }
+    }
     for (int step = 0; step < m; ++step) {
+      Mat* X = E[step & 1];
+      Mat* Xn = E[(step + 1) & 1];
+      int* sk = &st->skipd[step];  // leading steps beyond the device's m return at once
       // A = I + 4 E E
-      if ((r = gemm(*X, *X, *A, 4.0f, 0.0f, nullptr, 1.0f, nullptr))) return r;
+      if ((r = gemm(*X, *X, *A, 4.0f, 0.0f, nullptr, 1.0f, nullptr, sk))) return r;
       // Z1 = (32 A A - 144 A + 210 I) / 99, then Newton-Schulz
-      if ((r = gemm(*A, *A, *Z, 32.0f / 99.0f, -144.0f / 99.0f, A->m, 210.0f / 99.0f, nullptr))) return r;
+      if ((r = gemm(*A, *A, *Z, 32.0f / 99.0f, -144.0f / 99.0f, A->m, 210.0f / 99.0f, nullptr, sk))) return r;
       for (int k = 1; k < ns; ++k) {
-        if ((r = gemm(*A, *Z, *T, -1.0f, 0.0f, nullptr, 2.0f, nullptr))) return r;  // T = 2I - A Z
-        if ((r = gemm(*Z, *T, *Y, 1.0f, 0.0f, nullptr, 0.0f, nullptr))) return r;   // Z <- Z T
+        if ((r = gemm(*A, *Z, *T, -1.0f, 0.0f, nullptr, 2.0f, nullptr, sk))) return r;  // T = 2I - A Z
+        if ((r = gemm(*Z, *T, *Y, 1.0f, 0.0f, nullptr, 0.0f, nullptr, sk))) return r;   // Z <- Z T
         std::swap(Z, Y);
       }
       // E <- 2 E Z (trace partials of the last step); the product kernel
       // writes exactly symmetric results with their operand splits
       const bool last = step == m - 1;
-      if ((r = gemm(*X, *Z, *Y, 2.0f, 0.0f, nullptr, 0.0f, last ? parts : nullptr))) return r;
-      std::swap(X, Y);
+      if ((r = gemm(*X, *Z, *Xn, 2.0f, 0.0f, nullptr, 0.0f, last ? parts : nullptr, sk))) return r;
     }
+    Mat* X = E[m & 1];
     // E^2 and E^3 (with Tr E^3) for the canonical shift
     if ((r = gemm(*X, *X, *A, 1.0f, 0.0f, nullptr, 0.0f, nullptr))) return r;
     if ((r = gemm(*X, *A, *Z, 1.0f, 0.0f, nullptr, 0.0f, parts3))) return r;
@@ -396,7 +461,7 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
     TB_LAUNCH_CHECK(ctx);
   }
   const int fb = std::min(1184, (int)(((size_t)n * n + 255) / 256));
-  k_foe_finalize<<<fb, 256, 0, s>>>(st, n, L.ld, res, D, nocc, tol, m, mu, rep);
+  k_foe_finalize<<<fb, 256, 0, s>>>(st, n, L.ld, res, D, nocc, tol, mu, rep);
   TB_LAUNCH_CHECK(ctx);
   return TB_OK;
 }

@@ -296,6 +296,7 @@ int collect(tb_server* sv, tb_completion* out, int max_out, int* n_out) {
     c.traj = sl.req.traj;
     c.status = reinterpret_cast<const int*>(T.host + 8)[0];
     c.solver_iters = reinterpret_cast<const int*>(T.host + 8)[1];  // iters / mu_iters
+    c.solver_m = sv->o.kT > 0.0 ? reinterpret_cast<const int*>(T.host + 8)[2] : 0;  // tb_fermi_report.m
     c.step = (int64_t)T.host[7];
     c.t_submit = sl.req.t_submit;
     c.t_launch = sl.t_launch;

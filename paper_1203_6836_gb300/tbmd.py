@@ -104,7 +104,7 @@ class tb_server_opts(ctypes.Structure):
 
 class tb_completion(ctypes.Structure):
     _fields_ = [("request", ctypes.c_int64), ("traj", ctypes.c_int), ("status", ctypes.c_int),
-                ("solver_iters", ctypes.c_int), ("step", ctypes.c_int64), ("t_submit", ctypes.c_double), ("t_launch", ctypes.c_double),
+                ("solver_iters", ctypes.c_int), ("solver_m", ctypes.c_int), ("step", ctypes.c_int64), ("t_submit", ctypes.c_double), ("t_launch", ctypes.c_double),
                 ("t_done", ctypes.c_double), ("gpu_ms", ctypes.c_double), ("energies", ctypes.c_double * 8)]
 
 

@@ -3,7 +3,7 @@ the GPU against the oracle's diagonalised Fermi-Dirac density matrix with
 the canonical chemical potential (bisection to Tr D = N_occ).
 
 Tolerance: the tf32x3 products carry ~2^-22 relative error; in the deviation
-form E = X - I/2 those errors add up over the m = 16 doubling steps instead
+form E = X - I/2 those errors add up over the m (8..11 here) doubling steps instead
 of being doubled m times, leaving ~1e-6 absolute error in D.  mu is compared
 only where it is unique at this temperature (no wide gap around it)."""
 
@@ -97,3 +97,33 @@ def test_fermi_low_temperature_limit_is_the_projector(ctx):
     proj = density.density_T0(H, 100).D
     (D, rep), = _run(ctx, H, 100.0, 0.05)
     assert _err(D, proj) < 5e-6
+
+
+def test_fermi_spectrum_too_wide_for_the_doublings(ctx):
+    """beta (eps_max - eps_min + 80 kT + 2 eV) > 2^(m+1) for the largest m
+    allowed: the third-order start is not defined there, and the report says
+    TB_ERR_ARG (no expansion runs)."""
+    H, nocc = _c1_H()
+    Ht = torch.as_tensor(H, device="cuda")
+    D = torch.empty_like(Ht)
+    kT = 0.011  # Gershgorin width 21.6 eV: beta (21.6 + 0.9 + 2) ~ 2230 > 2^11
+    s = FermiSolver(ctx, H.shape[0], fermi_opts("tf32x3", m=10))
+    s(Ht, nocc, kT, D)
+    torch.cuda.synchronize()
+    rep = fermi_report_to_dict(s.report)
+    assert rep["status"] == tbmd.TB_ERR_ARG
+    assert rep["mu_iters"] == 0
+
+
+def test_fermi_uses_the_fewest_doublings_the_spectrum_allows(ctx):
+    """The device takes the smallest m >= 8 with beta (hi - lo) <= 2^(m+1):
+    8 for the 24-atom system at kT = 0.1 eV (beta (hi - lo) ~ 320), 11 at
+    kT = 0.011 eV (~2230)."""
+    H, nocc = _c1_H()
+    (D, rep), = _run(ctx, H, nocc, 0.1)
+    assert rep["m"] == 8 and rep["status"] == tbmd.TB_OK
+    assert _err(D, density.density_fermi(H, nocc, 0.1).D) < 1e-6
+    (D, rep), = _run(ctx, H, nocc, 0.011)
+    assert rep["m"] == 11
+    if rep["status"] == tbmd.TB_OK:
+        assert _err(D, density.density_fermi(H, nocc, 0.011).D) < 1e-5

@@ -1,8 +1,9 @@
 """Pins of the numerical methods the GPU path uses where the paper gives no
 recipe, checked in FP64 NumPy against exact definitions (no GPU):
 
-* the recursive Fermi-operator expansion in deviation form (m = 14 doublings
-  from the linearised start) against the Fermi function;
+* the recursive Fermi-operator expansion in deviation form against the
+  Fermi function: m = 14 doublings from the linearised start, m = 10 from the
+  third-order start E0 = L - 4/3 L^3 (with a linearised m = 10 control);
 * the second-order canonical shift of a Fermi density matrix and its
   remainder bound |u|^3/6 Tr[D(I - D)];
 * the quadratic minimax start of the Newton-Schulz inverse of I + 4E^2 and
@@ -52,6 +53,33 @@ def test_recursive_fermi_expansion_deviation_form(kT):
     assert np.abs(0.5 * np.eye(n) + E - ref).max() > 1e-3
 
 
+def _start3(H, mu, beta, m):
+    """E0 = L - 4/3 L^3, L = -beta/2^(m+2) (H - mu I): -tanh(Z)/2 to third order."""
+    L = -beta / 2.0 ** (m + 2) * (H - mu * np.eye(H.shape[0]))
+    return L - 4.0 / 3.0 * L @ L @ L
+
+
+@pytest.mark.parametrize("kT", [0.1, 0.5])
+def test_fermi_expansion_third_order_start(kT):
+    """From E0 = L - 4/3 L^3, m doublings give the Fermi function to ~1e-14
+    at m = 10 and ~1e-11 at m = 8 (start error 2 z^4/15, not amplified by the
+    doublings); the linearised start E0 = L misses by > 1e-7 at m = 8."""
+    n = 60
+    H, eps, Q = _random_h(n, seed=1)
+    mu, beta = 0.3, 1.0 / kT
+    ref = _fermi_matrix(eps, Q, mu, kT)
+    I = np.eye(n)
+
+    def expand(E, m):
+        for _ in range(m):
+            E = 2.0 * E @ np.linalg.inv(I + 4.0 * E @ E)
+        return np.abs(0.5 * I + E - ref).max()
+
+    assert expand(_start3(H, mu, beta, 10), 10) < 1e-12
+    assert expand(_start3(H, mu, beta, 8), 8) < 1e-10
+    assert expand(-beta / 2.0 ** 10 * (H - mu * I), 8) > 1e-7
+
+
 def _z1(A):
     """Quadratic start Z1 = (210 I - 144 A + 32 A^2) / 99 for A with spectrum in [1, 2]."""
     n = A.shape[0]
@@ -82,13 +110,14 @@ def test_newton_schulz_quadratic_start():
 
 
 def test_fermi_expansion_with_newton_schulz_inverse():
-    """The expansion with the inverse replaced by Z1 and two Newton-Schulz steps
-    (the products the tensor-core path forms) still equals the Fermi function to 1e-8."""
-    n, m, kT = 60, 14, 0.1
+    """The expansion from the third-order start with the inverse replaced by Z1
+    and two Newton-Schulz steps (the products the tensor-core path forms, m = 10)
+    still equals the Fermi function to 1e-8."""
+    n, m, kT = 60, 10, 0.1
     H, eps, Q = _random_h(n, seed=7)
     mu = 0.1
     I = np.eye(n)
-    E = -(1.0 / kT) / 2.0 ** (m + 2) * (H - mu * I)
+    E = _start3(H, mu, 1.0 / kT, m)
     for _ in range(m):
         A = I + 4.0 * E @ E
         Z = _z1(A)
