@@ -2,8 +2,8 @@
 recipe, checked in FP64 NumPy against exact definitions (no GPU):
 
 * the recursive Fermi-operator expansion in deviation form against the
-  Fermi function: m = 14 doublings from the linearised start, m = 10 from the
-  third-order start E0 = L - 4/3 L^3 (with a linearised m = 10 control);
+  Fermi function: m = 14 doublings from the linearised start, m = 10 and 8
+  from the third-order start E0 = L - 4/3 L^3 (with a linearised m = 8 control);
 * the second-order canonical shift of a Fermi density matrix and its
   remainder bound |u|^3/6 Tr[D(I - D)];
 * the quadratic minimax start of the Newton-Schulz inverse of I + 4E^2 and
