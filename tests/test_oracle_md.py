@@ -76,6 +76,52 @@ def test_forces_are_minus_energy_gradient_at_fixed_n(which):
     assert np.allclose(F.sum(axis=0), 0.0, atol=1e-9)
 
 
+@pytest.mark.parametrize("which,kT", [("molecule", 0.5), ("random24", 0.2)])
+def test_finite_temperature_forces_are_minus_free_energy_gradient(which, kT):
+    """At T_e > 0 the same force expression, evaluated on the Fermi-Dirac D,
+    is -d(U - T_e S)/dR at fixed n: D makes U - T_e S stationary at fixed
+    Tr D (Eqs. Etot, Entropy), so its response drops out of the derivative.
+    Five-point central differences (h = 2e-4 A: truncation O(h^4), rounding
+    ~1e-7 eV/A) of U - T_e S with D and mu recomputed at every displaced
+    geometry; U alone differs by the entropy term's gradient."""
+    if which == "molecule":
+        R, types, box = _water_molecule()
+        n_aux = np.array([1.2, -0.5, -0.7])
+        nocc = 4.0
+    else:
+        s = water_24_atoms()
+        R, types, box = s.R, s.types, s.box
+        n_aux = 0.3 * np.sin(np.arange(s.natoms))
+        n_aux -= n_aux.mean()
+        nocc = s.n_occ(P)
+
+    def energies(Rx):
+        H, G, res, q, pairs = md.electronic_state(Rx, types, box, P, n_aux, nocc, kT=kT)
+        U = observables.potential_energy(Rx, types, box, P, res.D, q, n_aux, pairs)
+        return U, kT * density.entropy_kB(np.linalg.eigvalsh(res.D))
+
+    H, G, res, q, pairs = md.electronic_state(R, types, box, P, n_aux, nocc, kT=kT)
+    F = observables.forces(R, types, box, P, res.D, q, n_aux, pairs)
+    h = 2e-4
+    atoms = range(len(types)) if which == "molecule" else [0, 5, 9, 17]
+    worst_u = 0.0
+    for a in atoms:
+        for k in range(3):
+            U, TS = {}, {}
+            for j in (-2, -1, 1, 2):
+                Rx = R.copy()
+                Rx[a, k] += j * h
+                U[j], TS[j] = energies(Rx)
+
+            def d5(f):
+                return (-f[2] + 8.0 * f[1] - 8.0 * f[-1] + f[-2]) / (12.0 * h)
+
+            fd = -(d5(U) - d5(TS))
+            assert F[a, k] == pytest.approx(fd, rel=1e-6, abs=1e-6)
+            worst_u = max(worst_u, abs(F[a, k] + d5(U)))
+    assert worst_u > 0.1  # the entropy term's gradient (0.45 and 4 eV/A here) is not negligible
+
+
 def test_energy_at_scf_is_the_scc_tb_energy():
     """At n = q: E = 2 Tr[hD] + 1/2 q^T gamma q (+ E_pair)."""
     R, types, box = _water_molecule()
