@@ -41,3 +41,29 @@ def test_status_strings_and_argument_errors_without_gpu():
     assert lib.tb_server_submit(None, 0, None) == tbmd.TB_ERR_ARG
     assert lib.tb_server_destroy(None) == tbmd.TB_OK
     assert ctypes.sizeof(tbmd.tb_completion) == 8 + 4 + 4 + 4 + 4 + 8 + 4 * 8 + 8 * 8
+
+
+def test_fermi_options_and_layouts_without_gpu():
+    """dm_fermi_workspace_size validates its options on the host; the workspace
+    holds six matrices (the iterate's two buffers, A, Z, T, Y) with their tf32x3
+    operand splits; the completion record carries the Fermi report's m at the
+    offsets the server reads."""
+    lib = tbmd.lib()
+    size = ctypes.c_size_t()
+    ok = tbmd.tb_fermi_opts(precision=tbmd.PREC["tf32x3"], m=14, ns_iters=3, mu_iters=30)
+    assert lib.dm_fermi_workspace_size(4094, ctypes.byref(ok), ctypes.byref(size)) == tbmd.TB_OK
+    assert size.value >= 6 * 12 * 4096 * 4096
+    for bad in (dict(m=41), dict(ns_iters=13), dict(mu_iters=0), dict(mu_iters=41), dict(precision=99)):
+        kw = dict(precision=tbmd.PREC["tf32x3"], m=14, ns_iters=3, mu_iters=30)
+        kw.update(bad)
+        o = tbmd.tb_fermi_opts(**kw)
+        assert lib.dm_fermi_workspace_size(100, ctypes.byref(o), ctypes.byref(size)) == tbmd.TB_ERR_ARG, bad
+    assert lib.dm_fermi_workspace_size(0, ctypes.byref(ok), ctypes.byref(size)) == tbmd.TB_ERR_ARG
+    # the server copies the report's first ints: status, mu_iters, m
+    assert tbmd.tb_fermi_report.status.offset == 0
+    assert tbmd.tb_fermi_report.mu_iters.offset == 4
+    assert tbmd.tb_fermi_report.m.offset == 8
+    assert tbmd.tb_completion.solver_iters.offset == 16
+    assert tbmd.tb_completion.solver_m.offset == 20
+    assert tbmd.tb_completion.step.offset == 24
+
