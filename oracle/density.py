@@ -1,12 +1,12 @@
 """Density matrices: diagonalisation (the plain definition) and the SP2 recursion.
 
 At T_e = 0 the density matrix is the step function of the Hamiltonian,
-D = theta(mu0 I - H) (App. D.2, "rho = theta(mu0 I - H[n])"): the projector on
+D = theta(mu0 I - H) (App. D.2, with H = H[n]): the projector on
 the N_occ lowest eigenvectors, doubly occupied (so Tr D = N_occ = N_e/2).  At
 T_e > 0 it is the Fermi operator D = (exp(beta (H - mu0 I)) + 1)^-1 of
 Eq. EL_4c / Eq. DM_perp, with mu0 fixed by Tr D = N_occ (canonical reading).
 
-SP2 ("recursive second order spectral projection", Sec. III.B): the paper
+SP2 (the recursive second-order spectral projection of Sec. III.B): the paper
 defers its details to the cited SP2 work.  Reading used here and on the GPU:
   X0 = (eps_max I - H)/(eps_max - eps_min) with Gershgorin bounds;
   at each step compute Tr X and Tr X^2 (= ||X||_F^2 for symmetric X); stop when

@@ -1,6 +1,6 @@
 // SP2 purification (rows a2, a3, a4 FP64 path, a6): D = theta(mu0 I - H).
 //
-// Sec. III.B ("recursive second order spectral projection"), with the
+// The recursive second-order spectral projection of Sec. III.B, with the
 // reading: X0 = (eps_max I - H)/(eps_max - eps_min) from Gershgorin bounds;
 // each projection replaces X by X^2 or by 2X - X^2, the branch chosen from
 // Tr X and Tr X^2 = ||X||_F^2 (look-ahead rule: the projection whose trace
