@@ -101,18 +101,29 @@ class SP2Result:
     eps_min: float
     eps_max: float
     idem_history: list
+    pre_drop_norms: np.ndarray = None  # tau > 0: bs x bs block norms of the last iterate before its drop
 
 
-def _drop_blocks(X: np.ndarray, bs: int, tau: float) -> np.ndarray:
+def block_norms(X: np.ndarray, bs: int) -> np.ndarray:
+    """Frobenius norm of every bs x bs block of X (ragged edge blocks are smaller)."""
     n = X.shape[0]
     nb = (n + bs - 1) // bs
-    Y = X.copy()
+    out = np.zeros((nb, nb))
     for I in range(nb):
         for J in range(nb):
-            blk = Y[I * bs:(I + 1) * bs, J * bs:(J + 1) * bs]
-            if np.sqrt(np.sum(blk * blk)) < tau:
-                blk[...] = 0.0
-    return Y
+            blk = X[I * bs:(I + 1) * bs, J * bs:(J + 1) * bs]
+            out[I, J] = np.sqrt(np.sum(blk * blk))
+    return out
+
+
+def _drop_blocks(X: np.ndarray, bs: int, tau: float) -> tuple[np.ndarray, np.ndarray]:
+    """Zero every bs x bs block of X whose Frobenius norm is below tau; also
+    returns the block norms before the drop."""
+    norms = block_norms(X, bs)
+    Y = X.copy()
+    for I, J in zip(*np.nonzero(norms < tau)):
+        Y[I * bs:(I + 1) * bs, J * bs:(J + 1) * bs] = 0.0
+    return Y, norms
 
 
 def sp2(H: np.ndarray, n_occ: float, tol: float = 1e-10, max_iter: int = 100,
@@ -124,8 +135,9 @@ def sp2(H: np.ndarray, n_occ: float, tol: float = 1e-10, max_iter: int = 100,
     emin, emax = gershgorin(H)
     n = H.shape[0]
     X = (emax * np.eye(n) - H) / (emax - emin)
+    norms = None
     if tau > 0:
-        X = _drop_blocks(X, bs, tau)
+        X, norms = _drop_blocks(X, bs, tau)
     branches, hist = [], []
     converged = False
     idem = float("nan")
@@ -146,10 +158,10 @@ def sp2(H: np.ndarray, n_occ: float, tol: float = 1e-10, max_iter: int = 100,
         X2 = X @ X
         X = X2 if b == 0 else 2.0 * X - X2
         if tau > 0:
-            X = _drop_blocks(X, bs, tau)
+            X, norms = _drop_blocks(X, bs, tau)
         branches.append(b)
     return SP2Result(X=X, iters=len(branches), branches=branches, converged=converged,
-                     idem=idem, eps_min=emin, eps_max=emax, idem_history=hist)
+                     idem=idem, eps_min=emin, eps_max=emax, idem_history=hist, pre_drop_norms=norms)
 
 
 def idempotency_fro(X: np.ndarray) -> float:

@@ -113,3 +113,101 @@ def test_fermi_dirac_trace_limit_and_entropy():
     # entropy: a half-filled level contributes 2 ln 2, filled/empty nothing
     assert density.entropy_kB(np.array([0.5])) == pytest.approx(2 * np.log(2))
     assert density.entropy_kB(np.array([0.0, 1.0])) == 0.0
+
+
+# ---------------------------------------------------------------- drop rule
+# Sec. III.B thresholds the iterate after each projection; the block-sparse
+# reading drops every 32 x 32 block whose Frobenius norm is below tau, after
+# X0 and after every projection.  The pins below separate that rule from its
+# near neighbours: an element-max rule (drop a block when max |x| < tau), an
+# element-wise rule (zero single elements below tau), a sum-of-|x| norm, a
+# strict/non-strict comparison at tau, and a recursion that does not drop
+# after X0.
+
+def test_block_rule_is_the_frobenius_norm_of_the_block():
+    tau = 1e-5
+    bs = 32
+    X = np.zeros((2 * bs, 2 * bs))
+    # every element below tau, Frobenius norm 3.2 tau: kept whole
+    X[:bs, bs:] = 0.1 * tau
+    # one element 2 tau, the others 1e-3 tau: kept with its small elements
+    X[bs:, :bs] = 1e-3 * tau
+    X[bs + 3, 5] = 2.0 * tau
+    # uniform blocks of norm 0.99 tau (dropped) and 1.01 tau (kept); their
+    # sum of |x| (32 x 32 elements of 0.99 tau / 32) is about 32 tau
+    X[:bs, :bs] = 0.99 * tau / bs
+    X[bs:, bs:] = 1.01 * tau / bs
+    Y, norms = density._drop_blocks(X, bs, tau)
+    assert norms[0, 1] == pytest.approx(3.2 * tau, rel=1e-12)
+    assert np.array_equal(Y[:bs, bs:], X[:bs, bs:])
+    assert np.array_equal(Y[bs:, :bs], X[bs:, :bs])
+    assert np.all(Y[:bs, :bs] == 0.0)
+    assert np.array_equal(Y[bs:, bs:], X[bs:, bs:])
+    # exactly tau is kept (drop only below tau)
+    Z = np.zeros((bs, bs))
+    Z[0, 0] = tau
+    assert np.array_equal(density._drop_blocks(Z, bs, tau)[0], Z)
+
+
+def test_block_rule_on_a_ragged_edge():
+    """n = 40 with 32 x 32 blocks: the edge blocks are 32 x 8, 8 x 32, 8 x 8 and
+    their norms are taken over the elements they hold."""
+    tau = 1e-5
+    X = np.zeros((40, 40))
+    X[32:, 32:] = 0.2 * tau          # 8 x 8 of 0.2 tau: norm 1.6 tau, kept
+    X[:32, 32:] = 0.01 * tau         # 32 x 8 of 0.01 tau: norm 0.16 tau, dropped
+    X[32:, :32] = 0.01 * tau
+    Y, norms = density._drop_blocks(X, 32, tau)
+    assert norms.shape == (2, 2)
+    assert norms[1, 1] == pytest.approx(1.6 * tau, rel=1e-12)
+    assert np.array_equal(Y[32:, 32:], X[32:, 32:])
+    assert np.all(Y[:32, 32:] == 0.0) and np.all(Y[32:, :32] == 0.0)
+
+
+def test_threshold_is_applied_to_X0():
+    """Two 64-orbital blocks coupled between the highest occupied state of one
+    and the lowest empty state of the other (N_occ = 40), every coupling block
+    of X0 below tau (largest 0.9 tau): dropped at X0, the coupling stays exactly
+    zero.  The first projection (X^2) raises that coupling above tau (both
+    states lie below the middle of the Gershgorin interval), so a recursion
+    that only drops after projections keeps it and returns a coupled D."""
+    tau, bs, nocc = 1e-5, 32, 40
+    rng = np.random.default_rng(3)
+    Qa = np.linalg.qr(rng.normal(size=(64, 64)))[0]
+    Qb = np.linalg.qr(rng.normal(size=(64, 64)))[0]
+    ea = np.sort(np.concatenate([rng.uniform(-2, -0.4, 32), rng.uniform(0.4, 2, 32)]))
+    eb = np.sort(np.concatenate([rng.uniform(-2, -0.4, 32), rng.uniform(0.4, 2, 32)]))
+    A, B = Qa @ np.diag(ea) @ Qa.T, Qb @ np.diag(eb) @ Qb.T
+    levels = np.sort(np.concatenate([ea, eb]))
+    mu = 0.5 * (levels[nocc - 1] + levels[nocc])
+    ia, ib = np.nonzero(ea < mu)[0][-1], np.nonzero(eb > mu)[0][0]
+    C = np.outer(Qa[:, ia], Qb[:, ib])
+
+    def x0(scale):
+        H = np.zeros((128, 128))
+        H[:64, :64], H[64:, 64:] = A, B
+        H[:64, 64:] = scale * C
+        H[64:, :64] = H[:64, 64:].T
+        lo, hi = density.gershgorin(H)
+        return H, (hi * np.eye(128) - H) / (hi - lo)
+
+    scale = 1.0
+    for _ in range(4):  # the Gershgorin width moves with the coupling
+        H, X0 = x0(scale)
+        scale *= 0.9 * tau / density.block_norms(X0, bs)[:2, 2:].max()
+    H, X0 = x0(scale)
+    assert density.block_norms(X0, bs)[:2, 2:].max() == pytest.approx(0.9 * tau, rel=1e-6)
+    s = density.sp2(H, nocc, tol=1e-10, tau=tau, bs=bs)
+    assert s.converged
+    assert np.all(s.X[:64, 64:] == 0.0)
+    # negative control: the same recursion without the drop at X0
+    X = X0
+    assert density.block_norms(X0 @ X0, bs)[:2, 2:].max() > tau  # the first projection is X^2
+    for _ in range(100):
+        t1, t2 = np.trace(X), np.sum(X * X)
+        if t1 - t2 <= 1e-10:
+            break
+        X2 = X @ X
+        X = X2 if abs(t2 - nocc) <= abs(2 * t1 - t2 - nocc) else 2 * X - X2
+        X = density._drop_blocks(X, bs, tau)[0]
+    assert np.abs(X[:64, 64:]).max() > 1e-6

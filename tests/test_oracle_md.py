@@ -226,3 +226,27 @@ def test_xlbomd_finite_temperature_entropy_term_restores_conservation():
     assert np.max(np.abs(E - E[0])) < 0.05 * np.max(np.abs(E_no_S - E_no_S[0]))
     # the charges still follow q at T_e > 0
     assert max(np.max(np.abs(a - b)) for a, b in zip(tr.n, tr.q)) < 0.05
+
+
+def test_energy_drift_measures_on_known_series():
+    """Table II's two measures on series with a known answer: sigma is the
+    standard deviation of E_tot about its mean (eV), drift the least-squares
+    slope per atom in eV/atom/ps (time step in fs)."""
+    from oracle.md import energy_drift
+    N, dt, natoms = 401, 0.25, 10
+    k = np.arange(N)
+    # a pure line rising 1e-3 eV per step: slope 1e-3 eV / 0.25 fs = 4 eV/ps,
+    # 0.4 eV/atom/ps; sigma of an evenly spaced line = step * sqrt((N^2 - 1)/12)
+    sigma, drift = energy_drift(list(-12.5 + 1e-3 * k), dt, natoms)
+    assert drift == pytest.approx(0.4, rel=1e-10)
+    assert sigma == pytest.approx(1e-3 * np.sqrt((N * N - 1) / 12.0), rel=1e-10)
+    # a palindromic fluctuation (E_k = E_{N-1-k}) has no slope; alternating
+    # +-eps about the mean gives sigma = eps
+    eps = 3e-6
+    E = np.where((k % 4 == 0) | (k % 4 == 3), eps, -eps)[:400]
+    sigma, drift = energy_drift(list(5.0 + E), dt, natoms)
+    assert sigma == pytest.approx(eps, rel=1e-9)
+    assert abs(drift) < 1e-12
+    # both together: the slope is unchanged by the palindromic part
+    sigma, drift = energy_drift(list(5.0 + E + 2e-4 * k[:400]), dt, natoms)
+    assert drift == pytest.approx(2e-4 / 0.25e-3 / natoms, rel=1e-9)
