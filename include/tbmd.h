@@ -149,6 +149,24 @@ const char* tb_ctx_last_error(const tb_ctx* ctx);
 int tb_ctx_set_profiling(tb_ctx* ctx, int enable);
 int tb_ctx_sp2_launch_times(tb_ctx* ctx, int phase, float* ms, int cap, int* count);
 
+/* Execution controls (no counterpart in the paper; for testing and tuning).
+ * tb_ctx_set_grid_limit caps the CTAs of the persistent tensor-core grids
+ * (dense projections, Fermi-expansion products, block-sparse products) at
+ * max_ctas (0: one CTA per SM, the default).  A smaller grid makes every CTA
+ * walk more tiles, so a small matrix runs the same multi-round schedule
+ * (several tiles per CTA, reuse of the two TMEM accumulators, 64-column half
+ * units in the last round) as a large one on the whole GPU; results are the
+ * same up to the order of the FP64 trace sums.  TB_ERR_ARG for max_ctas < 0.
+ * tb_ctx_set_wait_limit sets the time limit, in ns of the device's global
+ * timer (1 .. 2e9; default 2e9), of the pipeline waits (data and accumulator
+ * barriers) of the dense-projection and Fermi-product kernels.  A wait that
+ * runs out makes the kernel stop its pipeline, wait (at the full 2 s limit)
+ * for its own copies and MMAs in flight, free its TMEM and return; the call's
+ * report then says TB_ERR_TIMEOUT and the context stays usable.  Both apply
+ * to calls enqueued after them. */
+int tb_ctx_set_grid_limit(tb_ctx* ctx, int max_ctas);
+int tb_ctx_set_wait_limit(tb_ctx* ctx, unsigned long long ns);
+
 /* ----------------------------------------------------------- a1: H[n] build */
 
 /* H[n] = h(R) + diag(sum_l gamma_il n_l) over every orbital of atom i
@@ -190,9 +208,11 @@ int dm_sp2(tb_ctx* ctx, const double* H, int n, double n_occ, const tb_sp2_opts*
  * exits); larger n fails with TB_ERR_ARG, other precisions with
  * TB_ERR_UNSUPPORTED.  The first call on a device, made with that device
  * current, looks up the array's device address: make it before any stream
- * capture.  Every call reuses the same array (its state is cleared at the
- * start of each call), so calls that overlap on the GPU race: serialise
- * them on one stream.  H, D, report as for dm_sp2. */
+ * capture.  That address stays valid while the device's context lives (a
+ * cudaDeviceReset while the library is in use invalidates it, like every
+ * other device pointer).  Every call reuses the same array (its state is
+ * cleared at the start of each call), so calls that overlap on the GPU race:
+ * serialise them on one stream.  H, D, report as for dm_sp2. */
 #define TB_SP2_STATIC_MAX_N 512
 int dm_sp2_static(tb_ctx* ctx, const double* H, int n, double n_occ, const tb_sp2_opts* opts,
                   double* D, tb_sp2_report* report, void* stream);

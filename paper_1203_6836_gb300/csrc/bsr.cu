@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int o = sy.order[u];
       const int buf = it & 1;
       ++it;
-      if (!mbar_wait(&tfull[buf], ((it - 1) >> 1) & 1, &s_abort)) break;
+      if (!mbar_wait_warp(&tfull[buf], ((it - 1) >> 1) & 1, &s_abort)) break;
       tc_fence_after();
       const bool has = sy.pair_ptr[o + 1] > sy.pair_ptr[o];
       const int I = sy.out_row[o], J = bn.col[o];
@@ -851,7 +851,7 @@ int run_bsr(tb_ctx* ctx, const double* H, int n, double nocc, const tb_sp2_opts*
   using Cf = Prec<P>;
   static unsigned long long attr_done = 0;
   if (int rc_attr = tb_smem_attr(ctx, k_bsr_step_tc<P>, Cf::smem_bytes, &attr_done)) return rc_attr;
-  const int grid = std::max(1, std::min(ctx->sm_count, kMaxGrid));
+  const int grid = tb_persistent_grid(ctx, kMaxGrid);
   tb_prof_mark(ctx, 0, 0, s);
   for (int k = 0; k <= o->max_iter; ++k) {
     a.k = k;

@@ -29,7 +29,20 @@ struct tb_ctx {
   // side stream on which the body of a conditional (while) graph node is
   // captured (created on first use)
   cudaStream_t loop_stream;
+  // cap on the CTAs of the persistent tensor-core grids (0: one per SM)
+  int grid_limit;
+  // time limit (ns) of the pipeline waits of the tensor-core kernels
+  unsigned long long wait_ns;
 };
+
+// CTAs of a persistent grid over `units` work units: one per SM, at most
+// `units`, at most the context's grid limit.
+static inline int tb_persistent_grid(const tb_ctx* ctx, int units) {
+  int g = ctx->sm_count;
+  if (ctx->grid_limit > 0 && ctx->grid_limit < g) g = ctx->grid_limit;
+  if (units < g) g = units;
+  return g < 1 ? 1 : g;
+}
 
 // Record the profiling event `idx` of phase `ph` on stream s (no-op when off).
 static inline void tb_prof_mark(tb_ctx* ctx, int ph, int idx, cudaStream_t s) {
@@ -149,6 +162,7 @@ struct SP2StepArgs {
   SP2State* st;
   const double* parts_in;   // [nparts_in * 2]
   double* parts_out;        // [ntiles * 2]
+  unsigned long long wait_ns;  // pipeline wait limit (0: the 2 s default)
 };
 
 // Tensor-core purification step (gemm_tc.cu).  X_in / X_out are FP32 masters
@@ -187,6 +201,7 @@ struct GemmArgs {
   double* parts;
   const int* skip;
   int* err;
+  unsigned long long wait_ns;  // pipeline wait limit (0: the 2 s default)
 };
 int tc_gemm(tb_ctx* ctx, int precision, const GemmArgs& g, const CUtensorMap* ah, const CUtensorMap* al,
             const CUtensorMap* bh, const CUtensorMap* bl, cudaStream_t s);

@@ -49,6 +49,8 @@ extern "C" int tb_ctx_create(tb_ctx** out) {
     return TB_ERR_CUDA;
   }
   ctx->sm_count = prop.multiProcessorCount;
+  ctx->grid_limit = 0;
+  ctx->wait_ns = 2000000000ull;
   ctx->cc_major = prop.major;
   ctx->cc_minor = prop.minor;
   if (!(prop.major == 10 && prop.minor == 3)) {
@@ -121,6 +123,20 @@ extern "C" int tb_ctx_set_profiling(tb_ctx* ctx, int enable) {
   if (enable) ctx->prof_on = 1;
   ctx->prof_n[0] = ctx->prof_n[1] = 0;
   if (!enable) ctx->prof_on = 0;
+  return TB_OK;
+}
+
+extern "C" int tb_ctx_set_grid_limit(tb_ctx* ctx, int max_ctas) {
+  if (!ctx) return TB_ERR_ARG;
+  if (max_ctas < 0) return tb_fail(ctx, TB_ERR_ARG, "grid limit %d < 0", max_ctas);
+  ctx->grid_limit = max_ctas;
+  return TB_OK;
+}
+
+extern "C" int tb_ctx_set_wait_limit(tb_ctx* ctx, unsigned long long ns) {
+  if (!ctx) return TB_ERR_ARG;
+  if (ns < 1 || ns > 2000000000ull) return tb_fail(ctx, TB_ERR_ARG, "wait limit %llu ns outside 1..2e9", ns);
+  ctx->wait_ns = ns;
   return TB_OK;
 }
 

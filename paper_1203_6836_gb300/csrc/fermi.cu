@@ -389,6 +389,7 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
     g.parts = prt;
     g.skip = skp ? skp : skip;
     g.err = errp;
+    g.wait_ns = ctx->wait_ns;
     return tc_gemm(ctx, o->precision, g, &A.mh, &A.ml, &B.mh, &B.ml, ls);
   };
   Mat* xf = &M[0];  // final iterate, E^2 and E^3 after an expansion

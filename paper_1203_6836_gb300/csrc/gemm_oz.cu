@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int s, t;
       pair_of(p, &s, &t);
       const int acc = p % kNacc;
-      if (!mbar_wait(&tfull[acc], (p / kNacc) & 1, &s_abort)) {
+      if (!mbar_wait_warp(&tfull[acc], (p / kNacc) & 1, &s_abort)) {
         ok = false;
         break;
       }

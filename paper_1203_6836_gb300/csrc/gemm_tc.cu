@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int nt = a.ld / BM;
   const Units wu = make_units(nt * (nt + 1) / 2, gridDim.x);
+  const unsigned long long wl = a.wait_ns ? a.wait_ns : kWaitNs;  // pipeline wait limit
   const int nk = a.ld / C::bk;
 
   if (threadIdx.x == 0) {
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tri_tile(t, nt, &I, &J);
       for (int kb = 0; kb < nk; ++kb, ++g) {
         const int s = g % C::stages;
-        if (g >= C::stages && !mbar_wait(&empty[s], ((g / C::stages) - 1) & 1, &s_abort)) break;
+        if (g >= C::stages && !mbar_wait(&empty[s], ((g / C::stages) - 1) & 1, &s_abort, wl)) break;
         uint8_t* base = smem + s * C::stage_bytes;
         mbar_expect_tx(&full[s], C::stage_bytes);
         tma_load_2d(base, &mh, &full[s], kb * C::bk, I * BM);
@@ -219,12 +220,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       // 8 KB into it, a whole number of 1 KB swizzle atoms
       const uint32_t boff = half > 0 ? 64 * 128 : 0;
       const int buf = it & 1;
-      if (it >= 2 && !mbar_wait(&tempty[buf], ((it >> 1) - 1) & 1, &s_abort)) break;
+      if (it >= 2 && !mbar_wait(&tempty[buf], ((it >> 1) - 1) & 1, &s_abort, wl)) break;
       tc_fence_after();
       const uint32_t d = tmem + buf * BN;
       for (int kb = 0; kb < nk; ++kb, ++g) {
         const int s = g % C::stages;
-        if (!mbar_wait(&full[s], (g / C::stages) & 1, &s_abort)) break;
+        if (!mbar_wait(&full[s], (g / C::stages) & 1, &s_abort, wl)) break;
         tc_fence_after();
         const uint32_t base = smem_u32(smem + s * C::stage_bytes);
 #pragma unroll
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int it = 0;
     for (int u = blockIdx.x; u < wu.U; u += gridDim.x, ++it) {
       const int buf = it & 1;
-      if (!mbar_wait(&tfull[buf], (it >> 1) & 1, &s_abort)) break;
+      if (!mbar_wait_warp(&tfull[buf], (it >> 1) & 1, &s_abort, wl)) break;
       tc_fence_after();
       int t, half, I, J;
       unit_tile(wu, u, &t, &half);
@@ -374,7 +375,7 @@ int sp2_tc_tile() { return BM; }
 int sp2_tc_num_tiles(int ld) { return (ld / BM) * (ld / BN); }
 int sp2_tc_num_parts(const tb_ctx* ctx, int ld) {
   const int nt = ld / BM;
-  return std::max(1, std::min(nt * (nt + 1) / 2, ctx->sm_count));
+  return tb_persistent_grid(ctx, nt * (nt + 1) / 2);
 }
 size_t sp2_tc_operand_bytes(int precision) {
   return (precision == TB_PREC_TF32 || precision == TB_PREC_TF32X3) ? 4 : 2;
@@ -439,6 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int nt = g.ld / BM;
   const int ntiles = nt * (nt + 1) / 2;
+  const unsigned long long wl = g.wait_ns ? g.wait_ns : kWaitNs;  // pipeline wait limit
   const int nk = g.ld / C::bk;
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::stages; ++s) {
@@ -467,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tri_tile(t, nt, &I, &J);
       for (int kb = 0; kb < nk; ++kb, ++gk) {
         const int s = gk % C::stages;
-        if (gk >= C::stages && !mbar_wait(&empty[s], ((gk / C::stages) - 1) & 1, &s_abort)) break;
+        if (gk >= C::stages && !mbar_wait(&empty[s], ((gk / C::stages) - 1) & 1, &s_abort, wl)) break;
         uint8_t* base = smem + s * C::stage_bytes;
         mbar_expect_tx(&full[s], C::stage_bytes);
         tma_load_2d(base, &ah, &full[s], kb * C::bk, I * BM);
@@ -491,12 +493,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     int gk = 0, it = 0;
     for (int t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x, ++it) {
       const int buf = it & 1;
-      if (it >= 2 && !mbar_wait(&tempty[buf], ((it >> 1) - 1) & 1, &s_abort)) break;
+      if (it >= 2 && !mbar_wait(&tempty[buf], ((it >> 1) - 1) & 1, &s_abort, wl)) break;
       tc_fence_after();
       const uint32_t d = tmem + buf * BN;
       for (int kb = 0; kb < nk; ++kb, ++gk) {
         const int s = gk % C::stages;
-        if (!mbar_wait(&full[s], (gk / C::stages) & 1, &s_abort)) break;
+        if (!mbar_wait(&full[s], (gk / C::stages) & 1, &s_abort, wl)) break;
         tc_fence_after();
         const uint32_t base = smem_u32(smem + s * C::stage_bytes);
 #pragma unroll
@@ -522,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int it = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
       const int buf = it & 1;
-      if (!mbar_wait(&tfull[buf], (it >> 1) & 1, &s_abort)) break;
+      if (!mbar_wait_warp(&tfull[buf], (it >> 1) & 1, &s_abort, wl)) break;
       tc_fence_after();
       int I, J;
       tri_tile(t, nt, &I, &J);

@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         double t1 = 0.0, t2 = 0.0;
         for (int t = 0; t < ntiles; ++t, ++t_epi) {
           const int acc = t_epi & 1;
-          if (!mbar_wait(&tfull[acc], (t_epi >> 1) & 1, &s_abort)) break;
+          if (!mbar_wait_warp(&tfull[acc], (t_epi >> 1) & 1, &s_abort)) break;
           tc_fence_after();
           int m0 = (t / nt_n) * BM, n0 = (t % nt_n) * BN;
           if constexpr (kSym) {
@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         double t1 = 0.0, t2 = 0.0;
         for (int t = (int)rank; t < ntiles; t += CS, ++t_epi) {
           const int acc = t_epi & 1;
-          if (!mbar_wait(&tfull[acc], (t_epi >> 1) & 1, &s_abort)) break;
+          if (!mbar_wait_warp(&tfull[acc], (t_epi >> 1) & 1, &s_abort)) break;
           tc_fence_after();
           int I, J;
           tri_tile(t, nt, &I, &J);

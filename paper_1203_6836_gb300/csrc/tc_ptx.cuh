@@ -35,18 +35,28 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: true when the phase completed, false on abort/timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+// Bounded wait: true when the phase completed, false on abort/timeout (after
+// limit_ns of %globaltimer time).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned long long limit_ns = kWaitNs) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = gtime();
   while (true) {
     if (mbar_try(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (gtime() - t0 > kWaitNs) {
+    if (gtime() - t0 > limit_ns) {
       *abort_flag = 1;
       return false;
     }
   }
+}
+// The same wait made by all 32 lanes of a warp that goes on to warp-collective
+// tcgen05.ld: true only when every lane saw the phase complete, so the lanes
+// break out (or go on) together even when a time limit runs out between them.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                               unsigned long long limit_ns = kWaitNs) {
+  const bool ok = mbar_wait(bar, parity, abort_flag, limit_ns);
+  return __all_sync(0xffffffffu, ok);
 }
 __device__ __forceinline__ void fence_barrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

@@ -124,6 +124,8 @@ _SIGS = {
     "tb_ctx_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "tb_ctx_sp2_launch_times": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_int)]),
+    "tb_ctx_set_grid_limit": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tb_ctx_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_ulonglong]),
     "tb_build_H": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P, _P, _P, _P]),
     "dm_sp2_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(tb_sp2_opts),
                                              ctypes.POINTER(ctypes.c_size_t)]),
@@ -248,6 +250,14 @@ def tb_ctx_sp2_launch_times(ctx: Context, phase: int, cap: int = 130) -> list[fl
     ctx.check(lib().tb_ctx_sp2_launch_times(ctx.handle, int(phase), buf, cap, ctypes.byref(cnt)),
               "tb_ctx_sp2_launch_times")
     return [float(buf[i]) for i in range(cnt.value)]
+
+
+def tb_ctx_set_grid_limit(ctx: Context, max_ctas: int) -> int:
+    return ctx.check(lib().tb_ctx_set_grid_limit(ctx.handle, int(max_ctas)), "tb_ctx_set_grid_limit")
+
+
+def tb_ctx_set_wait_limit(ctx: Context, ns: int) -> int:
+    return ctx.check(lib().tb_ctx_set_wait_limit(ctx.handle, int(ns)), "tb_ctx_set_wait_limit")
 
 
 def tb_build_H(ctx: Context, p: tb_params, sys: tb_system, R, n_aux, H, gamma, stream=None) -> int:

@@ -66,6 +66,7 @@ def test_fermi_water_systems(ctx, prec, tol):
                    np.zeros(w.natoms))
     ref = density.density_fermi(H, w.n_occ(P), 0.1)
     (D, rep), = _run(ctx, H, w.n_occ(P), 0.1, prec)
+    print(f"PARITY fermi {prec} water 300: dD={_err(D, ref.D):.3e}")
     assert rep["status"] == tbmd.TB_OK
     assert _err(D, ref.D) < tol
     # D is a function of H: it commutes with H
@@ -87,6 +88,7 @@ def test_fermi_dense_random_spectrum(ctx):
     H, _ = random_gapped_matrix(500, 200, gap=0.5, width=20.0, seed=3)
     ref = density.density_fermi(H, 200.0, 0.1)
     (D, rep), = _run(ctx, H, 200.0, 0.1)
+    print(f"PARITY fermi random 500: dD={_err(D, ref.D):.3e}")
     assert rep["status"] == tbmd.TB_OK
     assert _err(D, ref.D) < 2e-5
 

@@ -68,6 +68,7 @@ def test_grouped_batch_matches_eigh(ctx, mode):
         assert r["status"] == tbmd.TB_OK, (i, r)
         assert abs(r["trace"] - nocc[i]) < 5e-4
         assert err < 2e-5, (i, H.shape[0], err, ref.gap)
+    print(f"PARITY grouped mode {mode}: dD max {max(errs):.3e} median {np.median(errs):.3e}")
     assert np.median(errs) < 3e-6
 
 

@@ -124,6 +124,9 @@ def test_tensor_core_split_paths_dense_random(ctx, prec, n, nocc, seed):
     H, eps = random_gapped_matrix(n, nocc, gap=2.0, width=30.0, seed=seed)
     ref = density.density_T0(H, nocc)
     D, rep = _run(ctx, H, nocc, prec=prec, refine=3)
+    lo, hi = density.gershgorin(H)
+    print(f"PARITY sp2 {prec} random n={n}: dD={_err(D, ref.D):.3e} trace-N={rep['trace'] - nocc:.2e} "
+          f"delta0={ref.gap / (hi - lo):.2e}")
     assert rep["status"] == tbmd.TB_OK, rep
     assert rep["refine_iters"] >= 2
     assert _err(D, ref.D) < 2e-4, (_err(D, ref.D), rep)
@@ -150,6 +153,7 @@ def test_tensor_core_water_system_meets_target(ctx, prec, natoms):
     nocc = s.n_occ(P)
     ref = density.density_T0(H, int(nocc))
     D, rep = _run(ctx, H, nocc, prec=prec, refine=3)
+    print(f"PARITY sp2 {prec} water {natoms}: dD={_err(D, ref.D):.3e} trace-N={rep['trace'] - nocc:.2e}")
     assert rep["status"] == tbmd.TB_OK
     assert _err(D, ref.D) < 1e-6
     assert abs(rep["trace"] - nocc) < 1e-6
