@@ -18,6 +18,14 @@
 // small steps fill the SMs that a large one leaves idle.  Completion is seen
 // by querying each slot's event; the step's energies and solver status come
 // back by one small asynchronous copy into pinned memory.
+//
+// Trajectory memory comes from the stream-ordered allocator on the runtime's
+// own stream (cudaMallocAsync / cudaFreeAsync), so admitting or retiring a
+// trajectory does not synchronise the device under the steps in flight; the
+// pinned completion buffers are kept in a free list.  Admission itself (the
+// initial SCF) runs on the host and holds up dispatch while it lasts.  A
+// trajectory whose admission fails gets its queued requests back as
+// completions with the failure status.
 
 #include "common.cuh"
 
@@ -84,6 +92,8 @@ struct tb_server {
   std::vector<Slot> slots;
   std::deque<int> waiting;  // trajectories awaiting admission, FIFO
   std::list<Request> pending;  // submitted, not launched, in submission order
+  std::deque<tb_completion> failed;  // requests of trajectories whose admission failed
+  std::vector<double*> host_pool;    // free pinned completion buffers
   size_t used = 0;
   int64_t next_id = 0, submitted = 0, completed = 0;
   cudaStream_t init_s = nullptr;
@@ -124,7 +134,7 @@ int layout_for(tb_server* sv, int N, int n, Layout* L) {
   L->orb = take(sizeof(int32_t) * (N + 1));
   L->ws = take(ws);
   L->ws_bytes = ws;
-  L->total = o;
+  L->total = o + kAlign;  // one alignment unit of slack (the block is aligned in admit)
   return TB_OK;
 }
 
@@ -135,13 +145,21 @@ int admit(tb_server* sv, int t) {
   Layout L{};
   int rc = layout_for(sv, T.natoms, T.norb, &L);
   if (rc) return rc;
-  TB_CUDA_TRY(ctx, cudaMalloc(&T.mem, L.total));
-  sv->used += T.footprint;
-  TB_CUDA_TRY(ctx, cudaHostAlloc((void**)&T.host, sizeof(double) * kHostDoubles, cudaHostAllocDefault));
-  char* b = static_cast<char*>(T.mem);
   cudaStream_t s = sv->init_s;
+  // the pool guarantees less than the 1024-byte alignment the workspace
+  // needs: the layout holds one alignment unit of slack, and the state starts
+  // at the first boundary
+  TB_CUDA_TRY(ctx, cudaMallocAsync(&T.mem, L.total, s));
+  sv->used += T.footprint;
+  if (!sv->host_pool.empty()) {
+    T.host = sv->host_pool.back();
+    sv->host_pool.pop_back();
+  } else {
+    TB_CUDA_TRY(ctx, cudaHostAlloc((void**)&T.host, sizeof(double) * kHostDoubles, cudaHostAllocDefault));
+  }
+  char* b = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(T.mem) + kAlign - 1) & ~uintptr_t(kAlign - 1));
   const int N = T.natoms;
-  TB_CUDA_TRY(ctx, cudaMemsetAsync(b, 0, L.total, s));
+  TB_CUDA_TRY(ctx, cudaMemsetAsync(b, 0, L.total - kAlign, s));
   TB_CUDA_TRY(ctx, cudaMemcpyAsync(b + L.R, T.R0.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
   TB_CUDA_TRY(ctx, cudaMemcpyAsync(b + L.v, T.v0.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
   TB_CUDA_TRY(ctx, cudaMemcpyAsync(b + L.mass, T.mass.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
@@ -197,11 +215,14 @@ int admit(tb_server* sv, int t) {
   return TB_OK;
 }
 
+// Give back a trajectory's memory: its device block to the stream-ordered
+// pool (after the work already on the runtime's stream; its own steps have
+// completed), its pinned buffer to the free list.
 void release(tb_server* sv, int t) {
   Traj& T = sv->trajs[t];
   if (T.exec) cudaGraphExecDestroy(T.exec);
-  if (T.mem) cudaFree(T.mem);
-  if (T.host) cudaFreeHost(T.host);
+  if (T.mem) cudaFreeAsync(T.mem, sv->init_s);
+  if (T.host) sv->host_pool.push_back(T.host);
   if (T.mem) sv->used -= T.footprint;
   T.exec = nullptr;
   T.mem = nullptr;
@@ -224,6 +245,22 @@ int admit_waiting(tb_server* sv) {
     if (rc) {
       release(sv, t);
       T.state = T_FAILED;
+      // its queued requests can never run: hand them back as failed completions
+      for (auto it = sv->pending.begin(); it != sv->pending.end();) {
+        if (it->traj != t) {
+          ++it;
+          continue;
+        }
+        tb_completion c{};
+        c.request = it->id;
+        c.traj = t;
+        c.status = rc;
+        c.t_submit = it->t_submit;
+        c.t_launch = c.t_done = sv->now();
+        sv->failed.push_back(c);
+        T.queued -= 1;
+        it = sv->pending.erase(it);
+      }
       return rc;
     }
   }
@@ -283,6 +320,11 @@ int dispatch(tb_server* sv) {
 // Collect finished slots into out[]; returns the count.
 int collect(tb_server* sv, tb_completion* out, int max_out, int* n_out) {
   int k = 0;
+  while (!sv->failed.empty() && k < max_out) {
+    out[k++] = sv->failed.front();
+    sv->failed.pop_front();
+    sv->completed += 1;
+  }
   for (Slot& sl : sv->slots) {
     if (!sl.busy || k >= max_out) continue;
     const cudaError_t q = cudaEventQuery(sl.done);
@@ -391,6 +433,8 @@ extern "C" int tb_server_destroy(tb_server* sv) {
     if (sl.s) cudaStreamSynchronize(sl.s);
   }
   for (size_t t = 0; t < sv->trajs.size(); ++t) release(sv, (int)t);
+  if (sv->init_s) cudaStreamSynchronize(sv->init_s);
+  for (double* h : sv->host_pool) cudaFreeHost(h);
   for (Slot& sl : sv->slots) {
     if (sl.start) cudaEventDestroy(sl.start);
     if (sl.done) cudaEventDestroy(sl.done);
@@ -515,6 +559,18 @@ extern "C" int tb_server_replay(tb_server* sv, int count, const double* arrival_
   }
   if (!sv->pending.empty() || any_busy(sv))
     return tb_fail(sv->ctx, TB_ERR_ARG, "replay needs a server with no request outstanding");
+  {
+    // free retired trajectories and admit what fits first: nothing retires
+    // during the replay, so a trajectory not admitted now never runs in it
+    int k = 0;
+    int rc = progress(sv, nullptr, 0, &k);
+    if (rc) return rc;
+  }
+  for (int i = 0; i < count; ++i) {
+    const int st = sv->trajs[traj[i]].state;
+    if (st != T_IDLE && st != T_RUNNING)
+      return tb_fail(sv->ctx, TB_ERR_ARG, "request %d names trajectory %d, which is not admitted", i, traj[i]);
+  }
   const int64_t first = sv->next_id;
   const double base = sv->now();
   std::vector<tb_completion> buf(sv->slots.size());
@@ -537,7 +593,11 @@ extern "C" int tb_server_replay(tb_server* sv, int count, const double* arrival_
         ++done;
       }
     }
-    if (k == 0) std::this_thread::yield();
+    if (k == 0) {
+      if (next == count && !any_busy(sv) && sv->failed.empty())
+        return tb_fail(sv->ctx, TB_ERR_ARG, "replay stalled: %d of %d requests cannot run", count - done, count);
+      std::this_thread::yield();
+    }
   }
   return TB_OK;
 }

@@ -192,12 +192,16 @@ class Server:
         return tbmd.tb_server_poll(self.ctx, self.handle, wait, max_out)
 
     def drain(self) -> list:
-        """Poll until nothing is queued or in flight; all completions."""
+        """Poll until nothing is in flight and nothing queued can start; all
+        completions.  Requests of trajectories still waiting for admission stay
+        queued (nothing that runs can free memory for them): stats()["queued"]
+        counts them."""
         out = []
         while True:
             out += self.poll(wait=True)
-            st = self.stats()
-            if st["running"] == 0 and st["queued"] == 0:
+            if self.stats()["running"] == 0:
+                # poll has dispatched whatever could start: nothing did
+                out += self.poll(wait=False)
                 return out
 
     def retire(self, traj: int):

@@ -80,10 +80,14 @@ def test_finite_temperature_trajectory_matches_oracle(ctx):
     xp = _xp()
     tbmd.xlbomd_init(ctx, TP, st.st, xp, opts, 1e-10, 300)
     o = md.xlbomd(s.R, s.types, s.box, P, XL, v0, M, s.n_occ(P), nsteps, kT=KT, record_R=True)
+    worst = [0.0, 0.0, 0.0]
     for k in range(nsteps + 1):
         if k:
             tbmd.xlbomd_step(ctx, TP, st.st, xp, opts)
         torch.cuda.synchronize()
+        worst = [max(worst[0], float(np.abs(st.q.cpu().numpy() - o.q[k]).max())),
+                 max(worst[1], float(np.abs(st.R.cpu().numpy() - o.R[k]).max())),
+                 max(worst[2], abs(st.energies[1].item() - o.E_pot[k]))]
         # the expansion's tf32x3 products leave q ~1e-7 from the oracle's
         # Fermi-Dirac charges (bounded here by 1e-5); the force difference that
         # causes (~ dq x 4 eV/A per e) moves an H atom by dF t^2 / 2M after 20
@@ -91,6 +95,7 @@ def test_finite_temperature_trajectory_matches_oracle(ctx):
         assert np.abs(st.q.cpu().numpy() - o.q[k]).max() < 1e-5, k
         assert np.abs(st.R.cpu().numpy() - o.R[k]).max() < 5e-7, k
         assert st.energies[1].item() == pytest.approx(o.E_pot[k], abs=2e-6 * s.natoms)
+    print(f"PARITY finite-T trajectory: dq max {worst[0]:.3e} dR max {worst[1]:.3e} dEpot max {worst[2]:.3e}")
     rep = tbmd.tb_fermi_report.from_buffer_copy(st.fermi_report.cpu().numpy().tobytes())
     assert rep.status == tbmd.TB_OK and rep.mu_iters >= 1
 
@@ -193,4 +198,32 @@ def test_server_replays_a_poisson_trace(ctx):
         per[c.traj].append(c.step)
     for t, steps in per.items():
         assert steps == list(range(1, len(steps) + 1))
+    sv.close()
+
+
+def test_server_requests_of_a_trajectory_that_cannot_be_admitted(ctx):
+    """A budget that admits one of two trajectories, requests for both: drain
+    returns the admitted one's steps and stops with the other's still queued
+    (nothing running can free memory for it); a replay that names it is
+    rejected instead of waiting forever; once the first retires, the second is
+    admitted and its queued steps run."""
+    systems = [_system(*x) for x in MIX[:2]]
+    probe = Server(ctx, TP, _xp(), kT=KT, max_slots=2, hbm_budget=1 << 40)
+    fp = [probe.footprint(x[0].types) for x in systems]
+    probe.close()
+    sv = Server(ctx, TP, _xp(), kT=KT, max_slots=2, hbm_budget=max(fp) + min(fp) // 2)
+    ids = [_add(sv, *x) for x in systems]
+    assert sv.stats()["admitted"] == 1 and sv.stats()["waiting"] == 1
+    for t in ids:
+        sv.submit(t)
+        sv.submit(t)
+    done = sv.drain()
+    assert sorted(c.step for c in done) == [1, 2] and {c.traj for c in done} == {ids[0]}
+    assert sv.stats()["queued"] == 2
+    with pytest.raises(tbmd.TBError):
+        sv.replay([0.0, 0.001], [ids[0], ids[1]])
+    sv.retire(ids[0])
+    rest = sv.drain()
+    assert sorted(c.step for c in rest if c.traj == ids[1]) == [1, 2]
+    assert all(c.status == tbmd.TB_OK for c in rest)
     sv.close()
