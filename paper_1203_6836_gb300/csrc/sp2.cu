@@ -22,6 +22,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <atomic>
 
 namespace {
 
@@ -483,6 +484,7 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
   a.nocc = nocc;
   a.rule = o->rule;
   a.st = st;
+  a.wait_ns = ctx->wait_ns;
   if (!tc) {
     a.tol = o->tol;
     a.max_iter = o->max_iter;
@@ -597,16 +599,21 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
 // for n <= TB_SP2_STATIC_MAX_N (about 4 MiB, held by every GPU that loads
 // the library until the process exits).  The symbol's device address is
 // looked up once per device, on the first call made with that device
-// current; make that first call before any stream capture.  All calls share
-// the array: the SP2 state is cleared at the start of every call, and calls
-// that overlap on the GPU (other streams, other host threads) race.
+// current; make that first call before any stream capture.  The address
+// stays valid while the device's context lives: a cudaDeviceReset while the
+// library is in use invalidates it, as it does every other device pointer.
+// All calls share the array: the SP2 state is cleared at the start of every
+// call, and calls that overlap on the GPU (other streams, other host threads)
+// race.
 // --------------------------------------------------------------------------
 
 namespace {
 constexpr size_t kStaticScratchBytes = (size_t)4 * 1024 * 1024 + 64 * 1024;
 static __device__ __align__(256) unsigned char g_sp2_scratch[kStaticScratchBytes];
 constexpr int kMaxDevices = 64;
-void* g_sp2_scratch_addr[kMaxDevices] = {nullptr};
+// device address of the array, per device; atomic, so host threads making a
+// first call on the same device at once store the same value without a race
+std::atomic<void*> g_sp2_scratch_addr[kMaxDevices] = {};
 }  // namespace
 
 extern "C" int dm_sp2_static(tb_ctx* ctx, const double* H, int n, double nocc, const tb_sp2_opts* o,
@@ -621,17 +628,19 @@ extern "C" int dm_sp2_static(tb_ctx* ctx, const double* H, int n, double nocc, c
   int dev = 0;
   TB_CUDA_TRY(ctx, cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "device %d out of range", dev);
-  if (!g_sp2_scratch_addr[dev]) {
+  void* addr = g_sp2_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!addr) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_sp2_scratch);
     if (e != cudaSuccess || !p)
       return tb_fail(ctx, TB_ERR_CUDA, "cudaGetSymbolAddress of the static SP2 scratch failed: %s",
                      cudaGetErrorString(e));
-    g_sp2_scratch_addr[dev] = p;
+    g_sp2_scratch_addr[dev].store(p, std::memory_order_release);
+    addr = p;
   }
   // dm_sp2 wants a 1024-byte aligned workspace: start at the first such
   // address inside the array
-  const uintptr_t base = reinterpret_cast<uintptr_t>(g_sp2_scratch_addr[dev]);
+  const uintptr_t base = reinterpret_cast<uintptr_t>(addr);
   const uintptr_t aligned = (base + 1023) & ~uintptr_t(1023);
   const size_t avail = kStaticScratchBytes - (size_t)(aligned - base);
   const Layout L = make_layout(n, TB_PREC_FP64, 0);

@@ -30,7 +30,10 @@ def test_static_scratch_matches_dm_sp2_on_consecutive_calls(ctx):
     Hw = tb.build_H(tb.build_h(w.R, w.types, w.box, P), tb.build_gamma(w.R, w.box, P), w.types,
                     np.zeros(w.natoms))
     Hr, _ = random_gapped_matrix(511, 200, gap=0.5, width=30.0, seed=12)
-    cases = [(torch.as_tensor(Hw, device="cuda"), w.n_occ(P)), (torch.as_tensor(Hr, device="cuda"), 200.0)]
+    # n = 512: the largest size the static scratch holds (its largest layout)
+    Hm, _ = random_gapped_matrix(tbmd.SP2_STATIC_MAX_N, 240, gap=0.5, width=30.0, seed=13)
+    cases = [(torch.as_tensor(Hw, device="cuda"), w.n_occ(P)), (torch.as_tensor(Hr, device="cuda"), 200.0),
+             (torch.as_tensor(Hm, device="cuda"), 240.0)]
     for H, nocc in cases + cases:          # two calls in a row, then again
         D = torch.full_like(H, float("nan"))
         rep = new_report()
