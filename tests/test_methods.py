@@ -261,3 +261,154 @@ def test_dropped_diagonal_pair_biases_the_diagonal():
     expect = n * np.mean(d[3].astype(np.float64) ** 2) * 2.0 ** -56
     assert bias_drop == pytest.approx(-expect, rel=0.2)
     assert abs(bias_full) < 0.03 * expect
+
+
+def _mu_search(eps, nocc, kT, mu, step_rule, iters=40, tol=1e-9):
+    """Safeguarded chemical-potential search on exact Fermi occupations:
+    the bracket starts 40 kT + 1 eV outside the spectrum; each step uses
+    dev = sum f - N_occ and t = sum f(1 - f)."""
+    beta = 1.0 / kT
+    lo, hi = eps[0] - 40 * kT - 1, eps[-1] + 40 * kT + 1
+    for it in range(iters):
+        f = density.fermi_occupations(eps, mu, kT)
+        dev, t = f.sum() - nocc, (f * (1 - f)).sum()
+        if abs(dev) <= tol:
+            return mu, it
+        if dev < 0:
+            lo = mu
+        else:
+            hi = mu
+        nxt = mu - dev / (beta * t) if t > 1e-300 else np.nan
+        r = abs(dev) / t if t > 0 else np.inf
+        if step_rule == "two-tail" and 0.5 <= r <= 1.5:
+            a, b = 0.5 * (t + dev), 0.5 * (t - dev)
+            if a > 0 and b > 0 and min(a, b) > 1e-3 * max(a, b):
+                nxt = mu + 0.5 * np.log(b / a) / beta
+            else:
+                nxt = mu - np.sign(dev) * min(np.log(abs(dev) / tol), 8.0) / beta
+        if not (lo < nxt < hi):
+            nxt = 0.5 * (lo + hi)
+        mu = nxt
+    return mu, iters
+
+
+def test_two_tail_chemical_potential_step():
+    """In a gap of 2.7 eV at kT = 0.1 eV, started 0.3 eV above the highest
+    occupied level, Newton's step moves mu by about kT per expansion, while
+    the tail steps (balance of the electron and hole tails, or one tail driven
+    to the tolerance) land within it in a few; in dense spectra, where
+    |dev| is far from Tr[D(I - D)], both rules take Newton's steps."""
+    rng = np.random.default_rng(3)
+    occ = np.sort(rng.uniform(-10, -1, 40))
+    virt = np.sort(rng.uniform(1, 10, 60))
+    eps = np.concatenate([occ, virt])
+    mu_ref = 0.5 * (occ[-1] + virt[0])
+    mu2, it2 = _mu_search(eps, 40.0, 0.1, occ[-1] + 0.3, "two-tail")
+    mun, itn = _mu_search(eps, 40.0, 0.1, occ[-1] + 0.3, "newton")
+    assert it2 <= 5 and itn >= 2 * it2 + 4
+    f = density.fermi_occupations(eps, mu2, 0.1)
+    assert abs(f.sum() - 40.0) <= 1e-9
+    assert abs(mu2 - mu_ref) < 1.0  # any mu inside the gap carries the occupation
+    eps_dense = np.sort(rng.uniform(-10, 10, 200))
+    for rule in ("two-tail", "newton"):
+        mu, it = _mu_search(eps_dense, 100.0, 0.5, 0.0, rule)
+        f = density.fermi_occupations(eps_dense, mu, 0.5)
+        assert abs(f.sum() - 100.0) <= 1e-9 and it <= 8
+
+
+# ------------------------------------------------------------------ entropy
+# Eq. Ent_Approx without diagonalisation.  Along the doubling chain of the
+# expansion (y_k = 2^k y_0, f_k = f(y_k), e_k = f_k - 1/2) the function
+# L(y) = ln(1 + e^y) = -ln(1 - f) obeys L(2y) = 2 L(y) - ln 2 + ln(1 + 4 e^2),
+# and per state s(f) = -f ln f - (1 - f) ln(1 - f) = L(y) - (1 - f) y.  So
+#   S/k_B = 2 (Tr L(Y) - Tr[(I - D) Y]),  Y = beta (H - mu I),
+#   Tr L(Y) = n ln 2 + Tr Y/2 + 2^m dL0 + sum_k 2^(m-1-k) Tr ln(I + 4 E_k^2),
+# with dL0 = Tr L(Y0) - n ln 2 - Tr Y0/2 from the Taylor series of L at
+# |y0| <= 1/8 and Tr ln A (spectrum of A in [1, 2]) from its Chebyshev series
+# of degree 20, whose traces come from T_0..T_10 and Frobenius products
+# (Tr T_{10+j} = 2 <T_10, T_j> - Tr T_{10-j}).  All in FP64: the terms are of
+# size beta |eps - mu| and cancel to the entropy, so FP32 products would not do.
+
+def chebyshev_log_coeffs(deg=20, nodes=64):
+    """Coefficients c_j of ln(3/2 + x/2) = sum_j c_j T_j(x) on [-1, 1] by
+    interpolation at Chebyshev nodes (discrete cosine sums)."""
+    th = np.pi * (np.arange(nodes) + 0.5) / nodes
+    fx = np.log(1.5 + 0.5 * np.cos(th))
+    c = np.array([2.0 / nodes * np.sum(fx * np.cos(j * th)) for j in range(deg + 1)])
+    c[0] *= 0.5
+    return c
+
+
+def fermi_entropy_recursive(H, mu, kT, y0max=0.125, P=10):
+    n = H.shape[0]
+    beta = 1.0 / kT
+    I = np.eye(n)
+    lo, hi = density.gershgorin(H)
+    ymax = beta * max(hi - mu, mu - lo)
+    m = 0
+    while ymax / 2.0 ** m > y0max:
+        m += 1
+    Y = beta * (H - mu * I)
+    Y0 = Y / 2.0 ** m
+    Y2 = Y0 @ Y0
+    Y4 = Y2 @ Y2
+    W = Y2 @ Y4
+    dL0 = (np.sum(Y0 * Y0) / 8 - np.sum(Y2 * Y2) / 192 + np.sum(Y2 * Y4) / 2880
+           - 17 * np.sum(Y4 * Y4) / 645120)
+    E = Y0 @ (-I / 4 + Y2 / 48 - Y4 / 480 + 17 * W / 80640)   # -tanh(y0/2)/2 to y0^7
+    c = chebyshev_log_coeffs(2 * P)
+    acc = 0.0
+    for k in range(m):
+        B = 8 * (E @ E) - I                                   # 2A - 3I, A = I + 4E^2
+        T = [I, B]
+        for j in range(2, P + 1):
+            T.append(2 * (B @ T[-1]) - T[-2])
+        tau = np.zeros(2 * P + 1)
+        for j in range(P + 1):
+            tau[j] = np.trace(T[j])
+        for j in range(P + 1, 2 * P + 1):
+            tau[j] = 2 * np.sum(T[P] * T[j - P]) - tau[2 * P - j]
+        acc += 2.0 ** (m - 1 - k) * np.dot(c, tau)
+        # A^-1: quadratic minimax start from A = (B + 3I)/2, A^2 = (T2 + 12B + 19I)/8,
+        # then three Newton-Schulz steps Z <- Z (2I - AZ)
+        Z = (210 * I - 72 * (B + 3 * I) + 4 * (T[2] + 12 * B + 19 * I)) / 99
+        for _ in range(3):
+            Z = Z @ (2 * I - 0.5 * (B @ Z + 3 * Z))
+        E = 2 * (E @ Z)
+    D = 0.5 * I + E
+    S = 2 * (n * np.log(2) - np.trace(Y) / 2 + 2.0 ** m * dL0 + acc + np.sum(D * Y))
+    return S, D, m
+
+
+def test_chebyshev_log_coefficients():
+    c = chebyshev_log_coeffs()
+    x = np.linspace(-1, 1, 1001)
+    assert np.abs(np.polynomial.chebyshev.chebval(x, c) - np.log(1.5 + 0.5 * x)).max() < 1e-15
+
+
+@pytest.mark.parametrize("n,seed,kT,width", [(40, 0, 0.1, 24.0), (90, 1, 0.5, 24.0), (150, 2, 0.1, 24.0),
+                                              (60, 3, 1.5, 24.0), (120, 4, 0.05, 16.0)])
+def test_recursive_fermi_entropy(n, seed, kT, width):
+    """The recursion gives the eigenvalue entropy -2 sum [f ln f + (1-f) ln(1-f)]
+    (Eq. Ent_Approx) to 2e-9 and the Fermi matrix to 1e-13 at the canonical mu,
+    for spectra 16-24 eV wide at kT = 0.05-1.5 eV (m = 9..13 doublings)."""
+    H, eps, Q = _random_h(n, seed, width)
+    nocc = n // 2
+    ref = density.density_fermi(H, nocc, kT)
+    S_ref = density.entropy_kB(ref.occ)
+    S, D, m = fermi_entropy_recursive(H, ref.mu, kT)
+    assert 9 <= m <= 14
+    assert abs(S - S_ref) < 2e-9 * max(1.0, S_ref)
+    assert np.abs(D - ref.D).max() < 1e-13
+
+
+def test_recursive_fermi_entropy_controls():
+    """Negative controls: a Chebyshev series of degree 12 instead of 20, or a
+    Taylor start at |y0| <= 3 (near the radius pi of the series) instead of
+    1/8, miss the entropy by more than 1e-6."""
+    H, eps, Q = _random_h(80, 7, 24.0)
+    ref = density.density_fermi(H, 40, 0.1)
+    S_ref = density.entropy_kB(ref.occ)
+    S12, _, _ = fermi_entropy_recursive(H, ref.mu, 0.1, P=6)
+    S3, _, _ = fermi_entropy_recursive(H, ref.mu, 0.1, y0max=3.0)
+    assert abs(S12 - S_ref) > 1e-6 and abs(S3 - S_ref) > 1e-6
