@@ -534,8 +534,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             umma<C::tf32>(d, ah, bh, id, first ? 0u : 1u);
             first = false;
             if constexpr (C::split) {
-              umma<C::tf32>(d, ah, sdesc(base + 3 * 128 * 128 + koff), id, 1u);
-              umma<C::tf32>(d, sdesc(base + 2 * 128 * 128 + koff), bh, id, 1u);
+              const uint64_t al = sdesc(base + 2 * 128 * 128 + koff), bl = sdesc(base + 3 * 128 * 128 + koff);
+              umma<C::tf32>(d, ah, bl, id, 1u);
+              umma<C::tf32>(d, al, bh, id, 1u);
+              umma<C::tf32>(d, al, bl, id, 1u);  // lo*lo: diagonal blocks sum squares (unbiased)
             }
           }
           umma_commit(&empty[s]);

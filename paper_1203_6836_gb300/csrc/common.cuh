@@ -117,8 +117,14 @@ struct ModelDev {
   double n0_O, n0_H;
   double pair_a, inv_prho;
   double Bhop[6], Bpair[6];
-  double range;  // max(rcut, gcut)
+  double zhop[3], zpair[3];  // A2..A4 of zeta(R) for the bond integrals and phi
+  double range;  // reach of the image loops: max(rcut, gcut), or rcut with the Ewald gamma
   double box;
+  int gamma_form;     // 0: windowed gamma, 1: Ewald-summed Gaussian charges
+  double ealpha;      // Ewald splitting (1/A)
+  double gwidth;      // Gaussian width c = 2k/(U sqrt(pi))
+  double erange;      // real-space reach: max(6.6/alpha, 6.6 c)
+  double gmax;        // reciprocal cut-off 13.2 alpha
 };
 
 int tb_model_from_params(tb_ctx* ctx, const tb_params* p, double box, ModelDev* m);
@@ -202,6 +208,7 @@ struct GemmArgs {
   const int* skip;
   int* err;
   unsigned long long wait_ns;  // pipeline wait limit (0: the 2 s default)
+  int lolo;                    // split precisions: also the lo*lo MMA (squares A A)
 };
 int tc_gemm(tb_ctx* ctx, int precision, const GemmArgs& g, const CUtensorMap* ah, const CUtensorMap* al,
             const CUtensorMap* bh, const CUtensorMap* bl, cudaStream_t s);
@@ -216,9 +223,12 @@ int dm_sp2_bsr_workspace(int n, const tb_sp2_opts* o, int nsm, size_t* bytes);
 int dm_sp2_bsr(tb_ctx* ctx, const double* H, int n, double nocc, const tb_sp2_opts* o, double* D, void* ws,
                size_t ws_bytes, tb_sp2_report* rep, cudaStream_t s);
 
-// Encode a 2D row-major tensor map over an ld x ld operand array for the
-// tensor-core kernel (gemm_tc.cu).
-int sp2_tc_make_map(tb_ctx* ctx, int precision, const void* base, int ld, CUtensorMap* map);
+// Encode a 2D row-major tensor map over an ld x ld operand array (gemm_tc.cu):
+// 128-row boxes of row_bytes (64 or 128) bytes, swizzled to the same width.
+// The projection and Fermi-product kernels read 64-byte rows
+// (sp2_tc_row_bytes()); the emulated-FP64 product reads 128-byte rows.
+int sp2_tc_make_map(tb_ctx* ctx, int precision, const void* base, int ld, CUtensorMap* map, int row_bytes = 128);
+int sp2_tc_row_bytes();
 
 // ------------------------------------------------------------ utilities
 

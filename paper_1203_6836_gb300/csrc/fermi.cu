@@ -24,11 +24,18 @@
 // E is small while the early steps double it, so FP32-level products keep a
 // relative accuracy there (errors add up over the m steps instead of being
 // doubled m times as absolute errors of X would be).  Per step:
-//   A = I + 4 E E                                  (one product, affine epilogue;
-//                                                   spectrum in [1, 2])
+//   W = (I - 2E)(I + 2E) = I - 4E^2                (one product; spectrum in [0, 1])
+//   A = 2I - W = I + 4E^2                          (elementwise; spectrum in [1, 2])
 //   Z = A^-1: Z1 = (210 I - 144 A + 32 A^2) / 99    (one product A A with the
 //             affine part in its epilogue), then Newton-Schulz Z <- Z (2I - A Z)
-//   E <- 2 E Z                                     (one product)
+//   E <- E + E (Z W)                               (two products; = 2 E Z)
+// The factored W and the update form keep the saturated states exact: where
+// E is near +-1/2 one factor of W is near 0, so W and Z W are small there and
+// carry small absolute errors, and E changes only by that small amount.  The
+// plain forms A = I + 4E^2, E <- 2EZ left every saturated occupied state of
+// a 2400-orbital gapped system 1.8e-7 above 1 on the GB300 tensor cores (the
+// error of the last products, which the saturated states do not forget), 3e-4
+// electrons in all, enough to drag mu across a 3 eV gap.
 // Z1 is the quadratic p minimising max |1 - x p(x)| on [1, 2]: 1 - x p(x) is
 // the Chebyshev polynomial T3(2x - 3) / T3(-3), so ||I - A Z1|| <= 1/99 and two
 // Newton-Schulz steps leave ||I - A Z|| <= 99^-4 ~ 1e-8 (seven products per
@@ -55,12 +62,12 @@ constexpr int kTile = 128;
 constexpr int kMaxMu = 40;
 constexpr int kMaxM = 40;   // doubling steps issued at most
 constexpr int kMinM = 8;    // doubling steps used at least
-constexpr int kMats = 6;    // E0/E1 (the iterate, alternating), A, Z, T, Y
+constexpr int kMats = 7;    // E0/E1 (the iterate, alternating), A, Z, T, Y, W
 // Canonical shift: the last expansion is accepted and shifted by u = beta dmu
 // to second order,
 //   D(mu + dmu) = D + u D(I - D) + u^2/2 D(I - D)(I - 2D) + R,
-// with D(I - D) = I/4 - E^2 and D(I - D)(I - 2D) = 2E^3 - E/2 (two products,
-// E^2 and E^3, after every expansion), u the root of the trace condition
+// with D(I - D) = W/4 and D(I - D)(I - 2D) = -E W/2, W = (I - 2E)(I + 2E) (two
+// products, W and E W, after every expansion), u the root of the trace condition
 // Tr D + u Tr[D(I-D)] + u^2/2 Tr[D(I-D)(I-2D)] = N_occ near -(Tr D - N)/Tr[D(I-D)].
 // The remainder involves the third derivative beta^3 f(1-f)(1-6f+6f^2), whose
 // last factor is at most 1 in magnitude, so ||R||_F <= |u|^3/6 Tr[D(I - D)]
@@ -150,8 +157,9 @@ __global__ void __launch_bounds__(256) k_foe_x0(const double* __restrict__ H, in
 // is the device count st->iters.  Inside a while graph node (cond != 0) the
 // condition is cleared on every stop: converged, capped, or an error flag
 // raised by a product of this expansion.
-__global__ void k_foe_mu(FoeState* st, const double* parts, const double* parts3, int np, int n, double nocc,
-                         double beta, double tol, int max_it, cudaGraphConditionalHandle handle, int cond) {
+__global__ void k_foe_mu(FoeState* st, const double* parts, const double* partsw, const double* parts3, int np,
+                         int n, double nocc, double beta, double tol, int max_it, cudaGraphConditionalHandle handle,
+                         int cond) {
   if (st->done || st->err || st->iters >= max_it) {
     if (threadIdx.x == 0) {
       st->ran = 0;
@@ -162,18 +170,18 @@ __global__ void k_foe_mu(FoeState* st, const double* parts, const double* parts3
   double x = 0.0, y = 0.0, z = 0.0;
   for (int i = threadIdx.x; i < np; i += 32) {
     x += parts[2 * i];
-    y += parts[2 * i + 1];
+    y += partsw[2 * i];
     z += parts3[2 * i];
   }
   x = warp_sum(x);  // Tr E
-  y = warp_sum(y);  // ||E||_F^2
-  z = warp_sum(z);  // Tr E^3
+  y = warp_sum(y);  // Tr W
+  z = warp_sum(z);  // Tr E W
   if (threadIdx.x != 0) return;
   const int it = st->iters;
   const double mu = st->mu;
   const double trd = 0.5 * n + x;
-  const double t1 = 0.25 * n - y;        // Tr D(I - D)
-  const double t2 = 2.0 * z - 0.5 * x;   // Tr D(I - D)(I - 2D)
+  const double t1 = 0.25 * y;    // Tr D(I - D)
+  const double t2 = -0.5 * z;    // Tr D(I - D)(I - 2D)
   st->tr[it] = trd;
   st->trdd[it] = t1;
   st->mus[it] = mu;
@@ -205,13 +213,52 @@ __global__ void k_foe_mu(FoeState* st, const double* parts, const double* parts3
   } else {
     if (dev < 0.0) st->lo = mu;
     else st->hi = mu;
+    // Newton's step -dev/(beta t1), except where |dev| ~ t1: then the partly
+    // occupied states sit in the tails of a gap (f(1-f) ~ f or 1-f), Newton
+    // moves mu by only ~kT per expansion, and the electrons above mu,
+    // a = (t1 + dev)/2, and the holes below it, b = (t1 - dev)/2, which move
+    // as a e^{beta dmu} and b e^{-beta dmu}, balance at dmu = ln(b/a)/(2 beta).
+    // With one tail below resolution the step shrinks the other towards the
+    // tolerance, by at most 8 kT.
     double next = mu + step;
+    const double r = t1 > 0.0 ? fabs(dev) / t1 : INFINITY;
+    if (r >= 0.5 && r <= 1.5) {
+      const double a = 0.5 * (t1 + dev), b = 0.5 * (t1 - dev);
+      if (a > 0.0 && b > 0.0 && fmin(a, b) > 1e-3 * fmax(a, b))
+        next = mu + 0.5 * log(b / a) / beta;
+      else
+        next = mu - copysign(fmin(log(fabs(dev) / tol), 8.0), dev) / beta;
+    }
     if (!(next > st->lo && next < st->hi)) next = 0.5 * (st->lo + st->hi);
     st->mu = next;
   }
   if (st->done)
     for (int k = 0; k < kMaxM; ++k) st->skipd[k] = 1;
   if (cond && st->done) cudaGraphSetConditional(handle, 0);
+}
+
+// P = I + 2E and M = I - 2E on the n x n block (FP32 masters; zero in the
+// padding, so W = M P is zero there too), skipped with the doubling step.
+__global__ void __launch_bounds__(256) k_foe_pm(const int* skip, int n, int ld, const float* __restrict__ E,
+                                                float* __restrict__ P, float* __restrict__ M) {
+  if (*skip) return;
+  const size_t total = (size_t)ld * ld;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = e / ld, c = e % ld;
+    const float id = (r == c && r < (size_t)n) ? 1.0f : 0.0f;
+    const float x = 2.0f * E[e];
+    P[e] = id + x;
+    M[e] = id - x;
+  }
+}
+
+// A = 2I - W (FP32 master), skipped with the doubling step.
+__global__ void __launch_bounds__(256) k_foe_a(const int* skip, int ld, const float* __restrict__ W,
+                                               float* __restrict__ A) {
+  if (*skip) return;
+  const size_t total = (size_t)ld * ld;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
+    A[e] = ((e / ld) == (e % ld) ? 2.0f : 0.0f) - W[e];
 }
 
 // Word copy of one iterate array into the other iterate buffer (skipped once
@@ -232,8 +279,9 @@ __global__ void __launch_bounds__(256) k_foe_keep(const FoeState* st, size_t cou
     dst[e] = src[e];
 }
 
-// E <- E + u (I/4 - E^2) + u^2/2 (2 E^3 - E/2) on the n x n block, with
-// T = E^2 and U = E^3 from the product kernel; skipped unless the shift applies.
+// E <- E + u W/4 - u^2/4 E W on the n x n block (D(I - D) = W/4,
+// D(I - D)(I - 2D) = -E W/2), with T = W and U = E W from the product kernel;
+// skipped unless the shift applies.
 __global__ void __launch_bounds__(256) k_foe_correct(const FoeState* st, int n, int ld, const float* __restrict__ T,
                                                      const float* __restrict__ U, float* __restrict__ E) {
   if (st->nocorr) return;
@@ -243,8 +291,8 @@ __global__ void __launch_bounds__(256) k_foe_correct(const FoeState* st, int n, 
     const int r = (int)(e / n), col = (int)(e % n);
     const size_t i = (size_t)r * ld + col;
     const float x = E[i];
-    const float first = (r == col ? 0.25f : 0.0f) - T[i];
-    const float second = 2.0f * U[i] - 0.5f * x;
+    const float first = 0.25f * T[i];
+    const float second = -0.5f * U[i];
     E[i] = fmaf(h, second, fmaf(u, first, x));
   }
 }
@@ -277,7 +325,7 @@ __global__ void __launch_bounds__(256) k_foe_finalize(const FoeState* st, int n,
 
 struct FoeLayout {
   int ld;
-  size_t off_state, off_bparts, off_parts, off_parts3, off_mat[kMats][3], off_res, total;
+  size_t off_state, off_bparts, off_parts, off_parts3, off_partsw, off_mat[kMats][3], off_res, total;
   int nparts;
 };
 
@@ -298,6 +346,7 @@ FoeLayout foe_layout(int n, int prec) {
   L.off_bparts = take(sizeof(double) * 2 * ((n + 7) / 8));
   L.off_parts = take(sizeof(double) * 2 * (size_t)L.nparts);
   L.off_parts3 = take(sizeof(double) * 2 * (size_t)L.nparts);
+  L.off_partsw = take(sizeof(double) * 2 * (size_t)L.nparts);
   for (int i = 0; i < kMats; ++i) {
     L.off_mat[i][0] = take(sizeof(float) * nn);
     L.off_mat[i][1] = take(eb * nn);
@@ -336,15 +385,16 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
   double* bparts = reinterpret_cast<double*>(base + L.off_bparts);
   double* parts = reinterpret_cast<double*>(base + L.off_parts);
   double* parts3 = reinterpret_cast<double*>(base + L.off_parts3);
-  Mat M[kMats];  // E (two, alternating), A, Z, T, Y
+  double* partsw = reinterpret_cast<double*>(base + L.off_partsw);
+  Mat M[kMats];  // E (two, alternating), A, Z, T, Y, W
   for (int i = 0; i < kMats; ++i) {
     M[i].m = reinterpret_cast<float*>(base + L.off_mat[i][0]);
     M[i].hi = base + L.off_mat[i][1];
     M[i].lo = L.off_mat[i][2] ? base + L.off_mat[i][2] : nullptr;
-    int rc = sp2_tc_make_map(ctx, o->precision, M[i].hi, L.ld, &M[i].mh);
+    int rc = sp2_tc_make_map(ctx, o->precision, M[i].hi, L.ld, &M[i].mh, sp2_tc_row_bytes());
     if (rc) return rc;
     if (M[i].lo) {
-      rc = sp2_tc_make_map(ctx, o->precision, M[i].lo, L.ld, &M[i].ml);
+      rc = sp2_tc_make_map(ctx, o->precision, M[i].lo, L.ld, &M[i].ml, sp2_tc_row_bytes());
       if (rc) return rc;
     } else {
       M[i].ml = M[i].mh;
@@ -355,7 +405,9 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
   // the fewest that the bracket allows, at least kMinM
   const int m = o->m > 0 ? o->m : 14;
   const int ns = o->ns_iters > 0 ? o->ns_iters : 3;
-  const double tol = o->trace_tol > 0.0 ? o->trace_tol : 1e-7 * std::max(1.0, nocc);
+  // default: 1e-6 electrons plus 1e-9 per electron pair, above the FP32 noise
+  // of the trace (~3e-8 sqrt(n)) and tight enough for 1e-6 e charges
+  const double tol = o->trace_tol > 0.0 ? o->trace_tol : 1e-6 + 1e-9 * nocc;
   const size_t nn = (size_t)L.ld * L.ld;
   const size_t eb = (o->precision == TB_PREC_TF32 || o->precision == TB_PREC_TF32X3) ? 4 : 2;
   int* skip = &st->done;
@@ -390,6 +442,7 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
     g.skip = skp ? skp : skip;
     g.err = errp;
     g.wait_ns = ctx->wait_ns;
+    g.lolo = &A == &B;
     return tc_gemm(ctx, o->precision, g, &A.mh, &A.ml, &B.mh, &B.ml, ls);
   };
   Mat* xf = &M[0];  // final iterate, E^2 and E^3 after an expansion
@@ -420,12 +473,26 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
         TB_LAUNCH_CHECK(ctx);
       }
     }
+    Mat* W = &M[6];
+    // P = I + 2E, M = I - 2E (in T and Y, free at that point) with their splits,
+    // then W = M P; skp: the step's skip flag (or the expansion's)
+    auto factored_w = [&](Mat& Ein, int* skp, double* prt) -> int {
+      k_foe_pm<<<1184, 256, 0, ls>>>(skp, n, L.ld, Ein.m, T->m, Y->m);
+      TB_LAUNCH_CHECK(ctx);
+      int q;
+      if ((q = tc_split(ctx, o->precision, T->m, nn, T->hi, T->lo, skp, ls))) return q;
+      if ((q = tc_split(ctx, o->precision, Y->m, nn, Y->hi, Y->lo, skp, ls))) return q;
+      return gemm(*Y, *T, *W, 1.0f, 0.0f, nullptr, 0.0f, prt, skp);
+    };
     for (int step = 0; step < m; ++step) {
       Mat* X = E[step & 1];
       Mat* Xn = E[(step + 1) & 1];
       int* sk = &st->skipd[step];  // leading steps beyond the device's m return at once
-      // A = I + 4 E E
-      if ((r = gemm(*X, *X, *A, 4.0f, 0.0f, nullptr, 1.0f, nullptr, sk))) return r;
+      // W = (I - 2E)(I + 2E), A = 2I - W
+      if ((r = factored_w(*X, sk, nullptr))) return r;
+      k_foe_a<<<1184, 256, 0, ls>>>(sk, L.ld, W->m, A->m);
+      TB_LAUNCH_CHECK(ctx);
+      if ((r = tc_split(ctx, o->precision, A->m, nn, A->hi, A->lo, sk, ls))) return r;
       // Z1 = (32 A A - 144 A + 210 I) / 99, then Newton-Schulz
       if ((r = gemm(*A, *A, *Z, 32.0f / 99.0f, -144.0f / 99.0f, A->m, 210.0f / 99.0f, nullptr, sk))) return r;
       for (int k = 1; k < ns; ++k) {
@@ -433,28 +500,29 @@ extern "C" int dm_fermi(tb_ctx* ctx, const double* H, int n, double nocc, double
         if ((r = gemm(*Z, *T, *Y, 1.0f, 0.0f, nullptr, 0.0f, nullptr, sk))) return r;   // Z <- Z T
         std::swap(Z, Y);
       }
-      // E <- 2 E Z (trace partials of the last step); the product kernel
-      // writes exactly symmetric results with their operand splits
+      // E <- E + E (Z W) (= 2 E Z); trace partials of the last step.  The
+      // product kernel writes exactly symmetric results with their splits
       const bool last = step == m - 1;
-      if ((r = gemm(*X, *Z, *Xn, 2.0f, 0.0f, nullptr, 0.0f, last ? parts : nullptr, sk))) return r;
+      if ((r = gemm(*Z, *W, *T, 1.0f, 0.0f, nullptr, 0.0f, nullptr, sk))) return r;
+      if ((r = gemm(*X, *T, *Xn, 1.0f, 1.0f, X->m, 0.0f, last ? parts : nullptr, sk))) return r;
     }
     Mat* X = E[m & 1];
-    // E^2 and E^3 (with Tr E^3) for the canonical shift
-    if ((r = gemm(*X, *X, *A, 1.0f, 0.0f, nullptr, 0.0f, nullptr))) return r;
-    if ((r = gemm(*X, *A, *Z, 1.0f, 0.0f, nullptr, 0.0f, parts3))) return r;
-    k_foe_mu<<<1, 32, 0, ls>>>(st, parts, parts3, sp2_tc_num_parts(ctx, L.ld), n, nocc, beta, tol, o->mu_iters,
-                               loop.handle, loop.graph);
+    // W and E W of the final E (with Tr W and Tr E W) for the canonical shift
+    if ((r = factored_w(*X, skip, partsw))) return r;
+    if ((r = gemm(*X, *W, *Z, 1.0f, 0.0f, nullptr, 0.0f, parts3))) return r;
+    k_foe_mu<<<1, 32, 0, ls>>>(st, parts, partsw, parts3, sp2_tc_num_parts(ctx, L.ld), n, nocc, beta, tol,
+                               o->mu_iters, loop.handle, loop.graph);
     TB_LAUNCH_CHECK(ctx);
     k_foe_keep<<<1184, 256, 0, ls>>>(st, nn, X->m, res);
     TB_LAUNCH_CHECK(ctx);
     xf = X;
-    af = A;
+    af = W;
     zf = Z;
     return TB_OK;
   };
   for (int it = 0; it < rounds && rc == TB_OK; ++it) rc = expansion();
   if ((rc = tb_loop_end(ctx, &loop, rc))) return rc;
-  // canonical shift of the accepted expansion (its E, E^2, E^3 are still in
+  // canonical shift of the accepted expansion (its E, W and E W are still in
   // *xf, *af, *zf)
   {
     const int fb = std::min(1184, (int)(((size_t)n * n + 255) / 256));

@@ -283,8 +283,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint64_t a0 = sdesc(base + koff), b0 = sdesc(base + G::a_bytes + koff);
               umma<C::tf32>(dt, a0, b0, id, (kb | ks) != 0);
               if constexpr (C::split) {
-                umma<C::tf32>(dt, a0, sdesc(base + 2 * G::a_bytes + G::b_bytes + koff), id, 1u);
-                umma<C::tf32>(dt, sdesc(base + G::a_bytes + G::b_bytes + koff), b0, id, 1u);
+                const uint64_t a1 = sdesc(base + G::a_bytes + G::b_bytes + koff);
+                const uint64_t b1 = sdesc(base + 2 * G::a_bytes + G::b_bytes + koff);
+                umma<C::tf32>(dt, a0, b1, id, 1u);
+                umma<C::tf32>(dt, a1, b0, id, 1u);
+                umma<C::tf32>(dt, a1, b1, id, 1u);  // lo*lo: X X is a square (unbiased diagonal)
               }
             }
             umma_commit(&empty[s]);
@@ -658,8 +661,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint64_t a0 = sdesc(base + koff), b0 = sdesc(base + G::a_bytes + koff);
               umma<C::tf32>(dt, a0, b0, id, (kb | ks) != 0);
               if constexpr (C::split) {
-                umma<C::tf32>(dt, a0, sdesc(base + 2 * G::a_bytes + G::b_bytes + koff), id, 1u);
-                umma<C::tf32>(dt, sdesc(base + G::a_bytes + G::b_bytes + koff), b0, id, 1u);
+                const uint64_t a1 = sdesc(base + G::a_bytes + G::b_bytes + koff);
+                const uint64_t b1 = sdesc(base + 2 * G::a_bytes + G::b_bytes + koff);
+                umma<C::tf32>(dt, a0, b1, id, 1u);
+                umma<C::tf32>(dt, a1, b0, id, 1u);
+                umma<C::tf32>(dt, a1, b1, id, 1u);  // lo*lo: X X is a square (unbiased diagonal)
               }
             }
             umma_commit(&empty[s]);

@@ -124,7 +124,7 @@ def test_fermi_expansion_above_one_round(ctx):
     assert rep["status"] == tbmd.TB_OK, rep
     assert eD < 2e-6
     assert eq < 2e-6
-    assert abs(ntr - nocc) <= 1e-7 * nocc
+    assert abs(ntr - nocc) <= 1e-6 + 1e-9 * nocc + 1e-6  # the default tolerance + the trace's FP32 noise
 
 
 def test_block_sparse_above_one_round(ctx):
@@ -196,9 +196,9 @@ def test_guards_above_one_round(ctx, kind):
     torch.cuda.synchronize()
     assert bool((buf[:g] == canary).all()) and bool((buf[g + n * n:] == canary).all())
     assert bool(torch.isfinite(D).all())
-    # dm_fermi stops at |Tr D - N_occ| <= 1e-7 N_occ (its default trace tolerance);
-    # the thresholded recursion's trace moves with the dropped blocks
-    bound = {"bsr": 1e-2, "fermi": 1e-7 * nocc + 1e-9}.get(kind, 1e-5)
+    # dm_fermi stops at |Tr D - N_occ| <= 1e-6 + 1e-9 N_occ (its default trace
+    # tolerance); the thresholded recursion's trace moves with the dropped blocks
+    bound = {"bsr": 1e-2, "fermi": 1e-6 + 1e-9 * nocc + 1e-6}.get(kind, 1e-5)
     assert abs(torch.trace(D).item() - nocc) <= bound
 
 
