@@ -7,9 +7,9 @@
 // operands are row blocks of X read K-major.  The grid is persistent (at
 // most one CTA per SM); CTA b takes tiles b, b + G, b + 2G, ... of the
 // row-major upper triangle.  Warp roles (192 threads):
-//   warp 0   one thread issues TMA tile loads (128B swizzle) into a ring of
-//            shared-memory stages that runs on across tiles, completion
-//            tracked by mbarriers;
+//   warp 0   one thread issues TMA tile loads (128-byte swizzled K-slices)
+//            into a ring of shared-memory stages that runs on across tiles,
+//            completion tracked by mbarriers;
 //   warp 1   allocates two TMEM accumulators (2 x 128 FP32 columns) and one
 //            thread issues tcgen05.mma (kind::f16 with bf16 or kind::tf32)
 //            into them alternately, so the next tile's MMAs overlap the
@@ -18,7 +18,8 @@
 //            using the FP32 master of X_k, write the FP32 master and the
 //            operand splits of X_{k+1} (the transposed copy with one
 //            coalesced 32-lane store per column), and accumulate the FP64
-//            trace partials (Tr X, ||X||_F^2, ||X^2 - X||_F^2) per CTA.
+//            trace partials (Tr X, ||X||_F^2) per CTA; the X^2 branch reads
+//            no FP32 master of X_k.
 // Split precisions (x3) keep X ~ hi + lo in two operand arrays and
 // accumulate hi*hi + hi*lo + lo*hi in the same FP32 accumulator.
 //
@@ -36,8 +37,31 @@ namespace {
 using namespace tcx;
 
 constexpr int BM = 128, BN = 128;
-constexpr int TILE_BYTES = 128 * 128;  // 128 rows x 128 bytes
 constexpr int kThreads = 192;
+
+// Shared-memory pipeline of the projection and Fermi-product kernels: each
+// stage holds a K-slice of `row` bytes (one swizzle row: 32 tf32 or 64 bf16
+// values at 128 bytes) of the A and B row blocks (and their lo splits), in
+// 192 KB: three 64 KB stages for the split precisions.  (64-byte slices fit
+// six stages but measured 18% slower per projection at n = 4096: twice the
+// TMA requests of half a cache line each.)
+// Shared-memory descriptor of a K-major tile with `row`-byte swizzle rows.
+template <int ROW>
+__device__ __forceinline__ uint64_t Pipe_sdesc(uint32_t saddr) {
+  if constexpr (ROW == 64) return sdesc64(saddr);
+  else return sdesc(saddr);
+}
+
+template <int P>
+struct Pipe {
+  using C = Prec<P>;
+  static constexpr int row = 128;                       // bytes of one K-slice row
+  static constexpr int bk = row / C::eb;                // K elements per stage
+  static constexpr int tile = 128 * row;                // one 128-row tile
+  static constexpr int stage_bytes = 2 * C::nop * tile;
+  static constexpr int stages = (192 * 1024) / stage_bytes;
+  static constexpr int smem_bytes = stages * stage_bytes + 1024;
+};
 
 
 // X0 (FP32 master) -> operand arrays, elementwise.
@@ -102,8 +126,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                   const __grid_constant__ CUtensorMap ml, const float* __restrict__ Xin,
                   float* __restrict__ Xout, void* __restrict__ ohi, void* __restrict__ olo) {
   using C = Prec<P>;
+  using Q = Pipe<P>;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[C::stages], empty[C::stages], tfull[2], tempty[2], mdone;
+  __shared__ __align__(8) uint64_t full[Q::stages], empty[Q::stages], tfull[2], tempty[2], mdone;
   __shared__ uint32_t tmem_base;
   __shared__ double s_t[3];
   __shared__ int s_dec[3];
@@ -155,10 +180,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nt = a.ld / BM;
   const Units wu = make_units(nt * (nt + 1) / 2, gridDim.x);
   const unsigned long long wl = a.wait_ns ? a.wait_ns : kWaitNs;  // pipeline wait limit
-  const int nk = a.ld / C::bk;
+  const int nk = a.ld / Q::bk;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < C::stages; ++s) {
+    for (int s = 0; s < Q::stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -186,24 +211,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       unit_tile(wu, u, &t, &half);
       tri_tile(t, nt, &I, &J);
       for (int kb = 0; kb < nk; ++kb, ++g) {
-        const int s = g % C::stages;
-        if (g >= C::stages && !mbar_wait(&empty[s], ((g / C::stages) - 1) & 1, &s_abort, wl)) break;
-        uint8_t* base = smem + s * C::stage_bytes;
-        mbar_expect_tx(&full[s], C::stage_bytes);
-        tma_load_2d(base, &mh, &full[s], kb * C::bk, I * BM);
-        tma_load_2d(base + TILE_BYTES, &mh, &full[s], kb * C::bk, J * BN);
+        const int s = g % Q::stages;
+        if (g >= Q::stages && !mbar_wait(&empty[s], ((g / Q::stages) - 1) & 1, &s_abort, wl)) break;
+        uint8_t* base = smem + s * Q::stage_bytes;
+        mbar_expect_tx(&full[s], Q::stage_bytes);
+        tma_load_2d(base, &mh, &full[s], kb * Q::bk, I * BM);
+        tma_load_2d(base + Q::tile, &mh, &full[s], kb * Q::bk, J * BN);
         if constexpr (C::split) {
-          tma_load_2d(base + 2 * TILE_BYTES, &ml, &full[s], kb * C::bk, I * BM);
-          tma_load_2d(base + 3 * TILE_BYTES, &ml, &full[s], kb * C::bk, J * BN);
+          tma_load_2d(base + 2 * Q::tile, &ml, &full[s], kb * Q::bk, I * BM);
+          tma_load_2d(base + 3 * Q::tile, &ml, &full[s], kb * Q::bk, J * BN);
         }
         issued = g + 1;
       }
     }
     if (s_abort) {
       // let every issued copy land before the CTA can exit
-      for (int q = (issued > C::stages ? issued - C::stages : 0); q < issued; ++q) {
+      for (int q = (issued > Q::stages ? issued - Q::stages : 0); q < issued; ++q) {
         const unsigned long long t0 = gtime();
-        while (!mbar_try(&full[q % C::stages], (q / C::stages) & 1) && gtime() - t0 < kWaitNs) {
+        while (!mbar_try(&full[q % Q::stages], (q / Q::stages) & 1) && gtime() - t0 < kWaitNs) {
         }
       }
     }
@@ -217,26 +242,26 @@ __global__ void __launch_bounds__(kThreads, 1)
       unit_tile(wu, u, &t, &half);
       const uint32_t id = half < 0 ? id128 : id64;
       // a half unit multiplies by rows [64 half, 64 half + 64) of the B tile:
-      // 8 KB into it, a whole number of 1 KB swizzle atoms
-      const uint32_t boff = half > 0 ? 64 * 128 : 0;
+      // 64 rows into it, a whole number of 8-row swizzle atoms
+      const uint32_t boff = half > 0 ? 64 * Q::row : 0;
       const int buf = it & 1;
       if (it >= 2 && !mbar_wait(&tempty[buf], ((it >> 1) - 1) & 1, &s_abort, wl)) break;
       tc_fence_after();
       const uint32_t d = tmem + buf * BN;
       for (int kb = 0; kb < nk; ++kb, ++g) {
-        const int s = g % C::stages;
-        if (!mbar_wait(&full[s], (g / C::stages) & 1, &s_abort, wl)) break;
+        const int s = g % Q::stages;
+        if (!mbar_wait(&full[s], (g / Q::stages) & 1, &s_abort, wl)) break;
         tc_fence_after();
-        const uint32_t base = smem_u32(smem + s * C::stage_bytes);
+        const uint32_t base = smem_u32(smem + s * Q::stage_bytes);
 #pragma unroll
-        for (int ks = 0; ks < C::bk / C::uk; ++ks) {
+        for (int ks = 0; ks < Q::bk / C::uk; ++ks) {
           const uint32_t koff = ks * 32;
-          const uint64_t ah = sdesc(base + koff);
-          const uint64_t bh = sdesc(base + TILE_BYTES + boff + koff);
+          const uint64_t ah = Pipe_sdesc<Q::row>(base + koff);
+          const uint64_t bh = Pipe_sdesc<Q::row>(base + Q::tile + boff + koff);
           umma<C::tf32>(d, ah, bh, id, (kb | ks) != 0);
           if constexpr (C::split) {
-            umma<C::tf32>(d, ah, sdesc(base + 3 * TILE_BYTES + boff + koff), id, 1u);
-            umma<C::tf32>(d, sdesc(base + 2 * TILE_BYTES + koff), bh, id, 1u);
+            umma<C::tf32>(d, ah, Pipe_sdesc<Q::row>(base + 3 * Q::tile + boff + koff), id, 1u);
+            umma<C::tf32>(d, Pipe_sdesc<Q::row>(base + 2 * Q::tile + koff), bh, id, 1u);
           }
         }
         umma_commit(&empty[s]);
@@ -267,28 +292,29 @@ __global__ void __launch_bounds__(kThreads, 1)
       float* xout = Xout + gr * a.ld + n0;
       char* hrow = static_cast<char*>(ohi) + (gr * a.ld + n0) * C::eb;
       char* lrow = olo ? static_cast<char*>(olo) + (gr * a.ld + n0) * C::eb : hrow;
-      double u2 = 0.0, u3 = 0.0;
+      // (the X^2 branch needs no X_k: its FP32 master is read only for 2X - X^2;
+      // ||X^2 - X||_F is left to the FP64 refinement, which reports it)
+      double u2 = 0.0;
 #pragma unroll 1
       for (int c = 0; c < nchunk; ++c) {
         uint32_t v[32];
         tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + buf * BN + 32 * c, v);
         float y[32];
-        const float4* xi = reinterpret_cast<const float4*>(xin + 32 * c);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float4 x4 = xi[j];
-          const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+        for (int j = 0; j < 32; ++j) y[j] = __uint_as_float(v[j]);
+        if (br) {
+          const float4* xi = reinterpret_cast<const float4*>(xin + 32 * c);
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float cxx = __uint_as_float(v[4 * j + e]);
-            const float x = xs[e];
-            const float yy = br ? fmaf(2.0f, x, -cxx) : cxx;
-            y[4 * j + e] = yy;
-            u2 += (double)yy * (double)yy;
-            const double dd = (double)cxx - (double)x;
-            u3 += dd * dd;
+          for (int j = 0; j < 8; ++j) {
+            const float4 x4 = xi[j];
+            y[4 * j] = fmaf(2.0f, x4.x, -y[4 * j]);
+            y[4 * j + 1] = fmaf(2.0f, x4.y, -y[4 * j + 1]);
+            y[4 * j + 2] = fmaf(2.0f, x4.z, -y[4 * j + 2]);
+            y[4 * j + 3] = fmaf(2.0f, x4.w, -y[4 * j + 3]);
           }
         }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) u2 = fma((double)y[j], (double)y[j], u2);
         if (!mirror) {
           // diagonal tile (or one of its halves): element j is on the diagonal
           // when m0 + row == n0 + 32c + j
@@ -316,7 +342,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       t2 += w * u2;
-      t3 += w * u3;
       tc_fence_before();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[buf])) : "memory");
     }
@@ -362,9 +387,9 @@ int launch_step(tb_ctx* ctx, const SP2StepArgs& a, const CUtensorMap* mh, const 
     return TB_OK;
   }
   static unsigned long long attr_done = 0;
-  if (int rc_attr = tb_smem_attr(ctx, k_sp2_step_tc<P>, C::smem_bytes, &attr_done)) return rc_attr;
+  if (int rc_attr = tb_smem_attr(ctx, k_sp2_step_tc<P>, Pipe<P>::smem_bytes, &attr_done)) return rc_attr;
   const int grid = sp2_tc_num_parts(ctx, a.ld);
-  k_sp2_step_tc<P><<<grid, kThreads, C::smem_bytes, s>>>(a, *mh, *ml, Xin, Xout, ohi, olo);
+  k_sp2_step_tc<P><<<grid, kThreads, Pipe<P>::smem_bytes, s>>>(a, *mh, *ml, Xin, Xout, ohi, olo);
   TB_LAUNCH_CHECK(ctx);
   return TB_OK;
 }
@@ -381,17 +406,21 @@ size_t sp2_tc_operand_bytes(int precision) {
   return (precision == TB_PREC_TF32 || precision == TB_PREC_TF32X3) ? 4 : 2;
 }
 
-int sp2_tc_make_map(tb_ctx* ctx, int precision, const void* base, int ld, CUtensorMap* map) {
+int sp2_tc_row_bytes() { return Pipe<TB_PREC_TF32X3>::row; }
+
+int sp2_tc_make_map(tb_ctx* ctx, int precision, const void* base, int ld, CUtensorMap* map, int row_bytes) {
   if (!ctx->encode_tiled) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
+  if (row_bytes != 64 && row_bytes != 128) return tb_fail(ctx, TB_ERR_ARG, "tile row of %d bytes", row_bytes);
   const bool tf = precision == TB_PREC_TF32 || precision == TB_PREC_TF32X3;
   const size_t eb = tf ? 4 : 2;
   const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)ld};
   const cuuint64_t strides[1] = {(cuuint64_t)(ld * eb)};
-  const cuuint32_t box[2] = {(cuuint32_t)(128 / eb), 128};
+  const cuuint32_t box[2] = {(cuuint32_t)(row_bytes / eb), 128};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = ctx->encode_tiled(map, tf ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                                  2, const_cast<void*>(base), dims, strides, box, estr,
-                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                 row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return tb_fail(ctx, TB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return TB_OK;
@@ -411,7 +440,12 @@ int sp2_tc_step(tb_ctx* ctx, int precision, const SP2StepArgs& a, const CUtensor
 
 // --------------------------------------------------------------------------
 // Generic product of two symmetric, mutually commuting matrices (functions of
-// the same H) for the Fermi-operator expansion:
+// the same H) for the Fermi-operator expansion.  With the split precisions a
+// square A A also takes the lo*lo term: its diagonal sum_k lo_ik^2 is never
+// negative, so dropping it would bias every diagonal element low (by ~2^-22
+// of it) and the trace of the expansion by ~1e-7 per orbital, enough to move
+// mu within a gap.  Products of different matrices drop lo*lo (their
+// rounding residues are uncorrelated).  The product computed is
 //   out = alpha * (A B) + beta * E + gamma * I
 // with A, B given as tensor-core operand splits (B symmetric, so its rows are
 // read K-major), E an optional symmetric FP32 matrix.  A B is then symmetric:
@@ -430,8 +464,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(GemmArgs g, const __grid_constant__ CUtensorMap ah, const __grid_constant__ CUtensorMap al,
               const __grid_constant__ CUtensorMap bh, const __grid_constant__ CUtensorMap bl) {
   using C = Prec<P>;
+  using Q = Pipe<P>;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[C::stages], empty[C::stages], tfull[2], tempty[2], mdone;
+  __shared__ __align__(8) uint64_t full[Q::stages], empty[Q::stages], tfull[2], tempty[2], mdone;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_abort;
   __shared__ double s_red[4][2];
@@ -441,9 +476,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nt = g.ld / BM;
   const int ntiles = nt * (nt + 1) / 2;
   const unsigned long long wl = g.wait_ns ? g.wait_ns : kWaitNs;  // pipeline wait limit
-  const int nk = g.ld / C::bk;
+  const int nk = g.ld / Q::bk;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < C::stages; ++s) {
+    for (int s = 0; s < Q::stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -468,23 +503,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       int I, J;
       tri_tile(t, nt, &I, &J);
       for (int kb = 0; kb < nk; ++kb, ++gk) {
-        const int s = gk % C::stages;
-        if (gk >= C::stages && !mbar_wait(&empty[s], ((gk / C::stages) - 1) & 1, &s_abort, wl)) break;
-        uint8_t* base = smem + s * C::stage_bytes;
-        mbar_expect_tx(&full[s], C::stage_bytes);
-        tma_load_2d(base, &ah, &full[s], kb * C::bk, I * BM);
-        tma_load_2d(base + TILE_BYTES, &bh, &full[s], kb * C::bk, J * BN);
+        const int s = gk % Q::stages;
+        if (gk >= Q::stages && !mbar_wait(&empty[s], ((gk / Q::stages) - 1) & 1, &s_abort, wl)) break;
+        uint8_t* base = smem + s * Q::stage_bytes;
+        mbar_expect_tx(&full[s], Q::stage_bytes);
+        tma_load_2d(base, &ah, &full[s], kb * Q::bk, I * BM);
+        tma_load_2d(base + Q::tile, &bh, &full[s], kb * Q::bk, J * BN);
         if constexpr (C::split) {
-          tma_load_2d(base + 2 * TILE_BYTES, &al, &full[s], kb * C::bk, I * BM);
-          tma_load_2d(base + 3 * TILE_BYTES, &bl, &full[s], kb * C::bk, J * BN);
+          tma_load_2d(base + 2 * Q::tile, &al, &full[s], kb * Q::bk, I * BM);
+          tma_load_2d(base + 3 * Q::tile, &bl, &full[s], kb * Q::bk, J * BN);
         }
         issued = gk + 1;
       }
     }
     if (s_abort) {
-      for (int q = (issued > C::stages ? issued - C::stages : 0); q < issued; ++q) {
+      for (int q = (issued > Q::stages ? issued - Q::stages : 0); q < issued; ++q) {
         const unsigned long long t0 = gtime();
-        while (!mbar_try(&full[q % C::stages], (q / C::stages) & 1) && gtime() - t0 < kWaitNs) {
+        while (!mbar_try(&full[q % Q::stages], (q / Q::stages) & 1) && gtime() - t0 < kWaitNs) {
         }
       }
     }
@@ -497,18 +532,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const uint32_t d = tmem + buf * BN;
       for (int kb = 0; kb < nk; ++kb, ++gk) {
-        const int s = gk % C::stages;
-        if (!mbar_wait(&full[s], (gk / C::stages) & 1, &s_abort, wl)) break;
+        const int s = gk % Q::stages;
+        if (!mbar_wait(&full[s], (gk / Q::stages) & 1, &s_abort, wl)) break;
         tc_fence_after();
-        const uint32_t base = smem_u32(smem + s * C::stage_bytes);
+        const uint32_t base = smem_u32(smem + s * Q::stage_bytes);
 #pragma unroll
-        for (int ks = 0; ks < C::bk / C::uk; ++ks) {
+        for (int ks = 0; ks < Q::bk / C::uk; ++ks) {
           const uint32_t koff = ks * 32;
-          const uint64_t a0 = sdesc(base + koff), b0 = sdesc(base + TILE_BYTES + koff);
+          const uint64_t a0 = Pipe_sdesc<Q::row>(base + koff), b0 = Pipe_sdesc<Q::row>(base + Q::tile + koff);
           umma<C::tf32>(d, a0, b0, id, (kb | ks) != 0);
           if constexpr (C::split) {
-            umma<C::tf32>(d, a0, sdesc(base + 3 * TILE_BYTES + koff), id, 1u);
-            umma<C::tf32>(d, sdesc(base + 2 * TILE_BYTES + koff), b0, id, 1u);
+            const uint64_t a1 = Pipe_sdesc<Q::row>(base + 2 * Q::tile + koff);
+            const uint64_t b1 = Pipe_sdesc<Q::row>(base + 3 * Q::tile + koff);
+            umma<C::tf32>(d, a0, b1, id, 1u);
+            umma<C::tf32>(d, a1, b0, id, 1u);
+            if (g.lolo) umma<C::tf32>(d, a1, b1, id, 1u);
           }
         }
         umma_commit(&empty[s]);
@@ -623,8 +661,8 @@ int launch_gemm(tb_ctx* ctx, const GemmArgs& g, const CUtensorMap* ah, const CUt
                 const CUtensorMap* bh, const CUtensorMap* bl, cudaStream_t s) {
   using C = Prec<P>;
   static unsigned long long attr_done = 0;
-  if (int rc_attr = tb_smem_attr(ctx, k_gemm_tc<P>, C::smem_bytes, &attr_done)) return rc_attr;
-  k_gemm_tc<P><<<sp2_tc_num_parts(ctx, g.ld), kThreads, C::smem_bytes, s>>>(g, *ah, *al, *bh, *bl);
+  if (int rc_attr = tb_smem_attr(ctx, k_gemm_tc<P>, Pipe<P>::smem_bytes, &attr_done)) return rc_attr;
+  k_gemm_tc<P><<<sp2_tc_num_parts(ctx, g.ld), kThreads, Pipe<P>::smem_bytes, s>>>(g, *ah, *al, *bh, *bl);
   TB_LAUNCH_CHECK(ctx);
   return TB_OK;
 }

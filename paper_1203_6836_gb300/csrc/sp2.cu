@@ -509,10 +509,10 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
   // tensor-core main phase: split X0 into operands, then projections
   CUtensorMap mh[2], ml[2];
   for (int b = 0; b < 2; ++b) {
-    int rc = sp2_tc_make_map(ctx, o->precision, Hi[b], ld, &mh[b]);
+    int rc = sp2_tc_make_map(ctx, o->precision, Hi[b], ld, &mh[b], sp2_tc_row_bytes());
     if (rc) return rc;
     if (Lo[b]) {
-      rc = sp2_tc_make_map(ctx, o->precision, Lo[b], ld, &ml[b]);
+      rc = sp2_tc_make_map(ctx, o->precision, Lo[b], ld, &ml[b], sp2_tc_row_bytes());
       if (rc) return rc;
     } else {
       ml[b] = mh[b];

@@ -98,6 +98,17 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   d |= static_cast<uint64_t>(2) << 61;
   return d;
 }
+// The same for a 64-byte swizzle (layout type 4): 8-row groups of 64-byte
+// rows, 512 bytes apart.
+__device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>(512 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(4) << 61;
+  return d;
+}
 // Instruction descriptor: D = F32, A/B format `fmt` (bf16 = 1, tf32 = 2),
 // both K-major, N x M tile.
 __host__ __device__ constexpr uint32_t idesc(uint32_t fmt, int M = 128, int N = 128) {
