@@ -56,7 +56,9 @@ extern "C" {
 /* arithmetic of the purification GEMMs */
 #define TB_PREC_FP64    0  /* FP64 FMA (the plain FP64 path) */
 #define TB_PREC_TF32    1  /* tcgen05 kind::tf32, FP32 accumulate */
-#define TB_PREC_TF32X3  2  /* tcgen05 kind::tf32 on hi/lo splits: hi*hi + hi*lo + lo*hi */
+#define TB_PREC_TF32X3  2  /* tcgen05 kind::tf32 on hi/lo splits: hi*hi + hi*lo + lo*hi (squares in the
+                              grouped, block-sparse and Fermi products also lo*lo, which keeps
+                              their diagonal unbiased) */
 #define TB_PREC_BF16    3  /* tcgen05 kind::f16 (bf16), FP32 accumulate */
 #define TB_PREC_BF16X3  4  /* tcgen05 kind::f16 (bf16) on hi/lo splits */
 
@@ -68,7 +70,7 @@ typedef struct tb_ctx tb_ctx;
  * potential phi(r) = pair_a exp(-r/pair_rho) are replaced on [r1, rcut) by
  * the quintic tail of App. D.  gamma(r) = coulomb_k / sqrt(r^2 + (coulomb_k/
  * hubbard_u)^2) * w(r/gamma_cut), w(x) = (1-x)^4 (1+4x), summed over periodic
- * images. */
+ * images (gamma_form 0), or the Ewald-summed Gaussian-charge gamma (gamma_form 1). */
 typedef struct {
   double eps_s_O, eps_p_O, eps_s_H;   /* onsite energies */
   double t_hop, r_decay;              /* hopping magnitude and decay length */
@@ -76,6 +78,19 @@ typedef struct {
   double r1, rcut;                    /* tail start, cut-off of h and phi */
   double n0_O, n0_H;                  /* valence electrons of the neutral atoms */
   double pair_a, pair_rho;            /* E_pair (pair_a = 0: off) */
+  /* App. D radial form zeta(R) = A0 exp(A1 R + A2 R^2 + A3 R^3 + A4 R^4): A0 = t_hop (pair_a),
+   * A1 = -1/r_decay (-1/pair_rho); these are A2..A4 of the bond integrals and of phi (0: plain
+   * exponentials).  The App. D tail matches zeta, zeta', zeta'' at r1. */
+  double zeta_a2, zeta_a3, zeta_a4;
+  double pair_a2, pair_a3, pair_a4;
+  /* gamma_form 0: the windowed gamma above.  1: long-range gamma of Gaussian charges,
+   * gamma_ij = coulomb_k sum_T erf(|R_j - R_i + T|/c)/|R_j - R_i + T| over all periodic images T
+   * (Ewald summation with a neutralising background), c = 2 coulomb_k/(hubbard_u sqrt(pi)) so
+   * that the on-site term is U; gamma_cut is then unused.  ewald_alpha: Ewald splitting (1/A),
+   * 0 = 6.5/max(box, 10 A).  The Ewald gamma costs O(N^2 (images + reciprocal vectors)) per build
+   * and per force call. */
+  int gamma_form;
+  double ewald_alpha;
 } tb_params;
 
 /* A periodic system.  types and orb_off are device arrays. */
@@ -261,7 +276,7 @@ typedef struct {
   int ns_iters;       /* steps per inverse of A = I + 4E^2: the quadratic start (one product)
                          and ns_iters - 1 Newton-Schulz steps (0: 3, residual <= 99^-4) */
   int mu_iters;       /* cap on chemical-potential updates (one expansion each), 1..40 */
-  double trace_tol;   /* stop when |Tr D - N_occ| <= trace_tol (0: 1e-7 max(1, N_occ)) */
+  double trace_tol;   /* stop when |Tr D - N_occ| <= trace_tol (0: 1e-6 + 1e-9 N_occ) */
 } tb_fermi_opts;
 
 /* Written on the device by dm_fermi. */
@@ -284,8 +299,10 @@ int dm_fermi_workspace_size(int n, const tb_fermi_opts* opts, size_t* bytes);
  * recursive Fermi-operator expansion: from X0 = f at beta/2^m (E0 = X0 - I/2 =
  * -tanh(beta (H - mu I)/2^(m+1))/2 to third order), m steps
  * X <- X^2 [X^2 + (I - X)^2]^-1, each doubling beta, carried out on
- * E = X - I/2 as E <- 2E (I + 4E^2)^-1 (inverse by Newton-Schulz).  mu: safeguarded Newton steps with dTr D/dmu =
- * beta Tr[D(I - D)] inside a bisection bracket, all on the device.  After each expansion the
+ * E = X - I/2 as E <- 2E (I + 4E^2)^-1 (inverse by Newton-Schulz).  mu: safeguarded steps inside a
+ * bisection bracket, all on the device: Newton's step -dev/(beta t) (t = Tr[D(I - D)], dev = Tr D - N_occ),
+ * or, where |dev| ~ t (mu in a gap), the balance of the electrons (t + dev)/2 above and the holes
+ * (t - dev)/2 below mu.  After each expansion the
  * products E^2 and E^3 give D(I - D) and D(I - D)(I - 2D); the expansion is accepted and shifted
  * by u = beta dmu to second order, D + u D(I - D) + u^2/2 D(I - D)(I - 2D), with u from the trace
  * condition, whenever the remainder bound |u|^3/6 Tr[D(I - D)] (Frobenius) is below 1e-7 sqrt(n);
@@ -295,6 +312,30 @@ int dm_fermi_workspace_size(int n, const tb_fermi_opts* opts, size_t* bytes);
 int dm_fermi(tb_ctx* ctx, const double* H, int n, double n_occ, double kT, const tb_fermi_opts* opts,
              double* D, double* mu, void* workspace, size_t workspace_bytes, tb_fermi_report* report,
              void* stream);
+
+/* Workspace bytes of dm_fermi_entropy for an n x n H (19 FP64 matrices of the
+ * padded size plus small buffers). */
+int dm_fermi_entropy_workspace_size(int n, size_t* bytes);
+
+/* Electronic entropy without diagonalisation (row f1): S/k_B =
+ * -2 sum_i [f_i ln f_i + (1 - f_i) ln(1 - f_i)] (Eq. Entropy, used as the
+ * approximation of Eq. Ent_Approx), f_i the occupations of the Fermi matrix
+ * f(beta (H - mu I)) (Eq. EL_4c) at the given mu (the one dm_fermi returns).
+ * FP64 recursive expansion, GEMMs and traces only: with Y = beta (H - mu I),
+ * L(y) = ln(1 + e^y) = -ln(1 - f) obeys L(2y) = 2L(y) - ln 2 + ln(1 + 4e^2)
+ * (e = f - 1/2) along the doubling chain and s = L(y) - (1 - f) y per state,
+ * so S/k_B = 2 (n ln 2 + 2^m (dL0 + <E_m, Y0>) + sum_k 2^(m-1-k) Tr ln(I + 4E_k^2));
+ * the start at |y0| <= 1/8 uses Taylor series, each Tr ln(I + 4E_k^2) a degree-20
+ * Chebyshev series, each inverse three Newton-Schulz steps (17 FP64 products
+ * per doubling; m from Gershgorin bounds, <= 16).
+ *   H [n*n] (FP64), mu: device double (read), kT > 0 (eV);
+ *   D [n*n] output or NULL: the FP64 Fermi matrix of the recursion at mu;
+ *   S: device double output or NULL (not both NULL): S/k_B, NaN when the
+ *   spectrum needs more than 16 doublings at this kT.
+ * Asynchronous on `stream`; the workspace must not be shared by concurrent
+ * calls. */
+int dm_fermi_entropy(tb_ctx* ctx, const double* H, int n, const double* mu, double kT, double* D, double* S,
+                     void* workspace, size_t workspace_bytes, void* stream);
 
 /* ------------------------------------------------------------- a7: charges */
 
@@ -343,7 +384,8 @@ typedef struct {
   double* D;            /* [n*n] */
   double* gamma;        /* [N*N] */
   double* energies;     /* [8]: E_tot, E_pot, 2Tr[hD], E_scc, E_pair, KE, max|n-q|, steps
-                           (E_pot, E_tot without the entropy term -T_e S at kT > 0) */
+                           (at kT > 0 E_tot includes -T_e S when the entropy fields below are
+                           set, else it is KE + E_pot) */
   tb_sp2_report* sp2_report;  /* may be NULL */
   void* workspace;      /* dm_sp2 workspace (dm_sp2_workspace_size(norb)), or the dm_fermi
                            workspace when kT > 0 */
@@ -358,6 +400,10 @@ typedef struct {
                            extrapolation 3 mu[1] - 3 mu[2] + mu[3] (linear or constant while
                            fewer are known) */
   tb_fermi_report* fermi_report;  /* device, may be NULL */
+  void* entropy_workspace;    /* kT > 0: dm_fermi_entropy workspace, or NULL (no entropy term) */
+  size_t entropy_workspace_bytes;
+  double* entropy;            /* device double: S/k_B of the last D (with entropy_workspace);
+                                 energies[0] is then E_tot = KE + E_pot - kT S (Eq. Etot) */
 } tb_md_state;
 
 /* Initial state (App. D.3): SCF-converge the charges with Anderson mixing

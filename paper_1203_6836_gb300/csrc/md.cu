@@ -59,7 +59,8 @@ __global__ void k_n_update(int N, double* __restrict__ hist, int K, const double
 __global__ void __launch_bounds__(256) k_kick_energy(int N, double* __restrict__ v, const double* __restrict__ F,
                                                      const double* __restrict__ mass, double dt, int kick,
                                                      const double* __restrict__ n_cur,
-                                                     const double* __restrict__ q, double* __restrict__ E) {
+                                                     const double* __restrict__ q, double* __restrict__ E,
+                                                     const double* __restrict__ S, double kT) {
   __shared__ double s_ke[8], s_dq[8];
   double ke = 0.0, dq = 0.0;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(256) k_kick_energy(int N, double* __restrict__
       b = fmax(b, s_dq[k]);
     }
     E[5] = a;
-    E[0] = a + E[1];
+    E[0] = a + E[1] - (S ? kT * S[0] : 0.0);  // Eq. Etot: - T_e S at finite temperature
     E[6] = b;
     E[7] = kick ? E[7] + 1.0 : 0.0;
   }
@@ -130,6 +131,8 @@ int check_state(tb_ctx* ctx, const tb_md_state* st, const tb_xl_params* xp, cons
   return TB_OK;
 }
 
+bool entropy_on(const tb_md_state* st) { return st->kT > 0.0 && st->entropy_workspace && st->entropy; }
+
 // D from H: Fermi operator (dm_fermi, mu carried in st->mu) when kT > 0, else
 // the T_e = 0 projector by SP2.
 int density(tb_ctx* ctx, tb_md_state* st, const tb_sp2_opts* so, cudaStream_t s) {
@@ -147,6 +150,12 @@ int electronic_step(tb_ctx* ctx, const tb_params* p, tb_md_state* st, const tb_s
   if (rc) return rc;
   rc = density(ctx, st, so, s);
   if (rc) return rc;
+  if (entropy_on(st)) {
+    // T_e S at the mu of this D (st->mu[0]), Eq. Ent_Approx; E_tot only
+    rc = dm_fermi_entropy(ctx, st->H, st->sys.norb, st->mu, st->kT, nullptr, st->entropy, st->entropy_workspace,
+                          st->entropy_workspace_bytes, s);
+    if (rc) return rc;
+  }
   rc = mulliken(ctx, p, &st->sys, st->D, st->q, s);
   if (rc) return rc;
   return tb_forces(ctx, p, &st->sys, st->R, st->D, st->q, n_aux, st->gamma, st->F, st->energies + 1, s);
@@ -278,7 +287,8 @@ extern "C" int xlbomd_init(tb_ctx* ctx, const tb_params* p, tb_md_state* st, con
   st->step = 0;
   rc = electronic_step(ctx, p, st, so, st->n_hist, s);
   if (rc) return rc;
-  k_kick_energy<<<1, 256, 0, s>>>(N, st->v, st->F, st->mass, xp->dt, 0, st->n_hist, st->q, st->energies);
+  k_kick_energy<<<1, 256, 0, s>>>(N, st->v, st->F, st->mass, xp->dt, 0, st->n_hist, st->q, st->energies,
+                                  entropy_on(st) ? st->entropy : nullptr, st->kT);
   TB_LAUNCH_CHECK(ctx);
   if (st->kT > 0.0) {
     const double nan3[3] = {NAN, NAN, NAN};
@@ -313,7 +323,8 @@ extern "C" int xlbomd_step(tb_ctx* ctx, const tb_params* p, tb_md_state* st, con
     k_mu_shift<<<1, 1, 0, s>>>(st->mu);
     TB_LAUNCH_CHECK(ctx);
   }
-  k_kick_energy<<<1, 256, 0, s>>>(N, st->v, st->F, st->mass, xp->dt, 1, st->n_hist, st->q, st->energies);
+  k_kick_energy<<<1, 256, 0, s>>>(N, st->v, st->F, st->mass, xp->dt, 1, st->n_hist, st->q, st->energies,
+                                  entropy_on(st) ? st->entropy : nullptr, st->kT);
   TB_LAUNCH_CHECK(ctx);
   st->step += 1;
   return TB_OK;

@@ -98,7 +98,8 @@ class MDState:
     SP2 options, or kT > 0 with Fermi-operator options)."""
 
     def __init__(self, ds: DeviceSystem, v0: np.ndarray, masses: np.ndarray, n_occ: float, K: int,
-                 opts: tbmd.tb_sp2_opts, kT: float = 0.0, fermi: "tbmd.tb_fermi_opts" = None):
+                 opts: tbmd.tb_sp2_opts, kT: float = 0.0, fermi: "tbmd.tb_fermi_opts" = None,
+                 entropy: bool = False):
         dev = ds.device
         N, n = ds.natoms, ds.norb
         f64 = dict(dtype=torch.float64, device=dev)
@@ -123,13 +124,19 @@ class MDState:
             fermi = tbmd.tb_fermi_opts()
             self.ws = Workspace(tbmd.dm_sp2_workspace_size(n, opts), dev)
         self.K = K
+        # kT > 0 with entropy: E_tot (energies[0]) includes -kT S, S/k_B in self.entropy
+        self.entropy = torch.full((1,), float("nan"), dtype=torch.float64, device=dev)
+        self.ent_ws = Workspace(tbmd.dm_fermi_entropy_workspace_size(n), dev) if (entropy and kT > 0.0) else None
         self.st = tbmd.tb_md_state(
             sys=ds.sys, n_occ=float(n_occ), R=self.R.data_ptr(), v=self.v.data_ptr(), F=self.F.data_ptr(),
             mass=self.mass.data_ptr(), n_hist=self.n_hist.data_ptr(), q=self.q.data_ptr(),
             H=self.H.data_ptr(), D=self.D.data_ptr(), gamma=self.gamma.data_ptr(),
             energies=self.energies.data_ptr(), sp2_report=self.report.data_ptr(),
             workspace=self.ws.ptr, workspace_bytes=self.ws.nbytes, step=0, kT=float(kT), fermi=fermi,
-            mu=self.mu.data_ptr(), fermi_report=self.fermi_report.data_ptr())
+            mu=self.mu.data_ptr(), fermi_report=self.fermi_report.data_ptr(),
+            entropy_workspace=self.ent_ws.ptr if self.ent_ws else None,
+            entropy_workspace_bytes=self.ent_ws.nbytes if self.ent_ws else 0,
+            entropy=self.entropy.data_ptr() if self.ent_ws else None)
 
     def n_current(self) -> torch.Tensor:
         return self.n_hist[0]
@@ -145,6 +152,20 @@ def fermi_report_to_dict(buf: torch.Tensor) -> dict:
     raw = buf.detach().cpu().numpy().tobytes()
     r = tbmd.tb_fermi_report.from_buffer_copy(raw[:ctypes.sizeof(tbmd.tb_fermi_report)])
     return {k: getattr(r, k) for k, _ in tbmd.tb_fermi_report._fields_}
+
+
+class EntropySolver:
+    """dm_fermi_entropy with its workspace sized for n: S/k_B (and optionally
+    the FP64 Fermi matrix) of H at a given device mu."""
+
+    def __init__(self, ctx: tbmd.Context, n: int, device="cuda"):
+        self.ctx, self.n = ctx, int(n)
+        self.ws = Workspace(tbmd.dm_fermi_entropy_workspace_size(n), device)
+        self.S = torch.full((1,), float("nan"), dtype=torch.float64, device=device)
+
+    def __call__(self, H: torch.Tensor, mu: torch.Tensor, kT: float, D: torch.Tensor = None, stream=None):
+        tbmd.dm_fermi_entropy(self.ctx, H, self.n, mu, kT, D, self.S, self.ws.ptr, self.ws.nbytes, stream)
+        return self.S
 
 
 class FermiSolver:

@@ -42,12 +42,14 @@ class TBError(RuntimeError):
 class tb_params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "eps_s_O", "eps_p_O", "eps_s_H", "t_hop", "r_decay", "hubbard_u", "coulomb_k",
-        "gamma_cut", "r1", "rcut", "n0_O", "n0_H", "pair_a", "pair_rho")]
+        "gamma_cut", "r1", "rcut", "n0_O", "n0_H", "pair_a", "pair_rho",
+        "zeta_a2", "zeta_a3", "zeta_a4", "pair_a2", "pair_a3", "pair_a4")] + [
+        ("gamma_form", ctypes.c_int), ("ewald_alpha", ctypes.c_double)]
 
     @classmethod
     def from_model(cls, m) -> "tb_params":
         """Copy the attributes of the same names from a model-constants object."""
-        return cls(**{n: float(getattr(m, n)) for n, _ in cls._fields_})
+        return cls(**{n: (int if t is ctypes.c_int else float)(getattr(m, n)) for n, t in cls._fields_})
 
 
 class tb_system(ctypes.Structure):
@@ -93,7 +95,9 @@ class tb_md_state(ctypes.Structure):
                 ("energies", ctypes.c_void_p), ("sp2_report", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
                 ("step", ctypes.c_int64), ("kT", ctypes.c_double), ("fermi", tb_fermi_opts),
-                ("mu", ctypes.c_void_p), ("fermi_report", ctypes.c_void_p)]
+                ("mu", ctypes.c_void_p), ("fermi_report", ctypes.c_void_p),
+                ("entropy_workspace", ctypes.c_void_p), ("entropy_workspace_bytes", ctypes.c_size_t),
+                ("entropy", ctypes.c_void_p)]
 
 
 class tb_server_opts(ctypes.Structure):
@@ -137,6 +141,9 @@ _SIGS = {
                                                ctypes.POINTER(ctypes.c_size_t)]),
     "dm_fermi": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                 ctypes.POINTER(tb_fermi_opts), _P, _P, _P, ctypes.c_size_t, _P, _P]),
+    "dm_fermi_entropy_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "dm_fermi_entropy": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_double, _P, _P, _P, ctypes.c_size_t,
+                                        _P]),
     "dm_sp2_grouped_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                      ctypes.POINTER(tb_sp2_opts), ctypes.POINTER(ctypes.c_size_t)]),
     "dm_sp2_grouped_plan": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -293,6 +300,21 @@ def dm_fermi(ctx: Context, H, n: int, n_occ: float, kT: float, opts: tb_fermi_op
     return ctx.check(lib().dm_fermi(ctx.handle, _ptr(H), int(n), float(n_occ), float(kT), ctypes.byref(opts),
                                     _ptr(D), _ptr(mu), _ptr(workspace), int(workspace_bytes), _ptr(report),
                                     _stream(stream)), "dm_fermi")
+
+
+def dm_fermi_entropy_workspace_size(n: int) -> int:
+    b = ctypes.c_size_t()
+    rc = lib().dm_fermi_entropy_workspace_size(int(n), ctypes.byref(b))
+    if rc != TB_OK:
+        raise TBError(rc, "dm_fermi_entropy_workspace_size")
+    return int(b.value)
+
+
+def dm_fermi_entropy(ctx: Context, H, n: int, mu, kT: float, D, S, workspace, workspace_bytes: int,
+                     stream=None) -> int:
+    return ctx.check(lib().dm_fermi_entropy(ctx.handle, _ptr(H), int(n), _ptr(mu), float(kT), _ptr(D), _ptr(S),
+                                            _ptr(workspace), int(workspace_bytes), _stream(stream)),
+                     "dm_fermi_entropy")
 
 
 def _ints(v):
