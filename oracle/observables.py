@@ -69,6 +69,15 @@ def forces(R, types, box, p: ModelParams, D, q, n_aux, pairs=None) -> np.ndarray
     pr = tb.pair_radial(p)
     w = 2.0 * q - n_aux
     dE = np.zeros((N, 3))
+    ewald = p.gamma_form == 1
+    if ewald:
+        # every pair interacts through the long-range gamma
+        _, dG = tb.gamma_ewald(R, box, p, with_grad=True)
+        for i in range(N):
+            for j in range(i + 1, N):
+                g = 0.5 * (w[i] * n_aux[j] + w[j] * n_aux[i]) * dG[i, j]
+                dE[j] += g
+                dE[i] -= g
     for i, j, d in zip(*pairs):
         if i == j:
             continue  # a self-image term depends on the box only
@@ -78,7 +87,7 @@ def forces(R, types, box, p: ModelParams, D, q, n_aux, pairs=None) -> np.ndarray
         Dij = D[offs[i]:offs[i + 1], offs[j]:offs[j + 1]]
         # 2 Tr[hD]: block (i,j) and its transpose (j,i) both depend on d
         g_band = 4.0 * np.einsum("ab,abk->k", Dij, dblk)
-        _, dg = gr(r)
+        dg = 0.0 if ewald else gr(r)[1]
         g_scc = 0.5 * (w[i] * n_aux[j] + w[j] * n_aux[i]) * dg * u
         _, dphi = pr(r)
         g_pair = dphi * u

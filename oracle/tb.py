@@ -20,7 +20,16 @@ are not given):
   * the radial functions of h and of the pair potential phi are replaced for
     r1 <= R < rcut by the quintic tail t(R) of App. D, whose coefficients
     B0..B5 match f, f', f'' at r1 and vanish with two derivatives at rcut;
-    beyond rcut they are zero.
+    beyond rcut they are zero;
+  * the radial form of the bond integrals and of phi is App. D's
+    zeta(R) = A0 exp(A1 R + A2 R^2 + A3 R^3 + A4 R^4), with A0 = t_hop
+    (pair_a), A1 = -1/r_decay (-1/pair_rho) and A2..A4 = zeta_a2..a4
+    (pair_a2..a4), all zero by default (a plain exponential);
+  * gamma_form = 1 replaces the windowed gamma by Gaussian charges of width
+    c = 2k/(U sqrt(pi)) (so that gamma_ii = U on site), whose interaction
+    k erf(r/c)/r decays like k/R and is summed over all periodic images by
+    Ewald's method with a neutralising background (the long-range gamma; the
+    paper only fixes the 1/R decay and the on-site U).
 """
 
 from __future__ import annotations
@@ -81,12 +90,29 @@ class Radial:
         return 0.0, 0.0
 
 
+def zeta_radial(A0: float, A: tuple, r1: float, rc: float) -> Radial:
+    """zeta(R) = A0 exp(A1 R + A2 R^2 + A3 R^3 + A4 R^4) (App. D) with its tail;
+    A = (A1, A2, A3, A4).  zeta' = P' zeta, zeta'' = (P'' + P'^2) zeta with
+    P the polynomial in the exponent."""
+    a1, a2, a3, a4 = A
+
+    def P(r):
+        return r * (a1 + r * (a2 + r * (a3 + r * a4)))
+
+    def dP(r):
+        return a1 + r * (2 * a2 + r * (3 * a3 + r * 4 * a4))
+
+    def d2P(r):
+        return 2 * a2 + r * (6 * a3 + r * 12 * a4)
+
+    return Radial(lambda r: A0 * np.exp(P(r)),
+                  lambda r: A0 * dP(r) * np.exp(P(r)),
+                  lambda r: A0 * (d2P(r) + dP(r) ** 2) * np.exp(P(r)), r1, rc)
+
+
 def hopping_radial(p: ModelParams) -> Radial:
-    """V(r) = t exp(-r/r_decay) with its tail."""
-    t, a = p.t_hop, p.r_decay
-    return Radial(lambda r: t * np.exp(-r / a),
-                  lambda r: -t / a * np.exp(-r / a),
-                  lambda r: t / a**2 * np.exp(-r / a), p.r1, p.rcut)
+    """V(r) = zeta(r) with A0 = t, A1 = -1/r_decay, and its tail."""
+    return zeta_radial(p.t_hop, (-1.0 / p.r_decay, p.zeta_a2, p.zeta_a3, p.zeta_a4), p.r1, p.rcut)
 
 
 class GammaRadial:
@@ -112,11 +138,10 @@ def gamma_radial(p: ModelParams) -> GammaRadial:
 
 
 def pair_radial(p: ModelParams) -> Radial:
-    """phi(r) = A exp(-r/rho) with its tail (the short-range repulsion of E_pair)."""
-    A, rho = p.pair_a, p.pair_rho
-    return Radial(lambda r: A * np.exp(-r / rho),
-                  lambda r: -A / rho * np.exp(-r / rho),
-                  lambda r: A / rho**2 * np.exp(-r / rho), p.r1, p.rcut)
+    """phi(r) = zeta(r) with A0 = pair_a, A1 = -1/pair_rho, and its tail (the
+    short-range repulsion of E_pair)."""
+    a1 = -1.0 / p.pair_rho if p.pair_a != 0.0 else 0.0
+    return zeta_radial(p.pair_a, (a1, p.pair_a2, p.pair_a3, p.pair_a4), p.r1, p.rcut)
 
 
 # --------------------------------------------------------------------------
@@ -124,8 +149,8 @@ def pair_radial(p: ModelParams) -> Radial:
 # --------------------------------------------------------------------------
 
 def pair_range(p: ModelParams) -> float:
-    """Largest interaction range: hopping, pair potential and gamma."""
-    return max(p.rcut, p.gamma_cut)
+    """Largest short-range interaction: hopping, pair potential and (windowed) gamma."""
+    return max(p.rcut, p.gamma_cut) if p.gamma_form == 0 else p.rcut
 
 
 def orbital_offsets(types: np.ndarray) -> np.ndarray:
@@ -250,7 +275,10 @@ def build_h(R: np.ndarray, types: np.ndarray, box: float, p: ModelParams,
 
 def build_gamma(R: np.ndarray, box: float, p: ModelParams, pairs=None) -> np.ndarray:
     """gamma_ij = sum over images T of g(|R_j - R_i + T|), including the
-    on-site g(0) = U on the diagonal."""
+    on-site g(0) = U on the diagonal (gamma_form 0), or the Ewald-summed
+    Gaussian-charge gamma (gamma_form 1)."""
+    if p.gamma_form == 1:
+        return gamma_ewald(R, box, p)
     N = R.shape[0]
     gr = gamma_radial(p)
     G = np.eye(N) * p.hubbard_u
@@ -289,3 +317,113 @@ def pair_energy(R: np.ndarray, box: float, p: ModelParams, pairs=None) -> float:
         phi, _ = pr(float(np.sqrt(d @ d)))
         E += phi if i != j else 0.5 * phi
     return E
+
+
+# --------------------------------------------------------------------------
+# long-range gamma: Gaussian charges, Ewald summation
+# --------------------------------------------------------------------------
+
+def gaussian_width(p: ModelParams) -> float:
+    """c with k erf(r/c)/r -> U at r -> 0: c = 2k / (U sqrt(pi))."""
+    return 2.0 * p.coulomb_k / (p.hubbard_u * np.sqrt(np.pi))
+
+
+def ewald_alpha(box: float, alpha: float = 0.0) -> float:
+    """Splitting parameter (1/A): the given one, else 6.5 / max(box, 10 A), so
+    the real-space sum needs images up to about max(box, 10 A)."""
+    return alpha if alpha > 0.0 else 6.5 / max(box, 10.0)
+
+
+def _lattice(box: float, rmax: float) -> np.ndarray:
+    m = int(np.ceil(rmax / box)) + 1
+    r = np.arange(-m, m + 1)
+    return np.array([(a, b, c) for a in r for b in r for c in r], dtype=np.float64) * box
+
+
+def _reciprocal(box: float, alpha: float):
+    """G != 0 with exp(-G^2/(4 alpha^2)) above 1e-19 and their weights
+    A_G = (4 pi / V) exp(-G^2/(4 alpha^2)) / G^2."""
+    gmax = 2.0 * alpha * 6.6
+    m = int(np.ceil(gmax * box / (2 * np.pi)))
+    r = np.arange(-m, m + 1)
+    G = np.array([(a, b, c) for a in r for b in r for c in r if (a, b, c) != (0, 0, 0)],
+                 dtype=np.float64) * (2 * np.pi / box)
+    G2 = np.einsum("gk,gk->g", G, G)
+    keep = G2 <= gmax * gmax
+    G, G2 = G[keep], G2[keep]
+    A = 4.0 * np.pi / box**3 * np.exp(-G2 / (4.0 * alpha * alpha)) / G2
+    return G, A
+
+
+def ewald_psi(d: np.ndarray, box: float, alpha: float, self_term: bool = False):
+    """Potential of a unit point charge and all its periodic images in a
+    neutralising background, at displacements d [M, 3] (Ewald's split):
+      psi(d) = sum_L erfc(alpha |d + L|)/|d + L|
+               + (4 pi / V) sum_{G != 0} exp(-G^2/4 alpha^2) cos(G.d) / G^2 - pi/(alpha^2 V).
+    self_term: d = 0 and the L = 0 term left out, which adds -2 alpha/sqrt(pi).
+    Returns (psi [M], grad [M, 3])."""
+    from scipy.special import erfc
+    d = np.atleast_2d(d)
+    L = _lattice(box, 6.6 / alpha)
+    G, A = _reciprocal(box, alpha)
+    psi = np.zeros(len(d))
+    grad = np.zeros((len(d), 3))
+    for m, dm in enumerate(d):
+        x = dm[None, :] + L
+        r = np.sqrt(np.einsum("lk,lk->l", x, x))
+        ok = r > 1e-12
+        x, r = x[ok], r[ok]
+        f = erfc(alpha * r) / r
+        df = (-2.0 * alpha / np.sqrt(np.pi) * np.exp(-(alpha * r) ** 2) - f) / r
+        psi[m] = np.sum(f)
+        grad[m] = np.sum((df / r)[:, None] * x, axis=0)
+        gd = G @ dm
+        psi[m] += np.sum(A * np.cos(gd))
+        grad[m] -= np.sum((A * np.sin(gd))[:, None] * G, axis=0)
+    psi -= np.pi / (alpha * alpha * box**3)
+    if self_term:
+        psi -= 2.0 * alpha / np.sqrt(np.pi)
+    return psi, grad
+
+
+def _gauss_short(d: np.ndarray, box: float, c: float, self_term: bool = False):
+    """sum_L erfc(|d + L|/c)/|d + L| over all images (L = 0 left out at d = 0),
+    and its gradient."""
+    from scipy.special import erfc
+    d = np.atleast_2d(d)
+    L = _lattice(box, 6.6 * c)
+    out = np.zeros(len(d))
+    grad = np.zeros((len(d), 3))
+    for m, dm in enumerate(d):
+        x = dm[None, :] + L
+        r = np.sqrt(np.einsum("lk,lk->l", x, x))
+        ok = r > 1e-12
+        x, r = x[ok], r[ok]
+        f = erfc(r / c) / r
+        df = (-2.0 / (c * np.sqrt(np.pi)) * np.exp(-(r / c) ** 2) - f) / r
+        out[m] = np.sum(f)
+        grad[m] = np.sum((df / r)[:, None] * x, axis=0)
+    return out, grad
+
+
+def gamma_ewald(R: np.ndarray, box: float, p: ModelParams, with_grad: bool = False):
+    """gamma_ij = k sum_L erf(|d + L|/c)/|d + L|, d = R_j - R_i, over all images
+    (Ewald, neutralising background) = k [psi(d) - sum_L erfc(|d + L|/c)/|d + L|];
+    on the diagonal the L = 0 term is its on-site limit 2k/(c sqrt(pi)) = U.
+    with_grad: also dgamma[i, j] = d gamma_ij / d d (antisymmetric in i, j)."""
+    N = R.shape[0]
+    k, c = p.coulomb_k, gaussian_width(p)
+    alpha = ewald_alpha(box, p.ewald_alpha)
+    G = np.zeros((N, N))
+    dG = np.zeros((N, N, 3))
+    iu, ju = np.triu_indices(N, 1)
+    d = R[ju] - R[iu]
+    psi, gpsi = ewald_psi(d, box, alpha)
+    sr, gsr = _gauss_short(d, box, c)
+    G[iu, ju] = G[ju, iu] = k * (psi - sr)
+    dG[iu, ju] = k * (gpsi - gsr)
+    dG[ju, iu] = -dG[iu, ju]
+    psi0, _ = ewald_psi(np.zeros((1, 3)), box, alpha, self_term=True)
+    s0, _ = _gauss_short(np.zeros((1, 3)), box, c)
+    G[np.arange(N), np.arange(N)] = p.hubbard_u + k * (psi0[0] - s0[0])
+    return (G, dG) if with_grad else G

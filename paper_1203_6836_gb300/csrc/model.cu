@@ -9,9 +9,12 @@
 //        D = theta(mu0 - H[n]) at fixed N_occ)
 //
 // Hopping: Slater-Koster two-centre table with ss-sigma = -V, sp-sigma = +V,
-// pp-sigma = +V, pp-pi = -V sharing V(r) = t exp(-r/r_decay); V and the pair
-// potential are replaced on [r1, rcut) by the quintic tail of App. D.
-// gamma(r) = k/sqrt(r^2 + (k/U)^2) * (1-x)^4 (1+4x), x = r/gamma_cut.
+// pp-sigma = +V, pp-pi = -V sharing V(r) = zeta(r) = t exp(P(r)),
+// P(r) = -r/r_decay + a2 r^2 + a3 r^3 + a4 r^4 (App. D's radial form); V and
+// the pair potential (same form) are replaced on [r1, rcut) by the quintic
+// tail of App. D.  gamma(r) = k/sqrt(r^2 + (k/U)^2) * (1-x)^4 (1+4x),
+// x = r/gamma_cut (gamma_form 0), or the Ewald sum over all images of the
+// Gaussian-charge interaction k erf(r/c)/r (gamma_form 1, k_gamma_ewald).
 //
 // Layout: H and D dense row-major n x n (FP64), orbitals grouped by atom;
 // gamma dense N x N.  Pair work is done once per ordered or unordered atom
@@ -70,16 +73,36 @@ int tb_model_from_params(tb_ctx* ctx, const tb_params* p, double box, ModelDev* 
   m->n0_H = p->n0_H;
   m->pair_a = p->pair_a;
   m->inv_prho = p->pair_a != 0.0 ? 1.0 / p->pair_rho : 0.0;
-  {
-    const double a = m->inv_decay, v = p->t_hop * exp(-p->r1 * a);
-    tail_closed_form(v, -a * v, a * a * v, p->r1, p->rcut, m->Bhop);
-  }
-  {
-    const double a = m->inv_prho, v = p->pair_a * exp(-p->r1 * a);
-    tail_closed_form(v, -a * v, a * a * v, p->r1, p->rcut, m->Bpair);
-  }
-  m->range = fmax(p->rcut, p->gamma_cut);
+  m->zhop[0] = p->zeta_a2;
+  m->zhop[1] = p->zeta_a3;
+  m->zhop[2] = p->zeta_a4;
+  m->zpair[0] = p->pair_a2;
+  m->zpair[1] = p->pair_a3;
+  m->zpair[2] = p->pair_a4;
+  // zeta, zeta', zeta'' at r1 for the tail: zeta' = P' zeta, zeta'' = (P'' + P'^2) zeta
+  auto zeta3 = [&](double A0, double a1, const double* a, double r, double* f) {
+    const double P = r * (a1 + r * (a[0] + r * (a[1] + r * a[2])));
+    const double dP = a1 + r * (2.0 * a[0] + r * (3.0 * a[1] + r * 4.0 * a[2]));
+    const double d2P = 2.0 * a[0] + r * (6.0 * a[1] + r * 12.0 * a[2]);
+    const double v = A0 * exp(P);
+    f[0] = v;
+    f[1] = dP * v;
+    f[2] = (d2P + dP * dP) * v;
+  };
+  double f[3];
+  zeta3(p->t_hop, -m->inv_decay, m->zhop, p->r1, f);
+  tail_closed_form(f[0], f[1], f[2], p->r1, p->rcut, m->Bhop);
+  zeta3(p->pair_a, -m->inv_prho, m->zpair, p->r1, f);
+  tail_closed_form(f[0], f[1], f[2], p->r1, p->rcut, m->Bpair);
+  if (p->gamma_form != 0 && p->gamma_form != 1) return tb_fail(ctx, TB_ERR_ARG, "gamma_form %d", p->gamma_form);
+  if (!(p->ewald_alpha >= 0.0)) return tb_fail(ctx, TB_ERR_ARG, "ewald_alpha %g < 0", p->ewald_alpha);
+  m->gamma_form = p->gamma_form;
+  m->range = p->gamma_form == 0 ? fmax(p->rcut, p->gamma_cut) : p->rcut;
   m->box = box;
+  m->ealpha = p->ewald_alpha > 0.0 ? p->ewald_alpha : 6.5 / fmax(box, 10.0);
+  m->gwidth = 2.0 * p->coulomb_k / (p->hubbard_u * sqrt(M_PI));
+  m->erange = fmax(6.6 / m->ealpha, 6.6 * m->gwidth);
+  m->gmax = 13.2 * m->ealpha;
   return TB_OK;
 }
 
@@ -92,12 +115,19 @@ __device__ __forceinline__ void tail_eval(const double* B, double x, double* f, 
   *df = B[1] + x * (2.0 * B[2] + x * (3.0 * B[3] + x * (4.0 * B[4] + x * 5.0 * B[5])));
 }
 
+// zeta(r) = A0 exp(P(r)), P(r) = a1 r + a2 r^2 + a3 r^3 + a4 r^4, and zeta'.
+__device__ __forceinline__ void zeta(double A0, double a1, const double* a, double r, double* f, double* df) {
+  const double P = r * (a1 + r * (a[0] + r * (a[1] + r * a[2])));
+  const double dP = a1 + r * (2.0 * a[0] + r * (3.0 * a[1] + r * 4.0 * a[2]));
+  const double v = A0 * exp(P);
+  *f = v;
+  *df = dP * v;
+}
+
 // V(r) and V'(r) of the hopping with its tail.
 __device__ __forceinline__ void hop_radial(const ModelDev& m, double r, double* V, double* dV) {
   if (r < m.r1) {
-    const double v = m.t_hop * exp(-r * m.inv_decay);
-    *V = v;
-    *dV = -m.inv_decay * v;
+    zeta(m.t_hop, -m.inv_decay, m.zhop, r, V, dV);
   } else if (r < m.rcut) {
     tail_eval(m.Bhop, r - m.r1, V, dV);
   } else {
@@ -111,9 +141,7 @@ __device__ __forceinline__ void pair_radial(const ModelDev& m, double r, double*
     *f = 0.0;
     *df = 0.0;
   } else if (r < m.r1) {
-    const double v = m.pair_a * exp(-r * m.inv_prho);
-    *f = v;
-    *df = -m.inv_prho * v;
+    zeta(m.pair_a, -m.inv_prho, m.zpair, r, f, df);
   } else {
     tail_eval(m.Bpair, r - m.r1, f, df);
   }
@@ -233,9 +261,11 @@ __global__ void __launch_bounds__(256) k_build_pairs(ModelDev m, int N, const in
           const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
           const double r = sqrt(r2);
           if (r >= m.range) continue;
-          double g, dg;
-          gamma_radial(m, r, &g, &dg);
-          gsum += g;
+          if (m.gamma_form == 0) {
+            double g, dg;
+            gamma_radial(m, r, &g, &dg);
+            gsum += g;
+          }
           if (r < m.rcut) {
             double V, dV;
             hop_radial(m, r, &V, &dV);
@@ -265,6 +295,162 @@ __global__ void __launch_bounds__(256) k_build_pairs(ModelDev m, int N, const in
     }
   G[(size_t)i * N + j] = gsum;
   if (i != j) G[(size_t)j * N + i] = gsum;
+}
+
+// --------------------------------------------------------------------------
+// long-range gamma (gamma_form 1): Gaussian charges, Ewald summation
+// --------------------------------------------------------------------------
+//
+// gamma_ij = k sum_T erf(|d + T|/c)/|d + T|, d = R_j - R_i, split as
+//   k [ sum_T (erfc(alpha r) - erfc(r/c))/r                  (real space, r = |d + T|)
+//     + (4 pi/V) sum_{G != 0} e^{-G^2/4 alpha^2} cos(G.d)/G^2 - pi/(alpha^2 V) ]
+// and on the diagonal (T = 0 left out of the real-space sum) U - 2 k alpha/sqrt(pi)
+// added.  The reciprocal vectors G = 2 pi/L (h, k, l), |G| <= 13.2 alpha, are
+// generated block-wise into shared memory (one per thread, weights with the
+// factor 2 of the half space h > 0 | h = 0, k > 0 | h = k = 0, l > 0).
+
+constexpr int kGChunk = 128;
+
+struct GChunk {
+  double gx[kGChunk], gy[kGChunk], gz[kGChunk], a[kGChunk];
+};
+
+// Fill chunk c (kGChunk cube indices starting at c * kGChunk) of the half-space
+// reciprocal vectors: the weight is zero outside the sphere or the half space.
+__device__ __forceinline__ void g_chunk(const ModelDev& m, int hmax, long long c, GChunk* s) {
+  const long long side = 2 * hmax + 1;
+  const long long idx = c * kGChunk + threadIdx.x % kGChunk;
+  double gx = 0.0, gy = 0.0, gz = 0.0, w = 0.0;
+  if (idx < side * side * side) {
+    const int h = (int)(idx / (side * side)) - hmax;
+    const int k = (int)((idx / side) % side) - hmax;
+    const int l = (int)(idx % side) - hmax;
+    const bool half = h > 0 || (h == 0 && (k > 0 || (k == 0 && l > 0)));
+    const double tp = 2.0 * M_PI / m.box;
+    gx = tp * h;
+    gy = tp * k;
+    gz = tp * l;
+    const double g2 = gx * gx + gy * gy + gz * gz;
+    if (half && g2 <= m.gmax * m.gmax) {
+      const double V = m.box * m.box * m.box;
+      w = 2.0 * 4.0 * M_PI / V * exp(-g2 / (4.0 * m.ealpha * m.ealpha)) / g2;
+    }
+  }
+  if (threadIdx.x < kGChunk) {
+    s->gx[threadIdx.x] = gx;
+    s->gy[threadIdx.x] = gy;
+    s->gz[threadIdx.x] = gz;
+    s->a[threadIdx.x] = w;
+  }
+}
+
+__device__ __forceinline__ int g_hmax(const ModelDev& m) { return (int)ceil(m.gmax * m.box / (2.0 * M_PI)); }
+
+// Real-space part of gamma_ij / k and its gradient, images with r < erange.
+__device__ __forceinline__ void ewald_real(const ModelDev& m, const double d0[3], bool self, double* v,
+                                           double g[3]) {
+  int lo[3], hi[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) image_range(d0[c], m.box, m.erange, &lo[c], &hi[c]);
+  const double a = m.ealpha, ic = 1.0 / m.gwidth;
+  const double ka = 2.0 * a / sqrt(M_PI), kc = 2.0 * ic / sqrt(M_PI);
+  for (int kx = lo[0]; kx <= hi[0]; ++kx)
+    for (int ky = lo[1]; ky <= hi[1]; ++ky)
+      for (int kz = lo[2]; kz <= hi[2]; ++kz) {
+        if (self && kx == 0 && ky == 0 && kz == 0) continue;
+        const double d[3] = {d0[0] + kx * m.box, d0[1] + ky * m.box, d0[2] + kz * m.box};
+        const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (r >= m.erange) continue;
+        const double f = (erfc(a * r) - erfc(r * ic)) / r;
+        const double df = (-ka * exp(-a * a * r * r) + kc * exp(-r * r * ic * ic) - f) / r;
+        *v += f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) g[c] += df * d[c] / r;
+      }
+}
+
+// One thread per unordered pair (i <= j): gamma_ij and gamma_ji.
+__global__ void __launch_bounds__(kGChunk) k_gamma_ewald(ModelDev m, int N, const double* __restrict__ R,
+                                                         double* __restrict__ G) {
+  __shared__ GChunk s;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  const bool live = i < N && j < N && j >= i;
+  double d0[3] = {0.0, 0.0, 0.0};
+  if (live) min_image(R + 3 * i, R + 3 * j, m.box, d0);
+  double v = 0.0, gr[3] = {0.0, 0.0, 0.0};
+  if (live) ewald_real(m, d0, i == j, &v, gr);
+  const int hmax = g_hmax(m);
+  const long long side = 2 * hmax + 1, chunks = (side * side * side + kGChunk - 1) / kGChunk;
+  double rec = 0.0;
+  for (long long c = 0; c < chunks; ++c) {
+    __syncthreads();
+    g_chunk(m, hmax, c, &s);
+    __syncthreads();
+    if (live)
+      for (int t = 0; t < kGChunk; ++t)
+        if (s.a[t] != 0.0) rec = fma(s.a[t], cos(s.gx[t] * d0[0] + s.gy[t] * d0[1] + s.gz[t] * d0[2]), rec);
+  }
+  if (!live) return;
+  const double V = m.box * m.box * m.box;
+  double gam = m.kc * (v + rec - M_PI / (m.ealpha * m.ealpha * V));
+  if (i == j) gam += m.U - m.kc * 2.0 * m.ealpha / sqrt(M_PI);
+  G[(size_t)i * N + j] = gam;
+  if (i != j) G[(size_t)j * N + i] = gam;
+}
+
+// SCC forces of the long-range gamma: F_a += sum_{b != a} 1/2 (w_a n_b + w_b n_a)
+// d gamma_ab / d d_ab (w = 2q - n, d = R_b - R_a).  One warp per atom a (8 per
+// block, the reciprocal vectors shared by the block).
+__global__ void __launch_bounds__(256) k_forces_ewald(ModelDev m, int N, const double* __restrict__ R,
+                                                      const double* __restrict__ q,
+                                                      const double* __restrict__ n_aux,
+                                                      double* __restrict__ F) {
+  __shared__ GChunk s;
+  const int a = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const bool live = a < N;
+  const double wa = live ? 2.0 * q[a] - n_aux[a] : 0.0, na = live ? n_aux[a] : 0.0;
+  double f[3] = {0.0, 0.0, 0.0};
+  const int hmax = g_hmax(m);
+  const long long side = 2 * hmax + 1, chunks = (side * side * side + kGChunk - 1) / kGChunk;
+  // real space first (no shared memory), then the reciprocal part chunk by chunk
+  if (live)
+    for (int b = lane; b < N; b += 32) {
+      if (b == a) continue;
+      double d0[3], v = 0.0, g[3] = {0.0, 0.0, 0.0};
+      min_image(R + 3 * a, R + 3 * b, m.box, d0);
+      ewald_real(m, d0, false, &v, g);
+      const double c = 0.5 * (wa * n_aux[b] + (2.0 * q[b] - n_aux[b]) * na) * m.kc;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) f[k] += c * g[k];
+    }
+  for (long long ch = 0; ch < chunks; ++ch) {
+    __syncthreads();
+    if (threadIdx.x < kGChunk) g_chunk(m, hmax, ch, &s);
+    __syncthreads();
+    if (!live) continue;
+    for (int b = lane; b < N; b += 32) {
+      if (b == a) continue;
+      double d0[3];
+      min_image(R + 3 * a, R + 3 * b, m.box, d0);
+      const double c = 0.5 * (wa * n_aux[b] + (2.0 * q[b] - n_aux[b]) * na) * m.kc;
+      for (int t = 0; t < kGChunk; ++t) {
+        if (s.a[t] == 0.0) continue;
+        const double sn = sin(s.gx[t] * d0[0] + s.gy[t] * d0[1] + s.gz[t] * d0[2]);
+        const double w = -c * s.a[t] * sn;
+        f[0] += w * s.gx[t];
+        f[1] += w * s.gy[t];
+        f[2] += w * s.gz[t];
+      }
+    }
+  }
+  if (!live) return;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) f[k] = warp_sum(f[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) F[3 * a + k] += f[k];
 }
 
 // SCC shift: one warp per atom i, shift_i = sum_l gamma_il n_l added to the
@@ -310,6 +496,10 @@ extern "C" int tb_build_H(tb_ctx* ctx, const tb_params* p, const tb_system* sys,
   dim3 grid((N + 255) / 256, N);
   k_build_pairs<<<grid, 256, 0, s>>>(m, N, sys->types, sys->orb_off, R, H, n, gamma);
   TB_LAUNCH_CHECK(ctx);
+  if (m.gamma_form == 1) {
+    k_gamma_ewald<<<dim3((N + kGChunk - 1) / kGChunk, N), kGChunk, 0, s>>>(m, N, R, gamma);
+    TB_LAUNCH_CHECK(ctx);
+  }
   if (n_aux) {
     k_add_shift<<<(N * 32 + 255) / 256, 256, 0, s>>>(N, sys->orb_off, gamma, n_aux, H, n);
     TB_LAUNCH_CHECK(ctx);
@@ -454,7 +644,7 @@ __global__ void __launch_bounds__(256) k_forces(ModelDev m, int N, const int32_t
 #pragma unroll
               for (int k = 0; k < 3; ++k) f[k] += dph * l[k];
           }
-          if (b != a) {
+          if (b != a && m.gamma_form == 0) {
             double gg, dgg;
             gamma_radial(m, r, &gg, &dgg);
             const double c = 0.5 * (wa * nb + wb * na) * dgg;
@@ -525,5 +715,9 @@ extern "C" int tb_forces(tb_ctx* ctx, const tb_params* p, const tb_system* sys, 
   k_forces<<<N, 32, 0, s>>>(m, N, sys->types, sys->orb_off, R, D, sys->norb, q,
                                                   n_aux, gamma, F, energy);
   TB_LAUNCH_CHECK(ctx);
+  if (m.gamma_form == 1) {
+    k_forces_ewald<<<(N + 7) / 8, 256, 0, s>>>(m, N, R, q, n_aux, F);
+    TB_LAUNCH_CHECK(ctx);
+  }
   return TB_OK;
 }

@@ -150,3 +150,143 @@ def test_periodic_images_small_box():
                     ref00 += -Vr(np.linalg.norm(T))[0]
     assert h[0, 1] == pytest.approx(ref01, rel=1e-12)
     assert h[0, 0] == pytest.approx(P.eps_s_H + ref00, rel=1e-12)
+
+
+# ---------------------------------------------------------------- long range
+# The Ewald-summed Coulomb potential and the Gaussian-charge gamma, pinned by
+# textbook lattice constants and closed-form limits.
+
+def test_ewald_nacl_madelung_constant():
+    """Rock salt (8 ions of charge +-1 in a cubic cell of side a): the Coulomb
+    energy per ion pair is -M / r0 with r0 = a/2 and Madelung's constant
+    M = 1.7475645946 (point charges; the background cancels for a neutral cell)."""
+    a = 5.64
+    na = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]]) * a
+    cl = na + np.array([.5, 0, 0]) * a
+    R = np.vstack([na, cl])
+    qv = np.array([1.0] * 4 + [-1.0] * 4)
+    for alpha in (0.5, 0.9):
+        E = 0.0
+        for i in range(8):
+            for j in range(8):
+                if i == j:
+                    psi, _ = tb.ewald_psi(np.zeros((1, 3)), a, alpha, self_term=True)
+                else:
+                    psi, _ = tb.ewald_psi((R[j] - R[i])[None, :], a, alpha)
+                E += 0.5 * qv[i] * qv[j] * psi[0]
+        assert E / 4 * (a / 2) == pytest.approx(-1.7475645946331822, rel=1e-10)
+
+
+def test_ewald_simple_cubic_self_term_and_small_distance_limit():
+    """A unit charge, its simple-cubic images and a neutralising background:
+    the potential of the images at the charge is xi/L with xi = -2.837297479
+    (the simple-cubic constant), and near the charge
+    psi(d) = 1/d + xi/L + (2 pi / 3) d^2 / L^3 + O(d^4/L^5) (the background's
+    uniform charge -1/V gives the d^2 term)."""
+    L = 7.0
+    xi = -2.837297479480620
+    psi0, _ = tb.ewald_psi(np.zeros((1, 3)), L, 0.8, self_term=True)
+    assert psi0[0] * L == pytest.approx(xi, rel=1e-10)
+    res = []
+    for s in (0.004, 0.002, 0.001):
+        d = np.array([[2.0, 1.0, -1.5]]) * s * L
+        r = np.linalg.norm(d)
+        psi, _ = tb.ewald_psi(d, L, 0.8)
+        res.append(psi[0] - (1 / r + xi / L + 2 * np.pi / 3 * r * r / L**3))
+    # the remainder is fourth order: it drops 16-fold per halving of d
+    assert res[0] / res[1] == pytest.approx(16.0, rel=0.03) and res[1] / res[2] == pytest.approx(16.0, rel=0.05)
+    assert abs(res[2]) < 1e-10
+
+
+def test_ewald_independent_of_the_split_and_gradient():
+    rng = np.random.default_rng(3)
+    box = 6.5
+    d = rng.uniform(-4, 4, (5, 3))
+    a, ga = tb.ewald_psi(d, box, 0.45)
+    b, gb = tb.ewald_psi(d, box, 1.1)
+    assert np.abs(a - b).max() < 1e-11 and np.abs(ga - gb).max() < 1e-11
+    h = 1e-5
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        fd = (tb.ewald_psi(d + e, box, 0.7)[0] - tb.ewald_psi(d - e, box, 0.7)[0]) / (2 * h)
+        assert np.abs(fd - ga[:, k]).max() < 1e-8
+
+
+def test_gaussian_gamma_onsite_long_range_and_positive():
+    """gamma_form = 1: gamma_ii = U + (images), gamma_ij -> k erf(r/c)/r + xi k/L
+    for a pair far from its images (large box), Ewald split independent,
+    positive definite on neutral charge vectors, gradient = finite differences."""
+    import dataclasses
+    P1 = dataclasses.replace(ModelParams(), gamma_form=1)
+    from scipy.special import erf
+    L = 60.0
+    R = np.array([[0.0, 0.0, 0.0], [2.3, 1.1, -0.7]])
+    G = tb.gamma_ewald(R, L, P1)
+    c = tb.gaussian_width(P1)
+    r = np.linalg.norm(R[1] - R[0])
+    xi = -2.837297479480620
+    k = P1.coulomb_k
+    assert G[0, 1] == pytest.approx(k * erf(r / c) / r + k * xi / L + k * 2 * np.pi / 3 * r * r / L**3, abs=1e-6)
+    assert G[0, 0] == pytest.approx(P1.hubbard_u + k * xi / L, abs=1e-9)
+    s = water_24_atoms()
+    Ga = tb.gamma_ewald(s.R, s.box, dataclasses.replace(P1, ewald_alpha=0.5))
+    Gb, dG = tb.gamma_ewald(s.R, s.box, dataclasses.replace(P1, ewald_alpha=0.9), with_grad=True)
+    assert np.abs(Ga - Gb).max() < 1e-10
+    assert np.allclose(Gb, Gb.T, atol=1e-14)
+    Pn = np.eye(24) - 1.0 / 24
+    assert np.linalg.eigvalsh(Pn @ Gb @ Pn)[1:].min() > 0
+    h = 1e-5
+    i, j = 2, 7
+    for kk in range(3):
+        Rp, Rm = s.R.copy(), s.R.copy()
+        Rp[j, kk] += h
+        Rm[j, kk] -= h
+        fd = (tb.gamma_ewald(Rp, s.box, P1)[i, j] - tb.gamma_ewald(Rm, s.box, P1)[i, j]) / (2 * h)
+        assert fd == pytest.approx(dG[i, j, kk], abs=1e-7)
+
+
+def test_zeta_radial_form():
+    """zeta(R) = A0 exp(A1 R + A2 R^2 + A3 R^3 + A4 R^4): with A2..A4 = 0 it is
+    the plain exponential; with them nonzero its derivative is the finite
+    difference of the value and the App. D tail joins it with two
+    continuous derivatives at r1 and vanishes at rcut."""
+    P = ModelParams()
+    plain = tb.hopping_radial(P)
+    for r in (0.8, 1.5, 3.0):
+        assert plain(r)[0] == pytest.approx(P.t_hop * np.exp(-r / P.r_decay), rel=1e-14)
+    z = tb.zeta_radial(3.0, (-2.0, 0.05, -0.01, 0.0005), P.r1, P.rcut)
+    h = 1e-6
+    for r in (1.0, 2.5, 4.5, 5.5):
+        fd = (z(r + h)[0] - z(r - h)[0]) / (2 * h)
+        assert fd == pytest.approx(z(r)[1], rel=1e-7)
+    a, b = z(P.r1 - 1e-9), z(P.r1 + 1e-9)
+    assert a[0] == pytest.approx(b[0], rel=1e-7) and a[1] == pytest.approx(b[1], rel=1e-6)
+    d2 = lambda r: (z(r + 1e-6)[1] - z(r - 1e-6)[1]) / 2e-6
+    assert d2(P.r1 - 3e-6) == pytest.approx(d2(P.r1 + 3e-6), rel=1e-4)
+    assert z(P.rcut)[0] == 0.0 and abs(z(P.rcut - 1e-6)[0]) < 1e-12
+
+
+def test_forces_are_minus_the_energy_gradient_with_long_range_gamma_and_zeta():
+    """Central differences of the energy at fixed n and D, with the Ewald gamma
+    and a nonzero zeta polynomial on both h and phi."""
+    import dataclasses
+    from oracle import observables, density
+    P1 = dataclasses.replace(ModelParams(), gamma_form=1, zeta_a2=0.02, zeta_a3=-0.004, pair_a2=0.1)
+    s = water_24_atoms()
+    rng = np.random.default_rng(8)
+    n = rng.normal(0, 0.2, 24)
+    n -= n.mean()
+    H = tb.build_H(tb.build_h(s.R, s.types, s.box, P1), tb.build_gamma(s.R, s.box, P1), s.types, n)
+    D = density.density_T0(H, int(s.n_occ(P1))).D
+    q = observables.mulliken(D, s.types, P1)
+    F = observables.forces(s.R, s.types, s.box, P1, D, q, n)
+    h = 1e-5
+    for a, kk in ((0, 0), (5, 2), (17, 1)):
+        Rp, Rm = s.R.copy(), s.R.copy()
+        Rp[a, kk] += h
+        Rm[a, kk] -= h
+        Ep = observables.potential_energy(Rp, s.types, s.box, P1, D, q, n)
+        Em = observables.potential_energy(Rm, s.types, s.box, P1, D, q, n)
+        assert -(Ep - Em) / (2 * h) == pytest.approx(F[a, kk], rel=2e-6, abs=1e-7)
+    assert np.abs(F.sum(axis=0)).max() < 1e-9

@@ -58,6 +58,19 @@ class ModelParams:
     mass_H: float = 1.0
     pair_a: float = 24.0
     pair_rho: float = 0.3
+    # radial form zeta(R) = A0 exp(A1 R + A2 R^2 + A3 R^3 + A4 R^4) of App. D:
+    # A0 = t_hop (pair_a), A1 = -1/r_decay (-1/pair_rho); A2..A4 below
+    zeta_a2: float = 0.0
+    zeta_a3: float = 0.0
+    zeta_a4: float = 0.0
+    pair_a2: float = 0.0
+    pair_a3: float = 0.0
+    pair_a4: float = 0.0
+    # gamma: 0 = the windowed short-range form, 1 = Gaussian charges of width
+    # set by U with the long-range 1/R tail summed by Ewald (ewald_alpha: the
+    # Ewald splitting in 1/A, 0 = chosen from the box)
+    gamma_form: int = 0
+    ewald_alpha: float = 0.0
 
 
 @dataclasses.dataclass(frozen=True)
