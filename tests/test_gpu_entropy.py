@@ -12,7 +12,7 @@ trajectory the GPU's E_pot carries the tf32x3 expansion's D error (held to
 2e-6 eV per atom as in the other finite-T tests); T_e S is exact for the GPU's
 H[n] and mu, but those differ from the oracle's by the charges (~1e-6 e) that
 the same D error moves, so T_e S is held to the same per-atom budget (at
-kT = 0.5 eV, where dS/d eps is largest, the difference is ~4e-6 eV on 6 atoms)."""
+kT = 0.5 eV, where dS/d eps is largest, the difference is ~1e-5 eV on 24 atoms)."""
 
 import dataclasses
 
@@ -122,7 +122,7 @@ def _gpu_trajectory(ctx, XL, s, M, v0, kT, nsteps):
     return st, xp, opts
 
 
-# kappa = s kappa0: the two-molecule box keeps a bounded charge residual up to
+# kappa = s kappa0: the 8-molecule box (24 atoms) keeps a bounded charge residual up to
 # s ~ 0.06 at kT = 0.5 eV (0.075 diverges in the oracle too) and 0.15 at 0.1 eV
 KAPPA = {0.1: 0.15, 0.5: 0.05}
 
@@ -153,7 +153,7 @@ def test_finite_temperature_total_energy_matches_oracle(ctx, kT):
 def test_kappa_study_at_half_an_electronvolt(ctx):
     """Sec. III.D / Table II: at k_B T_e = 0.5 eV the constant kappa rescaled
     by 3/4 instead of 1/2 conserves E_tot = KE + E_pot - T_e S better.  Here the
-    largest stable rescaling of the two-molecule box is ~0.06, so the pair is
+    largest stable rescaling of the 8-molecule box is ~0.06, so the pair is
     0.06 x 1/2 = 0.03 and 0.06 x 3/4 = 0.045; 200 steps of 0.25 fs on the GPU
     give the sigma (standard deviation of E_tot) and drift (least-squares
     slope per atom) of Table II.  The GPU values match the oracle's run of

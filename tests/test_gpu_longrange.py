@@ -75,7 +75,7 @@ def test_ewald_forces_and_energy_match_oracle(ctx):
 
 
 def test_xlbomd_with_long_range_gamma_matches_oracle(ctx):
-    """Ten steps of two H2O-like molecules with the Ewald gamma and the zeta
+    """Ten steps of 8 H2O-like molecules (24 atoms) with the Ewald gamma and the zeta
     polynomial (T_e = 0, FP64 SP2): positions, charges and E_tot agree."""
     XL = dataclasses.replace(XLParams(), kappa_scale=0.15)
     m = molecular_water(2, 8.0, seed=1)
