@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-check", action="store_true", help="skip the accuracy check against the oracle")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path step")
+    ap.add_argument("--no-dynamics", action="store_true",
+                    help="skip the T_e = 0 dynamics of the gapped 2046-atom system")
     ap.add_argument("--workload", default="dense", choices=["dense", "small", "sparse", "batched", "serving"])
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the arrival trace")
     ap.add_argument("--sparse-natoms", type=int, default=16384,
@@ -415,6 +417,10 @@ def run_ours(args):
                      "band_energy_abs_eV": float(abs(2 * np.sum(h0 * Dg) - 2 * np.sum(h0 * ref.D))),
                      "gap_eV": float(ref.gap), "inputs": "R of the 2048-atom system, n = 0"}
 
+        dyn = None
+        if not args.no_dynamics:
+            dyn = gapped_dynamics(ctx, args, stream)
+
         cpu = None
         if not args.no_cpu and world == 1:
             cpu = cpu_oracle_sample()
@@ -448,6 +454,7 @@ def run_ours(args):
                               "tflops": 2.0 * float(n) ** 3 / (ref_avg * 1e-3) / 1e12 if ref_work else None},
             "fp64_path": fp64,
             "accuracy_vs_oracle": check,
+            "gapped_dynamics": dyn,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
@@ -462,6 +469,61 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+def gapped_dynamics(ctx, args, stream, steps: int = 400, warmup: int = 5) -> dict:
+    """XL-BOMD at T_e = 0 on a system whose SCF converges: 682 H2O-like
+    molecules (2046 atoms, n = 4092) of the gapped recipe at 0.1 g/cc, the
+    paper's kappa = kappa0 / 2, the headline's SP2 options.  Device-timed
+    steps/s over `steps` steps, SP2 projections per step, and the sigma and
+    drift of E_tot (Table II definitions) over the same steps."""
+    import numpy as np
+    import torch
+    from paper_1203_6836_gb300 import tbmd
+    from paper_1203_6836_gb300.device import DeviceSystem, MDState, sp2_opts, xl_params, report_to_dict
+    from workloads import XLParams, gapped_params, gapped_vapour, thermal_velocities
+    from oracle import md as omd
+    P = gapped_params()
+    TP = tbmd.tb_params.from_model(P)
+    XL = XLParams()
+    s = gapped_vapour(682, seed=0)
+    M = s.masses(P)
+    ds = DeviceSystem(s.R, s.types, s.box)
+    opts = sp2_opts(args.precision, max_iter=100, tol=1e-10, refine=args.refine)
+    st = MDState(ds, thermal_velocities(M, 300.0, seed=100), M, s.n_occ(P), XL.K, opts)
+    xp = xl_params(XL.dt, XL.kappa, XL.alpha, XL.c)
+    scf_it = tbmd.xlbomd_init(ctx, TP, st.st, xp, opts, 1e-6, 200)
+    E0 = st.energies[0].item()
+    for _ in range(warmup):
+        tbmd.xlbomd_step(ctx, TP, st.st, xp, opts)
+    Ebuf = torch.empty(steps, st.energies.numel(), dtype=torch.float64, device="cuda")
+    reps = torch.empty(steps, st.report.numel(), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        tbmd.xlbomd_step(ctx, TP, st.st, xp, opts)
+        Ebuf[k].copy_(st.energies, non_blocking=True)
+        reps[k].copy_(st.report, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    E = Ebuf.cpu().numpy()
+    rr = [report_to_dict(reps[k]) for k in range(steps)]
+    sigma, drift = omd.energy_drift(list(E[:, 0]), XL.dt, s.natoms)
+    out = {"system": f"gapped recipe (t_hop {P.t_hop} eV, r_decay {P.r_decay} A, U {P.hubbard_u} eV, "
+                     f"pair_a {P.pair_a} eV), {s.natoms} atoms (682 H2O-like molecules), n={ds.norb}, "
+                     f"0.1 g/cc, seed 0, T_e = 0, kappa = kappa0/2, dt {XL.dt} fs",
+           "scf_init_iters": scf_it, "scf_tol_e": 1e-6, "steps": steps, "warmup": warmup,
+           "steps_per_s": 1e3 / ms, "ms_per_step": ms,
+           "sp2_projections_per_step": sum(r["iters"] + r["refine_iters"] for r in rr) / steps,
+           "sp2_status_nonzero": sum(1 for r in rr if r["status"] != 0),
+           "E_tot_sigma_eV": sigma, "E_tot_drift_eV_per_atom_ps": drift,
+           "E_tot_first_eV": E0, "max_abs_n_minus_q_e": float(E[:, 6].max()),
+           "timing": "CUDA events around the steps, energies and reports copied on the device each step"}
+    del st, ds
+    torch.cuda.empty_cache()
+    return out
+
 
 # ---------------------------------------------------------------- other workloads (1 GPU)
 
@@ -680,36 +742,35 @@ def run_sparse(args):
     md_ms = e0.elapsed_time(e1) / md_steps
     del st
     torch.cuda.empty_cache()
-    # the drift study runs on water-like vapour (125 H2O-like molecules, 0.1 g/cc,
-    # Morton order): the 1.0 g/cc random recipe has no T_e = 0 SCF fixed point
-    # and its XL-BOMD diverges on every path; the vapour keeps a gap (0.1-0.7 eV)
-    # at this size with kappa = 0.06 kappa0, while at 683 molecules the T_e = 0
-    # gap closes and both paths diverge
-    import dataclasses
-    from workloads import molecular_liquid
-    XLv = dataclasses.replace(XL, kappa_scale=0.06)
-    xp = xl_params(XLv.dt, XLv.kappa, XLv.alpha, XLv.c)
-    sub = molecular_liquid(125, 0.1, seed=0, morton=True)
-    Ms = sub.masses(P)
+    # the drift study runs on the 1/8-size subsystem of the gapped recipe: 682
+    # H2O-like molecules (2046 atoms) at 0.1 g/cc in Morton order, T_e = 0,
+    # kappa = kappa0 / 2 (the 1.0 g/cc random recipe has no T_e = 0 SCF fixed
+    # point and its XL-BOMD diverges on every path)
+    from workloads import gapped_params, gapped_vapour
+    Pg = gapped_params()
+    TPg = tbmd.tb_params.from_model(Pg)
+    sub = gapped_vapour(682, seed=0, morton=True)
+    Ms = sub.masses(Pg)
     v0 = thermal_velocities(Ms, 300.0, seed=100)
+    drift_steps = 200
     drift = {}
+    Es = {}
     for label, o in (("block_sparse_tau1e-5", sp2_opts(args.precision, max_iter=60, tau=1e-5)),
                      ("dense_refined", sp2_opts(args.precision, max_iter=100, tol=1e-10, refine=2))):
         dsub = DeviceSystem(sub.R, sub.types, sub.box)
-        st = MDState(dsub, v0, Ms, sub.n_occ(P), XLv.K, o)
-        tbmd.xlbomd_init(ctx, TP, st.st, xp, o, 1e-8, 200)
-        E = []
-        for k in range(51):
-            if k:
-                tbmd.xlbomd_step(ctx, TP, st.st, xp, o)
-            E.append(st.energies[0].item())
-        sig, slope = omd.energy_drift(E, XLv.dt, sub.natoms)
-        drift[label] = {"sigma_eV": sig, "drift_eV_per_atom_ps": slope, "E_tot": E}
+        st = MDState(dsub, v0, Ms, sub.n_occ(Pg), XL.K, o)
+        it = tbmd.xlbomd_init(ctx, TPg, st.st, xp, o, 1e-6, 200)
+        Eb = torch.empty(drift_steps + 1, dtype=torch.float64, device="cuda")
+        Eb[0].copy_(st.energies[0])
+        for k in range(drift_steps):
+            tbmd.xlbomd_step(ctx, TPg, st.st, xp, o)
+            Eb[k + 1].copy_(st.energies[0], non_blocking=True)
+        E = Eb.cpu().numpy()
+        sig, slope = omd.energy_drift(list(E), XL.dt, sub.natoms)
+        drift[label] = {"sigma_eV": sig, "drift_eV_per_atom_ps": slope, "scf_init_iters": it}
+        Es[label] = E
         del st
-    dE = float(np.max(np.abs(np.array(drift["block_sparse_tau1e-5"]["E_tot"]) -
-                             np.array(drift["dense_refined"]["E_tot"]))))
-    for v in drift.values():
-        del v["E_tot"]
+    dE = float(np.max(np.abs(Es["block_sparse_tau1e-5"] - Es["dense_refined"])))
     line = _common(args, "thresholded block-sparse SP2: block-product TFLOP/s", value, "TFLOP/s",
                    total / args.steps, f"{args.precision}+f64",
                    f"{s.natoms} atoms, n={n}, 1.0 g/cc, Morton order, seed 0; SP2 with "
@@ -732,9 +793,10 @@ def run_sparse(args):
                                  "sample": f"2 thresholded FP64 projections (NumPy, dense storage) of the "
                                            f"n={no} 1/8-size Morton system, {dt:.1f} s"},
                    xlbomd={"steps_per_s": 1e3 / md_ms, "ms_per_step": md_ms, "system": f"{s.natoms} atoms, tau=1e-5"},
-                   drift_50_steps={"system": f"water-like vapour, {sub.natoms} atoms (125 H2O-like molecules), "
-                                             "0.1 g/cc, Morton order, T_e = 0, kappa 0.06 kappa0", **drift,
-                                   "max_abs_dE_tot_eV": dE},
+                   drift_200_steps={"system": f"gapped recipe, {sub.natoms} atoms (682 H2O-like molecules, "
+                                              "the 1/8-size subsystem), 0.1 g/cc, Morton order, T_e = 0, "
+                                              "kappa = kappa0/2", **drift,
+                                    "max_abs_dE_tot_eV": dE},
                    e2e={"value": 2.0 * 128 ** 3 * r_e2e["block_products"] / e2e_s / 1e12, "unit": "TFLOP/s",
                         "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8},
                    gpu_launches=args.steps * (8 * 61 + 8), clocks=clocks)

@@ -151,6 +151,7 @@ struct SP2State {
   unsigned long long branch[2];
   unsigned long long rbranch;
   unsigned long long block_products;  // block-sparse path: executed 128^3 block products
+  int kc[2];                     // main-phase projection index inside a while graph node
 };
 
 // Parameters of a purification step shared by the FP64 and tensor-core kernels.
@@ -169,7 +170,28 @@ struct SP2StepArgs {
   const double* parts_in;   // [nparts_in * 2]
   double* parts_out;        // [ntiles * 2]
   unsigned long long wait_ns;  // pipeline wait limit (0: the 2 s default)
+  // Device-counted index (kc != nullptr): the launch reads k = kc[kpar] and
+  // writes kc[kpar ^ 1] = k + 1 for the next launch, so a captured run of
+  // launches of alternating parity can be replayed as the body of a while
+  // graph node; with cond the launch clears the node's condition once the
+  // phase has stopped, failed or reached its cap.
+  int* kc;
+  int kpar;
+  int cond;
+  cudaGraphConditionalHandle loop;
 };
+
+// Projection index of a step launch (see SP2StepArgs::kc); `over` is the
+// phase's done-or-error flag as read at kernel entry.
+__device__ __forceinline__ int sp2_step_index(const SP2StepArgs& a, int over) {
+  if (!a.kc) return a.k;
+  const int k = a.kc[a.kpar];
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    a.kc[a.kpar ^ 1] = k + 1;
+    if (a.cond && (over || k >= a.max_iter)) cudaGraphSetConditional(a.loop, 0);
+  }
+  return k;
+}
 
 // Tensor-core purification step (gemm_tc.cu).  X_in / X_out are FP32 masters
 // (ld x ld); hi/lo operand arrays of the input are read through the tensor

@@ -122,7 +122,7 @@ __device__ __forceinline__ void unit_tile(const Units& w, int u, int* t, int* ha
 
 template <int P>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_sp2_step_tc(SP2StepArgs a, const __grid_constant__ CUtensorMap mh,
+    k_sp2_step_tc(const SP2StepArgs a_in, const __grid_constant__ CUtensorMap mh,
                   const __grid_constant__ CUtensorMap ml, const float* __restrict__ Xin,
                   float* __restrict__ Xout, void* __restrict__ ohi, void* __restrict__ olo) {
   using C = Prec<P>;
@@ -135,7 +135,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ volatile int s_abort;
   __shared__ double s_red[4][3];
 
-  SP2State* st = a.st;
+  SP2State* st = a_in.st;
+  SP2StepArgs a = a_in;
+  a.k = sp2_step_index(a_in, st->done || st->err);
   if (st->done || st->err) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -170,6 +172,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       st->iters = a.k;
       st->capped = s_dec[2];
       st->done = 1;
+      if (a.cond) cudaGraphSetConditional(a.loop, 0);
     } else if (br) {
       st->branch[a.k >> 6] |= 1ull << (a.k & 63);
     }

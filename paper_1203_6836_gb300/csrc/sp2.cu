@@ -6,11 +6,13 @@
 // Tr X and Tr X^2 = ||X||_F^2 (look-ahead rule: the projection whose trace
 // lands closer to N_occ); stop when Tr X - Tr X^2 <= tol.
 //
-// Device-side control: the host enqueues max_iter + 1 step kernels; kernel k
-// first reduces, in a fixed order, the trace partials written by the
-// epilogue of kernel k-1, takes the stop/branch decision (identical in every
-// CTA) and either returns at once or computes X_{k+1}.  No host
-// synchronisation happens inside dm_sp2.
+// Device-side control: step kernel k first reduces, in a fixed order, the
+// trace partials written by the epilogue of kernel k-1, takes the
+// stop/branch decision (identical in every CTA) and either returns at once
+// or computes X_{k+1}.  Launched eagerly, the host enqueues max_iter + 1 step
+// kernels; captured into a CUDA graph, the projections after the first are
+// a while node that stops with the decision.  No host synchronisation
+// happens inside dm_sp2.
 //
 // Precision paths: TB_PREC_FP64 runs every projection as an FP64 GEMM (16 x 16
 // output tiles for ld <= 512, 64 x 64 above); the tensor-core paths
@@ -29,6 +31,7 @@ namespace {
 constexpr int kF64Tile = 64;     // FP64 GEMM output tile (padding unit of the FP64 path)
 constexpr int kF64K = 16;        // FP64 GEMM k-step
 constexpr int kInitTile = 64;    // X0 / conversion tile
+constexpr int kLoopUnroll = 16;  // projections per pass of the graph's while node (even)
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
@@ -204,15 +207,17 @@ __global__ void __launch_bounds__(256) k_init_x(const double* __restrict__ H, in
 // memory.  X is symmetric, so B = X is read row-major like A.
 // T x T output tile per CTA, 16 x 16 threads, (T/16)^2 outputs per thread.
 template <int T>
-__global__ void __launch_bounds__(256) k_sp2_step_f64(SP2StepArgs a, const double* __restrict__ X,
+__global__ void __launch_bounds__(256) k_sp2_step_f64(const SP2StepArgs a_in, const double* __restrict__ X,
                                                       double* __restrict__ Y) {
   constexpr int R = T / 16;
   __shared__ double As[kF64K][T + 1];
   __shared__ double Bs[kF64K][T + 1];
   __shared__ double s_t[3];
   __shared__ int s_dec[3];
-  SP2State* st = a.st;
-  const int done = a.phase == 0 ? st->done : st->rdone;
+  SP2State* st = a_in.st;
+  const int done = a_in.phase == 0 ? st->done : st->rdone;
+  SP2StepArgs a = a_in;
+  a.k = sp2_step_index(a_in, done || st->err);
   if (done || st->err) return;
   if (threadIdx.x < 32) {
     double t1, t2;
@@ -251,6 +256,7 @@ __global__ void __launch_bounds__(256) k_sp2_step_f64(SP2StepArgs a, const doubl
         st->iters = a.k;
         st->capped = s_dec[2];
         st->done = 1;
+        if (a.cond) cudaGraphSetConditional(a.loop, 0);
       } else if (br) {
         st->branch[a.k >> 6] |= 1ull << (a.k & 63);
       }
@@ -404,6 +410,58 @@ int sp2_launch_bounds(tb_ctx* ctx, const double* H, int n, double* bparts, cudaS
   return TB_OK;
 }
 
+// The main phase's projections k = 0..max_iter.  Projection 0 (whose input
+// partials come from the X0 kernel) is launched on `s` and seeds the device
+// counter st->kc.  When `s` is being captured into a CUDA graph, the rest is
+// one while node whose body is kLoopUnroll launches of alternating parity
+// (1, 0, 1, ...): the launches read their index from the counter and clear
+// the condition once the phase stops, so a replay runs the projections it
+// needs plus at most kLoopUnroll - 1 launches that return at once.  (Each
+// pass of a while node costs a few microseconds, more than an empty launch,
+// so the body holds several projections.)  Otherwise the host unrolls
+// k = 1..max_iter; the launches after the stop return at once.
+// `launch(args, k, stream)` enqueues one projection whose buffers are those
+// of parity k & 1.
+template <class F>
+int main_phase(tb_ctx* ctx, SP2StepArgs& a, int np_first, int np, double* const slot[2], cudaStream_t s,
+               F&& launch) {
+  a.k = 0;
+  a.kc = a.st->kc;
+  a.kpar = 0;
+  a.cond = 0;
+  a.nparts_in = np_first;
+  a.parts_in = slot[0];
+  a.parts_out = slot[1];
+  tb_prof_mark(ctx, 0, 0, s);
+  int rc = launch(a, 0, s);
+  if (rc) return rc;
+  tb_prof_mark(ctx, 0, 1, s);
+  a.nparts_in = np;
+  DevLoop loop;
+  if ((rc = tb_loop_begin(ctx, s, &loop))) return rc;
+  if (loop.graph) {
+    a.cond = 1;
+    a.loop = loop.handle;
+    for (int u = 0; u < kLoopUnroll && !rc; ++u) {
+      const int p = (u + 1) & 1;
+      a.kpar = p;
+      a.parts_in = slot[p];
+      a.parts_out = slot[p ^ 1];
+      rc = launch(a, p, loop.body_stream);
+    }
+    return tb_loop_end(ctx, &loop, rc);
+  }
+  a.kc = nullptr;
+  for (int k = 1; k <= a.max_iter; ++k) {
+    a.k = k;
+    a.parts_in = slot[k & 1];
+    a.parts_out = slot[(k + 1) & 1];
+    if ((rc = launch(a, k, s))) return rc;
+    tb_prof_mark(ctx, 0, k + 1, s);
+  }
+  return TB_OK;
+}
+
 extern "C" int dm_sp2_workspace_size(int n, const tb_sp2_opts* o, size_t* bytes) {
   if (!o || !bytes || n < 1) return TB_ERR_ARG;
   if (o->precision < TB_PREC_FP64 || o->precision > TB_PREC_BF16X3) return TB_ERR_ARG;
@@ -490,16 +548,13 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
     a.max_iter = o->max_iter;
     a.phase = 0;
     const dim3 g(ld / f64_tile(ld), ld / f64_tile(ld));
-    tb_prof_mark(ctx, 0, 0, s);
-    for (int k = 0; k <= o->max_iter; ++k) {
-      a.k = k;
-      a.nparts_in = k == 0 ? np_init : (int)(g.x * g.y);
-      a.parts_in = slot[k & 1];
-      a.parts_out = slot[(k + 1) & 1];
-      launch_f64(g, a, (k & 1) ? F1 : F0, (k & 1) ? F0 : F1, s);
+    const int npf = (int)(g.x * g.y);
+    const int rc = main_phase(ctx, a, np_init, npf, slot, s, [&](const SP2StepArgs& b, int k, cudaStream_t q) {
+      launch_f64(g, b, (k & 1) ? F1 : F0, (k & 1) ? F0 : F1, q);
       TB_LAUNCH_CHECK(ctx);
-      tb_prof_mark(ctx, 0, k + 1, s);
-    }
+      return TB_OK;
+    });
+    if (rc) return rc;
     const int fb = std::min(1184, (int)(((size_t)n * n + 255) / 256));
     k_finalize<<<fb, 256, 0, s>>>(st, n, ld, 0, F0, F1, nullptr, nullptr, D, nocc, rep);
     TB_LAUNCH_CHECK(ctx);
@@ -537,17 +592,15 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
     if (rc) return rc;
   }
   const int ntc = sp2_tc_num_parts(ctx, ld);
-  tb_prof_mark(ctx, 0, 0, s);
-  for (int k = 0; k <= o->max_iter; ++k) {
-    a.k = k;
-    a.nparts_in = k == 0 ? np_init : ntc;
-    a.parts_in = slot[k & 1];
-    a.parts_out = slot[(k + 1) & 1];
-    const int i = k & 1, j = (k + 1) & 1;
-    int rc = sp2_tc_step(ctx, o->precision, a, &mh[i], &ml[i], M[i], M[j], Hi[j], Lo[j], s);
+  {
+    const int rc = main_phase(ctx, a, np_init, ntc, slot, s, [&](const SP2StepArgs& b, int k, cudaStream_t q) {
+      const int i = k & 1, j = (k + 1) & 1;
+      return sp2_tc_step(ctx, o->precision, b, &mh[i], &ml[i], M[i], M[j], Hi[j], Lo[j], q);
+    });
     if (rc) return rc;
-    tb_prof_mark(ctx, 0, k + 1, s);
   }
+  a.kc = nullptr;
+  a.cond = 0;
   const int fb = std::min(1184, (int)(((size_t)n * n + 255) / 256));
   if (refine == 0) {
     k_finalize<<<fb, 256, 0, s>>>(st, n, ld, 2, nullptr, nullptr, M[0], M[1], D, nocc, rep);

@@ -188,3 +188,60 @@ def test_emulated_fp64_refinement_matches_fma_refinement(ctx, natoms):
     assert abs(re_["trace"] - nocc) < 1e-8
     assert abs(re_["idem_trace"]) < 1e-8
     assert _err(De, ref.D) < 1e-6
+
+
+@pytest.mark.parametrize("prec,natoms", [("fp64", 24), ("fp64", 150), ("tf32x3", 300)])
+def test_graph_captured_sp2_replays_like_eager_calls(ctx, prec, natoms):
+    """dm_sp2 captured into a CUDA graph runs its projections after the first
+    as a while node that stops with the device-side decision.  Replays on
+    Hamiltonians that need different numbers of projections give the same
+    D and report, bit for bit, as eager calls on the same workspace; the
+    number of projections varies with H, so the loop really stops on the
+    device and not at a fixed unroll."""
+    s = water_system(natoms, density=1.0, seed=3) if natoms != 24 else water_24_atoms()
+    h = tb.build_h(s.R, s.types, s.box, P)
+    g0 = tb.build_gamma(s.R, s.box, P)
+    nocc = s.n_occ(P)
+    rng = np.random.default_rng(5)
+    Hs = []
+    for amp in (0.0, 0.3):
+        na = rng.normal(0, amp, s.natoms) if amp else np.zeros(s.natoms)
+        na -= na.mean()
+        Hs.append(tb.build_H(h, g0, s.types, na))
+    n = Hs[0].shape[0]
+    # a spectrum with a much smaller relative gap needs more projections
+    Hs.append(random_gapped_matrix(n, int(nocc), gap=0.05, width=20.0, seed=11)[0])
+    opts = sp2_opts(prec, tol=1e-11 if prec == "fp64" else 1e-10, refine=2)
+    eager = []
+    solver = DensitySolver(ctx, n, opts)
+    for H in Hs:
+        Ht = torch.as_tensor(H, device="cuda")
+        D = torch.empty_like(Ht)
+        solver(Ht, nocc, D)
+        torch.cuda.synchronize()
+        eager.append((D.clone(), report_to_dict(solver.report)))
+    gs = DensitySolver(ctx, n, opts)
+    Hin = torch.empty(n, n, dtype=torch.float64, device="cuda")
+    Dout = torch.empty_like(Hin)
+    Hin.copy_(torch.as_tensor(Hs[0], device="cuda"))
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side, capture_error_mode="thread_local"):
+            gs(Hin, nocc, Dout, stream=side)
+    torch.cuda.synchronize()
+    iters = []
+    for H, (De, re_) in zip(Hs, eager):
+        Hin.copy_(torch.as_tensor(H, device="cuda"))
+        Dout.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        rg = report_to_dict(gs.report)
+        iters.append(rg["iters"])
+        assert rg == re_
+        assert torch.equal(Dout, De)
+        assert rg["status"] == tbmd.TB_OK
+    print(f"PARITY sp2 graph {prec} n={n}: projections per replay {iters}, bitwise equal to eager")
+    assert len(set(iters)) > 1
+    del g

@@ -357,3 +357,27 @@ def molecular_water(m: int, box: float, seed: int = 0, bond: float = 0.96,
     R = np.array(Os + Hs)
     types = np.array([TYPE_O] * len(Os) + [TYPE_H] * len(Hs), dtype=np.int32)
     return WaterSystem(R=R, types=types, box=float(box), seed=seed)
+
+
+def gapped_params() -> ModelParams:
+    """Constants of the gapped variant of the recipe, for T_e = 0 dynamics.
+
+    With the default constants an isolated H2O-like molecule has a gap of
+    only ~0.75 eV (hopping t(0.96 A) = 0.44 eV against U = 10 eV), and in any
+    box of more than a few molecules the neighbours' Coulomb fields close it,
+    so the T_e = 0 SCF has no fixed point and XL-BOMD diverges.  Here the
+    O-H hopping is stronger and shorter ranged (t_hop = 20 eV, r_decay =
+    0.4 A: 1.8 eV at the bond, 0.17 eV at 1.9 A, 0.02 eV at 2.8 A) and
+    U = 6 eV; the isolated molecule's gap is 3.8 eV.  pair_a = 65.75 eV is
+    the prefactor at which that molecule's O-H bond force vanishes at
+    r_OH = 0.96 A (pair_rho = 0.3 A as in the default recipe)."""
+    return dataclasses.replace(ModelParams(), t_hop=20.0, r_decay=0.4, hubbard_u=6.0, pair_a=65.75)
+
+
+def gapped_vapour(n_mol: int = 682, seed: int = 0, morton: bool = False) -> WaterSystem:
+    """n_mol H2O-like molecules at 0.1 g/cc (molecular_liquid), the system
+    the gapped recipe (gapped_params) keeps gapped at T_e = 0: 682 molecules
+    give 2046 atoms (n = 4092 orbitals) in a 58.85 A cube, O atoms ~6.5 A
+    apart; 8 molecules give the 24-atom system."""
+    return molecular_liquid(n_mol, 0.1, seed=seed, morton=morton)
+
