@@ -43,10 +43,11 @@ WORKLOAD = ("water-like orthogonal SCC-TB, 2048 atoms (682 O + 1366 H), n=4094 o
             "1.0 g/cc periodic cube, seed 0; one XL-BOMD (Fast-QMMD) step per step")
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_sp2_step_tc<tf32x3> launch on
-# the 2048-atom system (n = 4094), measured with ncu on the current kernel; None until
-# measured on it
-TRAFFIC_TC_N4094 = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dense tf32x3
+# projection on the 2048-atom system (n = 4094), mean of three launches of one ncu
+# capture of the current kernel (the CTA-pair form k_sp2_step_tc2, which dm_sp2 runs at
+# this size on GB300)
+TRAFFIC_TC2_N4094 = 390.7e6
 
 
 def parse():
@@ -321,6 +322,7 @@ def run_ours(args):
     last = reps[-1]
 
     # ---- dominant kernel: tensor-core projection of the last timed step
+    form, ctas = tbmd.tb_ctx_sp2_form_of(ctx, n)
     peaks = measured_peaks()
     tf = args.precision.startswith("tf32")
     ratio = 0.5 if tf else 1.0  # nominal tf32 : bf16 dense tensor rate
@@ -329,10 +331,10 @@ def run_ours(args):
     avg_ms = sum(work) / len(work) if work else float("nan")
     achieved = 2.0 * float(n) ** 3 / (avg_ms * 1e-3) / 1e12
     mmas = 3 if args.precision.endswith("x3") else 1
-    # the kernel computes the nt(nt+1)/2 upper-triangle 128 x 128 tiles of the
-    # padded ld x ld product and mirrors them
+    # the kernel computes the nt(nt+1)/2 upper-triangle tiles (128 x 128, or
+    # 256 x 256 for CTA pairs) of the padded ld x ld product and mirrors them
     ld = (n + 127) // 128 * 128
-    nt = ld // 128
+    nt = ld // (256 if form == tbmd.TB_SP2_FORM_PAIRS else 128)
     tri_frac = (nt + 1) / (2 * nt)
     ref_work = ref_ms[:last["refine_iters"]]
     ref_avg = sum(ref_work) / len(ref_work) if ref_work else float("nan")
@@ -442,8 +444,11 @@ def run_ours(args):
                          "frac": achieved / peak,
                          # DRAM bytes per launch (read + write) of this kernel on this workload
                          # from an ncu capture of the same command (tf32x3, n = 4094)
-                         "traffic": TRAFFIC_TC_N4094 if (args.precision == "tf32x3" and n == 4094) else None,
-                         "kernel": f"k_sp2_step_tc<{args.precision}>",
+                         "traffic": TRAFFIC_TC2_N4094 if (args.precision == "tf32x3" and n == 4094
+                                                          and form == tbmd.TB_SP2_FORM_PAIRS) else None,
+                         "kernel": (f"k_sp2_step_tc2<{args.precision}> (CTA pairs, cta_group::2, "
+                                    f"{ctas // 2} clusters)" if form == tbmd.TB_SP2_FORM_PAIRS
+                                    else f"k_sp2_step_tc<{args.precision}> ({ctas} CTAs)"),
                          "peak_source": f"{peaks['source']} bf16_tflops_sustained x {ratio} ({'tf32' if tf else 'bf16'})",
                          "mma_per_product": mmas, "upper_triangle_tiles": tri_frac,
                          "mma_frac": achieved * mmas * tri_frac * (ld / n) ** 3 / peak,

@@ -182,6 +182,28 @@ int tb_ctx_sp2_launch_times(tb_ctx* ctx, int phase, float* ms, int cap, int* cou
 int tb_ctx_set_grid_limit(tb_ctx* ctx, int max_ctas);
 int tb_ctx_set_wait_limit(tb_ctx* ctx, unsigned long long ns);
 
+/* Kernel form of dm_sp2's dense tensor-core projections (a4).  When the
+ * padded size ld is a multiple of 256, a projection can run on CTA pairs:
+ * clusters of two CTAs computing 256 x 256 tiles with one
+ * tcgen05.mma.cta_group::2, which halves the operand bytes each SM loads per
+ * flop; otherwise (and for every other tensor-core product) one CTA computes
+ * a 128 x 128 tile.  TB_SP2_FORM_AUTO (the default) takes the pair form
+ * where its tile schedule is predicted to finish first (on GB300: ld = 4096
+ * and up), TB_SP2_FORM_SINGLE never, TB_SP2_FORM_PAIRS wherever ld allows.
+ * Both forms compute the same products in the same order; results agree to
+ * the order of the FP64 trace sums.  A grid limit (tb_ctx_set_grid_limit)
+ * caps the pair form at max_ctas / 2 clusters.  TB_ERR_ARG for an unknown
+ * form; applies to calls enqueued after it. */
+#define TB_SP2_FORM_AUTO 0
+#define TB_SP2_FORM_SINGLE 1
+#define TB_SP2_FORM_PAIRS 2
+int tb_ctx_set_sp2_form(tb_ctx* ctx, int form);
+/* The form (TB_SP2_FORM_SINGLE or TB_SP2_FORM_PAIRS) and the CTAs of the
+ * persistent grid of the dense tensor-core projection dm_sp2 launches for
+ * size n under the context's current settings (host only; queries the
+ * device's cluster occupancy once).  TB_ERR_ARG for n < 1 or a null pointer. */
+int tb_ctx_sp2_form_of(tb_ctx* ctx, int n, int* form, int* ctas);
+
 /* ----------------------------------------------------------- a1: H[n] build */
 
 /* H[n] = h(R) + diag(sum_l gamma_il n_l) over every orbital of atom i

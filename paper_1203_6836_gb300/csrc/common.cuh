@@ -33,6 +33,10 @@ struct tb_ctx {
   int grid_limit;
   // time limit (ns) of the pipeline waits of the tensor-core kernels
   unsigned long long wait_ns;
+  // kernel form of the dense tensor-core projection (TB_SP2_FORM_*) and the
+  // co-resident clusters of its CTA-pair form (-1: not queried yet)
+  int sp2_form;
+  int pair_clusters;
 };
 
 // CTAs of a persistent grid over `units` work units: one per SM, at most
@@ -202,8 +206,12 @@ int sp2_tc_step(tb_ctx* ctx, int precision, const SP2StepArgs& a,
                 const float* X_in, float* X_out, void* out_hi, void* out_lo,
                 cudaStream_t stream);
 int sp2_tc_num_tiles(int ld);
-// Partials (CTAs) of one persistent tensor-core projection (<= sp2_tc_num_tiles).
+// CTAs of the persistent single-CTA tensor-core grids (<= sp2_tc_num_tiles).
 int sp2_tc_num_parts(const tb_ctx* ctx, int ld);
+// Clusters of the CTA-pair projection kernel dm_sp2 runs at this ld (0: the
+// single-CTA form), and the trace partials (CTAs) of one projection.
+int sp2_tc_pairs(tb_ctx* ctx, int ld);
+int sp2_tc_step_parts(tb_ctx* ctx, int ld);
 int sp2_tc_tile();
 size_t sp2_tc_operand_bytes(int precision);  // bytes per element of one operand array
 

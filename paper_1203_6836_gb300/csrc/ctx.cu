@@ -50,6 +50,8 @@ extern "C" int tb_ctx_create(tb_ctx** out) {
   }
   ctx->sm_count = prop.multiProcessorCount;
   ctx->grid_limit = 0;
+  ctx->sp2_form = TB_SP2_FORM_AUTO;
+  ctx->pair_clusters = -1;
   ctx->wait_ns = 2000000000ull;
   ctx->cc_major = prop.major;
   ctx->cc_minor = prop.minor;
@@ -130,6 +132,13 @@ extern "C" int tb_ctx_set_grid_limit(tb_ctx* ctx, int max_ctas) {
   if (!ctx) return TB_ERR_ARG;
   if (max_ctas < 0) return tb_fail(ctx, TB_ERR_ARG, "grid limit %d < 0", max_ctas);
   ctx->grid_limit = max_ctas;
+  return TB_OK;
+}
+
+extern "C" int tb_ctx_set_sp2_form(tb_ctx* ctx, int form) {
+  if (!ctx) return TB_ERR_ARG;
+  if (form < TB_SP2_FORM_AUTO || form > TB_SP2_FORM_PAIRS) return tb_fail(ctx, TB_ERR_ARG, "sp2 form %d", form);
+  ctx->sp2_form = form;
   return TB_OK;
 }
 

@@ -591,7 +591,7 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
     int rc = sp2_tc_step(ctx, o->precision, c, nullptr, nullptr, M[0], M[0], Hi[0], Lo[0], s);
     if (rc) return rc;
   }
-  const int ntc = sp2_tc_num_parts(ctx, ld);
+  const int ntc = sp2_tc_step_parts(ctx, ld);
   {
     const int rc = main_phase(ctx, a, np_init, ntc, slot, s, [&](const SP2StepArgs& b, int k, cudaStream_t q) {
       const int i = k & 1, j = (k + 1) & 1;

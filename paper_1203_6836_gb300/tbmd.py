@@ -25,6 +25,9 @@ TB_ERR_OOM = -4
 TB_ERR_TIMEOUT = -5
 TB_ERR_CUDA = -6
 TB_ERR_UNSUPPORTED = -7
+TB_SP2_FORM_AUTO = 0
+TB_SP2_FORM_SINGLE = 1
+TB_SP2_FORM_PAIRS = 2
 
 TB_TYPE_O = 0
 TB_TYPE_H = 1
@@ -130,6 +133,8 @@ _SIGS = {
                                                ctypes.POINTER(ctypes.c_int)]),
     "tb_ctx_set_grid_limit": (ctypes.c_int, [_P, ctypes.c_int]),
     "tb_ctx_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_ulonglong]),
+    "tb_ctx_set_sp2_form": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tb_ctx_sp2_form_of": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "tb_build_H": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P, _P, _P, _P]),
     "dm_sp2_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(tb_sp2_opts),
                                              ctypes.POINTER(ctypes.c_size_t)]),
@@ -265,6 +270,17 @@ def tb_ctx_set_grid_limit(ctx: Context, max_ctas: int) -> int:
 
 def tb_ctx_set_wait_limit(ctx: Context, ns: int) -> int:
     return ctx.check(lib().tb_ctx_set_wait_limit(ctx.handle, int(ns)), "tb_ctx_set_wait_limit")
+
+
+def tb_ctx_set_sp2_form(ctx: Context, form: int) -> int:
+    return ctx.check(lib().tb_ctx_set_sp2_form(ctx.handle, int(form)), "tb_ctx_set_sp2_form")
+
+
+def tb_ctx_sp2_form_of(ctx: Context, n: int) -> tuple[int, int]:
+    """(form, CTAs) of the dense tensor-core projection dm_sp2 launches for size n."""
+    f, c = ctypes.c_int(), ctypes.c_int()
+    ctx.check(lib().tb_ctx_sp2_form_of(ctx.handle, int(n), ctypes.byref(f), ctypes.byref(c)), "tb_ctx_sp2_form_of")
+    return f.value, c.value
 
 
 def tb_build_H(ctx: Context, p: tb_params, sys: tb_system, R, n_aux, H, gamma, stream=None) -> int:
