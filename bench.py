@@ -453,8 +453,10 @@ def run_ours(args):
                          "mma_per_product": mmas, "upper_triangle_tiles": tri_frac,
                          "mma_frac": achieved * mmas * tri_frac * (ld / n) ** 3 / peak,
                          "avg_launch_ms": avg_ms},
-            "refine_kernel": {"kind": "emulated FP64 (22 exact bf16 slice products)" if opts.refine_mode == 0
-                              else "FP64 FMA",
+            "refine_kernel": {"kind": (("emulated FP64 (22 exact bf16 slice products, k_oz_split + "
+                                        + ("k_sp2_step_oz2 on CTA pairs)" if ld % 256 == 0 else "k_sp2_step_oz)"))
+                                       if opts.refine_mode == 0 else "FP64 FMA"),
+                              "interval": "split + product, CUDA events between the refinement launches",
                               "avg_launch_ms": ref_avg,
                               "tflops": 2.0 * float(n) ** 3 / (ref_avg * 1e-3) / 1e12 if ref_work else None},
             "fp64_path": fp64,

@@ -37,6 +37,7 @@ struct tb_ctx {
   // co-resident clusters of its CTA-pair form (-1: not queried yet)
   int sp2_form;
   int pair_clusters;
+  int oz_pair_clusters;  // the same for the emulated-FP64 product's pair form
 };
 
 // CTAs of a persistent grid over `units` work units: one per SM, at most
@@ -220,8 +221,9 @@ size_t sp2_tc_operand_bytes(int precision);  // bytes per element of one operand
 int sp2_oz_step(tb_ctx* ctx, const SP2StepArgs& a, const double* Xin, double* Xout, void* slices, int* exps,
                 cudaStream_t s);
 int sp2_oz_max_ld();
-// Partials (CTAs, one per upper-triangle tile) of one emulated-FP64 projection.
-int sp2_oz_num_parts(int ld);
+// Partials (CTAs) of one emulated-FP64 projection: one per upper-triangle
+// tile, or the persistent grid of the CTA-pair form.
+int sp2_oz_num_parts(tb_ctx* ctx, int ld);
 size_t sp2_oz_slice_bytes(int ld);
 
 // Generic tensor-core product out = alpha A B + beta E + gamma I of symmetric,
@@ -254,10 +256,12 @@ int dm_sp2_bsr(tb_ctx* ctx, const double* H, int n, double nocc, const tb_sp2_op
                size_t ws_bytes, tb_sp2_report* rep, cudaStream_t s);
 
 // Encode a 2D row-major tensor map over an ld x ld operand array (gemm_tc.cu):
-// 128-row boxes of row_bytes (64 or 128) bytes, swizzled to the same width.
-// The projection and Fermi-product kernels read 64-byte rows
-// (sp2_tc_row_bytes()); the emulated-FP64 product reads 128-byte rows.
-int sp2_tc_make_map(tb_ctx* ctx, int precision, const void* base, int ld, CUtensorMap* map, int row_bytes = 128);
+// boxes of box_rows (64 or 128) rows of row_bytes (64 or 128) bytes, swizzled
+// to the row width.  The projection and Fermi-product kernels read 128-row
+// boxes of sp2_tc_row_bytes(); the emulated-FP64 product reads 128-byte rows,
+// in 64-row boxes for the B operand of its CTA-pair form.
+int sp2_tc_make_map(tb_ctx* ctx, int precision, const void* base, int ld, CUtensorMap* map, int row_bytes = 128,
+                    int box_rows = 128);
 int sp2_tc_row_bytes();
 
 // ------------------------------------------------------------ utilities

@@ -52,6 +52,7 @@ extern "C" int tb_ctx_create(tb_ctx** out) {
   ctx->grid_limit = 0;
   ctx->sp2_form = TB_SP2_FORM_AUTO;
   ctx->pair_clusters = -1;
+  ctx->oz_pair_clusters = -1;
   ctx->wait_ns = 2000000000ull;
   ctx->cc_major = prop.major;
   ctx->cc_minor = prop.minor;

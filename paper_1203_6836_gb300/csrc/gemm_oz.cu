@@ -36,6 +36,8 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 namespace {
 
 using namespace tcx;
@@ -294,11 +296,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int lsh = shift > 0 ? shift : 0;
       const float fs = shift >= 0 ? 1.0f : 1.0f / (float)(1 << -shift);
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        uint32_t v[32];
-        tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + acc * kTile + 64 * h + 32 * c, v);
+      for (int c = 0; c < 4; ++c) {
+        uint32_t v[16];
+        tmem_ld16(tmem + (static_cast<uint32_t>(32 * q) << 16) + acc * kTile + 64 * h + 16 * c, v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc64[32 * c + j] += __float2ll_rn(__uint_as_float(v[j]) * fs) << lsh;
+        for (int j = 0; j < 16; ++j) acc64[16 * c + j] += __float2ll_rn(__uint_as_float(v[j]) * fs) << lsh;
       }
       tc_fence_before();
       __syncwarp();
@@ -369,10 +371,338 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ------------------------------------------------------------------ CTA pairs
+// The same product on clusters of two CTAs (ld a multiple of 256).  A work
+// unit is a 256 x 128 block (I2, J) of the upper triangle, J >= 2 I2: the
+// pair's tcgen05.mma.cta_group::2 (M = 256, N = 128) takes A rows from both
+// CTAs (CTA r: row block 2 I2 + r) and B rows 64 per CTA (CTA r: rows
+// 128 J + 64 r); CTA r accumulates the 128 x 128 tile (2 I2 + r, J) (none when
+// that tile lies below the diagonal: it is the mirror of one above).  The 22
+// slice pairs run as 12 batches of one or two pairs that share their A slice
+// (s, t..t+1), so a k-slice stage holds one A tile (16 KB) and one or two B
+// half tiles (8 KB each) for one or two MMAs: with the pair split, 16.7 KB of
+// operands per 128 x 128 x 64 MMA per SM against 32 KB in the single-CTA form.
+// TMEM holds two sets of two 128-column accumulators, alternating between
+// batches, so the drain of one batch overlaps the next batch's MMAs.  The pair
+// protocol (agreed decision, copies completing on the even CTA's barriers,
+// multicast commits, final cluster barrier) is that of k_sp2_step_tc2.
+constexpr int kBatches = 12;
+__constant__ int c_batch_s[kBatches] = {1, 1, 1, 2, 2, 2, 3, 3, 4, 4, 5, 6};
+__constant__ int c_batch_t[kBatches] = {1, 3, 5, 1, 3, 5, 1, 3, 1, 3, 1, 1};
+__constant__ int c_batch_n[kBatches] = {2, 2, 2, 2, 2, 1, 2, 2, 2, 2, 2, 1};
+constexpr int kHalfBytes = 64 * 128;                   // 64-row B tile
+constexpr int kStage2 = kTileBytes + 2 * kHalfBytes;   // 32 KB
+constexpr int kStages2 = 6;
+constexpr int kSmem2 = kStages2 * kStage2 + 1024;
+constexpr unsigned long long kSettleNs = 1000000ull;
+
+struct SliceMaps2 {
+  CUtensorMap a[kS];  // 128-row boxes
+  CUtensorMap b[kS];  // 64-row boxes
+};
+
+// Unit u of the 256 x 128 upper-triangle units (row-major over I2, then J from 2 I2).
+__device__ __forceinline__ void pair_unit(int u, int nt, int* I2, int* J) {
+  int i = 0;
+  while (u >= nt - 2 * i) {
+    u -= nt - 2 * i;
+    ++i;
+  }
+  *I2 = i;
+  *J = 2 * i + u;
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    k_sp2_step_oz2(const SP2StepArgs a, const __grid_constant__ SliceMaps2 maps, const int* __restrict__ exps,
+                   const double* __restrict__ Xin, double* __restrict__ Xout) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[kStages2], empty[kStages2], tfull[2], tempty[2], mdone;
+  __shared__ uint32_t tmem_base;
+  __shared__ double s_t[3];
+  __shared__ int s_dec[3];
+  __shared__ uint32_t s_go;
+  __shared__ volatile int s_abort;
+  __shared__ double s_red[8][3];
+
+  SP2State* st = a.st;
+  const int over = st->rdone || st->err;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+
+  if (warp == 0) {
+    double x = 0, y = 0, z = 0;
+    if (!over) {
+      for (int i = lane; i < a.nparts_in; i += 32) {
+        x += a.parts_in[3 * i];
+        y += a.parts_in[3 * i + 1];
+        z += a.parts_in[3 * i + 2];
+      }
+      x = warp_sum(x);
+      y = warp_sum(y);
+      z = warp_sum(z);
+    }
+    if (lane == 0) {
+      int br = 0, capped = 0;
+      const int stop = over ? 1 : sp2_decide(a, x, y, st->rt1, st->rt2, false, &br, &capped);
+      s_t[0] = x;
+      s_t[1] = y;
+      s_t[2] = z;
+      s_dec[0] = stop;
+      s_dec[1] = br;
+      s_dec[2] = capped;
+    }
+  }
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kStages2; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 16);  // 8 epilogue warps x 2 CTAs
+    }
+    mbar_init(&mdone, 1);
+    s_abort = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (!over && blockIdx.x == 0 && threadIdx.x == 0) {
+    st->rt1[a.k] = s_t[0];
+    st->rt2[a.k] = s_t[1];
+    if (a.k > 0) st->idem_fro = sqrt(s_t[2]);
+    if (s_dec[0]) {
+      st->riters = a.k;
+      st->rcapped = s_dec[2];
+      st->rdone = 1;
+    } else if (s_dec[1]) {
+      st->rbranch |= 1ull << a.k;
+    }
+  }
+  if (threadIdx.x == 0) s_go = (s_dec[0] ? 0u : 1u) | (s_dec[1] ? 2u : 0u);
+  cluster_sync();
+  if (rank != 0 && threadIdx.x == 0) s_go = ld_cluster_u32(mapa_rank(smem_u32(&s_go), 0));
+  cluster_sync();
+  if (!(s_go & 1u)) return;
+  const int br = (s_go >> 1) & 1;
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int nt = a.ld / kTile, nt2 = a.ld / (2 * kTile);
+  const int U = nt * nt2 - nt2 * (nt2 - 1);  // sum over I2 of (nt - 2 I2)
+  const int ncl = gridDim.x >> 1, cl = blockIdx.x >> 1;
+  const int nk = a.ld / kBK;
+  if (warp == 1) tmem_alloc_pair(&tmem_base, 4 * kTile);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------------- producer
+    for (int i = 0; i < kS; ++i) {
+      prefetch_map(&maps.a[i]);
+      prefetch_map(&maps.b[i]);
+    }
+    const uint32_t full0 = mapa_rank(smem_u32(&full[0]), 0);
+    int g = 0, issued = 0;
+    for (int u = cl; u < U && !s_abort; u += ncl) {
+      int I2, J;
+      pair_unit(u, nt, &I2, &J);
+      const int ya = (2 * I2 + (int)rank) * kTile, yb = J * kTile + 64 * (int)rank;
+      for (int b = 0; b < kBatches && !s_abort; ++b) {
+        const int sa = c_batch_s[b], tb = c_batch_t[b], nb = c_batch_n[b];
+        const uint32_t bytes = kTileBytes + nb * kHalfBytes;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int stg = g % kStages2;
+          if (g >= kStages2 && !mbar_wait(&empty[stg], ((g / kStages2) - 1) & 1, &s_abort, a.wait_ns ? a.wait_ns : kWaitNs)) break;
+          uint8_t* base = smem + stg * kStage2;
+          if (rank == 0) mbar_expect_tx(&full[stg], 2 * bytes);
+          const uint32_t fb = full0 + 8u * stg;
+          tma_load_2d_pair(base, &maps.a[sa - 1], fb, kb * kBK, ya);
+          tma_load_2d_pair(base + kTileBytes, &maps.b[tb - 1], fb, kb * kBK, yb);
+          if (nb > 1) tma_load_2d_pair(base + kTileBytes + kHalfBytes, &maps.b[tb], fb, kb * kBK, yb);
+          issued = g + 1;
+        }
+      }
+    }
+    if (s_abort && rank == 0) {
+      for (int q = (issued > kStages2 ? issued - kStages2 : 0); q < issued; ++q) {
+        const unsigned long long t0 = gtime();
+        while (!mbar_try(&full[q % kStages2], (q / kStages2) & 1) && gtime() - t0 < kSettleNs) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    // ---------------------------------------------------------- MMA issuer (even CTA)
+    constexpr uint32_t id = idesc(1u, 256, 128);
+    const unsigned long long wl = a.wait_ns ? a.wait_ns : kWaitNs;
+    int g = 0, gb = 0;
+    for (int u = cl; u < U && !s_abort; u += ncl) {
+      for (int b = 0; b < kBatches && !s_abort; ++b, ++gb) {
+        const int nb = c_batch_n[b];
+        const int set = gb & 1;
+        if (gb >= 2 && !mbar_wait(&tempty[set], ((gb >> 1) - 1) & 1, &s_abort, wl)) break;
+        tc_fence_after();
+        const uint32_t d0 = tmem + 2 * set * kTile;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int stg = g % kStages2;
+          if (!mbar_wait(&full[stg], (g / kStages2) & 1, &s_abort, wl)) break;
+          tc_fence_after();
+          const uint32_t base = smem_u32(smem + stg * kStage2);
+#pragma unroll
+          for (int ks = 0; ks < kBK / 16; ++ks) {
+            const uint64_t ad = sdesc(base + ks * 32);
+            umma_pair<false>(d0, ad, sdesc(base + kTileBytes + ks * 32), id, (kb | ks) != 0);
+            if (nb > 1) umma_pair<false>(d0 + kTile, ad, sdesc(base + kTileBytes + kHalfBytes + ks * 32), id, (kb | ks) != 0);
+          }
+          umma_commit_pair(&empty[stg], 3);
+        }
+        umma_commit_pair(&tfull[set], 3);
+      }
+    }
+    umma_commit_pair(&mdone, 3);
+  } else if (warp >= 2) {
+    // ---------------------------------------------------------- epilogue (both CTAs)
+    const int q = warp & 3;          // TMEM lane quarter
+    const int h = (warp - 2) >> 2;   // column half
+    const int row = 32 * q + lane;
+    const uint32_t tempty0 = mapa_rank(smem_u32(&tempty[0]), 0);
+    const unsigned long long wl = a.wait_ns ? a.wait_ns : kWaitNs;
+    double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    bool ok = true;
+    int gb = 0;
+    for (int u = cl; u < U && ok; u += ncl) {
+      int I2, J;
+      pair_unit(u, nt, &I2, &J);
+      const int I = 2 * I2 + (int)rank;
+      long long acc64[64];
+#pragma unroll
+      for (int j = 0; j < 64; ++j) acc64[j] = 0;
+      for (int b = 0; b < kBatches; ++b, ++gb) {
+        const int set = gb & 1;
+        if (!mbar_wait_warp(&tfull[set], (gb >> 1) & 1, &s_abort, wl)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int p = 0; p < c_batch_n[b]; ++p) {
+          const int s = c_batch_s[b], t = c_batch_t[b] + p;
+          // fixed point 2^{-kBeta (kS + 1)} as in the single-CTA form
+          const int shift = kBeta * (kS + 1 - s - t);
+          const int lsh = shift > 0 ? shift : 0;
+          const float fs = shift >= 0 ? 1.0f : 1.0f / (float)(1 << -shift);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            uint32_t v[16];
+            tmem_ld16(tmem + (static_cast<uint32_t>(32 * q) << 16) + (2 * set + p) * kTile + 64 * h + 16 * c, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc64[16 * c + j] += __float2ll_rn(__uint_as_float(v[j]) * fs) << lsh;
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(tempty0 + 8u * set);
+      }
+      if (!ok || I > J) continue;  // below the diagonal: written as the mirror of (J, I)
+      const bool mirror = I != J;
+      const int m0 = I * kTile, n0 = J * kTile;
+      const int gr = m0 + row;
+      const int er = exps[gr];
+      const double* xin = Xin + (size_t)gr * a.ld + n0 + 64 * h;
+      double* xout = Xout + (size_t)gr * a.ld + n0 + 64 * h;
+      const int* ec = exps + n0 + 64 * h;
+      const double w = mirror ? 2.0 : 1.0;  // the transposed copy counts too
+      double u2 = 0.0, u3 = 0.0;
+#pragma unroll
+      for (int j = 0; j < 64; ++j) {
+        const double cxx = ldexp((double)acc64[j], er + ec[j] - kBeta * (kS + 1));
+        const double x = xin[j];
+        const double y = br ? 2.0 * x - cxx : cxx;
+        xout[j] = y;
+        if (mirror) Xout[(size_t)(n0 + 64 * h + j) * a.ld + gr] = y;
+        if (gr == n0 + 64 * h + j) t1 += y;
+        u2 += y * y;
+        u3 += (cxx - x) * (cxx - x);
+      }
+      t2 += w * u2;
+      t3 += w * u3;
+    }
+    t1 = warp_sum(t1);
+    t2 = warp_sum(t2);
+    t3 = warp_sum(t3);
+    if (lane == 0) {
+      s_red[warp - 2][0] = t1;
+      s_red[warp - 2][1] = t2;
+      s_red[warp - 2][2] = t3;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 64) {
+    double x = 0, y = 0, z = 0;
+    for (int w = 0; w < 8; ++w) {
+      x += s_red[w][0];
+      y += s_red[w][1];
+      z += s_red[w][2];
+    }
+    const int cta = blockIdx.x;
+    a.parts_out[3 * cta] = x;
+    a.parts_out[3 * cta + 1] = y;
+    a.parts_out[3 * cta + 2] = z;
+    if (s_abort) atomicExch(&st->err, TB_ERR_TIMEOUT);
+  }
+  if (warp == 1 && lane == 0) {
+    const unsigned long long t0 = gtime();
+    while (!mbar_try(&mdone, 0) && gtime() - t0 < kWaitNs) {
+    }
+    if (s_abort) {
+      const unsigned long long t1 = gtime();
+      while (gtime() - t1 < kSettleNs) {
+      }
+    }
+  }
+  __syncwarp();
+  cluster_sync();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem, 4 * kTile);
+  }
+}
+
+int oz_pair_capacity(tb_ctx* ctx) {
+  if (ctx->oz_pair_clusters >= 0) return ctx->oz_pair_clusters;
+  int n = 0;
+  static unsigned long long attr_done = 0;
+  if (tb_smem_attr(ctx, k_sp2_step_oz2, kSmem2, &attr_done) == TB_OK) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(2 * ctx->sm_count);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kSmem2;
+    if (cudaOccupancyMaxActiveClusters(&n, k_sp2_step_oz2, &cfg) != cudaSuccess) n = 0;
+  }
+  (void)cudaGetLastError();
+  ctx->oz_pair_clusters = n;
+  return n;
+}
+
+// Clusters of the pair form for this ld (0: the single-CTA form).  The pair
+// form moves half the operand bytes per MMA at the same tile count per SM, so
+// it is taken wherever ld allows unless the single form is forced.
+int oz_pairs(tb_ctx* ctx, int ld) {
+  if (ld % (2 * kTile) != 0 || ctx->sp2_form == TB_SP2_FORM_SINGLE) return 0;
+  int C = oz_pair_capacity(ctx);
+  if (ctx->grid_limit > 0) C = std::min(C, ctx->grid_limit / 2);
+  const int nt = ld / kTile, nt2 = ld / (2 * kTile);
+  const int U = nt * nt2 - nt2 * (nt2 - 1);
+  C = std::min(C, U);
+  return C > 0 ? C : 0;
+}
+
 }  // namespace
 
 int sp2_oz_max_ld() { return 4096; }
-int sp2_oz_num_parts(int ld) {
+int sp2_oz_num_parts(tb_ctx* ctx, int ld) {
+  const int p = oz_pairs(ctx, ld);
+  if (p > 0) return 2 * p;
   const int nt = ld / kTile;
   return nt * (nt + 1) / 2;
 }
@@ -385,8 +715,23 @@ int sp2_oz_step(tb_ctx* ctx, const SP2StepArgs& a, const double* Xin, double* Xo
   if (int rc_attr = tb_smem_attr(ctx, k_sp2_step_oz, kSmem, &attr_done)) return rc_attr;
   k_oz_split<<<(a.ld * 32 + 255) / 256, 256, 0, s>>>(a.st, Xin, a.ld, static_cast<__nv_bfloat16*>(slices), exps);
   TB_LAUNCH_CHECK(ctx);
-  SliceMaps maps;
   const size_t plane = (size_t)a.ld * a.ld * sizeof(__nv_bfloat16);
+  const int pairs = oz_pairs(ctx, a.ld);
+  if (pairs > 0) {
+    static unsigned long long attr2_done = 0;
+    if (int rc_attr = tb_smem_attr(ctx, k_sp2_step_oz2, kSmem2, &attr2_done)) return rc_attr;
+    SliceMaps2 m2;
+    for (int i = 0; i < kS; ++i) {
+      int rc = sp2_tc_make_map(ctx, TB_PREC_BF16, static_cast<char*>(slices) + i * plane, a.ld, &m2.a[i], 128, 128);
+      if (rc) return rc;
+      rc = sp2_tc_make_map(ctx, TB_PREC_BF16, static_cast<char*>(slices) + i * plane, a.ld, &m2.b[i], 128, 64);
+      if (rc) return rc;
+    }
+    k_sp2_step_oz2<<<2 * pairs, kThreads, kSmem2, s>>>(a, m2, exps, Xin, Xout);
+    TB_LAUNCH_CHECK(ctx);
+    return TB_OK;
+  }
+  SliceMaps maps;
   for (int i = 0; i < kS; ++i) {
     int rc = sp2_tc_make_map(ctx, TB_PREC_BF16, static_cast<char*>(slices) + i * plane, a.ld, &maps.m[i]);
     if (rc) return rc;

@@ -749,14 +749,16 @@ size_t sp2_tc_operand_bytes(int precision) {
 
 int sp2_tc_row_bytes() { return Pipe<TB_PREC_TF32X3>::row; }
 
-int sp2_tc_make_map(tb_ctx* ctx, int precision, const void* base, int ld, CUtensorMap* map, int row_bytes) {
+int sp2_tc_make_map(tb_ctx* ctx, int precision, const void* base, int ld, CUtensorMap* map, int row_bytes,
+                    int box_rows) {
   if (!ctx->encode_tiled) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
   if (row_bytes != 64 && row_bytes != 128) return tb_fail(ctx, TB_ERR_ARG, "tile row of %d bytes", row_bytes);
+  if (box_rows != 64 && box_rows != 128) return tb_fail(ctx, TB_ERR_ARG, "tile of %d rows", box_rows);
   const bool tf = precision == TB_PREC_TF32 || precision == TB_PREC_TF32X3;
   const size_t eb = tf ? 4 : 2;
   const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)ld};
   const cuuint64_t strides[1] = {(cuuint64_t)(ld * eb)};
-  const cuuint32_t box[2] = {(cuuint32_t)(row_bytes / eb), 128};
+  const cuuint32_t box[2] = {(cuuint32_t)(row_bytes / eb), (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = ctx->encode_tiled(map, tf ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                                  2, const_cast<void*>(base), dims, strides, box, estr,

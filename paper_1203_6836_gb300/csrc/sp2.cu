@@ -616,7 +616,7 @@ extern "C" int dm_sp2(tb_ctx* ctx, const double* H, int n, double nocc, const tb
   r.max_iter = refine;
   r.tol = o->tol;
   const dim3 g(ld / f64_tile(ld), ld / f64_tile(ld));
-  const int np_ref = L.oz ? sp2_oz_num_parts(ld) : (int)(g.x * g.y);
+  const int np_ref = L.oz ? sp2_oz_num_parts(ctx, ld) : (int)(g.x * g.y);
   tb_prof_mark(ctx, 1, 0, s);
   for (int k = 0; k <= refine; ++k) {
     r.k = k;
