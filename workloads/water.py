@@ -71,6 +71,11 @@ class ModelParams:
     # Ewald splitting in 1/A, 0 = chosen from the box)
     gamma_form: int = 0
     ewald_alpha: float = 0.0
+    # basis-set overlap between atoms (App. D.1): radial s(r) = overlap_s0
+    # exp(-r / overlap_rs) in the Slater-Koster table, the App. D tail between
+    # r1 and rcut; overlap_s0 = 0 is the orthogonal model (S = I)
+    overlap_s0: float = 0.0
+    overlap_rs: float = 0.4
 
 
 @dataclasses.dataclass(frozen=True)
@@ -372,6 +377,16 @@ def gapped_params() -> ModelParams:
     the prefactor at which that molecule's O-H bond force vanishes at
     r_OH = 0.96 A (pair_rho = 0.3 A as in the default recipe)."""
     return dataclasses.replace(ModelParams(), t_hop=20.0, r_decay=0.4, hubbard_u=6.0, pair_a=65.75)
+
+
+def nonorth_params() -> ModelParams:
+    """The gapped recipe with a basis-set overlap: s(r) = 1.1 exp(-r / 0.4 A),
+    0.10 at the O-H bond (the hopping there is 1.8 eV), 0.025 between the
+    two H of a molecule; S is positive definite with eigenvalues in about
+    [0.85, 1.2] for the molecular systems.  The overlap makes the bond
+    repel, so pair_a = 24.14 eV is refitted for the isolated molecule's
+    O-H bond force to vanish at 0.96 A (its gap is then 2.7 eV)."""
+    return dataclasses.replace(gapped_params(), overlap_s0=1.1, overlap_rs=0.4, pair_a=24.14)
 
 
 def gapped_vapour(n_mol: int = 682, seed: int = 0, morton: bool = False) -> WaterSystem:
