@@ -91,6 +91,13 @@ typedef struct {
    * and per force call. */
   int gamma_form;
   double ewald_alpha;
+  /* Basis-set overlap between atoms (App. D.1; non-orthogonal formulation when overlap_s0 != 0):
+   * S is the unit matrix on site and, between atoms, minus the Slater-Koster table above
+   * evaluated with s(r) = overlap_s0 exp(-r/overlap_rs) (with the App. D tail on [r1, rcut)),
+   * i.e. ss-sigma = +s, sp-sigma = -s, pp-sigma = -s, pp-pi = +s.  overlap_s0 = 0: S = I,
+   * the orthogonal model (tb_build_H); otherwise use tb_build_HS, dm_nonorth,
+   * mulliken_nonorth and tb_forces_nonorth (xlbomd_* switch to them by themselves). */
+  double overlap_s0, overlap_rs;
 } tb_params;
 
 /* A periodic system.  types and orb_off are device arrays. */
@@ -359,6 +366,61 @@ int dm_fermi_entropy_workspace_size(int n, size_t* bytes);
 int dm_fermi_entropy(tb_ctx* ctx, const double* H, int n, const double* mu, double kT, double* D, double* S,
                      void* workspace, size_t workspace_bytes, void* stream);
 
+/* ------------------------------------- f3: non-orthogonal formulation (App. D.1) */
+
+/* H[n] and the overlap S of the non-orthogonal formulation (Eq. DFTB_2 with the
+ * charges n, as in Eq. EL_Orth_c):
+ *   H_ab = h_ab + S_ab (v_a + v_b)/2,  v_a = sum_l gamma_{i(a) l} n_l (orbital a on atom i).
+ *   n_aux [N] or NULL (then H = h), H [n*n], S [n*n], gamma [N*N] outputs (fully
+ *   overwritten); v [N] output (the per-atom v, needed by tb_forces_nonorth), may be
+ *   NULL only when n_aux is.  With overlap_s0 = 0 it writes S = I and the H of tb_build_H. */
+int tb_build_HS(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const double* R,
+                const double* n_aux, double* H, double* S, double* gamma, double* v, void* stream);
+
+/* Report of dm_nonorth (device memory): the congruence factor's Newton-Schulz iterations
+ * and the final max |(Z Y)_ij - I_ij| (Y -> S^{1/2}, Z -> S^{-1/2}). */
+typedef struct {
+  int status;           /* TB_OK, TB_ERR_NOT_CONVERGED (Z not converged in 40 iterations) */
+  int ns_iters;
+  double ns_residual;
+} tb_nonorth_report;
+
+/* Density matrix in the non-orthogonal basis (Eqs. DM_perp, Congr):
+ *   Z = S^{-1/2} (Z^T S Z = I) by the coupled Newton-Schulz iteration (GEMM only, FP64,
+ *   stopped on the device at max |Z Y - I| <= 1e-13, or below 1e-9 once it stops halving);
+ *   H_perp = Z^T H Z;  rho_perp = theta(mu0 I - H_perp) by dm_sp2 with opts `so` (kT = 0), or
+ *   the Fermi-Dirac matrix by dm_fermi with `fo` and the device mu[4] (kT > 0; mu as for
+ *   dm_fermi: in the first element, warm start and result);
+ *   rho = Z rho_perp Z^T;  W = Z (H_perp rho_perp + rho_perp H_perp) Z^T / 2, the
+ *   energy-weighted density matrix of the Pulay force (rho H rho at kT = 0).
+ * The congruence products run as FP64 GEMMs on the FP64 units (GB300: ~1.2 TFLOP/s, about
+ * 25 n^3-products per call).
+ *   H, S [n*n] inputs; rho, W [n*n] outputs; sp2_report / fermi_report as for dm_sp2 /
+ *   dm_fermi (may be NULL); report may be NULL.  Workspace from dm_nonorth_workspace_size
+ *   (1024-byte aligned). */
+int dm_nonorth_workspace_size(int n, double kT, const tb_sp2_opts* so, const tb_fermi_opts* fo, size_t* bytes);
+int dm_nonorth(tb_ctx* ctx, const double* H, const double* S, int n, double n_occ, double kT,
+               const tb_sp2_opts* so, const tb_fermi_opts* fo, double* mu, double* rho, double* W,
+               void* workspace, size_t workspace_bytes, tb_sp2_report* sp2_report,
+               tb_fermi_report* fermi_report, tb_nonorth_report* report, void* stream);
+
+/* Mulliken net charges with the overlap: q_i = 2 sum_{a in i} (rho S)_aa - N0_i (App. D.1;
+ * the charge whose derivative dq/dR|_rho = 2 diag(rho S_R) Eq. EL_Nonorth_a uses).
+ *   rho, S [n*n], q [N] output. */
+int mulliken_nonorth(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const double* rho,
+                     const double* S, double* q, void* stream);
+
+/* F = -dE/dR at fixed n and E = 2 Tr[h rho] + 1/2 (2q - n)^T gamma n + E_pair in the
+ * non-orthogonal formulation (Eq. EL_Nonorth_a with n for q):
+ *   F = -d/dR { Tr[2 rho h] + Tr[(V rho + rho V - 2 W) S] }|_{rho, W} - (q - n/2)^T dgamma/dR n
+ *       - dE_pair/dR,  V = diag(v):
+ * the Pulay term Tr[(S^-1 H rho + rho H S^-1) S_R] = 2 Tr[W S_R] and the term of
+ * dq/dR|_rho.  rho, W from dm_nonorth; q from mulliken_nonorth; v from tb_build_HS;
+ * F [N*3], energy [4] outputs as for tb_forces. */
+int tb_forces_nonorth(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const double* R,
+                      const double* rho, const double* W, const double* q, const double* n_aux,
+                      const double* v, const double* gamma, double* F, double* energy, void* stream);
+
 /* ------------------------------------------------------------- a7: charges */
 
 /* Mulliken net charges q_i = 2 sum_{a in i} D_aa - N0_i (App. D).
@@ -426,6 +488,13 @@ typedef struct {
   size_t entropy_workspace_bytes;
   double* entropy;            /* device double: S/k_B of the last D (with entropy_workspace);
                                  energies[0] is then E_tot = KE + E_pot - kT S (Eq. Etot) */
+  /* non-orthogonal formulation (p->overlap_s0 != 0): D holds rho, and these are required */
+  double* S;                  /* [n*n] overlap */
+  double* W;                  /* [n*n] energy-weighted density matrix */
+  double* vscc;               /* [N] v = gamma n, the per-atom SCC potential */
+  void* nonorth_workspace;    /* dm_nonorth workspace (dm_nonorth_workspace_size) */
+  size_t nonorth_workspace_bytes;
+  tb_nonorth_report* nonorth_report;  /* device, may be NULL */
 } tb_md_state;
 
 /* Initial state (App. D.3): SCF-converge the charges with Anderson mixing

@@ -130,6 +130,8 @@ struct ModelDev {
   double gwidth;      // Gaussian width c = 2k/(U sqrt(pi))
   double erange;      // real-space reach: max(6.6/alpha, 6.6 c)
   double gmax;        // reciprocal cut-off 13.2 alpha
+  double s0, inv_srs; // overlap radial s(r) = s0 exp(-r inv_srs) (s0 = 0: S = I)
+  double Bov[6];      // its App. D tail
 };
 
 int tb_model_from_params(tb_ctx* ctx, const tb_params* p, double box, ModelDev* m);

@@ -131,11 +131,38 @@ int check_state(tb_ctx* ctx, const tb_md_state* st, const tb_xl_params* xp, cons
   return TB_OK;
 }
 
+// Non-orthogonal formulation (App. D.1) when the model has an overlap.
+bool nonorth_on(const tb_params* p) { return p && p->overlap_s0 != 0.0; }
+
+int check_nonorth(tb_ctx* ctx, const tb_params* p, const tb_md_state* st) {
+  if (!nonorth_on(p)) return TB_OK;
+  if (!st->S || !st->W || !st->vscc || !st->nonorth_workspace)
+    return tb_fail(ctx, TB_ERR_ARG, "overlap_s0 != 0: tb_md_state needs S, W, vscc and the dm_nonorth workspace");
+  if (st->kT > 0.0 && st->entropy_workspace)
+    return tb_fail(ctx, TB_ERR_UNSUPPORTED, "the entropy term is not available in the non-orthogonal formulation");
+  return TB_OK;
+}
+
+// H[n] (and S, v in the non-orthogonal formulation).
+int build_H_any(tb_ctx* ctx, const tb_params* p, tb_md_state* st, const double* n_aux, cudaStream_t s) {
+  if (nonorth_on(p)) return tb_build_HS(ctx, p, &st->sys, st->R, n_aux, st->H, st->S, st->gamma, st->vscc, s);
+  return tb_build_H(ctx, p, &st->sys, st->R, n_aux, st->H, st->gamma, s);
+}
+
+int charges_any(tb_ctx* ctx, const tb_params* p, tb_md_state* st, cudaStream_t s) {
+  if (nonorth_on(p)) return mulliken_nonorth(ctx, p, &st->sys, st->D, st->S, st->q, s);
+  return mulliken(ctx, p, &st->sys, st->D, st->q, s);
+}
+
 bool entropy_on(const tb_md_state* st) { return st->kT > 0.0 && st->entropy_workspace && st->entropy; }
 
 // D from H: Fermi operator (dm_fermi, mu carried in st->mu) when kT > 0, else
 // the T_e = 0 projector by SP2.
-int density(tb_ctx* ctx, tb_md_state* st, const tb_sp2_opts* so, cudaStream_t s) {
+int density(tb_ctx* ctx, const tb_params* p, tb_md_state* st, const tb_sp2_opts* so, cudaStream_t s) {
+  if (nonorth_on(p))
+    return dm_nonorth(ctx, st->H, st->S, st->sys.norb, st->n_occ, st->kT, so, &st->fermi, st->mu, st->D, st->W,
+                      st->nonorth_workspace, st->nonorth_workspace_bytes, st->sp2_report, st->fermi_report,
+                      st->nonorth_report, s);
   if (st->kT > 0.0)
     return dm_fermi(ctx, st->H, st->sys.norb, st->n_occ, st->kT, &st->fermi, st->D, st->mu, st->workspace,
                     st->workspace_bytes, st->fermi_report, s);
@@ -146,9 +173,9 @@ int density(tb_ctx* ctx, tb_md_state* st, const tb_sp2_opts* so, cudaStream_t s)
 // H[n] -> D -> q -> F, E for the current positions and the given n.
 int electronic_step(tb_ctx* ctx, const tb_params* p, tb_md_state* st, const tb_sp2_opts* so,
                     const double* n_aux, cudaStream_t s) {
-  int rc = tb_build_H(ctx, p, &st->sys, st->R, n_aux, st->H, st->gamma, s);
+  int rc = build_H_any(ctx, p, st, n_aux, s);
   if (rc) return rc;
-  rc = density(ctx, st, so, s);
+  rc = density(ctx, p, st, so, s);
   if (rc) return rc;
   if (entropy_on(st)) {
     // T_e S at the mu of this D (st->mu[0]), Eq. Ent_Approx; E_tot only
@@ -156,8 +183,11 @@ int electronic_step(tb_ctx* ctx, const tb_params* p, tb_md_state* st, const tb_s
                           st->entropy_workspace_bytes, s);
     if (rc) return rc;
   }
-  rc = mulliken(ctx, p, &st->sys, st->D, st->q, s);
+  rc = charges_any(ctx, p, st, s);
   if (rc) return rc;
+  if (nonorth_on(p))
+    return tb_forces_nonorth(ctx, p, &st->sys, st->R, st->D, st->W, st->q, n_aux, st->vscc, st->gamma, st->F,
+                             st->energies + 1, s);
   return tb_forces(ctx, p, &st->sys, st->R, st->D, st->q, n_aux, st->gamma, st->F, st->energies + 1, s);
 }
 
@@ -240,6 +270,7 @@ extern "C" int xlbomd_init(tb_ctx* ctx, const tb_params* p, tb_md_state* st, con
                            void* stream) {
   if (!ctx) return TB_ERR_ARG;
   int rc = check_state(ctx, st, xp, so);
+  if (!rc) rc = check_nonorth(ctx, p, st);
   if (rc) return rc;
   cudaStream_t s = as_stream(stream);
   const int N = st->sys.natoms;
@@ -253,11 +284,11 @@ extern "C" int xlbomd_init(tb_ctx* ctx, const tb_params* p, tb_md_state* st, con
   int iters = -1;
   for (int it = 0; it < scf_max_iter; ++it) {
     TB_CUDA_TRY(ctx, cudaMemcpyAsync(n_dev, n.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s));
-    rc = tb_build_H(ctx, p, &st->sys, st->R, n_dev, st->H, st->gamma, s);
+    rc = build_H_any(ctx, p, st, n_dev, s);
     if (rc) return rc;
-    rc = density(ctx, st, so, s);
+    rc = density(ctx, p, st, so, s);
     if (rc) return rc;
-    rc = mulliken(ctx, p, &st->sys, st->D, st->q, s);
+    rc = charges_any(ctx, p, st, s);
     if (rc) return rc;
     TB_CUDA_TRY(ctx, cudaMemcpyAsync(q.data(), st->q, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
     TB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
@@ -305,6 +336,7 @@ extern "C" int xlbomd_step(tb_ctx* ctx, const tb_params* p, tb_md_state* st, con
                            const tb_sp2_opts* so, void* stream) {
   if (!ctx) return TB_ERR_ARG;
   int rc = check_state(ctx, st, xp, so);
+  if (!rc) rc = check_nonorth(ctx, p, st);
   if (rc) return rc;
   cudaStream_t s = as_stream(stream);
   const int N = st->sys.natoms;

@@ -103,6 +103,13 @@ int tb_model_from_params(tb_ctx* ctx, const tb_params* p, double box, ModelDev* 
   m->gwidth = 2.0 * p->coulomb_k / (p->hubbard_u * sqrt(M_PI));
   m->erange = fmax(6.6 / m->ealpha, 6.6 * m->gwidth);
   m->gmax = 13.2 * m->ealpha;
+  if (p->overlap_s0 != 0.0 && !(p->overlap_rs > 0.0))
+    return tb_fail(ctx, TB_ERR_ARG, "overlap_rs %g must be > 0", p->overlap_rs);
+  m->s0 = p->overlap_s0;
+  m->inv_srs = p->overlap_s0 != 0.0 ? 1.0 / p->overlap_rs : 0.0;
+  const double zero3[3] = {0.0, 0.0, 0.0};
+  zeta3(p->overlap_s0, -m->inv_srs, zero3, p->r1, f);
+  tail_closed_form(f[0], f[1], f[2], p->r1, p->rcut, m->Bov);
   return TB_OK;
 }
 
@@ -133,6 +140,19 @@ __device__ __forceinline__ void hop_radial(const ModelDev& m, double r, double* 
   } else {
     *V = 0.0;
     *dV = 0.0;
+  }
+}
+
+// s(r) and s'(r) of the overlap with its tail.
+__device__ __forceinline__ void ovl_radial(const ModelDev& m, double r, double* sv, double* dsv) {
+  const double zero3[3] = {0.0, 0.0, 0.0};
+  if (r < m.r1) {
+    zeta(m.s0, -m.inv_srs, zero3, r, sv, dsv);
+  } else if (r < m.rcut) {
+    tail_eval(m.Bov, r - m.r1, sv, dsv);
+  } else {
+    *sv = 0.0;
+    *dsv = 0.0;
   }
 }
 
@@ -229,7 +249,7 @@ __global__ void __launch_bounds__(256) k_build_pairs(ModelDev m, int N, const in
                                                      const int32_t* __restrict__ offs,
                                                      const double* __restrict__ R,
                                                      double* __restrict__ H, int n,
-                                                     double* __restrict__ G) {
+                                                     double* __restrict__ G, double* __restrict__ S) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y;
   if (i >= N || j >= N || j < i) return;
@@ -243,8 +263,16 @@ __global__ void __launch_bounds__(256) k_build_pairs(ModelDev m, int N, const in
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) B[a][b] = 0.0;
+  double Bs[4][4];  // overlap block (S): unit on site, minus the table with s(r) between atoms
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) Bs[a][b] = (i == j && a == b) ? 1.0 : 0.0;
+  const bool ovl = S != nullptr && m.s0 != 0.0;
   double gsum = (i == j) ? m.U : 0.0;
-  // H and gamma were zeroed: pairs with no image in range write nothing
+  if (S && i == j)
+    for (int a = 0; a < ni; ++a) S[(size_t)(oi + a) * n + (oi + a)] = 1.0;
+  // H, gamma (and S) were zeroed: pairs with no image in range write nothing
   // (gamma's window and h's tail both end at the cut-off)
   if (!(screen_f32(Ri, Rj, (float)m.box, (float)m.range) || i == j)) return;
   {
@@ -274,6 +302,13 @@ __global__ void __launch_bounds__(256) k_build_pairs(ModelDev m, int N, const in
             sk_block(ti, tj, l, V, Bi);
             for (int a = 0; a < ni; ++a)
               for (int b = 0; b < nj; ++b) B[a][b] += Bi[a][b];
+            if (ovl) {
+              double sv, dsv;
+              ovl_radial(m, r, &sv, &dsv);
+              sk_block(ti, tj, l, sv, Bi);
+              for (int a = 0; a < ni; ++a)
+                for (int b = 0; b < nj; ++b) Bs[a][b] -= Bi[a][b];
+            }
           }
         }
   }
@@ -295,6 +330,12 @@ __global__ void __launch_bounds__(256) k_build_pairs(ModelDev m, int N, const in
     }
   G[(size_t)i * N + j] = gsum;
   if (i != j) G[(size_t)j * N + i] = gsum;
+  if (ovl)
+    for (int a = 0; a < ni; ++a)
+      for (int b = 0; b < nj; ++b) {
+        S[(size_t)(oi + a) * n + (oj + b)] = Bs[a][b];
+        if (i != j) S[(size_t)(oj + b) * n + (oi + a)] = Bs[a][b];
+      }
 }
 
 // --------------------------------------------------------------------------
@@ -489,12 +530,13 @@ extern "C" int tb_build_H(tb_ctx* ctx, const tb_params* p, const tb_system* sys,
   ModelDev m;
   rc = tb_model_from_params(ctx, p, sys->box, &m);
   if (rc) return rc;
+  if (m.s0 != 0.0) return tb_fail(ctx, TB_ERR_ARG, "overlap_s0 != 0: the non-orthogonal H needs tb_build_HS");
   cudaStream_t s = as_stream(stream);
   const int N = sys->natoms, n = sys->norb;
   TB_CUDA_TRY(ctx, cudaMemsetAsync(H, 0, sizeof(double) * (size_t)n * n, s));
   TB_CUDA_TRY(ctx, cudaMemsetAsync(gamma, 0, sizeof(double) * (size_t)N * N, s));
   dim3 grid((N + 255) / 256, N);
-  k_build_pairs<<<grid, 256, 0, s>>>(m, N, sys->types, sys->orb_off, R, H, n, gamma);
+  k_build_pairs<<<grid, 256, 0, s>>>(m, N, sys->types, sys->orb_off, R, H, n, gamma, nullptr);
   TB_LAUNCH_CHECK(ctx);
   if (m.gamma_form == 1) {
     k_gamma_ewald<<<dim3((N + kGChunk - 1) / kGChunk, N), kGChunk, 0, s>>>(m, N, R, gamma);
@@ -502,6 +544,74 @@ extern "C" int tb_build_H(tb_ctx* ctx, const tb_params* p, const tb_system* sys,
   }
   if (n_aux) {
     k_add_shift<<<(N * 32 + 255) / 256, 256, 0, s>>>(N, sys->orb_off, gamma, n_aux, H, n);
+    TB_LAUNCH_CHECK(ctx);
+  }
+  return TB_OK;
+}
+
+// v_i = sum_l gamma_il n_l, one warp per atom.
+__global__ void __launch_bounds__(256) k_scc_potential(int N, const double* __restrict__ G,
+                                                       const double* __restrict__ n_aux, double* __restrict__ v) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= N) return;
+  const double* Gi = G + (size_t)warp * N;
+  double s = 0.0;
+  for (int l = lane; l < N; l += 32) s += Gi[l] * n_aux[l];
+  s = warp_sum(s);
+  if (lane == 0) v[warp] = s;
+}
+
+// H_ab += S_ab (v_i(a) + v_j(b)) / 2 for the orbital rows of atom i = blockIdx.y
+// (Eq. DFTB_2): each thread of the row block walks the columns, the column's atom
+// found by bisection in the orbital offsets.
+__global__ void __launch_bounds__(256) k_add_shift_nonorth(int N, const int32_t* __restrict__ offs,
+                                                           const double* __restrict__ v,
+                                                           const double* __restrict__ S,
+                                                           double* __restrict__ H, int n) {
+  const int i = blockIdx.y;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  int lo = 0, hi = N - 1;  // atom j with offs[j] <= b < offs[j + 1]
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (offs[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const double vj = v[lo], vi = v[i];
+  for (int a = offs[i]; a < offs[i + 1]; ++a) {
+    const size_t e = (size_t)a * n + b;
+    const double sab = S[e];
+    if (sab != 0.0) H[e] += 0.5 * sab * (vi + vj);
+  }
+}
+
+extern "C" int tb_build_HS(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const double* R,
+                           const double* n_aux, double* H, double* S, double* gamma, double* v, void* stream) {
+  if (!ctx) return TB_ERR_ARG;
+  int rc = check_system(ctx, sys);
+  if (rc) return rc;
+  if (!R || !H || !S || !gamma) return tb_fail(ctx, TB_ERR_ARG, "null R/H/S/gamma");
+  if (n_aux && !v) return tb_fail(ctx, TB_ERR_ARG, "tb_build_HS with n_aux needs v");
+  ModelDev m;
+  rc = tb_model_from_params(ctx, p, sys->box, &m);
+  if (rc) return rc;
+  cudaStream_t s = as_stream(stream);
+  const int N = sys->natoms, n = sys->norb;
+  TB_CUDA_TRY(ctx, cudaMemsetAsync(H, 0, sizeof(double) * (size_t)n * n, s));
+  TB_CUDA_TRY(ctx, cudaMemsetAsync(S, 0, sizeof(double) * (size_t)n * n, s));
+  TB_CUDA_TRY(ctx, cudaMemsetAsync(gamma, 0, sizeof(double) * (size_t)N * N, s));
+  dim3 grid((N + 255) / 256, N);
+  k_build_pairs<<<grid, 256, 0, s>>>(m, N, sys->types, sys->orb_off, R, H, n, gamma, S);
+  TB_LAUNCH_CHECK(ctx);
+  if (m.gamma_form == 1) {
+    k_gamma_ewald<<<dim3((N + kGChunk - 1) / kGChunk, N), kGChunk, 0, s>>>(m, N, R, gamma);
+    TB_LAUNCH_CHECK(ctx);
+  }
+  if (n_aux) {
+    k_scc_potential<<<(N * 32 + 255) / 256, 256, 0, s>>>(N, gamma, n_aux, v);
+    TB_LAUNCH_CHECK(ctx);
+    k_add_shift_nonorth<<<dim3((n + 255) / 256, N), 256, 0, s>>>(N, sys->orb_off, v, S, H, n);
     TB_LAUNCH_CHECK(ctx);
   }
   return TB_OK;
@@ -519,6 +629,39 @@ __global__ void k_mulliken(int N, const int32_t* __restrict__ types, const int32
   double pop = 0.0;
   for (int a = offs[i]; a < offs[i + 1]; ++a) pop += D[(size_t)a * n + a];
   q[i] = 2.0 * pop - (types[i] == TB_TYPE_O ? n0_O : n0_H);
+}
+
+// q_i = 2 sum_{a in i} (rho S)_aa - N0_i: one warp per atom, lanes over the
+// columns of the rows of rho and S (S symmetric: (rho S)_aa = rho_a. . S_a.).
+__global__ void __launch_bounds__(256) k_mulliken_nonorth(int N, const int32_t* __restrict__ types,
+                                                          const int32_t* __restrict__ offs,
+                                                          const double* __restrict__ rho,
+                                                          const double* __restrict__ S, int n, double n0_O,
+                                                          double n0_H, double* __restrict__ q) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= N) return;
+  double pop = 0.0;
+  for (int a = offs[i]; a < offs[i + 1]; ++a) {
+    const double* ra = rho + (size_t)a * n;
+    const double* sa = S + (size_t)a * n;
+    for (int b = lane; b < n; b += 32) pop += ra[b] * sa[b];
+  }
+  pop = warp_sum(pop);
+  if (lane == 0) q[i] = 2.0 * pop - (types[i] == TB_TYPE_O ? n0_O : n0_H);
+}
+
+extern "C" int mulliken_nonorth(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const double* rho,
+                                const double* S, double* q, void* stream) {
+  if (!ctx) return TB_ERR_ARG;
+  int rc = check_system(ctx, sys);
+  if (rc) return rc;
+  if (!p || !rho || !S || !q) return tb_fail(ctx, TB_ERR_ARG, "null argument to mulliken_nonorth");
+  const int N = sys->natoms;
+  k_mulliken_nonorth<<<(N * 32 + 255) / 256, 256, 0, as_stream(stream)>>>(N, sys->types, sys->orb_off, rho, S,
+                                                                          sys->norb, p->n0_O, p->n0_H, q);
+  TB_LAUNCH_CHECK(ctx);
+  return TB_OK;
 }
 
 extern "C" int mulliken(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const double* D,
@@ -582,6 +725,7 @@ __device__ __forceinline__ void band_pair(int ta, int tb, const double* __restri
 // One warp per atom a; lanes sweep all atoms b and their images.
 // F_a = dE/dd summed over pairs (d = R_b - R_a + T), since dd/dR_a = -1.
 // Per-atom energy shares are reduced with FP64 atomics into energy[1..3].
+template <bool OVL>
 __global__ void __launch_bounds__(256) k_forces(ModelDev m, int N, const int32_t* __restrict__ types,
                                                 const int32_t* __restrict__ offs,
                                                 const double* __restrict__ R,
@@ -589,7 +733,9 @@ __global__ void __launch_bounds__(256) k_forces(ModelDev m, int N, const int32_t
                                                 const double* __restrict__ q,
                                                 const double* __restrict__ n_aux,
                                                 const double* __restrict__ G,
-                                                double* __restrict__ F, double* __restrict__ energy) {
+                                                double* __restrict__ F, double* __restrict__ energy,
+                                                const double* __restrict__ W,
+                                                const double* __restrict__ vscc) {
   const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (a >= N) return;
@@ -636,6 +782,18 @@ __global__ void __launch_bounds__(256) k_forces(ModelDev m, int N, const int32_t
               for (int k = 0; k < 3; ++k) f[k] += 4.0 * g[k];
             } else {
               e_band += 2.0 * Eblk;  // self-image block of h_aa
+            }
+            if constexpr (OVL) if (b != a) {
+              // overlap terms: Tr[(V rho + rho V - 2 W) S] over the blocks (a,b) and
+              // (b,a); S's block is minus the table with s(r), and V is v_a, v_b on
+              // the two atoms' orbitals
+              double sv, dsv, Er, Ew, gr[3], gw[3];
+              ovl_radial(m, r, &sv, &dsv);
+              band_pair(ta, tb, D, n, oa, ob, l, r, sv, dsv, &Er, gr);
+              band_pair(ta, tb, W, n, oa, ob, l, r, sv, dsv, &Ew, gw);
+              const double vv = vscc[a] + vscc[b];
+#pragma unroll
+              for (int k = 0; k < 3; ++k) f[k] -= 2.0 * (vv * gr[k] - 2.0 * gw[k]);
             }
             double ph, dph;
             pair_radial(m, r, &ph, &dph);
@@ -707,13 +865,42 @@ extern "C" int tb_forces(tb_ctx* ctx, const tb_params* p, const tb_system* sys, 
   ModelDev m;
   rc = tb_model_from_params(ctx, p, sys->box, &m);
   if (rc) return rc;
+  if (m.s0 != 0.0) return tb_fail(ctx, TB_ERR_ARG, "overlap_s0 != 0: forces need tb_forces_nonorth");
   cudaStream_t s = as_stream(stream);
   TB_CUDA_TRY(ctx, cudaMemsetAsync(energy, 0, 4 * sizeof(double), s));
   const int N = sys->natoms;
   // one warp per atom, one warp per block: FP64 runs at ~8 GFLOP/s per SM on
   // GB300, so small systems spread their atoms over as many SMs as possible
-  k_forces<<<N, 32, 0, s>>>(m, N, sys->types, sys->orb_off, R, D, sys->norb, q,
-                                                  n_aux, gamma, F, energy);
+  k_forces<false><<<N, 32, 0, s>>>(m, N, sys->types, sys->orb_off, R, D, sys->norb, q,
+                                                  n_aux, gamma, F, energy, nullptr, nullptr);
+  TB_LAUNCH_CHECK(ctx);
+  if (m.gamma_form == 1) {
+    k_forces_ewald<<<(N + 7) / 8, 256, 0, s>>>(m, N, R, q, n_aux, F);
+    TB_LAUNCH_CHECK(ctx);
+  }
+  return TB_OK;
+}
+
+extern "C" int tb_forces_nonorth(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const double* R,
+                                 const double* rho, const double* W, const double* q, const double* n_aux,
+                                 const double* v, const double* gamma, double* F, double* energy, void* stream) {
+  if (!ctx) return TB_ERR_ARG;
+  int rc = check_system(ctx, sys);
+  if (rc) return rc;
+  if (!R || !rho || !W || !q || !n_aux || !v || !gamma || !F || !energy)
+    return tb_fail(ctx, TB_ERR_ARG, "null argument to tb_forces_nonorth");
+  ModelDev m;
+  rc = tb_model_from_params(ctx, p, sys->box, &m);
+  if (rc) return rc;
+  cudaStream_t s = as_stream(stream);
+  TB_CUDA_TRY(ctx, cudaMemsetAsync(energy, 0, 4 * sizeof(double), s));
+  const int N = sys->natoms;
+  if (m.s0 != 0.0)
+    k_forces<true><<<N, 32, 0, s>>>(m, N, sys->types, sys->orb_off, R, rho, sys->norb, q, n_aux, gamma, F,
+                                    energy, W, v);
+  else
+    k_forces<false><<<N, 32, 0, s>>>(m, N, sys->types, sys->orb_off, R, rho, sys->norb, q, n_aux, gamma, F,
+                                     energy, nullptr, nullptr);
   TB_LAUNCH_CHECK(ctx);
   if (m.gamma_form == 1) {
     k_forces_ewald<<<(N + 7) / 8, 256, 0, s>>>(m, N, R, q, n_aux, F);

@@ -99,7 +99,7 @@ class MDState:
 
     def __init__(self, ds: DeviceSystem, v0: np.ndarray, masses: np.ndarray, n_occ: float, K: int,
                  opts: tbmd.tb_sp2_opts, kT: float = 0.0, fermi: "tbmd.tb_fermi_opts" = None,
-                 entropy: bool = False):
+                 entropy: bool = False, nonorth: bool = False):
         dev = ds.device
         N, n = ds.natoms, ds.norb
         f64 = dict(dtype=torch.float64, device=dev)
@@ -127,6 +127,16 @@ class MDState:
         # kT > 0 with entropy: E_tot (energies[0]) includes -kT S, S/k_B in self.entropy
         self.entropy = torch.full((1,), float("nan"), dtype=torch.float64, device=dev)
         self.ent_ws = Workspace(tbmd.dm_fermi_entropy_workspace_size(n), dev) if (entropy and kT > 0.0) else None
+        # the non-orthogonal formulation (a model with an overlap): S, W, v and dm_nonorth's
+        # workspace, which holds the SP2 / Fermi workspace of H_perp
+        self.nonorth_report = torch.zeros(ctypes.sizeof(tbmd.tb_nonorth_report), dtype=torch.uint8, device=dev)
+        if nonorth:
+            self.S = torch.zeros(n, n, **f64)
+            self.W = torch.zeros(n, n, **f64)
+            self.vscc = torch.zeros(N, **f64)
+            self.no_ws = Workspace(tbmd.dm_nonorth_workspace_size(n, kT, opts, fermi), dev)
+        else:
+            self.S = self.W = self.vscc = self.no_ws = None
         self.st = tbmd.tb_md_state(
             sys=ds.sys, n_occ=float(n_occ), R=self.R.data_ptr(), v=self.v.data_ptr(), F=self.F.data_ptr(),
             mass=self.mass.data_ptr(), n_hist=self.n_hist.data_ptr(), q=self.q.data_ptr(),
@@ -136,7 +146,12 @@ class MDState:
             mu=self.mu.data_ptr(), fermi_report=self.fermi_report.data_ptr(),
             entropy_workspace=self.ent_ws.ptr if self.ent_ws else None,
             entropy_workspace_bytes=self.ent_ws.nbytes if self.ent_ws else 0,
-            entropy=self.entropy.data_ptr() if self.ent_ws else None)
+            entropy=self.entropy.data_ptr() if self.ent_ws else None,
+            S=self.S.data_ptr() if nonorth else None, W=self.W.data_ptr() if nonorth else None,
+            vscc=self.vscc.data_ptr() if nonorth else None,
+            nonorth_workspace=self.no_ws.ptr if nonorth else None,
+            nonorth_workspace_bytes=self.no_ws.nbytes if nonorth else 0,
+            nonorth_report=self.nonorth_report.data_ptr())
 
     def n_current(self) -> torch.Tensor:
         return self.n_hist[0]
@@ -247,3 +262,29 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def nonorth_report_to_dict(buf: torch.Tensor) -> dict:
+    raw = buf.detach().cpu().numpy().tobytes()
+    r = tbmd.tb_nonorth_report.from_buffer_copy(raw[:ctypes.sizeof(tbmd.tb_nonorth_report)])
+    return {k: getattr(r, k) for k, _ in tbmd.tb_nonorth_report._fields_}
+
+
+class NonorthSolver:
+    """dm_nonorth with its workspace sized for n: rho and W of (H, S)."""
+
+    def __init__(self, ctx: tbmd.Context, n: int, kT: float = 0.0, sp2: "tbmd.tb_sp2_opts" = None,
+                 fermi: "tbmd.tb_fermi_opts" = None, device="cuda"):
+        self.ctx, self.n, self.kT = ctx, int(n), float(kT)
+        self.sp2 = sp2 if sp2 is not None else sp2_opts("fp64")
+        self.fermi = fermi if fermi is not None else fermi_opts()
+        self.ws = Workspace(tbmd.dm_nonorth_workspace_size(n, kT, self.sp2, self.fermi), device)
+        self.report = torch.zeros(ctypes.sizeof(tbmd.tb_nonorth_report), dtype=torch.uint8, device=device)
+        self.sp2_report = new_report(device)
+        self.fermi_report = torch.zeros(ctypes.sizeof(tbmd.tb_fermi_report), dtype=torch.uint8, device=device)
+        self.mu = torch.full((4,), float("nan"), dtype=torch.float64, device=device)
+
+    def __call__(self, H, S, n_occ: float, rho, W, stream=None):
+        tbmd.dm_nonorth(self.ctx, H, S, self.n, n_occ, self.kT, self.sp2, self.fermi, self.mu, rho, W,
+                        self.ws.ptr, self.ws.nbytes, self.sp2_report, self.fermi_report, self.report, stream)
+        return rho

@@ -47,7 +47,8 @@ class tb_params(ctypes.Structure):
         "eps_s_O", "eps_p_O", "eps_s_H", "t_hop", "r_decay", "hubbard_u", "coulomb_k",
         "gamma_cut", "r1", "rcut", "n0_O", "n0_H", "pair_a", "pair_rho",
         "zeta_a2", "zeta_a3", "zeta_a4", "pair_a2", "pair_a3", "pair_a4")] + [
-        ("gamma_form", ctypes.c_int), ("ewald_alpha", ctypes.c_double)]
+        ("gamma_form", ctypes.c_int), ("ewald_alpha", ctypes.c_double),
+        ("overlap_s0", ctypes.c_double), ("overlap_rs", ctypes.c_double)]
 
     @classmethod
     def from_model(cls, m) -> "tb_params":
@@ -100,7 +101,14 @@ class tb_md_state(ctypes.Structure):
                 ("step", ctypes.c_int64), ("kT", ctypes.c_double), ("fermi", tb_fermi_opts),
                 ("mu", ctypes.c_void_p), ("fermi_report", ctypes.c_void_p),
                 ("entropy_workspace", ctypes.c_void_p), ("entropy_workspace_bytes", ctypes.c_size_t),
-                ("entropy", ctypes.c_void_p)]
+                ("entropy", ctypes.c_void_p),
+                ("S", ctypes.c_void_p), ("W", ctypes.c_void_p), ("vscc", ctypes.c_void_p),
+                ("nonorth_workspace", ctypes.c_void_p), ("nonorth_workspace_bytes", ctypes.c_size_t),
+                ("nonorth_report", ctypes.c_void_p)]
+
+
+class tb_nonorth_report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("ns_iters", ctypes.c_int), ("ns_residual", ctypes.c_double)]
 
 
 class tb_server_opts(ctypes.Structure):
@@ -134,6 +142,16 @@ _SIGS = {
     "tb_ctx_set_grid_limit": (ctypes.c_int, [_P, ctypes.c_int]),
     "tb_ctx_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_ulonglong]),
     "tb_ctx_set_sp2_form": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tb_build_HS": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P, _P, _P, _P,
+                                   _P, _P]),
+    "dm_nonorth_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.POINTER(tb_sp2_opts),
+                                                 ctypes.POINTER(tb_fermi_opts), ctypes.POINTER(ctypes.c_size_t)]),
+    "dm_nonorth": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                  ctypes.POINTER(tb_sp2_opts), ctypes.POINTER(tb_fermi_opts), _P, _P, _P, _P,
+                                  ctypes.c_size_t, _P, _P, _P, _P]),
+    "mulliken_nonorth": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P, _P, _P]),
+    "tb_forces_nonorth": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P, _P, _P,
+                                         _P, _P, _P, _P, _P, _P]),
     "tb_ctx_sp2_form_of": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "tb_build_H": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P, _P, _P, _P]),
     "dm_sp2_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(tb_sp2_opts),
@@ -281,6 +299,42 @@ def tb_ctx_sp2_form_of(ctx: Context, n: int) -> tuple[int, int]:
     f, c = ctypes.c_int(), ctypes.c_int()
     ctx.check(lib().tb_ctx_sp2_form_of(ctx.handle, int(n), ctypes.byref(f), ctypes.byref(c)), "tb_ctx_sp2_form_of")
     return f.value, c.value
+
+
+def tb_build_HS(ctx: Context, p: tb_params, sys: tb_system, R, n_aux, H, S, gamma, v, stream=None) -> int:
+    return ctx.check(lib().tb_build_HS(ctx.handle, ctypes.byref(p), ctypes.byref(sys), _ptr(R), _ptr(n_aux),
+                                       _ptr(H), _ptr(S), _ptr(gamma), _ptr(v), _stream(stream)), "tb_build_HS")
+
+
+def dm_nonorth_workspace_size(n: int, kT: float, sp2: tb_sp2_opts = None, fermi: tb_fermi_opts = None) -> int:
+    b = ctypes.c_size_t()
+    rc = lib().dm_nonorth_workspace_size(int(n), float(kT), ctypes.byref(sp2) if sp2 is not None else None,
+                                         ctypes.byref(fermi) if fermi is not None else None, ctypes.byref(b))
+    if rc != TB_OK:
+        raise TBError(rc, "dm_nonorth_workspace_size")
+    return b.value
+
+
+def dm_nonorth(ctx: Context, H, S, n: int, n_occ: float, kT: float, sp2: tb_sp2_opts, fermi: tb_fermi_opts, mu,
+               rho, W, workspace, workspace_bytes: int, sp2_report=None, fermi_report=None, report=None,
+               stream=None) -> int:
+    return ctx.check(lib().dm_nonorth(ctx.handle, _ptr(H), _ptr(S), int(n), float(n_occ), float(kT),
+                                      ctypes.byref(sp2) if sp2 is not None else None,
+                                      ctypes.byref(fermi) if fermi is not None else None, _ptr(mu), _ptr(rho),
+                                      _ptr(W), _ptr(workspace), int(workspace_bytes), _ptr(sp2_report),
+                                      _ptr(fermi_report), _ptr(report), _stream(stream)), "dm_nonorth")
+
+
+def mulliken_nonorth(ctx: Context, p: tb_params, sys: tb_system, rho, S, q, stream=None) -> int:
+    return ctx.check(lib().mulliken_nonorth(ctx.handle, ctypes.byref(p), ctypes.byref(sys), _ptr(rho), _ptr(S),
+                                            _ptr(q), _stream(stream)), "mulliken_nonorth")
+
+
+def tb_forces_nonorth(ctx: Context, p: tb_params, sys: tb_system, R, rho, W, q, n_aux, v, gamma, F, energy,
+                      stream=None) -> int:
+    return ctx.check(lib().tb_forces_nonorth(ctx.handle, ctypes.byref(p), ctypes.byref(sys), _ptr(R), _ptr(rho),
+                                             _ptr(W), _ptr(q), _ptr(n_aux), _ptr(v), _ptr(gamma), _ptr(F),
+                                             _ptr(energy), _stream(stream)), "tb_forces_nonorth")
 
 
 def tb_build_H(ctx: Context, p: tb_params, sys: tb_system, R, n_aux, H, gamma, stream=None) -> int:
