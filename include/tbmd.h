@@ -380,7 +380,7 @@ int tb_build_HS(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const dou
 /* Report of dm_nonorth (device memory): the congruence factor's Newton-Schulz iterations
  * and the final max |(Z Y)_ij - I_ij| (Y -> S^{1/2}, Z -> S^{-1/2}). */
 typedef struct {
-  int status;           /* TB_OK, TB_ERR_NOT_CONVERGED (Z not converged in 40 iterations) */
+  int status;           /* TB_OK, TB_ERR_NOT_CONVERGED (Z not converged in 24 iterations) */
   int ns_iters;
   double ns_residual;
 } tb_nonorth_report;

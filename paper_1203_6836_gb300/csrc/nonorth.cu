@@ -26,7 +26,7 @@
 
 namespace {
 
-constexpr int kMaxNS = 40;     // Newton-Schulz iterations at most
+constexpr int kMaxNS = 24;     // Newton-Schulz iterations at most (about 12 reach 1e-13 for cond(S) = 100)
 constexpr double kNSTol = 1e-13;
 constexpr double kNSFloor = 1e-9;  // below it, a residual that no longer halves is the rounding floor
 constexpr int kK = 16;         // GEMM k-step
