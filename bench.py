@@ -1032,7 +1032,7 @@ def run_serving(args):
 
 def run_nonorth(args):
     """XL-BOMD in the non-orthogonal formulation (App. D.1): 64 H2O-like
-    molecules (192 atoms, n = 384) 3.2 A apart with the overlap recipe, T_e = 0,
+    molecules (192 atoms, n = 384) at 0.1 g/cc with the overlap recipe, T_e = 0,
     rho_perp by tf32x3 SP2 + 2 FP64-exact refinements; per step the FP64
     congruence products (Newton-Schulz for Z, Z H Z, Z rho_perp Z, W) dominate."""
     import numpy as np
@@ -1040,13 +1040,13 @@ def run_nonorth(args):
     from paper_1203_6836_gb300 import tbmd
     from paper_1203_6836_gb300.device import (DeviceSystem, MDState, nonorth_report_to_dict, report_to_dict,
                                               sp2_opts, xl_params)
-    from workloads import XLParams, molecular_water, nonorth_params, thermal_velocities
+    from workloads import XLParams, gapped_vapour, nonorth_params, thermal_velocities
     from oracle import md as omd, nonorth as onon
     ctx = _setup_gpu()
     P = nonorth_params()
     TP = tbmd.tb_params.from_model(P)
     XL = XLParams()
-    s = molecular_water(4, 12.8, seed=3)
+    s = gapped_vapour(64, seed=0)
     M = s.masses(P)
     v0 = thermal_velocities(M, 300.0, seed=100)
     ds = DeviceSystem(s.R, s.types, s.box)
@@ -1108,7 +1108,7 @@ def run_nonorth(args):
     cpu_s = time.perf_counter() - t0
     line = _common(args, "XL-BOMD steps/s, non-orthogonal formulation", 1e3 / per_step, "steps/s", per_step,
                    f"f64 congruence + {args.precision}+f64 SP2",
-                   f"{s.natoms} atoms (64 H2O-like molecules 3.2 A apart, seed 3), n={n}, overlap recipe "
+                   f"{s.natoms} atoms (64 H2O-like molecules, 0.1 g/cc, seed 0), n={n}, overlap recipe "
                    f"(s0 {P.overlap_s0}, rs {P.overlap_rs} A), T_e = 0, kappa0/2, dt {XL.dt} fs",
                    latency_ms={"p50": statistics.median(ms), "p99": _pct(ms, 0.99)},
                    scf_init_iters=scf_it, newton_schulz_iters=nrep["ns_iters"],
