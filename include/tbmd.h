@@ -421,6 +421,63 @@ int tb_forces_nonorth(tb_ctx* ctx, const tb_params* p, const tb_system* sys, con
                       const double* rho, const double* W, const double* q, const double* n_aux,
                       const double* v, const double* gamma, double* F, double* energy, void* stream);
 
+/* ------------------------------- a5 boundary: block-sparse (BSR) matrices (Sec. III.B) */
+
+/* A symmetric n x n matrix stored as 128 x 128 FP64 blocks in block-sparse-row form: the
+ * layout of the thresholded SP2 (linear scaling for spatially ordered systems).  Block
+ * (I, J) (block row I, block column J) sits in slot s with row_ptr[I] <= s < row_ptr[I + 1]
+ * and col[s] = J, columns ascending within a row; its element (r, c) is
+ * val[s * 16384 + r * 128 + c] = M[128 I + r][128 J + c], zero beyond n.  All arrays are
+ * device memory owned by the caller; cap is the capacity in blocks (val holds
+ * cap * 16384 doubles).  A call that would need more than cap blocks writes TB_ERR_OOM to
+ * *status (device int) and leaves the matrix incomplete. */
+#define TB_BSR_BLOCK 128
+typedef struct {
+  int n;          /* order */
+  int nsb;        /* block rows = (n + 127) / 128 */
+  int cap;        /* capacity in blocks */
+  int* row_ptr;   /* [nsb + 1] */
+  int* col;       /* [cap] */
+  double* val;    /* [cap * 16384] */
+  int* status;    /* device int: TB_OK or TB_ERR_OOM */
+} tb_bsr;
+
+/* Scratch of the block-sparse model calls: per block row, the atoms whose orbitals it holds
+ * and their bounding box, and the block pattern. */
+int tb_bsr_model_workspace_size(int natoms, int norb, size_t* bytes);
+
+/* H[n] (a1) in BSR.  The pattern holds block (I, J) when the bounding boxes of the atoms of
+ * block rows I and J (periodic minimum image) come within the model's range
+ * (max(rcut, gamma_cut)), so every atom pair within range lies in a stored block; with the
+ * atoms in spatial (e.g. Morton) order a block row has O(1) blocks and the build is
+ * O(N).  The windowed gamma only (gamma_form 0), orthogonal model only.
+ *   n_aux [N] or NULL; H: BSR output (structure and values); v [N] output, the per-atom SCC
+ *   potential sum_l gamma_il n_l (zero without n_aux), which tb_forces_bsr needs.  The
+ *   workspace (tb_bsr_model_workspace_size) keeps the block-row atom ranges and boxes for
+ *   mulliken_bsr and tb_forces_bsr of the same positions. */
+int tb_build_H_bsr(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const double* R,
+                   const double* n_aux, tb_bsr* H, double* v, void* workspace, size_t workspace_bytes,
+                   void* stream);
+
+/* D = theta(mu0 I - H) by the thresholded block-sparse SP2 (a5; Sec. III.B, opts.tau > 0, a
+ * tensor-core precision) with BSR input and output: X0 from H's blocks, the final iterate's
+ * blocks (FP32 master, stored as FP64) written to D with their structure.  n <= 32768.
+ * Workspace from dm_sp2_workspace_size(n, opts). */
+int dm_sp2_sparse(tb_ctx* ctx, const tb_bsr* H, double n_occ, const tb_sp2_opts* opts, tb_bsr* D,
+                  void* workspace, size_t workspace_bytes, tb_sp2_report* report, void* stream);
+
+/* Mulliken charges (a7) from a BSR D: q_i = 2 sum_{a in i} D_aa - N0_i. */
+int mulliken_bsr(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const tb_bsr* D, double* q,
+                 void* stream);
+
+/* Forces and energy (a8) as tb_forces, with D in BSR: the atom pairs within range are found
+ * through H's block pattern and the workspace of the tb_build_H_bsr call at the same R;
+ * gamma is evaluated on the fly (v from tb_build_H_bsr), so no N x N array is needed.
+ *   F [N*3], energy [4] outputs. */
+int tb_forces_bsr(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const double* R, const tb_bsr* H,
+                  const tb_bsr* D, const double* q, const double* n_aux, const double* v, double* F,
+                  double* energy, const void* workspace, size_t workspace_bytes, void* stream);
+
 /* ------------------------------------------------------------- a7: charges */
 
 /* Mulliken net charges q_i = 2 sum_{a in i} D_aa - N0_i (App. D).
@@ -495,6 +552,13 @@ typedef struct {
   void* nonorth_workspace;    /* dm_nonorth workspace (dm_nonorth_workspace_size) */
   size_t nonorth_workspace_bytes;
   tb_nonorth_report* nonorth_report;  /* device, may be NULL */
+  /* block-sparse boundary (T_e = 0, orthogonal, sp2 opts with tau > 0): when H_bsr is set the
+   * step builds H in BSR, runs dm_sp2_sparse into D_bsr, and takes q, F, E from it; H, D and
+   * gamma may then be NULL (no n x n or N x N array) */
+  tb_bsr* H_bsr;
+  tb_bsr* D_bsr;
+  void* bsr_workspace;        /* tb_bsr_model_workspace_size */
+  size_t bsr_workspace_bytes;
 } tb_md_state;
 
 /* Initial state (App. D.3): SCF-converge the charges with Anderson mixing

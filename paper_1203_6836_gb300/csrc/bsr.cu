@@ -236,6 +236,170 @@ __global__ void __launch_bounds__(256) k_bsr_init_fill(const double* __restrict_
   }
 }
 
+// ---- BSR input (dm_sp2_sparse): H given as 128 x 128 FP64 blocks
+
+// Slot of block (I, J) in a BSR row (binary search over its sorted columns), or -1.
+__device__ __forceinline__ int bsr_find(const int* __restrict__ row_ptr, const int* __restrict__ col, int I, int J) {
+  int lo = row_ptr[I], hi = row_ptr[I + 1] - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int c = col[mid];
+    if (c == J) return mid;
+    if (c < J) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+// Gershgorin partials of block row I (one block of 128 threads, a thread per
+// row): min(H_ii - r_i), max(H_ii + r_i) over the rows into bparts[2 I].
+__global__ void __launch_bounds__(128) k_bsr_bounds_in(tb_bsr H, double* __restrict__ bparts) {
+  __shared__ double smin[4], smax[4];
+  const int I = blockIdx.x, r = threadIdx.x;
+  if (*H.status != TB_OK) {  // an incomplete H (k_bsr_status_in fails the call)
+    if (r == 0) bparts[2 * I] = bparts[2 * I + 1] = 0.0;
+    return;
+  }
+  const int row = I * SB + r;
+  double lo = INFINITY, hi = -INFINITY;
+  if (row < H.n) {
+    double rad = 0.0, c = 0.0;
+    for (int o = H.row_ptr[I]; o < H.row_ptr[I + 1]; ++o) {
+      const double* blk = H.val + (size_t)o * kTiles + (size_t)r * SB;
+      const int J = H.col[o];
+      for (int j = 0; j < SB; ++j) {
+        const double x = blk[j];
+        if (J == I && j == r) c = x;
+        else rad += fabs(x);
+      }
+    }
+    lo = c - rad;
+    hi = c + rad;
+  }
+  lo = warp_min(lo);
+  hi = warp_max(hi);
+  if ((r & 31) == 0) {
+    smin[r >> 5] = lo;
+    smax[r >> 5] = hi;
+  }
+  __syncthreads();
+  if (r == 0) {
+    bparts[2 * I] = fmin(fmin(smin[0], smin[1]), fmin(smin[2], smin[3]));
+    bparts[2 * I + 1] = fmax(fmax(smax[0], smax[1]), fmax(smax[2], smax[3]));
+  }
+}
+
+__device__ __forceinline__ double x0_blk(const double* blk, int I, int J, int n, int r, int c, double emax,
+                                         double inv) {
+  const int gr = I * SB + r, gc = J * SB + c;
+  if (gr >= n || gc >= n) return 0.0;
+  const double h = blk ? blk[(size_t)r * SB + c] : 0.0;
+  return ((gr == gc ? emax : 0.0) - h) * inv;
+}
+
+// As k_bsr_init_flags, from the blocks of a BSR H (an absent block of H is
+// zero in X0 off the diagonal).
+// An H whose build overflowed its capacity fails the call (TB_ERR_OOM).
+__global__ void k_bsr_status_in(const int* Hstatus, SP2State* st) {
+  if (*Hstatus != TB_OK) st->err = TB_ERR_OOM;
+}
+
+__global__ void __launch_bounds__(256) k_bsr_init_flags_in(tb_bsr H, Args a, Sym sy) {
+  __shared__ double sq[16];
+  const int I = blockIdx.y, J = blockIdx.x;
+  if (*H.status != TB_OK) {
+    if (threadIdx.x == 0) sy.flags[(size_t)I * a.nsb + J] = 0;
+    return;
+  }
+  const int slot = bsr_find(H.row_ptr, H.col, I, J);
+  if (slot < 0 && I != J) {
+    if (threadIdx.x == 0) sy.flags[(size_t)I * a.nsb + J] = 0;
+    return;
+  }
+  const double* blk = slot >= 0 ? H.val + (size_t)slot * kTiles : nullptr;
+  if (threadIdx.x < 16) sq[threadIdx.x] = 0.0;
+  __syncthreads();
+  const double emin = a.st->emin, emax = a.st->emax;
+  double w = emax - emin;
+  if (!(w > 0.0)) w = 1.0;
+  const double inv = 1.0 / w;
+  const int r = threadIdx.x >> 1, h = threadIdx.x & 1;
+  double part[2] = {0.0, 0.0};
+  for (int c = 0; c < 64; ++c) {
+    const double x = x0_blk(blk, I, J, a.n, r, 64 * h + c, emax, inv);
+    part[c >> 5] += x * x;
+  }
+  atomicAdd(&sq[(r >> 5) * 4 + 2 * h], part[0]);
+  atomicAdd(&sq[(r >> 5) * 4 + 2 * h + 1], part[1]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint16_t f = 0;
+    for (int s2 = 0; s2 < 16; ++s2)
+      if (sq[s2] >= a.tau2 && sq[s2] > 0.0) f |= (uint16_t)(1u << s2);
+    sy.flags[(size_t)I * a.nsb + J] = f;
+  }
+}
+
+// As k_bsr_init_fill, from the blocks of a BSR H.
+template <int P>
+__global__ void __launch_bounds__(256) k_bsr_init_fill_in(tb_bsr H, Args a, Sym sy, Buf b) {
+  if (a.st->err) return;
+  const int I = blockIdx.x;
+  const double emin = a.st->emin, emax = a.st->emax;
+  double w = emax - emin;
+  if (!(w > 0.0)) w = 1.0;
+  const double inv = 1.0 / w;
+  double t1 = 0.0, t2 = 0.0;
+  int o = b.row_ptr[I];
+  for (int J = 0; J < a.nsb; ++J) {
+    const uint16_t f = sy.flags[(size_t)I * a.nsb + J];
+    if (!f) continue;
+    const int slot = bsr_find(H.row_ptr, H.col, I, J);
+    const double* blk = slot >= 0 ? H.val + (size_t)slot * kTiles : nullptr;
+    if (threadIdx.x == 0) {
+      b.col[o] = J;
+      b.nz[o] = 1;
+    }
+    for (int seg = threadIdx.x; seg < SB * 4; seg += blockDim.x) {
+      const int r = seg >> 2, cs = seg & 3;
+      const bool keep = (f >> ((r >> 5) * 4 + cs)) & 1;
+      float y[32];
+      for (int j = 0; j < 32; ++j) {
+        const double x = keep ? x0_blk(blk, I, J, a.n, r, 32 * cs + j, emax, inv) : 0.0;
+        y[j] = (float)x;
+        const double xf = (double)y[j];
+        t2 += xf * xf;
+        if (I == J && r == 32 * cs + j) t1 += xf;
+      }
+      const size_t e0 = (size_t)o * kTiles + (size_t)r * SB + 32 * cs;
+      float* dst = b.val + e0;
+      for (int j = 0; j < 32; ++j) dst[j] = y[j];
+      char* hp = static_cast<char*>(b.hi) + e0 * Prec<P>::eb;
+      char* lp = b.lo ? static_cast<char*>(b.lo) + e0 * Prec<P>::eb : hp;
+      store_operands<P>(y, hp, lp);
+    }
+    ++o;
+  }
+  __shared__ double s1[8], s2[8];
+  t1 = warp_sum(t1);
+  t2 = warp_sum(t2);
+  if ((threadIdx.x & 31) == 0) {
+    s1[threadIdx.x >> 5] = t1;
+    s2[threadIdx.x >> 5] = t2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0, y = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      x += s1[q];
+      y += s2[q];
+    }
+    a.parts_out[3 * I] = x;
+    a.parts_out[3 * I + 1] = y;
+    a.parts_out[3 * I + 2] = 0.0;
+  }
+}
+
 // ------------------------------------------------------- per projection
 
 // Decision for projection k (every block the same) and the bitmaps of row I
@@ -679,6 +843,27 @@ __global__ void k_bsr_to_dense(const SP2State* st, Args a, Buf b0, Buf b1, Sym s
   }
 }
 
+// Final iterate -> BSR D (structure and FP64 values); TB_ERR_OOM in D.status
+// when it holds more blocks than D.cap.
+__global__ void k_bsr_to_bsr(const SP2State* st, Args a, Buf b0, Buf b1, tb_bsr D) {
+  const Buf& b = (st->iters & 1) ? b1 : b0;
+  const int nblk = min(b.row_ptr[a.nsb], a.cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *D.status = nblk > D.cap ? TB_ERR_OOM : TB_OK;
+  if (nblk > D.cap || st->err) {
+    // an empty matrix: no row holds a block
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= a.nsb; i += gridDim.x * blockDim.x) D.row_ptr[i] = 0;
+    return;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= a.nsb; i += gridDim.x * blockDim.x)
+    D.row_ptr[i] = b.row_ptr[i];
+  for (int o = blockIdx.x; o < nblk; o += gridDim.x) {
+    if (threadIdx.x == 0) D.col[o] = b.col[o];
+    const float* src = b.val + (size_t)o * kTiles;
+    double* dst = D.val + (size_t)o * kTiles;
+    for (int e = threadIdx.x; e < kTiles; e += blockDim.x) dst[e] = (double)src[e];
+  }
+}
+
 __global__ void k_bsr_report(SP2State* st, Args a, Buf b0, Buf b1, tb_sp2_report* rep, int* nblk_out) {
   const Buf& b = (st->iters & 1) ? b1 : b0;
   if (nblk_out) *nblk_out = min(b.row_ptr[a.nsb], a.cap);
@@ -772,9 +957,10 @@ int make_block_map(tb_ctx* ctx, int prec, const void* base, int rows, CUtensorMa
   return TB_OK;
 }
 
+// H dense (Hb null) or BSR (Hb); D dense or BSR (Db).
 template <int P>
-int run_bsr(tb_ctx* ctx, const double* H, int n, double nocc, const tb_sp2_opts* o, double* D, void* ws,
-            size_t ws_bytes, tb_sp2_report* rep, cudaStream_t s) {
+int run_bsr(tb_ctx* ctx, const double* H, const tb_bsr* Hb, int n, double nocc, const tb_sp2_opts* o, double* D,
+            tb_bsr* Db, void* ws, size_t ws_bytes, tb_sp2_report* rep, cudaStream_t s) {
   const BsrLayout L = bsr_layout(n, o->precision, o->bsr_blocks_per_row, ctx->sm_count);
   if (ws_bytes < L.total)
     return tb_fail(ctx, TB_ERR_ARG, "workspace %zu bytes < required %zu (block-sparse)", ws_bytes, L.total);
@@ -835,19 +1021,31 @@ int run_bsr(tb_ctx* ctx, const double* H, int n, double nocc, const tb_sp2_opts*
   }
   ctx->prof_n[0] = ctx->prof_n[1] = 0;
   TB_CUDA_TRY(ctx, cudaMemsetAsync(st, 0, sizeof(SP2State), s));
-  const int nb = (n + 7) / 8;
-  int rc = sp2_launch_bounds(ctx, H, n, bparts, s);
-  if (rc) return rc;
-  k_bsr_bounds<<<1, 32, 0, s>>>(bparts, nb, st);
-  TB_LAUNCH_CHECK(ctx);
-  k_bsr_init_flags<<<dim3(L.nsb, L.nsb), 256, 0, s>>>(H, a, sy);
+  int rc = TB_OK;
+  if (Hb) {
+    k_bsr_status_in<<<1, 1, 0, s>>>(Hb->status, st);
+    TB_LAUNCH_CHECK(ctx);
+    k_bsr_bounds_in<<<L.nsb, 128, 0, s>>>(*Hb, bparts);
+    TB_LAUNCH_CHECK(ctx);
+    k_bsr_bounds<<<1, 32, 0, s>>>(bparts, L.nsb, st);
+    TB_LAUNCH_CHECK(ctx);
+    k_bsr_init_flags_in<<<dim3(L.nsb, L.nsb), 256, 0, s>>>(*Hb, a, sy);
+  } else {
+    const int nb = (n + 7) / 8;
+    rc = sp2_launch_bounds(ctx, H, n, bparts, s);
+    if (rc) return rc;
+    k_bsr_bounds<<<1, 32, 0, s>>>(bparts, nb, st);
+    TB_LAUNCH_CHECK(ctx);
+    k_bsr_init_flags<<<dim3(L.nsb, L.nsb), 256, 0, s>>>(H, a, sy);
+  }
   TB_LAUNCH_CHECK(ctx);
   k_bsr_init_rows<<<L.nsb, 256, 0, s>>>(a, sy, b[0]);
   TB_LAUNCH_CHECK(ctx);
   k_bsr_scan_rows<<<1, 32, 0, s>>>(a, sy, b[0].row_ptr);
   TB_LAUNCH_CHECK(ctx);
   a.parts_out = slot[0];
-  k_bsr_init_fill<P><<<L.nsb, 256, 0, s>>>(H, a, sy, b[0]);
+  if (Hb) k_bsr_init_fill_in<P><<<L.nsb, 256, 0, s>>>(*Hb, a, sy, b[0]);
+  else k_bsr_init_fill<P><<<L.nsb, 256, 0, s>>>(H, a, sy, b[0]);
   TB_LAUNCH_CHECK(ctx);
 
   using Cf = Prec<P>;
@@ -875,8 +1073,12 @@ int run_bsr(tb_ctx* ctx, const double* H, int n, double nocc, const tb_sp2_opts*
     tb_prof_mark(ctx, 1, 2 * k + 1, s);
     tb_prof_mark(ctx, 0, k + 1, s);
   }
-  TB_CUDA_TRY(ctx, cudaMemsetAsync(D, 0, sizeof(double) * (size_t)n * n, s));
-  k_bsr_to_dense<<<std::min(4096, std::max(1, L.cap)), 256, 0, s>>>(st, a, b[0], b[1], sy, sy, D);
+  if (Db) {
+    k_bsr_to_bsr<<<std::min(4096, std::max(1, L.cap)), 256, 0, s>>>(st, a, b[0], b[1], *Db);
+  } else {
+    TB_CUDA_TRY(ctx, cudaMemsetAsync(D, 0, sizeof(double) * (size_t)n * n, s));
+    k_bsr_to_dense<<<std::min(4096, std::max(1, L.cap)), 256, 0, s>>>(st, a, b[0], b[1], sy, sy, D);
+  }
   TB_LAUNCH_CHECK(ctx);
   k_bsr_report<<<1, 1, 0, s>>>(st, a, b[0], b[1], rep, nullptr);
   TB_LAUNCH_CHECK(ctx);
@@ -895,10 +1097,35 @@ int dm_sp2_bsr(tb_ctx* ctx, const double* H, int n, double nocc, const tb_sp2_op
                size_t ws_bytes, tb_sp2_report* rep, cudaStream_t s) {
   if (n > kMaxNsb * SB) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "block-sparse SP2 supports n <= %d", kMaxNsb * SB);
   switch (o->precision) {
-    case TB_PREC_TF32: return run_bsr<TB_PREC_TF32>(ctx, H, n, nocc, o, D, ws, ws_bytes, rep, s);
-    case TB_PREC_TF32X3: return run_bsr<TB_PREC_TF32X3>(ctx, H, n, nocc, o, D, ws, ws_bytes, rep, s);
-    case TB_PREC_BF16: return run_bsr<TB_PREC_BF16>(ctx, H, n, nocc, o, D, ws, ws_bytes, rep, s);
-    case TB_PREC_BF16X3: return run_bsr<TB_PREC_BF16X3>(ctx, H, n, nocc, o, D, ws, ws_bytes, rep, s);
+    case TB_PREC_TF32: return run_bsr<TB_PREC_TF32>(ctx, H, nullptr, n, nocc, o, D, nullptr, ws, ws_bytes, rep, s);
+    case TB_PREC_TF32X3: return run_bsr<TB_PREC_TF32X3>(ctx, H, nullptr, n, nocc, o, D, nullptr, ws, ws_bytes, rep, s);
+    case TB_PREC_BF16: return run_bsr<TB_PREC_BF16>(ctx, H, nullptr, n, nocc, o, D, nullptr, ws, ws_bytes, rep, s);
+    case TB_PREC_BF16X3: return run_bsr<TB_PREC_BF16X3>(ctx, H, nullptr, n, nocc, o, D, nullptr, ws, ws_bytes, rep, s);
+    default: return tb_fail(ctx, TB_ERR_UNSUPPORTED, "block-sparse SP2 needs a tensor-core precision");
+  }
+}
+
+extern "C" int dm_sp2_sparse(tb_ctx* ctx, const tb_bsr* H, double nocc, const tb_sp2_opts* o, tb_bsr* D, void* ws,
+                             size_t ws_bytes, tb_sp2_report* rep, void* stream) {
+  if (!ctx) return TB_ERR_ARG;
+  if (!H || !D || !o || !ws) return tb_fail(ctx, TB_ERR_ARG, "null argument to dm_sp2_sparse");
+  const int n = H->n;
+  if (n < 1 || D->n != n || H->nsb != (n + SB - 1) / SB || D->nsb != H->nsb)
+    return tb_fail(ctx, TB_ERR_ARG, "dm_sp2_sparse: inconsistent BSR sizes");
+  if (!H->row_ptr || !H->col || !H->val || !D->row_ptr || !D->col || !D->val || !D->status)
+    return tb_fail(ctx, TB_ERR_ARG, "dm_sp2_sparse: null BSR array");
+  if (!(o->tau > 0.0)) return tb_fail(ctx, TB_ERR_ARG, "dm_sp2_sparse needs tau > 0");
+  if (n > kMaxNsb * SB) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "block-sparse SP2 supports n <= %d", kMaxNsb * SB);
+  if (!(nocc >= 0.0) || nocc > n) return tb_fail(ctx, TB_ERR_ARG, "n_occ %g outside [0, n]", nocc);
+  if (o->max_iter < 1 || o->max_iter > SP2_MAX_ITER)
+    return tb_fail(ctx, TB_ERR_ARG, "max_iter %d outside 1..%d", o->max_iter, SP2_MAX_ITER);
+  if ((reinterpret_cast<uintptr_t>(ws) & 1023) != 0) return tb_fail(ctx, TB_ERR_ARG, "workspace must be 1024-byte aligned");
+  cudaStream_t s = as_stream(stream);
+  switch (o->precision) {
+    case TB_PREC_TF32: return run_bsr<TB_PREC_TF32>(ctx, nullptr, H, n, nocc, o, nullptr, D, ws, ws_bytes, rep, s);
+    case TB_PREC_TF32X3: return run_bsr<TB_PREC_TF32X3>(ctx, nullptr, H, n, nocc, o, nullptr, D, ws, ws_bytes, rep, s);
+    case TB_PREC_BF16: return run_bsr<TB_PREC_BF16>(ctx, nullptr, H, n, nocc, o, nullptr, D, ws, ws_bytes, rep, s);
+    case TB_PREC_BF16X3: return run_bsr<TB_PREC_BF16X3>(ctx, nullptr, H, n, nocc, o, nullptr, D, ws, ws_bytes, rep, s);
     default: return tb_fail(ctx, TB_ERR_UNSUPPORTED, "block-sparse SP2 needs a tensor-core precision");
   }
 }

@@ -123,9 +123,13 @@ __global__ void k_fill_hist(int N, int S, const double* __restrict__ q, double* 
 int check_state(tb_ctx* ctx, const tb_md_state* st, const tb_xl_params* xp, const tb_sp2_opts* so) {
   if (!st || !xp || !so) return tb_fail(ctx, TB_ERR_ARG, "null state/params/options");
   if (xp->K < 1 || xp->K > TB_XL_KMAX) return tb_fail(ctx, TB_ERR_ARG, "K = %d outside 1..%d", xp->K, TB_XL_KMAX);
-  if (!st->R || !st->v || !st->F || !st->mass || !st->n_hist || !st->q || !st->H || !st->D || !st->gamma ||
-      !st->energies || !st->workspace)
+  const bool bsr = st->H_bsr != nullptr;
+  if (!st->R || !st->v || !st->F || !st->mass || !st->n_hist || !st->q || !st->energies || !st->workspace ||
+      (!bsr && (!st->H || !st->D || !st->gamma)))
     return tb_fail(ctx, TB_ERR_ARG, "null array in tb_md_state");
+  if (bsr && (!st->D_bsr || !st->vscc || !st->bsr_workspace || st->kT > 0.0 || !(so->tau > 0.0)))
+    return tb_fail(ctx, TB_ERR_ARG,
+                   "the block-sparse state needs D_bsr, vscc, bsr_workspace, kT = 0 and sp2 opts with tau > 0");
   if (!(xp->dt > 0)) return tb_fail(ctx, TB_ERR_ARG, "dt must be > 0");
   if (st->kT > 0.0 && !st->mu) return tb_fail(ctx, TB_ERR_ARG, "kT > 0 needs the device mu");
   return TB_OK;
@@ -143,13 +147,17 @@ int check_nonorth(tb_ctx* ctx, const tb_params* p, const tb_md_state* st) {
   return TB_OK;
 }
 
-// H[n] (and S, v in the non-orthogonal formulation).
+// H[n] (and S, v in the non-orthogonal formulation; v with the block-sparse state).
 int build_H_any(tb_ctx* ctx, const tb_params* p, tb_md_state* st, const double* n_aux, cudaStream_t s) {
+  if (st->H_bsr)
+    return tb_build_H_bsr(ctx, p, &st->sys, st->R, n_aux, st->H_bsr, st->vscc, st->bsr_workspace,
+                          st->bsr_workspace_bytes, s);
   if (nonorth_on(p)) return tb_build_HS(ctx, p, &st->sys, st->R, n_aux, st->H, st->S, st->gamma, st->vscc, s);
   return tb_build_H(ctx, p, &st->sys, st->R, n_aux, st->H, st->gamma, s);
 }
 
 int charges_any(tb_ctx* ctx, const tb_params* p, tb_md_state* st, cudaStream_t s) {
+  if (st->H_bsr) return mulliken_bsr(ctx, p, &st->sys, st->D_bsr, st->q, s);
   if (nonorth_on(p)) return mulliken_nonorth(ctx, p, &st->sys, st->D, st->S, st->q, s);
   return mulliken(ctx, p, &st->sys, st->D, st->q, s);
 }
@@ -159,6 +167,9 @@ bool entropy_on(const tb_md_state* st) { return st->kT > 0.0 && st->entropy_work
 // D from H: Fermi operator (dm_fermi, mu carried in st->mu) when kT > 0, else
 // the T_e = 0 projector by SP2.
 int density(tb_ctx* ctx, const tb_params* p, tb_md_state* st, const tb_sp2_opts* so, cudaStream_t s) {
+  if (st->H_bsr)
+    return dm_sp2_sparse(ctx, st->H_bsr, st->n_occ, so, st->D_bsr, st->workspace, st->workspace_bytes,
+                         st->sp2_report, s);
   if (nonorth_on(p))
     return dm_nonorth(ctx, st->H, st->S, st->sys.norb, st->n_occ, st->kT, so, &st->fermi, st->mu, st->D, st->W,
                       st->nonorth_workspace, st->nonorth_workspace_bytes, st->sp2_report, st->fermi_report,
@@ -185,6 +196,9 @@ int electronic_step(tb_ctx* ctx, const tb_params* p, tb_md_state* st, const tb_s
   }
   rc = charges_any(ctx, p, st, s);
   if (rc) return rc;
+  if (st->H_bsr)
+    return tb_forces_bsr(ctx, p, &st->sys, st->R, st->H_bsr, st->D_bsr, st->q, n_aux, st->vscc, st->F,
+                         st->energies + 1, st->bsr_workspace, st->bsr_workspace_bytes, s);
   if (nonorth_on(p))
     return tb_forces_nonorth(ctx, p, &st->sys, st->R, st->D, st->W, st->q, n_aux, st->vscc, st->gamma, st->F,
                              st->energies + 1, s);

@@ -688,17 +688,17 @@ extern "C" int mulliken(tb_ctx* ctx, const tb_params* p, const tb_system* sys, c
 //   Eblk = -V D_ss + V u.l + 2V l^T P l - V tr P
 //   g = -V' D_ss l + V (u - (u.l) l)/r + V' (u.l) l
 //       + 2V (S l - (l^T S l) l)/r + V' (l^T S l) l - V' tr(P) l
-__device__ __forceinline__ void band_pair(int ta, int tb, const double* __restrict__ D, int n,
-                                          int oa, int ob, const double l[3], double r, double V,
-                                          double dV, double* Eblk, double g[3]) {
-  const double Dss = D[(size_t)oa * n + ob];
+template <class Get>
+__device__ __forceinline__ void band_pair_g(int ta, int tb, Get Dg, const double l[3], double r, double V,
+                                            double dV, double* Eblk, double g[3]) {
+  const double Dss = Dg(0, 0);
   double u[3] = {0.0, 0.0, 0.0};
   if (tb == TB_TYPE_O)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) u[c] += D[(size_t)oa * n + ob + 1 + c];
+    for (int c = 0; c < 3; ++c) u[c] += Dg(0, 1 + c);
   if (ta == TB_TYPE_O)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) u[c] -= D[(size_t)(oa + 1 + c) * n + ob];
+    for (int c = 0; c < 3; ++c) u[c] -= Dg(1 + c, 0);
   const double ul = u[0] * l[0] + u[1] * l[1] + u[2] * l[2];
   double E = -V * Dss + V * ul;
 #pragma unroll
@@ -708,7 +708,7 @@ __device__ __forceinline__ void band_pair(int ta, int tb, const double* __restri
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int e = 0; e < 3; ++e) P[c][e] = D[(size_t)(oa + 1 + c) * n + ob + 1 + e];
+      for (int e = 0; e < 3; ++e) P[c][e] = Dg(1 + c, 1 + e);
     const double trP = P[0][0] + P[1][1] + P[2][2];
     double Sl[3];
 #pragma unroll
@@ -720,6 +720,13 @@ __device__ __forceinline__ void band_pair(int ta, int tb, const double* __restri
     for (int k = 0; k < 3; ++k) g[k] += 2.0 * V * (Sl[k] - lSl * l[k]) / r + dV * lSl * l[k] - dV * trP * l[k];
   }
   *Eblk = E;
+}
+
+// The same for the (a, b) block of a dense row-major D.
+__device__ __forceinline__ void band_pair(int ta, int tb, const double* __restrict__ D, int n,
+                                          int oa, int ob, const double l[3], double r, double V,
+                                          double dV, double* Eblk, double g[3]) {
+  band_pair_g(ta, tb, [&](int x, int y) { return D[(size_t)(oa + x) * n + ob + y]; }, l, r, V, dV, Eblk, g);
 }
 
 // One warp per atom a; lanes sweep all atoms b and their images.
@@ -906,5 +913,504 @@ extern "C" int tb_forces_nonorth(tb_ctx* ctx, const tb_params* p, const tb_syste
     k_forces_ewald<<<(N + 7) / 8, 256, 0, s>>>(m, N, R, q, n_aux, F);
     TB_LAUNCH_CHECK(ctx);
   }
+  return TB_OK;
+}
+
+// --------------------------------------------------------------------------
+// a5 boundary: H, Mulliken charges and forces with block-sparse (BSR) matrices
+// --------------------------------------------------------------------------
+//
+// Block row I holds orbitals [128 I, 128 I + 128); its atoms are those with an
+// orbital there (an atom's orbitals may straddle two block rows).  The pattern
+// of H stores block (I, J) when the bounding boxes of the two rows' atoms come
+// within the model's range under the periodic minimum image, so every atom
+// pair within range lies in a stored block; the atom pairs of a block are
+// found from the two atom ranges, and the neighbours of an atom from its block
+// row's stored columns.
+
+namespace {
+
+constexpr int kBB = 128;  // BSR block side (TB_BSR_BLOCK)
+
+struct BsrModelWs {
+  int* atom_lo;      // [nsb]
+  int* atom_hi;      // [nsb] (exclusive)
+  double* bbox;      // [nsb * 6]: centre xyz, half-extent xyz
+  uint8_t* flags;    // [nsb * nsb]
+  int* cnt;          // [nsb]
+};
+
+size_t bsr_model_bytes(int N, int nsb, BsrModelWs* w, void* base) {
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    const size_t r = o;
+    o += (b + 255) / 256 * 256;
+    return r;
+  };
+  const size_t a = take(sizeof(int) * nsb), b = take(sizeof(int) * nsb), c = take(sizeof(double) * 6 * nsb),
+               d = take((size_t)nsb * nsb), e = take(sizeof(int) * nsb);
+  (void)N;
+  if (w && base) {
+    char* p = static_cast<char*>(base);
+    w->atom_lo = reinterpret_cast<int*>(p + a);
+    w->atom_hi = reinterpret_cast<int*>(p + b);
+    w->bbox = reinterpret_cast<double*>(p + c);
+    w->flags = reinterpret_cast<uint8_t*>(p + d);
+    w->cnt = reinterpret_cast<int*>(p + e);
+  }
+  return o;
+}
+
+__device__ __forceinline__ int bsr_slot(const int* __restrict__ row_ptr, const int* __restrict__ col, int I, int J) {
+  int lo = row_ptr[I], hi = row_ptr[I + 1] - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int c = col[mid];
+    if (c == J) return mid;
+    if (c < J) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+// Element (r, c) of a BSR matrix (0 where no block is stored).
+__device__ __forceinline__ double bsr_get(const tb_bsr& M, int r, int c) {
+  const int s = bsr_slot(M.row_ptr, M.col, r / kBB, c / kBB);
+  return s < 0 ? 0.0 : M.val[(size_t)s * kBB * kBB + (size_t)(r % kBB) * kBB + (c % kBB)];
+}
+
+// First atom with an orbital at or after orbital a: offs[i + 1] > a.
+__device__ __forceinline__ int atom_from(const int32_t* offs, int N, int a) {
+  int lo = 0, hi = N;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (offs[mid + 1] > a) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+__global__ void k_blk_atoms(int N, int n, int nsb, const int32_t* __restrict__ offs, BsrModelWs w) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nsb) return;
+  const int r0 = I * kBB, r1 = min(n, r0 + kBB);
+  w.atom_lo[I] = atom_from(offs, N, r0);
+  w.atom_hi[I] = atom_from(offs, N, r1);  // first atom starting at or after r1 ... below
+  // atoms with an orbital in [r0, r1): offs[i + 1] > r0 and offs[i] < r1
+  int hi = w.atom_hi[I];
+  while (hi < N && offs[hi] < r1) ++hi;
+  w.atom_hi[I] = hi;
+}
+
+// Bounding box of block row I's atoms in the minimum-image frame of its first atom.
+__global__ void __launch_bounds__(128) k_blk_box(ModelDev m, const double* __restrict__ R, int nsb, BsrModelWs w) {
+  __shared__ double red[6][4];
+  const int I = blockIdx.x;
+  const int lo = w.atom_lo[I], hi = w.atom_hi[I];
+  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  const double* R0 = R + 3 * lo;
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    double d[3];
+    min_image(R0, R + 3 * i, m.box, d);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      mn[k] = fmin(mn[k], d[k]);
+      mx[k] = fmax(mx[k], d[k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    mn[k] = warp_min(mn[k]);
+    mx[k] = warp_max(mx[k]);
+  }
+  if ((threadIdx.x & 31) == 0)
+    for (int k = 0; k < 3; ++k) {
+      red[k][threadIdx.x >> 5] = mn[k];
+      red[3 + k][threadIdx.x >> 5] = mx[k];
+    }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) {
+      const double a = fmin(fmin(red[k][0], red[k][1]), fmin(red[k][2], red[k][3]));
+      const double b = fmax(fmax(red[3 + k][0], red[3 + k][1]), fmax(red[3 + k][2], red[3 + k][3]));
+      const double ok = hi > lo;
+      w.bbox[6 * I + k] = ok ? R0[k] + 0.5 * (a + b) : 0.0;
+      w.bbox[6 * I + 3 + k] = ok ? 0.5 * (b - a) : 0.0;
+    }
+  }
+}
+
+// flags[I][J] = 1 when the boxes of rows I and J come within `range` (periodic
+// minimum image per axis; an axis whose boxes and range span half the box or
+// more is not used to exclude).
+__global__ void k_blk_pattern(ModelDev m, int nsb, BsrModelWs w) {
+  const int I = blockIdx.x;
+  for (int J = threadIdx.x; J < nsb; J += blockDim.x) {
+    double g2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      double dc = w.bbox[6 * J + k] - w.bbox[6 * I + k];
+      dc -= m.box * rint(dc / m.box);
+      const double hs = w.bbox[6 * I + 3 + k] + w.bbox[6 * J + 3 + k];
+      if (hs + m.range >= 0.5 * m.box) continue;
+      const double gap = fmax(0.0, fabs(dc) - hs);
+      g2 += gap * gap;
+    }
+    w.flags[(size_t)I * nsb + J] = (I == J || g2 < m.range * m.range) ? 1 : 0;
+  }
+}
+
+__global__ void k_blk_count(int nsb, BsrModelWs w) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nsb) return;
+  int c = 0;
+  for (int J = 0; J < nsb; ++J) c += w.flags[(size_t)I * nsb + J];
+  w.cnt[I] = c;
+}
+
+// row_ptr by a serial scan, OOM status, then each row's columns in order.
+__global__ void k_blk_scan(int nsb, BsrModelWs w, tb_bsr H) {
+  if (threadIdx.x != 0) return;
+  int s = 0;
+  for (int I = 0; I < nsb; ++I) {
+    H.row_ptr[I] = s;
+    s += w.cnt[I];
+  }
+  H.row_ptr[nsb] = s;
+  *H.status = s > H.cap ? TB_ERR_OOM : TB_OK;
+}
+
+__global__ void k_blk_cols(int nsb, BsrModelWs w, tb_bsr H) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nsb || *H.status != TB_OK) return;
+  int o = H.row_ptr[I];
+  for (int J = 0; J < nsb; ++J)
+    if (w.flags[(size_t)I * nsb + J]) H.col[o++] = J;
+}
+
+// The h elements of stored block o (one CTA per block, grid-stride): every
+// ordered atom pair (i, j) of the two rows, summed over the images within the
+// cut-off, onsite energies for i == j; each element belongs to one pair.
+__global__ void __launch_bounds__(256) k_h_blocks(ModelDev m, int N, const int32_t* __restrict__ types,
+                                                  const int32_t* __restrict__ offs, const double* __restrict__ R,
+                                                  BsrModelWs w, tb_bsr H) {
+  if (*H.status != TB_OK) return;
+  const int nblk = H.row_ptr[H.nsb];
+  for (int o = blockIdx.x; o < nblk; o += gridDim.x) {
+    int lo = 0, hi = H.nsb;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (H.row_ptr[mid] <= o) lo = mid;
+      else hi = mid;
+    }
+    const int I = lo, J = H.col[o];
+    double* blk = H.val + (size_t)o * kBB * kBB;
+    for (int e = threadIdx.x; e < kBB * kBB; e += blockDim.x) blk[e] = 0.0;
+    __syncthreads();
+    const int ilo = w.atom_lo[I], ihi = w.atom_hi[I], jlo = w.atom_lo[J], jhi = w.atom_hi[J];
+    const int nj = jhi - jlo, npair = (ihi - ilo) * nj;
+    const int r0 = I * kBB, c0 = J * kBB;
+    for (int p = threadIdx.x; p < npair; p += blockDim.x) {
+      const int i = ilo + p / nj, j = jlo + p % nj;
+      const int ti = types[i], tj = types[j];
+      const int ni = norb_of(ti), njo = norb_of(tj);
+      const int oi = offs[i], oj = offs[j];
+      double B[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) B[a][b] = 0.0;
+      const double* Ri = R + 3 * i;
+      const double* Rj = R + 3 * j;
+      if (i == j || screen_f32(Ri, Rj, (float)m.box, (float)m.rcut)) {
+        double d0[3];
+        min_image(Ri, Rj, m.box, d0);
+        int lo3[3], hi3[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) image_range(d0[c], m.box, m.rcut, &lo3[c], &hi3[c]);
+        for (int kx = lo3[0]; kx <= hi3[0]; ++kx)
+          for (int ky = lo3[1]; ky <= hi3[1]; ++ky)
+            for (int kz = lo3[2]; kz <= hi3[2]; ++kz) {
+              if (i == j && kx == 0 && ky == 0 && kz == 0) continue;
+              const double d[3] = {d0[0] + kx * m.box, d0[1] + ky * m.box, d0[2] + kz * m.box};
+              const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+              if (r >= m.rcut) continue;
+              double V, dV;
+              hop_radial(m, r, &V, &dV);
+              const double l[3] = {d[0] / r, d[1] / r, d[2] / r};
+              double Bi[4][4];
+              sk_block(ti, tj, l, V, Bi);
+              for (int a = 0; a < ni; ++a)
+                for (int b = 0; b < njo; ++b) B[a][b] += Bi[a][b];
+            }
+      }
+      if (i == j) {
+        if (ti == TB_TYPE_O) {
+          B[0][0] += m.eps_s_O;
+          B[1][1] += m.eps_p_O;
+          B[2][2] += m.eps_p_O;
+          B[3][3] += m.eps_p_O;
+        } else {
+          B[0][0] += m.eps_s_H;
+        }
+      }
+      for (int a = 0; a < ni; ++a) {
+        const int r = oi + a - r0;
+        if (r < 0 || r >= kBB) continue;
+        for (int b = 0; b < njo; ++b) {
+          const int c = oj + b - c0;
+          if (c < 0 || c >= kBB) continue;
+          blk[(size_t)r * kBB + c] = B[a][b];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Visit the atoms of the stored block columns of row I once each (consecutive
+// block rows share at most their straddling atom): fn(j).
+template <class Fn>
+__device__ __forceinline__ void for_neighbour_atoms(const tb_bsr& H, const BsrModelWs& w, int I, int lane, Fn fn) {
+  int next = 0;
+  for (int s = H.row_ptr[I]; s < H.row_ptr[I + 1]; ++s) {
+    const int J = H.col[s];
+    const int lo = max(next, w.atom_lo[J]), hi = w.atom_hi[J];
+    for (int j = lo + lane; j < hi; j += 32) fn(j);
+    next = max(next, hi);
+  }
+}
+
+// v_i = sum_l gamma_il n_l over the atoms within range (windowed gamma, its
+// on-site U and the self-images): one warp per atom.
+__global__ void __launch_bounds__(256) k_v_bsr(ModelDev m, int N, const int32_t* __restrict__ offs,
+                                               const double* __restrict__ R, const double* __restrict__ n_aux,
+                                               tb_bsr H, BsrModelWs w, double* __restrict__ v) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= N || *H.status != TB_OK) return;  // an overflowed pattern has no columns to visit
+  const double* Ri = R + 3 * i;
+  double s = 0.0;
+  for_neighbour_atoms(H, w, offs[i] / kBB, lane, [&](int j) {
+    const double* Rj = R + 3 * j;
+    if (j != i && !screen_f32(Ri, Rj, (float)m.box, (float)m.gcut)) return;
+    double d0[3];
+    min_image(Ri, Rj, m.box, d0);
+    int lo3[3], hi3[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) image_range(d0[c], m.box, m.gcut, &lo3[c], &hi3[c]);
+    double g = 0.0;
+    for (int kx = lo3[0]; kx <= hi3[0]; ++kx)
+      for (int ky = lo3[1]; ky <= hi3[1]; ++ky)
+        for (int kz = lo3[2]; kz <= hi3[2]; ++kz) {
+          if (j == i && kx == 0 && ky == 0 && kz == 0) continue;
+          const double d[3] = {d0[0] + kx * m.box, d0[1] + ky * m.box, d0[2] + kz * m.box};
+          const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+          if (r >= m.gcut) continue;
+          double gg, dgg;
+          gamma_radial(m, r, &gg, &dgg);
+          g += gg;
+        }
+    s += g * n_aux[j];
+  });
+  s = warp_sum(s);
+  if (lane == 0) v[i] = s + m.U * n_aux[i];
+}
+
+// H_aa += v_i on every orbital a of atom i.
+__global__ void k_shift_bsr(int N, const int32_t* __restrict__ offs, const double* __restrict__ v, tb_bsr H) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N || *H.status != TB_OK) return;
+  for (int a = offs[i]; a < offs[i + 1]; ++a) {
+    const int s = bsr_slot(H.row_ptr, H.col, a / kBB, a / kBB);
+    if (s >= 0) H.val[(size_t)s * kBB * kBB + (size_t)(a % kBB) * (kBB + 1)] += v[i];
+  }
+}
+
+__global__ void k_mulliken_bsr(int N, const int32_t* __restrict__ types, const int32_t* __restrict__ offs, tb_bsr D,
+                               double n0_O, double n0_H, double* __restrict__ q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N || *D.status != TB_OK) return;
+  double pop = 0.0;
+  for (int a = offs[i]; a < offs[i + 1]; ++a) pop += bsr_get(D, a, a);
+  q[i] = 2.0 * pop - (types[i] == TB_TYPE_O ? n0_O : n0_H);
+}
+
+// As k_forces, with D read from BSR and the neighbours from H's pattern.
+__global__ void __launch_bounds__(32) k_forces_bsr(ModelDev m, int N, const int32_t* __restrict__ types,
+                                                   const int32_t* __restrict__ offs, const double* __restrict__ R,
+                                                   tb_bsr H, tb_bsr D, BsrModelWs w, const double* __restrict__ q,
+                                                   const double* __restrict__ n_aux, const double* __restrict__ v,
+                                                   double* __restrict__ F, double* __restrict__ energy) {
+  const int a = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  if (a >= N || *H.status != TB_OK || *D.status != TB_OK) return;
+  const double* Ra = R + 3 * a;
+  const int ta = types[a], oa = offs[a];
+  const double wa = 2.0 * q[a] - n_aux[a];
+  const double na = n_aux[a];
+  double f[3] = {0.0, 0.0, 0.0};
+  double e_band = 0.0, e_pair = 0.0;
+  for_neighbour_atoms(H, w, oa / kBB, lane, [&](int b) {
+    const double* Rb = R + 3 * b;
+    if (b != a && !screen_f32(Ra, Rb, (float)m.box, (float)m.range)) return;
+    const int tb = types[b], ob = offs[b];
+    const double wb = 2.0 * q[b] - n_aux[b];
+    const double nb = n_aux[b];
+    double Dl[4][4];
+    const int nra = norb_of(ta), nrb = norb_of(tb);
+    for (int x = 0; x < 4; ++x)
+      for (int y = 0; y < 4; ++y) Dl[x][y] = (x < nra && y < nrb) ? bsr_get(D, oa + x, ob + y) : 0.0;
+    double d0[3];
+    min_image(Ra, Rb, m.box, d0);
+    int lo3[3], hi3[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) image_range(d0[c], m.box, m.range, &lo3[c], &hi3[c]);
+    for (int kx = lo3[0]; kx <= hi3[0]; ++kx)
+      for (int ky = lo3[1]; ky <= hi3[1]; ++ky)
+        for (int kz = lo3[2]; kz <= hi3[2]; ++kz) {
+          if (b == a && kx == 0 && ky == 0 && kz == 0) continue;
+          const double d[3] = {d0[0] + kx * m.box, d0[1] + ky * m.box, d0[2] + kz * m.box};
+          const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+          if (r >= m.range) continue;
+          const double l[3] = {d[0] / r, d[1] / r, d[2] / r};
+          if (r < m.rcut) {
+            double V, dV, Eblk, g[3];
+            hop_radial(m, r, &V, &dV);
+            band_pair_g(ta, tb, [&](int x, int y) { return Dl[x][y]; }, l, r, V, dV, &Eblk, g);
+            e_band += 2.0 * Eblk;
+            if (b != a)
+#pragma unroll
+              for (int k = 0; k < 3; ++k) f[k] += 4.0 * g[k];
+            double ph, dph;
+            pair_radial(m, r, &ph, &dph);
+            e_pair += 0.5 * ph;
+            if (b != a)
+#pragma unroll
+              for (int k = 0; k < 3; ++k) f[k] += dph * l[k];
+          }
+          if (b != a) {
+            double gg, dgg;
+            gamma_radial(m, r, &gg, &dgg);
+            const double c = 0.5 * (wa * nb + wb * na) * dgg;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) f[k] += c * l[k];
+          }
+        }
+  });
+#pragma unroll
+  for (int k = 0; k < 3; ++k) f[k] = warp_sum(f[k]);
+  e_band = warp_sum(e_band);
+  e_pair = warp_sum(e_pair);
+  if (lane == 0) {
+    if (ta == TB_TYPE_O) {
+      e_band += 2.0 * (m.eps_s_O * bsr_get(D, oa, oa) +
+                       m.eps_p_O * (bsr_get(D, oa + 1, oa + 1) + bsr_get(D, oa + 2, oa + 2) + bsr_get(D, oa + 3, oa + 3)));
+    } else {
+      e_band += 2.0 * m.eps_s_H * bsr_get(D, oa, oa);
+    }
+    const double e_scc = 0.5 * wa * v[a];
+    F[3 * a + 0] = f[0];
+    F[3 * a + 1] = f[1];
+    F[3 * a + 2] = f[2];
+    atomicAdd(&energy[1], e_band);
+    atomicAdd(&energy[2], e_scc);
+    atomicAdd(&energy[3], e_pair);
+    atomicAdd(&energy[0], e_band + e_scc + e_pair);
+  }
+}
+
+int bsr_check(tb_ctx* ctx, const tb_bsr* M, int n, const char* what) {
+  if (!M || !M->row_ptr || !M->col || !M->val || !M->status)
+    return tb_fail(ctx, TB_ERR_ARG, "%s: null BSR array", what);
+  if (M->n != n || M->nsb != (n + kBB - 1) / kBB || M->cap < 1)
+    return tb_fail(ctx, TB_ERR_ARG, "%s: BSR sizes (n %d, nsb %d, cap %d) do not fit n = %d", what, M->n, M->nsb,
+                   M->cap, n);
+  return TB_OK;
+}
+
+}  // namespace
+
+extern "C" int tb_bsr_model_workspace_size(int natoms, int norb, size_t* bytes) {
+  if (natoms < 1 || norb < 1 || !bytes) return TB_ERR_ARG;
+  *bytes = bsr_model_bytes(natoms, (norb + kBB - 1) / kBB, nullptr, nullptr);
+  return TB_OK;
+}
+
+extern "C" int tb_build_H_bsr(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const double* R,
+                              const double* n_aux, tb_bsr* H, double* v, void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx) return TB_ERR_ARG;
+  int rc = check_system(ctx, sys);
+  if (rc) return rc;
+  if (!R || !v || !ws) return tb_fail(ctx, TB_ERR_ARG, "null argument to tb_build_H_bsr");
+  if ((rc = bsr_check(ctx, H, sys->norb, "tb_build_H_bsr"))) return rc;
+  ModelDev m;
+  rc = tb_model_from_params(ctx, p, sys->box, &m);
+  if (rc) return rc;
+  if (m.gamma_form != 0) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "tb_build_H_bsr needs the windowed gamma");
+  if (m.s0 != 0.0) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "tb_build_H_bsr: orthogonal model only");
+  const int N = sys->natoms, n = sys->norb, nsb = H->nsb;
+  BsrModelWs w;
+  if (ws_bytes < bsr_model_bytes(N, nsb, &w, ws)) return tb_fail(ctx, TB_ERR_ARG, "tb_build_H_bsr: workspace too small");
+  cudaStream_t s = as_stream(stream);
+  k_blk_atoms<<<(nsb + 127) / 128, 128, 0, s>>>(N, n, nsb, sys->orb_off, w);
+  TB_LAUNCH_CHECK(ctx);
+  k_blk_box<<<nsb, 128, 0, s>>>(m, R, nsb, w);
+  TB_LAUNCH_CHECK(ctx);
+  k_blk_pattern<<<nsb, 256, 0, s>>>(m, nsb, w);
+  TB_LAUNCH_CHECK(ctx);
+  k_blk_count<<<(nsb + 127) / 128, 128, 0, s>>>(nsb, w);
+  TB_LAUNCH_CHECK(ctx);
+  k_blk_scan<<<1, 32, 0, s>>>(nsb, w, *H);
+  TB_LAUNCH_CHECK(ctx);
+  k_blk_cols<<<(nsb + 127) / 128, 128, 0, s>>>(nsb, w, *H);
+  TB_LAUNCH_CHECK(ctx);
+  k_h_blocks<<<std::min(H->cap, 4096), 256, 0, s>>>(m, N, sys->types, sys->orb_off, R, w, *H);
+  TB_LAUNCH_CHECK(ctx);
+  if (n_aux) {
+    k_v_bsr<<<(N * 32 + 255) / 256, 256, 0, s>>>(m, N, sys->orb_off, R, n_aux, *H, w, v);
+    TB_LAUNCH_CHECK(ctx);
+    k_shift_bsr<<<(N + 127) / 128, 128, 0, s>>>(N, sys->orb_off, v, *H);
+  } else {
+    TB_CUDA_TRY(ctx, cudaMemsetAsync(v, 0, sizeof(double) * N, s));
+  }
+  TB_LAUNCH_CHECK(ctx);
+  return TB_OK;
+}
+
+extern "C" int mulliken_bsr(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const tb_bsr* D, double* q,
+                            void* stream) {
+  if (!ctx) return TB_ERR_ARG;
+  int rc = check_system(ctx, sys);
+  if (rc) return rc;
+  if (!p || !q) return tb_fail(ctx, TB_ERR_ARG, "null argument to mulliken_bsr");
+  if ((rc = bsr_check(ctx, D, sys->norb, "mulliken_bsr"))) return rc;
+  const int N = sys->natoms;
+  k_mulliken_bsr<<<(N + 127) / 128, 128, 0, as_stream(stream)>>>(N, sys->types, sys->orb_off, *D, p->n0_O, p->n0_H, q);
+  TB_LAUNCH_CHECK(ctx);
+  return TB_OK;
+}
+
+extern "C" int tb_forces_bsr(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const double* R, const tb_bsr* H,
+                             const tb_bsr* D, const double* q, const double* n_aux, const double* v, double* F,
+                             double* energy, const void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx) return TB_ERR_ARG;
+  int rc = check_system(ctx, sys);
+  if (rc) return rc;
+  if (!R || !q || !n_aux || !v || !F || !energy || !ws) return tb_fail(ctx, TB_ERR_ARG, "null argument to tb_forces_bsr");
+  if ((rc = bsr_check(ctx, H, sys->norb, "tb_forces_bsr (H)"))) return rc;
+  if ((rc = bsr_check(ctx, D, sys->norb, "tb_forces_bsr (D)"))) return rc;
+  ModelDev m;
+  rc = tb_model_from_params(ctx, p, sys->box, &m);
+  if (rc) return rc;
+  if (m.gamma_form != 0 || m.s0 != 0.0)
+    return tb_fail(ctx, TB_ERR_UNSUPPORTED, "tb_forces_bsr: windowed gamma, orthogonal model only");
+  const int N = sys->natoms;
+  BsrModelWs w;
+  if (ws_bytes < bsr_model_bytes(N, H->nsb, &w, const_cast<void*>(ws)))
+    return tb_fail(ctx, TB_ERR_ARG, "tb_forces_bsr: workspace too small");
+  cudaStream_t s = as_stream(stream);
+  TB_CUDA_TRY(ctx, cudaMemsetAsync(energy, 0, 4 * sizeof(double), s));
+  k_forces_bsr<<<N, 32, 0, s>>>(m, N, sys->types, sys->orb_off, R, *H, *D, w, q, n_aux, v, F, energy);
+  TB_LAUNCH_CHECK(ctx);
   return TB_OK;
 }

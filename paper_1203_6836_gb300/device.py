@@ -93,13 +93,45 @@ class DensitySolver:
         return D
 
 
+class BsrMatrix:
+    """A tb_bsr (128 x 128 FP64 blocks) with device arrays of `cap` blocks."""
+
+    B = 128
+
+    def __init__(self, n: int, cap: int, device="cuda"):
+        nsb = (n + self.B - 1) // self.B
+        self.n, self.nsb, self.cap = int(n), nsb, int(cap)
+        self.row_ptr = torch.zeros(nsb + 1, dtype=torch.int32, device=device)
+        self.col = torch.zeros(max(1, cap), dtype=torch.int32, device=device)
+        self.val = torch.zeros(max(1, cap) * self.B * self.B, dtype=torch.float64, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.mat = tbmd.tb_bsr(n=self.n, nsb=nsb, cap=self.cap, row_ptr=self.row_ptr.data_ptr(),
+                               col=self.col.data_ptr(), val=self.val.data_ptr(), status=self.status.data_ptr())
+
+    def blocks(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def to_dense(self) -> np.ndarray:
+        """The matrix on the host (small systems, for checks)."""
+        rp = self.row_ptr.cpu().numpy()
+        col = self.col.cpu().numpy()
+        val = self.val.cpu().numpy().reshape(-1, self.B, self.B)
+        ld = self.nsb * self.B
+        M = np.zeros((ld, ld))
+        for I in range(self.nsb):
+            for s in range(rp[I], rp[I + 1]):
+                J = col[s]
+                M[I * self.B:(I + 1) * self.B, J * self.B:(J + 1) * self.B] = val[s]
+        return M[:self.n, :self.n]
+
+
 class MDState:
     """Device arrays of one XL-BOMD trajectory and its tb_md_state (T_e = 0 with
     SP2 options, or kT > 0 with Fermi-operator options)."""
 
     def __init__(self, ds: DeviceSystem, v0: np.ndarray, masses: np.ndarray, n_occ: float, K: int,
                  opts: tbmd.tb_sp2_opts, kT: float = 0.0, fermi: "tbmd.tb_fermi_opts" = None,
-                 entropy: bool = False, nonorth: bool = False):
+                 entropy: bool = False, nonorth: bool = False, bsr_cap: tuple = None):
         dev = ds.device
         N, n = ds.natoms, ds.norb
         f64 = dict(dtype=torch.float64, device=dev)
@@ -110,9 +142,18 @@ class MDState:
         self.mass = torch.as_tensor(np.asarray(masses, dtype=np.float64), device=dev)
         self.n_hist = torch.zeros(K + 1, N, **f64)
         self.q = torch.zeros(N, **f64)
-        self.H = torch.zeros(n, n, **f64)
-        self.D = torch.zeros(n, n, **f64)
-        self.gamma = torch.zeros(N, N, **f64)
+        # bsr_cap = (blocks of H, blocks of D): the block-sparse state, no n x n or N x N array
+        self.bsr = bsr_cap is not None
+        if self.bsr:
+            self.H = self.D = self.gamma = None
+            self.H_bsr = BsrMatrix(n, bsr_cap[0], dev)
+            self.D_bsr = BsrMatrix(n, bsr_cap[1], dev)
+            self.bsr_ws = Workspace(tbmd.tb_bsr_model_workspace_size(N, n), dev)
+        else:
+            self.H = torch.zeros(n, n, **f64)
+            self.D = torch.zeros(n, n, **f64)
+            self.gamma = torch.zeros(N, N, **f64)
+            self.H_bsr = self.D_bsr = self.bsr_ws = None
         self.energies = torch.zeros(8, **f64)
         self.report = new_report(dev)
         self.fermi_report = torch.zeros(ctypes.sizeof(tbmd.tb_fermi_report), dtype=torch.uint8, device=dev)
@@ -136,11 +177,13 @@ class MDState:
             self.vscc = torch.zeros(N, **f64)
             self.no_ws = Workspace(tbmd.dm_nonorth_workspace_size(n, kT, opts, fermi), dev)
         else:
-            self.S = self.W = self.vscc = self.no_ws = None
+            self.S = self.W = self.no_ws = None
+            self.vscc = torch.zeros(N, **f64) if self.bsr else None
         self.st = tbmd.tb_md_state(
             sys=ds.sys, n_occ=float(n_occ), R=self.R.data_ptr(), v=self.v.data_ptr(), F=self.F.data_ptr(),
             mass=self.mass.data_ptr(), n_hist=self.n_hist.data_ptr(), q=self.q.data_ptr(),
-            H=self.H.data_ptr(), D=self.D.data_ptr(), gamma=self.gamma.data_ptr(),
+            H=self.H.data_ptr() if self.H is not None else None, D=self.D.data_ptr() if self.D is not None else None,
+            gamma=self.gamma.data_ptr() if self.gamma is not None else None,
             energies=self.energies.data_ptr(), sp2_report=self.report.data_ptr(),
             workspace=self.ws.ptr, workspace_bytes=self.ws.nbytes, step=0, kT=float(kT), fermi=fermi,
             mu=self.mu.data_ptr(), fermi_report=self.fermi_report.data_ptr(),
@@ -148,10 +191,14 @@ class MDState:
             entropy_workspace_bytes=self.ent_ws.nbytes if self.ent_ws else 0,
             entropy=self.entropy.data_ptr() if self.ent_ws else None,
             S=self.S.data_ptr() if nonorth else None, W=self.W.data_ptr() if nonorth else None,
-            vscc=self.vscc.data_ptr() if nonorth else None,
+            vscc=self.vscc.data_ptr() if self.vscc is not None else None,
             nonorth_workspace=self.no_ws.ptr if nonorth else None,
             nonorth_workspace_bytes=self.no_ws.nbytes if nonorth else 0,
-            nonorth_report=self.nonorth_report.data_ptr())
+            nonorth_report=self.nonorth_report.data_ptr(),
+            H_bsr=ctypes.addressof(self.H_bsr.mat) if self.bsr else None,
+            D_bsr=ctypes.addressof(self.D_bsr.mat) if self.bsr else None,
+            bsr_workspace=self.bsr_ws.ptr if self.bsr else None,
+            bsr_workspace_bytes=self.bsr_ws.nbytes if self.bsr else 0)
 
     def n_current(self) -> torch.Tensor:
         return self.n_hist[0]

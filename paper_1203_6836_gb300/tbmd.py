@@ -91,6 +91,11 @@ class tb_fermi_report(ctypes.Structure):
                 ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double)]
 
 
+class tb_bsr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("nsb", ctypes.c_int), ("cap", ctypes.c_int), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p), ("status", ctypes.c_void_p)]
+
+
 class tb_md_state(ctypes.Structure):
     _fields_ = [("sys", tb_system), ("n_occ", ctypes.c_double),
                 ("R", ctypes.c_void_p), ("v", ctypes.c_void_p), ("F", ctypes.c_void_p),
@@ -104,7 +109,9 @@ class tb_md_state(ctypes.Structure):
                 ("entropy", ctypes.c_void_p),
                 ("S", ctypes.c_void_p), ("W", ctypes.c_void_p), ("vscc", ctypes.c_void_p),
                 ("nonorth_workspace", ctypes.c_void_p), ("nonorth_workspace_bytes", ctypes.c_size_t),
-                ("nonorth_report", ctypes.c_void_p)]
+                ("nonorth_report", ctypes.c_void_p),
+                ("H_bsr", ctypes.c_void_p), ("D_bsr", ctypes.c_void_p),
+                ("bsr_workspace", ctypes.c_void_p), ("bsr_workspace_bytes", ctypes.c_size_t)]
 
 
 class tb_nonorth_report(ctypes.Structure):
@@ -142,6 +149,16 @@ _SIGS = {
     "tb_ctx_set_grid_limit": (ctypes.c_int, [_P, ctypes.c_int]),
     "tb_ctx_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_ulonglong]),
     "tb_ctx_set_sp2_form": (ctypes.c_int, [_P, ctypes.c_int]),
+    "tb_bsr_model_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "tb_build_H_bsr": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P,
+                                      ctypes.POINTER(tb_bsr), _P, _P, ctypes.c_size_t, _P]),
+    "dm_sp2_sparse": (ctypes.c_int, [_P, ctypes.POINTER(tb_bsr), ctypes.c_double, ctypes.POINTER(tb_sp2_opts),
+                                     ctypes.POINTER(tb_bsr), _P, ctypes.c_size_t, _P, _P]),
+    "mulliken_bsr": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), ctypes.POINTER(tb_bsr),
+                                    _P, _P]),
+    "tb_forces_bsr": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P,
+                                     ctypes.POINTER(tb_bsr), ctypes.POINTER(tb_bsr), _P, _P, _P, _P, _P, _P,
+                                     ctypes.c_size_t, _P]),
     "tb_build_HS": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P, _P, _P, _P, _P,
                                    _P, _P]),
     "dm_nonorth_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.POINTER(tb_sp2_opts),
@@ -299,6 +316,40 @@ def tb_ctx_sp2_form_of(ctx: Context, n: int) -> tuple[int, int]:
     f, c = ctypes.c_int(), ctypes.c_int()
     ctx.check(lib().tb_ctx_sp2_form_of(ctx.handle, int(n), ctypes.byref(f), ctypes.byref(c)), "tb_ctx_sp2_form_of")
     return f.value, c.value
+
+
+def tb_bsr_model_workspace_size(natoms: int, norb: int) -> int:
+    b = ctypes.c_size_t()
+    rc = lib().tb_bsr_model_workspace_size(int(natoms), int(norb), ctypes.byref(b))
+    if rc != TB_OK:
+        raise TBError(rc, "tb_bsr_model_workspace_size")
+    return b.value
+
+
+def tb_build_H_bsr(ctx: Context, p: tb_params, sys: tb_system, R, n_aux, H: tb_bsr, v, workspace,
+                   workspace_bytes: int, stream=None) -> int:
+    return ctx.check(lib().tb_build_H_bsr(ctx.handle, ctypes.byref(p), ctypes.byref(sys), _ptr(R), _ptr(n_aux),
+                                          ctypes.byref(H), _ptr(v), _ptr(workspace), int(workspace_bytes),
+                                          _stream(stream)), "tb_build_H_bsr")
+
+
+def dm_sp2_sparse(ctx: Context, H: tb_bsr, n_occ: float, opts: tb_sp2_opts, D: tb_bsr, workspace,
+                  workspace_bytes: int, report=None, stream=None) -> int:
+    return ctx.check(lib().dm_sp2_sparse(ctx.handle, ctypes.byref(H), float(n_occ), ctypes.byref(opts),
+                                         ctypes.byref(D), _ptr(workspace), int(workspace_bytes), _ptr(report),
+                                         _stream(stream)), "dm_sp2_sparse")
+
+
+def mulliken_bsr(ctx: Context, p: tb_params, sys: tb_system, D: tb_bsr, q, stream=None) -> int:
+    return ctx.check(lib().mulliken_bsr(ctx.handle, ctypes.byref(p), ctypes.byref(sys), ctypes.byref(D), _ptr(q),
+                                        _stream(stream)), "mulliken_bsr")
+
+
+def tb_forces_bsr(ctx: Context, p: tb_params, sys: tb_system, R, H: tb_bsr, D: tb_bsr, q, n_aux, v, F, energy,
+                  workspace, workspace_bytes: int, stream=None) -> int:
+    return ctx.check(lib().tb_forces_bsr(ctx.handle, ctypes.byref(p), ctypes.byref(sys), _ptr(R), ctypes.byref(H),
+                                         ctypes.byref(D), _ptr(q), _ptr(n_aux), _ptr(v), _ptr(F), _ptr(energy),
+                                         _ptr(workspace), int(workspace_bytes), _stream(stream)), "tb_forces_bsr")
 
 
 def tb_build_HS(ctx: Context, p: tb_params, sys: tb_system, R, n_aux, H, S, gamma, v, stream=None) -> int:
