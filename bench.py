@@ -737,20 +737,36 @@ def run_sparse(args):
     del sol, D, H, G, hH, hD
     torch.cuda.empty_cache()
     M = s.masses(P)
-    st = MDState(ds, thermal_velocities(M, 300.0, seed=100), M, s.n_occ(P), XL.K, opts)
-    tbmd.xlbomd_init(ctx, TP, st.st, xp, opts, 1e-6, 2)
-    tbmd.xlbomd_step(ctx, TP, st.st, xp, opts)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    md_steps = 3
-    e0.record(stream)
-    for _ in range(md_steps):
+    # the XL-BOMD step on BSR matrices (block-sparse boundary: no n x n or N x N array);
+    # capacities: H 64 blocks per block row, D every block
+    md = {}
+    for label, bsr in (("bsr_state", True), ("dense_boundary", False)):
+        torch.cuda.synchronize()
+        m0 = torch.cuda.memory_allocated()
+        st = MDState(ds, thermal_velocities(M, 300.0, seed=100), M, s.n_occ(P), XL.K, opts,
+                     bsr_cap=(64 * nsb, nsb * nsb) if bsr else None)
+        state_bytes = torch.cuda.memory_allocated() - m0
+        tbmd.xlbomd_init(ctx, TP, st.st, xp, opts, 1e-6, 2)
         tbmd.xlbomd_step(ctx, TP, st.st, xp, opts)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    md_ms = e0.elapsed_time(e1) / md_steps
-    del st
-    torch.cuda.empty_cache()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        md_steps = 3
+        e0.record(stream)
+        for _ in range(md_steps):
+            tbmd.xlbomd_step(ctx, TP, st.st, xp, opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        md[label] = {"ms_per_step": e0.elapsed_time(e1) / md_steps, "state_bytes": state_bytes}
+        if bsr:
+            md[label]["H_blocks"] = st.H_bsr.blocks()
+            md[label]["D_blocks"] = st.D_bsr.blocks()
+            md[label]["note"] = ("state = R, v, F, q, n history, BSR H and D at their capacities, the SP2 and model "
+                                 "workspaces")
+        else:
+            md[label]["note"] = "dense H, D (n x n) and gamma (N x N) at the boundary, the same thresholded SP2"
+        del st
+        torch.cuda.empty_cache()
+    md_ms = md["bsr_state"]["ms_per_step"]
     # the drift study runs on the 1/8-size subsystem of the gapped recipe: 682
     # H2O-like molecules (2046 atoms) at 0.1 g/cc in Morton order, T_e = 0,
     # kappa = kappa0 / 2 (the 1.0 g/cc random recipe has no T_e = 0 SCF fixed
@@ -801,7 +817,8 @@ def run_sparse(args):
                                  "kind": "oracle",
                                  "sample": f"2 thresholded FP64 projections (NumPy, dense storage) of the "
                                            f"n={no} 1/8-size Morton system, {dt:.1f} s"},
-                   xlbomd={"steps_per_s": 1e3 / md_ms, "ms_per_step": md_ms, "system": f"{s.natoms} atoms, tau=1e-5"},
+                   xlbomd={"steps_per_s": 1e3 / md_ms, "ms_per_step": md_ms, "system": f"{s.natoms} atoms, tau=1e-5",
+                           "boundary": "BSR matrices", "compare": md},
                    drift_200_steps={"system": f"gapped recipe, {sub.natoms} atoms (682 H2O-like molecules, "
                                               "the 1/8-size subsystem), 0.1 g/cc, Morton order, T_e = 0, "
                                               "kappa = kappa0/2", **drift,
