@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the arrival trace")
     ap.add_argument("--sparse-natoms", type=int, default=16384,
                     help="sparse: atoms of the Morton-ordered water-like system (16384 = the headline case)")
+    ap.add_argument("--scaling-molecules", type=int, nargs="*", default=[682, 5461, 21845],
+                    help="sparse: gapped-vapour sizes (H2O-like molecules) of the BSR-state scaling study")
     return ap.parse_args()
 
 
@@ -796,6 +798,42 @@ def run_sparse(args):
         Es[label] = E
         del st
     dE = float(np.max(np.abs(Es["block_sparse_tau1e-5"] - Es["dense_refined"])))
+    # linear scaling: the XL-BOMD step on the BSR state (no n x n or N x N
+    # array) for the gapped vapour from 2046 to 65535 atoms (n up to 131070);
+    # capacities 64 blocks per block row for H and D, 96 for the SP2 iterates
+    from paper_1203_6836_gb300.device import BsrMatrix  # noqa: F401
+    og = sp2_opts(args.precision, max_iter=80, tau=1e-5, blocks_per_row=96)
+    scaling = []
+    for nmol in args.scaling_molecules:
+        w = gapped_vapour(nmol, seed=0, morton=True)
+        dw = DeviceSystem(w.R, w.types, w.box)
+        nsbw = (dw.norb + 127) // 128
+        Mw = w.masses(Pg)
+        torch.cuda.synchronize()
+        m0 = torch.cuda.memory_allocated()
+        st = MDState(dw, thermal_velocities(Mw, 300.0, seed=100), Mw, w.n_occ(Pg), XL.K, og,
+                     bsr_cap=(64 * nsbw, 64 * nsbw))
+        state_bytes = torch.cuda.memory_allocated() - m0
+        it = tbmd.xlbomd_init(ctx, TPg, st.st, xp, og, 1e-6, 40)
+        tbmd.xlbomd_step(ctx, TPg, st.st, xp, og)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        md_steps = 3
+        e0.record(stream)
+        for _ in range(md_steps):
+            tbmd.xlbomd_step(ctx, TPg, st.st, xp, og)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rw = report_to_dict(st.report)
+        ms_w = e0.elapsed_time(e1) / md_steps
+        scaling.append({"atoms": w.natoms, "n": dw.norb, "box_A": round(w.box, 2), "ms_per_step": ms_w,
+                        "us_per_atom_step": 1e3 * ms_w / w.natoms, "sp2_iters": rw["iters"],
+                        "sp2_status": rw["status"], "H_blocks": st.H_bsr.blocks(), "D_blocks": st.D_bsr.blocks(),
+                        "D_blocks_per_row": st.D_bsr.blocks() / nsbw,
+                        "block_products_per_D": rw["block_products"], "state_GB": state_bytes / 1e9,
+                        "scf_init_iters": it})
+        del st, dw
+        torch.cuda.empty_cache()
     line = _common(args, "thresholded block-sparse SP2: block-product TFLOP/s", value, "TFLOP/s",
                    total / args.steps, f"{args.precision}+f64",
                    f"{s.natoms} atoms, n={n}, 1.0 g/cc, Morton order, seed 0; SP2 with "
@@ -819,6 +857,8 @@ def run_sparse(args):
                                            f"n={no} 1/8-size Morton system, {dt:.1f} s"},
                    xlbomd={"steps_per_s": 1e3 / md_ms, "ms_per_step": md_ms, "system": f"{s.natoms} atoms, tau=1e-5",
                            "boundary": "BSR matrices", "compare": md},
+                   xlbomd_linear_scaling={"system": "gapped recipe vapour, 0.1 g/cc, Morton order, tau=1e-5, "
+                                                    "BSR state (no n x n or N x N array)", "sizes": scaling},
                    drift_200_steps={"system": f"gapped recipe, {sub.natoms} atoms (682 H2O-like molecules, "
                                               "the 1/8-size subsystem), 0.1 g/cc, Morton order, T_e = 0, "
                                               "kappa = kappa0/2", **drift,

@@ -121,7 +121,7 @@ typedef struct {
                            1: FP64 FMA */
   double tau;           /* > 0: thresholded block-sparse SP2 (Sec. III.B): after X0 and after every
                            projection, 32 x 32 blocks with Frobenius norm < tau are set to zero;
-                           tensor-core precisions only, n <= 32768, no refinement */
+                           tensor-core precisions only, n <= 131072, no refinement */
   int bsr_blocks_per_row; /* capacity of the block-sparse pattern in 128 x 128 blocks per block
                              row (0: all, never overflows); exceeding it reports TB_ERR_OOM */
 } tb_sp2_opts;
@@ -461,7 +461,7 @@ int tb_build_H_bsr(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const 
 
 /* D = theta(mu0 I - H) by the thresholded block-sparse SP2 (a5; Sec. III.B, opts.tau > 0, a
  * tensor-core precision) with BSR input and output: X0 from H's blocks, the final iterate's
- * blocks (FP32 master, stored as FP64) written to D with their structure.  n <= 32768.
+ * blocks (FP32 master, stored as FP64) written to D with their structure.  n <= 131072.
  * Workspace from dm_sp2_workspace_size(n, opts). */
 int dm_sp2_sparse(tb_ctx* ctx, const tb_bsr* H, double n_occ, const tb_sp2_opts* opts, tb_bsr* D,
                   void* workspace, size_t workspace_bytes, tb_sp2_report* report, void* stream);

@@ -9,8 +9,8 @@
 // block-sparse-row structure, ping-ponged between two buffers.  A super-block
 // is stored when at least one of its sixteen 32 x 32 sub-blocks survives the
 // drop rule; dropped sub-blocks inside a stored super-block hold zeros, so the
-// arithmetic is the same as dropping 32 x 32 blocks.  For n <= 32768 there are
-// at most 256 super-rows and each row's pattern is a 256-bit bitmap.
+// arithmetic is the same as dropping 32 x 32 blocks.  For n <= 131072 there are
+// at most 1024 super-rows and each row's pattern is a 1024-bit bitmap.
 //
 // Per projection (all on the device, no host synchronisation):
 //   decide  reduce the trace partials of X_k, take the stop/branch decision
@@ -41,7 +41,7 @@ namespace {
 using namespace tcx;
 
 constexpr int SB = 128;            // super-block side (tcgen05 tile)
-constexpr int MW = 8;              // bitmap words per row (256 super-rows)
+constexpr int MW = 32;             // bitmap words per row (1024 super-rows: n <= 131072)
 constexpr int kMaxNsb = MW * 32;
 constexpr int kThreads = 192;      // numeric kernel: TMA, MMA, 4 epilogue warps
 constexpr int kTiles = SB * SB;    // elements per super-block
@@ -76,6 +76,7 @@ struct Sym {
 
 struct Args {
   int n, ld, nsb, cap, pcap;
+  int mw;                 // bitmap words in use: ceil(nsb / 32)
   double nocc, tau2, floor, tol;
   int rule, k, max_iter;
   SP2State* st;
@@ -470,7 +471,7 @@ __global__ void k_bsr_cand(Args a, Buf b, Sym sy) {
   const uint32_t* li = b.live + I * MW;
   for (int K = threadIdx.x; K < a.nsb; K += blockDim.x)
     if ((li[K >> 5] >> (K & 31)) & 1u)
-      for (int w = 0; w < MW; ++w) atomicOr(&c[w], b.live[K * MW + w]);
+      for (int w = 0; w < a.mw; ++w) atomicOr(&c[w], b.live[K * MW + w]);
   __syncthreads();
   if (threadIdx.x < MW) sy.cand[I * MW + threadIdx.x] = c[threadIdx.x];
   if (threadIdx.x == 0) {
@@ -497,7 +498,7 @@ __global__ void k_bsr_fill_out(Args a, Buf bo, Buf bn, Sym sy) {
     int pc = 0;
     const uint32_t* lj = bo.live + J * MW;
     if (J >= I)  // X^2 is symmetric: blocks below the diagonal are written as mirrors
-      for (int w = 0; w < MW; ++w) pc += __popc(li[w] & lj[w]);
+      for (int w = 0; w < a.mw; ++w) pc += __popc(li[w] & lj[w]);
     sy.pcnt[o] = pc;
   }
 }
@@ -547,7 +548,7 @@ __global__ void k_bsr_pairs(Args a, Buf bo, Buf bn, Sym sy) {
     int p = sy.pair_ptr[o];
     // the mirrored block (J, I) of the full product has as many block products
     if (J > I) atomicAdd(&a.st->block_products, (unsigned long long)sy.pcnt[o]);
-    for (int w = 0; w < MW; ++w) {
+    for (int w = 0; w < a.mw; ++w) {
       uint32_t m = li[w] & lj[w];
       while (m) {
         const int K = 32 * w + __ffs(m) - 1;
@@ -1006,6 +1007,7 @@ int run_bsr(tb_ctx* ctx, const double* H, const tb_bsr* Hb, int n, double nocc, 
   a.n = n;
   a.ld = L.ld;
   a.nsb = L.nsb;
+  a.mw = (L.nsb + 31) / 32;
   a.cap = L.cap;
   a.pcap = L.pcap;
   a.nocc = nocc;

@@ -124,6 +124,28 @@ class BsrMatrix:
                 M[I * self.B:(I + 1) * self.B, J * self.B:(J + 1) * self.B] = val[s]
         return M[:self.n, :self.n]
 
+    def window(self, r0: int, r1: int, c0: int, c1: int) -> np.ndarray:
+        """Rows [r0, r1) x columns [c0, c1) on the host, gathered from the
+        stored blocks that meet them (any n: for checks of a large matrix)."""
+        B = self.B
+        rp = self.row_ptr.cpu().numpy()
+        col = self.col.cpu().numpy()
+        I0, I1 = r0 // B, (r1 - 1) // B + 1
+        J0, J1 = c0 // B, (c1 - 1) // B + 1
+        slots, where = [], []
+        for I in range(I0, I1):
+            for s in range(rp[I], rp[I + 1]):
+                if J0 <= col[s] < J1:
+                    slots.append(s)
+                    where.append((I - I0, col[s] - J0))
+        W = np.zeros(((I1 - I0) * B, (J1 - J0) * B))
+        if slots:
+            idx = torch.as_tensor(slots, dtype=torch.long, device=self.val.device)
+            blk = self.val.view(-1, B, B).index_select(0, idx).cpu().numpy()
+            for (i, j), b in zip(where, blk):
+                W[i * B:(i + 1) * B, j * B:(j + 1) * B] = b
+        return W[r0 - I0 * B:r1 - I0 * B, c0 - J0 * B:c1 - J0 * B]
+
 
 class MDState:
     """Device arrays of one XL-BOMD trajectory and its tb_md_state (T_e = 0 with

@@ -23,8 +23,8 @@ import numpy as np
 import pytest
 import torch
 
-from workloads import ModelParams, XLParams, gapped_params, gapped_vapour, thermal_velocities, water_24_atoms, \
-    water_system
+from workloads import ModelParams, XLParams, gapped_params, gapped_vapour, isolated_clusters, thermal_velocities, \
+    water_24_atoms, water_system
 from oracle import density, observables, tb
 from paper_1203_6836_gb300 import tbmd
 from paper_1203_6836_gb300.device import BsrMatrix, DeviceSystem, MDState, Workspace, report_to_dict, sp2_opts, \
@@ -211,3 +211,66 @@ def test_bsr_state_trajectory_follows_the_dense_state(ctx):
     assert i_b >= 0 and i_d >= 0
     assert st_b.H is None and st_b.D is None and st_b.gamma is None
     assert dE < 1e-6 * s.natoms and dR < 1e-6
+
+
+def test_dm_sp2_sparse_beyond_32768_orbitals_on_isolated_clusters(ctx):
+    """n = 105456 (824 block rows, the row bitmaps' words 8..25 in use):
+    13^3 rotated copies of an 8-molecule cluster 16 A apart, H = h (no
+    charges).  Clusters do not interact, so h is block diagonal by cluster;
+    every cluster has the same spectrum, so the global SP2 projection is, on
+    each cluster, the projection on its own 32 lowest states.  The oracle
+    computes that (eigh of the 48 x 48 cluster h) for sampled clusters: the
+    first, the last, the ones across orbital 32768 (bitmap word 8) and n / 2,
+    and 12 at random.  Bound: the tf32x3 phase without refinement stops at
+    its FP32 noise floor (2e-5 max, as for the grouped path); entries
+    between clusters are products with an exact zero factor, so exactly 0;
+    the block pattern of D stays within two blocks of the diagonal (the
+    symbolic square of H's one-block band); and the
+    whole run holds no n x n array (BSR capacities of 16 / 8 blocks per
+    row)."""
+    PG = gapped_params()
+    TPG = tbmd.tb_params.from_model(PG)
+    s = isolated_clusters(13)
+    nc, na, no = 13 ** 3, 24, 48
+    ds = DeviceSystem(s.R, s.types, s.box)
+    n = ds.norb
+    assert n == nc * no and n > 32768
+    nsb = (n + 127) // 128
+    Hb = BsrMatrix(n, 16 * nsb)
+    v = torch.zeros(s.natoms, **f64)
+    ws = Workspace(tbmd.tb_bsr_model_workspace_size(s.natoms, n))
+    tbmd.tb_build_H_bsr(ctx, TPG, ds.sys, ds.R, None, Hb.mat, v, ws.ptr, ws.nbytes)
+    opts = sp2_opts("tf32x3", max_iter=100, tau=1e-9, blocks_per_row=8)
+    Db = BsrMatrix(n, 8 * nsb)
+    sws = Workspace(tbmd.dm_sp2_workspace_size(n, opts))
+    rep = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    nocc = s.n_occ(PG)
+    tbmd.dm_sp2_sparse(ctx, Hb.mat, nocc, opts, Db.mat, sws.ptr, sws.nbytes, rep)
+    torch.cuda.synchronize()
+    r = report_to_dict(rep)
+    assert int(Hb.status) == tbmd.TB_OK and int(Db.status) == tbmd.TB_OK and r["status"] == tbmd.TB_OK
+    rp, col = Db.row_ptr.cpu().numpy(), Db.col.cpu().numpy()
+    rows = np.repeat(np.arange(nsb), np.diff(rp))
+    # X^2's symbolic pattern of a one-block band: two blocks off the diagonal
+    # (stored, valued 0 where no cluster spans both), no farther
+    assert np.abs(col[:rp[-1]] - rows).max() <= 2
+    rng = np.random.default_rng(7)
+    picks = {0, nc - 1, 32768 // no, (n // 2) // no} | set(rng.choice(nc, 12, replace=False).tolist())
+    worst, worst_out, tr = 0.0, 0.0, []
+    for c in sorted(picks):
+        a, b = c * no, (c + 1) * no
+        Rc, tc = s.R[c * na:(c + 1) * na], s.types[c * na:(c + 1) * na]
+        Dc = density.density_T0(tb.build_h(Rc, tc, 1000.0, PG), 32).D
+        lo, hi = max(0, (a // 128 - 2) * 128), min(n, ((b - 1) // 128 + 3) * 128)
+        W = Db.window(a, b, lo, hi)
+        inner = W[:, a - lo:b - lo]
+        worst = max(worst, float(np.abs(inner - Dc).max()))
+        outer = np.concatenate([W[:, :a - lo], W[:, b - lo:]], axis=1)
+        worst_out = max(worst_out, float(np.abs(outer).max()) if outer.size else 0.0)
+        tr.append(np.trace(inner))
+    print(f"PARITY dm_sp2_sparse n={n}: {len(picks)} sampled clusters max|dD| {worst:.2e}, "
+          f"max|D| between clusters {worst_out:.1e}, cluster traces {min(tr):.6f}..{max(tr):.6f}; "
+          f"{Hb.blocks()} H blocks, {Db.blocks()} D blocks, iters {r['iters']}, trace {r['trace']:.4f} of {nocc}")
+    assert worst < 2e-5 and worst_out == 0.0
+    assert max(abs(t - 32.0) for t in tr) < 1e-4
+    assert abs(r["trace"] - nocc) < 1e-5 * nocc

@@ -13,5 +13,5 @@ from .water import (  # noqa: F401
     atom_counts, box_from_density, water_system, thermal_velocities,
     random_gapped_matrix, batch_sizes, serving_trajectories,
     water_24_atoms, water_2048_atoms, water_16384_atoms_morton, molecular_water, molecular_liquid,
-    gapped_params, gapped_vapour, nonorth_params,
+    gapped_params, gapped_vapour, nonorth_params, isolated_clusters,
 )

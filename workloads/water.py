@@ -396,3 +396,26 @@ def gapped_vapour(n_mol: int = 682, seed: int = 0, morton: bool = False) -> Wate
     apart; 8 molecules give the 24-atom system."""
     return molecular_liquid(n_mol, 0.1, seed=seed, morton=morton)
 
+
+
+def isolated_clusters(m: int, spacing: float = 16.0, seed: int = 0) -> WaterSystem:
+    """m^3 rigid copies of one 8-molecule cluster (molecular_water(2, 8.0)),
+    each under its own random rotation about the cluster's centroid, centred
+    on an m x m x m lattice of `spacing` A in a periodic cube of m * spacing.
+    Atoms are ordered cluster by cluster (8 O, then 16 H each).  The cluster
+    reaches ~4.5 A from its centroid, so at 16 A spacing two clusters are at
+    least 7 A apart: beyond a 6 A interaction range every cluster is
+    isolated and all clusters have one spectrum."""
+    base = molecular_water(2, 8.0, seed=1)
+    c0 = base.R - base.R.mean(axis=0)
+    rng = np.random.default_rng(seed)
+    grid = (np.arange(m) + 0.5) * spacing
+    Rs = []
+    for x in grid:
+        for y in grid:
+            for z in grid:
+                Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+                Rs.append(c0 @ Q.T + np.array([x, y, z]))
+    R = np.concatenate(Rs)
+    types = np.tile(base.types, m ** 3)
+    return WaterSystem(R=R, types=types, box=float(m * spacing), seed=seed)
