@@ -17,6 +17,24 @@ The thresholded variant drops, after X0 and after every projection, every
 bs x bs block whose Frobenius norm is below tau (Sec. III.B applies the
 threshold elementwise after each projection; the block rule is the
 block-sparse reading).
+
+The recursive Fermi-operator expansion (the finite-temperature construction
+the paper cites for linear scaling at T_e > 0, end of Sec. III.C, left
+unimplemented there): with f(t) = 1/(1 + e^t), f(t)^2 / (f(t)^2 + (1 -
+f(t))^2) = f(2t), so m steps X <- X^2 [X^2 + (I - X)^2]^-1 take the Fermi
+operator at beta / 2^m to the one at beta.  Reading used here and on the
+GPU: the steps act on E = X - I/2, for which the map is E <- 2E (I + 4E^2)^-1,
+starting from E0 = L - 4/3 L^3, L = -beta (H - mu I) / 2^(m+2) (tanh to third
+order at beta / 2^m), and each step is written with products only:
+  W = (I - 2E)(I + 2E),  A = 2I - W,
+  Z = (32 A^2 - 144 A + 210 I) / 99, then ns - 1 Newton-Schulz steps
+      T = 2I - A Z, Z <- Z T,
+  E <- E + E (Z W).
+m is the smallest value >= 8 with beta (hi - lo) <= 2^(m+1) over the
+chemical-potential bracket [lo, hi] (the start needs |beta (eps - mu)| <=
+2^(m+1)).  D = I/2 + E.  The thresholded variant drops every bs x bs block
+with Frobenius norm below tau after L and after every product (the affine
+steps P, Q, A are exact and drop nothing).
 """
 
 from __future__ import annotations
@@ -162,6 +180,72 @@ def sp2(H: np.ndarray, n_occ: float, tol: float = 1e-10, max_iter: int = 100,
         branches.append(b)
     return SP2Result(X=X, iters=len(branches), branches=branches, converged=converged,
                      idem=idem, eps_min=emin, eps_max=emax, idem_history=hist, pre_drop_norms=norms)
+
+
+@dataclasses.dataclass
+class FermiExpansionResult:
+    D: np.ndarray
+    mu: float
+    m: int                     # doubling steps
+    expansions: int            # chemical-potential iterations (one expansion each)
+    trace: float               # Tr D
+    converged: bool
+    pre_drop_norms: np.ndarray = None  # tau > 0: bs x bs block norms of the final E before its drop
+
+
+def fermi_expansion(H: np.ndarray, n_occ: float, kT: float, tau: float = 0.0, bs: int = 32,
+                    m_max: int = 14, ns_iters: int = 3, trace_tol: float = 1e-10,
+                    mu_iters: int = 80) -> FermiExpansionResult:
+    """The recursive Fermi-operator expansion in FP64 (reading in the module
+    docstring), with mu such that Tr D = N_occ to trace_tol: bisection on the
+    bracket [eps_min - 40 kT - 1, eps_max + 40 kT + 1] (Gershgorin), taking
+    Newton's step -dev / (beta Tr D(I - D)) when it stays inside the bracket
+    (Tr D(I - D) = n/4 - ||E||_F^2)."""
+    n = H.shape[0]
+    beta = 1.0 / kT
+    I = np.eye(n)
+    emin, emax = gershgorin(H)
+    lo, hi = emin - 40.0 * kT - 1.0, emax + 40.0 * kT + 1.0
+    m = min(8, m_max)
+    while m < m_max and not beta * (hi - lo) <= 2.0 ** (m + 1):
+        m += 1
+
+    def drop(X):
+        return _drop_blocks(X, bs, tau) if tau > 0 else (X, None)
+
+    def expansion(mu):
+        L, _ = drop(-beta / 2.0 ** (m + 2) * (H - mu * I))
+        L2, _ = drop(L @ L)
+        E, norms = drop(L - 4.0 / 3.0 * (L @ L2))
+        for _ in range(m):
+            W, _ = drop((I - 2.0 * E) @ (I + 2.0 * E))
+            A = 2.0 * I - W
+            Z, _ = drop((32.0 * (A @ A) - 144.0 * A + 210.0 * I) / 99.0)
+            for _ in range(ns_iters - 1):
+                T, _ = drop(2.0 * I - A @ Z)
+                Z, _ = drop(Z @ T)
+            V, _ = drop(Z @ W)
+            E, norms = drop(E + E @ V)
+        return E, norms
+
+    mu = 0.5 * (emin + emax)
+    E, norms, it, converged = None, None, 0, False
+    for it in range(1, mu_iters + 1):
+        E, norms = expansion(mu)
+        dev = 0.5 * n + float(np.trace(E)) - n_occ
+        if abs(dev) <= trace_tol:
+            converged = True
+            break
+        if dev > 0:
+            hi = mu
+        else:
+            lo = mu
+        t1 = 0.25 * n - float(np.sum(E * E))
+        nxt = mu - dev / (beta * t1) if t1 > 1e-14 else float("nan")
+        mu = nxt if lo < nxt < hi else 0.5 * (lo + hi)
+    D = 0.5 * I + E
+    return FermiExpansionResult(D=D, mu=float(mu), m=m, expansions=it, trace=float(np.trace(D)),
+                                converged=converged, pre_drop_norms=norms)
 
 
 def idempotency_fro(X: np.ndarray) -> float:
