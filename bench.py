@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the arrival trace")
     ap.add_argument("--sparse-natoms", type=int, default=16384,
                     help="sparse: atoms of the Morton-ordered water-like system (16384 = the headline case)")
+    ap.add_argument("--fermi-molecules", type=int, default=5461,
+                    help="sparse: gapped-vapour molecules of the finite-temperature block-sparse line (0: off)")
     ap.add_argument("--scaling-molecules", type=int, nargs="*", default=[682, 5461, 21845],
                     help="sparse: gapped-vapour sizes (H2O-like molecules) of the BSR-state scaling study")
     return ap.parse_args()
@@ -834,6 +836,55 @@ def run_sparse(args):
                         "scf_init_iters": it})
         del st, dw
         torch.cuda.empty_cache()
+    # finite temperature on the block-sparse machinery: dm_fermi_sparse on the
+    # gapped vapour (16383 atoms, kT = 0.2 eV, tau = 1e-5), from a cold start
+    # (mu unknown) and warm (mu of the previous call), and the kT > 0 XL-BOMD
+    # step on the BSR state
+    from paper_1203_6836_gb300.device import BsrMatrix, Workspace, fermi_opts, fermi_report_to_dict
+    finite_t = {}
+    if args.fermi_molecules > 0:
+        w = gapped_vapour(args.fermi_molecules, seed=0, morton=True)
+        dw = DeviceSystem(w.R, w.types, w.box)
+        nw = dw.norb
+        nsbw = (nw + 127) // 128
+        fo = fermi_opts(args.precision)
+        Hb = BsrMatrix(nw, 64 * nsbw)
+        Db = BsrMatrix(nw, 64 * nsbw)
+        vw = torch.zeros(w.natoms, dtype=torch.float64, device="cuda")
+        mws = Workspace(tbmd.tb_bsr_model_workspace_size(w.natoms, nw))
+        tbmd.tb_build_H_bsr(ctx, TPg, dw.sys, dw.R, None, Hb.mat, vw, mws.ptr, mws.nbytes)
+        fws = Workspace(tbmd.dm_fermi_sparse_workspace_size(nw, fo, 96))
+        mu = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+        frep = torch.zeros(128, dtype=torch.uint8, device="cuda")
+        for label in ("cold", "warm"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tbmd.dm_fermi_sparse(ctx, Hb.mat, w.n_occ(Pg), 0.2, fo, 1e-5, 96, Db.mat, mu, fws.ptr, fws.nbytes, frep)
+            torch.cuda.synchronize()
+            fr = fermi_report_to_dict(frep)
+            finite_t[label] = {"ms": 1e3 * (time.perf_counter() - t0), "expansions": fr["mu_iters"], "m": fr["m"],
+                               "status": fr["status"], "trace_error": fr["trace"] - w.n_occ(Pg),
+                               "D_blocks": Db.blocks(), "H_blocks": Hb.blocks()}
+        del Hb, Db, fws, mws
+        torch.cuda.empty_cache()
+        Mw = w.masses(Pg)
+        st = MDState(dw, thermal_velocities(Mw, 300.0, seed=100), Mw, w.n_occ(Pg), XL.K, og, kT=0.2, fermi=fo,
+                     bsr_cap=(64 * nsbw, 64 * nsbw))
+        it = tbmd.xlbomd_init(ctx, TPg, st.st, xp, og, 1e-6, 40)
+        tbmd.xlbomd_step(ctx, TPg, st.st, xp, og)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            tbmd.xlbomd_step(ctx, TPg, st.st, xp, og)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        finite_t["xlbomd_ms_per_step"] = e0.elapsed_time(e1) / 3
+        finite_t["xlbomd_scf_init_iters"] = it
+        finite_t["system"] = (f"gapped vapour {w.natoms} atoms (n={nw}), kT=0.2 eV, tau=1e-5, BSR in and out; "
+                              "the chemical potential on the host between expansions")
+        del st, dw
+        torch.cuda.empty_cache()
     line = _common(args, "thresholded block-sparse SP2: block-product TFLOP/s", value, "TFLOP/s",
                    total / args.steps, f"{args.precision}+f64",
                    f"{s.natoms} atoms, n={n}, 1.0 g/cc, Morton order, seed 0; SP2 with "
@@ -859,6 +910,7 @@ def run_sparse(args):
                            "boundary": "BSR matrices", "compare": md},
                    xlbomd_linear_scaling={"system": "gapped recipe vapour, 0.1 g/cc, Morton order, tau=1e-5, "
                                                     "BSR state (no n x n or N x N array)", "sizes": scaling},
+                   finite_temperature_block_sparse=finite_t,
                    drift_200_steps={"system": f"gapped recipe, {sub.natoms} atoms (682 H2O-like molecules, "
                                               "the 1/8-size subsystem), 0.1 g/cc, Morton order, T_e = 0, "
                                               "kappa = kappa0/2", **drift,

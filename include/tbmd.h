@@ -466,6 +466,38 @@ int tb_build_H_bsr(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const 
 int dm_sp2_sparse(tb_ctx* ctx, const tb_bsr* H, double n_occ, const tb_sp2_opts* opts, tb_bsr* D,
                   void* workspace, size_t workspace_bytes, tb_sp2_report* report, void* stream);
 
+/* Workspace bytes of dm_fermi_sparse: seven block-sparse matrices (the iterate E twice, the
+ * start L and the factors of each doubling step) of blocks_per_row x ceil(n/128) blocks of
+ * 128 x 128 (FP32 master and operand splits; blocks_per_row <= 0: every block) and the
+ * symbolic arrays.  TB_ERR_UNSUPPORTED for n > 131072. */
+int dm_fermi_sparse_workspace_size(int n, const tb_fermi_opts* opts, int blocks_per_row, size_t* bytes);
+
+/* Linear-scaling finite-temperature density matrix (row f2): the Fermi operator
+ * D = (exp(beta (H - mu I)) + 1)^-1 with Tr D = n_occ (Eq. EL_4c, Eq. DM_perp; canonical) by
+ * the recursive Fermi-operator expansion of dm_fermi (the construction the paper cites for
+ * linear scaling at T_e > 0 and leaves unimplemented, end of Sec. III.C) on thresholded
+ * block-sparse products: the start L = beta/2^(m+2) (mu I - H) and every product of the
+ * expansion drop the 32 x 32 blocks with Frobenius norm < tau (the block reading of
+ * Sec. III.B's threshold); the affine steps I -+ 2E and 2I - W are exact.  Per doubling step
+ * W = (I - 2E)(I + 2E), A = 2I - W, Z = (32 A^2 - 144 A + 210 I)/99, ns_iters - 1
+ * Newton-Schulz steps Z <- Z (2I - A Z), E <- E + E (Z W); m as in dm_fermi (the fewest
+ * >= 8 with beta (eps_max - eps_min + 80 kT + 2 eV) <= 2^(m+1), at most opts.m).  D = I/2 + E.
+ * The chemical potential is chosen on the host between expansions (dm_fermi's rule: Newton,
+ * the gap-tail balance, bisection), from Tr D = n/2 + Tr E and Tr D(I - D) = n/4 - ||E||_F^2,
+ * which it reads back after each expansion: the call synchronises `stream` once per
+ * expansion and cannot be captured in a graph (TB_ERR_UNSUPPORTED).  No canonical shift:
+ * expansions repeat until |Tr D - n_occ| <= opts.trace_tol (0: 1e-6 + 1e-9 n_occ) or
+ * opts.mu_iters (1..100) have run (report status TB_ERR_NOT_CONVERGED, D of the last one).
+ *   H: BSR (n <= 131072; H.status TB_OK, else TB_ERR_OOM in the report); tau > 0; kT > 0;
+ *   blocks_per_row: capacity of every iterate as in tb_sp2_opts.bsr_blocks_per_row, exceeded:
+ *   report status TB_ERR_OOM and an empty D; D: BSR output (blocks FP32-accurate, stored as
+ *   FP64; D.status TB_ERR_OOM when more than D.cap blocks); mu: device double, in = initial
+ *   guess (NaN or outside the Gershgorin bracket: the spectral midpoint), out = the chemical
+ *   potential of D (written when the status is TB_OK); report: device or NULL. */
+int dm_fermi_sparse(tb_ctx* ctx, const tb_bsr* H, double n_occ, double kT, const tb_fermi_opts* opts,
+                    double tau, int blocks_per_row, tb_bsr* D, double* mu, void* workspace,
+                    size_t workspace_bytes, tb_fermi_report* report, void* stream);
+
 /* Mulliken charges (a7) from a BSR D: q_i = 2 sum_{a in i} D_aa - N0_i. */
 int mulliken_bsr(tb_ctx* ctx, const tb_params* p, const tb_system* sys, const tb_bsr* D, double* q,
                  void* stream);
@@ -552,9 +584,11 @@ typedef struct {
   void* nonorth_workspace;    /* dm_nonorth workspace (dm_nonorth_workspace_size) */
   size_t nonorth_workspace_bytes;
   tb_nonorth_report* nonorth_report;  /* device, may be NULL */
-  /* block-sparse boundary (T_e = 0, orthogonal, sp2 opts with tau > 0): when H_bsr is set the
-   * step builds H in BSR, runs dm_sp2_sparse into D_bsr, and takes q, F, E from it; H, D and
-   * gamma may then be NULL (no n x n or N x N array) */
+  /* block-sparse boundary (orthogonal, sp2 opts with tau > 0): when H_bsr is set the step
+   * builds H in BSR, runs dm_sp2_sparse (kT = 0) or dm_fermi_sparse (kT > 0, with the fermi
+   * options, sp2 opts' tau and bsr_blocks_per_row; no entropy term; the workspace from
+   * dm_fermi_sparse_workspace_size) into D_bsr, and takes q, F, E from it; H, D and gamma
+   * may then be NULL (no n x n or N x N array) */
   tb_bsr* H_bsr;
   tb_bsr* D_bsr;
   void* bsr_workspace;        /* tb_bsr_model_workspace_size */

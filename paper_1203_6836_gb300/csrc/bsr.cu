@@ -35,6 +35,8 @@
 #include "tc_ptx.cuh"
 
 #include <algorithm>
+#include <cmath>
+#include <vector>
 
 namespace {
 
@@ -83,6 +85,20 @@ struct Args {
   const double* parts_in;
   int nparts_in;
   double* parts_out;
+  // start X0 = x0_s (x0_e I - H); x0_s = 0: the SP2 start from the Gershgorin
+  // bounds in st (e = eps_max, s = 1/(eps_max - eps_min))
+  double x0_e, x0_s;
+  int keep_diag;          // every pattern stores the diagonal blocks
+  int same_ab;            // the product's operands are one matrix
+};
+
+// Epilogue of a product C = alpha A B + gamma S + delta I: (alpha, gamma) =
+// (a1, g1) when branch is set and bit k of the SP2 branch record is, else
+// (a0, g0); delta on the diagonal of the n x n block.  lolo: also the lo x lo
+// split product (squares, where it keeps the diagonal unbiased).
+struct Epi {
+  float a0, g0, a1, g1, d;
+  int branch, lolo;
 };
 
 __device__ __forceinline__ int popc_below(const uint32_t* m, int bit) {
@@ -90,6 +106,17 @@ __device__ __forceinline__ int popc_below(const uint32_t* m, int bit) {
   for (int w = 0; w < (bit >> 5); ++w) r += __popc(m[w]);
   const uint32_t part = m[bit >> 5] & ((1u << (bit & 31)) - 1u);
   return r + __popc(part);
+}
+
+// Row of slot o of b: the last row whose start is <= o.
+__device__ __forceinline__ int slot_row(const Buf& b, int nsb, int o) {
+  int lo = 0, hi = nsb;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (b.row_ptr[mid] <= o) lo = mid;
+    else hi = mid;
+  }
+  return lo;
 }
 
 // ------------------------------------------------------------------ init
@@ -109,40 +136,68 @@ __global__ void k_bsr_bounds(const double* bparts, int nb, SP2State* st) {
   }
 }
 
+// (e, s) of the start X0 = s (e I - H).
+__device__ __forceinline__ void x0_affine(const Args& a, double* e, double* s) {
+  if (a.x0_s != 0.0) {
+    *e = a.x0_e;
+    *s = a.x0_s;
+    return;
+  }
+  const double emin = a.st->emin, emax = a.st->emax;
+  double w = emax - emin;
+  if (!(w > 0.0)) w = 1.0;
+  *e = emax;
+  *s = 1.0 / w;
+}
+
 __device__ __forceinline__ double x0_val(const double* H, int n, int r, int c, double emax, double inv) {
   if (r >= n || c >= n) return 0.0;
   return ((r == c ? emax : 0.0) - H[(size_t)r * n + c]) * inv;
 }
 
-// One block per super-block (I, J) of X0: the 16 sub-block norms of
-// X0 = (emax I - H)/(emax - emin), kept where ||.||_F >= tau.
-__global__ void __launch_bounds__(256) k_bsr_init_flags(const double* __restrict__ H, Args a, Sym sy) {
+// Keep mask of super-block (I, J) of X0 from the per-row sums of squares rs
+// of its upper twin (min(I,J), max(I,J)) (256 threads: row r = tid / 2,
+// columns 64 (tid % 2) ..): the 16 sub-block norms summed in a fixed order,
+// kept where ||.||_F >= tau; below the diagonal the twin's mask transposed,
+// so that the pattern is exactly symmetric (the products compute upper
+// blocks and mirror them).
+__device__ uint16_t keep_mask(const Args& a, int I, int J, double (*rs)[4]) {
   __shared__ double sq[16];
-  if (threadIdx.x < 16) sq[threadIdx.x] = 0.0;
   __syncthreads();
+  if (threadIdx.x < 16) {
+    const int rb = threadIdx.x >> 2, cb = threadIdx.x & 3;
+    double t = 0.0;
+    for (int rr = 0; rr < 32; ++rr) t += rs[32 * rb + rr][cb];
+    sq[threadIdx.x] = t;
+  }
+  __syncthreads();
+  uint16_t f = 0;
+  for (int s = 0; s < 16; ++s)
+    if (sq[s] >= a.tau2 && sq[s] > 0.0) f |= (uint16_t)(1u << (I <= J ? s : (s & 3) * 4 + (s >> 2)));
+  return f;
+}
+
+// One block per super-block (I, J) of X0 = s (e I - H): its keep mask.
+__global__ void __launch_bounds__(256) k_bsr_init_flags(const double* __restrict__ H, Args a, Sym sy) {
+  __shared__ double rs[SB][4];
   const int I = blockIdx.y, J = blockIdx.x;
-  const double emin = a.st->emin, emax = a.st->emax;
-  double w = emax - emin;
-  if (!(w > 0.0)) w = 1.0;
-  const double inv = 1.0 / w;
+  const int I0 = min(I, J), J0 = max(I, J);
+  double emax, inv;
+  x0_affine(a, &emax, &inv);
   const int r = threadIdx.x >> 1, h = threadIdx.x & 1;
   double part[2] = {0.0, 0.0};
   for (int c = 0; c < 64; ++c) {
-    const double x = x0_val(H, a.n, I * SB + r, J * SB + 64 * h + c, emax, inv);
+    const double x = x0_val(H, a.n, I0 * SB + r, J0 * SB + 64 * h + c, emax, inv);
     part[c >> 5] += x * x;
   }
-  atomicAdd(&sq[(r >> 5) * 4 + 2 * h], part[0]);
-  atomicAdd(&sq[(r >> 5) * 4 + 2 * h + 1], part[1]);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint16_t f = 0;
-    for (int s = 0; s < 16; ++s)
-      if (sq[s] >= a.tau2 && sq[s] > 0.0) f |= (uint16_t)(1u << s);
-    sy.flags[(size_t)I * a.nsb + J] = f;
-  }
+  rs[r][2 * h] = part[0];
+  rs[r][2 * h + 1] = part[1];
+  const uint16_t f = keep_mask(a, I, J, rs);
+  if (threadIdx.x == 0) sy.flags[(size_t)I * a.nsb + J] = f;
 }
 
-// Row I of X0: stored = live bitmap of its kept super-blocks, count.
+// Row I of X0: live bitmap of its kept super-blocks; stored = live (and the
+// diagonal block with keep_diag); count of stored blocks.
 __global__ void k_bsr_init_rows(Args a, Sym sy, Buf b) {
   const int I = blockIdx.x;
   __shared__ uint32_t m[MW];
@@ -152,9 +207,12 @@ __global__ void k_bsr_init_rows(Args a, Sym sy, Buf b) {
     if (sy.flags[(size_t)I * a.nsb + J]) atomicOr(&m[J >> 5], 1u << (J & 31));
   __syncthreads();
   if (threadIdx.x < MW) {
-    b.stored[I * MW + threadIdx.x] = m[threadIdx.x];
+    const uint32_t diag = (a.keep_diag && (I >> 5) == (int)threadIdx.x) ? 1u << (I & 31) : 0u;
+    b.stored[I * MW + threadIdx.x] = m[threadIdx.x] | diag;
     b.live[I * MW + threadIdx.x] = m[threadIdx.x];
+    m[threadIdx.x] |= diag;
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
     int c = 0;
     for (int w = 0; w < MW; ++w) c += __popc(m[w]);
@@ -183,18 +241,16 @@ template <int P>
 __global__ void __launch_bounds__(256) k_bsr_init_fill(const double* __restrict__ H, Args a, Sym sy, Buf b) {
   if (a.st->err) return;
   const int I = blockIdx.x;
-  const double emin = a.st->emin, emax = a.st->emax;
-  double w = emax - emin;
-  if (!(w > 0.0)) w = 1.0;
-  const double inv = 1.0 / w;
+  double emax, inv;
+  x0_affine(a, &emax, &inv);
   double t1 = 0.0, t2 = 0.0;
   int o = b.row_ptr[I];
   for (int J = 0; J < a.nsb; ++J) {
     const uint16_t f = sy.flags[(size_t)I * a.nsb + J];
-    if (!f) continue;
+    if (!f && !(a.keep_diag && J == I)) continue;
     if (threadIdx.x == 0) {
       b.col[o] = J;
-      b.nz[o] = 1;
+      b.nz[o] = f != 0;
     }
     // 128 rows x 4 segments of 32: 512 segments over 256 threads
     for (int seg = threadIdx.x; seg < SB * 4; seg += blockDim.x) {
@@ -306,39 +362,31 @@ __global__ void k_bsr_status_in(const int* Hstatus, SP2State* st) {
 }
 
 __global__ void __launch_bounds__(256) k_bsr_init_flags_in(tb_bsr H, Args a, Sym sy) {
-  __shared__ double sq[16];
+  __shared__ double rs[SB][4];
   const int I = blockIdx.y, J = blockIdx.x;
+  const int I0 = min(I, J), J0 = max(I, J);
   if (*H.status != TB_OK) {
     if (threadIdx.x == 0) sy.flags[(size_t)I * a.nsb + J] = 0;
     return;
   }
-  const int slot = bsr_find(H.row_ptr, H.col, I, J);
+  const int slot = bsr_find(H.row_ptr, H.col, I0, J0);
   if (slot < 0 && I != J) {
     if (threadIdx.x == 0) sy.flags[(size_t)I * a.nsb + J] = 0;
     return;
   }
   const double* blk = slot >= 0 ? H.val + (size_t)slot * kTiles : nullptr;
-  if (threadIdx.x < 16) sq[threadIdx.x] = 0.0;
-  __syncthreads();
-  const double emin = a.st->emin, emax = a.st->emax;
-  double w = emax - emin;
-  if (!(w > 0.0)) w = 1.0;
-  const double inv = 1.0 / w;
+  double emax, inv;
+  x0_affine(a, &emax, &inv);
   const int r = threadIdx.x >> 1, h = threadIdx.x & 1;
   double part[2] = {0.0, 0.0};
   for (int c = 0; c < 64; ++c) {
-    const double x = x0_blk(blk, I, J, a.n, r, 64 * h + c, emax, inv);
+    const double x = x0_blk(blk, I0, J0, a.n, r, 64 * h + c, emax, inv);
     part[c >> 5] += x * x;
   }
-  atomicAdd(&sq[(r >> 5) * 4 + 2 * h], part[0]);
-  atomicAdd(&sq[(r >> 5) * 4 + 2 * h + 1], part[1]);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint16_t f = 0;
-    for (int s2 = 0; s2 < 16; ++s2)
-      if (sq[s2] >= a.tau2 && sq[s2] > 0.0) f |= (uint16_t)(1u << s2);
-    sy.flags[(size_t)I * a.nsb + J] = f;
-  }
+  rs[r][2 * h] = part[0];
+  rs[r][2 * h + 1] = part[1];
+  const uint16_t f = keep_mask(a, I, J, rs);
+  if (threadIdx.x == 0) sy.flags[(size_t)I * a.nsb + J] = f;
 }
 
 // As k_bsr_init_fill, from the blocks of a BSR H.
@@ -346,20 +394,18 @@ template <int P>
 __global__ void __launch_bounds__(256) k_bsr_init_fill_in(tb_bsr H, Args a, Sym sy, Buf b) {
   if (a.st->err) return;
   const int I = blockIdx.x;
-  const double emin = a.st->emin, emax = a.st->emax;
-  double w = emax - emin;
-  if (!(w > 0.0)) w = 1.0;
-  const double inv = 1.0 / w;
+  double emax, inv;
+  x0_affine(a, &emax, &inv);
   double t1 = 0.0, t2 = 0.0;
   int o = b.row_ptr[I];
   for (int J = 0; J < a.nsb; ++J) {
     const uint16_t f = sy.flags[(size_t)I * a.nsb + J];
-    if (!f) continue;
+    if (!f && !(a.keep_diag && J == I)) continue;
     const int slot = bsr_find(H.row_ptr, H.col, I, J);
     const double* blk = slot >= 0 ? H.val + (size_t)slot * kTiles : nullptr;
     if (threadIdx.x == 0) {
       b.col[o] = J;
-      b.nz[o] = 1;
+      b.nz[o] = f != 0;
     }
     for (int seg = threadIdx.x; seg < SB * 4; seg += blockDim.x) {
       const int r = seg >> 2, cs = seg & 3;
@@ -402,6 +448,21 @@ __global__ void __launch_bounds__(256) k_bsr_init_fill_in(tb_bsr H, Args a, Sym 
 }
 
 // ------------------------------------------------------- per projection
+
+// Bitmaps of row I of b: stored blocks and live (not all-zero) blocks; ms and
+// ml are zeroed shared arrays of the calling block.
+__device__ void row_bitmaps(const Buf& b, int I, uint32_t* ms, uint32_t* ml) {
+  for (int o = b.row_ptr[I] + threadIdx.x; o < b.row_ptr[I + 1]; o += blockDim.x) {
+    const int J = b.col[o];
+    atomicOr(&ms[J >> 5], 1u << (J & 31));
+    if (b.nz[o]) atomicOr(&ml[J >> 5], 1u << (J & 31));
+  }
+  __syncthreads();
+  if (threadIdx.x < MW) {
+    b.stored[I * MW + threadIdx.x] = ms[threadIdx.x];
+    b.live[I * MW + threadIdx.x] = ml[threadIdx.x];
+  }
+}
 
 // Decision for projection k (every block the same) and the bitmaps of row I
 // of X_k: stored blocks and live (not all-zero) blocks.
@@ -448,32 +509,51 @@ __global__ void k_bsr_decide(Args a, Buf b) {
   }
   __syncthreads();
   if (s_stop) return;
-  const int I = blockIdx.x;
-  for (int o = b.row_ptr[I] + threadIdx.x; o < b.row_ptr[I + 1]; o += blockDim.x) {
-    const int J = b.col[o];
-    atomicOr(&ms[J >> 5], 1u << (J & 31));
-    if (b.nz[o]) atomicOr(&ml[J >> 5], 1u << (J & 31));
-  }
-  __syncthreads();
-  if (threadIdx.x < MW) {
-    b.stored[I * MW + threadIdx.x] = ms[threadIdx.x];
-    b.live[I * MW + threadIdx.x] = ml[threadIdx.x];
-  }
+  row_bitmaps(b, blockIdx.x, ms, ml);
 }
 
-// Candidate columns of row I: OR of the live bitmaps of its live columns.
-__global__ void k_bsr_cand(Args a, Buf b, Sym sy) {
+// Bitmaps of stored and live blocks of every row of a product's output.
+__global__ void k_bsr_bitmaps(Args a, Buf b) {
+  __shared__ uint32_t ms[MW], ml[MW];
+  if (a.st->done || a.st->err) return;
+  if (threadIdx.x < MW) {
+    ms[threadIdx.x] = 0u;
+    ml[threadIdx.x] = 0u;
+  }
+  __syncthreads();
+  row_bitmaps(b, blockIdx.x, ms, ml);
+}
+
+// Candidate columns of row I of A B: the OR of B's live rows over A's live
+// columns of row I; unless A and B are one matrix also the same with A and B
+// exchanged (the pattern of B A = (A B)^T), so that the pattern is symmetric
+// as the upper-block computation with mirrors needs; S's live blocks; the
+// diagonal block with keep_diag.  A and B are symmetric (rows = columns).
+__global__ void k_bsr_cand(Args a, Buf A, Buf B, Buf S, Sym sy) {
   __shared__ uint32_t c[MW];
   if (a.st->done || a.st->err) return;
   const int I = blockIdx.x;
   if (threadIdx.x < MW) c[threadIdx.x] = 0u;
   __syncthreads();
-  const uint32_t* li = b.live + I * MW;
-  for (int K = threadIdx.x; K < a.nsb; K += blockDim.x)
-    if ((li[K >> 5] >> (K & 31)) & 1u)
-      for (int w = 0; w < a.mw; ++w) atomicOr(&c[w], b.live[K * MW + w]);
+  for (int side = 0; side < (a.same_ab ? 1 : 2); ++side) {
+    const uint32_t* li = (side ? B.live : A.live) + I * MW;
+    const uint32_t* rows = side ? A.live : B.live;
+    for (int K = threadIdx.x; K < a.nsb; K += blockDim.x)
+      if ((li[K >> 5] >> (K & 31)) & 1u)
+        for (int w = 0; w < a.mw; ++w) {
+          const uint32_t v = rows[K * MW + w];
+          if (v) atomicOr(&c[w], v);
+        }
+  }
   __syncthreads();
-  if (threadIdx.x < MW) sy.cand[I * MW + threadIdx.x] = c[threadIdx.x];
+  if (threadIdx.x < MW) {
+    uint32_t v = c[threadIdx.x];
+    if (S.live) v |= S.live[I * MW + threadIdx.x];
+    if (a.keep_diag && (I >> 5) == (int)threadIdx.x) v |= 1u << (I & 31);
+    sy.cand[I * MW + threadIdx.x] = v;
+    c[threadIdx.x] = v;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     int s = 0;
     for (int w = 0; w < MW; ++w) s += __popc(c[w]);
@@ -481,23 +561,23 @@ __global__ void k_bsr_cand(Args a, Buf b, Sym sy) {
   }
 }
 
-// Output blocks of row I: column, source slot of X_IJ (or -1), pair count.
-__global__ void k_bsr_fill_out(Args a, Buf bo, Buf bn, Sym sy) {
+// Output blocks of row I: column, slot of S_IJ (or -1), pair count.
+__global__ void k_bsr_fill_out(Args a, Buf A, Buf B, Buf S, Buf bn, Sym sy) {
   if (a.st->done || a.st->err) return;
   const int I = blockIdx.x;
   const uint32_t* ci = sy.cand + I * MW;
-  const uint32_t* si = bo.stored + I * MW;
-  const uint32_t* li = bo.live + I * MW;
+  const uint32_t* si = S.stored ? S.stored + I * MW : nullptr;
+  const uint32_t* li = A.live + I * MW;
   for (int J = threadIdx.x; J < a.nsb; J += blockDim.x) {
     if (!((ci[J >> 5] >> (J & 31)) & 1u)) continue;
     const int o = bn.row_ptr[I] + popc_below(ci, J);
     bn.col[o] = J;
     bn.nz[o] = 0;
     sy.out_row[o] = I;
-    sy.old_idx[o] = ((si[J >> 5] >> (J & 31)) & 1u) ? bo.row_ptr[I] + popc_below(si, J) : -1;
+    sy.old_idx[o] = (si && ((si[J >> 5] >> (J & 31)) & 1u)) ? S.row_ptr[I] + popc_below(si, J) : -1;
     int pc = 0;
-    const uint32_t* lj = bo.live + J * MW;
-    if (J >= I)  // X^2 is symmetric: blocks below the diagonal are written as mirrors
+    const uint32_t* lj = B.live + J * MW;
+    if (J >= I)  // the product is symmetric: blocks below the diagonal are written as mirrors
       for (int w = 0; w < a.mw; ++w) pc += __popc(li[w] & lj[w]);
     sy.pcnt[o] = pc;
   }
@@ -534,17 +614,18 @@ __global__ void __launch_bounds__(1024) k_bsr_scan_pairs(Args a, Sym sy) {
   }
 }
 
-// Pairs (slot of X_IK, slot of X_JK) of every output block (I, J).
-__global__ void k_bsr_pairs(Args a, Buf bo, Buf bn, Sym sy) {
+// Pairs (slot of A_IK, slot of B_JK) of every upper output block (I, J):
+// (A B)_IJ = sum_K A_IK B_JK^T for a symmetric B.
+__global__ void k_bsr_pairs(Args a, Buf A, Buf B, Buf bn, Sym sy) {
   if (a.st->done || a.st->err) return;
   const int nb = sy.scal[0];
   for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < nb; o += gridDim.x * blockDim.x) {
     const int I = sy.out_row[o], J = bn.col[o];
     if (J < I) continue;
-    const uint32_t* li = bo.live + I * MW;
-    const uint32_t* lj = bo.live + J * MW;
-    const uint32_t* si = bo.stored + I * MW;
-    const uint32_t* sj = bo.stored + J * MW;
+    const uint32_t* li = A.live + I * MW;
+    const uint32_t* lj = B.live + J * MW;
+    const uint32_t* si = A.stored + I * MW;
+    const uint32_t* sj = B.stored + J * MW;
     int p = sy.pair_ptr[o];
     // the mirrored block (J, I) of the full product has as many block products
     if (J > I) atomicAdd(&a.st->block_products, (unsigned long long)sy.pcnt[o]);
@@ -553,7 +634,7 @@ __global__ void k_bsr_pairs(Args a, Buf bo, Buf bn, Sym sy) {
       while (m) {
         const int K = 32 * w + __ffs(m) - 1;
         m &= m - 1u;
-        sy.pairs[p++] = make_int2(bo.row_ptr[I] + popc_below(si, K), bo.row_ptr[J] + popc_below(sj, K));
+        sy.pairs[p++] = make_int2(A.row_ptr[I] + popc_below(si, K), B.row_ptr[J] + popc_below(sj, K));
       }
     }
   }
@@ -610,17 +691,20 @@ __global__ void __launch_bounds__(1024) k_bsr_order(Args a, Buf bn, Sym sy) {
 // Persistent numeric projection.
 template <int P>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_bsr_step_tc(Args a, const __grid_constant__ CUtensorMap mh, const __grid_constant__ CUtensorMap ml,
-                  Buf bo, Buf bn, Sym sy) {
+    k_bsr_step_tc(Args a, const __grid_constant__ CUtensorMap ah, const __grid_constant__ CUtensorMap al,
+                  const __grid_constant__ CUtensorMap bh, const __grid_constant__ CUtensorMap bl, Buf S, Buf bn,
+                  Sym sy, Epi ep) {
   using C = Prec<P>;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[C::stages], empty[C::stages], tfull[2], tempty[2], mdone;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_abort;
   __shared__ double s_red[4][3];
+  __shared__ float s_sym[4][32][33];  // per epilogue warp: one 32 x 32 diagonal sub-block
   SP2State* st = a.st;
   if (st->done || st->err) return;
-  const int br = (int)((st->branch[a.k >> 6] >> (a.k & 63)) & 1ull);
+  const int br = ep.branch ? (int)((st->branch[a.k >> 6] >> (a.k & 63)) & 1ull) : 0;
+  const float alpha = br ? ep.a1 : ep.a0, gamma = br ? ep.g1 : ep.g0;
   const int nu = sy.scal[2];  // upper output blocks, walked in sy.order
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -645,8 +729,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int chunks = SB / C::bk;  // k-steps of one super-block
 
   if (warp == 0 && lane == 0) {
-    prefetch_map(&mh);
-    if (C::split) prefetch_map(&ml);
+    prefetch_map(&ah);
+    prefetch_map(&bh);
+    if (C::split) {
+      prefetch_map(&al);
+      prefetch_map(&bl);
+    }
     int g = 0, issued = 0;
     for (int u = blockIdx.x; u < nu && !s_abort; u += gridDim.x) {
       const int o = sy.order[u];
@@ -658,11 +746,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (g >= C::stages && !mbar_wait(&empty[s], ((g / C::stages) - 1) & 1, &s_abort)) break;
           uint8_t* base = smem + s * C::stage_bytes;
           mbar_expect_tx(&full[s], C::stage_bytes);
-          tma_load_2d(base, &mh, &full[s], c * C::bk, pr.x * SB);
-          tma_load_2d(base + 128 * 128, &mh, &full[s], c * C::bk, pr.y * SB);
+          tma_load_2d(base, &ah, &full[s], c * C::bk, pr.x * SB);
+          tma_load_2d(base + 128 * 128, &bh, &full[s], c * C::bk, pr.y * SB);
           if constexpr (C::split) {
-            tma_load_2d(base + 2 * 128 * 128, &ml, &full[s], c * C::bk, pr.x * SB);
-            tma_load_2d(base + 3 * 128 * 128, &ml, &full[s], c * C::bk, pr.y * SB);
+            tma_load_2d(base + 2 * 128 * 128, &al, &full[s], c * C::bk, pr.x * SB);
+            tma_load_2d(base + 3 * 128 * 128, &bl, &full[s], c * C::bk, pr.y * SB);
           }
           issued = g + 1;
         }
@@ -695,14 +783,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int ks = 0; ks < C::bk / C::uk; ++ks) {
             const uint32_t koff = ks * 32;
-            const uint64_t ah = sdesc(base + koff), bh = sdesc(base + 128 * 128 + koff);
-            umma<C::tf32>(d, ah, bh, id, first ? 0u : 1u);
+            const uint64_t dah = sdesc(base + koff), dbh = sdesc(base + 128 * 128 + koff);
+            umma<C::tf32>(d, dah, dbh, id, first ? 0u : 1u);
             first = false;
             if constexpr (C::split) {
-              const uint64_t al = sdesc(base + 2 * 128 * 128 + koff), bl = sdesc(base + 3 * 128 * 128 + koff);
-              umma<C::tf32>(d, ah, bl, id, 1u);
-              umma<C::tf32>(d, al, bh, id, 1u);
-              umma<C::tf32>(d, al, bl, id, 1u);  // lo*lo: diagonal blocks sum squares (unbiased)
+              const uint64_t dal = sdesc(base + 2 * 128 * 128 + koff), dbl = sdesc(base + 3 * 128 * 128 + koff);
+              umma<C::tf32>(d, dah, dbl, id, 1u);
+              umma<C::tf32>(d, dal, dbh, id, 1u);
+              // lo x lo: in a square it keeps the diagonal blocks' sums of squares unbiased
+              if (ep.lolo) umma<C::tf32>(d, dal, dbl, id, 1u);
             }
           }
           umma_commit(&empty[s]);
@@ -731,13 +820,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int om = mirror ? bn.row_ptr[J] + popc_below(sy.cand + J * MW, I) : o;
       float* xmir = bn.val + (size_t)om * kTiles;
       const int oi = sy.old_idx[o];
-      const float* xold = oi >= 0 ? bo.val + (size_t)oi * kTiles + (size_t)row * SB : nullptr;
+      const float* xold = oi >= 0 ? S.val + (size_t)oi * kTiles + (size_t)row * SB : nullptr;
       float* xnew = bn.val + (size_t)o * kTiles + (size_t)row * SB;
       char* hrow = static_cast<char*>(bn.hi) + ((size_t)o * kTiles + (size_t)row * SB) * C::eb;
       char* lrow = bn.lo ? static_cast<char*>(bn.lo) + ((size_t)o * kTiles + (size_t)row * SB) * C::eb : hrow;
       int kept = 0;
+      // a diagonal block of a product of two matrices is not exactly symmetric
+      // in rounding (A B against B A): its upper triangle is kept and mirrored
+      const bool symd = I == J && !a.same_ab;
 #pragma unroll 1
       for (int c = 0; c < 4; ++c) {
+        if (symd && c < q) continue;  // written as the mirror of sub-block (c, q)
         uint32_t v[32];
         if (has) {
           tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + buf * SB + 32 * c, v);
@@ -751,9 +844,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int j = 0; j < 32; ++j) {
           const float cxx = __uint_as_float(v[j]);
           const float x = xold ? xold[32 * c + j] : 0.0f;
-          y[j] = br ? fmaf(2.0f, x, -cxx) : cxx;
-          ss += (double)y[j] * (double)y[j];
+          y[j] = fmaf(gamma, x, alpha * cxx);
+          if (ep.d != 0.0f && I == J && row == 32 * c + j && I * SB + row < a.n) y[j] += ep.d;
         }
+        if (symd && c == q) {
+          // the 32 x 32 diagonal sub-block: element (l, j) with j < l from lane j
+#pragma unroll
+          for (int j = 0; j < 32; ++j) s_sym[q][lane][j] = y[j];
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j < lane) y[j] = s_sym[q][j][lane];
+          __syncwarp();
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) ss += (double)y[j] * (double)y[j];
         ss = warp_sum(ss);  // squared Frobenius norm of sub-block (q, c)
         const bool keep = ss >= a.tau2 && ss > 0.0;
         if (!keep) {
@@ -768,14 +873,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           u2 += (double)y[j] * (double)y[j];
           if (I == J && row == 32 * c + j) t1 += (double)y[j];
         }
-        t2 += mirror ? 2.0 * u2 : u2;
+        const bool twice = mirror || (symd && c > q);
+        t2 += twice ? 2.0 * u2 : u2;
         float4* xo = reinterpret_cast<float4*>(xnew + 32 * c);
 #pragma unroll
         for (int j = 0; j < 8; ++j) xo[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
         store_operands<P>(y, hrow + 32 * c * C::eb, lrow + 32 * c * C::eb);
-        if (mirror) {
+        if (twice) {
           // element (row, 32c + j) of block (I, J) is element (32c + j, row) of
-          // block (J, I): for each j the 32 lanes write 32 consecutive values
+          // block (J, I) (of this block itself for symd): for each j the 32
+          // lanes write 32 consecutive values
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const size_t e = (size_t)(32 * c + j) * SB + row;
@@ -829,14 +936,7 @@ __global__ void k_bsr_to_dense(const SP2State* st, Args a, Buf b0, Buf b1, Sym s
   const Buf& b = (st->iters & 1) ? b1 : b0;
   const int nblk = min(b.row_ptr[a.nsb], a.cap);
   for (int o = blockIdx.x; o < nblk; o += gridDim.x) {
-    // the row of slot o: last row whose start is <= o
-    int lo = 0, hi = a.nsb;
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (b.row_ptr[mid] <= o) lo = mid;
-      else hi = mid;
-    }
-    const int I = lo, J = b.col[o];
+    const int I = slot_row(b, a.nsb, o), J = b.col[o];
     for (int e = threadIdx.x; e < kTiles; e += blockDim.x) {
       const int r = I * SB + e / SB, c = J * SB + e % SB;
       if (r < a.n && c < a.n) D[(size_t)r * a.n + c] = (double)b.val[(size_t)o * kTiles + e];
@@ -844,11 +944,54 @@ __global__ void k_bsr_to_dense(const SP2State* st, Args a, Buf b0, Buf b1, Sym s
   }
 }
 
-// Final iterate -> BSR D (structure and FP64 values); TB_ERR_OOM in D.status
-// when it holds more blocks than D.cap.
-__global__ void k_bsr_to_bsr(const SP2State* st, Args a, Buf b0, Buf b1, tb_bsr D) {
-  const Buf& b = (st->iters & 1) ? b1 : b0;
-  const int nblk = min(b.row_ptr[a.nsb], a.cap);
+// out = alpha X + delta I on X's pattern (X stores every diagonal block when
+// delta != 0): values, operand splits, live flags and bitmaps.  Exact up to
+// the FP32 rounding of the values; nothing is dropped.
+template <int P>
+__global__ void __launch_bounds__(256) k_bsr_affine(Args a, Buf X, Buf out, float alpha, float delta) {
+  if (a.st->done || a.st->err) return;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  for (int i = tid; i <= a.nsb; i += nth) out.row_ptr[i] = X.row_ptr[i];
+  for (int i = tid; i < a.nsb * MW; i += nth) {
+    const int I = i / MW, w = i % MW;
+    out.stored[i] = X.stored[i];
+    out.live[i] = X.live[i] | ((delta != 0.0f && (I >> 5) == w) ? 1u << (I & 31) : 0u);
+  }
+  const int nblk = X.row_ptr[a.nsb];
+  for (int o = blockIdx.x; o < nblk; o += gridDim.x) {
+    const int I = slot_row(X, a.nsb, o), J = X.col[o];
+    const bool diag = I == J && delta != 0.0f;
+    if (threadIdx.x == 0) {
+      out.col[o] = J;
+      out.nz[o] = X.nz[o] | (diag ? 1 : 0);
+    }
+    for (int seg = threadIdx.x; seg < SB * 4; seg += blockDim.x) {
+      const int r = seg >> 2, cs = seg & 3;
+      const size_t e0 = (size_t)o * kTiles + (size_t)r * SB + 32 * cs;
+      float y[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        y[j] = alpha * X.val[e0 + j];
+        if (diag && r == 32 * cs + j && I * SB + r < a.n) y[j] += delta;
+      }
+      float* dst = out.val + e0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) dst[j] = y[j];
+      char* hp = static_cast<char*>(out.hi) + e0 * Prec<P>::eb;
+      char* lp = out.lo ? static_cast<char*>(out.lo) + e0 * Prec<P>::eb : hp;
+      store_operands<P>(y, hp, lp);
+    }
+  }
+}
+
+// Final iterate -> BSR D (structure and FP64 values, plus dshift on the
+// diagonal of the n x n block); TB_ERR_OOM in D.status when it holds more
+// blocks than D.cap.  sel < 0: the SP2 iterate (buffer by the iteration
+// count), else buffer sel.
+__global__ void k_bsr_to_bsr(const SP2State* st, Args a, Buf b0, Buf b1, int sel, double dshift, tb_bsr D) {
+  const Buf& b = (sel < 0 ? (st->iters & 1) : sel) ? b1 : b0;
+  // after an error the iterate may never have been written: no blocks
+  const int nblk = st->err ? 0 : min(b.row_ptr[a.nsb], a.cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) *D.status = nblk > D.cap ? TB_ERR_OOM : TB_OK;
   if (nblk > D.cap || st->err) {
     // an empty matrix: no row holds a block
@@ -858,10 +1001,16 @@ __global__ void k_bsr_to_bsr(const SP2State* st, Args a, Buf b0, Buf b1, tb_bsr 
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= a.nsb; i += gridDim.x * blockDim.x)
     D.row_ptr[i] = b.row_ptr[i];
   for (int o = blockIdx.x; o < nblk; o += gridDim.x) {
-    if (threadIdx.x == 0) D.col[o] = b.col[o];
+    const int J = b.col[o];
+    if (threadIdx.x == 0) D.col[o] = J;
+    const int I = dshift != 0.0 ? slot_row(b, a.nsb, o) : -1;
     const float* src = b.val + (size_t)o * kTiles;
     double* dst = D.val + (size_t)o * kTiles;
-    for (int e = threadIdx.x; e < kTiles; e += blockDim.x) dst[e] = (double)src[e];
+    for (int e = threadIdx.x; e < kTiles; e += blockDim.x) {
+      const int r = e / SB;
+      const bool dg = I == J && r == e % SB && I * SB + r < a.n;
+      dst[e] = (double)src[e] + (dg ? dshift : 0.0);
+    }
   }
 }
 
@@ -889,25 +1038,30 @@ __global__ void k_bsr_report(SP2State* st, Args a, Buf b0, Buf b1, tb_sp2_report
   rep->blocks = min(b.row_ptr[a.nsb], a.cap);
 }
 
+constexpr int kMaxBufs = 7;  // matrices of the Fermi expansion (SP2: two)
+
 struct BsrLayout {
-  int n, ld, nsb, cap, pcap;
+  int n, ld, nsb, cap, pcap, nbuf;
   size_t off_state, off_bparts, off_parts, off_scal, off_flags, off_cand, off_cnt, off_outrow, off_oldidx,
       off_pcnt, off_pptr, off_pairs, off_order;
-  size_t off_rp[2], off_col[2], off_nz[2], off_st[2], off_lv[2], off_val[2], off_hi[2], off_lo[2];
+  size_t off_rp[kMaxBufs], off_col[kMaxBufs], off_nz[kMaxBufs], off_st[kMaxBufs], off_lv[kMaxBufs],
+      off_val[kMaxBufs], off_hi[kMaxBufs], off_lo[kMaxBufs];
   size_t total;
   int nparts;
 };
 
-BsrLayout bsr_layout(int n, int prec, int bpr, int nsm) {
+// Workspace of nbuf block-sparse matrices of bpr blocks per block row on
+// average (0: every block) and the shared symbolic arrays.
+BsrLayout bsr_layout(int n, int prec, int bpr, int nbuf) {
   BsrLayout L{};
   L.n = n;
   L.ld = round_up(std::max(n, 1), SB);
   L.nsb = L.ld / SB;
+  L.nbuf = nbuf;
   const int per_row = (bpr <= 0 || bpr > L.nsb) ? L.nsb : bpr;
   L.cap = L.nsb * per_row;
   L.pcap = L.cap * per_row;
   L.nparts = std::max(L.nsb, kMaxGrid);
-  (void)nsm;
   size_t o = 0;
   auto take = [&](size_t bytes) {
     size_t r = o;
@@ -917,7 +1071,7 @@ BsrLayout bsr_layout(int n, int prec, int bpr, int nsm) {
   const size_t eb = (prec == TB_PREC_TF32 || prec == TB_PREC_TF32X3) ? 4 : 2;
   const bool split = prec == TB_PREC_TF32X3 || prec == TB_PREC_BF16X3;
   L.off_state = take(sizeof(SP2State));
-  L.off_bparts = take(sizeof(double) * 2 * ((n + 7) / 8));
+  L.off_bparts = take(sizeof(double) * 2 * std::max((n + 7) / 8, L.nsb));
   L.off_parts = take(sizeof(double) * 3 * 2 * L.nparts);
   L.off_scal = take(sizeof(int) * 4);
   L.off_flags = take(sizeof(uint16_t) * (size_t)L.nsb * L.nsb);
@@ -929,7 +1083,7 @@ BsrLayout bsr_layout(int n, int prec, int bpr, int nsm) {
   L.off_pptr = take(sizeof(int) * (L.cap + 1));
   L.off_pairs = take(sizeof(int2) * (size_t)L.pcap);
   L.off_order = take(sizeof(int) * L.cap);
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < nbuf; ++b) {
     L.off_rp[b] = take(sizeof(int) * (L.nsb + 1));
     L.off_col[b] = take(sizeof(int) * L.cap);
     L.off_nz[b] = take(sizeof(int) * L.cap);
@@ -958,19 +1112,29 @@ int make_block_map(tb_ctx* ctx, int prec, const void* base, int rows, CUtensorMa
   return TB_OK;
 }
 
-// H dense (Hb null) or BSR (Hb); D dense or BSR (Db).
-template <int P>
-int run_bsr(tb_ctx* ctx, const double* H, const tb_bsr* Hb, int n, double nocc, const tb_sp2_opts* o, double* D,
-            tb_bsr* Db, void* ws, size_t ws_bytes, tb_sp2_report* rep, cudaStream_t s) {
-  const BsrLayout L = bsr_layout(n, o->precision, o->bsr_blocks_per_row, ctx->sm_count);
-  if (ws_bytes < L.total)
-    return tb_fail(ctx, TB_ERR_ARG, "workspace %zu bytes < required %zu (block-sparse)", ws_bytes, L.total);
+// One block-sparse matrix of the workspace and the tensor maps of its operands.
+struct Mat {
+  Buf b;
+  CUtensorMap mh, ml;
+};
+
+// The workspace bound to its parts.
+struct Engine {
+  BsrLayout L;
+  SP2State* st;
+  double* bparts;
+  double* parts;  // two slots of 3 * nparts
+  Sym sy;
+  Mat m[kMaxBufs];
+};
+
+int bind_engine(tb_ctx* ctx, int prec, const BsrLayout& L, void* ws, Engine* e) {
   char* base = static_cast<char*>(ws);
-  SP2State* st = reinterpret_cast<SP2State*>(base + L.off_state);
-  double* bparts = reinterpret_cast<double*>(base + L.off_bparts);
-  double* parts = reinterpret_cast<double*>(base + L.off_parts);
-  double* slot[2] = {parts, parts + 3 * (size_t)L.nparts};
-  Sym sy{};
+  e->L = L;
+  e->st = reinterpret_cast<SP2State*>(base + L.off_state);
+  e->bparts = reinterpret_cast<double*>(base + L.off_bparts);
+  e->parts = reinterpret_cast<double*>(base + L.off_parts);
+  Sym& sy = e->sy;
   sy.cand = reinterpret_cast<uint32_t*>(base + L.off_cand);
   sy.cnt = reinterpret_cast<int*>(base + L.off_cnt);
   sy.out_row = reinterpret_cast<int*>(base + L.off_outrow);
@@ -981,41 +1145,109 @@ int run_bsr(tb_ctx* ctx, const double* H, const tb_bsr* Hb, int n, double nocc, 
   sy.scal = reinterpret_cast<int*>(base + L.off_scal);
   sy.order = reinterpret_cast<int*>(base + L.off_order);
   sy.flags = reinterpret_cast<uint16_t*>(base + L.off_flags);
-  Buf b[2];
-  for (int i = 0; i < 2; ++i) {
-    b[i].row_ptr = reinterpret_cast<int*>(base + L.off_rp[i]);
-    b[i].col = reinterpret_cast<int*>(base + L.off_col[i]);
-    b[i].nz = reinterpret_cast<int*>(base + L.off_nz[i]);
-    b[i].stored = reinterpret_cast<uint32_t*>(base + L.off_st[i]);
-    b[i].live = reinterpret_cast<uint32_t*>(base + L.off_lv[i]);
-    b[i].val = reinterpret_cast<float*>(base + L.off_val[i]);
-    b[i].hi = base + L.off_hi[i];
-    b[i].lo = L.off_lo[i] ? base + L.off_lo[i] : nullptr;
-  }
-  CUtensorMap mh[2], ml[2];
-  for (int i = 0; i < 2; ++i) {
-    int rc = make_block_map(ctx, o->precision, b[i].hi, L.cap * SB, &mh[i]);
+  for (int i = 0; i < L.nbuf; ++i) {
+    Buf& b = e->m[i].b;
+    b.row_ptr = reinterpret_cast<int*>(base + L.off_rp[i]);
+    b.col = reinterpret_cast<int*>(base + L.off_col[i]);
+    b.nz = reinterpret_cast<int*>(base + L.off_nz[i]);
+    b.stored = reinterpret_cast<uint32_t*>(base + L.off_st[i]);
+    b.live = reinterpret_cast<uint32_t*>(base + L.off_lv[i]);
+    b.val = reinterpret_cast<float*>(base + L.off_val[i]);
+    b.hi = base + L.off_hi[i];
+    b.lo = L.off_lo[i] ? base + L.off_lo[i] : nullptr;
+    int rc = make_block_map(ctx, prec, b.hi, L.cap * SB, &e->m[i].mh);
     if (rc) return rc;
-    if (b[i].lo) {
-      rc = make_block_map(ctx, o->precision, b[i].lo, L.cap * SB, &ml[i]);
-      if (rc) return rc;
+    if (b.lo) {
+      if ((rc = make_block_map(ctx, prec, b.lo, L.cap * SB, &e->m[i].ml))) return rc;
     } else {
-      ml[i] = mh[i];
+      e->m[i].ml = e->m[i].mh;
     }
   }
+  return TB_OK;
+}
+
+Args engine_args(const Engine& e, double tau) {
   Args a{};
-  a.n = n;
-  a.ld = L.ld;
-  a.nsb = L.nsb;
-  a.mw = (L.nsb + 31) / 32;
-  a.cap = L.cap;
-  a.pcap = L.pcap;
+  a.n = e.L.n;
+  a.ld = e.L.ld;
+  a.nsb = e.L.nsb;
+  a.mw = (e.L.nsb + 31) / 32;
+  a.cap = e.L.cap;
+  a.pcap = e.L.pcap;
+  a.tau2 = tau * tau;
+  a.st = e.st;
+  return a;
+}
+
+// X0 = s (e I - H) into out, with the drop, from a dense H (Hb null) or a BSR
+// H; trace partials per block row into a.parts_out.
+template <int P>
+int launch_start(tb_ctx* ctx, Engine& e, const Args& a, const double* H, const tb_bsr* Hb, Mat& out,
+                 cudaStream_t s) {
+  const int nsb = e.L.nsb;
+  if (Hb) k_bsr_init_flags_in<<<dim3(nsb, nsb), 256, 0, s>>>(*Hb, a, e.sy);
+  else k_bsr_init_flags<<<dim3(nsb, nsb), 256, 0, s>>>(H, a, e.sy);
+  TB_LAUNCH_CHECK(ctx);
+  k_bsr_init_rows<<<nsb, 256, 0, s>>>(a, e.sy, out.b);
+  TB_LAUNCH_CHECK(ctx);
+  k_bsr_scan_rows<<<1, 32, 0, s>>>(a, e.sy, out.b.row_ptr);
+  TB_LAUNCH_CHECK(ctx);
+  if (Hb) k_bsr_init_fill_in<P><<<nsb, 256, 0, s>>>(*Hb, a, e.sy, out.b);
+  else k_bsr_init_fill<P><<<nsb, 256, 0, s>>>(H, a, e.sy, out.b);
+  TB_LAUNCH_CHECK(ctx);
+  return TB_OK;
+}
+
+// out = alpha A B + gamma S + delta I (S may be null), thresholded: the
+// symbolic phase, then the persistent numeric kernel (trace partials per CTA
+// into a.parts_out).  A and B are symmetric and their bitmaps current; out
+// is none of A, B, S.  prof_k >= 0 marks the numeric launch for profiling.
+template <int P>
+int launch_product(tb_ctx* ctx, Engine& e, Args a, const Mat& A, const Mat& B, const Mat* S, Mat& out, Epi ep,
+                   int grid, cudaStream_t s, int prof_k = -1) {
+  a.same_ab = &A == &B;
+  const Buf none{};
+  const Buf& Sb = S ? S->b : none;
+  const int nsb = e.L.nsb;
+  k_bsr_cand<<<nsb, 256, 0, s>>>(a, A.b, B.b, Sb, e.sy);
+  k_bsr_scan_rows<<<1, 32, 0, s>>>(a, e.sy, out.b.row_ptr);
+  k_bsr_fill_out<<<nsb, 256, 0, s>>>(a, A.b, B.b, Sb, out.b, e.sy);
+  k_bsr_scan_pairs<<<1, 1024, 0, s>>>(a, e.sy);
+  k_bsr_pairs<<<std::max(1, std::min(e.L.cap, 4096) / 128 + 1), 128, 0, s>>>(a, A.b, B.b, out.b, e.sy);
+  k_bsr_order<<<1, 1024, 0, s>>>(a, out.b, e.sy);
+  TB_LAUNCH_CHECK(ctx);
+  if (prof_k >= 0) tb_prof_mark(ctx, 1, 2 * prof_k, s);
+  k_bsr_step_tc<P><<<grid, kThreads, Prec<P>::smem_bytes, s>>>(a, A.mh, A.ml, B.mh, B.ml, Sb, out.b, e.sy, ep);
+  TB_LAUNCH_CHECK(ctx);
+  if (prof_k >= 0) tb_prof_mark(ctx, 1, 2 * prof_k + 1, s);
+  return TB_OK;
+}
+
+template <int P>
+int prepare_numeric(tb_ctx* ctx, int* grid) {
+  static unsigned long long attr_done = 0;
+  if (int rc = tb_smem_attr(ctx, k_bsr_step_tc<P>, Prec<P>::smem_bytes, &attr_done)) return rc;
+  *grid = tb_persistent_grid(ctx, kMaxGrid);
+  return TB_OK;
+}
+
+// H dense (Hb null) or BSR (Hb); D dense or BSR (Db).
+template <int P>
+int run_bsr(tb_ctx* ctx, const double* H, const tb_bsr* Hb, int n, double nocc, const tb_sp2_opts* o, double* D,
+            tb_bsr* Db, void* ws, size_t ws_bytes, tb_sp2_report* rep, cudaStream_t s) {
+  const BsrLayout L = bsr_layout(n, o->precision, o->bsr_blocks_per_row, 2);
+  if (ws_bytes < L.total)
+    return tb_fail(ctx, TB_ERR_ARG, "workspace %zu bytes < required %zu (block-sparse)", ws_bytes, L.total);
+  Engine e;
+  int rc = bind_engine(ctx, o->precision, L, ws, &e);
+  if (rc) return rc;
+  SP2State* st = e.st;
+  double* slot[2] = {e.parts, e.parts + 3 * (size_t)L.nparts};
+  Args a = engine_args(e, o->tau);
   a.nocc = nocc;
-  a.tau2 = o->tau * o->tau;
   a.tol = o->tol;
   a.rule = o->rule;
   a.max_iter = o->max_iter;
-  a.st = st;
   {
     const double u = (o->precision == TB_PREC_TF32X3 || o->precision == TB_PREC_BF16X3) ? 0x1p-24
                      : o->precision == TB_PREC_TF32 ? 0x1p-11 : 0x1p-8;
@@ -1023,66 +1255,195 @@ int run_bsr(tb_ctx* ctx, const double* H, const tb_bsr* Hb, int n, double nocc, 
   }
   ctx->prof_n[0] = ctx->prof_n[1] = 0;
   TB_CUDA_TRY(ctx, cudaMemsetAsync(st, 0, sizeof(SP2State), s));
-  int rc = TB_OK;
   if (Hb) {
     k_bsr_status_in<<<1, 1, 0, s>>>(Hb->status, st);
     TB_LAUNCH_CHECK(ctx);
-    k_bsr_bounds_in<<<L.nsb, 128, 0, s>>>(*Hb, bparts);
+    k_bsr_bounds_in<<<L.nsb, 128, 0, s>>>(*Hb, e.bparts);
     TB_LAUNCH_CHECK(ctx);
-    k_bsr_bounds<<<1, 32, 0, s>>>(bparts, L.nsb, st);
-    TB_LAUNCH_CHECK(ctx);
-    k_bsr_init_flags_in<<<dim3(L.nsb, L.nsb), 256, 0, s>>>(*Hb, a, sy);
+    k_bsr_bounds<<<1, 32, 0, s>>>(e.bparts, L.nsb, st);
   } else {
     const int nb = (n + 7) / 8;
-    rc = sp2_launch_bounds(ctx, H, n, bparts, s);
-    if (rc) return rc;
-    k_bsr_bounds<<<1, 32, 0, s>>>(bparts, nb, st);
-    TB_LAUNCH_CHECK(ctx);
-    k_bsr_init_flags<<<dim3(L.nsb, L.nsb), 256, 0, s>>>(H, a, sy);
+    if ((rc = sp2_launch_bounds(ctx, H, n, e.bparts, s))) return rc;
+    k_bsr_bounds<<<1, 32, 0, s>>>(e.bparts, nb, st);
   }
   TB_LAUNCH_CHECK(ctx);
-  k_bsr_init_rows<<<L.nsb, 256, 0, s>>>(a, sy, b[0]);
-  TB_LAUNCH_CHECK(ctx);
-  k_bsr_scan_rows<<<1, 32, 0, s>>>(a, sy, b[0].row_ptr);
-  TB_LAUNCH_CHECK(ctx);
   a.parts_out = slot[0];
-  if (Hb) k_bsr_init_fill_in<P><<<L.nsb, 256, 0, s>>>(*Hb, a, sy, b[0]);
-  else k_bsr_init_fill<P><<<L.nsb, 256, 0, s>>>(H, a, sy, b[0]);
-  TB_LAUNCH_CHECK(ctx);
+  if ((rc = launch_start<P>(ctx, e, a, H, Hb, e.m[0], s))) return rc;
 
-  using Cf = Prec<P>;
-  static unsigned long long attr_done = 0;
-  if (int rc_attr = tb_smem_attr(ctx, k_bsr_step_tc<P>, Cf::smem_bytes, &attr_done)) return rc_attr;
-  const int grid = tb_persistent_grid(ctx, kMaxGrid);
+  int grid = 0;
+  if ((rc = prepare_numeric<P>(ctx, &grid))) return rc;
+  // X^2 (branch 0) or 2X - X^2 (branch 1), the lo x lo product of a square
+  const Epi sp2_epi{1.0f, 0.0f, -1.0f, 2.0f, 0.0f, 1, 1};
   tb_prof_mark(ctx, 0, 0, s);
   for (int k = 0; k <= o->max_iter; ++k) {
     a.k = k;
     a.parts_in = slot[k & 1];
     a.nparts_in = k == 0 ? L.nsb : grid;
     a.parts_out = slot[(k + 1) & 1];
-    Buf& bo = b[k & 1];
-    Buf& bn = b[(k + 1) & 1];
-    k_bsr_decide<<<L.nsb, 128, 0, s>>>(a, bo);
-    k_bsr_cand<<<L.nsb, 256, 0, s>>>(a, bo, sy);
-    k_bsr_scan_rows<<<1, 32, 0, s>>>(a, sy, bn.row_ptr);
-    k_bsr_fill_out<<<L.nsb, 256, 0, s>>>(a, bo, bn, sy);
-    k_bsr_scan_pairs<<<1, 1024, 0, s>>>(a, sy);
-    k_bsr_pairs<<<std::max(1, std::min(L.cap, 4096) / 128 + 1), 128, 0, s>>>(a, bo, bn, sy);
-    k_bsr_order<<<1, 1024, 0, s>>>(a, bn, sy);
-    tb_prof_mark(ctx, 1, 2 * k, s);
-    k_bsr_step_tc<P><<<grid, kThreads, Cf::smem_bytes, s>>>(a, mh[k & 1], ml[k & 1], bo, bn, sy);
-    TB_LAUNCH_CHECK(ctx);
-    tb_prof_mark(ctx, 1, 2 * k + 1, s);
+    Mat& bo = e.m[k & 1];
+    Mat& bn = e.m[(k + 1) & 1];
+    k_bsr_decide<<<L.nsb, 128, 0, s>>>(a, bo.b);
+    if ((rc = launch_product<P>(ctx, e, a, bo, bo, &bo, bn, sp2_epi, grid, s, k))) return rc;
     tb_prof_mark(ctx, 0, k + 1, s);
   }
   if (Db) {
-    k_bsr_to_bsr<<<std::min(4096, std::max(1, L.cap)), 256, 0, s>>>(st, a, b[0], b[1], *Db);
+    k_bsr_to_bsr<<<std::min(4096, std::max(1, L.cap)), 256, 0, s>>>(st, a, e.m[0].b, e.m[1].b, -1, 0.0, *Db);
   } else {
     TB_CUDA_TRY(ctx, cudaMemsetAsync(D, 0, sizeof(double) * (size_t)n * n, s));
-    k_bsr_to_dense<<<std::min(4096, std::max(1, L.cap)), 256, 0, s>>>(st, a, b[0], b[1], sy, sy, D);
+    k_bsr_to_dense<<<std::min(4096, std::max(1, L.cap)), 256, 0, s>>>(st, a, e.m[0].b, e.m[1].b, e.sy, e.sy, D);
   }
   TB_LAUNCH_CHECK(ctx);
-  k_bsr_report<<<1, 1, 0, s>>>(st, a, b[0], b[1], rep, nullptr);
+  k_bsr_report<<<1, 1, 0, s>>>(st, a, e.m[0].b, e.m[1].b, rep, nullptr);
+  TB_LAUNCH_CHECK(ctx);
+  return TB_OK;
+}
+
+// ------------------------------------------------ block-sparse Fermi expansion
+
+constexpr int kFoeBufs = 7;  // E (two, alternating), Y, A, Z, T, W
+constexpr int kFoeMinM = 8;
+
+__global__ void k_bsr_fail(SP2State* st, int code) { st->err = code; }
+
+__global__ void k_bsr_fermi_report(tb_fermi_report* rep, double* mu_out, int status, int iters, int m, int n,
+                                   double mu, double trace, double trace_dd, double emin, double emax) {
+  if (mu_out && status == TB_OK) *mu_out = mu;
+  if (!rep) return;
+  rep->status = status;
+  rep->mu_iters = iters;
+  rep->m = m;
+  rep->n = n;
+  rep->mu = mu;
+  rep->trace = trace;
+  rep->trace_dd = trace_dd;
+  rep->eps_min = emin;
+  rep->eps_max = emax;
+}
+
+// The recursive Fermi-operator expansion of dm_fermi on thresholded
+// block-sparse products (every product and the start drop 32 x 32 blocks
+// with Frobenius norm < tau; the affine steps are exact), the chemical
+// potential by the host: one expansion per step, two traces read back.
+template <int P>
+int run_bsr_fermi(tb_ctx* ctx, const tb_bsr* Hb, int n, double nocc, double kT, const tb_fermi_opts* o,
+                  double tau, int bpr, tb_bsr* Db, double* mu_dev, void* ws, size_t ws_bytes,
+                  tb_fermi_report* rep, cudaStream_t s) {
+  const BsrLayout L = bsr_layout(n, o->precision, bpr, kFoeBufs);
+  if (ws_bytes < L.total)
+    return tb_fail(ctx, TB_ERR_ARG, "workspace %zu bytes < required %zu (block-sparse)", ws_bytes, L.total);
+  Engine e;
+  int rc = bind_engine(ctx, o->precision, L, ws, &e);
+  if (rc) return rc;
+  SP2State* st = e.st;
+  Args a = engine_args(e, tau);
+  a.keep_diag = 1;
+  a.parts_out = e.parts;
+  const int m_max = o->m > 0 ? o->m : 14;
+  const int ns = o->ns_iters > 0 ? o->ns_iters : 3;
+  const double tol = o->trace_tol > 0.0 ? o->trace_tol : 1e-6 + 1e-9 * nocc;
+  const double beta = 1.0 / kT;
+  TB_CUDA_TRY(ctx, cudaMemsetAsync(st, 0, sizeof(SP2State), s));
+  k_bsr_status_in<<<1, 1, 0, s>>>(Hb->status, st);
+  k_bsr_bounds_in<<<L.nsb, 128, 0, s>>>(*Hb, e.bparts);
+  k_bsr_bounds<<<1, 32, 0, s>>>(e.bparts, L.nsb, st);
+  TB_LAUNCH_CHECK(ctx);
+  SP2State hs;
+  double mu0 = NAN;
+  TB_CUDA_TRY(ctx, cudaMemcpyAsync(&hs, st, sizeof(SP2State), cudaMemcpyDeviceToHost, s));
+  if (mu_dev) TB_CUDA_TRY(ctx, cudaMemcpyAsync(&mu0, mu_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  const double emin = hs.emin, emax = hs.emax;
+  double lo = emin - 40.0 * kT - 1.0, hi = emax + 40.0 * kT + 1.0;
+  int m = std::min(kFoeMinM, m_max);
+  while (m < m_max && !(beta * (hi - lo) <= std::ldexp(1.0, m + 1))) ++m;
+  double mu = (std::isfinite(mu0) && mu0 > lo && mu0 < hi) ? mu0 : 0.5 * (emin + emax);
+  int status = hs.err ? hs.err : TB_ERR_NOT_CONVERGED;
+  if (!hs.err && !(beta * (hi - lo) <= std::ldexp(1.0, m + 1))) status = TB_ERR_ARG;  // start undefined
+  int grid = 0;
+  if ((rc = prepare_numeric<P>(ctx, &grid))) return rc;
+  std::vector<double> hp(3 * (size_t)grid);
+  Mat* E[2] = {&e.m[0], &e.m[1]};
+  Mat* Y = &e.m[2];
+  Mat* A = &e.m[3];
+  Mat* Z = &e.m[4];
+  Mat* T = &e.m[5];
+  Mat* W = &e.m[6];
+  auto affine = [&](const Mat& X, Mat& out, float alpha, float delta) -> int {
+    k_bsr_affine<P><<<std::min(4096, std::max(1, L.cap)), 256, 0, s>>>(a, X.b, out.b, alpha, delta);
+    TB_LAUNCH_CHECK(ctx);
+    return TB_OK;
+  };
+  auto product = [&](const Mat& X1, const Mat& X2, const Mat* S, Mat& out, Epi ep) -> int {
+    int r = launch_product<P>(ctx, e, a, X1, X2, S, out, ep, grid, s);
+    if (r) return r;
+    k_bsr_bitmaps<<<L.nsb, 128, 0, s>>>(a, out.b);
+    TB_LAUNCH_CHECK(ctx);
+    return TB_OK;
+  };
+  const Epi plain{1.0f, 0.0f, 1.0f, 0.0f, 0.0f, 0, 0};
+  auto with = [](float alpha, float gamma, float delta, int lolo) { return Epi{alpha, gamma, alpha, gamma, delta, 0, lolo}; };
+  int it = 0, fin = 0;
+  double trd = NAN, t1 = NAN;
+  for (it = 1; status == TB_ERR_NOT_CONVERGED && it <= o->mu_iters; ++it) {
+    // L = beta/2^(m+2) (mu I - H), then E0 = L - 4/3 L L^2
+    a.x0_e = mu;
+    a.x0_s = beta / std::ldexp(1.0, m + 2);
+    if ((rc = launch_start<P>(ctx, e, a, nullptr, Hb, *Y, s))) return rc;
+    a.x0_s = 0.0;
+    if ((rc = product(*Y, *Y, nullptr, *A, with(1.0f, 0.0f, 0.0f, 1)))) return rc;
+    if ((rc = product(*Y, *A, Y, *E[0], with(-4.0f / 3.0f, 1.0f, 0.0f, 0)))) return rc;
+    int cur = 0;
+    for (int step = 0; step < m; ++step) {
+      Mat* Zc = Z;
+      Mat* Yc = Y;
+      // W = (I - 2E)(I + 2E), A = 2I - W
+      if ((rc = affine(*E[cur], *T, -2.0f, 1.0f)) || (rc = affine(*E[cur], *Y, 2.0f, 1.0f))) return rc;
+      if ((rc = product(*T, *Y, nullptr, *W, plain))) return rc;
+      if ((rc = affine(*W, *A, -1.0f, 2.0f))) return rc;
+      // Z1 = (32 A A - 144 A + 210 I) / 99, then Newton-Schulz Z <- Z (2I - A Z)
+      if ((rc = product(*A, *A, A, *Zc, with(32.0f / 99.0f, -144.0f / 99.0f, 210.0f / 99.0f, 1)))) return rc;
+      for (int k = 1; k < ns; ++k) {
+        if ((rc = product(*A, *Zc, nullptr, *T, with(-1.0f, 0.0f, 2.0f, 0)))) return rc;
+        if ((rc = product(*Zc, *T, nullptr, *Yc, plain))) return rc;
+        std::swap(Zc, Yc);
+      }
+      // E <- E + E (Z W): the last product's partials are Tr E and ||E||_F^2
+      if ((rc = product(*Zc, *W, nullptr, *T, plain))) return rc;
+      if ((rc = product(*E[cur], *T, E[cur], *E[1 - cur], with(1.0f, 1.0f, 0.0f, 0)))) return rc;
+      cur = 1 - cur;
+    }
+    TB_CUDA_TRY(ctx, cudaMemcpyAsync(hp.data(), e.parts, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, s));
+    TB_CUDA_TRY(ctx, cudaMemcpyAsync(&hs, st, sizeof(SP2State), cudaMemcpyDeviceToHost, s));
+    TB_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (hs.err) {
+      status = hs.err;
+      break;
+    }
+    double tr = 0.0, fro = 0.0;
+    for (int i = 0; i < grid; ++i) {
+      tr += hp[3 * i];
+      fro += hp[3 * i + 1];
+    }
+    fin = cur;
+    trd = 0.5 * n + tr;
+    t1 = 0.25 * n - fro;  // Tr D(I - D) = n/4 - ||E||_F^2
+    const double dev = trd - nocc;
+    if (fabs(dev) <= tol) {
+      status = TB_OK;
+      break;
+    }
+    if (it == o->mu_iters) break;
+    if (dev < 0.0) lo = mu;
+    else hi = mu;
+    mu = foe_next_mu(mu, dev, t1, beta, tol, lo, hi);
+  }
+  it = std::min(it, o->mu_iters);
+  // D = I/2 + E; after an error (the state's flag, raised here for one the
+  // host found) an empty matrix
+  if (status != TB_OK && status != TB_ERR_NOT_CONVERGED) k_bsr_fail<<<1, 1, 0, s>>>(st, status);
+  k_bsr_to_bsr<<<std::min(4096, std::max(1, L.cap)), 256, 0, s>>>(st, a, E[0]->b, E[1]->b, fin, 0.5, *Db);
+  TB_LAUNCH_CHECK(ctx);
+  k_bsr_fermi_report<<<1, 1, 0, s>>>(rep, mu_dev, status, it, m, n, mu, trd, t1, emin, emax);
   TB_LAUNCH_CHECK(ctx);
   return TB_OK;
 }
@@ -1091,7 +1452,8 @@ int run_bsr(tb_ctx* ctx, const double* H, const tb_bsr* Hb, int n, double nocc, 
 
 int dm_sp2_bsr_workspace(int n, const tb_sp2_opts* o, int nsm, size_t* bytes) {
   if (n > kMaxNsb * SB) return TB_ERR_UNSUPPORTED;
-  *bytes = bsr_layout(n, o->precision, o->bsr_blocks_per_row, nsm).total;
+  (void)nsm;
+  *bytes = bsr_layout(n, o->precision, o->bsr_blocks_per_row, 2).total;
   return TB_OK;
 }
 
@@ -1129,5 +1491,48 @@ extern "C" int dm_sp2_sparse(tb_ctx* ctx, const tb_bsr* H, double nocc, const tb
     case TB_PREC_BF16: return run_bsr<TB_PREC_BF16>(ctx, nullptr, H, n, nocc, o, nullptr, D, ws, ws_bytes, rep, s);
     case TB_PREC_BF16X3: return run_bsr<TB_PREC_BF16X3>(ctx, nullptr, H, n, nocc, o, nullptr, D, ws, ws_bytes, rep, s);
     default: return tb_fail(ctx, TB_ERR_UNSUPPORTED, "block-sparse SP2 needs a tensor-core precision");
+  }
+}
+
+extern "C" int dm_fermi_sparse_workspace_size(int n, const tb_fermi_opts* o, int blocks_per_row, size_t* bytes) {
+  if (n < 1 || !o || !bytes) return TB_ERR_ARG;
+  if (n > kMaxNsb * SB) return TB_ERR_UNSUPPORTED;
+  *bytes = bsr_layout(n, o->precision, blocks_per_row, kFoeBufs).total;
+  return TB_OK;
+}
+
+extern "C" int dm_fermi_sparse(tb_ctx* ctx, const tb_bsr* H, double nocc, double kT, const tb_fermi_opts* o,
+                               double tau, int blocks_per_row, tb_bsr* D, double* mu, void* ws, size_t ws_bytes,
+                               tb_fermi_report* rep, void* stream) {
+  if (!ctx) return TB_ERR_ARG;
+  if (!H || !D || !o || !ws) return tb_fail(ctx, TB_ERR_ARG, "null argument to dm_fermi_sparse");
+  const int n = H->n;
+  if (n < 1 || D->n != n || H->nsb != (n + SB - 1) / SB || D->nsb != H->nsb)
+    return tb_fail(ctx, TB_ERR_ARG, "dm_fermi_sparse: inconsistent BSR sizes");
+  if (!H->row_ptr || !H->col || !H->val || !H->status || !D->row_ptr || !D->col || !D->val || !D->status)
+    return tb_fail(ctx, TB_ERR_ARG, "dm_fermi_sparse: null BSR array");
+  if (!(tau > 0.0)) return tb_fail(ctx, TB_ERR_ARG, "dm_fermi_sparse needs tau > 0");
+  if (!(kT > 0.0)) return tb_fail(ctx, TB_ERR_ARG, "dm_fermi_sparse needs kT > 0");
+  if (n > kMaxNsb * SB) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "block-sparse expansion supports n <= %d", kMaxNsb * SB);
+  if (!(nocc >= 0.0) || nocc > n) return tb_fail(ctx, TB_ERR_ARG, "n_occ %g outside [0, n]", nocc);
+  if (o->mu_iters < 1 || o->mu_iters > 100) return tb_fail(ctx, TB_ERR_ARG, "mu_iters %d outside 1..100", o->mu_iters);
+  if (o->m < 0 || o->m > 30 || o->ns_iters < 0 || o->ns_iters > 8)
+    return tb_fail(ctx, TB_ERR_ARG, "dm_fermi_sparse: m or ns_iters out of range");
+  if ((reinterpret_cast<uintptr_t>(ws) & 1023) != 0) return tb_fail(ctx, TB_ERR_ARG, "workspace must be 1024-byte aligned");
+  cudaStream_t s = as_stream(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  TB_CUDA_TRY(ctx, cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return tb_fail(ctx, TB_ERR_UNSUPPORTED, "dm_fermi_sparse reads traces on the host: not capturable");
+  switch (o->precision) {
+    case TB_PREC_TF32:
+      return run_bsr_fermi<TB_PREC_TF32>(ctx, H, n, nocc, kT, o, tau, blocks_per_row, D, mu, ws, ws_bytes, rep, s);
+    case TB_PREC_TF32X3:
+      return run_bsr_fermi<TB_PREC_TF32X3>(ctx, H, n, nocc, kT, o, tau, blocks_per_row, D, mu, ws, ws_bytes, rep, s);
+    case TB_PREC_BF16:
+      return run_bsr_fermi<TB_PREC_BF16>(ctx, H, n, nocc, kT, o, tau, blocks_per_row, D, mu, ws, ws_bytes, rep, s);
+    case TB_PREC_BF16X3:
+      return run_bsr_fermi<TB_PREC_BF16X3>(ctx, H, n, nocc, kT, o, tau, blocks_per_row, D, mu, ws, ws_bytes, rep, s);
+    default: return tb_fail(ctx, TB_ERR_UNSUPPORTED, "block-sparse expansion needs a tensor-core precision");
   }
 }

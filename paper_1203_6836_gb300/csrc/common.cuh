@@ -333,3 +333,28 @@ __device__ __forceinline__ int sp2_decide(const SP2StepArgs& a, double t1, doubl
     *branch = (t1 > a.nocc) ? 0 : 1;
   return 0;
 }
+
+// Next chemical potential of the Fermi expansion after an expansion at mu
+// (dev = Tr D - N_occ, t1 = Tr D(I - D), beta = 1/kT), inside the bisection
+// bracket (lo, hi) already narrowed by this expansion's sign.  Newton's step
+// -dev/(beta t1), except where |dev| ~ t1: then the partly occupied states
+// sit in the tails of a gap (f(1-f) ~ f or 1-f), Newton moves mu by only ~kT
+// per expansion, and the electrons above mu, a = (t1 + dev)/2, and the holes
+// below it, b = (t1 - dev)/2, which move as a e^{beta dmu} and b e^{-beta dmu},
+// balance at dmu = ln(b/a)/(2 beta).  With one tail below resolution the step
+// shrinks the other towards the tolerance, by at most 8 kT.  A step that
+// leaves the bracket bisects it.
+__host__ __device__ inline double foe_next_mu(double mu, double dev, double t1, double beta, double tol, double lo,
+                                              double hi) {
+  double next = t1 > 1e-12 ? mu - dev / (beta * t1) : NAN;
+  const double r = t1 > 0.0 ? fabs(dev) / t1 : INFINITY;
+  if (r >= 0.5 && r <= 1.5) {
+    const double a = 0.5 * (t1 + dev), b = 0.5 * (t1 - dev);
+    if (a > 0.0 && b > 0.0 && fmin(a, b) > 1e-3 * fmax(a, b))
+      next = mu + 0.5 * log(b / a) / beta;
+    else
+      next = mu - copysign(fmin(log(fabs(dev) / tol), 8.0), dev) / beta;
+  }
+  if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
+  return next;
+}

@@ -213,24 +213,7 @@ __global__ void k_foe_mu(FoeState* st, const double* parts, const double* partsw
   } else {
     if (dev < 0.0) st->lo = mu;
     else st->hi = mu;
-    // Newton's step -dev/(beta t1), except where |dev| ~ t1: then the partly
-    // occupied states sit in the tails of a gap (f(1-f) ~ f or 1-f), Newton
-    // moves mu by only ~kT per expansion, and the electrons above mu,
-    // a = (t1 + dev)/2, and the holes below it, b = (t1 - dev)/2, which move
-    // as a e^{beta dmu} and b e^{-beta dmu}, balance at dmu = ln(b/a)/(2 beta).
-    // With one tail below resolution the step shrinks the other towards the
-    // tolerance, by at most 8 kT.
-    double next = mu + step;
-    const double r = t1 > 0.0 ? fabs(dev) / t1 : INFINITY;
-    if (r >= 0.5 && r <= 1.5) {
-      const double a = 0.5 * (t1 + dev), b = 0.5 * (t1 - dev);
-      if (a > 0.0 && b > 0.0 && fmin(a, b) > 1e-3 * fmax(a, b))
-        next = mu + 0.5 * log(b / a) / beta;
-      else
-        next = mu - copysign(fmin(log(fabs(dev) / tol), 8.0), dev) / beta;
-    }
-    if (!(next > st->lo && next < st->hi)) next = 0.5 * (st->lo + st->hi);
-    st->mu = next;
+    st->mu = foe_next_mu(mu, dev, t1, beta, tol, st->lo, st->hi);
   }
   if (st->done)
     for (int k = 0; k < kMaxM; ++k) st->skipd[k] = 1;

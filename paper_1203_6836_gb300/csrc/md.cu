@@ -127,9 +127,10 @@ int check_state(tb_ctx* ctx, const tb_md_state* st, const tb_xl_params* xp, cons
   if (!st->R || !st->v || !st->F || !st->mass || !st->n_hist || !st->q || !st->energies || !st->workspace ||
       (!bsr && (!st->H || !st->D || !st->gamma)))
     return tb_fail(ctx, TB_ERR_ARG, "null array in tb_md_state");
-  if (bsr && (!st->D_bsr || !st->vscc || !st->bsr_workspace || st->kT > 0.0 || !(so->tau > 0.0)))
-    return tb_fail(ctx, TB_ERR_ARG,
-                   "the block-sparse state needs D_bsr, vscc, bsr_workspace, kT = 0 and sp2 opts with tau > 0");
+  if (bsr && (!st->D_bsr || !st->vscc || !st->bsr_workspace || !(so->tau > 0.0)))
+    return tb_fail(ctx, TB_ERR_ARG, "the block-sparse state needs D_bsr, vscc, bsr_workspace and sp2 opts with tau > 0");
+  if (bsr && st->kT > 0.0 && st->entropy_workspace)
+    return tb_fail(ctx, TB_ERR_UNSUPPORTED, "the entropy term is not available with the block-sparse state");
   if (!(xp->dt > 0)) return tb_fail(ctx, TB_ERR_ARG, "dt must be > 0");
   if (st->kT > 0.0 && !st->mu) return tb_fail(ctx, TB_ERR_ARG, "kT > 0 needs the device mu");
   return TB_OK;
@@ -164,9 +165,12 @@ int charges_any(tb_ctx* ctx, const tb_params* p, tb_md_state* st, cudaStream_t s
 
 bool entropy_on(const tb_md_state* st) { return st->kT > 0.0 && st->entropy_workspace && st->entropy; }
 
-// D from H: Fermi operator (dm_fermi, mu carried in st->mu) when kT > 0, else
-// the T_e = 0 projector by SP2.
+// D from H: Fermi operator (dm_fermi, or dm_fermi_sparse with the block-sparse
+// state; mu carried in st->mu) when kT > 0, else the T_e = 0 projector by SP2.
 int density(tb_ctx* ctx, const tb_params* p, tb_md_state* st, const tb_sp2_opts* so, cudaStream_t s) {
+  if (st->H_bsr && st->kT > 0.0)
+    return dm_fermi_sparse(ctx, st->H_bsr, st->n_occ, st->kT, &st->fermi, so->tau, so->bsr_blocks_per_row,
+                           st->D_bsr, st->mu, st->workspace, st->workspace_bytes, st->fermi_report, s);
   if (st->H_bsr)
     return dm_sp2_sparse(ctx, st->H_bsr, st->n_occ, so, st->D_bsr, st->workspace, st->workspace_bytes,
                          st->sp2_report, s);

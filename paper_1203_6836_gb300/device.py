@@ -182,7 +182,11 @@ class MDState:
         self.mu = torch.full((4,), float("nan"), dtype=torch.float64, device=dev)
         if kT > 0.0:
             fermi = fermi or fermi_opts()
-            self.ws = Workspace(tbmd.dm_fermi_workspace_size(n, fermi), dev)
+            if self.bsr:
+                ws = tbmd.dm_fermi_sparse_workspace_size(n, fermi, opts.bsr_blocks_per_row)
+            else:
+                ws = tbmd.dm_fermi_workspace_size(n, fermi)
+            self.ws = Workspace(ws, dev)
         else:
             fermi = tbmd.tb_fermi_opts()
             self.ws = Workspace(tbmd.dm_sp2_workspace_size(n, opts), dev)

@@ -154,6 +154,11 @@ _SIGS = {
                                       ctypes.POINTER(tb_bsr), _P, _P, ctypes.c_size_t, _P]),
     "dm_sp2_sparse": (ctypes.c_int, [_P, ctypes.POINTER(tb_bsr), ctypes.c_double, ctypes.POINTER(tb_sp2_opts),
                                      ctypes.POINTER(tb_bsr), _P, ctypes.c_size_t, _P, _P]),
+    "dm_fermi_sparse_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(tb_fermi_opts), ctypes.c_int,
+                                                      ctypes.POINTER(ctypes.c_size_t)]),
+    "dm_fermi_sparse": (ctypes.c_int, [_P, ctypes.POINTER(tb_bsr), ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(tb_fermi_opts), ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(tb_bsr), _P, _P, ctypes.c_size_t, _P, _P]),
     "mulliken_bsr": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), ctypes.POINTER(tb_bsr),
                                     _P, _P]),
     "tb_forces_bsr": (ctypes.c_int, [_P, ctypes.POINTER(tb_params), ctypes.POINTER(tb_system), _P,
@@ -338,6 +343,23 @@ def dm_sp2_sparse(ctx: Context, H: tb_bsr, n_occ: float, opts: tb_sp2_opts, D: t
     return ctx.check(lib().dm_sp2_sparse(ctx.handle, ctypes.byref(H), float(n_occ), ctypes.byref(opts),
                                          ctypes.byref(D), _ptr(workspace), int(workspace_bytes), _ptr(report),
                                          _stream(stream)), "dm_sp2_sparse")
+
+
+def dm_fermi_sparse_workspace_size(n: int, opts: "tb_fermi_opts", blocks_per_row: int) -> int:
+    b = ctypes.c_size_t()
+    rc = lib().dm_fermi_sparse_workspace_size(int(n), ctypes.byref(opts), int(blocks_per_row), ctypes.byref(b))
+    if rc != TB_OK:
+        raise TBError(rc, "dm_fermi_sparse_workspace_size")
+    return int(b.value)
+
+
+def dm_fermi_sparse(ctx: Context, H: tb_bsr, n_occ: float, kT: float, opts: "tb_fermi_opts", tau: float,
+                    blocks_per_row: int, D: tb_bsr, mu, workspace, workspace_bytes: int, report=None,
+                    stream=None) -> int:
+    return ctx.check(lib().dm_fermi_sparse(ctx.handle, ctypes.byref(H), float(n_occ), float(kT), ctypes.byref(opts),
+                                           float(tau), int(blocks_per_row), ctypes.byref(D), _ptr(mu),
+                                           _ptr(workspace), int(workspace_bytes), _ptr(report), _stream(stream)),
+                     "dm_fermi_sparse")
 
 
 def mulliken_bsr(ctx: Context, p: tb_params, sys: tb_system, D: tb_bsr, q, stream=None) -> int:
