@@ -275,9 +275,13 @@ int dm_sp2_grouped_workspace_size(int count, const int* n, const tb_sp2_opts* op
  * Copies the per-system descriptors into the workspace.  autotune selects the
  * launch form: 0 = one CTA per system, 128-wide tiles, one CTA per SM;
  * 4 or 8 = thread-block clusters of that many CTAs per system (the CTAs split
- * each projection's tiles; as many clusters as fit at once); 1 = time every
- * form (tile width 64 or 128 with all or half the SMs, clusters of 4 or 8) on
- * the batch itself and keep the fastest (the batch is solved several times).
+ * each projection's tiles; as many clusters as fit at once); 3 = the FP32-staged
+ * form (tf32x3 only, else TB_ERR_UNSUPPORTED): one CTA per system that loads only
+ * the FP32 X and splits it into the hi/lo operands in shared memory, bitwise the
+ * result of form 0; 1 = time every form (tile width 64 or 128 with all or half
+ * the SMs, clusters of 4 or 8, the FP32-staged form) on the batch itself and
+ * keep the fastest (the batch is solved several times).  config_out of the run
+ * call reports the FP32-staged form as tile width 0.
  * Synchronises `stream`.  One plan per context at a time: a new plan replaces
  * the previous one. */
 int dm_sp2_grouped_plan(tb_ctx* ctx, int count, const int* n, const double* n_occ, const double* const* H,

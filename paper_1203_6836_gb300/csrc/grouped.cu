@@ -33,6 +33,7 @@ using namespace tcx;
 
 constexpr int BM = 128;
 constexpr int kThreads = 192;
+constexpr int kThreadsFs = 320;  // FP32-staged form: four converter warps more
 constexpr int kMaxLd = 512;
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -81,8 +82,14 @@ __device__ __forceinline__ void tri_tile(int t, int nt, int* I, int* J) {
   *J = i + t;
 }
 
-template <int P, int BN>
-__global__ void __launch_bounds__(kThreads, 1)
+// FS (tf32x3, BN = 128): the FP32-staged form.  TMA loads the FP32 masters
+// of X_k only; four converter warps split each stage into hi and lo in shared
+// memory, in place (the split is elementwise, so the 128B swizzle is kept),
+// and the epilogue writes only the FP32 master of X_{k+1}.  The operands are
+// bitwise those of the stored-split form, at half the operand bytes and a
+// third of the epilogue's stores.
+template <int P, int BN, bool FS>
+__global__ void __launch_bounds__(FS ? kThreadsFs : kThreads, 1)
     k_sp2_grouped(GArgs ga, const __grid_constant__ CUtensorMap ah0, const __grid_constant__ CUtensorMap al0,
                   const __grid_constant__ CUtensorMap bh0, const __grid_constant__ CUtensorMap bl0,
                   const __grid_constant__ CUtensorMap ah1, const __grid_constant__ CUtensorMap al1,
@@ -91,11 +98,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   using G = GCfg<P, BN>;
   constexpr bool kSym = BN == BM;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[G::stages], empty[G::stages], tfull[2], tempty[2];
+  __shared__ __align__(8) uint64_t full[G::stages], empty[G::stages], tfull[2], tempty[2], conv[G::stages];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_abort;
   __shared__ int s_sys, s_stop, s_br;
-  __shared__ double s_red[8][3];
+  __shared__ double s_red[kThreadsFs / 32][3];
   __shared__ double s_t1, s_t2, s_lo, s_hi;
   __shared__ double s_hist[2][SP2_MAX_ITER + 2];
   __shared__ unsigned long long s_branch[2];
@@ -106,6 +113,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int s = 0; s < G::stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      mbar_init(&conv[s], 4);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -120,7 +128,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_base;
   // pipeline counters persist across tiles, projections and systems
-  int g_prod = 0, g_mma = 0, t_mma = 0, t_epi = 0;
+  int g_prod = 0, g_mma = 0, t_mma = 0, t_epi = 0, g_conv = 0;
+  constexpr int kWarps = (FS ? kThreadsFs : kThreads) / 32;
 
   while (true) {
     if (threadIdx.x == 0) s_sys = atomicAdd(ga.queue, 1);
@@ -137,7 +146,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     // ---- Gershgorin bounds (warp per row)
     double lo = INFINITY, hi = -INFINITY;
-    for (int r = warp; r < n; r += kThreads / 32) {
+    for (int r = warp; r < n; r += kWarps) {
       double sabs = 0.0;
       for (int c = lane; c < n; c += 32) sabs += (c == r) ? 0.0 : fabs(d.H[(size_t)r * n + c]);
       sabs = warp_sum(sabs);
@@ -152,7 +161,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     if (threadIdx.x == 0) {
       double a = s_red[0][0], b = s_red[0][1];
-      for (int w = 1; w < kThreads / 32; ++w) {
+      for (int w = 1; w < kWarps; ++w) {
         a = fmin(a, s_red[w][0]);
         b = fmax(b, s_red[w][1]);
       }
@@ -169,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const double inv = 1.0 / w;
       const float invf = (float)inv, emaxf = (float)emax;
       double t1 = 0.0, t2 = 0.0;
-      for (int seg = threadIdx.x; seg < ld * (ld / 32); seg += kThreads) {
+      for (int seg = threadIdx.x; seg < ld * (ld / 32); seg += kWarps * 32) {
         const int r = seg / (ld / 32), c0 = 32 * (seg % (ld / 32));
         float y[32];
         float s2 = 0.0f;
@@ -189,9 +198,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         float4* dst = reinterpret_cast<float4*>(ga.M[0] + e0);
 #pragma unroll
         for (int j = 0; j < 8; ++j) dst[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
-        char* h = static_cast<char*>(ga.Hi[0]) + e0 * C::eb;
-        char* l = ga.Lo[0] ? static_cast<char*>(ga.Lo[0]) + e0 * C::eb : h;
-        store_operands<P>(y, h, l);
+        if constexpr (!FS) {
+          char* h = static_cast<char*>(ga.Hi[0]) + e0 * C::eb;
+          char* l = ga.Lo[0] ? static_cast<char*>(ga.Lo[0]) + e0 * C::eb : h;
+          store_operands<P>(y, h, l);
+        }
       }
       t1 = warp_sum(t1);
       t2 = warp_sum(t2);
@@ -208,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ---- decision for projection k (every thread the same)
       if (threadIdx.x == 0) {
         double t1 = 0.0, t2 = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) {
+        for (int w = 0; w < kWarps; ++w) {
           t1 += s_red[w][0];
           t2 += s_red[w][1];
         }
@@ -235,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       __syncthreads();
       if (s_stop || s_abort) break;
-      for (int w = threadIdx.x; w < 8; w += kThreads) s_red[w][0] = s_red[w][1] = 0.0;
+      for (int w = threadIdx.x; w < kWarps; w += kWarps * 32) s_red[w][0] = s_red[w][1] = 0.0;
       const int br = s_br;
       const int ib = k & 1, ob = (k + 1) & 1;
       __syncthreads();
@@ -256,10 +267,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int s = g_prod % G::stages;
             if (g_prod >= G::stages && !mbar_wait(&empty[s], ((g_prod / G::stages) - 1) & 1, &s_abort)) break;
             uint8_t* base = smem + s * G::stage_bytes;
-            mbar_expect_tx(&full[s], G::stage_bytes);
+            // FS: the FP32 masters only, into the hi positions
+            mbar_expect_tx(&full[s], FS ? G::a_bytes + G::b_bytes : G::stage_bytes);
             tma_load_2d(base, mah, &full[s], kb * C::bk, ro + m0);
             tma_load_2d(base + G::a_bytes, mbh, &full[s], kb * C::bk, ro + n0);
-            if constexpr (C::split) {
+            if constexpr (C::split && !FS) {
               tma_load_2d(base + G::a_bytes + G::b_bytes, mal, &full[s], kb * C::bk, ro + m0);
               tma_load_2d(base + 2 * G::a_bytes + G::b_bytes, mbl, &full[s], kb * C::bk, ro + n0);
             }
@@ -274,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t dt = tmem + acc * BN;
           for (int kb = 0; kb < nk; ++kb, ++g_mma) {
             const int s = g_mma % G::stages;
-            if (!mbar_wait(&full[s], (g_mma / G::stages) & 1, &s_abort)) break;
+            if (!mbar_wait(FS ? &conv[s] : &full[s], (g_mma / G::stages) & 1, &s_abort)) break;
             tc_fence_after();
             const uint32_t base = smem_u32(smem + s * G::stage_bytes);
 #pragma unroll
@@ -293,6 +305,30 @@ __global__ void __launch_bounds__(kThreads, 1)
             umma_commit(&empty[s]);
           }
           umma_commit(&tfull[acc]);
+        }
+      } else if (FS && warp >= 6) {
+        // converters: each stage's FP32 tiles of A and B (16 KB each, the hi
+        // positions) become hi in place and lo at +32 KB, 16 float4 a thread
+        const int ct = threadIdx.x - 192;
+        for (int t = 0; t < ntiles && !s_abort; ++t) {
+          for (int kb = 0; kb < nk; ++kb, ++g_conv) {
+            const int s = g_conv % G::stages;
+            if (!mbar_wait_warp(&full[s], (g_conv / G::stages) & 1, &s_abort)) break;
+            float4* stage = reinterpret_cast<float4*>(smem + s * G::stage_bytes);
+            constexpr int kHalf = (G::a_bytes + G::b_bytes) / 16;  // float4 of A and B
+#pragma unroll 4
+            for (int i = ct; i < kHalf; i += 128) {
+              const float4 x = stage[i];
+              const float4 h = make_float4(to_tf32(x.x), to_tf32(x.y), to_tf32(x.z), to_tf32(x.w));
+              stage[i] = h;
+              stage[i + kHalf] = make_float4(to_tf32(x.x - h.x), to_tf32(x.y - h.y), to_tf32(x.z - h.z),
+                                             to_tf32(x.w - h.w));
+            }
+            // the generic-proxy stores must be visible to the tensor core's reads
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&conv[s])) : "memory");
+          }
         }
       } else if (warp >= 2) {
         const int q = warp & 3;
@@ -334,7 +370,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             float4* xo = reinterpret_cast<float4*>(xout + 32 * c);
 #pragma unroll
             for (int j = 0; j < 8; ++j) xo[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
-            store_operands<P>(y, hrow + 32 * c * C::eb, lrow + 32 * c * C::eb);
+            if constexpr (!FS) store_operands<P>(y, hrow + 32 * c * C::eb, lrow + 32 * c * C::eb);
             if (mirror) {
               // element (m0 + row, n0 + 32c + j) is also (n0 + 32c + j, m0 + row):
               // for each j the 32 lanes write 32 consecutive values
@@ -342,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int j = 0; j < 32; ++j) {
                 const size_t idx = (size_t)(ro + n0 + 32 * c + j) * ga.cols + m0 + row;
                 ga.M[ob][idx] = y[j];
-                store_operand1<P>(y[j], ga.Hi[ob], ga.Lo[ob] ? ga.Lo[ob] : ga.Hi[ob], idx);
+                if constexpr (!FS) store_operand1<P>(y[j], ga.Hi[ob], ga.Lo[ob] ? ga.Lo[ob] : ga.Hi[ob], idx);
               }
             }
           }
@@ -364,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---- D from the final iterate (buffer k % 2), report
     {
       const float* X = ga.M[k & 1];
-      for (int r = warp; r < n; r += kThreads / 32)
+      for (int r = warp; r < n; r += kWarps)
         for (int c = lane; c < n; c += 32) d.D[(size_t)r * n + c] = (double)X[(size_t)(ro + r) * ga.cols + c];
       if (threadIdx.x == 0 && d.rep) {
         tb_sp2_report* rp = d.rep;
@@ -793,11 +829,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 struct Plan {
   int count, precision, rule, max_iter;
   int rows, cols;
-  int bn, grid, cs;  // cs > 1: cluster form with cs CTAs per system
+  int bn, grid, cs;  // cs > 1: cluster form with cs CTAs per system; bn = 0: the FP32-staged form (tf32x3)
   double u;
   size_t off_desc, off_queue, off_err, off_m[2], off_hi[2], off_lo[2], total;
   CUtensorMap ah[2], al[2], bh[2], bl[2];  // bh/bl for the chosen bn
   CUtensorMap bh64[2], bl64[2], bh128[2], bl128[2];
+  CUtensorMap am[2];  // FP32 masters, 128-row boxes (FP32-staged form)
 };
 
 static_assert(sizeof(Plan) <= sizeof(((tb_ctx*)nullptr)->plan_cache), "plan cache too small");
@@ -865,17 +902,23 @@ GArgs make_args(const Plan& p, char* base) {
   return ga;
 }
 
-template <int P, int BN>
+template <int P, int BN, bool FS = false>
 int launch(tb_ctx* ctx, const Plan& p, char* base, int grid, cudaStream_t s) {
   using G = GCfg<P, BN>;
   static unsigned long long attr_done = 0;
-  if (int rc_attr = tb_smem_attr(ctx, k_sp2_grouped<P, BN>, G::smem, &attr_done)) return rc_attr;
+  if (int rc_attr = tb_smem_attr(ctx, k_sp2_grouped<P, BN, FS>, G::smem, &attr_done)) return rc_attr;
   const GArgs ga = make_args(p, base);
-  const CUtensorMap* bh = BN == 64 ? p.bh64 : p.bh128;
-  const CUtensorMap* bl = BN == 64 ? p.bl64 : p.bl128;
   TB_CUDA_TRY(ctx, cudaMemsetAsync(ga.queue, 0, sizeof(int), s));
-  k_sp2_grouped<P, BN><<<grid, kThreads, G::smem, s>>>(ga, p.ah[0], p.al[0], bh[0], bl[0], p.ah[1], p.al[1],
-                                                       bh[1], bl[1]);
+  if constexpr (FS) {
+    // A and B are row panels of the FP32 masters (BN = BM: one map per buffer)
+    k_sp2_grouped<P, BN, true><<<grid, kThreadsFs, G::smem, s>>>(ga, p.am[0], p.am[0], p.am[0], p.am[0], p.am[1],
+                                                                 p.am[1], p.am[1], p.am[1]);
+  } else {
+    const CUtensorMap* bh = BN == 64 ? p.bh64 : p.bh128;
+    const CUtensorMap* bl = BN == 64 ? p.bl64 : p.bl128;
+    k_sp2_grouped<P, BN, false><<<grid, kThreads, G::smem, s>>>(ga, p.ah[0], p.al[0], bh[0], bl[0], p.ah[1],
+                                                                p.al[1], bh[1], bl[1]);
+  }
   TB_LAUNCH_CHECK(ctx);
   return TB_OK;
 }
@@ -929,6 +972,10 @@ int launch_cl_any(tb_ctx* ctx, const Plan& p, char* base, int cs, cudaStream_t s
 
 int launch_any(tb_ctx* ctx, const Plan& p, char* base, int bn, int grid, cudaStream_t s) {
   const bool b64 = bn == 64;
+  if (bn == 0) {
+    if (p.precision != TB_PREC_TF32X3) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "the FP32-staged form is tf32x3 only");
+    return launch<TB_PREC_TF32X3, 128, true>(ctx, p, base, grid, s);
+  }
   switch (p.precision) {
     case TB_PREC_TF32: return b64 ? launch<TB_PREC_TF32, 64>(ctx, p, base, grid, s) : launch<TB_PREC_TF32, 128>(ctx, p, base, grid, s);
     case TB_PREC_TF32X3: return b64 ? launch<TB_PREC_TF32X3, 64>(ctx, p, base, grid, s) : launch<TB_PREC_TF32X3, 128>(ctx, p, base, grid, s);
@@ -1016,23 +1063,32 @@ extern "C" int dm_sp2_grouped_plan(tb_ctx* ctx, int count, const int* n, const d
       p.bl128[b] = p.bh128[b];
     }
   }
+  for (int b = 0; b < 2; ++b)
+    if (p.precision == TB_PREC_TF32X3) {
+      const int rc = make_map(ctx, p.precision, base + p.off_m[b], p.rows, p.cols, BM, &p.am[b]);
+      if (rc) return rc;
+    }
   p.bn = 128;
   p.grid = std::max(1, ctx->sm_count);
   p.cs = 1;
-  if (autotune == 4 || autotune == 8) {
+  if (autotune == 3) {
+    if (p.precision != TB_PREC_TF32X3) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "the FP32-staged form is tf32x3 only");
+    p.bn = 0;
+  } else if (autotune == 4 || autotune == 8) {
     p.cs = autotune;
     int rc = launch_cl_any(ctx, p, base, p.cs, s, &p.grid);  // sizes the grid (and warms up)
     if (rc) return rc;
   } else if (autotune) {
     // time every candidate on the batch itself and keep the fastest: one CTA
-    // per system with 128- or 64-wide tiles and a full or half grid, or
-    // clusters of 4 or 8 CTAs per system
+    // per system with 128- or 64-wide tiles and a full or half grid,
+    // clusters of 4 or 8 CTAs per system, or (tf32x3) the FP32-staged form
     struct Cand {
       int bn, grid, cs;
     };
-    const Cand cands[6] = {{128, ctx->sm_count, 1}, {128, std::max(1, ctx->sm_count / 2), 1},
+    const Cand cands[7] = {{128, ctx->sm_count, 1}, {128, std::max(1, ctx->sm_count / 2), 1},
                            {64, ctx->sm_count, 1},  {64, std::max(1, ctx->sm_count / 2), 1},
-                           {128, 0, 4},             {128, 0, 8}};
+                           {128, 0, 4},             {128, 0, 8},
+                           {0, ctx->sm_count, 1}};
     cudaEvent_t e0, e1;
     TB_CUDA_TRY(ctx, cudaEventCreate(&e0));
     TB_CUDA_TRY(ctx, cudaEventCreate(&e1));
@@ -1042,6 +1098,7 @@ extern "C" int dm_sp2_grouped_plan(tb_ctx* ctx, int count, const int* n, const d
       auto run = [&]() {
         return c.cs > 1 ? launch_cl_any(ctx, p, base, c.cs, s, &grid) : launch_any(ctx, p, base, c.bn, c.grid, s);
       };
+      if (c.bn == 0 && p.precision != TB_PREC_TF32X3) continue;
       int rc = run();  // warm-up
       if (rc == TB_ERR_UNSUPPORTED) continue;  // no cluster of that size fits
       if (rc) return rc;

@@ -50,14 +50,17 @@ def ctypes_size():
     return ctypes.sizeof(tbmd.tb_sp2_report)
 
 
-@pytest.mark.parametrize("mode", [1, 4, 8])
+@pytest.mark.parametrize("mode", [1, 3, 4, 8])
 def test_grouped_batch_matches_eigh(ctx, mode):
-    """mode 1: autotuned launch form; 4 / 8: clusters of that many CTAs per system."""
+    """mode 1: autotuned launch form; 3: the FP32-staged form; 4 / 8: clusters
+    of that many CTAs per system."""
     Hs, nocc = _batch(40)
     Ht, Dt, rep, ws, cfg = _solve(ctx, Hs, nocc, autotune=mode)
     cs, bn = cfg // 10 ** 7, (cfg // 10 ** 4) % 1000
-    assert bn in (64, 128) and cs in (1, 4, 8)
-    if mode > 1:
+    assert bn in (0, 64, 128) and cs in (1, 4, 8)
+    if mode == 3:
+        assert bn == 0 and cs == 1
+    elif mode > 1:
         assert cs == mode
     errs = []
     for i, H in enumerate(Hs):
@@ -81,7 +84,21 @@ def test_grouped_same_alone_and_in_the_mix(ctx, mode):
         assert torch.equal(Done[0], Dall[j])
 
 
-@pytest.mark.parametrize("mode", [0, 8])
+def test_fp32_staged_form_is_bitwise_the_stored_split_form(ctx):
+    """The converter warps split the FP32 X in shared memory exactly as the
+    stored-split form's epilogue splits it before storing (same rounding of
+    the same FP32 values), and the MMAs, their order and the epilogue
+    arithmetic are the same: D and every report are bitwise equal."""
+    Hs, nocc = _batch(40, seed=5)
+    _, D0, r0, _, _ = _solve(ctx, Hs, nocc, autotune=0)
+    _, D3, r3, _, cfg = _solve(ctx, Hs, nocc, autotune=3)
+    assert (cfg // 10 ** 4) % 1000 == 0
+    for a, b in zip(D0, D3):
+        assert torch.equal(a, b)
+    assert torch.equal(r0, r3)
+
+
+@pytest.mark.parametrize("mode", [0, 3, 8])
 def test_grouped_run_replays_in_a_cuda_graph(ctx, mode):
     Hs, nocc = _batch(16, seed=11)
     Ht, Dt, rep, ws, cfg = _solve(ctx, Hs, nocc, autotune=mode)
