@@ -15,7 +15,8 @@
 // maps per ping-pong buffer cover the batch.
 //
 // The plan call copies the per-system descriptors to the device once and
-// autotunes the launch (tile width BN in {64, 128} and the persistent grid)
+// autotunes the launch (tile width BN in {64, 128}, the persistent grid, the
+// cluster and FP32-staged forms)
 // by timing each candidate on the batch itself; the run call is a memset of
 // the queue counter and one kernel launch, so it can be captured into a CUDA
 // graph.
@@ -1009,6 +1010,8 @@ extern "C" int dm_sp2_grouped_plan(tb_ctx* ctx, int count, const int* n, const d
     if (n[i] < 1 || n[i] > kMaxLd || !H[i] || !D[i] || !(nocc[i] >= 0.0) || nocc[i] > n[i])
       return tb_fail(ctx, TB_ERR_ARG, "system %d: n = %d (1..%d), n_occ = %g", i, n[i], kMaxLd, nocc[i]);
   if ((reinterpret_cast<uintptr_t>(ws) & 1023) != 0) return tb_fail(ctx, TB_ERR_ARG, "workspace must be 1024-byte aligned");
+  if (autotune < 0 || autotune > 8 || (autotune > 4 && autotune != 8))
+    return tb_fail(ctx, TB_ERR_ARG, "autotune %d is not a launch form (0..4, 8)", autotune);
   Plan p{};
   const size_t need = layout(count, n, o->precision, &p);
   if (ws_bytes < need) return tb_fail(ctx, TB_ERR_ARG, "workspace %zu bytes < required %zu", ws_bytes, need);
@@ -1071,14 +1074,16 @@ extern "C" int dm_sp2_grouped_plan(tb_ctx* ctx, int count, const int* n, const d
   p.bn = 128;
   p.grid = std::max(1, ctx->sm_count);
   p.cs = 1;
-  if (autotune == 3) {
+  if (autotune == 0 && p.precision == TB_PREC_TF32X3) {
+    p.bn = 0;  // the FP32-staged form: bitwise the stored-split form's result, faster
+  } else if (autotune == 3) {
     if (p.precision != TB_PREC_TF32X3) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "the FP32-staged form is tf32x3 only");
     p.bn = 0;
   } else if (autotune == 4 || autotune == 8) {
     p.cs = autotune;
     int rc = launch_cl_any(ctx, p, base, p.cs, s, &p.grid);  // sizes the grid (and warms up)
     if (rc) return rc;
-  } else if (autotune) {
+  } else if (autotune == 1) {
     // time every candidate on the batch itself and keep the fastest: one CTA
     // per system with 128- or 64-wide tiles and a full or half grid,
     // clusters of 4 or 8 CTAs per system, or (tf32x3) the FP32-staged form

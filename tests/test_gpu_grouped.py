@@ -75,7 +75,7 @@ def test_grouped_batch_matches_eigh(ctx, mode):
     assert np.median(errs) < 3e-6
 
 
-@pytest.mark.parametrize("mode", [0, 4])
+@pytest.mark.parametrize("mode", [0, 2, 4])
 def test_grouped_same_alone_and_in_the_mix(ctx, mode):
     Hs, nocc = _batch(24, seed=9)
     _, Dall, _, _, _ = _solve(ctx, Hs, nocc, autotune=mode)
@@ -90,8 +90,9 @@ def test_fp32_staged_form_is_bitwise_the_stored_split_form(ctx):
     the same FP32 values), and the MMAs, their order and the epilogue
     arithmetic are the same: D and every report are bitwise equal."""
     Hs, nocc = _batch(40, seed=5)
-    _, D0, r0, _, _ = _solve(ctx, Hs, nocc, autotune=0)
+    _, D0, r0, _, cfg0 = _solve(ctx, Hs, nocc, autotune=2)
     _, D3, r3, _, cfg = _solve(ctx, Hs, nocc, autotune=3)
+    assert (cfg0 // 10 ** 4) % 1000 == 128
     assert (cfg // 10 ** 4) % 1000 == 0
     for a, b in zip(D0, D3):
         assert torch.equal(a, b)
