@@ -277,10 +277,10 @@ int dm_sp2_grouped_workspace_size(int count, const int* n, const tb_sp2_opts* op
  * operands stored by each projection's epilogue; 3 = the FP32-staged form
  * (tf32x3 only, else TB_ERR_UNSUPPORTED): the same but loading only the FP32 X
  * and splitting it into hi/lo in shared memory, bitwise the result of form 2;
- * 0 = form 3 for tf32x3, else form 2; 4 or 8 = thread-block clusters of that
- * many CTAs per system (the CTAs split each projection's tiles; as many clusters
- * as fit at once); 1 = time every form (tile width 64 or 128 with all or half
- * the SMs, clusters of 4 or 8, the FP32-staged form) on the batch itself and
+ * 0 = form 3 for tf32x3, else form 2; 4 or 8 (5: 2) = thread-block clusters of
+ * that many CTAs per system (the CTAs split each projection's tiles; as many
+ * clusters as fit at once); 1 = time every form (tile width 64 or 128 with all or
+ * half the SMs, clusters of 2, 4 or 8, the FP32-staged form) on the batch itself and
  * keep the fastest (the batch is solved several times).  config_out of the run
  * call reports the FP32-staged form as tile width 0.
  * Synchronises `stream`.  One plan per context at a time: a new plan replaces

@@ -953,20 +953,22 @@ int launch_cl(tb_ctx* ctx, const Plan& p, char* base, cudaStream_t s, int* grid_
   return TB_OK;
 }
 
+template <int P>
+int launch_cl_p(tb_ctx* ctx, const Plan& p, char* base, int cs, cudaStream_t s, int* grid_out) {
+  switch (cs) {
+    case 2: return launch_cl<P, 2>(ctx, p, base, s, grid_out);
+    case 4: return launch_cl<P, 4>(ctx, p, base, s, grid_out);
+    case 8: return launch_cl<P, 8>(ctx, p, base, s, grid_out);
+    default: return tb_fail(ctx, TB_ERR_ARG, "cluster size %d (2, 4 or 8)", cs);
+  }
+}
+
 int launch_cl_any(tb_ctx* ctx, const Plan& p, char* base, int cs, cudaStream_t s, int* grid_out) {
   switch (p.precision) {
-    case TB_PREC_TF32:
-      return cs == 8 ? launch_cl<TB_PREC_TF32, 8>(ctx, p, base, s, grid_out)
-                     : launch_cl<TB_PREC_TF32, 4>(ctx, p, base, s, grid_out);
-    case TB_PREC_TF32X3:
-      return cs == 8 ? launch_cl<TB_PREC_TF32X3, 8>(ctx, p, base, s, grid_out)
-                     : launch_cl<TB_PREC_TF32X3, 4>(ctx, p, base, s, grid_out);
-    case TB_PREC_BF16:
-      return cs == 8 ? launch_cl<TB_PREC_BF16, 8>(ctx, p, base, s, grid_out)
-                     : launch_cl<TB_PREC_BF16, 4>(ctx, p, base, s, grid_out);
-    case TB_PREC_BF16X3:
-      return cs == 8 ? launch_cl<TB_PREC_BF16X3, 8>(ctx, p, base, s, grid_out)
-                     : launch_cl<TB_PREC_BF16X3, 4>(ctx, p, base, s, grid_out);
+    case TB_PREC_TF32: return launch_cl_p<TB_PREC_TF32>(ctx, p, base, cs, s, grid_out);
+    case TB_PREC_TF32X3: return launch_cl_p<TB_PREC_TF32X3>(ctx, p, base, cs, s, grid_out);
+    case TB_PREC_BF16: return launch_cl_p<TB_PREC_BF16>(ctx, p, base, cs, s, grid_out);
+    case TB_PREC_BF16X3: return launch_cl_p<TB_PREC_BF16X3>(ctx, p, base, cs, s, grid_out);
     default: return tb_fail(ctx, TB_ERR_UNSUPPORTED, "grouped SP2 needs a tensor-core precision");
   }
 }
@@ -1010,8 +1012,8 @@ extern "C" int dm_sp2_grouped_plan(tb_ctx* ctx, int count, const int* n, const d
     if (n[i] < 1 || n[i] > kMaxLd || !H[i] || !D[i] || !(nocc[i] >= 0.0) || nocc[i] > n[i])
       return tb_fail(ctx, TB_ERR_ARG, "system %d: n = %d (1..%d), n_occ = %g", i, n[i], kMaxLd, nocc[i]);
   if ((reinterpret_cast<uintptr_t>(ws) & 1023) != 0) return tb_fail(ctx, TB_ERR_ARG, "workspace must be 1024-byte aligned");
-  if (autotune < 0 || autotune > 8 || (autotune > 4 && autotune != 8))
-    return tb_fail(ctx, TB_ERR_ARG, "autotune %d is not a launch form (0..4, 8)", autotune);
+  if (autotune < 0 || autotune > 8 || autotune == 6 || autotune == 7)
+    return tb_fail(ctx, TB_ERR_ARG, "autotune %d is not a launch form (0..5, 8)", autotune);
   Plan p{};
   const size_t need = layout(count, n, o->precision, &p);
   if (ws_bytes < need) return tb_fail(ctx, TB_ERR_ARG, "workspace %zu bytes < required %zu", ws_bytes, need);
@@ -1079,21 +1081,21 @@ extern "C" int dm_sp2_grouped_plan(tb_ctx* ctx, int count, const int* n, const d
   } else if (autotune == 3) {
     if (p.precision != TB_PREC_TF32X3) return tb_fail(ctx, TB_ERR_UNSUPPORTED, "the FP32-staged form is tf32x3 only");
     p.bn = 0;
-  } else if (autotune == 4 || autotune == 8) {
-    p.cs = autotune;
+  } else if (autotune == 4 || autotune == 8 || autotune == 5) {
+    p.cs = autotune == 5 ? 2 : autotune;
     int rc = launch_cl_any(ctx, p, base, p.cs, s, &p.grid);  // sizes the grid (and warms up)
     if (rc) return rc;
   } else if (autotune == 1) {
     // time every candidate on the batch itself and keep the fastest: one CTA
     // per system with 128- or 64-wide tiles and a full or half grid,
-    // clusters of 4 or 8 CTAs per system, or (tf32x3) the FP32-staged form
+    // clusters of 2, 4 or 8 CTAs per system, or (tf32x3) the FP32-staged form
     struct Cand {
       int bn, grid, cs;
     };
-    const Cand cands[7] = {{128, ctx->sm_count, 1}, {128, std::max(1, ctx->sm_count / 2), 1},
+    const Cand cands[8] = {{128, ctx->sm_count, 1}, {128, std::max(1, ctx->sm_count / 2), 1},
                            {64, ctx->sm_count, 1},  {64, std::max(1, ctx->sm_count / 2), 1},
-                           {128, 0, 4},             {128, 0, 8},
-                           {0, ctx->sm_count, 1}};
+                           {128, 0, 2},             {128, 0, 4},
+                           {128, 0, 8},             {0, ctx->sm_count, 1}};
     cudaEvent_t e0, e1;
     TB_CUDA_TRY(ctx, cudaEventCreate(&e0));
     TB_CUDA_TRY(ctx, cudaEventCreate(&e1));
