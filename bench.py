@@ -951,6 +951,25 @@ def run_batched(args):
     rep = torch.zeros(len(ns), rep_sz, dtype=torch.uint8, device="cuda")
     ws = Workspace(tbmd.dm_sp2_grouped_workspace_size(ns, opts))
     stream = torch.cuda.current_stream()
+    # every launch form on its own (ms per batch, best of 3 direct runs):
+    # 2 stored split, 3 FP32-staged (tf32x3), 5/4/8 clusters of 2/4/8 CTAs
+    forms = {}
+    for code, name in ((2, "one CTA per system, stored split"), (3, "one CTA per system, FP32-staged"),
+                       (5, "clusters of 2"), (4, "clusters of 4"), (8, "clusters of 8")):
+        try:
+            tbmd.dm_sp2_grouped_plan(ctx, ns, nocc, Ht, Dt, rep, opts, code, ws.ptr, ws.nbytes)
+        except tbmd.TBError:
+            continue
+        tbmd.dm_sp2_grouped_run(ctx, ws.ptr)
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tbmd.dm_sp2_grouped_run(ctx, ws.ptr)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best or 1e30, e0.elapsed_time(e1))
+        forms[name] = best
     results = {}
     for label, auto in (("fixed", 0), ("autotuned", 1)):
         tbmd.dm_sp2_grouped_plan(ctx, ns, nocc, Ht, Dt, rep, opts, auto, ws.ptr, ws.nbytes)
@@ -1022,7 +1041,8 @@ def run_batched(args):
                                         "grid": a["config"] % 10 ** 4},
                              "autotuned_ms": a["ms"], "fixed_ms": results["fixed"]["ms"],
                              "fixed": {"cluster": 1, "tile_n": (results["fixed"]["config"] // 10 ** 4) % 1000,
-                                       "grid": results["fixed"]["config"] % 10 ** 4}},
+                                       "grid": results["fixed"]["config"] % 10 ** 4},
+                             "ms_per_batch_by_form": forms},
                    latency_ms={"p50": a["ms"], "p99": _pct(a["ms_all"], 0.99)},
                    roofline={"bound": "tensor", "achieved": value, "peak": peak, "unit": "TFLOP/s",
                              "frac": value / peak, "traffic": None,

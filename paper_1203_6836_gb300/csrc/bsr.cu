@@ -46,6 +46,14 @@ constexpr int SB = 128;            // super-block side (tcgen05 tile)
 constexpr int MW = 32;             // bitmap words per row (1024 super-rows: n <= 131072)
 constexpr int kMaxNsb = MW * 32;
 constexpr int kThreads = 192;      // numeric kernel: TMA, MMA, 4 epilogue warps
+// tf32x3 keeps only the FP32 master of every block: the numeric kernel loads the
+// masters and four converter warps split them into hi and lo in shared memory
+// (the same rounding the stored splits had, so the products are bitwise those
+// of stored splits), at half the operand bytes and a third of the stores
+template <int P>
+constexpr bool kStaged = P == TB_PREC_TF32X3;
+template <int P>
+constexpr int kNumThreads = kStaged<P> ? 320 : kThreads;
 constexpr int kTiles = SB * SB;    // elements per super-block
 constexpr int kMaxGrid = 256;      // persistent numeric grid (<= SMs)
 constexpr int kBand = 8;           // block rows whose outputs the numeric kernel walks together
@@ -267,9 +275,11 @@ __global__ void __launch_bounds__(256) k_bsr_init_fill(const double* __restrict_
       const size_t e0 = (size_t)o * kTiles + (size_t)r * SB + 32 * cs;
       float* dst = b.val + e0;
       for (int j = 0; j < 32; ++j) dst[j] = y[j];
-      char* h = static_cast<char*>(b.hi) + e0 * Prec<P>::eb;
-      char* l = b.lo ? static_cast<char*>(b.lo) + e0 * Prec<P>::eb : h;
-      store_operands<P>(y, h, l);
+      if constexpr (!kStaged<P>) {
+        char* h = static_cast<char*>(b.hi) + e0 * Prec<P>::eb;
+        char* l = b.lo ? static_cast<char*>(b.lo) + e0 * Prec<P>::eb : h;
+        store_operands<P>(y, h, l);
+      }
     }
     ++o;
   }
@@ -421,9 +431,11 @@ __global__ void __launch_bounds__(256) k_bsr_init_fill_in(tb_bsr H, Args a, Sym 
       const size_t e0 = (size_t)o * kTiles + (size_t)r * SB + 32 * cs;
       float* dst = b.val + e0;
       for (int j = 0; j < 32; ++j) dst[j] = y[j];
-      char* hp = static_cast<char*>(b.hi) + e0 * Prec<P>::eb;
-      char* lp = b.lo ? static_cast<char*>(b.lo) + e0 * Prec<P>::eb : hp;
-      store_operands<P>(y, hp, lp);
+      if constexpr (!kStaged<P>) {
+        char* hp = static_cast<char*>(b.hi) + e0 * Prec<P>::eb;
+        char* lp = b.lo ? static_cast<char*>(b.lo) + e0 * Prec<P>::eb : hp;
+        store_operands<P>(y, hp, lp);
+      }
     }
     ++o;
   }
@@ -690,13 +702,13 @@ __global__ void __launch_bounds__(1024) k_bsr_order(Args a, Buf bn, Sym sy) {
 
 // Persistent numeric projection.
 template <int P>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kNumThreads<P>, 1)
     k_bsr_step_tc(Args a, const __grid_constant__ CUtensorMap ah, const __grid_constant__ CUtensorMap al,
                   const __grid_constant__ CUtensorMap bh, const __grid_constant__ CUtensorMap bl, Buf S, Buf bn,
                   Sym sy, Epi ep) {
   using C = Prec<P>;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[C::stages], empty[C::stages], tfull[2], tempty[2], mdone;
+  __shared__ __align__(8) uint64_t full[C::stages], empty[C::stages], tfull[2], tempty[2], mdone, conv[C::stages];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_abort;
   __shared__ double s_red[4][3];
@@ -712,6 +724,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int s = 0; s < C::stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      mbar_init(&conv[s], 4);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -745,10 +758,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int s = g % C::stages;
           if (g >= C::stages && !mbar_wait(&empty[s], ((g / C::stages) - 1) & 1, &s_abort)) break;
           uint8_t* base = smem + s * C::stage_bytes;
-          mbar_expect_tx(&full[s], C::stage_bytes);
+          // staged: the FP32 masters into the hi positions only
+          mbar_expect_tx(&full[s], kStaged<P> ? 2 * 128 * 128 : C::stage_bytes);
           tma_load_2d(base, &ah, &full[s], c * C::bk, pr.x * SB);
           tma_load_2d(base + 128 * 128, &bh, &full[s], c * C::bk, pr.y * SB);
-          if constexpr (C::split) {
+          if constexpr (C::split && !kStaged<P>) {
             tma_load_2d(base + 2 * 128 * 128, &al, &full[s], c * C::bk, pr.x * SB);
             tma_load_2d(base + 3 * 128 * 128, &bl, &full[s], c * C::bk, pr.y * SB);
           }
@@ -777,7 +791,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int p = p0; p < p1 && !s_abort; ++p) {
         for (int c = 0; c < chunks; ++c, ++g) {
           const int s = g % C::stages;
-          if (!mbar_wait(&full[s], (g / C::stages) & 1, &s_abort)) break;
+          if (!mbar_wait(kStaged<P> ? &conv[s] : &full[s], (g / C::stages) & 1, &s_abort)) break;
           tc_fence_after();
           const uint32_t base = smem_u32(smem + s * C::stage_bytes);
 #pragma unroll
@@ -802,6 +816,33 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     // arrives once every MMA this thread issued has completed
     umma_commit(&mdone);
+  } else if (kStaged<P> && warp >= 6) {
+    // converters: each stage's FP32 tiles of A and B (16 KB each, the hi
+    // positions) become hi in place and lo at +32 KB, 16 float4 a thread
+    const int ct = threadIdx.x - 192;
+    constexpr int kHalf = 2 * 128 * 128 / 16;  // float4 of A and B
+    int g = 0;
+    for (int u = blockIdx.x; u < nu && !s_abort; u += gridDim.x) {
+      const int o = sy.order[u];
+      const int npc = (sy.pair_ptr[o + 1] - sy.pair_ptr[o]) * chunks;
+      for (int i = 0; i < npc && !s_abort; ++i, ++g) {
+        const int s = g % C::stages;
+        if (!mbar_wait_warp(&full[s], (g / C::stages) & 1, &s_abort)) break;
+        float4* stage = reinterpret_cast<float4*>(smem + s * C::stage_bytes);
+#pragma unroll 4
+        for (int e = ct; e < kHalf; e += 128) {
+          const float4 x = stage[e];
+          const float4 h = make_float4(to_tf32(x.x), to_tf32(x.y), to_tf32(x.z), to_tf32(x.w));
+          stage[e] = h;
+          stage[e + kHalf] = make_float4(to_tf32(x.x - h.x), to_tf32(x.y - h.y), to_tf32(x.z - h.z),
+                                         to_tf32(x.w - h.w));
+        }
+        // the generic-proxy stores must be visible to the tensor core's reads
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&conv[s])) : "memory");
+      }
+    }
   } else if (warp >= 2) {
     const int q = warp & 3;
     const int row = 32 * q + lane;
@@ -822,7 +863,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int oi = sy.old_idx[o];
       const float* xold = oi >= 0 ? S.val + (size_t)oi * kTiles + (size_t)row * SB : nullptr;
       float* xnew = bn.val + (size_t)o * kTiles + (size_t)row * SB;
-      char* hrow = static_cast<char*>(bn.hi) + ((size_t)o * kTiles + (size_t)row * SB) * C::eb;
+      // stored splits (not with kStaged)
+      char* hrow = kStaged<P> ? nullptr : static_cast<char*>(bn.hi) + ((size_t)o * kTiles + (size_t)row * SB) * C::eb;
       char* lrow = bn.lo ? static_cast<char*>(bn.lo) + ((size_t)o * kTiles + (size_t)row * SB) * C::eb : hrow;
       int kept = 0;
       // a diagonal block of a product of two matrices is not exactly symmetric
@@ -878,7 +920,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         float4* xo = reinterpret_cast<float4*>(xnew + 32 * c);
 #pragma unroll
         for (int j = 0; j < 8; ++j) xo[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
-        store_operands<P>(y, hrow + 32 * c * C::eb, lrow + 32 * c * C::eb);
+        if constexpr (!kStaged<P>) store_operands<P>(y, hrow + 32 * c * C::eb, lrow + 32 * c * C::eb);
         if (twice) {
           // element (row, 32c + j) of block (I, J) is element (32c + j, row) of
           // block (J, I) (of this block itself for symd): for each j the 32
@@ -887,7 +929,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int j = 0; j < 32; ++j) {
             const size_t e = (size_t)(32 * c + j) * SB + row;
             xmir[e] = y[j];
-            store_operand1<P>(y[j], bn.hi, bn.lo ? bn.lo : bn.hi, (size_t)om * kTiles + e);
+            if constexpr (!kStaged<P>) store_operand1<P>(y[j], bn.hi, bn.lo ? bn.lo : bn.hi, (size_t)om * kTiles + e);
           }
         }
       }
@@ -977,9 +1019,11 @@ __global__ void __launch_bounds__(256) k_bsr_affine(Args a, Buf X, Buf out, floa
       float* dst = out.val + e0;
 #pragma unroll
       for (int j = 0; j < 32; ++j) dst[j] = y[j];
-      char* hp = static_cast<char*>(out.hi) + e0 * Prec<P>::eb;
-      char* lp = out.lo ? static_cast<char*>(out.lo) + e0 * Prec<P>::eb : hp;
-      store_operands<P>(y, hp, lp);
+      if constexpr (!kStaged<P>) {
+        char* hp = static_cast<char*>(out.hi) + e0 * Prec<P>::eb;
+        char* lp = out.lo ? static_cast<char*>(out.lo) + e0 * Prec<P>::eb : hp;
+        store_operands<P>(y, hp, lp);
+      }
     }
   }
 }
@@ -1042,6 +1086,7 @@ constexpr int kMaxBufs = 7;  // matrices of the Fermi expansion (SP2: two)
 
 struct BsrLayout {
   int n, ld, nsb, cap, pcap, nbuf;
+  bool staged;  // tf32x3: FP32 masters only, no stored operand splits
   size_t off_state, off_bparts, off_parts, off_scal, off_flags, off_cand, off_cnt, off_outrow, off_oldidx,
       off_pcnt, off_pptr, off_pairs, off_order;
   size_t off_rp[kMaxBufs], off_col[kMaxBufs], off_nz[kMaxBufs], off_st[kMaxBufs], off_lv[kMaxBufs],
@@ -1070,6 +1115,7 @@ BsrLayout bsr_layout(int n, int prec, int bpr, int nbuf) {
   };
   const size_t eb = (prec == TB_PREC_TF32 || prec == TB_PREC_TF32X3) ? 4 : 2;
   const bool split = prec == TB_PREC_TF32X3 || prec == TB_PREC_BF16X3;
+  L.staged = prec == TB_PREC_TF32X3;
   L.off_state = take(sizeof(SP2State));
   L.off_bparts = take(sizeof(double) * 2 * std::max((n + 7) / 8, L.nsb));
   L.off_parts = take(sizeof(double) * 3 * 2 * L.nparts);
@@ -1090,8 +1136,8 @@ BsrLayout bsr_layout(int n, int prec, int bpr, int nbuf) {
     L.off_st[b] = take(sizeof(uint32_t) * MW * L.nsb);
     L.off_lv[b] = take(sizeof(uint32_t) * MW * L.nsb);
     L.off_val[b] = take(sizeof(float) * (size_t)L.cap * kTiles);
-    L.off_hi[b] = take(eb * (size_t)L.cap * kTiles);
-    L.off_lo[b] = split ? take(eb * (size_t)L.cap * kTiles) : 0;
+    L.off_hi[b] = L.staged ? 0 : take(eb * (size_t)L.cap * kTiles);
+    L.off_lo[b] = (split && !L.staged) ? take(eb * (size_t)L.cap * kTiles) : 0;
   }
   L.total = o;
   return L;
@@ -1153,9 +1199,10 @@ int bind_engine(tb_ctx* ctx, int prec, const BsrLayout& L, void* ws, Engine* e) 
     b.stored = reinterpret_cast<uint32_t*>(base + L.off_st[i]);
     b.live = reinterpret_cast<uint32_t*>(base + L.off_lv[i]);
     b.val = reinterpret_cast<float*>(base + L.off_val[i]);
-    b.hi = base + L.off_hi[i];
+    b.hi = L.staged ? nullptr : base + L.off_hi[i];
     b.lo = L.off_lo[i] ? base + L.off_lo[i] : nullptr;
-    int rc = make_block_map(ctx, prec, b.hi, L.cap * SB, &e->m[i].mh);
+    // staged: the numeric kernel reads the FP32 masters (tf32 tiles of the same shape)
+    int rc = make_block_map(ctx, prec, L.staged ? static_cast<void*>(b.val) : b.hi, L.cap * SB, &e->m[i].mh);
     if (rc) return rc;
     if (b.lo) {
       if ((rc = make_block_map(ctx, prec, b.lo, L.cap * SB, &e->m[i].ml))) return rc;
@@ -1217,7 +1264,7 @@ int launch_product(tb_ctx* ctx, Engine& e, Args a, const Mat& A, const Mat& B, c
   k_bsr_order<<<1, 1024, 0, s>>>(a, out.b, e.sy);
   TB_LAUNCH_CHECK(ctx);
   if (prof_k >= 0) tb_prof_mark(ctx, 1, 2 * prof_k, s);
-  k_bsr_step_tc<P><<<grid, kThreads, Prec<P>::smem_bytes, s>>>(a, A.mh, A.ml, B.mh, B.ml, Sb, out.b, e.sy, ep);
+  k_bsr_step_tc<P><<<grid, kNumThreads<P>, Prec<P>::smem_bytes, s>>>(a, A.mh, A.ml, B.mh, B.ml, Sb, out.b, e.sy, ep);
   TB_LAUNCH_CHECK(ctx);
   if (prof_k >= 0) tb_prof_mark(ctx, 1, 2 * prof_k + 1, s);
   return TB_OK;
