@@ -880,13 +880,29 @@ __global__ void __launch_bounds__(kNumThreads<P>, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = 0u;
         }
+        // S's row segment: eight 16-byte loads (a scalar load per element would
+        // touch 32 rows' lines per warp instruction 32 times over)
+        float xs[32];
+        if (xold) {
+          const float4* x4 = reinterpret_cast<const float4*>(xold + 32 * c);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 t = x4[j];
+            xs[4 * j] = t.x;
+            xs[4 * j + 1] = t.y;
+            xs[4 * j + 2] = t.z;
+            xs[4 * j + 3] = t.w;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) xs[j] = 0.0f;
+        }
         float y[32];
         double ss = 0.0;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const float cxx = __uint_as_float(v[j]);
-          const float x = xold ? xold[32 * c + j] : 0.0f;
-          y[j] = fmaf(gamma, x, alpha * cxx);
+          y[j] = fmaf(gamma, xs[j], alpha * cxx);
           if (ep.d != 0.0f && I == J && row == 32 * c + j && I * SB + row < a.n) y[j] += ep.d;
         }
         if (symd && c == q) {
