@@ -921,12 +921,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int c = 0; c < BN / 32; ++c) {
         uint32_t v[32];
         tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + buf * BN + 32 * c, v);
+        // E's row segment: eight 16-byte loads instead of 32 scalar ones
+        float es[32];
+        if (erow) {
+          const float4* e4 = reinterpret_cast<const float4*>(erow + 32 * c);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 t = e4[j];
+            es[4 * j] = t.x;
+            es[4 * j + 1] = t.y;
+            es[4 * j + 2] = t.z;
+            es[4 * j + 3] = t.w;
+          }
+        }
         float y[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int col = n0 + 32 * c + j;
           float val = g.alpha * __uint_as_float(v[j]);
-          if (erow) val = fmaf(g.beta, erow[32 * c + j], val);
+          if (erow) val = fmaf(g.beta, es[j], val);
           if (col == (int)gr && (int)gr < g.n) val += g.gamma;
           y[j] = val;
           u2 += (double)val * (double)val;

@@ -744,12 +744,25 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int c = 0; c < BN / 32; ++c) {
             uint32_t v[32];
             tmem_ld32(tmem + (static_cast<uint32_t>(32 * q) << 16) + acc * BN + 32 * c, v);
+            // X_k's row segment: eight 16-byte loads instead of 32 scalar ones
+            float xs[32];
+            {
+              const float4* x4 = reinterpret_cast<const float4*>(xin + 32 * c);
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const float4 t = x4[j];
+                xs[4 * j] = t.x;
+                xs[4 * j + 1] = t.y;
+                xs[4 * j + 2] = t.z;
+                xs[4 * j + 3] = t.w;
+              }
+            }
             float y[32];
             float c2 = 0.0f;  // chunk sum in FP32, accumulated in FP64 (GB300 FP64 is slow)
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const float cxx = __uint_as_float(v[j]);
-              const float x = xin[32 * c + j];
+              const float x = xs[j];
               y[j] = br ? fmaf(2.0f, x, -cxx) : cxx;
               c2 = fmaf(y[j], y[j], c2);
               if (m0 + row == n0 + 32 * c + j) t1 += (double)y[j];
