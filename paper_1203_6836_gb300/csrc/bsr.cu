@@ -22,14 +22,23 @@
 //           K (live in both rows I and J) as pairs of source slots; the upper
 //           blocks are listed in (band of 8 block rows, column, row) order;
 //   numeric  a persistent tcgen05 kernel walks that list: TMA loads the (I,K)
-//           and (J,K) tiles of every pair into shared memory, the MMA
-//           accumulates in TMEM (double-buffered between blocks), the epilogue
-//           applies the branch (X^2 or 2X - X^2), zeroes every 32 x 32
-//           sub-block with ||.||_F < tau (one warp owns a 32-row band, so a
-//           sub-block norm is a warp reduction), writes the FP32 master and
-//           operand splits of block (I,J) and, transposed, of its mirror (J,I),
+//           and (J,K) tiles of every pair into shared memory (tf32x3: the FP32
+//           blocks, split into hi and lo there by four converter warps; other
+//           precisions: their stored splits), the MMA accumulates in TMEM
+//           (double-buffered between blocks), the epilogue applies the branch
+//           (X^2 or 2X - X^2), zeroes every 32 x 32 sub-block with ||.||_F <
+//           tau (one warp owns a 32-row band, so a sub-block norm is a warp
+//           reduction), writes block (I,J) and, transposed, its mirror (J,I),
 //           and accumulates FP64 trace partials.
-// The final iterate is scattered into the dense FP64 D.
+// The final iterate is written to the dense FP64 D or, with BSR input and
+// output (dm_sp2_sparse), to a BSR D.
+//
+// The same engine computes C = alpha A B + gamma S + delta I for two
+// different symmetric, commuting matrices (the candidate pattern is that of
+// A B and B A together, so it is symmetric; the diagonal blocks keep their
+// upper triangle and mirror it), which is what the block-sparse Fermi
+// expansion (dm_fermi_sparse, row f2) is built from, with exact affine steps
+// alpha X + delta I on X's pattern.
 
 #include "common.cuh"
 #include "tc_ptx.cuh"
