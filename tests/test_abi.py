@@ -67,3 +67,40 @@ def test_fermi_options_and_layouts_without_gpu():
     assert tbmd.tb_completion.solver_m.offset == 20
     assert tbmd.tb_completion.step.offset == 24
 
+
+
+def test_block_sparse_workspaces_without_gpu():
+    """The block-sparse SP2 and Fermi-expansion workspaces: n up to 131072
+    (1024-bit row bitmaps), TB_ERR_UNSUPPORTED above; tf32x3 keeps only the
+    FP32 master of each block (64 KB) where bf16x3 also stores two 32 KB
+    operand splits; the expansion holds seven matrices where SP2 holds two;
+    the capacity grows with the blocks per row."""
+    lib = tbmd.lib()
+    size = ctypes.c_size_t()
+
+    def sp2(n, prec, bpr):
+        o = tbmd.tb_sp2_opts(precision=tbmd.PREC[prec], max_iter=60, tol=1e-10, refine_iters=0, rule=0,
+                             refine_mode=1, tau=1e-5, bsr_blocks_per_row=bpr)
+        rc = lib.dm_sp2_workspace_size(n, ctypes.byref(o), ctypes.byref(size))
+        return rc, size.value
+
+    def foe(n, prec, bpr):
+        o = tbmd.tb_fermi_opts(precision=tbmd.PREC[prec], m=14, ns_iters=3, mu_iters=30)
+        rc = lib.dm_fermi_sparse_workspace_size(n, ctypes.byref(o), bpr, ctypes.byref(size))
+        return rc, size.value
+
+    assert sp2(131072, "tf32x3", 8)[0] == tbmd.TB_OK
+    assert sp2(131073, "tf32x3", 8)[0] == tbmd.TB_ERR_UNSUPPORTED
+    assert foe(131072, "tf32x3", 8)[0] == tbmd.TB_OK
+    assert foe(131073, "tf32x3", 8)[0] == tbmd.TB_ERR_UNSUPPORTED
+    assert foe(0, "tf32x3", 8)[0] == tbmd.TB_ERR_ARG
+    nsb, bpr = 64, 16
+    cap = nsb * bpr
+    _, s_tf = sp2(nsb * 128, "tf32x3", bpr)
+    _, s_bf = sp2(nsb * 128, "bf16x3", bpr)
+    blk = 128 * 128
+    assert s_tf >= 2 * cap * 4 * blk and s_tf < 2 * cap * 6 * blk  # FP32 masters, no splits
+    assert s_bf - s_tf >= 2 * cap * 2 * 2 * blk - 2 * 1024  # bf16x3 adds hi and lo (2 B each)
+    _, f_tf = foe(nsb * 128, "tf32x3", bpr)
+    assert f_tf >= 7 * cap * 4 * blk and f_tf > 3 * s_tf
+    assert foe(nsb * 128, "tf32x3", 2 * bpr)[1] > f_tf
