@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--workload", default="dense",
                     choices=["dense", "small", "sparse", "batched", "serving", "nonorth"])
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the arrival trace")
+    ap.add_argument("--slots", type=int, default=32, help="serving: steps in flight at once (one stream each)")
     ap.add_argument("--sparse-natoms", type=int, default=16384,
                     help="sparse: atoms of the Morton-ordered water-like system (16384 = the headline case)")
     ap.add_argument("--fermi-molecules", type=int, default=5461,
@@ -1083,7 +1084,7 @@ def run_serving(args):
     xp = xl_params(XL.dt, XL.kappa, XL.alpha, XL.c)
     sizes, arrivals, which = serving_trajectories(n_requests=args.requests)
     fo = fermi_opts(args.precision)
-    sv = Server(ctx, TP, xp, kT=0.1, max_slots=32, fermi=fo, scf_tol=1e-6, scf_max_iter=100)
+    sv = Server(ctx, TP, xp, kT=0.1, max_slots=args.slots, fermi=fo, scf_tol=1e-6, scf_max_iter=100)
     systems = []
     t0 = time.perf_counter()
     for i, N in enumerate(sizes):
@@ -1138,7 +1139,7 @@ def run_serving(args):
                    latency_ms={"p50": _pct(lat, 0.5), "p99": _pct(lat, 0.99), "max": max(lat)},
                    service_ms={"p50": _pct(svc, 0.5), "p99": _pct(svc, 0.99)},
                    requests_ok=ok, wall_s=wall, admission_s=admit_s,
-                   server={"slots": 32, "bytes_in_use": st["bytes_in_use"], "budget": st["budget"],
+                   server={"slots": args.slots, "bytes_in_use": st["bytes_in_use"], "budget": st["budget"],
                            "admitted": st["admitted"]},
                    foe={"m_max": fo.m, "m_used": sorted({c.solver_m for c in out}), "ns_iters": ns,
                         "mean_expansions_per_step": sum(c.solver_iters for c in out) / len(out)},
