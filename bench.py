@@ -808,7 +808,9 @@ def run_sparse(args):
     # array) for the gapped vapour from 2046 to 65535 atoms (n up to 131070);
     # capacities 64 blocks per block row for H and D, 96 for the SP2 iterates
     from paper_1203_6836_gb300.device import BsrMatrix  # noqa: F401
-    og = sp2_opts(args.precision, max_iter=80, tau=1e-5, blocks_per_row=96)
+    # max_iter 40: the vapour needs 16 projections; the host issues max_iter + 1
+    # projection launches per D and those after the device-side stop return at once
+    og = sp2_opts(args.precision, max_iter=40, tau=1e-5, blocks_per_row=96)
     scaling = []
     for nmol in args.scaling_molecules:
         w = gapped_vapour(nmol, seed=0, morton=True)

@@ -172,9 +172,9 @@ __device__ __forceinline__ double x0_val(const double* H, int n, int r, int c, d
   return ((r == c ? emax : 0.0) - H[(size_t)r * n + c]) * inv;
 }
 
-// Keep mask of super-block (I, J) of X0 from the per-row sums of squares rs
-// of its upper twin (min(I,J), max(I,J)) (256 threads: row r = tid / 2,
-// columns 64 (tid % 2) ..): the 16 sub-block norms summed in a fixed order,
+// Keep mask of super-block (I, J) of X0 from the per-row, per-32-column sums
+// of squares rs of its upper twin (min(I,J), max(I,J)): the 16 sub-block
+// norms summed in a fixed order,
 // kept where ||.||_F >= tau; below the diagonal the twin's mask transposed,
 // so that the pattern is exactly symmetric (the products compute upper
 // blocks and mirror them).
@@ -201,14 +201,17 @@ __global__ void __launch_bounds__(256) k_bsr_init_flags(const double* __restrict
   const int I0 = min(I, J), J0 = max(I, J);
   double emax, inv;
   x0_affine(a, &emax, &inv);
-  const int r = threadIdx.x >> 1, h = threadIdx.x & 1;
-  double part[2] = {0.0, 0.0};
-  for (int c = 0; c < 64; ++c) {
-    const double x = x0_val(H, a.n, I0 * SB + r, J0 * SB + 64 * h + c, emax, inv);
-    part[c >> 5] += x * x;
+  // a warp per row, lanes across the columns (coalesced): the row's four
+  // 32-column sums of squares
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = warp; r < SB; r += 8) {
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const double x = x0_val(H, a.n, I0 * SB + r, J0 * SB + 32 * cc + lane, emax, inv);
+      const double q2 = warp_sum(x * x);
+      if (lane == 0) rs[r][cc] = q2;
+    }
   }
-  rs[r][2 * h] = part[0];
-  rs[r][2 * h + 1] = part[1];
   const uint16_t f = keep_mask(a, I, J, rs);
   if (threadIdx.x == 0) sy.flags[(size_t)I * a.nsb + J] = f;
 }
@@ -327,39 +330,40 @@ __device__ __forceinline__ int bsr_find(const int* __restrict__ row_ptr, const i
   return -1;
 }
 
-// Gershgorin partials of block row I (one block of 128 threads, a thread per
-// row): min(H_ii - r_i), max(H_ii + r_i) over the rows into bparts[2 I].
+// Gershgorin partials of block row I (one block of 128 threads; a warp per
+// row, its lanes across the columns, so every load is a coalesced 256-byte
+// row segment): min(H_ii - r_i), max(H_ii + r_i) over the rows into bparts[2 I].
 __global__ void __launch_bounds__(128) k_bsr_bounds_in(tb_bsr H, double* __restrict__ bparts) {
   __shared__ double smin[4], smax[4];
-  const int I = blockIdx.x, r = threadIdx.x;
+  const int I = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (*H.status != TB_OK) {  // an incomplete H (k_bsr_status_in fails the call)
-    if (r == 0) bparts[2 * I] = bparts[2 * I + 1] = 0.0;
+    if (threadIdx.x == 0) bparts[2 * I] = bparts[2 * I + 1] = 0.0;
     return;
   }
-  const int row = I * SB + r;
   double lo = INFINITY, hi = -INFINITY;
-  if (row < H.n) {
+  for (int r = warp; r < SB && I * SB + r < H.n; r += 4) {
     double rad = 0.0, c = 0.0;
     for (int o = H.row_ptr[I]; o < H.row_ptr[I + 1]; ++o) {
       const double* blk = H.val + (size_t)o * kTiles + (size_t)r * SB;
-      const int J = H.col[o];
-      for (int j = 0; j < SB; ++j) {
-        const double x = blk[j];
-        if (J == I && j == r) c = x;
+      const bool dblk = H.col[o] == I;
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const double x = blk[32 * cc + lane];
+        if (dblk && 32 * cc + lane == r) c += x;
         else rad += fabs(x);
       }
     }
-    lo = c - rad;
-    hi = c + rad;
+    rad = warp_sum(rad);
+    c = warp_sum(c);  // one lane holds the diagonal element
+    lo = fmin(lo, c - rad);
+    hi = fmax(hi, c + rad);
   }
-  lo = warp_min(lo);
-  hi = warp_max(hi);
-  if ((r & 31) == 0) {
-    smin[r >> 5] = lo;
-    smax[r >> 5] = hi;
+  if (lane == 0) {
+    smin[warp] = lo;
+    smax[warp] = hi;
   }
   __syncthreads();
-  if (r == 0) {
+  if (threadIdx.x == 0) {
     bparts[2 * I] = fmin(fmin(smin[0], smin[1]), fmin(smin[2], smin[3]));
     bparts[2 * I + 1] = fmax(fmax(smax[0], smax[1]), fmax(smax[2], smax[3]));
   }
@@ -396,14 +400,15 @@ __global__ void __launch_bounds__(256) k_bsr_init_flags_in(tb_bsr H, Args a, Sym
   const double* blk = slot >= 0 ? H.val + (size_t)slot * kTiles : nullptr;
   double emax, inv;
   x0_affine(a, &emax, &inv);
-  const int r = threadIdx.x >> 1, h = threadIdx.x & 1;
-  double part[2] = {0.0, 0.0};
-  for (int c = 0; c < 64; ++c) {
-    const double x = x0_blk(blk, I0, J0, a.n, r, 64 * h + c, emax, inv);
-    part[c >> 5] += x * x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = warp; r < SB; r += 8) {
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const double x = x0_blk(blk, I0, J0, a.n, r, 32 * cc + lane, emax, inv);
+      const double q2 = warp_sum(x * x);
+      if (lane == 0) rs[r][cc] = q2;
+    }
   }
-  rs[r][2 * h] = part[0];
-  rs[r][2 * h + 1] = part[1];
   const uint16_t f = keep_mask(a, I, J, rs);
   if (threadIdx.x == 0) sy.flags[(size_t)I * a.nsb + J] = f;
 }
