@@ -172,47 +172,61 @@ __device__ __forceinline__ double x0_val(const double* H, int n, int r, int c, d
   return ((r == c ? emax : 0.0) - H[(size_t)r * n + c]) * inv;
 }
 
-// Keep mask of super-block (I, J) of X0 from the per-row, per-32-column sums
-// of squares rs of its upper twin (min(I,J), max(I,J)): the 16 sub-block
-// norms summed in a fixed order,
-// kept where ||.||_F >= tau; below the diagonal the twin's mask transposed,
-// so that the pattern is exactly symmetric (the products compute upper
-// blocks and mirror them).
-__device__ uint16_t keep_mask(const Args& a, int I, int J, double (*rs)[4]) {
-  __shared__ double sq[16];
-  __syncthreads();
-  if (threadIdx.x < 16) {
-    const int rb = threadIdx.x >> 2, cb = threadIdx.x & 3;
-    double t = 0.0;
-    for (int rr = 0; rr < 32; ++rr) t += rs[32 * rb + rr][cb];
-    sq[threadIdx.x] = t;
+// Per-lane partial sums of squares of the 16 32 x 32 sub-blocks of a 128 x 128
+// block x(r, c) (256 threads: warp w takes rows w + 8k, lane l the columns
+// 32 c + l, so every row segment is one coalesced load; row w + 8k lies in
+// sub-block row k / 4).
+template <class X>
+__device__ __forceinline__ void block_partials(X x, double (&acc)[16]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < 16; ++s) acc[s] = 0.0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int r = warp + 8 * k;
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const double v = x(r, 32 * cc + lane);
+      acc[(k >> 2) * 4 + cc] = fma(v, v, acc[(k >> 2) * 4 + cc]);
+    }
+  }
+}
+
+// Keep mask of super-block (I, J) of X0 from the partial sums (block_partials)
+// of its upper twin (min(I,J), max(I,J)): a warp sum per sub-block, the eight
+// warps combined in a fixed order, kept where ||.||_F >= tau; below the
+// diagonal the twin's mask transposed, so that the pattern is exactly
+// symmetric (the products compute upper blocks and mirror them).  Called by
+// every thread of the block; the mask is valid in thread 0.
+__device__ uint16_t keep_mask(const Args& a, int I, int J, const double (&acc)[16]) {
+  __shared__ double wsum[8][16];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    const double v = warp_sum(acc[s]);
+    if (lane == 0) wsum[warp][s] = v;
   }
   __syncthreads();
   uint16_t f = 0;
-  for (int s = 0; s < 16; ++s)
-    if (sq[s] >= a.tau2 && sq[s] > 0.0) f |= (uint16_t)(1u << (I <= J ? s : (s & 3) * 4 + (s >> 2)));
+  if (threadIdx.x == 0)
+    for (int s = 0; s < 16; ++s) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += wsum[w][s];
+      if (t >= a.tau2 && t > 0.0) f |= (uint16_t)(1u << (I <= J ? s : (s & 3) * 4 + (s >> 2)));
+    }
+  __syncthreads();  // wsum is reused by the next block of a grid-stride loop
   return f;
 }
 
 // One block per super-block (I, J) of X0 = s (e I - H): its keep mask.
 __global__ void __launch_bounds__(256) k_bsr_init_flags(const double* __restrict__ H, Args a, Sym sy) {
-  __shared__ double rs[SB][4];
   const int I = blockIdx.y, J = blockIdx.x;
   const int I0 = min(I, J), J0 = max(I, J);
   double emax, inv;
   x0_affine(a, &emax, &inv);
-  // a warp per row, lanes across the columns (coalesced): the row's four
-  // 32-column sums of squares
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int r = warp; r < SB; r += 8) {
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      const double x = x0_val(H, a.n, I0 * SB + r, J0 * SB + 32 * cc + lane, emax, inv);
-      const double q2 = warp_sum(x * x);
-      if (lane == 0) rs[r][cc] = q2;
-    }
-  }
-  const uint16_t f = keep_mask(a, I, J, rs);
+  double acc[16];
+  block_partials([&](int r, int c) { return x0_val(H, a.n, I0 * SB + r, J0 * SB + c, emax, inv); }, acc);
+  const uint16_t f = keep_mask(a, I, J, acc);
   if (threadIdx.x == 0) sy.flags[(size_t)I * a.nsb + J] = f;
 }
 
@@ -384,33 +398,46 @@ __global__ void k_bsr_status_in(const int* Hstatus, SP2State* st) {
   if (*Hstatus != TB_OK) st->err = TB_ERR_OOM;
 }
 
+// Row of slot o of a BSR matrix: the last row whose start is <= o.
+__device__ __forceinline__ int bsr_row_of(const int* __restrict__ row_ptr, int nsb, int o) {
+  int lo = 0, hi = nsb;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (row_ptr[mid] <= o) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Keep masks of X0 from a BSR H, one block per stored block of H (grid-stride;
+// the masks start zeroed, and a block H does not store is zero in X0 off the
+// diagonal); k_bsr_init_flags_diag covers diagonal blocks H does not store.
 __global__ void __launch_bounds__(256) k_bsr_init_flags_in(tb_bsr H, Args a, Sym sy) {
-  __shared__ double rs[SB][4];
-  const int I = blockIdx.y, J = blockIdx.x;
-  const int I0 = min(I, J), J0 = max(I, J);
-  if (*H.status != TB_OK) {
-    if (threadIdx.x == 0) sy.flags[(size_t)I * a.nsb + J] = 0;
-    return;
-  }
-  const int slot = bsr_find(H.row_ptr, H.col, I0, J0);
-  if (slot < 0 && I != J) {
-    if (threadIdx.x == 0) sy.flags[(size_t)I * a.nsb + J] = 0;
-    return;
-  }
-  const double* blk = slot >= 0 ? H.val + (size_t)slot * kTiles : nullptr;
+  if (*H.status != TB_OK) return;  // the call fails through k_bsr_status_in
+  const int nblk = min(H.row_ptr[H.nsb], H.cap);
   double emax, inv;
   x0_affine(a, &emax, &inv);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int r = warp; r < SB; r += 8) {
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      const double x = x0_blk(blk, I0, J0, a.n, r, 32 * cc + lane, emax, inv);
-      const double q2 = warp_sum(x * x);
-      if (lane == 0) rs[r][cc] = q2;
-    }
+  for (int o = blockIdx.x; o < nblk; o += gridDim.x) {
+    const int I = bsr_row_of(H.row_ptr, H.nsb, o), J = H.col[o];
+    const int I0 = min(I, J), J0 = max(I, J);
+    const int slot = I <= J ? o : bsr_find(H.row_ptr, H.col, I0, J0);
+    const double* blk = slot >= 0 ? H.val + (size_t)slot * kTiles : nullptr;
+    double acc[16];
+    block_partials([&](int r, int c) { return x0_blk(blk, I0, J0, a.n, r, c, emax, inv); }, acc);
+    const uint16_t f = keep_mask(a, I, J, acc);
+    if (threadIdx.x == 0) sy.flags[(size_t)I * a.nsb + J] = f;
   }
-  const uint16_t f = keep_mask(a, I, J, rs);
-  if (threadIdx.x == 0) sy.flags[(size_t)I * a.nsb + J] = f;
+}
+
+__global__ void __launch_bounds__(256) k_bsr_init_flags_diag(tb_bsr H, Args a, Sym sy) {
+  const int I = blockIdx.x;
+  if (*H.status != TB_OK || bsr_find(H.row_ptr, H.col, I, I) >= 0) return;
+  double emax, inv;
+  x0_affine(a, &emax, &inv);
+  double acc[16];
+  block_partials([&](int r, int c) { return x0_blk(nullptr, I, I, a.n, r, c, emax, inv); }, acc);
+  const uint16_t f = keep_mask(a, I, I, acc);
+  if (threadIdx.x == 0) sy.flags[(size_t)I * a.nsb + I] = f;
 }
 
 // As k_bsr_init_fill, from the blocks of a BSR H.
@@ -1262,8 +1289,14 @@ template <int P>
 int launch_start(tb_ctx* ctx, Engine& e, const Args& a, const double* H, const tb_bsr* Hb, Mat& out,
                  cudaStream_t s) {
   const int nsb = e.L.nsb;
-  if (Hb) k_bsr_init_flags_in<<<dim3(nsb, nsb), 256, 0, s>>>(*Hb, a, e.sy);
-  else k_bsr_init_flags<<<dim3(nsb, nsb), 256, 0, s>>>(H, a, e.sy);
+  if (Hb) {
+    TB_CUDA_TRY(ctx, cudaMemsetAsync(e.sy.flags, 0, sizeof(uint16_t) * (size_t)nsb * nsb, s));
+    k_bsr_init_flags_in<<<std::max(1, std::min(Hb->cap, 8192)), 256, 0, s>>>(*Hb, a, e.sy);
+    TB_LAUNCH_CHECK(ctx);
+    k_bsr_init_flags_diag<<<nsb, 256, 0, s>>>(*Hb, a, e.sy);
+  } else {
+    k_bsr_init_flags<<<dim3(nsb, nsb), 256, 0, s>>>(H, a, e.sy);
+  }
   TB_LAUNCH_CHECK(ctx);
   k_bsr_init_rows<<<nsb, 256, 0, s>>>(a, e.sy, out.b);
   TB_LAUNCH_CHECK(ctx);
