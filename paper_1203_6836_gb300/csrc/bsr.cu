@@ -344,33 +344,43 @@ __device__ __forceinline__ int bsr_find(const int* __restrict__ row_ptr, const i
   return -1;
 }
 
-// Gershgorin partials of block row I (one block of 128 threads; a warp per
-// row, its lanes across the columns, so every load is a coalesced 256-byte
-// row segment): min(H_ii - r_i), max(H_ii + r_i) over the rows into bparts[2 I].
-__global__ void __launch_bounds__(128) k_bsr_bounds_in(tb_bsr H, double* __restrict__ bparts) {
-  __shared__ double smin[4], smax[4];
+// Gershgorin partials of block row I (one block of 256 threads): warp w
+// takes rows w + 8k of every block of the row, lane l the columns 32 c + l, so
+// each block is read as 64 independent coalesced loads a lane, and the row
+// sums stay in registers until one warp sum per row; min(H_ii - r_i) and
+// max(H_ii + r_i) over the rows go into bparts[2 I].
+__global__ void __launch_bounds__(256) k_bsr_bounds_in(tb_bsr H, double* __restrict__ bparts) {
+  __shared__ double smin[8], smax[8];
   const int I = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (*H.status != TB_OK) {  // an incomplete H (k_bsr_status_in fails the call)
     if (threadIdx.x == 0) bparts[2 * I] = bparts[2 * I + 1] = 0.0;
     return;
   }
-  double lo = INFINITY, hi = -INFINITY;
-  for (int r = warp; r < SB && I * SB + r < H.n; r += 4) {
-    double rad = 0.0, c = 0.0;
-    for (int o = H.row_ptr[I]; o < H.row_ptr[I + 1]; ++o) {
-      const double* blk = H.val + (size_t)o * kTiles + (size_t)r * SB;
-      const bool dblk = H.col[o] == I;
+  double rad[16], dia[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) rad[k] = dia[k] = 0.0;
+  for (int o = H.row_ptr[I]; o < H.row_ptr[I + 1]; ++o) {
+    const double* blk = H.val + (size_t)o * kTiles;
+    const bool dblk = H.col[o] == I;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int r = warp + 8 * k;
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {
-        const double x = blk[32 * cc + lane];
-        if (dblk && 32 * cc + lane == r) c += x;
-        else rad += fabs(x);
+        const double x = blk[(size_t)r * SB + 32 * cc + lane];
+        if (dblk && 32 * cc + lane == r) dia[k] += x;
+        else rad[k] += fabs(x);
       }
     }
-    rad = warp_sum(rad);
-    c = warp_sum(c);  // one lane holds the diagonal element
-    lo = fmin(lo, c - rad);
-    hi = fmax(hi, c + rad);
+  }
+  double lo = INFINITY, hi = -INFINITY;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const double rs = warp_sum(rad[k]), c = warp_sum(dia[k]);  // one lane holds the diagonal element
+    if (I * SB + warp + 8 * k < H.n) {
+      lo = fmin(lo, c - rs);
+      hi = fmax(hi, c + rs);
+    }
   }
   if (lane == 0) {
     smin[warp] = lo;
@@ -378,8 +388,13 @@ __global__ void __launch_bounds__(128) k_bsr_bounds_in(tb_bsr H, double* __restr
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    bparts[2 * I] = fmin(fmin(smin[0], smin[1]), fmin(smin[2], smin[3]));
-    bparts[2 * I + 1] = fmax(fmax(smax[0], smax[1]), fmax(smax[2], smax[3]));
+    double a = smin[0], b = smax[0];
+    for (int w = 1; w < 8; ++w) {
+      a = fmin(a, smin[w]);
+      b = fmax(b, smax[w]);
+    }
+    bparts[2 * I] = a;
+    bparts[2 * I + 1] = b;
   }
 }
 
@@ -1368,7 +1383,7 @@ int run_bsr(tb_ctx* ctx, const double* H, const tb_bsr* Hb, int n, double nocc, 
   if (Hb) {
     k_bsr_status_in<<<1, 1, 0, s>>>(Hb->status, st);
     TB_LAUNCH_CHECK(ctx);
-    k_bsr_bounds_in<<<L.nsb, 128, 0, s>>>(*Hb, e.bparts);
+    k_bsr_bounds_in<<<L.nsb, 256, 0, s>>>(*Hb, e.bparts);
     TB_LAUNCH_CHECK(ctx);
     k_bsr_bounds<<<1, 32, 0, s>>>(e.bparts, L.nsb, st);
   } else {
@@ -1454,7 +1469,7 @@ int run_bsr_fermi(tb_ctx* ctx, const tb_bsr* Hb, int n, double nocc, double kT, 
   const double beta = 1.0 / kT;
   TB_CUDA_TRY(ctx, cudaMemsetAsync(st, 0, sizeof(SP2State), s));
   k_bsr_status_in<<<1, 1, 0, s>>>(Hb->status, st);
-  k_bsr_bounds_in<<<L.nsb, 128, 0, s>>>(*Hb, e.bparts);
+  k_bsr_bounds_in<<<L.nsb, 256, 0, s>>>(*Hb, e.bparts);
   k_bsr_bounds<<<1, 32, 0, s>>>(e.bparts, L.nsb, st);
   TB_LAUNCH_CHECK(ctx);
   SP2State hs;
