@@ -192,13 +192,15 @@ __device__ __forceinline__ void block_partials(X x, double (&acc)[16]) {
   }
 }
 
-// Keep mask of super-block (I, J) of X0 from the partial sums (block_partials)
-// of its upper twin (min(I,J), max(I,J)): a warp sum per sub-block, the eight
-// warps combined in a fixed order, kept where ||.||_F >= tau; below the
+// Keep mask of super-block (I, J) of X0 = s (e I - H) from the partial sums
+// (block_partials) of e I - H over its upper twin (min(I,J), max(I,J)): a
+// warp sum per sub-block, the eight warps combined in a fixed order, times
+// scale2 = s^2, kept where ||.||_F >= tau (one FMA per element: GB300's FP64
+// rate is low); below the
 // diagonal the twin's mask transposed, so that the pattern is exactly
 // symmetric (the products compute upper blocks and mirror them).  Called by
 // every thread of the block; the mask is valid in thread 0.
-__device__ uint16_t keep_mask(const Args& a, int I, int J, const double (&acc)[16]) {
+__device__ uint16_t keep_mask(const Args& a, int I, int J, const double (&acc)[16], double scale2) {
   __shared__ double wsum[8][16];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -212,6 +214,7 @@ __device__ uint16_t keep_mask(const Args& a, int I, int J, const double (&acc)[1
     for (int s = 0; s < 16; ++s) {
       double t = 0.0;
       for (int w = 0; w < 8; ++w) t += wsum[w][s];
+      t *= scale2;
       if (t >= a.tau2 && t > 0.0) f |= (uint16_t)(1u << (I <= J ? s : (s & 3) * 4 + (s >> 2)));
     }
   __syncthreads();  // wsum is reused by the next block of a grid-stride loop
@@ -225,8 +228,8 @@ __global__ void __launch_bounds__(256) k_bsr_init_flags(const double* __restrict
   double emax, inv;
   x0_affine(a, &emax, &inv);
   double acc[16];
-  block_partials([&](int r, int c) { return x0_val(H, a.n, I0 * SB + r, J0 * SB + c, emax, inv); }, acc);
-  const uint16_t f = keep_mask(a, I, J, acc);
+  block_partials([&](int r, int c) { return x0_val(H, a.n, I0 * SB + r, J0 * SB + c, emax, 1.0); }, acc);
+  const uint16_t f = keep_mask(a, I, J, acc, inv * inv);
   if (threadIdx.x == 0) sy.flags[(size_t)I * a.nsb + J] = f;
 }
 
@@ -255,17 +258,29 @@ __global__ void k_bsr_init_rows(Args a, Sym sy, Buf b) {
 }
 
 // Exclusive scan of cnt[0..nsb) into row_ptr (one block); total into scal[0].
+// One warp: lane l scans rows [l * per, (l + 1) * per) after an exclusive
+// warp scan of the lanes' sums.
 __global__ void k_bsr_scan_rows(Args a, Sym sy, int* row_ptr) {
   if (a.st->done || a.st->err) return;
-  if (threadIdx.x == 0) {
-    int s = 0;
-    for (int i = 0; i < a.nsb; ++i) {
-      row_ptr[i] = s;
-      s += sy.cnt[i];
-    }
-    row_ptr[a.nsb] = s;
-    sy.scal[0] = s;
-    if (s > a.cap) atomicExch(&a.st->err, TB_ERR_OOM);
+  const int lane = threadIdx.x & 31, per = (a.nsb + 31) / 32;
+  const int lo = min(a.nsb, lane * per), hi = min(a.nsb, lo + per);
+  int mine = 0;
+  for (int i = lo; i < hi; ++i) mine += sy.cnt[i];
+  int incl = mine;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  int run = incl - mine;
+  for (int i = lo; i < hi; ++i) {
+    row_ptr[i] = run;
+    run += sy.cnt[i];
+  }
+  if (lane == 31) {
+    row_ptr[a.nsb] = incl;
+    sy.scal[0] = incl;
+    if (incl > a.cap) atomicExch(&a.st->err, TB_ERR_OOM);
   }
 }
 
@@ -398,6 +413,14 @@ __global__ void __launch_bounds__(256) k_bsr_bounds_in(tb_bsr H, double* __restr
   }
 }
 
+// e delta - h at element (r, c) of block (I, J) (zero outside the n x n matrix).
+__device__ __forceinline__ double x0_unscaled(const double* blk, int I, int J, int n, int r, int c, double e) {
+  const int gr = I * SB + r, gc = J * SB + c;
+  if (gr >= n || gc >= n) return 0.0;
+  const double h = blk ? blk[(size_t)r * SB + c] : 0.0;
+  return gr == gc ? e - h : -h;
+}
+
 __device__ __forceinline__ double x0_blk(const double* blk, int I, int J, int n, int r, int c, double emax,
                                          double inv) {
   const int gr = I * SB + r, gc = J * SB + c;
@@ -438,8 +461,8 @@ __global__ void __launch_bounds__(256) k_bsr_init_flags_in(tb_bsr H, Args a, Sym
     const int slot = I <= J ? o : bsr_find(H.row_ptr, H.col, I0, J0);
     const double* blk = slot >= 0 ? H.val + (size_t)slot * kTiles : nullptr;
     double acc[16];
-    block_partials([&](int r, int c) { return x0_blk(blk, I0, J0, a.n, r, c, emax, inv); }, acc);
-    const uint16_t f = keep_mask(a, I, J, acc);
+    block_partials([&](int r, int c) { return x0_unscaled(blk, I0, J0, a.n, r, c, emax); }, acc);
+    const uint16_t f = keep_mask(a, I, J, acc, inv * inv);
     if (threadIdx.x == 0) sy.flags[(size_t)I * a.nsb + J] = f;
   }
 }
@@ -450,8 +473,8 @@ __global__ void __launch_bounds__(256) k_bsr_init_flags_diag(tb_bsr H, Args a, S
   double emax, inv;
   x0_affine(a, &emax, &inv);
   double acc[16];
-  block_partials([&](int r, int c) { return x0_blk(nullptr, I, I, a.n, r, c, emax, inv); }, acc);
-  const uint16_t f = keep_mask(a, I, I, acc);
+  block_partials([&](int r, int c) { return x0_unscaled(nullptr, I, I, a.n, r, c, emax); }, acc);
+  const uint16_t f = keep_mask(a, I, I, acc, inv * inv);
   if (threadIdx.x == 0) sy.flags[(size_t)I * a.nsb + I] = f;
 }
 
