@@ -1167,15 +1167,35 @@ __global__ void __launch_bounds__(256) k_h_blocks(ModelDev m, int N, const int32
   }
 }
 
+// Whether block row J's atom box can come within m.range of the point x under
+// the periodic images (k_blk_pattern's test with a box of zero extent).
+__device__ __forceinline__ bool box_in_range(const ModelDev& m, const BsrModelWs& w, int J, const double* x) {
+  double g2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double dc = w.bbox[6 * J + k] - x[k];
+    dc -= m.box * rint(dc / m.box);
+    const double hs = w.bbox[6 * J + 3 + k];
+    if (hs + m.range >= 0.5 * m.box) continue;
+    const double gap = fmax(0.0, fabs(dc) - hs);
+    g2 += gap * gap;
+  }
+  return g2 < m.range * m.range;
+}
+
 // Visit the atoms of the stored block columns of row I once each (consecutive
-// block rows share at most their straddling atom): fn(j).
+// block rows share at most their straddling atom): fn(j), skipping the blocks
+// whose atom box lies beyond m.range of the point x (their atoms, the
+// straddling one included, are out of range and contribute nothing).
 template <class Fn>
-__device__ __forceinline__ void for_neighbour_atoms(const tb_bsr& H, const BsrModelWs& w, int I, int lane, Fn fn) {
+__device__ __forceinline__ void for_neighbour_atoms(const tb_bsr& H, const BsrModelWs& w, const ModelDev& m, int I,
+                                                    const double* x, int lane, Fn fn) {
   int next = 0;
   for (int s = H.row_ptr[I]; s < H.row_ptr[I + 1]; ++s) {
     const int J = H.col[s];
     const int lo = max(next, w.atom_lo[J]), hi = w.atom_hi[J];
-    for (int j = lo + lane; j < hi; j += 32) fn(j);
+    if (box_in_range(m, w, J, x))
+      for (int j = lo + lane; j < hi; j += 32) fn(j);
     next = max(next, hi);
   }
 }
@@ -1190,7 +1210,7 @@ __global__ void __launch_bounds__(256) k_v_bsr(ModelDev m, int N, const int32_t*
   if (i >= N || *H.status != TB_OK) return;  // an overflowed pattern has no columns to visit
   const double* Ri = R + 3 * i;
   double s = 0.0;
-  for_neighbour_atoms(H, w, offs[i] / kBB, lane, [&](int j) {
+  for_neighbour_atoms(H, w, m, offs[i] / kBB, Ri, lane, [&](int j) {
     const double* Rj = R + 3 * j;
     if (j != i && !screen_f32(Ri, Rj, (float)m.box, (float)m.gcut)) return;
     double d0[3];
@@ -1250,7 +1270,7 @@ __global__ void __launch_bounds__(32) k_forces_bsr(ModelDev m, int N, const int3
   const double na = n_aux[a];
   double f[3] = {0.0, 0.0, 0.0};
   double e_band = 0.0, e_pair = 0.0;
-  for_neighbour_atoms(H, w, oa / kBB, lane, [&](int b) {
+  for_neighbour_atoms(H, w, m, oa / kBB, Ra, lane, [&](int b) {
     const double* Rb = R + 3 * b;
     if (b != a && !screen_f32(Ra, Rb, (float)m.box, (float)m.range)) return;
     const int tb = types[b], ob = offs[b];
