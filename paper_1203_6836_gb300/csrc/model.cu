@@ -1168,35 +1168,45 @@ __global__ void __launch_bounds__(256) k_h_blocks(ModelDev m, int N, const int32
 }
 
 // Whether block row J's atom box can come within m.range of the point x under
-// the periodic images (k_blk_pattern's test with a box of zero extent).
-__device__ __forceinline__ bool box_in_range(const ModelDev& m, const BsrModelWs& w, int J, const double* x) {
-  double g2 = 0.0;
+// the periodic images (k_blk_pattern's test with a box of zero extent), in
+// FP32 with a 1e-3 A margin, so that it errs only towards visiting a block.
+__device__ __forceinline__ bool box_in_range(const ModelDev& m, const BsrModelWs& w, int J, const float (&x)[3]) {
+  const float box = (float)m.box, reach = (float)m.range + 1e-3f;
+  float g2 = 0.0f;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    double dc = w.bbox[6 * J + k] - x[k];
-    dc -= m.box * rint(dc / m.box);
-    const double hs = w.bbox[6 * J + 3 + k];
-    if (hs + m.range >= 0.5 * m.box) continue;
-    const double gap = fmax(0.0, fabs(dc) - hs);
+    float dc = (float)w.bbox[6 * J + k] - x[k];
+    dc -= box * rintf(dc / box);
+    const float hs = (float)w.bbox[6 * J + 3 + k];
+    if (hs + reach >= 0.5f * box) continue;
+    const float gap = fmaxf(0.0f, fabsf(dc) - hs);
     g2 += gap * gap;
   }
-  return g2 < m.range * m.range;
+  return g2 < reach * reach;
 }
 
 // Visit the atoms of the stored block columns of row I once each (consecutive
 // block rows share at most their straddling atom): fn(j), skipping the blocks
 // whose atom box lies beyond m.range of the point x (their atoms, the
-// straddling one included, are out of range and contribute nothing).
+// straddling one included, are out of range and contribute nothing).  The
+// lanes test 32 blocks at a time.
 template <class Fn>
 __device__ __forceinline__ void for_neighbour_atoms(const tb_bsr& H, const BsrModelWs& w, const ModelDev& m, int I,
                                                     const double* x, int lane, Fn fn) {
+  const float xf[3] = {(float)x[0], (float)x[1], (float)x[2]};
+  const int s1 = H.row_ptr[I + 1];
   int next = 0;
-  for (int s = H.row_ptr[I]; s < H.row_ptr[I + 1]; ++s) {
-    const int J = H.col[s];
-    const int lo = max(next, w.atom_lo[J]), hi = w.atom_hi[J];
-    if (box_in_range(m, w, J, x))
-      for (int j = lo + lane; j < hi; j += 32) fn(j);
-    next = max(next, hi);
+  for (int s0 = H.row_ptr[I]; s0 < s1; s0 += 32) {
+    const bool near = s0 + lane < s1 && box_in_range(m, w, H.col[s0 + lane], xf);
+    const unsigned mask = __ballot_sync(0xffffffffu, near);
+    const int cnt = min(32, s1 - s0);
+    for (int t = 0; t < cnt; ++t) {
+      const int J = H.col[s0 + t];
+      const int lo = max(next, w.atom_lo[J]), hi = w.atom_hi[J];
+      if ((mask >> t) & 1u)
+        for (int j = lo + lane; j < hi; j += 32) fn(j);
+      next = max(next, hi);
+    }
   }
 }
 
