@@ -1087,12 +1087,32 @@ __global__ void k_blk_cols(int nsb, BsrModelWs w, tb_bsr H) {
     if (w.flags[(size_t)I * nsb + J]) H.col[o++] = J;
 }
 
+// Whether block row J's atom box can come within m.range of the point x under
+// the periodic images (k_blk_pattern's test with a box of zero extent), in
+// FP32 with a 1e-3 A margin, so that it errs only towards visiting a block.
+__device__ __forceinline__ bool box_in_range(const ModelDev& m, const BsrModelWs& w, int J, const float (&x)[3]) {
+  const float box = (float)m.box, reach = (float)m.range + 1e-3f;
+  float g2 = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float dc = (float)w.bbox[6 * J + k] - x[k];
+    dc -= box * rintf(dc / box);
+    const float hs = (float)w.bbox[6 * J + 3 + k];
+    if (hs + reach >= 0.5f * box) continue;
+    const float gap = fmaxf(0.0f, fabsf(dc) - hs);
+    g2 += gap * gap;
+  }
+  return g2 < reach * reach;
+}
+
 // The h elements of stored block o (one CTA per block, grid-stride): every
 // ordered atom pair (i, j) of the two rows, summed over the images within the
 // cut-off, onsite energies for i == j; each element belongs to one pair.
 __global__ void __launch_bounds__(256) k_h_blocks(ModelDev m, int N, const int32_t* __restrict__ types,
                                                   const int32_t* __restrict__ offs, const double* __restrict__ R,
                                                   BsrModelWs w, tb_bsr H) {
+  __shared__ int s_near[kBB];  // a block row holds at most kBB atoms (each has an orbital in it)
+  __shared__ int s_nnear;
   if (*H.status != TB_OK) return;
   const int nblk = H.row_ptr[H.nsb];
   for (int o = blockIdx.x; o < nblk; o += gridDim.x) {
@@ -1107,10 +1127,28 @@ __global__ void __launch_bounds__(256) k_h_blocks(ModelDev m, int N, const int32
     for (int e = threadIdx.x; e < kBB * kBB; e += blockDim.x) blk[e] = 0.0;
     __syncthreads();
     const int ilo = w.atom_lo[I], ihi = w.atom_hi[I], jlo = w.atom_lo[J], jhi = w.atom_hi[J];
-    const int nj = jhi - jlo, npair = (ihi - ilo) * nj;
+    // the atoms of row block I within range of column block J's atom box (the
+    // others only have zero elements in this block): one warp, ballots
+    if (threadIdx.x < 32) {
+      int cnt = 0;
+      for (int base = ilo; base < ihi; base += 32) {
+        const int i = base + (int)threadIdx.x;
+        bool ok = false;
+        if (i < ihi) {
+          const float xf[3] = {(float)R[3 * i], (float)R[3 * i + 1], (float)R[3 * i + 2]};
+          ok = box_in_range(m, w, J, xf);
+        }
+        const unsigned msk = __ballot_sync(0xffffffffu, ok);
+        if (ok) s_near[cnt + __popc(msk & ((1u << threadIdx.x) - 1u))] = i;
+        cnt += __popc(msk);
+      }
+      if (threadIdx.x == 0) s_nnear = cnt;
+    }
+    __syncthreads();
+    const int nj = jhi - jlo, npair = s_nnear * nj;
     const int r0 = I * kBB, c0 = J * kBB;
     for (int p = threadIdx.x; p < npair; p += blockDim.x) {
-      const int i = ilo + p / nj, j = jlo + p % nj;
+      const int i = s_near[p / nj], j = jlo + p % nj;
       const int ti = types[i], tj = types[j];
       const int ni = norb_of(ti), njo = norb_of(tj);
       const int oi = offs[i], oj = offs[j];
@@ -1165,24 +1203,6 @@ __global__ void __launch_bounds__(256) k_h_blocks(ModelDev m, int N, const int32
     }
     __syncthreads();
   }
-}
-
-// Whether block row J's atom box can come within m.range of the point x under
-// the periodic images (k_blk_pattern's test with a box of zero extent), in
-// FP32 with a 1e-3 A margin, so that it errs only towards visiting a block.
-__device__ __forceinline__ bool box_in_range(const ModelDev& m, const BsrModelWs& w, int J, const float (&x)[3]) {
-  const float box = (float)m.box, reach = (float)m.range + 1e-3f;
-  float g2 = 0.0f;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    float dc = (float)w.bbox[6 * J + k] - x[k];
-    dc -= box * rintf(dc / box);
-    const float hs = (float)w.bbox[6 * J + 3 + k];
-    if (hs + reach >= 0.5f * box) continue;
-    const float gap = fmaxf(0.0f, fabsf(dc) - hs);
-    g2 += gap * gap;
-  }
-  return g2 < reach * reach;
 }
 
 // Visit the atoms of the stored block columns of row I once each (consecutive
