@@ -1012,9 +1012,18 @@ __global__ void __launch_bounds__(kNumThreads<P>, 1)
         }
         const bool twice = mirror || (symd && c > q);
         t2 += twice ? 2.0 * u2 : u2;
-        float4* xo = reinterpret_cast<float4*>(xnew + 32 * c);
+        {
+          // the 32 x 32 sub-tile through shared memory (lane l holds row l), so
+          // that each warp store writes one row's 128 contiguous bytes
+          __syncwarp();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) xo[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
+          for (int j = 0; j < 32; ++j) s_sym[q][lane][j] = y[j];
+          __syncwarp();
+          float* rows = xnew - (size_t)lane * SB + 32 * c;  // row 32 q of the block, column 32 c
+#pragma unroll 8
+          for (int rr = 0; rr < 32; ++rr) rows[(size_t)rr * SB + lane] = s_sym[q][rr][lane];
+          __syncwarp();
+        }
         if constexpr (!kStaged<P>) store_operands<P>(y, hrow + 32 * c * C::eb, lrow + 32 * c * C::eb);
         if (twice) {
           // element (row, 32c + j) of block (I, J) is element (32c + j, row) of
