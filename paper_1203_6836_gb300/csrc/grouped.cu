@@ -104,7 +104,6 @@ __global__ void __launch_bounds__(FS ? kThreadsFs : kThreads, 1)
   __shared__ volatile int s_abort;
   __shared__ int s_sys, s_stop, s_br;
   __shared__ double s_red[kThreadsFs / 32][3];
-  __shared__ float s_tr[4][32][33];  // per epilogue warp: one 32 x 32 sub-tile in transposition
   __shared__ double s_t1, s_t2, s_lo, s_hi;
   __shared__ double s_hist[2][SP2_MAX_ITER + 2];
   __shared__ unsigned long long s_branch[2];
@@ -382,18 +381,9 @@ __global__ void __launch_bounds__(FS ? kThreadsFs : kThreads, 1)
               if (m0 + row == n0 + 32 * c + j) t1 += (double)y[j];
             }
             u2 += (double)c2;
-            {
-              // the 32 x 32 sub-tile through shared memory (lane l holds row l),
-              // so that each warp store writes one row's 128 contiguous bytes
-              __syncwarp();
+            float4* xo = reinterpret_cast<float4*>(xout + 32 * c);
 #pragma unroll
-              for (int j = 0; j < 32; ++j) s_tr[q][lane][j] = y[j];
-              __syncwarp();
-              float* rows = xout - (size_t)lane * ga.cols + 32 * c;  // row m0 + 32 q, column n0 + 32 c
-#pragma unroll 8
-              for (int rr = 0; rr < 32; ++rr) rows[(size_t)rr * ga.cols + lane] = s_tr[q][rr][lane];
-              __syncwarp();
-            }
+            for (int j = 0; j < 8; ++j) xo[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
             if constexpr (!FS) store_operands<P>(y, hrow + 32 * c * C::eb, lrow + 32 * c * C::eb);
             if (mirror) {
               // element (m0 + row, n0 + 32c + j) is also (n0 + 32c + j, m0 + row):
