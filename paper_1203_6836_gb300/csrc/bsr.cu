@@ -770,11 +770,20 @@ __global__ void __launch_bounds__(1024) k_bsr_order(Args a, Buf bn, Sym sy) {
     int pos = s_off[b];
     const int I0 = b * kBand;
     const int I = I0 + lane;
-    for (int J = I0; J < a.nsb; ++J) {
-      const bool has = lane < kBand && I < a.nsb && I <= J && ((sy.cand[I * MW + (J >> 5)] >> (J & 31)) & 1u);
-      const unsigned m = __ballot_sync(0xffffffffu, has);
-      if (has) sy.order[pos + __popc(m & ((1u << lane) - 1u))] = bn.row_ptr[I] + popc_below(sy.cand + I * MW, J);
-      pos += __popc(m);
+    // only the columns J >= I0 that some row of the band holds (the OR of the
+    // band's candidate words), in increasing order
+    for (int w = I0 >> 5; w < a.mw; ++w) {
+      uint32_t any = 0u;
+      for (int r = 0; r < kBand && I0 + r < a.nsb; ++r) any |= sy.cand[(I0 + r) * MW + w];
+      if (w == (I0 >> 5)) any &= ~((1u << (I0 & 31)) - 1u);
+      while (any) {
+        const int J = 32 * w + __ffs(any) - 1;
+        any &= any - 1u;
+        const bool has = lane < kBand && I < a.nsb && I <= J && ((sy.cand[I * MW + w] >> (J & 31)) & 1u);
+        const unsigned m = __ballot_sync(0xffffffffu, has);
+        if (has) sy.order[pos + __popc(m & ((1u << lane) - 1u))] = bn.row_ptr[I] + popc_below(sy.cand + I * MW, J);
+        pos += __popc(m);
+      }
     }
   }
 }
