@@ -290,3 +290,26 @@ def test_gapped_vapour_converges_and_conserves_energy_at_half_kappa0():
     assert min(tr.gap) > 1.0
     assert sigma < 5e-3 and abs(drift) < 0.05
     assert max(np.max(np.abs(a - b)) for a, b in zip(tr.n, tr.q)) < 0.02
+
+
+def test_isolated_clusters_geometry():
+    """The isolated-cluster workload's claims: rigid copies (every cluster has
+    the base cluster's interatomic distances), clusters more than 6 A (the
+    model's interaction range) apart under the periodic images, and, for the
+    oracle's h, no element between two clusters."""
+    from workloads import isolated_clusters, gapped_params
+    from oracle import tb
+    s = isolated_clusters(3)
+    nc, na = 27, 24
+    C = s.R.reshape(nc, na, 3)
+    d0 = np.linalg.norm(C[0][:, None] - C[0][None], axis=2)
+    for c in range(1, nc):
+        assert np.abs(np.linalg.norm(C[c][:, None] - C[c][None], axis=2) - d0).max() < 1e-12
+    d = s.R[:, None, :] - s.R[None, :, :]
+    d -= s.box * np.round(d / s.box)
+    dist = np.linalg.norm(d, axis=2)
+    cl = np.repeat(np.arange(nc), na)
+    assert dist[cl[:, None] != cl[None, :]].min() > 6.0
+    h = tb.build_h(s.R, s.types, s.box, gapped_params())
+    oc = np.repeat(np.arange(nc), 48)
+    assert np.count_nonzero(h[oc[:, None] != oc[None, :]]) == 0
