@@ -64,7 +64,7 @@ constexpr bool kStaged = P == TB_PREC_TF32X3;
 template <int P>
 constexpr int kNumThreads = kStaged<P> ? 320 : kThreads;
 constexpr int kTiles = SB * SB;    // elements per super-block
-constexpr int kMaxGrid = 256;      // persistent numeric grid (<= SMs)
+constexpr int kMaxGrid = 256;      // cap of the persistent numeric grid (which is also at most the SM count)
 constexpr int kBand = 8;           // block rows whose outputs the numeric kernel walks together
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -76,7 +76,7 @@ struct Buf {
   uint32_t* stored;  // [nsb * MW]
   uint32_t* live;    // [nsb * MW]
   float* val;        // [cap * kTiles] FP32 master
-  void* hi;          // [cap * kTiles] operands
+  void* hi;          // [cap * kTiles] stored operand splits (null with kStaged)
   void* lo;
 };
 
